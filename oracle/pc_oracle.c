@@ -1,0 +1,452 @@
+/*
+ * FP64 CPU oracle for the Lienard-Wiechert hot path of PyCharge (arXiv 2107.12437).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py may load this file.  It shares no code, header, table or
+ * constant generator with the CUDA library; it is plain, slow and literal on purpose.
+ *
+ * What it computes, and where the paper defines it:
+ *   - retarded time t' = t - R(t')/c  (Sec. 2.1, Eq. ret_t), solved here by plain bisection on the
+ *     delay tau = t - t' (the paper uses a secant method; both converge to the unique root of the
+ *     same piecewise-linear trajectory, Sec. 3.1: discrete histories are linearly interpolated);
+ *   - Lienard-Wiechert potentials and fields in Jackson's notation (Sec. 2.1, Eqs. V, A, E, B and
+ *     the Coulomb / radiation split Eqs. ECoulomb, Eradiation).  Reading of Eq. A: the printed
+ *     mu0 q/(4 pi) [beta/(kappa R)] lacks a factor c; we use A = mu0 q c beta / (4 pi kappa R),
+ *     which equals (v/c^2) Phi.  A second, independent evaluation in Griffiths' notation
+ *     (footnote to Sec. 2.1) is exposed for a consistency check;
+ *   - superposition over all charges (Sec. 2.2);
+ *   - dipole charges from the dipole moment (Sec. 2.3, Eqs. eff_mass, r_1, r_2), static for t <= 0
+ *     (Sec. 3.2);
+ *   - the Lorentz-oscillator run of Algorithm 1 with the equation of motion Eq. LO_equation,
+ *     RK4 in time, driving field E_d = p . E at the dipole origin from all other dipoles (Sec. 2.3,
+ *     Sec. 3.2), energy Eq. dipoleE, velocity guard (Sec. 3.2, default c/100).
+ *
+ * Units: SI throughout, all arithmetic in double precision.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* CODATA 2018 exact / recommended values */
+#define ORC_C 299792458.0
+#define ORC_EPS0 8.8541878128e-12
+#define ORC_PI 3.14159265358979323846
+
+/* oracle status codes (independent of the library's codes) */
+enum {
+  ORC_OK = 0,
+  ORC_ERR_ARG = 1,
+  ORC_ERR_HISTORY = 2,   /* retarded time before the first sample (no static extension) or after the last */
+  ORC_ERR_VELOCITY = 3,  /* a dipole charge exceeded v_max */
+  ORC_ERR_CAUSALITY = 4, /* a stage time needs history that is not computed yet */
+  ORC_ERR_NOCONV = 5
+};
+
+/* field kinds (Sec. 3.2: calculate_E/B select total, Coulomb or radiation) */
+enum { ORC_TOTAL = 0, ORC_COULOMB = 1, ORC_RADIATION = 2 };
+
+typedef struct {
+  /* point charges with sampled trajectories: sample k is at time t0 + k dt */
+  int32_t M;
+  int64_t S;
+  double t0, dt;
+  const double *q;             /* [M] */
+  const double *pos, *vel, *acc; /* [M][S][3] */
+  int32_t static_before;       /* 1: at rest at sample 0 for t < t0; 0: error */
+  /* dipoles (Lorentz oscillators): moment history along a fixed unit axis */
+  int32_t N;
+  int64_t Sd;                  /* samples per dipole */
+  double t0d, dtd;
+  const double *origin;        /* [N][3] centre of mass R */
+  const double *axis;          /* [N][3] unit polarisation axis */
+  const double *qd, *m1, *m2;  /* [N] charge magnitude and the two masses */
+  const double *d, *d_dot, *d_ddot; /* [N][Sd] moment along axis, C m, and its derivatives */
+  int64_t last_valid;          /* dipole samples 0..last_valid are known; -1 = all */
+} orc_sources;
+
+static inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static inline void cross3(const double *a, const double *b, double *o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+int orc_n_charges(const orc_sources *s) { return s->M + 2 * s->N; }
+
+/*
+ * State (charge, position, velocity, acceleration) of charge c at time tp.
+ * Charges 0..M-1 are the sampled ones; charge M + 2j is the positive charge of dipole j (Eq. r_1),
+ * M + 2j + 1 its negative charge (Eq. r_2).  Between samples every quantity is linearly
+ * interpolated (Sec. 3.1).
+ */
+static int charge_state(const orc_sources *s, int c, double tp, double *qc, double p[3], double v[3], double a[3]) {
+  if (c < s->M) {
+    const double *P = s->pos + (int64_t)c * s->S * 3;
+    const double *V = s->vel + (int64_t)c * s->S * 3;
+    const double *A = s->acc + (int64_t)c * s->S * 3;
+    *qc = s->q[c];
+    double x = (tp - s->t0) / s->dt;
+    /* the edge times t0 and t0 + (S-1) dt are rounded doubles: snap within 1e-9 step of an edge */
+    if (x < 0.0 && x > -1e-9) x = 0.0;
+    if (x > (double)(s->S - 1) && x < (double)(s->S - 1) + 1e-9) x = (double)(s->S - 1);
+    if (x < 0.0) {
+      if (!s->static_before) return ORC_ERR_HISTORY;
+      for (int i = 0; i < 3; ++i) { p[i] = P[i]; v[i] = 0.0; a[i] = 0.0; }
+      return ORC_OK;
+    }
+    int64_t k = (int64_t)floor(x);
+    if (k >= s->S - 1) {
+      if (x > (double)(s->S - 1)) return ORC_ERR_HISTORY;
+      k = s->S - 2; /* exactly at the last sample */
+    }
+    double th = x - (double)k;
+    for (int i = 0; i < 3; ++i) {
+      p[i] = P[k * 3 + i] + th * (P[(k + 1) * 3 + i] - P[k * 3 + i]);
+      v[i] = V[k * 3 + i] + th * (V[(k + 1) * 3 + i] - V[k * 3 + i]);
+      a[i] = A[k * 3 + i] + th * (A[(k + 1) * 3 + i] - A[k * 3 + i]);
+    }
+    return ORC_OK;
+  }
+  int j = (c - s->M) / 2;
+  int neg = (c - s->M) % 2;
+  double m1 = s->m1[j], m2 = s->m2[j], q = s->qd[j];
+  const double *u = s->axis + 3 * j;
+  const double *R = s->origin + 3 * j;
+  double dd, dv, da;
+  double x = (tp - s->t0d) / s->dtd;
+  const double *D = s->d + (int64_t)j * s->Sd;
+  const double *DV = s->d_dot + (int64_t)j * s->Sd;
+  const double *DA = s->d_ddot + (int64_t)j * s->Sd;
+  if (x <= 0.0) {
+    /* stationary dipole moment for t <= t0 (Sec. 3.2) */
+    dd = D[0]; dv = 0.0; da = 0.0;
+  } else {
+    int64_t last = (s->last_valid >= 0) ? s->last_valid : (s->Sd - 1);
+    if (x > (double)last && x < (double)last + 1e-9) x = (double)last;
+    int64_t k = (int64_t)floor(x);
+    if (k >= last) {
+      if (x > (double)last) return (s->last_valid >= 0) ? ORC_ERR_CAUSALITY : ORC_ERR_HISTORY;
+      k = last - 1;
+    }
+    double th = x - (double)k;
+    dd = D[k] + th * (D[k + 1] - D[k]);
+    dv = DV[k] + th * (DV[k + 1] - DV[k]);
+    da = DA[k] + th * (DA[k + 1] - DA[k]);
+  }
+  /* r_dip = d / q along the axis; r_1 = R + m2/(m1+m2) r_dip, r_2 = R - m1/(m1+m2) r_dip */
+  double w = neg ? -m1 / (m1 + m2) : m2 / (m1 + m2);
+  *qc = neg ? -q : q;
+  for (int i = 0; i < 3; ++i) {
+    p[i] = R[i] + w * (dd / q) * u[i];
+    v[i] = w * (dv / q) * u[i];
+    a[i] = w * (da / q) * u[i];
+  }
+  return ORC_OK;
+}
+
+/*
+ * Retarded time t' of charge c seen from r at time t: the root of
+ * g(t') = c (t - t') - |r - r_c(t')|  (Eq. ret_t).  g(t) <= 0 and g is strictly decreasing in t' while
+ * the charge is slower than light, so plain bisection on a bracket [t'_lo, t'_hi] with
+ * g(t'_lo) >= 0 >= g(t'_hi) converges to the unique root; it stops when the bracket cannot shrink.
+ * The bracket is kept inside the stored history: before the first sample a charge either rests at
+ * its first position (static extension) or the call fails with ORC_ERR_HISTORY; a root after the
+ * last known sample fails with ORC_ERR_HISTORY, or ORC_ERR_CAUSALITY during a dipole run.
+ */
+static double g_at(const orc_sources *s, int c, double t, const double r[3], double tp, int *st) {
+  double qc, p[3], v[3], a[3];
+  *st = charge_state(s, c, tp, &qc, p, v, a);
+  double D[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+  return ORC_C * (t - tp) - sqrt(dot3(D, D));
+}
+
+int orc_retarded_time(const orc_sources *s, int c, double t, const double r[3], double *tp_out) {
+  int st;
+  int sampled = (c < s->M);
+  double t_first = sampled ? s->t0 : s->t0d;
+  double t_last;
+  if (sampled) t_last = s->t0 + (double)(s->S - 1) * s->dt;
+  else t_last = s->t0d + (double)((s->last_valid >= 0) ? s->last_valid : (s->Sd - 1)) * s->dtd;
+  int err_late = (!sampled && s->last_valid >= 0) ? ORC_ERR_CAUSALITY : ORC_ERR_HISTORY;
+  double hi = (t < t_last) ? t : t_last;
+  double lo;
+  if (sampled && !s->static_before) {
+    lo = t_first;
+    if (lo > hi) return ORC_ERR_HISTORY;
+    double g = g_at(s, c, t, r, lo, &st);
+    if (st) return st;
+    if (g < 0.0) return ORC_ERR_HISTORY;   /* the root precedes the first sample */
+  } else {
+    /* before the first sample the charge rests at its first position */
+    double qc, p[3], v[3], a[3];
+    st = charge_state(s, c, (t < t_first) ? t : t_first, &qc, p, v, a);
+    if (st) return st;
+    double D[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+    lo = t - sqrt(dot3(D, D)) / ORC_C * (1.0 + 1e-12) - 1e-30;
+    if (lo > t_first) lo = t_first;
+    if (lo > hi) lo = hi;
+  }
+  if (hi < t) {
+    double g = g_at(s, c, t, r, hi, &st);
+    if (st) return st;
+    if (g > 0.0) return err_late;           /* the root lies after the last known sample */
+    if (g == 0.0) { *tp_out = hi; return ORC_OK; }
+  }
+  for (int it = 0; it < 4000; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    double g = g_at(s, c, t, r, mid, &st);
+    if (st) return st;
+    if (g >= 0.0) lo = mid; else hi = mid;
+  }
+  *tp_out = 0.5 * (lo + hi);
+  return ORC_OK;
+}
+
+int orc_retarded_delay(const orc_sources *s, int c, double t, const double r[3], double *tau_out) {
+  double tp;
+  int st = orc_retarded_time(s, c, t, r, &tp);
+  if (st) return st;
+  *tau_out = t - tp;
+  return ORC_OK;
+}
+
+/*
+ * Lienard-Wiechert fields and potentials of one charge, Jackson's notation (Eqs. V, A, E, B).
+ * aR = r - r_p(t'), v and acc at t'.  Outputs are added into Ec (Coulomb E), Er (radiation E),
+ * phi and A.
+ */
+static void lw_jackson(double q, const double aR[3], const double v[3], const double acc[3], double Ec[3],
+                       double Er[3], double *phi, double A[3]) {
+  double R = sqrt(dot3(aR, aR));
+  double n[3] = {aR[0] / R, aR[1] / R, aR[2] / R};
+  double beta[3] = {v[0] / ORC_C, v[1] / ORC_C, v[2] / ORC_C};
+  double bdot[3] = {acc[0] / ORC_C, acc[1] / ORC_C, acc[2] / ORC_C};
+  double kappa = 1.0 - dot3(n, beta);
+  double b2 = dot3(beta, beta);
+  double k = q / (4.0 * ORC_PI * ORC_EPS0);
+  double nb[3] = {n[0] - beta[0], n[1] - beta[1], n[2] - beta[2]};
+  double k3 = kappa * kappa * kappa;
+  /* Coulomb term: (n - beta)(1 - beta^2) / (kappa^3 R^2) */
+  for (int i = 0; i < 3; ++i) Ec[i] = k * nb[i] * (1.0 - b2) / (k3 * R * R);
+  /* radiation term: n x ((n - beta) x beta_dot) / (c kappa^3 R) */
+  double w[3], nw[3];
+  cross3(nb, bdot, w);
+  cross3(n, w, nw);
+  for (int i = 0; i < 3; ++i) Er[i] = k * nw[i] / (ORC_C * k3 * R);
+  *phi = k / (kappa * R);
+  double mu0 = 1.0 / (ORC_EPS0 * ORC_C * ORC_C);
+  for (int i = 0; i < 3; ++i) A[i] = mu0 * q * ORC_C / (4.0 * ORC_PI) * beta[i] / (kappa * R);
+}
+
+/*
+ * The same field in Griffiths' notation: E = q/(4 pi eps0) R/(aR.u)^3 [(c^2 - v^2) u + aR x (u x acc)],
+ * u = c n - v.  Used only to cross-check lw_jackson.
+ */
+void orc_lw_griffiths(double q, const double aR[3], const double v[3], const double acc[3], double E[3],
+                      double B[3]) {
+  double R = sqrt(dot3(aR, aR));
+  double u[3];
+  for (int i = 0; i < 3; ++i) u[i] = ORC_C * aR[i] / R - v[i];
+  double Ru = dot3(aR, u);
+  double f = q / (4.0 * ORC_PI * ORC_EPS0) * R / (Ru * Ru * Ru);
+  double c2v2 = ORC_C * ORC_C - dot3(v, v);
+  double ua[3], rua[3];
+  cross3(u, acc, ua);
+  cross3(aR, ua, rua);
+  for (int i = 0; i < 3; ++i) E[i] = f * (c2v2 * u[i] + rua[i]);
+  double n[3] = {aR[0] / R, aR[1] / R, aR[2] / R};
+  double nE[3];
+  cross3(n, E, nE);
+  for (int i = 0; i < 3; ++i) B[i] = nE[i] / ORC_C;
+}
+
+void orc_lw_jackson(double q, const double aR[3], const double v[3], const double acc[3], double Ec[3], double Er[3],
+                    double *phi, double A[3]) {
+  lw_jackson(q, aR, v, acc, Ec, Er, phi, A);
+}
+
+/*
+ * Fields at one point r and time t, summed over all charges except those of dipole `exclude`
+ * (-1: none).  A charge closer than r_excl at its retarded position contributes nothing and sets
+ * *mask.  Outputs are overwritten.
+ */
+static int fields_at(const orc_sources *s, const double r[3], double t, int kind, double r_excl, int exclude,
+                     double E[3], double B[3], double *phi, double A[3], uint8_t *mask) {
+  int nc = orc_n_charges(s);
+  for (int i = 0; i < 3; ++i) { E[i] = 0.0; B[i] = 0.0; A[i] = 0.0; }
+  *phi = 0.0;
+  *mask = 0;
+  for (int c = 0; c < nc; ++c) {
+    if (exclude >= 0 && c >= s->M && (c - s->M) / 2 == exclude) continue;
+    double tp;
+    int st = orc_retarded_time(s, c, t, r, &tp);
+    if (st) return st;
+    double qc, p[3], v[3], a[3];
+    st = charge_state(s, c, tp, &qc, p, v, a);
+    if (st) return st;
+    double aR[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+    double R = sqrt(dot3(aR, aR));
+    if (R <= r_excl) { *mask = 1; continue; }
+    double Ec[3], Er[3], ph, Ac[3];
+    lw_jackson(qc, aR, v, a, Ec, Er, &ph, Ac);
+    double Ek[3];
+    for (int i = 0; i < 3; ++i)
+      Ek[i] = (kind == ORC_COULOMB) ? Ec[i] : (kind == ORC_RADIATION) ? Er[i] : Ec[i] + Er[i];
+    double n[3] = {aR[0] / R, aR[1] / R, aR[2] / R}, nE[3];
+    cross3(n, Ek, nE);
+    for (int i = 0; i < 3; ++i) {
+      E[i] += Ek[i];
+      B[i] += nE[i] / ORC_C; /* Eq. B */
+      A[i] += Ac[i];
+    }
+    *phi += ph;
+  }
+  return ORC_OK;
+}
+
+/*
+ * Fields on P points at T times: E, B, A [T][P][3], phi [T][P], mask [T][P] (Sec. 2.2, Sec. 3.2).
+ */
+int orc_fields(const orc_sources *s, const double *points, int64_t P, const double *times, int32_t T, int32_t kind,
+               double r_excl, double *E, double *B, double *phi, double *A, uint8_t *mask, int32_t nthreads) {
+  if (kind < 0 || kind > 2 || P < 0 || T < 0) return ORC_ERR_ARG;
+  int status = ORC_OK;
+  int64_t total = P * (int64_t)T;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+#endif
+  for (int64_t idx = 0; idx < total; ++idx) {
+    int64_t f = idx / P, pidx = idx % P;
+    int st = fields_at(s, points + 3 * pidx, times[f], kind, r_excl, -1, E + 3 * idx, B + 3 * idx, phi + idx,
+                       A + 3 * idx, mask + idx);
+    if (st) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      if (status == ORC_OK) status = st;
+    }
+  }
+  (void)nthreads;
+  return status;
+}
+
+/*
+ * Lorentz-oscillator run, Algorithm 1, for one configuration of N dipoles.
+ *
+ * Dipole i: origin R_i, unit axis p_i, charges +-q_i with masses m1_i (positive) and m2_i
+ * (negative), natural frequency omega0_i, initial moment d0_i along p_i (d = q r_dip, Sec. 2.3).
+ * Equation of motion (Eq. LO_equation) projected on p_i:
+ *     d'' + gamma0 d' + omega0^2 d = (q^2/m) E_d(t),  gamma0 = q^2 omega0^2 / (6 pi eps0 c^3 m),
+ *     m = m1 m2 / (m1 + m2)  (Eq. eff_mass),
+ * E_d = p_i . E(R_i, t) summed over every other dipole's two charges (Sec. 3.2).
+ * RK4 on y = (d, d'); with ed_mode == 0 E_d is evaluated at each RK4 stage time t, t + dt/2, t + dt,
+ * with ed_mode == 1 it is held at its value at t for all stages.
+ * History: d, d', d'' at t_n = n dt; the dipoles are stationary for t <= 0 (d = d0, d' = d'' = 0).
+ * After each step d''_{n+1} is taken from the equation of motion at t_{n+1}.
+ * Energy (Eq. dipoleE): m omega0^2 d^2 / (2 q^2) + m d'^2 / (2 q^2).
+ * The run stops with ORC_ERR_VELOCITY if a charge exceeds v_max (Sec. 3.2).
+ *
+ * Outputs d, dd, ddd, energy, Ed: [N][n_steps + 1] (Ed may be NULL).
+ */
+int orc_dipoles_run(int32_t N, const double *origin, const double *axis, const double *q, const double *m1,
+                    const double *m2, const double *omega0, const double *d0, double dt, int64_t n_steps,
+                    double v_max, int32_t ed_mode, double *d, double *dd, double *ddd, double *energy, double *Ed,
+                    int32_t nthreads) {
+  if (N <= 0 || n_steps < 0 || !(dt > 0.0)) return ORC_ERR_ARG;
+  int64_t S = n_steps + 1;
+  orc_sources s;
+  memset(&s, 0, sizeof(s));
+  s.N = N; s.Sd = S; s.t0d = 0.0; s.dtd = dt;
+  s.origin = origin; s.axis = axis; s.qd = q; s.m1 = m1; s.m2 = m2;
+  s.d = d; s.d_dot = dd; s.d_ddot = ddd;
+  double *ed_now = (double *)calloc((size_t)N, sizeof(double));
+  double *ed_half = (double *)calloc((size_t)N, sizeof(double));
+  double *ed_next = (double *)calloc((size_t)N, sizeof(double));
+  if (!ed_now || !ed_half || !ed_next) { free(ed_now); free(ed_half); free(ed_next); return ORC_ERR_ARG; }
+  for (int i = 0; i < N; ++i) {
+    d[(int64_t)i * S] = d0[i];
+    dd[(int64_t)i * S] = 0.0;
+    ddd[(int64_t)i * S] = 0.0;
+  }
+  int status = ORC_OK;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#endif
+  for (int64_t n = 0; n < n_steps && status == ORC_OK; ++n) {
+    s.last_valid = n;
+    double t = n * dt;
+    int st_loop = ORC_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+    for (int i = 0; i < N; ++i) {
+      double E[3], B[3], ph, A[3];
+      uint8_t mk;
+      int st = ORC_OK;
+      const double *p = axis + 3 * i;
+      if (n == 0) {
+        st = fields_at(&s, origin + 3 * i, t, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk);
+        ed_now[i] = dot3(p, E);
+        if (Ed) Ed[(int64_t)i * S] = ed_now[i];
+      }
+      if (!st) {
+        st = fields_at(&s, origin + 3 * i, t + 0.5 * dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk);
+        ed_half[i] = dot3(p, E);
+      }
+      if (!st) {
+        st = fields_at(&s, origin + 3 * i, t + dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk);
+        ed_next[i] = dot3(p, E);
+      }
+      if (st) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        if (st_loop == ORC_OK) st_loop = st;
+      }
+    }
+    if (st_loop) { status = st_loop; break; }
+    for (int i = 0; i < N; ++i) {
+      double m = m1[i] * m2[i] / (m1[i] + m2[i]);
+      double w0 = omega0[i];
+      double g0 = q[i] * q[i] * w0 * w0 / (6.0 * ORC_PI * ORC_EPS0 * ORC_C * ORC_C * ORC_C * m);
+      double qm = q[i] * q[i] / m;
+      double e1 = ed_now[i];
+      double e2 = (ed_mode == 1) ? ed_now[i] : ed_half[i];
+      double e4 = (ed_mode == 1) ? ed_now[i] : ed_next[i];
+      double y0 = d[(int64_t)i * S + n], y1 = dd[(int64_t)i * S + n];
+      /* f(t, d, d') = (d', -gamma0 d' - omega0^2 d + (q^2/m) E_d(t)) */
+      double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
+      double k2a = y1 + 0.5 * dt * k1b, k2b = -g0 * (y1 + 0.5 * dt * k1b) - w0 * w0 * (y0 + 0.5 * dt * k1a) + qm * e2;
+      double k3a = y1 + 0.5 * dt * k2b, k3b = -g0 * (y1 + 0.5 * dt * k2b) - w0 * w0 * (y0 + 0.5 * dt * k2a) + qm * e2;
+      double k4a = y1 + dt * k3b, k4b = -g0 * (y1 + dt * k3b) - w0 * w0 * (y0 + dt * k3a) + qm * e4;
+      double yn0 = y0 + dt / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+      double yn1 = y1 + dt / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+      d[(int64_t)i * S + n + 1] = yn0;
+      dd[(int64_t)i * S + n + 1] = yn1;
+      /* d'' at the step end from the equation of motion (field at t_{n+1}) */
+      ddd[(int64_t)i * S + n + 1] = qm * ed_next[i] - g0 * yn1 - w0 * w0 * yn0;
+      if (Ed) Ed[(int64_t)i * S + n + 1] = ed_next[i];
+      double vmax_charge = fabs(yn1) / q[i] * ((m1[i] > m2[i] ? m1[i] : m2[i]) / (m1[i] + m2[i]));
+      if (vmax_charge > v_max) status = ORC_ERR_VELOCITY;
+      ed_now[i] = ed_next[i];
+    }
+  }
+  for (int i = 0; i < N; ++i) {
+    double m = m1[i] * m2[i] / (m1[i] + m2[i]);
+    for (int64_t n = 0; n < S; ++n) {
+      double x = d[(int64_t)i * S + n], xv = dd[(int64_t)i * S + n];
+      energy[(int64_t)i * S + n] = m * omega0[i] * omega0[i] * x * x / (2.0 * q[i] * q[i]) + m * xv * xv / (2.0 * q[i] * q[i]);
+    }
+  }
+  free(ed_now); free(ed_half); free(ed_next);
+  return status;
+}
+
+/* sizeof check for the Python binding */
+int64_t orc_sources_size(void) { return (int64_t)sizeof(orc_sources); }

@@ -1,0 +1,290 @@
+"""Seeded synthetic inputs for the Lienard-Wiechert field grid and the Lorentz-oscillator runs.
+
+This module only draws and lays out inputs: positions, axes, prescribed trajectories and
+parameters.  It holds none of the method's arithmetic (no retarded time, no field, no
+equation of motion), so that both the CUDA path and the CPU oracle can take their inputs from
+here without sharing any of the computation.
+
+Shapes follow the paper's workloads (arXiv 2107.12437):
+  * Sec. 4.1 / Listing 1: point charges with predefined trajectories on a planar grid;
+  * Sec. 4.2 / Listing 2: Lorentz oscillators with charges +-e, electron masses, dt = 1e-18 s.
+All arrays are float64 numpy arrays in SI units.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# CODATA 2018 (exact SI values for c and e)
+C = 299792458.0
+E_CHARGE = 1.602176634e-19
+M_E = 9.1093837015e-31
+EPS0 = 8.8541878128e-12
+
+SEED_CFG2 = 2107
+SEED_CFG4 = 12437
+SEED_CFG5 = 210712437
+
+
+@dataclasses.dataclass
+class Charges:
+    """Point charges with sampled trajectories: sample k at time t0 + k dt."""
+
+    q: np.ndarray  # [M]
+    pos: np.ndarray  # [M][S][3]
+    vel: np.ndarray  # [M][S][3]
+    acc: np.ndarray  # [M][S][3]
+    t0: float
+    dt: float
+    static_before: int = 0
+
+    @property
+    def M(self) -> int:
+        return int(self.q.shape[0])
+
+    @property
+    def S(self) -> int:
+        return int(self.pos.shape[1])
+
+
+@dataclasses.dataclass
+class Dipoles:
+    """Dipole sources: moment d(t) along a fixed unit axis, samples at t0 + n dt."""
+
+    origin: np.ndarray  # [N][3]
+    axis: np.ndarray  # [N][3]
+    q: np.ndarray  # [N]
+    m1: np.ndarray  # [N] mass of the positive charge
+    m2: np.ndarray  # [N] mass of the negative charge
+    d: np.ndarray  # [N][S]
+    d_dot: np.ndarray  # [N][S]
+    d_ddot: np.ndarray  # [N][S]
+    t0: float
+    dt: float
+
+    @property
+    def N(self) -> int:
+        return int(self.origin.shape[0])
+
+    @property
+    def S(self) -> int:
+        return int(self.d.shape[1])
+
+
+@dataclasses.dataclass
+class LOConfig:
+    """A batch of B independent Lorentz-oscillator configurations of N dipoles each."""
+
+    origin: np.ndarray  # [B][N][3]
+    axis: np.ndarray  # [B][N][3]
+    q: np.ndarray  # [B][N]
+    m1: np.ndarray  # [B][N]
+    m2: np.ndarray  # [B][N]
+    omega0: np.ndarray  # [B][N]
+    d0: np.ndarray  # [B][N] initial moment along the axis
+    dt: float
+    n_steps: int
+    first_index: int
+
+    @property
+    def B(self) -> int:
+        return int(self.origin.shape[0])
+
+    @property
+    def N(self) -> int:
+        return int(self.origin.shape[1])
+
+
+def unit_vectors(rng: np.random.Generator, n: int) -> np.ndarray:
+    v = rng.standard_normal((n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# Field-grid workloads
+# ----------------------------------------------------------------------------------------------
+def plane_grid(x: np.ndarray, y: np.ndarray, z: float) -> np.ndarray:
+    """Points [len(x)*len(y)][3], x the slow index (numpy meshgrid 'ij' order)."""
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1).astype(np.float64)
+
+
+def orbit_pair(dt: float = 1e-18, t_end: float = 10e-15, radius: float = 1e-9, beta: float = 0.1):
+    """Static +e at the origin and -e on a circle of the given radius in the z = 0 plane.
+
+    Angular speed beta c / radius; position, velocity and acceleration sampled exactly.
+    """
+    S = int(round(t_end / dt)) + 1
+    t = np.arange(S) * dt
+    w = beta * C / radius
+    pos = np.zeros((2, S, 3))
+    vel = np.zeros((2, S, 3))
+    acc = np.zeros((2, S, 3))
+    pos[1, :, 0] = radius * np.cos(w * t)
+    pos[1, :, 1] = radius * np.sin(w * t)
+    vel[1, :, 0] = -radius * w * np.sin(w * t)
+    vel[1, :, 1] = radius * w * np.cos(w * t)
+    acc[1, :, 0] = -radius * w * w * np.cos(w * t)
+    acc[1, :, 1] = -radius * w * w * np.sin(w * t)
+    q = np.array([E_CHARGE, -E_CHARGE])
+    return Charges(q=q, pos=pos, vel=vel, acc=acc, t0=0.0, dt=dt, static_before=1)
+
+
+def cfg1(n_grid: int = 101):
+    """Two charges (static +e at the origin, -e on a 1 nm orbit at 0.1 c), grid +-50 nm, t = 10 fs."""
+    ch = orbit_pair()
+    g = np.linspace(-50e-9, 50e-9, n_grid)
+    points = plane_grid(g, g, 0.0)
+    times = np.array([10e-15])
+    return ch, points, times
+
+
+def sinusoidal_dipoles(origin, axis, omega0, amp, dt, t_end, q=E_CHARGE):
+    """Dipoles whose charge separation is amp*sin(omega0 t) along the axis: d = q amp sin(omega0 t)."""
+    N = origin.shape[0]
+    S = int(round(t_end / dt)) + 1
+    t = np.arange(S) * dt
+    s = amp * np.sin(omega0 * t)
+    sd = amp * omega0 * np.cos(omega0 * t)
+    sdd = -amp * omega0 * omega0 * np.sin(omega0 * t)
+    ones = np.ones((N, 1))
+    return Dipoles(
+        origin=np.ascontiguousarray(origin, dtype=np.float64),
+        axis=np.ascontiguousarray(axis, dtype=np.float64),
+        q=np.full(N, q),
+        m1=np.full(N, M_E),
+        m2=np.full(N, M_E),
+        d=q * ones * s[None, :],
+        d_dot=q * ones * sd[None, :],
+        d_ddot=q * ones * sdd[None, :],
+        t0=0.0,
+        dt=dt,
+    )
+
+
+def cfg2(n_grid: int = 2048, n_frames: int = 16, n_dipoles: int = 64, t_end: float = 15e-15):
+    """64 oscillating dipoles (128 charges +-e) in a 1 um cube, 2048^2 plane grid at z = 0.5 um, 16 frames."""
+    rng = np.random.default_rng(SEED_CFG2)
+    origin = rng.uniform(0.0, 1e-6, size=(n_dipoles, 3))
+    axis = unit_vectors(rng, n_dipoles)
+    omega0 = 2 * math.pi * 200e12
+    dp = sinusoidal_dipoles(origin, axis, omega0, 1e-11, 1e-18, t_end)
+    g = np.linspace(0.0, 1e-6, n_grid)
+    times = 10e-15 + np.arange(n_frames) * (5e-15 / 16)
+    return dp, g, 0.5e-6, times
+
+
+def dipoles_as_charges(dp: Dipoles) -> Charges:
+    """The same sinusoidal sources written as independent charges +q at R + s/2 u, -q at R - s/2 u.
+
+    Valid for the equal-mass sinusoidal sources built by sinusoidal_dipoles (the separation s is
+    d/q and each charge sits s/2 from the origin); used to feed the generic-charge path.
+    """
+    N, S = dp.N, dp.S
+    s = dp.d / dp.q[:, None]
+    sd = dp.d_dot / dp.q[:, None]
+    sdd = dp.d_ddot / dp.q[:, None]
+    pos = np.zeros((2 * N, S, 3))
+    vel = np.zeros((2 * N, S, 3))
+    acc = np.zeros((2 * N, S, 3))
+    q = np.zeros(2 * N)
+    for j in range(N):
+        u = dp.axis[j]
+        for k, sign in ((2 * j, 1.0), (2 * j + 1, -1.0)):
+            pos[k] = dp.origin[j][None, :] + sign * 0.5 * s[j][:, None] * u[None, :]
+            vel[k] = sign * 0.5 * sd[j][:, None] * u[None, :]
+            acc[k] = sign * 0.5 * sdd[j][:, None] * u[None, :]
+            q[k] = sign * dp.q[j]
+    return Charges(q=q, pos=pos, vel=vel, acc=acc, t0=dp.t0, dt=dp.dt, static_before=1)
+
+
+# ----------------------------------------------------------------------------------------------
+# Lorentz-oscillator workloads
+# ----------------------------------------------------------------------------------------------
+def lo_batch(origins, axes, omega0, r_dip0, dt, n_steps, first_index, q=E_CHARGE, m=M_E) -> LOConfig:
+    origins = np.asarray(origins, dtype=np.float64)
+    axes = np.asarray(axes, dtype=np.float64)
+    B, N = origins.shape[:2]
+    om = np.broadcast_to(np.asarray(omega0, dtype=np.float64), (B, N)).copy()
+    return LOConfig(
+        origin=origins.copy(),
+        axis=axes.copy(),
+        q=np.full((B, N), q),
+        m1=np.full((B, N), m),
+        m2=np.full((B, N), m),
+        omega0=om,
+        d0=np.full((B, N), q * r_dip0),
+        dt=dt,
+        n_steps=n_steps,
+        first_index=first_index,
+    )
+
+
+def cfg3(B: int = 256, n_steps: int = 40000, orientation: str = "s"):
+    """Two in-phase LOs (moments along x) at B separations log-spaced 1 nm .. 1 um.
+
+    orientation 's': separation along y (transverse); 'p': separation along x (longitudinal).
+    """
+    sep = np.logspace(-9, -6, B)
+    origins = np.zeros((B, 2, 3))
+    k = 1 if orientation == "s" else 0
+    origins[:, 1, k] = sep
+    axes = np.zeros((B, 2, 3))
+    axes[:, :, 0] = 1.0
+    cfg = lo_batch(origins, axes, 2 * math.pi * 200e12, 1e-11, 1e-18, n_steps, 10000)
+    return cfg, sep
+
+
+def listing2(n_steps: int = 40000):
+    """Two s dipoles of the paper's listing: axis y, 80 nm apart along x, 2 pi 100 THz, r_dip 1 nm."""
+    origins = np.array([[[0.0, 0.0, 0.0], [80e-9, 0.0, 0.0]]])
+    axes = np.array([[[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]])
+    return lo_batch(origins, axes, 2 * math.pi * 100e12, 1e-9, 1e-18, n_steps, 10000)
+
+
+def cfg4(N: int = 256, n_steps: int = 20000):
+    """N LOs on a ring of radius 200 nm, moments along z, omega0 jittered +-1% (seeded)."""
+    rng = np.random.default_rng(SEED_CFG4)
+    ang = 2 * math.pi * np.arange(N) / N
+    origins = np.stack([200e-9 * np.cos(ang), 200e-9 * np.sin(ang), np.zeros(N)], axis=1)[None]
+    axes = np.zeros((1, N, 3))
+    axes[..., 2] = 1.0
+    om = 2 * math.pi * 200e12 * (1.0 + rng.uniform(-0.01, 0.01, size=(1, N)))
+    return lo_batch(origins, axes, om, 1e-11, 1e-18, n_steps, 10000)
+
+
+def cfg5(N: int = 4096, n_steps: int = 20000, side: float = 600e-9, min_spacing: float = 5e-9):
+    """N LOs at seeded random positions in a cube with a minimum spacing, random axes."""
+    rng = np.random.default_rng(SEED_CFG5)
+    pts = np.empty((0, 3))
+    cell = min_spacing
+    grid = {}
+    out = []
+    while len(out) < N:
+        cand = rng.uniform(0.0, side, size=(4096, 3))
+        for p in cand:
+            key = tuple((p // cell).astype(int))
+            ok = True
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        for qidx in grid.get((key[0] + dx, key[1] + dy, key[2] + dz), ()):
+                            if np.sum((out[qidx] - p) ** 2) < min_spacing * min_spacing:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                grid.setdefault(key, []).append(len(out))
+                out.append(p)
+                if len(out) == N:
+                    break
+    pts = np.array(out)[None]
+    axes = unit_vectors(rng, N)[None]
+    return lo_batch(pts, axes, 2 * math.pi * 200e12, 1e-11, 1e-18, n_steps, 10000)
