@@ -1,0 +1,368 @@
+"""Benchmark of the Lienard-Wiechert field-grid hot path on GB300 (one JSON line on stdout).
+
+Step = one pc_fields_plane call on the field-grid workload: 64 oscillating dipoles (128 charges),
+2048 x 2048 plane at z = 0.5 um, 16 frames, mixed precision (float64 delays per tile, float32
+pair algebra), i.e. 16 * 2048^2 * 128 = 8.59e9 retarded Lienard-Wiechert pair evaluations.
+`value` = pair evaluations per second over all ranks, inputs resident in HBM.
+
+Also reported on the same line: the plain float64 GPU path on a bounded sample of the same
+workload, the batched two-oscillator run (256 separations x 40 000 RK4 steps + fit) in
+dipole-steps/s, the end-to-end number through the C ABI with host buffers, the roofline of the
+field kernel, clocks sampled during the timed region and the FP64 CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --profile fields_mixed_small|fields_f64_small|lo_small   (one small run for ncu)
+Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own copy of the workload
+(independent problems, no data-path collective), so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "LW pair evals/s & dipole-steps/s at 1 GB300, mixed vs plain FP64 GPU path"
+# Algorithmic floating-point operations of one retarded pair evaluation (point, charge, time):
+# segment quadratic for the retarded time (34), interpolation of position, velocity and
+# acceleration (30), Lienard-Wiechert E, B, phi, A in Griffiths' form (78), accumulation (10);
+# an add, multiply, divide or square root counts 1, a fused multiply-add 2.
+FLOPS_PER_PAIR = 152
+N_SM = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def rank_info():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(n_side=160, threads=0):
+    """The FP64 oracle on one frame of a strided n_side x n_side sub-grid of the field-grid workload."""
+    import oracle
+
+    dp, g, z, times = W.cfg2()
+    idx = np.linspace(0, 2047, n_side).astype(int)
+    pts = W.plane_grid(g[idx], g[idx], z)
+    threads = threads or len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    r = oracle.fields(pts, times[:1], dipoles=dp, nthreads=threads)
+    sec = time.perf_counter() - t0
+    assert r["status"] == oracle.OK
+    pairs = pts.shape[0] * 2 * dp.N
+    return dict(value=pairs / sec, unit="LW pair evals/s", cores=threads, kind="oracle",
+                sample=f"1 frame x {n_side}x{n_side} strided points of the 2048^2 grid x 128 charges "
+                       f"({pairs:.3g} pair evals, {sec:.2f} s wall)")
+
+
+def oracle_lo_sample(threads=0):
+    """The FP64 oracle on two coupled oscillators (one separation of the batched run), 4000 steps."""
+    import oracle
+
+    cfg, _ = W.cfg3(B=256, n_steps=4000)
+    t0 = time.perf_counter()
+    r = oracle.dipoles_run(cfg, b=128, nthreads=threads or 1)
+    sec = time.perf_counter() - t0
+    assert r["status"] == oracle.OK
+    return dict(value=2 * 4000 / sec, unit="dipole-steps/s", cores=threads or 1, kind="oracle",
+                sample="1 of 256 separations (2 oscillators) x 4000 steps")
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    threads = len(os.sched_getaffinity(0))
+    for _ in range(args.warmup):
+        oracle_sample(n_side=64, threads=threads)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_sample(n_side=96, threads=threads)
+        secs.append(time.perf_counter() - t0)
+        vals.append(r["value"])
+    value = sum(96 * 96 * 128 for _ in secs) / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "LW pair evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "field grid: 64 oscillating dipoles (128 charges), 2048^2 plane, 16 frames; each "
+                               "reference step evaluates a bounded sample: 1 frame x 96x96 strided points",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "LW pair evals/s", "cores": threads, "kind": "oracle",
+                         "sample": "1 frame x 96x96 strided points x 128 charges per step"},
+        "e2e": {"value": value, "unit": "LW pair evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU legs
+# ------------------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", default=None, choices=["fields_mixed_small", "fields_f64_small", "lo_small"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the float64, oscillator and CPU legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2107_12437_gb300 as pc
+
+    rank, world, local = rank_info()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    ctx = pc.Context(dev.index)
+    dp, g, z, times = W.cfg2()
+    step = float(g[1] - g[0])
+    dpd = pc.dipoles_to_device(dp, dev)
+    NU = NV = 2048
+    T = len(times)
+    pairs_per_step = NU * NV * T * 2 * dp.N
+
+    if args.profile:
+        if args.profile == "fields_mixed_small":
+            pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=512,
+                               nv=2048, times=list(times[:2]), precision=pc.PC_MIXED)
+        elif args.profile == "fields_f64_small":
+            pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=64,
+                               nv=2048, times=list(times[:1]), precision=pc.PC_F64)
+        else:
+            cfg, _ = W.cfg3(B=256, n_steps=2000)
+            pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps)
+        torch.cuda.synchronize()
+        return 0
+
+    out = pc.capi.alloc_field_out(NU * NV, T, pc.PC_MIXED, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step_fn():
+        pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=NU, nv=NV,
+                           times=list(times), precision=pc.PC_MIXED, out=out)
+
+    for _ in range(args.warmup):
+        step_fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.fill_(1.0)  # between steps: evict L2 (outside the timed events)
+            e0.record(s)
+            step_fn()
+            e1.record(s)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * pairs_per_step * args.steps / (total_ms * 1e-3)
+    kernel_ms = min(ms)  # dominant kernel: fields_mixed_kernel (prep kernel < 0.1 % of the step)
+    avg_ms = total_ms / args.steps
+
+    # ---- end to end through the C ABI with host buffers ----
+    host_in = {k: getattr(dp, k).copy() for k in ("origin", "axis", "q", "m1", "m2", "d", "d_dot", "d_ddot")}
+    pin_in = {k: torch.from_numpy(v).pin_memory() for k, v in host_in.items()}
+    pin_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    h2d = sum(v.numel() * v.element_size() for v in pin_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+
+    def e2e_step():
+        dev_in = {k: v.to(dev, non_blocking=True) for k, v in pin_in.items()}
+        from types import SimpleNamespace
+
+        dps = SimpleNamespace(t0=dp.t0, dt=dp.dt, **dev_in)
+        pc.pc_fields_plane(ctx, dipoles=dps, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=NU, nv=NV,
+                           times=list(times), precision=pc.PC_MIXED, out=out)
+        for k in out:
+            pin_out[k].copy_(out[k], non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    e2e_step()
+    n_e2e = max(2, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    e2e_sec = (time.perf_counter() - t0) / n_e2e
+    if dist:
+        t = torch.tensor([e2e_sec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    e2e_value = world * pairs_per_step / e2e_sec
+
+    # ---- roofline of the field kernel (float32 ALU) ----
+    fp32_fma, fp64_fma = pc.pc_alu_peaks(ctx)
+    peak_tflops = 2.0 * N_SM * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs_per_step / (kernel_ms * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "fields_mixed_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_full_launch")
+        except Exception:
+            traffic = None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "LW pair evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": {"workload": "field grid: 64 oscillating dipoles (128 charges +-e, 1e-11 m sin(w0 t), "
+                               "w0 = 2 pi 200 THz, origins in a 1 um cube, seed 2107), 2048x2048 plane at "
+                               "z = 0.5 um, 16 frames t = 10 fs + f 5/16 fs, mixed precision, float32 outputs",
+                   "pairs_per_step": pairs_per_step, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MB write); outputs 2.7 GB > L2"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": "LW pair evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "fields_mixed_kernel", "flops_per_pair": FLOPS_PER_PAIR,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
+                     "measured_fp32_fma_per_s": fp32_fma, "measured_fp64_fma_per_s": fp64_fma},
+    }
+
+    if not args.no_extra:
+        # plain float64 GPU path on a bounded sample (64 rows x 2048 x 1 frame), per pair evaluation
+        def f64_step():
+            pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=64,
+                               nv=NV, times=[float(times[0])], precision=pc.PC_F64)
+
+        f64_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(3):
+            f64_step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        f64_ms = e0.elapsed_time(e1) / 3
+        f64_pairs = 64 * NV * 2 * dp.N
+        f64_value = f64_pairs / (f64_ms * 1e-3)
+        line["fp64_path"] = {"value": f64_value, "unit": "LW pair evals/s",
+                             "sample": "64 rows x 2048 x 1 frame of the same grid, float64 path",
+                             "mixed_over_fp64": value / world / f64_value,
+                             "roofline": {"bound": "alu", "achieved": FLOPS_PER_PAIR * f64_value / 1e12,
+                                          "peak": 2.0 * fp64_fma / 1e12, "unit": "TFLOP/s",
+                                          "frac": FLOPS_PER_PAIR * f64_value / (2.0 * fp64_fma),
+                                          "peak_basis": "measured float64 FMA rate (pc_alu_peaks)"}}
+        # batched self-consistent pair: 256 separations x 40 000 steps + fit
+        cfg, _ = W.cfg3(B=256, n_steps=40000)
+        lod = pc.lo_config_to_device(cfg, dev)
+        pc.pc_dipoles_run(ctx, lod, cfg.dt, 2000)
+        torch.cuda.synchronize()
+        e0.record(s)
+        pc.pc_dipoles_run(ctx, lod, cfg.dt, cfg.n_steps, fit=True, first_index=cfg.first_index)
+        e1.record(s)
+        torch.cuda.synchronize()
+        lo_ms = e0.elapsed_time(e1)
+        line["dipole_steps"] = {"value": cfg.B * cfg.N * cfg.n_steps / (lo_ms * 1e-3), "unit": "dipole-steps/s",
+                                "workload": "256 separations (1 nm .. 1 um) x 2 oscillators x 40000 RK4 steps "
+                                            "+ KE fit, float64", "ms": lo_ms}
+        if rank == 0:
+            import oracle
+
+            oracle.build()
+            line["cpu_baseline"] = oracle_sample()
+            line["cpu_baseline_lo"] = oracle_lo_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

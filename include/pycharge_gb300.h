@@ -1,0 +1,199 @@
+/*
+ * pycharge_gb300.h -- C ABI of a GB300 (sm_103a) implementation of the data-parallel hot path of
+ * PyCharge (Filipovich & Hughes, arXiv 2107.12437): retarded Lienard-Wiechert fields of point
+ * charges with stored trajectories, and the self-consistent Lorentz-oscillator (LO) loop.
+ *
+ * Conventions for every entry point
+ *   - SI units, float64 inputs.
+ *   - Array arguments named "device" are CUDA device pointers on the context's device; the caller
+ *     owns them and keeps them alive until the call returns.  Small descriptors (the structs
+ *     below) live in host memory and are read during the call only.
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).  Every call
+ *     ends by reading the device status word back, so when it returns the outputs are complete.
+ *   - Errors are returned as pc_status; no call aborts, traps or falls back to the CPU.  On error
+ *     the content of the outputs is unspecified.
+ *   - A context must not be used by two host threads at once (it owns one workspace).
+ */
+#ifndef PYCHARGE_GB300_H
+#define PYCHARGE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PC_OK = 0,
+  PC_ERR_ARG = 1,       /* invalid argument (null pointer, non-positive size, bad enum, |axis| != 1) */
+  PC_ERR_CUDA = 2,      /* a CUDA runtime call failed (allocation, launch) */
+  PC_ERR_HISTORY = 3,   /* a retarded time falls outside a charge's stored samples (Eq. ret_t) */
+  PC_ERR_VELOCITY = 4,  /* a dipole charge exceeded v_max (Sec. 3.2, default c/100) */
+  PC_ERR_CAUSALITY = 5, /* dt exceeds a light-crossing time between dipoles (Sec. 3.2) */
+  PC_ERR_NOCONV = 6,    /* the retarded-time solve or the energy fit did not converge */
+  PC_ERR_TIMEOUT = 7    /* a device-side wait exceeded its iteration limit */
+} pc_status;
+
+/* field kind, Sec. 3.2 (calculate_E / calculate_B select total, Coulomb or radiation field) */
+enum { PC_TOTAL = 0, PC_COULOMB = 1, PC_RADIATION = 2 };
+
+/* arithmetic of the field sum */
+enum {
+  PC_F64 = 0,  /* every step in float64; float64 outputs */
+  PC_MIXED = 1 /* float64 delays per tile, float32 per-pair algebra with dipole pairs in difference
+                  form and compensated summation; float32 outputs */
+};
+
+typedef struct pc_ctx pc_ctx;
+
+/*
+ * Point charges with predefined trajectories (Sec. 3.1: Charge objects), sampled at t0 + k dt,
+ * k = 0..S-1, linearly interpolated between samples (Sec. 3.1).
+ */
+typedef struct {
+  int32_t M;             /* number of charges (0 = none) */
+  int64_t S;             /* samples per charge, >= 2 */
+  double t0, dt;         /* time of sample 0, sample spacing (s) */
+  const double *q;       /* device [M] charge (C) */
+  const double *pos;     /* device [M][S][3] position (m) */
+  const double *vel;     /* device [M][S][3] velocity (m/s), |vel| < c */
+  const double *acc;     /* device [M][S][3] acceleration (m/s^2) */
+  int32_t static_before; /* 1: before t0 a charge rests at its sample-0 position; 0: PC_ERR_HISTORY */
+} pc_charges;
+
+/*
+ * Dipoles as field sources (Sec. 3.1: Dipole objects): two charges +q (mass m1) and -q (mass m2)
+ * about the centre of mass `origin`, with moment d(t) along the fixed unit `axis`:
+ *   r_1 = R + m2/(m1+m2) (d/q) axis,  r_2 = R - m1/(m1+m2) (d/q) axis   (Eqs. r_1, r_2).
+ * d, d', d'' are sampled at t0 + n dt and linearly interpolated; before t0 the dipole is at rest
+ * with moment d[0] (Sec. 3.2).  This is also the layout pc_dipoles_run writes, so a run's output
+ * can be passed here directly (per configuration).
+ */
+typedef struct {
+  int32_t N;                /* number of dipoles (0 = none) */
+  int64_t S;                /* samples per dipole, >= 2 */
+  double t0, dt;
+  const double *origin;     /* device [N][3] (m) */
+  const double *axis;       /* device [N][3] unit vectors */
+  const double *q;          /* device [N] charge magnitude (C), > 0 */
+  const double *m1, *m2;    /* device [N] masses of the positive and negative charge (kg) */
+  const double *d;          /* device [N][S] moment along axis (C m) */
+  const double *d_dot;      /* device [N][S] (C m / s) */
+  const double *d_ddot;     /* device [N][S] (C m / s^2) */
+} pc_dipole_sources;
+
+/* Outputs of pc_fields; any pointer may be NULL to skip that output.
+ * PC_F64 writes double, PC_MIXED writes float.  Layout [T][P][...] with the point index fastest. */
+typedef struct {
+  void *E;       /* device [T][P][3] electric field (V/m) */
+  void *B;       /* device [T][P][3] magnetic field (T) */
+  void *phi;     /* device [T][P] scalar potential (V) */
+  void *A;       /* device [T][P][3] vector potential (V s/m) */
+  uint8_t *mask; /* device [T][P]: 1 where some charge was within r_excl of the point at its
+                    retarded time; that charge then contributes nothing */
+} pc_field_out;
+
+/* Plane grid: point (iu, iv) = origin + iu*eu + iv*ev, output index iu*nv + iv (meshgrid 'ij'). */
+typedef struct {
+  double origin[3], eu[3], ev[3];
+  int64_t nu, nv;
+} pc_plane;
+
+/* Context: owns the workspace (device status word, float32 history mirrors, run scratch). */
+pc_status pc_ctx_create(pc_ctx **out, int device);
+pc_status pc_ctx_destroy(pc_ctx *ctx);
+const char *pc_status_string(pc_status s);
+
+/*
+ * pc_fields -- E, B, phi, A of all sources at P points and T times (Sec. 2.2).
+ *
+ * For every (point r, time t, charge) the retarded time t' = t - |r - r_s(t')|/c (Eq. ret_t) is
+ * solved against the charge's piecewise-linear history, the Lienard-Wiechert potentials and fields
+ * (Eqs. V, A, E, B; `kind` selects Eq. E, ECoulomb or Eradiation for E and B) are evaluated there,
+ * and the contributions of all charges are summed (Sec. 2.2).  Vector potential: A = (v/c^2) phi.
+ *   ch, dp      sources (either may be NULL or empty, not both)
+ *   points      device [P][3] (m); P >= 0
+ *   times       host [T] evaluation times (s); T >= 1
+ *   r_excl      a charge closer than r_excl (m) at its retarded position is skipped and masked;
+ *               r_excl = 0 masks exact coincidence only
+ * Errors: PC_ERR_ARG, PC_ERR_HISTORY (retarded time outside the samples), PC_ERR_NOCONV,
+ * PC_ERR_CUDA.
+ */
+pc_status pc_fields(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const double *points,
+                    int64_t P, const double *times, int32_t T, int32_t kind, int32_t precision, double r_excl,
+                    const pc_field_out *out, void *stream);
+
+/* pc_fields on a plane grid (P = nu*nv points generated on the device); same semantics. */
+pc_status pc_fields_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const pc_plane *grid,
+                          const double *times, int32_t T, int32_t kind, int32_t precision, double r_excl,
+                          const pc_field_out *out, void *stream);
+
+/*
+ * Lorentz-oscillator configurations for pc_dipoles_run: B independent configurations of N dipoles
+ * each (Sec. 2.3, Sec. 4.2).  Dipole (b, i): centre `origin`, unit `axis`, charges +-q with masses
+ * m1 (positive) and m2 (negative), natural angular frequency omega0, initial moment d0 along the
+ * axis (d = q r_dip).  All device arrays, [B][N] or [B][N][3].
+ */
+typedef struct {
+  int32_t B, N;
+  const double *origin, *axis;
+  const double *q, *m1, *m2, *omega0, *d0;
+} pc_dipoles;
+
+typedef struct {
+  double v_max;        /* maximum charge speed (m/s); <= 0 selects c/100 (Sec. 3.2) */
+  int32_t ed_mode;     /* 0: E_d at every RK4 stage time (default); 1: E_d held at t over the step */
+  int32_t fit;         /* 1: fit Eq. KE per dipole after the run (outputs gamma, omega) */
+  int64_t first_index; /* first step used by the fit (Sec. 3.4: after 10 000 steps) */
+  int32_t precision;   /* PC_F64 or PC_MIXED for the driving-field sum */
+} pc_run_opts;
+
+/* Outputs of pc_dipoles_run; layout [B][N][n_steps+1] (time fastest). d, d_dot, d_ddot are
+ * required: they are the trajectory history the run reads back at retarded times. */
+typedef struct {
+  double *d, *d_dot, *d_ddot; /* device, required */
+  double *energy;             /* device [B][N][n_steps+1] Eq. dipoleE, or NULL */
+  double *Ed;                 /* device [B][N][n_steps+1] driving field at t_n (V/m), or NULL */
+  double *gamma;              /* device [B][N] fitted energy decay rate (1/s), or NULL */
+  double *omega;              /* device [B][N] fitted angular frequency (rad/s); delta = omega - omega0 */
+} pc_run_out;
+
+/*
+ * pc_dipoles_run -- Algorithm 1 for B configurations at once.
+ *
+ * Each dipole obeys d'' + gamma0 d' + omega0^2 d = (q^2/m) E_d(R, t) (Eq. LO_equation) with
+ * m = m1 m2/(m1+m2) (Eq. eff_mass), gamma0 = q^2 omega0^2/(6 pi eps0 c^3 m) and E_d the component
+ * along its axis of the retarded field of every other dipole of its configuration at its origin
+ * (Sec. 2.3).  RK4 from t = 0 to n_steps*dt; the dipoles rest at d0 for t <= 0 (Sec. 3.2); after
+ * each step d'' is set from the equation of motion at the step end.  Optionally the kinetic energy
+ * m d'^2/(2 q^2) from first_index on is fitted to Eq. KE (Levenberg-Marquardt), giving gamma and
+ * omega per dipole.
+ * Errors: PC_ERR_ARG, PC_ERR_CAUSALITY (two dipoles closer than c dt), PC_ERR_VELOCITY,
+ * PC_ERR_NOCONV, PC_ERR_CUDA.
+ */
+pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
+                         const pc_run_out *out, void *stream);
+
+/*
+ * pc_ke_fit -- Levenberg-Marquardt fit of Eq. KE (Sec. 2.4) to K series of kinetic energies.
+ *   ke        device [K][S] samples at spacing dt; samples first_index..S-1 are fitted
+ *   gamma     device [K] out: energy decay rate (1/s)
+ *   omega     device [K] out: angular frequency (rad/s)
+ *   amp, phase device [K] out or NULL: A and phi of Eq. KE with time counted from sample first_index
+ * Errors: PC_ERR_ARG, PC_ERR_NOCONV (fewer than two kinetic-energy minima in the window).
+ */
+pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t S, double dt, int64_t first_index,
+                    double *gamma, double *omega, double *amp, double *phase, void *stream);
+
+/*
+ * pc_alu_peaks -- measures this GPU's float32 and float64 fused-multiply-add throughput (FMA/s)
+ * with dependent-chain kernels; used as roofline denominators.  Writes fp32_fma_per_s,
+ * fp64_fma_per_s (host pointers).
+ */
+pc_status pc_alu_peaks(pc_ctx *ctx, double *fp32_fma_per_s, double *fp64_fma_per_s, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

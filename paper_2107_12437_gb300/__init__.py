@@ -1,0 +1,24 @@
+"""GB300-native (sm_103a) Lienard-Wiechert hot path of PyCharge (arXiv 2107.12437).
+
+The computation lives in libpycharge_gb300.so (C ABI: include/pycharge_gb300.h); `capi` is its
+thin ctypes binding.  Names follow the header: pc_fields, pc_fields_plane, pc_dipoles_run,
+pc_ke_fit.
+"""
+from .capi import (  # noqa: F401
+    PC_COULOMB,
+    PC_F64,
+    PC_MIXED,
+    PC_RADIATION,
+    PC_TOTAL,
+    Context,
+    PcError,
+    charges_to_device,
+    dipoles_to_device,
+    lo_config_to_device,
+    load,
+    pc_alu_peaks,
+    pc_dipoles_run,
+    pc_fields,
+    pc_fields_plane,
+    pc_ke_fit,
+)

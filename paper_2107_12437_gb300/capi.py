@@ -1,0 +1,296 @@
+"""ctypes binding of libpycharge_gb300.so (include/pycharge_gb300.h); argument marshalling only.
+
+Every computation happens in the CUDA library.  Sources and outputs are torch CUDA tensors (the
+library only sees their device pointers and the current CUDA stream).  If the library cannot be
+loaded the import fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from types import SimpleNamespace
+
+import torch
+
+from . import build as _build
+
+PC_OK, PC_ERR_ARG, PC_ERR_CUDA, PC_ERR_HISTORY, PC_ERR_VELOCITY, PC_ERR_CAUSALITY, PC_ERR_NOCONV, PC_ERR_TIMEOUT = range(8)
+PC_TOTAL, PC_COULOMB, PC_RADIATION = 0, 1, 2
+PC_F64, PC_MIXED = 0, 1
+
+STATUS_NAMES = {
+    PC_OK: "PC_OK", PC_ERR_ARG: "PC_ERR_ARG", PC_ERR_CUDA: "PC_ERR_CUDA", PC_ERR_HISTORY: "PC_ERR_HISTORY",
+    PC_ERR_VELOCITY: "PC_ERR_VELOCITY", PC_ERR_CAUSALITY: "PC_ERR_CAUSALITY", PC_ERR_NOCONV: "PC_ERR_NOCONV",
+    PC_ERR_TIMEOUT: "PC_ERR_TIMEOUT",
+}
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_f64 = ctypes.c_double
+
+
+class PcCharges(ctypes.Structure):
+    _fields_ = [("M", _i32), ("S", _i64), ("t0", _f64), ("dt", _f64), ("q", _vp), ("pos", _vp), ("vel", _vp),
+                ("acc", _vp), ("static_before", _i32)]
+
+
+class PcDipoleSources(ctypes.Structure):
+    _fields_ = [("N", _i32), ("S", _i64), ("t0", _f64), ("dt", _f64), ("origin", _vp), ("axis", _vp), ("q", _vp),
+                ("m1", _vp), ("m2", _vp), ("d", _vp), ("d_dot", _vp), ("d_ddot", _vp)]
+
+
+class PcFieldOut(ctypes.Structure):
+    _fields_ = [("E", _vp), ("B", _vp), ("phi", _vp), ("A", _vp), ("mask", _vp)]
+
+
+class PcPlane(ctypes.Structure):
+    _fields_ = [("origin", _f64 * 3), ("eu", _f64 * 3), ("ev", _f64 * 3), ("nu", _i64), ("nv", _i64)]
+
+
+class PcDipoles(ctypes.Structure):
+    _fields_ = [("B", _i32), ("N", _i32), ("origin", _vp), ("axis", _vp), ("q", _vp), ("m1", _vp), ("m2", _vp),
+                ("omega0", _vp), ("d0", _vp)]
+
+
+class PcRunOpts(ctypes.Structure):
+    _fields_ = [("v_max", _f64), ("ed_mode", _i32), ("fit", _i32), ("first_index", _i64), ("precision", _i32)]
+
+
+class PcRunOut(ctypes.Structure):
+    _fields_ = [("d", _vp), ("d_dot", _vp), ("d_ddot", _vp), ("energy", _vp), ("Ed", _vp), ("gamma", _vp),
+                ("omega", _vp)]
+
+
+# every entry point of include/pycharge_gb300.h with its argument types
+SIGNATURES = {
+    "pc_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
+    "pc_ctx_destroy": (ctypes.c_int, [_vp]),
+    "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pc_fields": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
+                                 ctypes.POINTER(_f64), _i32, _i32, _i32, _f64, ctypes.POINTER(PcFieldOut), _vp]),
+    "pc_fields_plane": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources),
+                                       ctypes.POINTER(PcPlane), ctypes.POINTER(_f64), _i32, _i32, _i32, _f64,
+                                       ctypes.POINTER(PcFieldOut), _vp]),
+    "pc_dipoles_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
+                                      ctypes.POINTER(PcRunOut), _vp]),
+    "pc_ke_fit": (ctypes.c_int, [_vp, _vp, _i32, _i64, _f64, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "pc_alu_peaks": (ctypes.c_int, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _vp]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load the shared library (building it first if asked); raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpycharge_gb300.so not found at {path}; run paper_2107_12437_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = load().pc_status_string(status).decode()
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({msg})")
+
+
+def _check(st: int, where: str):
+    if st != PC_OK:
+        raise PcError(st, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """pc_ctx on one device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        h = _vp()
+        _check(self.lib.pc_ctx_create(ctypes.byref(h), device), "pc_ctx_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.lib.pc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dev(x, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(x, dtype=torch.float64, device=device).contiguous()
+
+
+def charges_to_device(ch, device="cuda"):
+    """Copy a host description of point charges (fields q, pos, vel, acc, t0, dt, static_before)."""
+    return SimpleNamespace(q=_dev(ch.q, device), pos=_dev(ch.pos, device), vel=_dev(ch.vel, device),
+                           acc=_dev(ch.acc, device), t0=float(ch.t0), dt=float(ch.dt),
+                           static_before=int(getattr(ch, "static_before", 0)))
+
+
+def dipoles_to_device(dp, device="cuda"):
+    """Copy a host description of dipole sources (origin, axis, q, m1, m2, d, d_dot, d_ddot, t0, dt)."""
+    return SimpleNamespace(origin=_dev(dp.origin, device), axis=_dev(dp.axis, device), q=_dev(dp.q, device),
+                           m1=_dev(dp.m1, device), m2=_dev(dp.m2, device), d=_dev(dp.d, device),
+                           d_dot=_dev(dp.d_dot, device), d_ddot=_dev(dp.d_ddot, device), t0=float(dp.t0),
+                           dt=float(dp.dt))
+
+
+def _charges_struct(ch):
+    if ch is None:
+        return None
+    return PcCharges(M=int(ch.q.shape[0]), S=int(ch.pos.shape[1]), t0=ch.t0, dt=ch.dt, q=_ptr(ch.q),
+                     pos=_ptr(ch.pos), vel=_ptr(ch.vel), acc=_ptr(ch.acc), static_before=int(ch.static_before))
+
+
+def _dipoles_struct(dp):
+    if dp is None:
+        return None
+    return PcDipoleSources(N=int(dp.origin.shape[0]), S=int(dp.d.shape[1]), t0=dp.t0, dt=dp.dt,
+                           origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1), m2=_ptr(dp.m2),
+                           d=_ptr(dp.d), d_dot=_ptr(dp.d_dot), d_ddot=_ptr(dp.d_ddot))
+
+
+def alloc_field_out(P, T, precision, device="cuda", which=("E", "B", "phi", "A", "mask")):
+    dt = torch.float64 if precision == PC_F64 else torch.float32
+    o = {}
+    if "E" in which:
+        o["E"] = torch.empty((T, P, 3), dtype=dt, device=device)
+    if "B" in which:
+        o["B"] = torch.empty((T, P, 3), dtype=dt, device=device)
+    if "phi" in which:
+        o["phi"] = torch.empty((T, P), dtype=dt, device=device)
+    if "A" in which:
+        o["A"] = torch.empty((T, P, 3), dtype=dt, device=device)
+    if "mask" in which:
+        o["mask"] = torch.empty((T, P), dtype=torch.uint8, device=device)
+    return o
+
+
+def _out_struct(o):
+    return PcFieldOut(E=_ptr(o.get("E")), B=_ptr(o.get("B")), phi=_ptr(o.get("phi")), A=_ptr(o.get("A")),
+                      mask=_ptr(o.get("mask")))
+
+
+def pc_fields(ctx, charges=None, dipoles=None, points=None, times=(0.0,), kind=PC_TOTAL, precision=PC_F64,
+              r_excl=0.0, out=None, stream=None):
+    """pc_fields: points is a [P][3] float64 CUDA tensor; returns the dict of output tensors."""
+    P = int(points.shape[0])
+    T = len(times)
+    o = alloc_field_out(P, T, precision, points.device) if out is None else out
+    tarr = (_f64 * T)(*[float(t) for t in times])
+    chs = _charges_struct(charges)
+    dps = _dipoles_struct(dipoles)
+    st = ctx.lib.pc_fields(ctx.handle, ctypes.byref(chs) if chs else None, ctypes.byref(dps) if dps else None,
+                           _ptr(points), P, tarr, T, kind, precision, float(r_excl), ctypes.byref(_out_struct(o)),
+                           _stream(stream))
+    _check(st, "pc_fields")
+    return o
+
+
+def pc_fields_plane(ctx, charges=None, dipoles=None, origin=(0, 0, 0), eu=(1, 0, 0), ev=(0, 1, 0), nu=1, nv=1,
+                    times=(0.0,), kind=PC_TOTAL, precision=PC_F64, r_excl=0.0, out=None, stream=None,
+                    device="cuda"):
+    """pc_fields_plane: point (iu, iv) = origin + iu eu + iv ev, output index iu*nv + iv."""
+    T = len(times)
+    o = alloc_field_out(nu * nv, T, precision, device) if out is None else out
+    pl = PcPlane(origin=(_f64 * 3)(*origin), eu=(_f64 * 3)(*eu), ev=(_f64 * 3)(*ev), nu=nu, nv=nv)
+    tarr = (_f64 * T)(*[float(t) for t in times])
+    chs = _charges_struct(charges)
+    dps = _dipoles_struct(dipoles)
+    st = ctx.lib.pc_fields_plane(ctx.handle, ctypes.byref(chs) if chs else None, ctypes.byref(dps) if dps else None,
+                                 ctypes.byref(pl), tarr, T, kind, precision, float(r_excl),
+                                 ctypes.byref(_out_struct(o)), _stream(stream))
+    _check(st, "pc_fields_plane")
+    return o
+
+
+def lo_config_to_device(cfg, device="cuda"):
+    """Copy a host LO configuration batch (origin, axis, q, m1, m2, omega0, d0 with leading [B][N])."""
+    return SimpleNamespace(origin=_dev(cfg.origin, device), axis=_dev(cfg.axis, device), q=_dev(cfg.q, device),
+                           m1=_dev(cfg.m1, device), m2=_dev(cfg.m2, device), omega0=_dev(cfg.omega0, device),
+                           d0=_dev(cfg.d0, device))
+
+
+def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_index=0, precision=PC_F64,
+                   want_energy=True, want_Ed=False, out=None, stream=None):
+    """pc_dipoles_run: dp holds [B][N] / [B][N][3] CUDA tensors; returns the dict of outputs."""
+    B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
+    S = int(n_steps) + 1
+    dev = dp.origin.device
+    if out is None:
+        out = dict(d=torch.empty((B, N, S), dtype=torch.float64, device=dev),
+                   d_dot=torch.empty((B, N, S), dtype=torch.float64, device=dev),
+                   d_ddot=torch.empty((B, N, S), dtype=torch.float64, device=dev))
+        if want_energy:
+            out["energy"] = torch.empty((B, N, S), dtype=torch.float64, device=dev)
+        if want_Ed:
+            out["Ed"] = torch.empty((B, N, S), dtype=torch.float64, device=dev)
+        if fit:
+            out["gamma"] = torch.empty((B, N), dtype=torch.float64, device=dev)
+            out["omega"] = torch.empty((B, N), dtype=torch.float64, device=dev)
+    d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
+                  m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=int(ed_mode), fit=int(bool(fit)), first_index=int(first_index),
+                     precision=int(precision))
+    ro = PcRunOut(d=_ptr(out["d"]), d_dot=_ptr(out["d_dot"]), d_ddot=_ptr(out["d_ddot"]),
+                  energy=_ptr(out.get("energy")), Ed=_ptr(out.get("Ed")), gamma=_ptr(out.get("gamma")),
+                  omega=_ptr(out.get("omega")))
+    st = ctx.lib.pc_dipoles_run(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
+                                ctypes.byref(ro), _stream(stream))
+    _check(st, "pc_dipoles_run")
+    return out
+
+
+def pc_ke_fit(ctx, ke, dt, first_index, stream=None):
+    """pc_ke_fit on a [K][S] float64 CUDA tensor; returns (gamma, omega, amp, phase) tensors [K]."""
+    K, S = int(ke.shape[0]), int(ke.shape[1])
+    dev = ke.device
+    g = torch.empty(K, dtype=torch.float64, device=dev)
+    w = torch.empty(K, dtype=torch.float64, device=dev)
+    a = torch.empty(K, dtype=torch.float64, device=dev)
+    p = torch.empty(K, dtype=torch.float64, device=dev)
+    st = ctx.lib.pc_ke_fit(ctx.handle, _ptr(ke), K, S, float(dt), int(first_index), _ptr(g), _ptr(w), _ptr(a),
+                           _ptr(p), _stream(stream))
+    _check(st, "pc_ke_fit")
+    return g, w, a, p
+
+
+def pc_alu_peaks(ctx, stream=None):
+    """(fp32 FMA/s, fp64 FMA/s) measured on the context's device."""
+    a, b = _f64(0.0), _f64(0.0)
+    _check(ctx.lib.pc_alu_peaks(ctx.handle, ctypes.byref(a), ctypes.byref(b), _stream(stream)), "pc_alu_peaks")
+    return a.value, b.value

@@ -1,0 +1,854 @@
+// Retarded Lienard-Wiechert field sum (arXiv 2107.12437, Sec. 2.1-2.2) on sm_103a.
+//
+// Two paths:
+//   PC_F64   one thread per (point, time); every charge's retarded time is found by solving, on one
+//            segment of its piecewise-linear history, the quadratic c^2 (t - t')^2 = |r - r_s(t')|^2
+//            (Eq. ret_t with linear interpolation, Sec. 3.1), moving to the segment the root points
+//            to until it lies inside; fields from Griffiths' form of Eqs. E, B, V, A in float64.
+//   PC_MIXED a CTA owns a tile of points.  Per (tile, source) the float64 distance from the tile's
+//            anchor point to the source reference gives the integer part of the retarded sample
+//            index; per (point, source) everything else runs in float32 on offsets (lengths in
+//            units of c*dt, so a delay in samples equals a distance).  The two charges of a dipole
+//            are evaluated together in difference form: the net field q[E(x+) - E(x-)] is built
+//            from differences of the scalar coefficients of the Lienard-Wiechert field that carry
+//            no cancellation, so the s/R loss of the +-q pair (s = charge separation) does not
+//            appear.  Contributions are summed in groups of eight and the group sums are added
+//            with Kahan compensation.
+#include <stdio.h>
+
+#include "pc_internal.cuh"
+#include "pc_lw_f64.cuh"
+
+namespace pc {
+
+constexpr int kMaxT = 32;        // times per launch (the host splits longer lists)
+constexpr int kMixThreads = 256; // points per CTA in the mixed path
+constexpr int kChunk = 64;       // sources staged in shared memory at a time
+
+struct Points {
+  const double *list;  // [P][3] or null for a plane
+  double o[3], eu[3], ev[3];
+  int64_t nu, nv;
+  int64_t P;
+};
+
+__device__ __forceinline__ void point_at(const Points &pd, int64_t p, double r[3]) {
+  if (pd.list) {
+    r[0] = pd.list[3 * p];
+    r[1] = pd.list[3 * p + 1];
+    r[2] = pd.list[3 * p + 2];
+  } else {
+    double iu = (double)(p / pd.nv), iv = (double)(p % pd.nv);
+    r[0] = pd.o[0] + iu * pd.eu[0] + iv * pd.ev[0];
+    r[1] = pd.o[1] + iu * pd.eu[1] + iv * pd.ev[1];
+    r[2] = pd.o[2] + iu * pd.eu[2] + iv * pd.ev[2];
+  }
+}
+
+struct Sources {
+  // point charges
+  int32_t M;
+  int64_t S;
+  double t0, dt;
+  const double *q, *pos, *vel, *acc;
+  int32_t static_before;
+  // dipoles
+  int32_t N;
+  int64_t Sd;
+  double t0d, dtd;
+  const double *origin, *axis, *qd, *m1, *m2, *d, *dd, *ddd;
+};
+
+struct Outs {
+  void *E, *B, *phi, *A;
+  uint8_t *mask;
+};
+
+struct Launch {
+  Points pts;
+  Sources src;
+  Outs out;
+  int32_t T;            // times in this launch
+  int64_t frame0;       // output frame of times[0]
+  double times[kMaxT];
+  double r_excl;
+  int *status;
+  // mixed path: float32 mirrors and per-charge references
+  const float4 *Hd;     // [N][Sd] (d/(qL), d'/(qc), d'' dt/(qc), 0)
+  const float4 *Hc;     // [M][S][3]: offset/L, v/c, a dt/c
+  const double *cref;   // [M][3] reference position (sample 0)
+};
+
+// ================================================================================================
+// float64 path
+// ================================================================================================
+template <int KIND>
+__global__ void __launch_bounds__(128) fields_f64_kernel(const Launch L) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int f = blockIdx.y;
+  if (p >= L.pts.P || f >= L.T) return;
+  double r[3];
+  point_at(L.pts, p, r);
+  const double t = L.times[f];
+  double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, A[3] = {0, 0, 0}, phi = 0.0;
+  uint8_t mask = 0;
+  int err = 0;
+  const Sources &s = L.src;
+  // ---- point charges ----
+  if (s.M > 0) {
+    const double u = (t - s.t0) / s.dt, cdt = kC * s.dt;
+    for (int c = 0; c < s.M && !err; ++c) {
+      TrajF64 tr;
+      tr.dipole = false;
+      tr.pos = s.pos + (size_t)c * s.S * 3;
+      tr.vel = s.vel + (size_t)c * s.S * 3;
+      tr.acc = s.acc + (size_t)c * s.S * 3;
+      int64_t kr = (int64_t)floor(u);
+      kr = kr < 0 ? 0 : (kr > s.S - 1 ? s.S - 1 : kr);
+      double pr[3];
+      tr.p(kr, pr);
+      double dv[3] = {r[0] - pr[0], r[1] - pr[1], r[2] - pr[2]};
+      double tau0 = sqrt(dot3(dv, dv)) / cdt;
+      int64_t k;
+      double th;
+      err = solve_f64(tr, s.S, s.static_before, r, u, cdt, (int64_t)floor(u - tau0), &k, &th);
+      if (err) break;
+      double p0[3], v[3], a[3];
+      if (k < 0) {
+        tr.p(0, p0);
+        v[0] = v[1] = v[2] = 0.0;
+        a[0] = a[1] = a[2] = 0.0;
+      } else {
+        double p1[3], v1[3], a1[3];
+        tr.p(k, p0);
+        tr.p(k + 1, p1);
+        tr.va(k, v, a);
+        tr.va(k + 1, v1, a1);
+        for (int i = 0; i < 3; ++i) {
+          p0[i] += th * (p1[i] - p0[i]);
+          v[i] += th * (v1[i] - v[i]);
+          a[i] += th * (a1[i] - a[i]);
+        }
+      }
+      double av[3] = {r[0] - p0[0], r[1] - p0[1], r[2] - p0[2]};
+      lw_add_f64<KIND>(s.q[c], av, v, a, L.r_excl, E, B, &phi, A, &mask);
+    }
+  }
+  // ---- dipoles: two charges each (Eqs. r_1, r_2) ----
+  if (s.N > 0 && !err) {
+    const double u = (t - s.t0d) / s.dtd, cdt = kC * s.dtd;
+    for (int j = 0; j < s.N && !err; ++j) {
+      TrajF64 tr;
+      tr.dipole = true;
+      tr.d = s.d + (size_t)j * s.Sd;
+      tr.dd = s.dd + (size_t)j * s.Sd;
+      tr.ddd = s.ddd + (size_t)j * s.Sd;
+      for (int i = 0; i < 3; ++i) {
+        tr.R[i] = s.origin[3 * j + i];
+        tr.ax[i] = s.axis[3 * j + i];
+      }
+      const double q = s.qd[j], m1 = s.m1[j], m2 = s.m2[j];
+      double dv[3] = {r[0] - tr.R[0], r[1] - tr.R[1], r[2] - tr.R[2]};
+      double tau0 = sqrt(dot3(dv, dv)) / cdt;
+      int64_t kg = (int64_t)floor(u - tau0);
+      for (int sg = 0; sg < 2 && !err; ++sg) {
+        tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+        int64_t k;
+        double th;
+        err = solve_f64(tr, s.Sd, 1, r, u, cdt, kg, &k, &th);
+        if (err) break;
+        double p0[3], v[3], a[3];
+        if (k < 0 || (k == 0 && th == 0.0)) {
+          // at rest with moment d[0] for t <= t0 (Sec. 3.2)
+          tr.p(0, p0);
+          v[0] = v[1] = v[2] = 0.0;
+          a[0] = a[1] = a[2] = 0.0;
+        } else {
+          double p1[3], v1[3], a1[3];
+          tr.p(k, p0);
+          tr.p(k + 1, p1);
+          tr.va(k, v, a);
+          tr.va(k + 1, v1, a1);
+          for (int i = 0; i < 3; ++i) {
+            p0[i] += th * (p1[i] - p0[i]);
+            v[i] += th * (v1[i] - v[i]);
+            a[i] += th * (a1[i] - a[i]);
+          }
+        }
+        double av[3] = {r[0] - p0[0], r[1] - p0[1], r[2] - p0[2]};
+        lw_add_f64<KIND>(sg == 0 ? q : -q, av, v, a, L.r_excl, E, B, &phi, A, &mask);
+      }
+    }
+  }
+  if (err) {
+    set_status(L.status, err);
+    return;
+  }
+  const int64_t o = (L.frame0 + f) * L.pts.P + p;
+  if (L.out.E) {
+    double *e = (double *)L.out.E + 3 * o;
+    e[0] = E[0];
+    e[1] = E[1];
+    e[2] = E[2];
+  }
+  if (L.out.B) {
+    double *b = (double *)L.out.B + 3 * o;
+    b[0] = B[0];
+    b[1] = B[1];
+    b[2] = B[2];
+  }
+  if (L.out.phi) ((double *)L.out.phi)[o] = phi;
+  if (L.out.A) {
+    double *a = (double *)L.out.A + 3 * o;
+    a[0] = A[0];
+    a[1] = A[1];
+    a[2] = A[2];
+  }
+  if (L.out.mask) L.out.mask[o] = mask;
+}
+
+// ================================================================================================
+// mixed path
+// ================================================================================================
+__global__ void prep_dipoles_f32(const Sources s, float4 *H) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)s.N * s.Sd;
+  if (i >= n) return;
+  int j = (int)(i / s.Sd);
+  const double q = s.qd[j];
+  const double Lc = kC * s.dtd;
+  H[i] = make_float4((float)(s.d[i] / (q * Lc)), (float)(s.dd[i] / (q * kC)), (float)(s.ddd[i] * s.dtd / (q * kC)),
+                     0.f);
+}
+
+__global__ void prep_charges_f32(const Sources s, float4 *H, double *cref) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)s.M * s.S;
+  if (i >= n) return;
+  int c = (int)(i / s.S);
+  const double *p0 = s.pos + (size_t)c * s.S * 3;
+  const double Lc = kC * s.dt;
+  const double *p = s.pos + 3 * i, *v = s.vel + 3 * i, *a = s.acc + 3 * i;
+  H[3 * i + 0] = make_float4((float)((p[0] - p0[0]) / Lc), (float)((p[1] - p0[1]) / Lc), (float)((p[2] - p0[2]) / Lc),
+                             0.f);
+  H[3 * i + 1] = make_float4((float)(v[0] / kC), (float)(v[1] / kC), (float)(v[2] / kC), 0.f);
+  H[3 * i + 2] = make_float4((float)(a[0] * s.dt / kC), (float)(a[1] * s.dt / kC), (float)(a[2] * s.dt / kC), 0.f);
+  if (i % s.S == 0) {
+    cref[3 * c] = p0[0];
+    cref[3 * c + 1] = p0[1];
+    cref[3 * c + 2] = p0[2];
+  }
+}
+
+__device__ __forceinline__ float fsqrt_approx(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// Sample j of a dipole history; before the first sample the dipole rests with moment d[0].
+__device__ __forceinline__ float4 dip_sample(const float4 *H, int64_t j) {
+  if (j >= 0) return __ldg(H + j);
+  float4 h0 = __ldg(H);
+  return make_float4(h0.x, 0.f, 0.f, 0.f);
+}
+
+// Retarded state of one dipole charge at offset sigma*mu*X along the axis from the dipole centre.
+//   xc: retarded time of the centre, in samples relative to ka (float)
+//   rn = |rho|, rp = rho . axis (units of c dt)
+// Out: X, V, Ac interpolated at the charge's own retarded time; delta = its distance minus rn.
+__device__ __forceinline__ int dip_charge_solve(const float4 *H, int64_t S, int64_t ka, float xc, float rn, float rp,
+                                                float smu, float &X, float &V, float &Ac, float &delta) {
+  if (!(fabsf(xc) < 1e8f)) return PC_ERR_NOCONV;
+  float kcf = floorf(xc);
+  float thc = xc - kcf;
+  int64_t j = ka + (int64_t)kcf;
+  // first-order estimate of the charge's delay offset picks its segment
+  {
+    float4 h = dip_sample(H, j < S ? j : S - 1);
+    float d0 = (rn > 0.f) ? -smu * h.x * __fdividef(rp, rn) : 0.f;
+    float st = floorf(thc - d0);
+    j += (int64_t)st;
+    thc -= st;
+  }
+  for (int it = 0; it < 6; ++it) {
+    if (j + 1 > S - 1) return PC_ERR_HISTORY;
+    float4 h0 = dip_sample(H, j), h1 = dip_sample(H, j + 1);
+    if (j < 0) h1 = h0;  // static segment
+    float dx = h1.x - h0.x;
+    float sc = smu * (h0.x + thc * dx);
+    float w = smu * dx;
+    float A = 1.f - w * w;
+    float B = rn - w * (rp - sc);
+    float C = sc * (2.f * rp - sc);
+    float sq = fsqrt_approx(fmaxf(B * B - A * C, 0.f));
+    float dl = (B > 0.f) ? -__fdividef(C, B + sq) : __fdividef(-B + sq, A);
+    float th = thc - dl;
+    bool ok = (j < 0) ? ((float)j + th <= 1e-4f) : (th >= -1e-4f && th <= 1.0001f);
+    if (ok) {
+      th = fminf(fmaxf(th, 0.f), 1.f);
+      X = h0.x + th * dx;
+      V = h0.y + th * (h1.y - h0.y);
+      Ac = h0.z + th * (h1.z - h0.z);
+      delta = dl;
+      return 0;
+    }
+    if (!(fabsf(th) < 1e8f)) return PC_ERR_NOCONV;
+    float st = floorf(th);
+    j += (int64_t)st;
+    thc -= st;
+  }
+  return PC_ERR_NOCONV;
+}
+
+struct Acc10 {
+  float v[10];
+};
+
+template <int KIND>
+__device__ __forceinline__ void dipole_pair_mixed(float rx, float ry, float rz, float rn, float px, float py, float pz,
+                                                  float rp, float mup, float mum, float qs, float Xp, float Vp,
+                                                  float Ap, float dp, float Xm, float Vm, float Am, float dm,
+                                                  float rex, float *acc, uint8_t &mask) {
+  // charge 1 = positive (offset +mup X), charge 0 = negative (offset -mum X)
+  const float s1 = mup * Xp, s0 = -mum * Xm, ds = mup * Xp + mum * Xm;
+  const float v1 = mup * Vp, v0 = -mum * Vm, dv = mup * Vp + mum * Vm;
+  const float a1 = mup * Ap, a0 = -mum * Am, da = mup * Ap + mum * Am;
+  const float R0 = rn + dm, dR = dp - dm, R1 = R0 + dR;
+  if (R0 <= rex || R1 <= rex) {
+    mask = 1;
+    // one charge coincides with the point: add the other one alone
+    const bool use1 = R1 > rex;
+    if (!(R0 > rex) && !use1) return;
+    const float s = use1 ? s1 : s0, v = use1 ? v1 : v0, al = use1 ? a1 : a0, R = use1 ? R1 : R0;
+    const float sign = use1 ? qs : -qs;
+    const float ap = rp - s;
+    const float Ru = R - v * ap;
+    const float i1 = __frcp_rn(Ru);
+    const float i2 = i1 * i1, i3 = i2 * i1;
+    float G = 0.f, Q = 0.f;
+    if (KIND != PC_RADIATION) G += 1.f - v * v;
+    if (KIND != PC_COULOMB) {
+      G += al * ap;
+      Q = al;
+    }
+    const float Ca = G * i3;
+    const float Cp = -R * v * G * i3 - Q * R * i2;
+    const float Bc = -v * G * i3 - Q * i2;
+    const float ax_ = rx - s * px, ay_ = ry - s * py, az_ = rz - s * pz;
+    acc[0] += sign * (Ca * ax_ + Cp * px);
+    acc[1] += sign * (Ca * ay_ + Cp * py);
+    acc[2] += sign * (Ca * az_ + Cp * pz);
+    const float cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
+    acc[3] += sign * Bc * cx;
+    acc[4] += sign * Bc * cy;
+    acc[5] += sign * Bc * cz;
+    acc[6] += sign * i1;
+    const float va = sign * v * i1;
+    acc[7] += va * px;
+    acc[8] += va * py;
+    acc[9] += va * pz;
+    return;
+  }
+  const float ap0 = rp - s0, ap1 = rp - s1, dap = -ds;
+  const float Ru0 = R0 - v0 * ap0;
+  const float dRu = dR - (dv * ap1 + v0 * dap);
+  const float Ru1 = Ru0 + dRu;
+  const float i0 = __frcp_rn(Ru0), i1 = __frcp_rn(Ru1);
+  const float di = -dRu * i0 * i1;
+  const float i02 = i0 * i0, i12 = i1 * i1;
+  const float i03 = i02 * i0, i13 = i12 * i1;
+  const float di2 = di * (i0 + i1);
+  const float di3 = di * (i12 + i1 * i0 + i02);
+  float G0 = 0.f, dG = 0.f;
+  if (KIND != PC_RADIATION) {
+    G0 += 1.f - v0 * v0;
+    dG += -dv * (v1 + v0);
+  }
+  if (KIND != PC_COULOMB) {
+    G0 += a0 * ap0;
+    dG += da * ap1 + a0 * dap;
+  }
+  const float G1 = G0 + dG;
+  const float Ca0 = G0 * i03, Ca1 = G1 * i13;
+  const float dCa = dG * i13 + G0 * di3;
+  // C_p = -R v G i^3 - alpha R i^2 ; B coefficient C_p / R = -v G i^3 - alpha i^2
+  const float P0 = R0 * v0 * G0;
+  const float dP = dR * v1 * G1 + R0 * (dv * G1 + v0 * dG);
+  float dCp = -(dP * i13 + P0 * di3);
+  const float dvG = dv * G1 + v0 * dG;
+  float dBc = -(dvG * i13 + v0 * G0 * di3);
+  if (KIND != PC_COULOMB) {
+    const float Q0 = a0 * R0, dQ = da * R1 + a0 * dR;
+    dCp -= dQ * i12 + Q0 * di2;
+    dBc -= da * i12 + a0 * di2;
+  }
+  const float ep = dCp - (Ca1 * s1 - Ca0 * s0);
+  acc[0] += qs * (dCa * rx + ep * px);
+  acc[1] += qs * (dCa * ry + ep * py);
+  acc[2] += qs * (dCa * rz + ep * pz);
+  const float cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
+  acc[3] += qs * dBc * cx;
+  acc[4] += qs * dBc * cy;
+  acc[5] += qs * dBc * cz;
+  acc[6] += qs * di;
+  const float dA = qs * (dv * i1 + v0 * di);
+  acc[7] += dA * px;
+  acc[8] += dA * py;
+  acc[9] += dA * pz;
+}
+
+// Generic charge in float32 (no pairing): Griffiths form with c = 1.
+template <int KIND>
+__device__ __forceinline__ void charge_mixed(float ax, float ay, float az, float vx, float vy, float vz, float gx,
+                                             float gy, float gz, float qs, float rex, float *acc, uint8_t &mask) {
+  const float R2 = ax * ax + ay * ay + az * az;
+  const float iR = rsqrtf(R2);
+  const float R = R2 * iR;
+  if (R <= rex) {
+    mask = 1;
+    return;
+  }
+  const float ux = ax * iR - vx, uy = ay * iR - vy, uz = az * iR - vz;
+  const float Ru = R - (ax * vx + ay * vy + az * vz);
+  const float i1 = __frcp_rn(Ru);
+  const float f = qs * R * i1 * i1 * i1;
+  float ex = 0.f, ey = 0.f, ez = 0.f;
+  if (KIND != PC_RADIATION) {
+    const float g = f * (1.f - (vx * vx + vy * vy + vz * vz));
+    ex = g * ux;
+    ey = g * uy;
+    ez = g * uz;
+  }
+  if (KIND != PC_COULOMB) {
+    const float aa = ax * gx + ay * gy + az * gz;
+    ex += f * (ux * aa - gx * Ru);
+    ey += f * (uy * aa - gy * Ru);
+    ez += f * (uz * aa - gz * Ru);
+  }
+  acc[0] += ex;
+  acc[1] += ey;
+  acc[2] += ez;
+  const float nx = ax * iR, ny = ay * iR, nz = az * iR;
+  acc[3] += ny * ez - nz * ey;
+  acc[4] += nz * ex - nx * ez;
+  acc[5] += nx * ey - ny * ex;
+  acc[6] += qs * i1;
+  acc[7] += qs * i1 * vx;
+  acc[8] += qs * i1 * vy;
+  acc[9] += qs * i1 * vz;
+}
+
+__device__ __forceinline__ void kahan_add(float *sum, float *comp, const float *part) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    float y = part[i] - comp[i];
+    float t = sum[i] + y;
+    comp[i] = (t - sum[i]) - y;
+    sum[i] = t;
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
+  __shared__ double s_anchor[3];
+  __shared__ float4 s_geo[kChunk];   // rho_a (x,y,z), |rho_a|
+  __shared__ float4 s_ax[kChunk];    // axis (x,y,z), q/e
+  __shared__ float2 s_mu[kChunk];    // m2/(m1+m2), m1/(m1+m2)
+  __shared__ long long s_ka[kChunk];
+  __shared__ float s_fa[kChunk];
+
+  const int tid = threadIdx.x;
+  const int f = blockIdx.y;
+  const Sources &s = L.src;
+  // ---- tile -> points ----
+  int64_t p;
+  if (L.pts.list) {
+    p = (int64_t)blockIdx.x * kMixThreads + tid;
+  } else {
+    int64_t tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
+    int64_t iu = tu * 16 + (tid >> 4), iv = tv * 16 + (tid & 15);
+    p = (iu < L.pts.nu && iv < L.pts.nv) ? iu * L.pts.nv + iv : L.pts.P;
+  }
+  const bool active = p < L.pts.P;
+  if (tid == 0) {
+    double a[3];
+    if (L.pts.list) {
+      int64_t pa = (int64_t)blockIdx.x * kMixThreads + kMixThreads / 2;
+      if (pa >= L.pts.P) pa = L.pts.P - 1;
+      point_at(L.pts, pa, a);
+    } else {
+      int64_t tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
+      double iu = (double)(tu * 16) + 7.5, iv = (double)(tv * 16) + 7.5;
+      for (int i = 0; i < 3; ++i) a[i] = L.pts.o[i] + iu * L.pts.eu[i] + iv * L.pts.ev[i];
+    }
+    s_anchor[0] = a[0];
+    s_anchor[1] = a[1];
+    s_anchor[2] = a[2];
+  }
+  __syncthreads();
+  double r[3];
+  point_at(L.pts, active ? p : 0, r);
+  const double t = L.times[f];
+  float sum[10], comp[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) sum[i] = comp[i] = 0.f;
+  uint8_t mask = 0;
+  int err = 0;
+  // lengths of the two source groups (c dt) and scale of group g relative to the output unit
+  const double Ld = kC * s.dtd, Lch = kC * s.dt;
+  const double Lref = (s.N > 0) ? Ld : Lch;
+
+  // ---------------- dipoles ----------------
+  if (s.N > 0) {
+    const float drx = (float)((r[0] - s_anchor[0]) / Ld), dry = (float)((r[1] - s_anchor[1]) / Ld),
+                drz = (float)((r[2] - s_anchor[2]) / Ld);
+    const float dr2 = drx * drx + dry * dry + drz * drz;
+    const double u = (t - s.t0d) / s.dtd;
+    const float rex = (float)(L.r_excl / Ld);
+    for (int base = 0; base < s.N; base += kChunk) {
+      const int nch = min(kChunk, s.N - base);
+      __syncthreads();
+      if (tid < nch) {
+        const int j = base + tid;
+        double ra[3];
+        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - s.origin[3 * j + i]) / Ld;
+        const double rna = sqrt(ra[0] * ra[0] + ra[1] * ra[1] + ra[2] * ra[2]);
+        const double x = u - rna;
+        const double kaf = floor(x);
+        s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
+        s_ax[tid] = make_float4((float)s.axis[3 * j], (float)s.axis[3 * j + 1], (float)s.axis[3 * j + 2],
+                                (float)(s.qd[j] / kE));
+        const double m1 = s.m1[j], m2 = s.m2[j];
+        s_mu[tid] = make_float2((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)));
+        s_ka[tid] = (long long)kaf;
+        s_fa[tid] = (float)(x - kaf);
+      }
+      __syncthreads();
+      if (!active || err) continue;
+      float part[10];
+#pragma unroll
+      for (int i = 0; i < 10; ++i) part[i] = 0.f;
+      for (int jj = 0; jj < nch; ++jj) {
+        const float4 g = s_geo[jj];
+        const float4 ax = s_ax[jj];
+        const float2 mu = s_mu[jj];
+        const float rx = g.x + drx, ry = g.y + dry, rz = g.z + drz;
+        const float rho2 = rx * rx + ry * ry + rz * rz;
+        const float irn = rsqrtf(rho2);
+        const float rn = rho2 > 0.f ? rho2 * irn : 0.f;
+        // |rho| - |rho_a| without cancellation
+        const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
+        const float xc = s_fa[jj] - corr;
+        const float rp = rx * ax.x + ry * ax.y + rz * ax.z;
+        const float4 *H = L.Hd + (size_t)(base + jj) * s.Sd;
+        float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
+        int e1 = dip_charge_solve(H, s.Sd, s_ka[jj], xc, rn, rp, mu.x, Xp, Vp, Ap, dp);
+        int e2 = dip_charge_solve(H, s.Sd, s_ka[jj], xc, rn, rp, -mu.y, Xm, Vm, Am, dm);
+        if (e1 | e2) {
+          err = e1 ? e1 : e2;
+          break;
+        }
+        dipole_pair_mixed<KIND>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm, Am,
+                                dm, rex, part, mask);
+        if ((jj & 7) == 7) {
+          kahan_add(sum, comp, part);
+#pragma unroll
+          for (int i = 0; i < 10; ++i) part[i] = 0.f;
+        }
+      }
+      kahan_add(sum, comp, part);
+    }
+  }
+  // ---------------- point charges ----------------
+  if (s.M > 0) {
+    const float drx = (float)((r[0] - s_anchor[0]) / Lch), dry = (float)((r[1] - s_anchor[1]) / Lch),
+                drz = (float)((r[2] - s_anchor[2]) / Lch);
+    const float dr2 = drx * drx + dry * dry + drz * drz;
+    const double u = (t - s.t0) / s.dt;
+    const float rex = (float)(L.r_excl / Lch);
+    const float sE = (float)((Lref / Lch) * (Lref / Lch)), sP = (float)(Lref / Lch);
+    for (int base = 0; base < s.M; base += kChunk) {
+      const int nch = min(kChunk, s.M - base);
+      __syncthreads();
+      if (tid < nch) {
+        const int c = base + tid;
+        double ra[3];
+        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - L.cref[3 * c + i]) / Lch;
+        const double rna = sqrt(ra[0] * ra[0] + ra[1] * ra[1] + ra[2] * ra[2]);
+        const double x = u - rna;
+        const double kaf = floor(x);
+        s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
+        s_ax[tid] = make_float4(0.f, 0.f, 0.f, (float)(s.q[c] / kE));
+        s_ka[tid] = (long long)kaf;
+        s_fa[tid] = (float)(x - kaf);
+      }
+      __syncthreads();
+      if (!active || err) continue;
+      float part[10];
+#pragma unroll
+      for (int i = 0; i < 10; ++i) part[i] = 0.f;
+      for (int cc = 0; cc < nch; ++cc) {
+        const float4 g = s_geo[cc];
+        const float qs = s_ax[cc].w;
+        const float rx = g.x + drx, ry = g.y + dry, rz = g.z + drz;
+        const float rho2 = rx * rx + ry * ry + rz * rz;
+        const float irn = rho2 > 0.f ? rsqrtf(rho2) : 0.f;
+        const float rn = rho2 * irn;
+        const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
+        const float xc = s_fa[cc] - corr;
+        if (!(fabsf(xc) < 1e8f)) {
+          err = PC_ERR_NOCONV;
+          break;
+        }
+        const float4 *H = L.Hc + (size_t)(base + cc) * s.S * 3;
+        const int64_t S = s.S;
+        // first-order estimate of the charge's delay offset: -rho_hat . o(center time)
+        float kcf = floorf(xc);
+        float thc = xc - kcf;
+        int64_t j = s_ka[cc] + (int64_t)kcf;
+        {
+          int64_t jc = j < 0 ? 0 : (j > S - 1 ? S - 1 : j);
+          float4 o = __ldg(H + 3 * jc);
+          float d0 = -(rx * o.x + ry * o.y + rz * o.z) * irn;
+          float st = floorf(thc - d0);
+          j += (int64_t)st;
+          thc -= st;
+        }
+        float ox = 0, oy = 0, oz = 0, vx = 0, vy = 0, vz = 0, gx = 0, gy = 0, gz = 0;
+        bool done = false;
+        for (int it = 0; it < 32 && !done; ++it) {
+          if (j + 1 > S - 1) {
+            err = PC_ERR_HISTORY;
+            break;
+          }
+          if (j < 0 && !s.static_before) {
+            err = PC_ERR_HISTORY;
+            break;
+          }
+          const int64_t j0 = j < 0 ? 0 : j, j1 = j < 0 ? 0 : j + 1;
+          const float4 o0 = __ldg(H + 3 * j0), o1 = __ldg(H + 3 * j1);
+          const float wx = o1.x - o0.x, wy = o1.y - o0.y, wz = o1.z - o0.z;
+          const float ocx = o0.x + thc * wx, ocy = o0.y + thc * wy, ocz = o0.z + thc * wz;
+          const float A = 1.f - (wx * wx + wy * wy + wz * wz);
+          const float B = rn - ((rx - ocx) * wx + (ry - ocy) * wy + (rz - ocz) * wz);
+          const float C = ocx * (2.f * rx - ocx) + ocy * (2.f * ry - ocy) + ocz * (2.f * rz - ocz);
+          const float sq = fsqrt_approx(fmaxf(B * B - A * C, 0.f));
+          const float dl = (B > 0.f) ? -__fdividef(C, B + sq) : __fdividef(-B + sq, A);
+          float th = thc - dl;
+          const bool ok = (j < 0) ? ((float)j + th <= 1e-4f) : (th >= -1e-4f && th <= 1.0001f);
+          if (ok) {
+            th = fminf(fmaxf(th, 0.f), 1.f);
+            if (j < 0) {
+              ox = o0.x;
+              oy = o0.y;
+              oz = o0.z;
+            } else {
+              const float4 v0 = __ldg(H + 3 * j0 + 1), v1 = __ldg(H + 3 * j1 + 1);
+              const float4 a0 = __ldg(H + 3 * j0 + 2), a1 = __ldg(H + 3 * j1 + 2);
+              ox = o0.x + th * wx;
+              oy = o0.y + th * wy;
+              oz = o0.z + th * wz;
+              vx = v0.x + th * (v1.x - v0.x);
+              vy = v0.y + th * (v1.y - v0.y);
+              vz = v0.z + th * (v1.z - v0.z);
+              gx = a0.x + th * (a1.x - a0.x);
+              gy = a0.y + th * (a1.y - a0.y);
+              gz = a0.z + th * (a1.z - a0.z);
+            }
+            done = true;
+          } else {
+            if (!(fabsf(th) < 1e8f)) break;
+            const float st = floorf(th);
+            j += (int64_t)st;
+            thc -= st;
+          }
+        }
+        if (!done) {
+          if (!err) err = PC_ERR_NOCONV;
+          break;
+        }
+        float c10[10];
+#pragma unroll
+        for (int i = 0; i < 10; ++i) c10[i] = 0.f;
+        charge_mixed<KIND>(rx - ox, ry - oy, rz - oz, vx, vy, vz, gx, gy, gz, qs, rex, c10, mask);
+        // E and B carry q through f; scale E/B by sE and phi/A by sP
+#pragma unroll
+        for (int i = 0; i < 6; ++i) part[i] += sE * c10[i];
+#pragma unroll
+        for (int i = 6; i < 10; ++i) part[i] += sP * c10[i];
+        if ((cc & 7) == 7) {
+          kahan_add(sum, comp, part);
+#pragma unroll
+          for (int i = 0; i < 10; ++i) part[i] = 0.f;
+        }
+      }
+      kahan_add(sum, comp, part);
+    }
+  }
+  if (!active) return;
+  if (err) {
+    set_status(L.status, err);
+    return;
+  }
+  // units: E in k_e e / L^2, B in k_e e / (L^2 c), phi in k_e e / L, A in k_e e / (L c)
+  const double kE2 = kKe * kE / (Lref * Lref), kP = kKe * kE / Lref;
+  const float fE = (float)kE2, fB = (float)(kE2 / kC), fP = (float)kP, fA = (float)(kP / kC);
+  const int64_t o = (L.frame0 + f) * L.pts.P + p;
+  if (L.out.E) {
+    float *e = (float *)L.out.E + 3 * o;
+    e[0] = fE * (sum[0] - comp[0]);
+    e[1] = fE * (sum[1] - comp[1]);
+    e[2] = fE * (sum[2] - comp[2]);
+  }
+  if (L.out.B) {
+    float *b = (float *)L.out.B + 3 * o;
+    b[0] = fB * (sum[3] - comp[3]);
+    b[1] = fB * (sum[4] - comp[4]);
+    b[2] = fB * (sum[5] - comp[5]);
+  }
+  if (L.out.phi) ((float *)L.out.phi)[o] = fP * (sum[6] - comp[6]);
+  if (L.out.A) {
+    float *a = (float *)L.out.A + 3 * o;
+    a[0] = fA * (sum[7] - comp[7]);
+    a[1] = fA * (sum[8] - comp[8]);
+    a[2] = fA * (sum[9] - comp[9]);
+  }
+  if (L.out.mask) L.out.mask[o] = mask;
+}
+
+// ================================================================================================
+// host side
+// ================================================================================================
+static bool finite3(const double *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const double *list,
+                             const pc_plane *plane, int64_t P, const double *times, int32_t T, int32_t kind,
+                             int32_t precision, double r_excl, const pc_field_out *out, void *stream) {
+  if (!ctx || !out || !times || T < 1 || P < 0) return PC_ERR_ARG;
+  if (kind < PC_TOTAL || kind > PC_RADIATION || (precision != PC_F64 && precision != PC_MIXED)) return PC_ERR_ARG;
+  if (!(r_excl >= 0.0)) return PC_ERR_ARG;
+  const bool has_ch = ch && ch->M > 0, has_dp = dp && dp->N > 0;
+  if (!has_ch && !has_dp) return PC_ERR_ARG;
+  if ((ch && ch->M < 0) || (dp && dp->N < 0)) return PC_ERR_ARG;
+  if (has_ch && (ch->S < 2 || !(ch->dt > 0.0) || !isfinite(ch->t0) || !ch->q || !ch->pos || !ch->vel || !ch->acc))
+    return PC_ERR_ARG;
+  if (has_dp && (dp->S < 2 || !(dp->dt > 0.0) || !isfinite(dp->t0) || !dp->origin || !dp->axis || !dp->q ||
+                 !dp->m1 || !dp->m2 || !dp->d || !dp->d_dot || !dp->d_ddot))
+    return PC_ERR_ARG;
+  if (!list && !plane) return PC_ERR_ARG;
+  if (list == nullptr && plane && (plane->nu < 0 || plane->nv < 0 || !finite3(plane->origin) ||
+                                   !finite3(plane->eu) || !finite3(plane->ev)))
+    return PC_ERR_ARG;
+  for (int i = 0; i < T; ++i)
+    if (!isfinite(times[i])) return PC_ERR_ARG;
+  if (P == 0) return PC_OK;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+
+  Launch L;
+  memset(&L, 0, sizeof(L));
+  L.pts.list = list;
+  L.pts.P = P;
+  if (!list) {
+    for (int i = 0; i < 3; ++i) {
+      L.pts.o[i] = plane->origin[i];
+      L.pts.eu[i] = plane->eu[i];
+      L.pts.ev[i] = plane->ev[i];
+    }
+    L.pts.nu = plane->nu;
+    L.pts.nv = plane->nv;
+  }
+  Sources &s = L.src;
+  if (has_ch) {
+    s.M = ch->M;
+    s.S = ch->S;
+    s.t0 = ch->t0;
+    s.dt = ch->dt;
+    s.q = ch->q;
+    s.pos = ch->pos;
+    s.vel = ch->vel;
+    s.acc = ch->acc;
+    s.static_before = ch->static_before;
+  }
+  if (has_dp) {
+    s.N = dp->N;
+    s.Sd = dp->S;
+    s.t0d = dp->t0;
+    s.dtd = dp->dt;
+    s.origin = dp->origin;
+    s.axis = dp->axis;
+    s.qd = dp->q;
+    s.m1 = dp->m1;
+    s.m2 = dp->m2;
+    s.d = dp->d;
+    s.dd = dp->d_dot;
+    s.ddd = dp->d_ddot;
+  }
+  L.out.E = out->E;
+  L.out.B = out->B;
+  L.out.phi = out->phi;
+  L.out.A = out->A;
+  L.out.mask = out->mask;
+  L.r_excl = r_excl;
+  L.status = ctx->d_status;
+
+  if (precision == PC_MIXED) {
+    size_t nd = has_dp ? (size_t)s.N * s.Sd : 0, nc = has_ch ? (size_t)s.M * s.S * 3 : 0;
+    if (ctx->hist_f32.reserve((nd + nc) * sizeof(float4)) != cudaSuccess) return PC_ERR_CUDA;
+    if (has_ch && ctx->charge_ref.reserve((size_t)s.M * 3 * sizeof(double)) != cudaSuccess) return PC_ERR_CUDA;
+    float4 *Hd = (float4 *)ctx->hist_f32.ptr;
+    float4 *Hc = Hd + nd;
+    L.Hd = Hd;
+    L.Hc = Hc;
+    L.cref = (const double *)ctx->charge_ref.ptr;
+    if (has_dp) {
+      int64_t n = (int64_t)nd;
+      prep_dipoles_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hd);
+    }
+    if (has_ch) {
+      int64_t n = (int64_t)s.M * s.S;
+      prep_charges_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hc, (double *)ctx->charge_ref.ptr);
+    }
+  }
+  for (int32_t f0 = 0; f0 < T; f0 += kMaxT) {
+    L.T = min(kMaxT, T - f0);
+    L.frame0 = f0;
+    for (int i = 0; i < L.T; ++i) L.times[i] = times[f0 + i];
+    if (precision == PC_F64) {
+      dim3 grid((unsigned)((P + 127) / 128), (unsigned)L.T);
+      if (kind == PC_TOTAL) fields_f64_kernel<PC_TOTAL><<<grid, 128, 0, st>>>(L);
+      else if (kind == PC_COULOMB) fields_f64_kernel<PC_COULOMB><<<grid, 128, 0, st>>>(L);
+      else fields_f64_kernel<PC_RADIATION><<<grid, 128, 0, st>>>(L);
+    } else {
+      int64_t tiles, tiles_v = 1;
+      if (list) {
+        tiles = (P + kMixThreads - 1) / kMixThreads;
+      } else {
+        int64_t tu = (L.pts.nu + 15) / 16;
+        tiles_v = (L.pts.nv + 15) / 16;
+        tiles = tu * tiles_v;
+      }
+      dim3 grid((unsigned)tiles, (unsigned)L.T);
+      if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+      else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+      else fields_mixed_kernel<PC_RADIATION><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+    }
+  }
+  return end_call(ctx, st);
+}
+
+}  // namespace pc
+
+extern "C" pc_status pc_fields(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const double *points,
+                               int64_t P, const double *times, int32_t T, int32_t kind, int32_t precision,
+                               double r_excl, const pc_field_out *out, void *stream) {
+  if (P > 0 && !points) return PC_ERR_ARG;
+  return pc::fields_impl(ctx, ch, dp, points, nullptr, P, times, T, kind, precision, r_excl, out, stream);
+}
+
+extern "C" pc_status pc_fields_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,
+                                     const pc_plane *grid, const double *times, int32_t T, int32_t kind,
+                                     int32_t precision, double r_excl, const pc_field_out *out, void *stream) {
+  if (!grid || grid->nu < 0 || grid->nv < 0) return PC_ERR_ARG;
+  return pc::fields_impl(ctx, ch, dp, nullptr, grid, grid->nu * grid->nv, times, T, kind, precision, r_excl, out,
+                         stream);
+}

@@ -1,0 +1,96 @@
+"""Parity of pc_dipoles_run and pc_ke_fit (CUDA, through the C ABI) with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2107_12437_gb300 as pc
+import workloads as W
+from oracle import fit, theory as th
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pc.Context(0)
+    yield c
+    c.close()
+
+
+def hist_err(gpu, ref):
+    g = gpu.cpu().numpy() if isinstance(gpu, torch.Tensor) else gpu
+    return float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+
+
+def test_listing2_f64_history_and_fit(ctx):
+    cfg = W.listing2()
+    ref = oracle.dipoles_run(cfg)
+    assert ref["status"] == oracle.OK
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, fit=True,
+                            first_index=cfg.first_index, want_Ed=True)
+    for k in ("d", "d_dot", "d_ddot", "energy", "Ed"):
+        assert hist_err(out[k][0], ref[k]) < 1e-10, k
+    m = W.M_E / 2
+    g0 = th.gamma0(W.E_CHARGE, m, cfg.omega0[0, 0])
+    for i in range(2):
+        ke = m * ref["d_dot"][i] ** 2 / (2 * W.E_CHARGE ** 2)
+        f = fit.ke_fit(ke, cfg.dt, cfg.first_index)
+        w = float(out["omega"][0, i])
+        g = float(out["gamma"][0, i])
+        assert abs(w - f["omega"]) / f["omega"] < 1e-11
+        assert abs(g - f["gamma"]) / g0 < 1e-5
+        # the paper prints delta_12 = 156.919 gamma0 for this listing
+        assert round((w - cfg.omega0[0, 0]) / g0, 3) == 156.919
+
+
+def test_cfg3_subset_batched(ctx):
+    # eight separations of config 3 in one launch (1 nm .. 1 um), 12 000 steps, against the oracle
+    cfg, sep = W.cfg3(B=256, n_steps=12000)
+    sel = np.array([0, 30, 70, 110, 150, 190, 230, 255])
+    sub = W.lo_batch(cfg.origin[sel], cfg.axis[sel], cfg.omega0[0, 0], 1e-11, cfg.dt, cfg.n_steps, 4000)
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(sub), sub.dt, sub.n_steps)
+    for b in range(len(sel)):
+        ref = oracle.dipoles_run(sub, b=b)
+        assert ref["status"] == oracle.OK
+        for k in ("d", "d_dot", "energy"):
+            assert hist_err(out[k][b], ref[k]) < 1e-10, (b, k)
+
+
+def test_isolated_lo_matches_closed_form(ctx):
+    # one dipole alone: E_d = 0 and d(t) is the damped oscillator of Eq. LO_equation
+    dt = 1e-17
+    cfg = W.lo_batch([[[0.0, 0.0, 0.0]]], [[[0.0, 0.0, 1.0]]], 2 * math.pi * 200e12, 1e-11, dt, 2000, 0)
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), dt, cfg.n_steps)
+    t = np.arange(cfg.n_steps + 1) * dt
+    g0 = th.gamma0(W.E_CHARGE, W.M_E / 2, cfg.omega0[0, 0])
+    d_ex, _ = th.isolated_lo(t, cfg.d0[0, 0], cfg.omega0[0, 0], g0)
+    assert hist_err(out["d"][0, 0], d_ex) < 1e-7
+
+
+def test_causality_and_velocity_errors(ctx):
+    origins = np.array([[[0.0, 0.0, 0.0], [0.2e-9, 0.0, 0.0]]])
+    axes = np.array([[[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]])
+    cfg = W.lo_batch(origins, axes, 2 * math.pi * 200e12, 1e-12, 1e-18, 10, 0)
+    with pytest.raises(pc.PcError) as ei:
+        pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps)
+    assert ei.value.status == pc.capi.PC_ERR_CAUSALITY
+    cfg = W.lo_batch([[[0.0, 0.0, 0.0]]], [[[1.0, 0.0, 0.0]]], 2 * math.pi * 200e12, 1e-8, 1e-18, 2000, 0)
+    with pytest.raises(pc.PcError) as ei:
+        pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps)
+    assert ei.value.status == pc.capi.PC_ERR_VELOCITY
+
+
+@pytest.mark.parametrize("gamma", [0.0, 2e7, 3e10])
+def test_ke_fit_synthetic(ctx, gamma):
+    dt = 1e-18
+    w = 2 * math.pi * 200e12 * (1 + 3.1e-7)
+    t = np.arange(40000) * dt
+    ke = 2.5e-21 * np.exp(-gamma * t) * np.sin(w * t + 0.4) ** 2
+    f = fit.ke_fit(ke, dt, 10000)
+    g, om, a, p = pc.pc_ke_fit(ctx, torch.as_tensor(ke[None], device="cuda"), dt, 10000)
+    assert abs(float(om[0]) / w - 1) < 1e-10
+    assert abs(float(g[0]) - gamma) < 1e-6 * max(gamma, 2e7)
+    assert abs(float(om[0]) - f["omega"]) / w < 1e-11

@@ -1,0 +1,219 @@
+"""Parity of pc_fields / pc_fields_plane (CUDA, through the C ABI) with the FP64 oracle.
+
+Error metric per point: |F_gpu - F_oracle|_2 / |F_oracle|_2 over the vector (E, B, A) or the scalar
+phi, maximum over unmasked points.  Tolerances: 1e-10 for the float64 path, 1e-5 for the mixed path
+on dipole sources (pair difference form).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2107_12437_gb300 as pc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+MIX_TOL = 1e-5
+R_EXCL = 1e-15
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pc.Context(0)
+    yield c
+    c.close()
+
+
+def rel_err(gpu, ref, mask=None):
+    g = np.asarray(gpu, dtype=np.float64)
+    r = np.asarray(ref, dtype=np.float64)
+    if r.ndim == g.ndim and g.shape[-1] == 3:
+        num = np.linalg.norm(g - r, axis=-1)
+        den = np.linalg.norm(r, axis=-1)
+    else:
+        num = np.abs(g - r)
+        den = np.abs(r)
+    if mask is not None:
+        num = num[~mask]
+        den = den[~mask]
+    return float(np.max(num / den))
+
+
+def compare(out, ref, tol, keys=("E", "B", "phi", "A")):
+    m = ref["mask"].astype(bool)
+    assert np.array_equal(out["mask"].cpu().numpy().astype(bool), m)
+    errs = {}
+    for k in keys:
+        errs[k] = rel_err(out[k].cpu().numpy(), ref[k], m)
+    for k, e in errs.items():
+        assert e < tol, (k, e, errs)
+    return errs
+
+
+# ------------------------------------------------------------------------------------------------
+# config 1: two point charges, 101 x 101 grid, float64
+# ------------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg1_data():
+    ch, pts, times = W.cfg1()
+    # the grid point nearest the static charge is 9e-24 m from it: r_excl = 1 fm masks it on both sides
+    refs = {k: oracle.fields(pts, times, charges=ch, kind=k, r_excl=R_EXCL)
+            for k in (pc.PC_TOTAL, pc.PC_COULOMB, pc.PC_RADIATION)}
+    return ch, pts, times, refs
+
+
+@pytest.mark.parametrize("kind", [pc.PC_TOTAL, pc.PC_COULOMB, pc.PC_RADIATION])
+def test_cfg1_f64_list(ctx, cfg1_data, kind):
+    ch, pts, times, refs = cfg1_data
+    assert refs[kind]["status"] == oracle.OK
+    out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(pts, device="cuda"),
+                       times=list(times), kind=kind, precision=pc.PC_F64, r_excl=R_EXCL)
+    # the static charge sits within r_excl of one grid point: exactly one masked point
+    assert int(out["mask"].sum()) == 1
+    keys = ("E", "B", "phi", "A") if kind == pc.PC_TOTAL else ("E", "B")
+    compare(out, refs[kind], F64_TOL, keys)
+
+
+def test_cfg1_f64_plane_matches_list(ctx, cfg1_data):
+    ch, pts, times, refs = cfg1_data
+    g = np.linspace(-50e-9, 50e-9, 101)
+    out = pc.pc_fields_plane(ctx, charges=pc.charges_to_device(ch), origin=(g[0], g[0], 0.0),
+                             eu=(g[1] - g[0], 0, 0), ev=(0, g[1] - g[0], 0), nu=101, nv=101, times=list(times))
+    # plane points are generated on the device: agree with the oracle on its own point list
+    m = refs[pc.PC_TOTAL]["mask"].astype(bool)
+    # grid spacing rounding moves points by ~1e-24 m: compare at the float64 tolerance
+    assert rel_err(out["E"].cpu().numpy(), refs[pc.PC_TOTAL]["E"], m | out["mask"].cpu().numpy().astype(bool)) < 1e-9
+
+
+def test_cfg1_mixed(ctx, cfg1_data):
+    ch, pts, times, refs = cfg1_data
+    out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(pts, device="cuda"),
+                       times=list(times), precision=pc.PC_MIXED, r_excl=R_EXCL)
+    ref = refs[pc.PC_TOTAL]
+    m = ref["mask"].astype(bool)
+    # unpaired charges in float32: the +-e pair (1 nm) seen from up to 70 nm cancels by R/s <= 70
+    e = rel_err(out["E"].cpu().numpy(), ref["E"], m)
+    assert e < 2e-5, e
+
+
+# ------------------------------------------------------------------------------------------------
+# config 2: 64 oscillating dipoles, plane at z = 0.5 um; sub-grids that the oracle finishes in seconds
+# ------------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg2_sub():
+    dp, g, z, times = W.cfg2()
+    # 61 x 53 strided sub-grid (several 16 x 16 tiles plus ragged edges) and two frames
+    iu = np.arange(0, 2048, 34)[:61]
+    iv = np.arange(5, 2048, 39)[:53]
+    gu, gv = g[iu], g[iv]
+    pts = W.plane_grid(gu, gv, z)
+    tsel = times[[0, 11]]
+    ref = oracle.fields(pts, tsel, dipoles=dp)
+    assert ref["status"] == oracle.OK
+    return dp, pts, tsel, ref
+
+
+@pytest.mark.parametrize("prec,tol", [(pc.PC_F64, F64_TOL), (pc.PC_MIXED, MIX_TOL)])
+def test_cfg2_dipoles_list(ctx, cfg2_sub, prec, tol):
+    dp, pts, tsel, ref = cfg2_sub
+    out = pc.pc_fields(ctx, dipoles=pc.dipoles_to_device(dp), points=torch.as_tensor(pts, device="cuda"),
+                       times=list(tsel), precision=prec)
+    compare(out, ref, tol)
+
+
+def test_cfg2_generic_charges_f64(ctx, cfg2_sub):
+    dp, pts, tsel, ref = cfg2_sub
+    ch = W.dipoles_as_charges(dp)
+    out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(pts[:700], device="cuda"),
+                       times=list(tsel), precision=pc.PC_F64)
+    sub = {k: v[:, :700] for k, v in ref.items() if k != "status"}
+    compare(out, sub, F64_TOL)
+
+
+@pytest.mark.parametrize("prec,tol", [(pc.PC_F64, F64_TOL), (pc.PC_MIXED, MIX_TOL)])
+def test_cfg2_plane_tiles(ctx, prec, tol):
+    # a contiguous 40 x 37 block of the full grid: 2-D tiles with ragged edges in both directions
+    dp, g, z, times = W.cfg2()
+    u0, v0 = 700, 1301
+    nu, nv = 40, 37
+    pts = W.plane_grid(g[u0:u0 + nu], g[v0:v0 + nv], z)
+    ref = oracle.fields(pts, times[[3]], dipoles=dp)
+    step = g[1] - g[0]
+    out = pc.pc_fields_plane(ctx, dipoles=pc.dipoles_to_device(dp), origin=(g[u0], g[v0], z), eu=(step, 0, 0),
+                             ev=(0, step, 0), nu=nu, nv=nv, times=[times[3]], precision=prec)
+    # device-generated points differ from linspace by rounding (~1e-22 m): negligible at both tolerances
+    compare(out, ref, tol)
+
+
+def test_cfg2_full_size_sampled(ctx):
+    # the launch the benchmark times: 2048 x 2048 plane, 16 frames, mixed precision, float32 outputs
+    dp, g, z, times = W.cfg2()
+    step = g[1] - g[0]
+    out = pc.pc_fields_plane(ctx, dipoles=pc.dipoles_to_device(dp), origin=(0.0, 0.0, z), eu=(step, 0, 0),
+                             ev=(0, step, 0), nu=2048, nv=2048, times=list(times), precision=pc.PC_MIXED)
+    for k in ("E", "B", "phi", "A"):
+        assert torch.isfinite(out[k]).all()
+    rng = np.random.default_rng(99)
+    idx = rng.integers(0, 2048 * 2048, size=96)
+    fr = [0, 7, 15]
+    iu, iv = idx // 2048, idx % 2048
+    pts = np.stack([iu * step, iv * step, np.full(idx.size, z)], axis=1)
+    ref = oracle.fields(pts, times[fr], dipoles=dp)
+    sub = {k: out[k][fr][:, idx] for k in ("E", "B", "phi", "A", "mask")}
+    compare(sub, ref, MIX_TOL)
+
+
+# ------------------------------------------------------------------------------------------------
+# edge cases and errors
+# ------------------------------------------------------------------------------------------------
+def test_empty_points(ctx, cfg1_data):
+    ch = cfg1_data[0]
+    out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.zeros((0, 3), dtype=torch.float64,
+                                                                                  device="cuda"), times=[1e-14])
+    assert out["E"].shape == (1, 0, 3)
+
+
+def test_history_error_and_static_extension(ctx):
+    ch, pts, _ = W.cfg1()
+    ch.static_before = 0
+    chd = pc.charges_to_device(ch)
+    ptd = torch.as_tensor(pts, device="cuda")
+    with pytest.raises(pc.PcError) as ei:
+        pc.pc_fields(ctx, charges=chd, points=ptd, times=[1e-16])
+    assert ei.value.status == pc.capi.PC_ERR_HISTORY
+    ch.static_before = 1
+    ref = oracle.fields(pts, [1e-16], charges=ch, r_excl=R_EXCL)
+    out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=ptd, times=[1e-16], r_excl=R_EXCL)
+    compare(out, ref, F64_TOL, ("E",))
+    # evaluating after the last sample: retarded times beyond the history
+    with pytest.raises(pc.PcError) as ei:
+        pc.pc_fields(ctx, charges=chd, points=ptd[:3], times=[10.5e-15])
+    assert ei.value.status == pc.capi.PC_ERR_HISTORY
+
+
+def test_bad_arguments(ctx, cfg1_data):
+    ch = pc.charges_to_device(cfg1_data[0])
+    ptd = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    for kw in (dict(kind=7), dict(precision=5), dict(r_excl=-1.0), dict(times=[float("nan")])):
+        args = dict(charges=ch, points=ptd, times=[1e-14])
+        args.update(kw)
+        with pytest.raises(pc.PcError) as ei:
+            pc.pc_fields(ctx, **args)
+        assert ei.value.status == pc.capi.PC_ERR_ARG
+    with pytest.raises(pc.PcError):
+        pc.pc_fields(ctx, points=ptd, times=[1e-14])  # no sources
+
+
+def test_many_frames_split_launches(ctx):
+    # more than 32 times per call: the host splits the launch; frames stay in order
+    ch, pts, _ = W.cfg1()
+    times = np.linspace(8e-15, 10e-15, 40)
+    sel = pts[::997]
+    ref = oracle.fields(sel, times, charges=ch, r_excl=R_EXCL)
+    out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(sel, device="cuda"),
+                       times=list(times), r_excl=R_EXCL)
+    compare(out, ref, F64_TOL, ("E", "phi"))
