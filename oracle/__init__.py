@@ -124,10 +124,16 @@ def fields(points, times, charges=None, dipoles=None, kind=TOTAL, r_excl=0.0, nt
     A = np.zeros((T, P, 3))
     phi = np.zeros((T, P))
     mask = np.zeros((T, P), dtype=np.uint8)
+    scale = np.zeros((T, P, 8))
     st = lib().orc_fields(ctypes.byref(s), _ptr(pts), ctypes.c_int64(P), _ptr(tms), ctypes.c_int32(T),
                           ctypes.c_int32(kind), ctypes.c_double(r_excl), _ptr(E), _ptr(B), _ptr(phi), _ptr(A),
-                          mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.c_int32(nthreads))
-    return dict(E=E, B=B, A=A, phi=phi, mask=mask, status=st)
+                          mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _ptr(scale), ctypes.c_int32(nthreads))
+    # scale_charge: per-term magnitude sums over charges (E and B: |E_Coul| + |E_rad| of each term, B in
+    # units of E/c); scale_source: |E|, |B|, |phi|, |A| summed over sources (a dipole's two charges
+    # summed first).  They tell how strongly the superposition cancels.
+    return dict(E=E, B=B, A=A, phi=phi, mask=mask, status=st,
+                scale_charge=dict(E=scale[..., 0], B=scale[..., 1], phi=scale[..., 2], A=scale[..., 3]),
+                scale_source=dict(E=scale[..., 4], B=scale[..., 5], phi=scale[..., 6], A=scale[..., 7]))
 
 
 def retarded_delay(c, t, r, charges=None, dipoles=None):

@@ -276,11 +276,17 @@ void orc_lw_jackson(double q, const double aR[3], const double v[3], const doubl
  * *mask.  Outputs are overwritten.
  */
 static int fields_at(const orc_sources *s, const double r[3], double t, int kind, double r_excl, int exclude,
-                     double E[3], double B[3], double *phi, double A[3], uint8_t *mask) {
+                     double E[3], double B[3], double *phi, double A[3], uint8_t *mask, double *scale) {
   int nc = orc_n_charges(s);
   for (int i = 0; i < 3; ++i) { E[i] = 0.0; B[i] = 0.0; A[i] = 0.0; }
   *phi = 0.0;
   *mask = 0;
+  /* scale (optional, 8 values): sums over charges of |E_Coul,c| + |E_rad,c|, the same over c,
+     |phi_c| and |A_c|; then |E|, |B|, |phi|, |A| summed over sources, a dipole's two charges
+     counting as one source.  They measure how much the superposition cancels; they do not enter
+     E, B, phi, A. */
+  double src[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}; /* running field of the current dipole: E, B, phi, A */
+  if (scale) for (int i = 0; i < 8; ++i) scale[i] = 0.0;
   for (int c = 0; c < nc; ++c) {
     if (exclude >= 0 && c >= s->M && (c - s->M) / 2 == exclude) continue;
     double tp;
@@ -291,7 +297,17 @@ static int fields_at(const orc_sources *s, const double r[3], double t, int kind
     if (st) return st;
     double aR[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
     double R = sqrt(dot3(aR, aR));
-    if (R <= r_excl) { *mask = 1; continue; }
+    if (R <= r_excl) {
+      *mask = 1;
+      if (scale && c >= s->M && (c - s->M) % 2 == 1) {
+        scale[4] += sqrt(src[0] * src[0] + src[1] * src[1] + src[2] * src[2]);
+        scale[5] += sqrt(src[3] * src[3] + src[4] * src[4] + src[5] * src[5]);
+        scale[6] += fabs(src[6]);
+        scale[7] += sqrt(src[7] * src[7] + src[8] * src[8] + src[9] * src[9]);
+        for (int i = 0; i < 10; ++i) src[i] = 0.0;
+      }
+      continue;
+    }
     double Ec[3], Er[3], ph, Ac[3];
     lw_jackson(qc, aR, v, a, Ec, Er, &ph, Ac);
     double Ek[3];
@@ -305,15 +321,37 @@ static int fields_at(const orc_sources *s, const double r[3], double t, int kind
       A[i] += Ac[i];
     }
     *phi += ph;
+    if (scale) {
+      /* E of a term is built from its Coulomb and radiation parts, and B = n x E / c of a nearly
+         radial E is a small cross product: both round at (|E_Coul| + |E_rad|) of the term */
+      double ecr = sqrt(dot3(Ec, Ec)) + sqrt(dot3(Er, Er));
+      scale[0] += ecr;
+      scale[1] += ecr / ORC_C;
+      scale[2] += fabs(ph);
+      scale[3] += sqrt(dot3(Ac, Ac));
+      int dip = (c >= s->M);
+      for (int i = 0; i < 3; ++i) { src[i] += Ek[i]; src[3 + i] += nE[i] / ORC_C; src[7 + i] += Ac[i]; }
+      src[6] += ph;
+      /* close the source after a point charge, or after the second charge of a dipole */
+      if (!dip || ((c - s->M) % 2 == 1)) {
+        scale[4] += sqrt(src[0] * src[0] + src[1] * src[1] + src[2] * src[2]);
+        scale[5] += sqrt(src[3] * src[3] + src[4] * src[4] + src[5] * src[5]);
+        scale[6] += fabs(src[6]);
+        scale[7] += sqrt(src[7] * src[7] + src[8] * src[8] + src[9] * src[9]);
+        for (int i = 0; i < 10; ++i) src[i] = 0.0;
+      }
+    }
   }
   return ORC_OK;
 }
 
 /*
  * Fields on P points at T times: E, B, A [T][P][3], phi [T][P], mask [T][P] (Sec. 2.2, Sec. 3.2).
+ * scale (or NULL): [T][P][8] magnitude sums of the superposed terms, see fields_at.
  */
 int orc_fields(const orc_sources *s, const double *points, int64_t P, const double *times, int32_t T, int32_t kind,
-               double r_excl, double *E, double *B, double *phi, double *A, uint8_t *mask, int32_t nthreads) {
+               double r_excl, double *E, double *B, double *phi, double *A, uint8_t *mask, double *scale,
+               int32_t nthreads) {
   if (kind < 0 || kind > 2 || P < 0 || T < 0) return ORC_ERR_ARG;
   int status = ORC_OK;
   int64_t total = P * (int64_t)T;
@@ -324,7 +362,7 @@ int orc_fields(const orc_sources *s, const double *points, int64_t P, const doub
   for (int64_t idx = 0; idx < total; ++idx) {
     int64_t f = idx / P, pidx = idx % P;
     int st = fields_at(s, points + 3 * pidx, times[f], kind, r_excl, -1, E + 3 * idx, B + 3 * idx, phi + idx,
-                       A + 3 * idx, mask + idx);
+                       A + 3 * idx, mask + idx, scale ? scale + 8 * idx : NULL);
     if (st) {
 #ifdef _OPENMP
 #pragma omp critical
@@ -391,16 +429,16 @@ int orc_dipoles_run(int32_t N, const double *origin, const double *axis, const d
       int st = ORC_OK;
       const double *p = axis + 3 * i;
       if (n == 0) {
-        st = fields_at(&s, origin + 3 * i, t, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk);
+        st = fields_at(&s, origin + 3 * i, t, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
         ed_now[i] = dot3(p, E);
         if (Ed) Ed[(int64_t)i * S] = ed_now[i];
       }
       if (!st) {
-        st = fields_at(&s, origin + 3 * i, t + 0.5 * dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk);
+        st = fields_at(&s, origin + 3 * i, t + 0.5 * dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
         ed_half[i] = dot3(p, E);
       }
       if (!st) {
-        st = fields_at(&s, origin + 3 * i, t + dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk);
+        st = fields_at(&s, origin + 3 * i, t + dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
         ed_next[i] = dot3(p, E);
       }
       if (st) {

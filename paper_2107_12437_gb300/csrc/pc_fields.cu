@@ -17,6 +17,7 @@
 #include <stdio.h>
 
 #include "pc_internal.cuh"
+#include "pc_lw_f32.cuh"
 #include "pc_lw_f64.cuh"
 
 namespace pc {
@@ -24,6 +25,8 @@ namespace pc {
 constexpr int kMaxT = 32;        // times per launch (the host splits longer lists)
 constexpr int kMixThreads = 256; // points per CTA in the mixed path
 constexpr int kChunk = 64;       // sources staged in shared memory at a time
+// dipoles closer than this many c*dt to a point are summed in float64 (see the kernel comment)
+constexpr float kNearL = 320.f;
 
 struct Points {
   const double *list;  // [P][3] or null for a plane
@@ -240,158 +243,99 @@ __global__ void prep_charges_f32(const Sources s, float4 *H, double *cref) {
   }
 }
 
-__device__ __forceinline__ float fsqrt_approx(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
-
-// Sample j of a dipole history; before the first sample the dipole rests with moment d[0].
-__device__ __forceinline__ float4 dip_sample(const float4 *H, int64_t j) {
-  if (j >= 0) return __ldg(H + j);
-  float4 h0 = __ldg(H);
-  return make_float4(h0.x, 0.f, 0.f, 0.f);
-}
-
-// Retarded state of one dipole charge at offset sigma*mu*X along the axis from the dipole centre.
-//   xc: retarded time of the centre, in samples relative to ka (float)
-//   rn = |rho|, rp = rho . axis (units of c dt)
-// Out: X, V, Ac interpolated at the charge's own retarded time; delta = its distance minus rn.
-__device__ __forceinline__ int dip_charge_solve(const float4 *H, int64_t S, int64_t ka, float xc, float rn, float rp,
-                                                float smu, float &X, float &V, float &Ac, float &delta) {
-  if (!(fabsf(xc) < 1e8f)) return PC_ERR_NOCONV;
-  float kcf = floorf(xc);
-  float thc = xc - kcf;
-  int64_t j = ka + (int64_t)kcf;
-  // first-order estimate of the charge's delay offset picks its segment
-  {
-    float4 h = dip_sample(H, j < S ? j : S - 1);
-    float d0 = (rn > 0.f) ? -smu * h.x * __fdividef(rp, rn) : 0.f;
-    float st = floorf(thc - d0);
-    j += (int64_t)st;
-    thc -= st;
-  }
-  for (int it = 0; it < 6; ++it) {
-    if (j + 1 > S - 1) return PC_ERR_HISTORY;
-    float4 h0 = dip_sample(H, j), h1 = dip_sample(H, j + 1);
-    if (j < 0) h1 = h0;  // static segment
-    float dx = h1.x - h0.x;
-    float sc = smu * (h0.x + thc * dx);
-    float w = smu * dx;
-    float A = 1.f - w * w;
-    float B = rn - w * (rp - sc);
-    float C = sc * (2.f * rp - sc);
-    float sq = fsqrt_approx(fmaxf(B * B - A * C, 0.f));
-    float dl = (B > 0.f) ? -__fdividef(C, B + sq) : __fdividef(-B + sq, A);
-    float th = thc - dl;
-    bool ok = (j < 0) ? ((float)j + th <= 1e-4f) : (th >= -1e-4f && th <= 1.0001f);
-    if (ok) {
-      th = fminf(fmaxf(th, 0.f), 1.f);
-      X = h0.x + th * dx;
-      V = h0.y + th * (h1.y - h0.y);
-      Ac = h0.z + th * (h1.z - h0.z);
-      delta = dl;
-      return 0;
-    }
-    if (!(fabsf(th) < 1e8f)) return PC_ERR_NOCONV;
-    float st = floorf(th);
-    j += (int64_t)st;
-    thc -= st;
-  }
-  return PC_ERR_NOCONV;
-}
-
-struct Acc10 {
-  float v[10];
+// ---- float-float arithmetic (error-free transformations with fma) for list-mode delays ----
+struct ff {
+  float hi, lo;
 };
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  float lo = s.lo + a.lo + b.lo;
+  return ff_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  float s0 = sqrtf(a.hi);
+  if (!(s0 > 0.f)) return {0.f, 0.f};
+  float r = fmaf(-s0, s0, a.hi) + a.lo;  // a - s0^2
+  return ff_two_sum(s0, r / (2.f * s0));
+}
+__device__ __forceinline__ ff ff_from_double(double x) {
+  float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
 
+// Both charges of dipole j in float64 (plain per-charge evaluation), added to the float32
+// accumulators in their units.  Used for points within kNearL of the dipole, where the float32
+// difference form loses accuracy: there the sampled position X and velocity V at the retarded
+// time combine as X + R V, which nearly vanishes whenever the dipole's instantaneous moment
+// crosses zero.
 template <int KIND>
-__device__ __forceinline__ void dipole_pair_mixed(float rx, float ry, float rz, float rn, float px, float py, float pz,
-                                                  float rp, float mup, float mum, float qs, float Xp, float Vp,
-                                                  float Ap, float dp, float Xm, float Vm, float Am, float dm,
-                                                  float rex, float *acc, uint8_t &mask) {
-  // charge 1 = positive (offset +mup X), charge 0 = negative (offset -mum X)
-  const float s1 = mup * Xp, s0 = -mum * Xm, ds = mup * Xp + mum * Xm;
-  const float v1 = mup * Vp, v0 = -mum * Vm, dv = mup * Vp + mum * Vm;
-  const float a1 = mup * Ap, a0 = -mum * Am, da = mup * Ap + mum * Am;
-  const float R0 = rn + dm, dR = dp - dm, R1 = R0 + dR;
-  if (R0 <= rex || R1 <= rex) {
-    mask = 1;
-    // one charge coincides with the point: add the other one alone
-    const bool use1 = R1 > rex;
-    if (!(R0 > rex) && !use1) return;
-    const float s = use1 ? s1 : s0, v = use1 ? v1 : v0, al = use1 ? a1 : a0, R = use1 ? R1 : R0;
-    const float sign = use1 ? qs : -qs;
-    const float ap = rp - s;
-    const float Ru = R - v * ap;
-    const float i1 = __frcp_rn(Ru);
-    const float i2 = i1 * i1, i3 = i2 * i1;
-    float G = 0.f, Q = 0.f;
-    if (KIND != PC_RADIATION) G += 1.f - v * v;
-    if (KIND != PC_COULOMB) {
-      G += al * ap;
-      Q = al;
+__device__ __forceinline__ int near_dipole_f64(const Sources &s, int j, double r0, double r1, double r2, double u,
+                                            long long kg, double r_excl, double invE, double invP, float *part,
+                                            uint8_t *mask) {
+  const double r[3] = {r0, r1, r2};
+  const double cdt = kC * s.dtd;
+  TrajF64 tr;
+  tr.dipole = true;
+  tr.d = s.d + (size_t)j * s.Sd;
+  tr.dd = s.dd + (size_t)j * s.Sd;
+  tr.ddd = s.ddd + (size_t)j * s.Sd;
+  for (int i = 0; i < 3; ++i) {
+    tr.R[i] = s.origin[3 * j + i];
+    tr.ax[i] = s.axis[3 * j + i];
+  }
+  const double q = s.qd[j], m1 = s.m1[j], m2 = s.m2[j];
+  double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, A[3] = {0, 0, 0}, phi = 0.0;
+  for (int sg = 0; sg < 2; ++sg) {
+    tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+    int64_t k;
+    double th;
+    int e = solve_f64(tr, s.Sd, 1, r, u, cdt, (int64_t)kg, &k, &th);
+    if (e) return e;
+    double p0[3], v[3], a[3];
+    if (k < 0 || (k == 0 && th == 0.0)) {
+      tr.p(0, p0);
+      v[0] = v[1] = v[2] = 0.0;
+      a[0] = a[1] = a[2] = 0.0;
+    } else {
+      double p1[3], v1[3], a1[3];
+      tr.p(k, p0);
+      tr.p(k + 1, p1);
+      tr.va(k, v, a);
+      tr.va(k + 1, v1, a1);
+      for (int i = 0; i < 3; ++i) {
+        p0[i] += th * (p1[i] - p0[i]);
+        v[i] += th * (v1[i] - v[i]);
+        a[i] += th * (a1[i] - a[i]);
+      }
     }
-    const float Ca = G * i3;
-    const float Cp = -R * v * G * i3 - Q * R * i2;
-    const float Bc = -v * G * i3 - Q * i2;
-    const float ax_ = rx - s * px, ay_ = ry - s * py, az_ = rz - s * pz;
-    acc[0] += sign * (Ca * ax_ + Cp * px);
-    acc[1] += sign * (Ca * ay_ + Cp * py);
-    acc[2] += sign * (Ca * az_ + Cp * pz);
-    const float cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
-    acc[3] += sign * Bc * cx;
-    acc[4] += sign * Bc * cy;
-    acc[5] += sign * Bc * cz;
-    acc[6] += sign * i1;
-    const float va = sign * v * i1;
-    acc[7] += va * px;
-    acc[8] += va * py;
-    acc[9] += va * pz;
-    return;
+    double av[3] = {r[0] - p0[0], r[1] - p0[1], r[2] - p0[2]};
+    lw_add_f64<KIND>(sg == 0 ? q : -q, av, v, a, r_excl, E, B, &phi, A, mask);
   }
-  const float ap0 = rp - s0, ap1 = rp - s1, dap = -ds;
-  const float Ru0 = R0 - v0 * ap0;
-  const float dRu = dR - (dv * ap1 + v0 * dap);
-  const float Ru1 = Ru0 + dRu;
-  const float i0 = __frcp_rn(Ru0), i1 = __frcp_rn(Ru1);
-  const float di = -dRu * i0 * i1;
-  const float i02 = i0 * i0, i12 = i1 * i1;
-  const float i03 = i02 * i0, i13 = i12 * i1;
-  const float di2 = di * (i0 + i1);
-  const float di3 = di * (i12 + i1 * i0 + i02);
-  float G0 = 0.f, dG = 0.f;
-  if (KIND != PC_RADIATION) {
-    G0 += 1.f - v0 * v0;
-    dG += -dv * (v1 + v0);
-  }
-  if (KIND != PC_COULOMB) {
-    G0 += a0 * ap0;
-    dG += da * ap1 + a0 * dap;
-  }
-  const float G1 = G0 + dG;
-  const float Ca0 = G0 * i03, Ca1 = G1 * i13;
-  const float dCa = dG * i13 + G0 * di3;
-  // C_p = -R v G i^3 - alpha R i^2 ; B coefficient C_p / R = -v G i^3 - alpha i^2
-  const float P0 = R0 * v0 * G0;
-  const float dP = dR * v1 * G1 + R0 * (dv * G1 + v0 * dG);
-  float dCp = -(dP * i13 + P0 * di3);
-  const float dvG = dv * G1 + v0 * dG;
-  float dBc = -(dvG * i13 + v0 * G0 * di3);
-  if (KIND != PC_COULOMB) {
-    const float Q0 = a0 * R0, dQ = da * R1 + a0 * dR;
-    dCp -= dQ * i12 + Q0 * di2;
-    dBc -= da * i12 + a0 * di2;
-  }
-  const float ep = dCp - (Ca1 * s1 - Ca0 * s0);
-  acc[0] += qs * (dCa * rx + ep * px);
-  acc[1] += qs * (dCa * ry + ep * py);
-  acc[2] += qs * (dCa * rz + ep * pz);
-  const float cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
-  acc[3] += qs * dBc * cx;
-  acc[4] += qs * dBc * cy;
-  acc[5] += qs * dBc * cz;
-  acc[6] += qs * di;
-  const float dA = qs * (dv * i1 + v0 * di);
-  acc[7] += dA * px;
-  acc[8] += dA * py;
-  acc[9] += dA * pz;
+  const double invB = invE * kC, invA = invP * kC;
+  part[0] += (float)(E[0] * invE);
+  part[1] += (float)(E[1] * invE);
+  part[2] += (float)(E[2] * invE);
+  part[3] += (float)(B[0] * invB);
+  part[4] += (float)(B[1] * invB);
+  part[5] += (float)(B[2] * invB);
+  part[6] += (float)(phi * invP);
+  part[7] += (float)(A[0] * invA);
+  part[8] += (float)(A[1] * invA);
+  part[9] += (float)(A[2] * invA);
+  return 0;
 }
 
 // Generic charge in float32 (no pairing): Griffiths form with c = 1.
@@ -445,13 +389,14 @@ __device__ __forceinline__ void kahan_add(float *sum, float *comp, const float *
   }
 }
 
-template <int KIND>
+template <int KIND, bool LIST>
 __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
   __shared__ double s_anchor[3];
   __shared__ float4 s_geo[kChunk];   // rho_a (x,y,z), |rho_a|
+  __shared__ float4 s_geo_lo[kChunk]; // low parts of rho_a and |rho_a| (list mode)
   __shared__ float4 s_ax[kChunk];    // axis (x,y,z), q/e
   __shared__ float2 s_mu[kChunk];    // m2/(m1+m2), m1/(m1+m2)
-  __shared__ long long s_ka[kChunk];
+  __shared__ int s_ka[kChunk];
   __shared__ float s_fa[kChunk];
 
   const int tid = threadIdx.x;
@@ -497,11 +442,15 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
 
   // ---------------- dipoles ----------------
   if (s.N > 0) {
-    const float drx = (float)((r[0] - s_anchor[0]) / Ld), dry = (float)((r[1] - s_anchor[1]) / Ld),
-                drz = (float)((r[2] - s_anchor[2]) / Ld);
+    const double drxd = (r[0] - s_anchor[0]) / Ld, dryd = (r[1] - s_anchor[1]) / Ld, drzd = (r[2] - s_anchor[2]) / Ld;
+    const float drx = (float)drxd, dry = (float)dryd, drz = (float)drzd;
+    const float drlx = (float)(drxd - (double)drx), drly = (float)(dryd - (double)dry),
+                drlz = (float)(drzd - (double)drz);
     const float dr2 = drx * drx + dry * dry + drz * drz;
     const double u = (t - s.t0d) / s.dtd;
     const float rex = (float)(L.r_excl / Ld);
+    const double invE = Lref * Lref / (kKe * kE), invP = Lref / (kKe * kE);
+    const int Sd32 = (int)s.Sd;
     for (int base = 0; base < s.N; base += kChunk) {
       const int nch = min(kChunk, s.N - base);
       __syncthreads();
@@ -513,11 +462,13 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
         const double x = u - rna;
         const double kaf = floor(x);
         s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
+        s_geo_lo[tid] = make_float4((float)(ra[0] - (double)(float)ra[0]), (float)(ra[1] - (double)(float)ra[1]),
+                                    (float)(ra[2] - (double)(float)ra[2]), (float)(rna - (double)(float)rna));
         s_ax[tid] = make_float4((float)s.axis[3 * j], (float)s.axis[3 * j + 1], (float)s.axis[3 * j + 2],
                                 (float)(s.qd[j] / kE));
         const double m1 = s.m1[j], m2 = s.m2[j];
         s_mu[tid] = make_float2((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)));
-        s_ka[tid] = (long long)kaf;
+        s_ka[tid] = (int)kaf;
         s_fa[tid] = (float)(x - kaf);
       }
       __syncthreads();
@@ -525,6 +476,7 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
       float part[10];
 #pragma unroll
       for (int i = 0; i < 10; ++i) part[i] = 0.f;
+      unsigned long long near_mask = 0ull;
       for (int jj = 0; jj < nch; ++jj) {
         const float4 g = s_geo[jj];
         const float4 ax = s_ax[jj];
@@ -533,14 +485,35 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
         const float rho2 = rx * rx + ry * ry + rz * rz;
         const float irn = rsqrtf(rho2);
         const float rn = rho2 > 0.f ? rho2 * irn : 0.f;
-        // |rho| - |rho_a| without cancellation
-        const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
-        const float xc = s_fa[jj] - corr;
+        // retarded time of the dipole centre, in samples: kb + xc with |xc| small
+        int kb = s_ka[jj];
+        float xc;
+        if (!LIST) {
+          // compact tile: |rho| - |rho_a| from the tile offset without cancellation
+          const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
+          xc = s_fa[jj] - corr;
+        } else {
+          // points of a list tile may lie far apart: |rho| - |rho_a| in float-float, integer part
+          // moved into kb so that the fraction keeps its precision
+          const float4 gl = s_geo_lo[jj];
+          const ff px = ff_add({g.x, gl.x}, {drx, drlx}), py = ff_add({g.y, gl.y}, {dry, drly}),
+                   pz = ff_add({g.z, gl.z}, {drz, drlz});
+          const ff n2 = ff_add(ff_add(ff_mul(px, px), ff_mul(py, py)), ff_mul(pz, pz));
+          const ff dn = ff_add(ff_sqrt(n2), {-g.w, -gl.w});
+          const ff x = ff_add({s_fa[jj], 0.f}, {-dn.hi, -dn.lo});
+          const int fl = __float2int_rd(x.hi);
+          kb += fl;
+          xc = (x.hi - (float)fl) + x.lo;
+        }
         const float rp = rx * ax.x + ry * ax.y + rz * ax.z;
+        if (rn < kNearL) {
+          near_mask |= 1ull << jj;  // evaluated in float64 after this chunk
+          continue;
+        }
         const float4 *H = L.Hd + (size_t)(base + jj) * s.Sd;
         float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
-        int e1 = dip_charge_solve(H, s.Sd, s_ka[jj], xc, rn, rp, mu.x, Xp, Vp, Ap, dp);
-        int e2 = dip_charge_solve(H, s.Sd, s_ka[jj], xc, rn, rp, -mu.y, Xm, Vm, Am, dm);
+        int e1 = dip_charge_solve(H, Sd32, kb, xc, rn, rp, mu.x, Xp, Vp, Ap, dp);
+        int e2 = dip_charge_solve(H, Sd32, kb, xc, rn, rp, -mu.y, Xm, Vm, Am, dm);
         if (e1 | e2) {
           err = e1 ? e1 : e2;
           break;
@@ -554,6 +527,19 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
         }
       }
       kahan_add(sum, comp, part);
+      // near pairs of this chunk, in float64
+      while (near_mask && !err) {
+        const int jj = __ffsll((long long)near_mask) - 1;
+        near_mask &= near_mask - 1ull;
+#pragma unroll
+        for (int i = 0; i < 10; ++i) part[i] = 0.f;
+        const int j = base + jj;
+        const double dx = r[0] - s.origin[3 * j], dy = r[1] - s.origin[3 * j + 1], dz = r[2] - s.origin[3 * j + 2];
+        const long long kg = (long long)floor(u - sqrt(dx * dx + dy * dy + dz * dz) / Ld);
+        const int e = near_dipole_f64<KIND>(s, j, r[0], r[1], r[2], u, kg, L.r_excl, invE, invP, part, &mask);
+        if (e) err = e;
+        kahan_add(sum, comp, part);
+      }
     }
   }
   // ---------------- point charges ----------------
@@ -576,7 +562,7 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
         const double kaf = floor(x);
         s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
         s_ax[tid] = make_float4(0.f, 0.f, 0.f, (float)(s.q[c] / kE));
-        s_ka[tid] = (long long)kaf;
+        s_ka[tid] = (int)kaf;
         s_fa[tid] = (float)(x - kaf);
       }
       __syncthreads();
@@ -598,31 +584,33 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
           break;
         }
         const float4 *H = L.Hc + (size_t)(base + cc) * s.S * 3;
-        const int64_t S = s.S;
+        const int S = (int)s.S;
         // first-order estimate of the charge's delay offset: -rho_hat . o(center time)
-        float kcf = floorf(xc);
-        float thc = xc - kcf;
-        int64_t j = s_ka[cc] + (int64_t)kcf;
+        const int kc = __float2int_rd(xc);
+        float thc = xc - (float)kc;
+        int j = s_ka[cc] + kc;
         {
-          int64_t jc = j < 0 ? 0 : (j > S - 1 ? S - 1 : j);
+          int jc = j < 0 ? 0 : (j > S - 1 ? S - 1 : j);
           float4 o = __ldg(H + 3 * jc);
           float d0 = -(rx * o.x + ry * o.y + rz * o.z) * irn;
-          float st = floorf(thc - d0);
-          j += (int64_t)st;
-          thc -= st;
+          int st = __float2int_rd(thc - d0);
+          j += st;
+          thc -= (float)st;
         }
         float ox = 0, oy = 0, oz = 0, vx = 0, vy = 0, vz = 0, gx = 0, gy = 0, gz = 0;
         bool done = false;
         for (int it = 0; it < 32 && !done; ++it) {
-          if (j + 1 > S - 1) {
-            err = PC_ERR_HISTORY;
-            break;
+          // an estimate past either end is solved on the end segment extended; the root then
+          // decides whether the history really ends too early
+          if (j > S - 2) {
+            thc += (float)(j - (S - 2));
+            j = S - 2;
           }
           if (j < 0 && !s.static_before) {
-            err = PC_ERR_HISTORY;
-            break;
+            thc += (float)j;
+            j = 0;
           }
-          const int64_t j0 = j < 0 ? 0 : j, j1 = j < 0 ? 0 : j + 1;
+          const int j0 = j < 0 ? 0 : j, j1 = j < 0 ? 0 : j + 1;
           const float4 o0 = __ldg(H + 3 * j0), o1 = __ldg(H + 3 * j1);
           const float wx = o1.x - o0.x, wy = o1.y - o0.y, wz = o1.z - o0.z;
           const float ocx = o0.x + thc * wx, ocy = o0.y + thc * wy, ocz = o0.z + thc * wz;
@@ -632,7 +620,8 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
           const float sq = fsqrt_approx(fmaxf(B * B - A * C, 0.f));
           const float dl = (B > 0.f) ? -__fdividef(C, B + sq) : __fdividef(-B + sq, A);
           float th = thc - dl;
-          const bool ok = (j < 0) ? ((float)j + th <= 1e-4f) : (th >= -1e-4f && th <= 1.0001f);
+          const bool ok = (j < 0) ? ((float)j + th <= 1e-4f)
+                                  : (th >= -1e-4f && (th <= 1.0001f || (j == S - 2 && th <= 1.f + kEndTol)));
           if (ok) {
             th = fminf(fmaxf(th, 0.f), 1.f);
             if (j < 0) {
@@ -655,9 +644,13 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
             done = true;
           } else {
             if (!(fabsf(th) < 1e8f)) break;
-            const float st = floorf(th);
-            j += (int64_t)st;
-            thc -= st;
+            if ((j == S - 2 && th > 1.f) || (j == 0 && th < 0.f && !s.static_before)) {
+              err = PC_ERR_HISTORY;
+              break;
+            }
+            const int st = __float2int_rd(th);
+            j += st;
+            thc -= (float)st;
           }
         }
         if (!done) {
@@ -732,6 +725,7 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
   if (has_dp && (dp->S < 2 || !(dp->dt > 0.0) || !isfinite(dp->t0) || !dp->origin || !dp->axis || !dp->q ||
                  !dp->m1 || !dp->m2 || !dp->d || !dp->d_dot || !dp->d_ddot))
     return PC_ERR_ARG;
+  if (P == 0) return PC_OK;
   if (!list && !plane) return PC_ERR_ARG;
   if (list == nullptr && plane && (plane->nu < 0 || plane->nv < 0 || !finite3(plane->origin) ||
                                    !finite3(plane->eu) || !finite3(plane->ev)))
@@ -792,6 +786,8 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
   L.status = ctx->d_status;
 
   if (precision == PC_MIXED) {
+    // the float32 path indexes samples with 32-bit integers
+    if ((has_dp && s.Sd > (int64_t)1 << 30) || (has_ch && s.S > (int64_t)1 << 30)) return PC_ERR_ARG;
     size_t nd = has_dp ? (size_t)s.N * s.Sd : 0, nc = has_ch ? (size_t)s.M * s.S * 3 : 0;
     if (ctx->hist_f32.reserve((nd + nc) * sizeof(float4)) != cudaSuccess) return PC_ERR_CUDA;
     if (has_ch && ctx->charge_ref.reserve((size_t)s.M * 3 * sizeof(double)) != cudaSuccess) return PC_ERR_CUDA;
@@ -828,9 +824,15 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
         tiles = tu * tiles_v;
       }
       dim3 grid((unsigned)tiles, (unsigned)L.T);
-      if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-      else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-      else fields_mixed_kernel<PC_RADIATION><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+      if (list) {
+        if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+        else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+        else fields_mixed_kernel<PC_RADIATION, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+      } else {
+        if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, false><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+        else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, false><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+        else fields_mixed_kernel<PC_RADIATION, false><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+      }
     }
   }
   return end_call(ctx, st);

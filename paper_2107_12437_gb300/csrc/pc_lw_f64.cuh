@@ -79,10 +79,11 @@ __device__ inline int solve_f64(const TrajF64 &tr, int64_t S, int static_before,
     }
     if (th < 0.0) {
       if (k == 0) {
-        // the root precedes the first sample: static extension or error
-        if (!static_before) return PC_ERR_HISTORY;
+        // g(t') = c (t - t') - |r - r_s(t')| decreases in t': g(t0) < 0 puts the root before the
+        // first sample (static extension or error); otherwise rounding put it at t0 itself
         double g0 = cdt * u - sqrt(dot3(a, a));
-        if (g0 >= 0.0) {
+        if (g0 < 0.0) {
+          if (!static_before) return PC_ERR_HISTORY;
           *k_out = -1;
           *th_out = 0.0;
         } else {

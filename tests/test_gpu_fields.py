@@ -1,8 +1,15 @@
 """Parity of pc_fields / pc_fields_plane (CUDA, through the C ABI) with the FP64 oracle.
 
-Error metric per point: |F_gpu - F_oracle|_2 / |F_oracle|_2 over the vector (E, B, A) or the scalar
-phi, maximum over unmasked points.  Tolerances: 1e-10 for the float64 path, 1e-5 for the mixed path
-on dipole sources (pair difference form).
+Error metrics (per point, maximum over unmasked points), F the oracle's total field or potential:
+  * float64 path: |F_gpu - F| <= 1e-12 * sum_c |F_c| (sum over charges of each term's magnitude --
+    for E and B the magnitudes of its Coulomb and radiation parts, B in units of E/c -- the scale at
+    which any float64 evaluation of the superposition rounds), and |F_gpu - F| / |F| <= 1e-10
+    wherever the superposition is well conditioned (sum_c |F_c| / |F| < 1e3).  The +-q pair of a
+    dipole cancels by R/s (up to ~1e7 near a dipole whose moment crosses zero), which puts the
+    oracle's own rounding above 1e-10 of |F| at such points.
+  * mixed path: |F_gpu - F| <= 1e-5 * sum_j |F_j| with the sum over sources (a dipole's two charges
+    summed first), and |F_gpu - F| / |F| <= 1e-5 wherever the sources do not cancel
+    (sum_j |F_j| / |F| < 10).
 """
 import math
 
@@ -16,6 +23,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+F64_COND_TOL = 1e-12
 F64_TOL = 1e-10
 MIX_TOL = 1e-5
 R_EXCL = 1e-15
@@ -28,30 +36,44 @@ def ctx():
     c.close()
 
 
+def _norm(x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.abs(x) if x.ndim == 2 else np.linalg.norm(x, axis=-1)
+
+
 def rel_err(gpu, ref, mask=None):
-    g = np.asarray(gpu, dtype=np.float64)
-    r = np.asarray(ref, dtype=np.float64)
-    if r.ndim == g.ndim and g.shape[-1] == 3:
-        num = np.linalg.norm(g - r, axis=-1)
-        den = np.linalg.norm(r, axis=-1)
-    else:
-        num = np.abs(g - r)
-        den = np.abs(r)
+    num = _norm(np.asarray(gpu, dtype=np.float64) - np.asarray(ref, dtype=np.float64))
+    den = _norm(ref)
     if mask is not None:
-        num = num[~mask]
-        den = den[~mask]
+        num, den = num[~mask], den[~mask]
     return float(np.max(num / den))
 
 
-def compare(out, ref, tol, keys=("E", "B", "phi", "A")):
+def compare(out, ref, prec, keys=("E", "B", "phi", "A"), mix_tol=MIX_TOL):
+    """Checks the metrics of the module docstring; returns {key: (max metric, max plain relative error)}."""
     m = ref["mask"].astype(bool)
     assert np.array_equal(out["mask"].cpu().numpy().astype(bool), m)
-    errs = {}
+    res = {}
     for k in keys:
-        errs[k] = rel_err(out[k].cpu().numpy(), ref[k], m)
-    for k, e in errs.items():
-        assert e < tol, (k, e, errs)
-    return errs
+        g = out[k].cpu().numpy() if isinstance(out[k], torch.Tensor) else out[k]
+        num = _norm(np.asarray(g, dtype=np.float64) - ref[k])[~m]
+        den = _norm(ref[k])[~m]
+        if prec == pc.PC_F64:
+            scale = ref["scale_charge"][k][~m]
+            metric = float(np.max(num / scale))
+            well = scale / den < 1e3
+            plain = float(np.max((num / den)[well])) if well.any() else 0.0
+            assert metric < F64_COND_TOL, (k, metric)
+            assert plain < F64_TOL, (k, plain)
+        else:
+            scale = ref["scale_source"][k][~m]
+            metric = float(np.max(num / scale))
+            well = scale / den < 10
+            plain = float(np.max((num / den)[well])) if well.any() else 0.0
+            assert metric < mix_tol, (k, metric)
+            assert plain < mix_tol, (k, plain)
+        res[k] = (metric, float(np.max(num / den)))
+    return res
 
 
 # ------------------------------------------------------------------------------------------------
@@ -75,29 +97,29 @@ def test_cfg1_f64_list(ctx, cfg1_data, kind):
     # the static charge sits within r_excl of one grid point: exactly one masked point
     assert int(out["mask"].sum()) == 1
     keys = ("E", "B", "phi", "A") if kind == pc.PC_TOTAL else ("E", "B")
-    compare(out, refs[kind], F64_TOL, keys)
+    compare(out, refs[kind], pc.PC_F64, keys)
 
 
 def test_cfg1_f64_plane_matches_list(ctx, cfg1_data):
     ch, pts, times, refs = cfg1_data
     g = np.linspace(-50e-9, 50e-9, 101)
     out = pc.pc_fields_plane(ctx, charges=pc.charges_to_device(ch), origin=(g[0], g[0], 0.0),
-                             eu=(g[1] - g[0], 0, 0), ev=(0, g[1] - g[0], 0), nu=101, nv=101, times=list(times))
-    # plane points are generated on the device: agree with the oracle on its own point list
-    m = refs[pc.PC_TOTAL]["mask"].astype(bool)
-    # grid spacing rounding moves points by ~1e-24 m: compare at the float64 tolerance
-    assert rel_err(out["E"].cpu().numpy(), refs[pc.PC_TOTAL]["E"], m | out["mask"].cpu().numpy().astype(bool)) < 1e-9
+                             eu=(g[1] - g[0], 0, 0), ev=(0, g[1] - g[0], 0), nu=101, nv=101, times=list(times),
+                             r_excl=R_EXCL)
+    # device-generated points differ from linspace by rounding (~1e-24 m, 1e-15 relative)
+    compare(out, refs[pc.PC_TOTAL], pc.PC_F64)
 
 
 def test_cfg1_mixed(ctx, cfg1_data):
-    ch, pts, times, refs = cfg1_data
+    ch, pts, times, _ = cfg1_data
+    # float32 offsets resolve ~1e-5 c dt (3e-15 m) near a tile anchor: the exclusion radius of the
+    # mixed path is set to 1 pm, which still masks exactly the grid point on the static charge
+    ref = oracle.fields(pts, times, charges=ch, r_excl=1e-12)
     out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(pts, device="cuda"),
-                       times=list(times), precision=pc.PC_MIXED, r_excl=R_EXCL)
-    ref = refs[pc.PC_TOTAL]
-    m = ref["mask"].astype(bool)
-    # unpaired charges in float32: the +-e pair (1 nm) seen from up to 70 nm cancels by R/s <= 70
-    e = rel_err(out["E"].cpu().numpy(), ref["E"], m)
-    assert e < 2e-5, e
+                       times=list(times), precision=pc.PC_MIXED, r_excl=1e-12)
+    assert int(out["mask"].sum()) == 1
+    # two unpaired charges in float32: the +-e pair 1 nm apart is two sources to the metric
+    compare(out, ref, pc.PC_MIXED)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -117,12 +139,12 @@ def cfg2_sub():
     return dp, pts, tsel, ref
 
 
-@pytest.mark.parametrize("prec,tol", [(pc.PC_F64, F64_TOL), (pc.PC_MIXED, MIX_TOL)])
-def test_cfg2_dipoles_list(ctx, cfg2_sub, prec, tol):
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+def test_cfg2_dipoles_list(ctx, cfg2_sub, prec):
     dp, pts, tsel, ref = cfg2_sub
     out = pc.pc_fields(ctx, dipoles=pc.dipoles_to_device(dp), points=torch.as_tensor(pts, device="cuda"),
                        times=list(tsel), precision=prec)
-    compare(out, ref, tol)
+    compare(out, ref, prec)
 
 
 def test_cfg2_generic_charges_f64(ctx, cfg2_sub):
@@ -130,12 +152,13 @@ def test_cfg2_generic_charges_f64(ctx, cfg2_sub):
     ch = W.dipoles_as_charges(dp)
     out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(pts[:700], device="cuda"),
                        times=list(tsel), precision=pc.PC_F64)
-    sub = {k: v[:, :700] for k, v in ref.items() if k != "status"}
-    compare(out, sub, F64_TOL)
+    sub = {k: (v[:, :700] if not isinstance(v, dict) else {kk: vv[:, :700] for kk, vv in v.items()})
+           for k, v in ref.items() if k != "status"}
+    compare(out, sub, pc.PC_F64)
 
 
-@pytest.mark.parametrize("prec,tol", [(pc.PC_F64, F64_TOL), (pc.PC_MIXED, MIX_TOL)])
-def test_cfg2_plane_tiles(ctx, prec, tol):
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+def test_cfg2_plane_tiles(ctx, prec):
     # a contiguous 40 x 37 block of the full grid: 2-D tiles with ragged edges in both directions
     dp, g, z, times = W.cfg2()
     u0, v0 = 700, 1301
@@ -146,7 +169,7 @@ def test_cfg2_plane_tiles(ctx, prec, tol):
     out = pc.pc_fields_plane(ctx, dipoles=pc.dipoles_to_device(dp), origin=(g[u0], g[v0], z), eu=(step, 0, 0),
                              ev=(0, step, 0), nu=nu, nv=nv, times=[times[3]], precision=prec)
     # device-generated points differ from linspace by rounding (~1e-22 m): negligible at both tolerances
-    compare(out, ref, tol)
+    compare(out, ref, prec)
 
 
 def test_cfg2_full_size_sampled(ctx):
@@ -164,7 +187,7 @@ def test_cfg2_full_size_sampled(ctx):
     pts = np.stack([iu * step, iv * step, np.full(idx.size, z)], axis=1)
     ref = oracle.fields(pts, times[fr], dipoles=dp)
     sub = {k: out[k][fr][:, idx] for k in ("E", "B", "phi", "A", "mask")}
-    compare(sub, ref, MIX_TOL)
+    compare(sub, ref, pc.PC_MIXED)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -188,7 +211,7 @@ def test_history_error_and_static_extension(ctx):
     ch.static_before = 1
     ref = oracle.fields(pts, [1e-16], charges=ch, r_excl=R_EXCL)
     out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=ptd, times=[1e-16], r_excl=R_EXCL)
-    compare(out, ref, F64_TOL, ("E",))
+    compare(out, ref, pc.PC_F64, ("E",))
     # evaluating after the last sample: retarded times beyond the history
     with pytest.raises(pc.PcError) as ei:
         pc.pc_fields(ctx, charges=chd, points=ptd[:3], times=[10.5e-15])
@@ -216,4 +239,4 @@ def test_many_frames_split_launches(ctx):
     ref = oracle.fields(sel, times, charges=ch, r_excl=R_EXCL)
     out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(sel, device="cuda"),
                        times=list(times), r_excl=R_EXCL)
-    compare(out, ref, F64_TOL, ("E", "phi"))
+    compare(out, ref, pc.PC_F64, ("E", "phi"))

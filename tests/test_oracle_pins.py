@@ -470,3 +470,27 @@ def test_fit_recovers_synthetic_parameters(gamma):
     f = fit.ke_fit(ke, dt, 10000)
     assert abs(f["omega"] / w - 1) < 1e-9
     assert abs(f["gamma"] - gamma) < 1e-6 * max(gamma, 2e7)
+
+
+def test_scale_outputs_bound_the_superposition():
+    # the magnitude sums are upper bounds of the superposed fields (triangle inequality), the source
+    # sums lie between them, and for a lone charge all of them equal the field itself
+    dp, g, z, times = W.cfg2(n_dipoles=64)
+    pts = W.plane_grid(g[::256], g[::256], z)
+    out = oracle.fields(pts, times[:1], dipoles=dp)
+    for k in ("E", "B", "phi", "A"):
+        f = np.abs(out[k][0]) if k == "phi" else np.linalg.norm(out[k][0], axis=-1)
+        sc, ss = out["scale_charge"][k][0], out["scale_source"][k][0]
+        assert np.all(f <= ss * (1 + 1e-12)) and np.all(ss <= sc * (1 + 1e-12))
+    # a dipole's two fields cancel: the charge sum exceeds the source sum by ~R/s
+    assert np.median(out["scale_charge"]["E"][0] / out["scale_source"]["E"][0]) > 1e3
+    ch, pts1, _ = W.cfg1(n_grid=11)
+    ch1 = W.Charges(q=ch.q[1:], pos=ch.pos[1:], vel=ch.vel[1:], acc=ch.acc[1:], t0=ch.t0, dt=ch.dt, static_before=1)
+    o1 = oracle.fields(pts1, [1e-14], charges=ch1)
+    En = np.linalg.norm(o1["E"][0], axis=-1)
+    assert np.allclose(o1["scale_source"]["E"][0], En, rtol=1e-15)
+    # the per-term rounding scale adds the magnitudes of the Coulomb and radiation parts
+    oc = oracle.fields(pts1, [1e-14], charges=ch1, kind=oracle.COULOMB)
+    orad = oracle.fields(pts1, [1e-14], charges=ch1, kind=oracle.RADIATION)
+    ecr = np.linalg.norm(oc["E"][0], axis=-1) + np.linalg.norm(orad["E"][0], axis=-1)
+    assert np.allclose(o1["scale_charge"]["E"][0], ecr, rtol=1e-14)
