@@ -1,17 +1,26 @@
 // Lorentz-oscillator run (Algorithm 1 of arXiv 2107.12437) and the kinetic-energy fit (Eq. KE).
 //
-// pc_dipoles_run: one CTA per configuration; its threads own dipoles.  Every step each thread
-// evaluates the driving field of its dipoles at the two new RK4 stage times t + dt/2 and t + dt
-// (the field at t is the previous step's t + dt value) from the stored history of every other
-// dipole of the configuration, advances (d, d') by RK4 (Eq. LO_equation) and appends d, d', d''
-// to the history; a CTA barrier separates steps.  The history arrays are the caller's outputs.
+// pc_dipoles_run: one persistent CTA per configuration.  Time advances in causal blocks of K steps:
+// with R_min the smallest distance between a receiving dipole's origin and another dipole's
+// charges, every field needed by the RK4 stages of steps n0 .. n0+K-1 (times n0 + 1/2, n0 + 1, ...,
+// n0 + K, in steps) has its retarded time at or before n0 when K c dt <= R_min, so all 2K stage
+// fields of all receivers are independent and are computed together (phase A); then each receiver
+// advances K RK4 steps (Eq. LO_equation) and appends d, d', d'' to the history (phase B).
+// Phase A: one warp per receiver; lane = (stage, source slot); each lane sums its sources for its
+// stage (float32 pair difference form, or float64 per charge) and the slots are reduced in shared
+// memory.  The caller's history arrays are the trajectory store; the mixed path also keeps a
+// float32 mirror of it.
 // pc_ke_fit: one CTA per series; Levenberg-Marquardt with block reductions.
 #include <stdio.h>
 
 #include "pc_internal.cuh"
+#include "pc_lw_f32.cuh"
 #include "pc_lw_f64.cuh"
 
 namespace pc {
+
+constexpr int kRunWarps = 8;   // receivers advanced concurrently by one CTA
+constexpr int kMaxBlock = 16;  // steps per causal block (2K <= 32 stages, one per lane)
 
 struct RunArgs {
   int B, N;
@@ -21,98 +30,181 @@ struct RunArgs {
   double v_max;
   int ed_mode;
   double *d, *dd, *ddd, *energy, *Ed;
-  double *ed_now;  // scratch [B][N]
+  float4 *H32;        // [B][N][S] float32 mirror (mixed path)
+  double *Es;         // scratch [B][N][2*kMaxBlock+1] stage fields
   int *status;
 };
 
-// Driving field of dipole i of configuration b at time u (in steps), history samples 0..n_valid.
-__device__ double drive_f64(const RunArgs &a, int b, int i, double u, int64_t n_valid, int *err) {
-  const int N = a.N;
+__device__ __forceinline__ size_t bidx(const RunArgs &a, int b, int i) { return (size_t)b * a.N + i; }
+
+// Contribution of dipole j to the driving field of receiver i at time u (steps), history 0..nv.
+// float64: both charges per charge (Eqs. r_1, r_2, E); returns p_i . E.
+__device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int *err) {
   const int64_t S = a.n_steps + 1;
   const double cdt = kC * a.dt;
-  const double *Ri = a.origin + 3 * ((size_t)b * N + i);
-  const double *pi = a.axis + 3 * ((size_t)b * N + i);
+  const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+  const double *Ri = a.origin + 3 * bi;
+  const double *pi = a.axis + 3 * bi;
+  TrajF64 tr;
+  tr.dipole = true;
+  tr.d = a.d + bj * S;
+  tr.dd = a.dd + bj * S;
+  tr.ddd = a.ddd + bj * S;
+  for (int k = 0; k < 3; ++k) {
+    tr.R[k] = a.origin[3 * bj + k];
+    tr.ax[k] = a.axis[3 * bj + k];
+  }
+  const double q = a.q[bj], m1 = a.m1[bj], m2 = a.m2[bj];
+  double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
+  const int64_t kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
   double E[3] = {0.0, 0.0, 0.0};
-  for (int j = 0; j < N; ++j) {
-    if (j == i) continue;
-    const size_t bj = (size_t)b * N + j;
-    TrajF64 tr;
-    tr.dipole = true;
-    tr.d = a.d + bj * S;
-    tr.dd = a.dd + bj * S;
-    tr.ddd = a.ddd + bj * S;
-    for (int k = 0; k < 3; ++k) {
-      tr.R[k] = a.origin[3 * bj + k];
-      tr.ax[k] = a.axis[3 * bj + k];
-    }
-    const double q = a.q[bj], m1 = a.m1[bj], m2 = a.m2[bj];
-    double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
-    const double tau0 = sqrt(dot3(dv, dv)) / cdt;
-    const int64_t kg = (int64_t)floor(u - tau0);
-    for (int sg = 0; sg < 2; ++sg) {
-      tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
-      double p0[3], v[3] = {0, 0, 0}, ac[3] = {0, 0, 0};
-      if (n_valid == 0) {
-        // only the static pre-history exists: the root must precede t = 0
+  for (int sg = 0; sg < 2; ++sg) {
+    tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+    double p0[3], v[3] = {0, 0, 0}, ac[3] = {0, 0, 0};
+    if (nv == 0) {
+      // only the static pre-history exists: the root must precede t = 0
+      tr.p(0, p0);
+      double av[3] = {Ri[0] - p0[0], Ri[1] - p0[1], Ri[2] - p0[2]};
+      if (u * cdt - sqrt(dot3(av, av)) > 0.0) {
+        *err = PC_ERR_CAUSALITY;
+        return 0.0;
+      }
+    } else {
+      int64_t k;
+      double th;
+      int e = solve_f64(tr, nv + 1, 1, Ri, u, cdt, kg, &k, &th);
+      if (e) {
+        *err = (e == PC_ERR_HISTORY) ? PC_ERR_CAUSALITY : e;
+        return 0.0;
+      }
+      if (k < 0 || (k == 0 && th == 0.0)) {
         tr.p(0, p0);
-        double av[3] = {Ri[0] - p0[0], Ri[1] - p0[1], Ri[2] - p0[2]};
-        if (u * cdt - sqrt(dot3(av, av)) > 0.0) {
-          *err = PC_ERR_CAUSALITY;
-          return 0.0;
-        }
       } else {
-        int64_t k;
-        double th;
-        int e = solve_f64(tr, n_valid + 1, 1, Ri, u, cdt, kg, &k, &th);
-        if (e) {
-          *err = (e == PC_ERR_HISTORY) ? PC_ERR_CAUSALITY : e;
-          return 0.0;
-        }
-        if (k < 0 || (k == 0 && th == 0.0)) {
-          tr.p(0, p0);
-        } else {
-          double p1[3], v1[3], a1[3];
-          tr.p(k, p0);
-          tr.p(k + 1, p1);
-          tr.va(k, v, ac);
-          tr.va(k + 1, v1, a1);
-          for (int c = 0; c < 3; ++c) {
-            p0[c] += th * (p1[c] - p0[c]);
-            v[c] += th * (v1[c] - v[c]);
-            ac[c] += th * (a1[c] - ac[c]);
-          }
+        double p1[3], v1[3], a1[3];
+        tr.p(k, p0);
+        tr.p(k + 1, p1);
+        tr.va(k, v, ac);
+        tr.va(k + 1, v1, a1);
+        for (int c = 0; c < 3; ++c) {
+          p0[c] += th * (p1[c] - p0[c]);
+          v[c] += th * (v1[c] - v[c]);
+          ac[c] += th * (a1[c] - ac[c]);
         }
       }
-      double av[3] = {Ri[0] - p0[0], Ri[1] - p0[1], Ri[2] - p0[2]};
-      lw_E_f64(sg == 0 ? q : -q, av, v, ac, E);
     }
+    double av[3] = {Ri[0] - p0[0], Ri[1] - p0[1], Ri[2] - p0[2]};
+    lw_E_f64(sg == 0 ? q : -q, av, v, ac, E);
   }
   return dot3(pi, E);
 }
 
-__global__ void __launch_bounds__(256) lo_run_f64_kernel(const RunArgs a) {
+// float32: the dipole pair in difference form from the float32 mirror; returns p_i . E in units
+// of k_e e / (c dt)^2.  kb + xc is the retarded time of dipole j's centre.
+__device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, float xc, int nvalid, int *err) {
+  const double L = kC * a.dt;
+  const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+  const float rx = (float)((a.origin[3 * bi] - a.origin[3 * bj]) / L);
+  const float ry = (float)((a.origin[3 * bi + 1] - a.origin[3 * bj + 1]) / L);
+  const float rz = (float)((a.origin[3 * bi + 2] - a.origin[3 * bj + 2]) / L);
+  const float rn = sqrtf(rx * rx + ry * ry + rz * rz);
+  const float px = (float)a.axis[3 * bj], py = (float)a.axis[3 * bj + 1], pz = (float)a.axis[3 * bj + 2];
+  const float rp = rx * px + ry * py + rz * pz;
+  const double m1 = a.m1[bj], m2 = a.m2[bj];
+  const float mup = (float)(m2 / (m1 + m2)), mum = (float)(m1 / (m1 + m2));
+  const float4 *H = a.H32 + bj * (size_t)(a.n_steps + 1);
+  float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
+  int e1 = dip_charge_solve(H, nvalid, kb, xc, rn, rp, mup, Xp, Vp, Ap, dp);
+  int e2 = dip_charge_solve(H, nvalid, kb, xc, rn, rp, -mum, Xm, Vm, Am, dm);
+  if (e1 | e2) {
+    int e = e1 ? e1 : e2;
+    *err = (e == PC_ERR_HISTORY) ? PC_ERR_CAUSALITY : e;
+    return 0.f;
+  }
+  float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  uint8_t mk = 0;
+  dipole_pair_mixed<PC_TOTAL>(rx, ry, rz, rn, px, py, pz, rp, mup, mum, (float)(a.q[bj] / kE), Xp, Vp, Ap, dp, Xm,
+                              Vm, Am, dm, 0.f, acc, mk);
+  return acc[0] * (float)a.axis[3 * bi] + acc[1] * (float)a.axis[3 * bi + 1] + acc[2] * (float)a.axis[3 * bi + 2];
+}
+
+// Phase A for one receiver (one warp): stage fields E_d(n0 + (s+1)/2), s < ns, into Es[1 + s];
+// ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.
+template <bool MIXED>
+__device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int nst = ns > 0 ? ns : 1;
+  const int slots = 32 / nst;
+  const int s = lane % nst, m = lane / nst;
+  const double stage = ns > 0 ? 0.5 * (s + 1) : 0.0;
+  double accd = 0.0;
+  float accf = 0.f, comp = 0.f;
+  if (m < slots) {
+    for (int j = m; j < a.N; j += slots) {
+      if (j == i) continue;
+      if (MIXED) {
+        // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
+        const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+        const double L = kC * a.dt;
+        const double dx = a.origin[3 * bi] - a.origin[3 * bj], dy = a.origin[3 * bi + 1] - a.origin[3 * bj + 1],
+                     dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
+        const double x = stage - sqrt(dx * dx + dy * dy + dz * dz) / L;
+        const double fl = floor(x);
+        const float v = pair_drive_f32(a, b, i, j, (int)n0 + (int)fl, (float)(x - fl), (int)n0 + 1, err);
+        // Kahan sum over sources
+        const float y = v - comp;
+        const float t = accf + y;
+        comp = (t - accf) - y;
+        accf = t;
+      } else {
+        accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, err);
+      }
+    }
+  }
+  double mine = MIXED ? (double)accf * (kKe * kE / ((kC * a.dt) * (kC * a.dt))) : accd;
+  sh[lane] = (m < slots) ? mine : 0.0;
+  __syncwarp();
+  if (lane < nst) {
+    double t = 0.0;
+    for (int mm = 0; mm < slots; ++mm) t += sh[mm * nst + lane];
+    a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = t;
+  }
+  __syncwarp();
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a) {
   const int b = blockIdx.x;
   const int N = a.N;
   const int64_t S = a.n_steps + 1;
-  __shared__ int s_stop;
-  if (threadIdx.x == 0) s_stop = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double sh[kRunWarps][32];
+  __shared__ int s_stop, s_K;
+  const double L = kC * a.dt;
+  // ---- block length from the smallest origin-to-charge distance of this configuration ----
+  if (threadIdx.x == 0) {
+    double rmin = 1e300, smax = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const size_t bi = bidx(a, b, i);
+      smax = fmax(smax, fabs(a.d0[bi] / a.q[bi]));
+      for (int j = i + 1; j < N; ++j) {
+        const size_t bj = bidx(a, b, j);
+        const double dx = a.origin[3 * bi] - a.origin[3 * bj], dy = a.origin[3 * bi + 1] - a.origin[3 * bj + 1],
+                     dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
+        rmin = fmin(rmin, sqrt(dx * dx + dy * dy + dz * dz));
+      }
+    }
+    // charges sit up to |r_dip| from their origin; allow three times the initial amplitude
+    const double kk = floor((rmin - 3.0 * smax) / L);
+    s_K = (int)fmax(1.0, fmin((double)kMaxBlock, kk));
+    s_stop = 0;
+  }
+  // ---- history sample 0: at rest with moment d0 (Sec. 3.2) ----
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const size_t bi = (size_t)b * N + i;
+    const size_t bi = bidx(a, b, i);
     a.d[bi * S] = a.d0[bi];
     a.dd[bi * S] = 0.0;
     a.ddd[bi * S] = 0.0;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    int err = 0;
-    const size_t bi = (size_t)b * N + i;
-    double e0 = drive_f64(a, b, i, 0.0, 0, &err);
-    if (err) {
-      set_status(a.status, err);
-      s_stop = 1;
-    }
-    a.ed_now[bi] = e0;
-    if (a.Ed) a.Ed[bi * S] = e0;
+    if (MIXED) a.H32[bi * S] = make_float4((float)(a.d0[bi] / (a.q[bi] * L)), 0.f, 0.f, 0.f);
     if (a.energy) {
       const double m = a.m1[bi] * a.m2[bi] / (a.m1[bi] + a.m2[bi]);
       const double w0 = a.omega0[bi], q = a.q[bi], x = a.d0[bi];
@@ -120,49 +212,78 @@ __global__ void __launch_bounds__(256) lo_run_f64_kernel(const RunArgs a) {
     }
   }
   __syncthreads();
-  for (int64_t n = 0; n < a.n_steps; ++n) {
+  const int K = s_K;
+  // ---- E_d at t = 0 from the static configuration ----
+  for (int i = warp; i < N; i += kRunWarps) {
+    int err = 0;
+    drive_phase<MIXED>(a, b, i, 0, 0, sh[warp], &err);
+    if (err) {
+      set_status(a.status, err);
+      s_stop = 1;
+    }
+    if (lane == 0 && a.Ed) a.Ed[bidx(a, b, i) * S] = a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)];
+  }
+  __syncthreads();
+  for (int64_t n0 = 0; n0 < a.n_steps; n0 += K) {
     if (s_stop) break;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int kb = (int)min((int64_t)K, a.n_steps - n0);
+    // phase A: all stage fields of the block
+    for (int i = warp; i < N; i += kRunWarps) {
       int err = 0;
-      const size_t bi = (size_t)b * N + i;
-      const double e1 = a.ed_now[bi];
-      double e2 = 0.0, e4 = 0.0;
-      e2 = drive_f64(a, b, i, (double)n + 0.5, n, &err);
-      if (!err) e4 = drive_f64(a, b, i, (double)n + 1.0, n, &err);
+      drive_phase<MIXED>(a, b, i, n0, 2 * kb, sh[warp], &err);
       if (err) {
         set_status(a.status, err);
         s_stop = 1;
-        continue;
       }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    // phase B: kb RK4 steps per receiver (lane 0 of its warp)
+    for (int i = warp; i < N; i += kRunWarps) {
+      if (lane != 0) continue;
+      const size_t bi = bidx(a, b, i);
+      double *Es = a.Es + bi * (2 * kMaxBlock + 1);
       const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
       const double m = m1 * m2 / (m1 + m2);
       const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
       const double qm = q * q / m;
       const double dt = a.dt;
-      const double f2 = (a.ed_mode == 1) ? e1 : e2;
-      const double f4 = (a.ed_mode == 1) ? e1 : e4;
-      const double y0 = a.d[bi * S + n], y1 = a.dd[bi * S + n];
-      // RK4 on (d, d') with d'' = -gamma0 d' - omega0^2 d + (q^2/m) E_d(t)
-      const double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
-      const double y0b = y0 + 0.5 * dt * k1a, y1b = y1 + 0.5 * dt * k1b;
-      const double k2a = y1b, k2b = -g0 * y1b - w0 * w0 * y0b + qm * f2;
-      const double y0c = y0 + 0.5 * dt * k2a, y1c = y1 + 0.5 * dt * k2b;
-      const double k3a = y1c, k3b = -g0 * y1c - w0 * w0 * y0c + qm * f2;
-      const double y0d = y0 + dt * k3a, y1d = y1 + dt * k3b;
-      const double k4a = y1d, k4b = -g0 * y1d - w0 * w0 * y0d + qm * f4;
-      const double yn0 = y0 + dt / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
-      const double yn1 = y1 + dt / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
-      a.d[bi * S + n + 1] = yn0;
-      a.dd[bi * S + n + 1] = yn1;
-      a.ddd[bi * S + n + 1] = qm * e4 - g0 * yn1 - w0 * w0 * yn0;
-      if (a.Ed) a.Ed[bi * S + n + 1] = e4;
-      if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
-      a.ed_now[bi] = e4;
-      const double vch = fabs(yn1) / q * (fmax(m1, m2) / (m1 + m2));
-      if (vch > a.v_max) {
-        set_status(a.status, PC_ERR_VELOCITY);
-        s_stop = 1;
+      const double vfac = fmax(m1, m2) / (m1 + m2) / q;
+      double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
+      for (int k = 0; k < kb; ++k) {
+        const int64_t n = n0 + k;
+        const double e1 = Es[2 * k];
+        const double f2 = (a.ed_mode == 1) ? e1 : Es[2 * k + 1];
+        const double e4 = Es[2 * k + 2];
+        const double f4 = (a.ed_mode == 1) ? e1 : e4;
+        // RK4 on (d, d') with d'' = -gamma0 d' - omega0^2 d + (q^2/m) E_d(t)
+        const double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
+        const double y0b = y0 + 0.5 * dt * k1a, y1b = y1 + 0.5 * dt * k1b;
+        const double k2a = y1b, k2b = -g0 * y1b - w0 * w0 * y0b + qm * f2;
+        const double y0c = y0 + 0.5 * dt * k2a, y1c = y1 + 0.5 * dt * k2b;
+        const double k3a = y1c, k3b = -g0 * y1c - w0 * w0 * y0c + qm * f2;
+        const double y0d = y0 + dt * k3a, y1d = y1 + dt * k3b;
+        const double k4a = y1d, k4b = -g0 * y1d - w0 * w0 * y0d + qm * f4;
+        const double yn0 = y0 + dt / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+        const double yn1 = y1 + dt / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+        const double ydd = qm * e4 - g0 * yn1 - w0 * w0 * yn0;
+        a.d[bi * S + n + 1] = yn0;
+        a.dd[bi * S + n + 1] = yn1;
+        a.ddd[bi * S + n + 1] = ydd;
+        if (MIXED)
+          a.H32[bi * S + n + 1] =
+              make_float4((float)(yn0 / (q * L)), (float)(yn1 / (q * kC)), (float)(ydd * dt / (q * kC)), 0.f);
+        if (a.Ed) a.Ed[bi * S + n + 1] = e4;
+        if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
+        if (fabs(yn1) * vfac > a.v_max) {
+          set_status(a.status, PC_ERR_VELOCITY);
+          s_stop = 1;
+          break;
+        }
+        y0 = yn0;
+        y1 = yn1;
       }
+      Es[0] = Es[2 * kb];
     }
     __syncthreads();
   }
@@ -502,9 +623,14 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
   if (bs != PC_OK) return bs;
   const int64_t S = n_steps + 1;
   const size_t nbn = (size_t)dp->B * dp->N;
-  size_t scratch = nbn * sizeof(double);
-  if (opts->fit) scratch += nbn * S * sizeof(double);
-  if (ctx->run_scratch.reserve(scratch) != cudaSuccess) return PC_ERR_CUDA;
+  const bool mixed = opts->precision == PC_MIXED;
+  if (mixed && S > ((int64_t)1 << 30)) return PC_ERR_ARG;
+  // scratch: stage fields, the float32 mirror (mixed), kinetic energies for the fit
+  const size_t es_bytes = nbn * (2 * pc::kMaxBlock + 1) * sizeof(double);
+  const size_t h_bytes = mixed ? nbn * S * sizeof(float4) : 0;
+  const size_t ke_bytes = opts->fit ? nbn * S * sizeof(double) : 0;
+  if (ctx->run_scratch.reserve(es_bytes + h_bytes + ke_bytes) != cudaSuccess) return PC_ERR_CUDA;
+  char *scr = (char *)ctx->run_scratch.ptr;
   pc::RunArgs a;
   a.B = dp->B;
   a.N = dp->N;
@@ -524,12 +650,13 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
   a.ddd = out->d_ddot;
   a.energy = out->energy;
   a.Ed = out->Ed;
-  a.ed_now = (double *)ctx->run_scratch.ptr;
+  a.Es = (double *)scr;
+  a.H32 = mixed ? (float4 *)(scr + es_bytes) : nullptr;
   a.status = ctx->d_status;
-  int threads = dp->N >= 256 ? 256 : ((dp->N + 31) / 32) * 32;
-  pc::lo_run_f64_kernel<<<dp->B, threads, 0, st>>>(a);
+  if (mixed) pc::lo_run_kernel<true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
+  else pc::lo_run_kernel<false><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
   if (opts->fit) {
-    double *ke = a.ed_now + nbn;
+    double *ke = (double *)(scr + es_bytes + h_bytes);
     pc::ke_series_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, ke);
     pc_status ls = pc::launch_fit(ctx, ke, (int)nbn, S, dt, opts->first_index, out->gamma, out->omega, nullptr,
                                   nullptr, st);

@@ -344,7 +344,7 @@ __device__ __forceinline__ void charge_mixed(float ax, float ay, float az, float
                                              float gy, float gz, float qs, float rex, float *acc, uint8_t &mask) {
   const float R2 = ax * ax + ay * ay + az * az;
   const float iR = rsqrtf(R2);
-  const float R = R2 * iR;
+  const float R = R2 > 0.f ? R2 * iR : 0.f;  // exact cancellation: 0 * inf would be NaN
   if (R <= rex) {
     mask = 1;
     return;
@@ -854,3 +854,4 @@ extern "C" pc_status pc_fields_plane(pc_ctx *ctx, const pc_charges *ch, const pc
   return pc::fields_impl(ctx, ch, dp, nullptr, grid, grid->nu * grid->nv, times, T, kind, precision, r_excl, out,
                          stream);
 }
+

@@ -8,8 +8,8 @@ Error metrics (per point, maximum over unmasked points), F the oracle's total fi
     dipole cancels by R/s (up to ~1e7 near a dipole whose moment crosses zero), which puts the
     oracle's own rounding above 1e-10 of |F| at such points.
   * mixed path: |F_gpu - F| <= 1e-5 * sum_j |F_j| with the sum over sources (a dipole's two charges
-    summed first), and |F_gpu - F| / |F| <= 1e-5 wherever the sources do not cancel
-    (sum_j |F_j| / |F| < 10).
+    summed first; for B the sum of |E_j| / c, the scale at which n x E / c rounds), and
+    |F_gpu - F| / |F| <= 1e-5 wherever the sources do not cancel (that sum / |F| < 10).
 """
 import math
 
@@ -66,7 +66,8 @@ def compare(out, ref, prec, keys=("E", "B", "phi", "A"), mix_tol=MIX_TOL):
             assert metric < F64_COND_TOL, (k, metric)
             assert plain < F64_TOL, (k, plain)
         else:
-            scale = ref["scale_source"][k][~m]
+            # B = n x E / c of each term rounds at |E| / c, like E itself
+            scale = (ref["scale_source"]["E"] / W.C if k == "B" else ref["scale_source"][k])[~m]
             metric = float(np.max(num / scale))
             well = scale / den < 10
             plain = float(np.max((num / den)[well])) if well.any() else 0.0
