@@ -187,6 +187,30 @@ pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t S, double 
                     double *gamma, double *omega, double *amp, double *phase, void *stream);
 
 /*
+ * pc_fields_noalloc -- pc_fields on a point list in PC_MIXED precision (float32 outputs) that
+ * allocates nothing.  The paper has no counterpart; this entry point exists for callers that may
+ * not allocate device memory: code inside a framework that owns the whole device pool through its
+ * own allocator, and latency-critical loops where cudaMalloc/cudaFree (which can synchronise the
+ * device) or an allocation failure in mid-run are not acceptable.  It needs no pc_ctx.
+ *
+ * Scratch: the float32 history mirrors, the point-charge reference positions and the status word
+ * live in one static device array of 16 MiB (plus a 256-byte header) that the library reserves on
+ * every GPU that loads it and keeps until the process exits.  The sources must fit it:
+ *   16 * N * S_dipoles + 48 * M * S_charges + 24 * M  <=  16 MiB  (bytes),
+ * otherwise the call returns PC_ERR_ARG without touching the device.
+ * Set-up: the first call on a device resolves the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  The device used is
+ * the caller's current device.
+ * Every call shares the one array and leaves its contents behind: each call clears the status word
+ * and rewrites the mirrors it reads, so calls in sequence are independent, but calls that overlap
+ * on the GPU (other streams, other host threads) race on the array and must not be issued.
+ * Arguments, outputs and errors are those of pc_fields with precision = PC_MIXED.
+ */
+pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sources *dp, const double *points, int64_t P,
+                            const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,
+                            void *stream);
+
+/*
  * pc_alu_peaks -- measures this GPU's float32 and float64 fused-multiply-add throughput (FMA/s)
  * with dependent-chain kernels; used as roofline denominators.  Writes fp32_fma_per_s,
  * fp64_fma_per_s (host pointers).

@@ -76,6 +76,8 @@ SIGNATURES = {
                                       ctypes.POINTER(PcRunOut), _vp]),
     "pc_ke_fit": (ctypes.c_int, [_vp, _vp, _i32, _i64, _f64, _i64, _vp, _vp, _vp, _vp, _vp]),
     "pc_alu_peaks": (ctypes.c_int, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _vp]),
+    "pc_fields_noalloc": (ctypes.c_int, [ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
+                                         ctypes.POINTER(_f64), _i32, _i32, _f64, ctypes.POINTER(PcFieldOut), _vp]),
 }
 
 _lib = None
@@ -294,3 +296,23 @@ def pc_alu_peaks(ctx, stream=None):
     a, b = _f64(0.0), _f64(0.0)
     _check(ctx.lib.pc_alu_peaks(ctx.handle, ctypes.byref(a), ctypes.byref(b), _stream(stream)), "pc_alu_peaks")
     return a.value, b.value
+
+
+def pc_fields_noalloc(charges=None, dipoles=None, points=None, times=(0.0,), kind=PC_TOTAL, r_excl=0.0, out=None,
+                      stream=None):
+    """pc_fields_noalloc on the current device: mixed precision, no allocation inside the library.
+
+    `out` (float32 tensors, see alloc_field_out) should be allocated by the caller ahead of time.
+    """
+    lib = load()
+    P = int(points.shape[0])
+    T = len(times)
+    o = alloc_field_out(P, T, PC_MIXED, points.device) if out is None else out
+    tarr = (_f64 * T)(*[float(t) for t in times])
+    chs = _charges_struct(charges)
+    dps = _dipoles_struct(dipoles)
+    st = lib.pc_fields_noalloc(ctypes.byref(chs) if chs else None, ctypes.byref(dps) if dps else None,
+                               _ptr(points), P, tarr, T, kind, float(r_excl), ctypes.byref(_out_struct(o)),
+                               _stream(stream))
+    _check(st, "pc_fields_noalloc")
+    return o

@@ -855,3 +855,128 @@ extern "C" pc_status pc_fields_plane(pc_ctx *ctx, const pc_charges *ch, const pc
                          stream);
 }
 
+// ================================================================================================
+// pc_fields_noalloc: the mixed-precision point-list evaluation with its scratch in a static device
+// array instead of a context workspace, for callers that may not allocate device memory.
+// ================================================================================================
+#include <mutex>
+
+namespace pc {
+
+// float32 history mirrors (dipoles, then point charges), the point-charge reference positions and
+// the status word of every pc_fields_noalloc call live here
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB
+constexpr size_t kStaticHeader = 256;                     // status word, padded to 256 B
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticHeader + kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void *g_noalloc_addr[kMaxDevices];
+static cudaError_t g_noalloc_err[kMaxDevices];
+static std::once_flag g_noalloc_once[kMaxDevices];
+
+}  // namespace pc
+
+extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sources *dp, const double *points,
+                                       int64_t P, const double *times, int32_t T, int32_t kind, double r_excl,
+                                       const pc_field_out *out, void *stream) {
+  using namespace pc;
+  if (!out || !times || T < 1 || P < 0) return PC_ERR_ARG;
+  if (kind < PC_TOTAL || kind > PC_RADIATION || !(r_excl >= 0.0)) return PC_ERR_ARG;
+  const bool has_ch = ch && ch->M > 0, has_dp = dp && dp->N > 0;
+  if (!has_ch && !has_dp) return PC_ERR_ARG;
+  if ((ch && ch->M < 0) || (dp && dp->N < 0)) return PC_ERR_ARG;
+  if (has_ch && (ch->S < 2 || !(ch->dt > 0.0) || !isfinite(ch->t0) || !ch->q || !ch->pos || !ch->vel || !ch->acc))
+    return PC_ERR_ARG;
+  if (has_dp && (dp->S < 2 || !(dp->dt > 0.0) || !isfinite(dp->t0) || !dp->origin || !dp->axis || !dp->q ||
+                 !dp->m1 || !dp->m2 || !dp->d || !dp->d_dot || !dp->d_ddot))
+    return PC_ERR_ARG;
+  for (int i = 0; i < T; ++i)
+    if (!isfinite(times[i])) return PC_ERR_ARG;
+  if (P == 0) return PC_OK;
+  if (!points) return PC_ERR_ARG;
+  // the scratch must hold the float32 mirrors and the reference positions
+  const size_t nd = has_dp ? (size_t)dp->N * (size_t)dp->S : 0;
+  const size_t nc = has_ch ? (size_t)ch->M * (size_t)ch->S * 3 : 0;
+  const size_t need = (nd + nc) * sizeof(float4) + (has_ch ? (size_t)ch->M * 3 * sizeof(double) : 0);
+  if (need > kStaticScratchBytes) return PC_ERR_ARG;
+  if ((has_dp && dp->S > (int64_t)1 << 30) || (has_ch && ch->S > (int64_t)1 << 30)) return PC_ERR_ARG;
+
+  // once per device, with that device current: the device address of the static scratch
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PC_ERR_CUDA;
+  std::call_once(g_noalloc_once[dev],
+                 [dev] { g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch); });
+  if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev]) return PC_ERR_CUDA;
+  unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
+  int *status = (int *)base;
+  float4 *Hd = (float4 *)(base + kStaticHeader);
+  float4 *Hc = Hd + nd;
+  double *cref = (double *)(Hc + nc);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaGetLastError();
+  // the array keeps the previous call's contents: the status word must start at zero
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PC_ERR_CUDA;
+
+  Launch L;
+  memset(&L, 0, sizeof(L));
+  L.pts.list = points;
+  L.pts.P = P;
+  Sources &s = L.src;
+  if (has_ch) {
+    s.M = ch->M;
+    s.S = ch->S;
+    s.t0 = ch->t0;
+    s.dt = ch->dt;
+    s.q = ch->q;
+    s.pos = ch->pos;
+    s.vel = ch->vel;
+    s.acc = ch->acc;
+    s.static_before = ch->static_before;
+  }
+  if (has_dp) {
+    s.N = dp->N;
+    s.Sd = dp->S;
+    s.t0d = dp->t0;
+    s.dtd = dp->dt;
+    s.origin = dp->origin;
+    s.axis = dp->axis;
+    s.qd = dp->q;
+    s.m1 = dp->m1;
+    s.m2 = dp->m2;
+    s.d = dp->d;
+    s.dd = dp->d_dot;
+    s.ddd = dp->d_ddot;
+  }
+  L.out.E = out->E;
+  L.out.B = out->B;
+  L.out.phi = out->phi;
+  L.out.A = out->A;
+  L.out.mask = out->mask;
+  L.r_excl = r_excl;
+  L.status = status;
+  L.Hd = Hd;
+  L.Hc = Hc;
+  L.cref = cref;
+  // the mirrors are rewritten in full by every call
+  if (has_dp) prep_dipoles_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(s, Hd);
+  if (has_ch) {
+    const int64_t n = (int64_t)s.M * s.S;
+    prep_charges_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hc, cref);
+  }
+  const int64_t tiles = (P + kMixThreads - 1) / kMixThreads;
+  for (int32_t f0 = 0; f0 < T; f0 += kMaxT) {
+    L.T = min(kMaxT, T - f0);
+    L.frame0 = f0;
+    for (int i = 0; i < L.T; ++i) L.times[i] = times[f0 + i];
+    dim3 grid((unsigned)tiles, (unsigned)L.T);
+    if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, true><<<grid, kMixThreads, 0, st>>>(L, 1);
+    else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, true><<<grid, kMixThreads, 0, st>>>(L, 1);
+    else fields_mixed_kernel<PC_RADIATION, true><<<grid, kMixThreads, 0, st>>>(L, 1);
+  }
+  if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+  int h = 0;  // pageable host word: the copy completes before cudaMemcpyAsync returns to the stream order
+  if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PC_ERR_CUDA;
+  return (pc_status)h;
+}
