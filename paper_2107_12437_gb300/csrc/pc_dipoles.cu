@@ -13,6 +13,9 @@
 // pc_ke_fit: one CTA per series; Levenberg-Marquardt with block reductions.
 #include <stdio.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "pc_internal.cuh"
 #include "pc_lw_f32.cuh"
 #include "pc_lw_f64.cuh"
@@ -21,6 +24,7 @@ namespace pc {
 
 constexpr int kRunWarps = 8;   // receivers advanced concurrently by one CTA
 constexpr int kMaxBlock = 16;  // steps per causal block (2K <= 32 stages, one per lane)
+constexpr int kSmallN = 64;    // configurations up to this size run as one persistent CTA each
 
 struct RunArgs {
   int B, N;
@@ -33,9 +37,18 @@ struct RunArgs {
   float4 *H32;        // [B][N][S] float32 mirror (mixed path)
   double *Es;         // scratch [B][N][2*kMaxBlock+1] stage fields
   int *status;
+  // tables built once per run (mixed path): per-dipole float records, per-pair centre delays
+  float *dipf;        // [B][N][kDipF]: origin/L as hi+lo (6), axis (3), m2/(m1+m2), m1/(m1+m2), q/e
+  int2 *delay;        // [B][N][N]: |R_i - R_j| / (c dt) = x + y * 2^-30, x integer, y the fraction
+  int *kblock;        // [B] causal block length per configuration
 };
 
+constexpr int kDipF = 12;
+
 __device__ __forceinline__ size_t bidx(const RunArgs &a, int b, int i) { return (size_t)b * a.N + i; }
+
+template <bool MIXED>
+__device__ void rk4_block(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop);
 
 // Contribution of dipole j to the driving field of receiver i at time u (steps), history 0..nv.
 // float64: both charges per charge (Eqs. r_1, r_2, E); returns p_i . E.
@@ -101,30 +114,25 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
 // float32: the dipole pair in difference form from the float32 mirror; returns p_i . E in units
 // of k_e e / (c dt)^2.  kb + xc is the retarded time of dipole j's centre.
 __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, float xc, int nvalid, int *err) {
-  const double L = kC * a.dt;
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
-  const float rx = (float)((a.origin[3 * bi] - a.origin[3 * bj]) / L);
-  const float ry = (float)((a.origin[3 * bi + 1] - a.origin[3 * bj + 1]) / L);
-  const float rz = (float)((a.origin[3 * bi + 2] - a.origin[3 * bj + 2]) / L);
+  const float *fi = a.dipf + bi * kDipF, *fj = a.dipf + bj * kDipF;
+  // origin offsets from hi + lo parts: the hi difference of nearby origins is exact
+  const float rx = (fi[0] - fj[0]) + (fi[3] - fj[3]);
+  const float ry = (fi[1] - fj[1]) + (fi[4] - fj[4]);
+  const float rz = (fi[2] - fj[2]) + (fi[5] - fj[5]);
   const float rn = sqrtf(rx * rx + ry * ry + rz * rz);
-  const float px = (float)a.axis[3 * bj], py = (float)a.axis[3 * bj + 1], pz = (float)a.axis[3 * bj + 2];
+  const float px = fj[6], py = fj[7], pz = fj[8];
   const float rp = rx * px + ry * py + rz * pz;
-  const double m1 = a.m1[bj], m2 = a.m2[bj];
-  const float mup = (float)(m2 / (m1 + m2)), mum = (float)(m1 / (m1 + m2));
-  const float4 *H = a.H32 + bj * (size_t)(a.n_steps + 1);
-  float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
-  int e1 = dip_charge_solve(H, nvalid, kb, xc, rn, rp, mup, Xp, Vp, Ap, dp);
-  int e2 = dip_charge_solve(H, nvalid, kb, xc, rn, rp, -mum, Xm, Vm, Am, dm);
-  if (e1 | e2) {
-    int e = e1 ? e1 : e2;
+  const HistF32 H{a.H32 + bj * (size_t)(a.n_steps + 1)};
+  float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  uint8_t mk = 0;
+  const int e = dipole_net<PC_TOTAL, float, HistF32>(H, nvalid, kb, xc, rx, ry, rz, rn, px, py, pz, rp, fj[9], fj[10],
+                                                     fj[11], 0.f, false, acc, mk);
+  if (e) {
     *err = (e == PC_ERR_HISTORY) ? PC_ERR_CAUSALITY : e;
     return 0.f;
   }
-  float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  uint8_t mk = 0;
-  dipole_pair_mixed<PC_TOTAL>(rx, ry, rz, rn, px, py, pz, rp, mup, mum, (float)(a.q[bj] / kE), Xp, Vp, Ap, dp, Xm,
-                              Vm, Am, dm, 0.f, acc, mk);
-  return acc[0] * (float)a.axis[3 * bi] + acc[1] * (float)a.axis[3 * bi + 1] + acc[2] * (float)a.axis[3 * bi + 2];
+  return acc[0] * fi[6] + acc[1] * fi[7] + acc[2] * fi[8];
 }
 
 // Phase A for one receiver (one warp): stage fields E_d(n0 + (s+1)/2), s < ns, into Es[1 + s];
@@ -143,13 +151,10 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       if (j == i) continue;
       if (MIXED) {
         // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
-        const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
-        const double L = kC * a.dt;
-        const double dx = a.origin[3 * bi] - a.origin[3 * bj], dy = a.origin[3 * bi + 1] - a.origin[3 * bj + 1],
-                     dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
-        const double x = stage - sqrt(dx * dx + dy * dy + dz * dz) / L;
-        const double fl = floor(x);
-        const float v = pair_drive_f32(a, b, i, j, (int)n0 + (int)fl, (float)(x - fl), (int)n0 + 1, err);
+        const int2 dl = a.delay[(size_t)bidx(a, b, i) * a.N + j];
+        const float xs = (float)stage - (float)dl.y * 0x1p-30f;
+        const int fl = __float2int_rd(xs);
+        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - (float)fl, (int)n0 + 1, err);
         // Kahan sum over sources
         const float y = v - comp;
         const float t = accf + y;
@@ -180,22 +185,8 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
   __shared__ double sh[kRunWarps][32];
   __shared__ int s_stop, s_K;
   const double L = kC * a.dt;
-  // ---- block length from the smallest origin-to-charge distance of this configuration ----
   if (threadIdx.x == 0) {
-    double rmin = 1e300, smax = 0.0;
-    for (int i = 0; i < N; ++i) {
-      const size_t bi = bidx(a, b, i);
-      smax = fmax(smax, fabs(a.d0[bi] / a.q[bi]));
-      for (int j = i + 1; j < N; ++j) {
-        const size_t bj = bidx(a, b, j);
-        const double dx = a.origin[3 * bi] - a.origin[3 * bj], dy = a.origin[3 * bi + 1] - a.origin[3 * bj + 1],
-                     dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
-        rmin = fmin(rmin, sqrt(dx * dx + dy * dy + dz * dz));
-      }
-    }
-    // charges sit up to |r_dip| from their origin; allow three times the initial amplitude
-    const double kk = floor((rmin - 3.0 * smax) / L);
-    s_K = (int)fmax(1.0, fmin((double)kMaxBlock, kk));
+    s_K = a.kblock[b];
     s_stop = 0;
   }
   // ---- history sample 0: at rest with moment d0 (Sec. 3.2) ----
@@ -241,52 +232,156 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     // phase B: kb RK4 steps per receiver (lane 0 of its warp)
     for (int i = warp; i < N; i += kRunWarps) {
       if (lane != 0) continue;
-      const size_t bi = bidx(a, b, i);
-      double *Es = a.Es + bi * (2 * kMaxBlock + 1);
-      const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
-      const double m = m1 * m2 / (m1 + m2);
-      const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
-      const double qm = q * q / m;
-      const double dt = a.dt;
-      const double vfac = fmax(m1, m2) / (m1 + m2) / q;
-      double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
-      for (int k = 0; k < kb; ++k) {
-        const int64_t n = n0 + k;
-        const double e1 = Es[2 * k];
-        const double f2 = (a.ed_mode == 1) ? e1 : Es[2 * k + 1];
-        const double e4 = Es[2 * k + 2];
-        const double f4 = (a.ed_mode == 1) ? e1 : e4;
-        // RK4 on (d, d') with d'' = -gamma0 d' - omega0^2 d + (q^2/m) E_d(t)
-        const double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
-        const double y0b = y0 + 0.5 * dt * k1a, y1b = y1 + 0.5 * dt * k1b;
-        const double k2a = y1b, k2b = -g0 * y1b - w0 * w0 * y0b + qm * f2;
-        const double y0c = y0 + 0.5 * dt * k2a, y1c = y1 + 0.5 * dt * k2b;
-        const double k3a = y1c, k3b = -g0 * y1c - w0 * w0 * y0c + qm * f2;
-        const double y0d = y0 + dt * k3a, y1d = y1 + dt * k3b;
-        const double k4a = y1d, k4b = -g0 * y1d - w0 * w0 * y0d + qm * f4;
-        const double yn0 = y0 + dt / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
-        const double yn1 = y1 + dt / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
-        const double ydd = qm * e4 - g0 * yn1 - w0 * w0 * yn0;
-        a.d[bi * S + n + 1] = yn0;
-        a.dd[bi * S + n + 1] = yn1;
-        a.ddd[bi * S + n + 1] = ydd;
-        if (MIXED)
-          a.H32[bi * S + n + 1] =
-              make_float4((float)(yn0 / (q * L)), (float)(yn1 / (q * kC)), (float)(ydd * dt / (q * kC)), 0.f);
-        if (a.Ed) a.Ed[bi * S + n + 1] = e4;
-        if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
-        if (fabs(yn1) * vfac > a.v_max) {
-          set_status(a.status, PC_ERR_VELOCITY);
-          s_stop = 1;
-          break;
-        }
-        y0 = yn0;
-        y1 = yn1;
-      }
-      Es[0] = Es[2 * kb];
+      int stop = 0;
+      rk4_block<MIXED>(a, b, i, n0, kb, &stop);
+      if (stop) s_stop = 1;
     }
     __syncthreads();
   }
+}
+
+// Per-run tables: float records of every dipole, centre-to-centre delays of every pair, and the
+// causal block length of every configuration (the smallest distance between an origin and another
+// dipole's charges, which sit up to |r_dip| from their origin; three times the initial amplitude
+// is allowed for).  One CTA per configuration.
+__global__ void lo_tables_kernel(const RunArgs a) {
+  const int b = blockIdx.x;
+  const int N = a.N;
+  const double L = kC * a.dt;
+  __shared__ double s_rmin[256], s_smax[256];
+  double rmin = 1e300, smax = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const size_t bi = bidx(a, b, i);
+    float *f = a.dipf + bi * kDipF;
+    for (int c = 0; c < 3; ++c) {
+      const double x = a.origin[3 * bi + c] / L;
+      const float hi = (float)x;
+      f[c] = hi;
+      f[3 + c] = (float)(x - (double)hi);
+      f[6 + c] = (float)a.axis[3 * bi + c];
+    }
+    const double m1 = a.m1[bi], m2 = a.m2[bi];
+    f[9] = (float)(m2 / (m1 + m2));
+    f[10] = (float)(m1 / (m1 + m2));
+    f[11] = (float)(a.q[bi] / kE);
+    smax = fmax(smax, fabs(a.d0[bi] / a.q[bi]));
+  }
+  for (int64_t ij = threadIdx.x; ij < (int64_t)N * N; ij += blockDim.x) {
+    const int i = (int)(ij / N), j = (int)(ij % N);
+    const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+    const double dx = a.origin[3 * bi] - a.origin[3 * bj], dy = a.origin[3 * bi + 1] - a.origin[3 * bj + 1],
+                 dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (i != j) rmin = fmin(rmin, r);
+    const double x = r / L;
+    const double fl = floor(x);
+    if (a.delay) a.delay[(size_t)bi * N + j] = make_int2((int)fl, (int)((x - fl) * 0x1p30));
+  }
+  s_rmin[threadIdx.x] = rmin;
+  s_smax[threadIdx.x] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < blockDim.x; ++t) {
+      rmin = fmin(rmin, s_rmin[t]);
+      smax = fmax(smax, s_smax[t]);
+    }
+    const double kk = floor((rmin - 3.0 * smax) / L);
+    a.kblock[b] = (int)fmax(1.0, fmin((double)kMaxBlock, kk));
+  }
+}
+
+// Grid-wide phases for large configurations: history sample 0, stage fields (one warp per
+// receiver) and RK4 (one thread per receiver), one launch each per causal block.
+template <bool MIXED>
+__global__ void lo_init_kernel(const RunArgs a) {
+  const int64_t S = a.n_steps + 1;
+  const double L = kC * a.dt;
+  for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < (int64_t)a.B * a.N;
+       bi += (int64_t)gridDim.x * blockDim.x) {
+    a.d[bi * S] = a.d0[bi];
+    a.dd[bi * S] = 0.0;
+    a.ddd[bi * S] = 0.0;
+    if (MIXED) a.H32[bi * S] = make_float4((float)(a.d0[bi] / (a.q[bi] * L)), 0.f, 0.f, 0.f);
+    if (a.energy) {
+      const double m = a.m1[bi] * a.m2[bi] / (a.m1[bi] + a.m2[bi]);
+      const double w0 = a.omega0[bi], q = a.q[bi], x = a.d0[bi];
+      a.energy[bi * S] = m * w0 * w0 * x * x / (2.0 * q * q);
+    }
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs a, int64_t n0, int ns) {
+  __shared__ double sh[kRunWarps][32];
+  if (*((volatile int *)a.status)) return;  // an earlier block failed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  const int i = blockIdx.x * kRunWarps + warp;
+  if (i >= a.N) return;
+  int err = 0;
+  drive_phase<MIXED>(a, b, i, n0, ns, sh[warp], &err);
+  if (err) set_status(a.status, err);
+  if (ns == 0 && lane == 0 && a.Ed) a.Ed[bidx(a, b, i) * (a.n_steps + 1)] = a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)];
+}
+
+template <bool MIXED>
+__global__ void lo_rk4_kernel(const RunArgs a, int64_t n0, int kb) {
+  if (*((volatile int *)a.status)) return;
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= (int64_t)a.B * a.N) return;
+  int stop = 0;
+  rk4_block<MIXED>(a, (int)(bi / a.N), (int)(bi % a.N), n0, kb, &stop);
+}
+
+// Phase B for receiver i: kb RK4 steps (Eq. LO_equation) from step n0 with the stage fields Es,
+// appending d, d', d'' (and the float32 mirror, energy, E_d) to the history.
+template <bool MIXED>
+__device__ void rk4_block(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop) {
+  const int64_t S = a.n_steps + 1;
+  const double L = kC * a.dt;
+  const size_t bi = bidx(a, b, i);
+  double *Es = a.Es + bi * (2 * kMaxBlock + 1);
+  const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
+  const double m = m1 * m2 / (m1 + m2);
+  const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
+  const double qm = q * q / m;
+  const double dt = a.dt;
+  const double vfac = fmax(m1, m2) / (m1 + m2) / q;
+  double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
+  for (int k = 0; k < kb; ++k) {
+    const int64_t n = n0 + k;
+    const double e1 = Es[2 * k];
+    const double f2 = (a.ed_mode == 1) ? e1 : Es[2 * k + 1];
+    const double e4 = Es[2 * k + 2];
+    const double f4 = (a.ed_mode == 1) ? e1 : e4;
+    // RK4 on (d, d') with d'' = -gamma0 d' - omega0^2 d + (q^2/m) E_d(t)
+    const double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
+    const double y0b = y0 + 0.5 * dt * k1a, y1b = y1 + 0.5 * dt * k1b;
+    const double k2a = y1b, k2b = -g0 * y1b - w0 * w0 * y0b + qm * f2;
+    const double y0c = y0 + 0.5 * dt * k2a, y1c = y1 + 0.5 * dt * k2b;
+    const double k3a = y1c, k3b = -g0 * y1c - w0 * w0 * y0c + qm * f2;
+    const double y0d = y0 + dt * k3a, y1d = y1 + dt * k3b;
+    const double k4a = y1d, k4b = -g0 * y1d - w0 * w0 * y0d + qm * f4;
+    const double yn0 = y0 + dt / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+    const double yn1 = y1 + dt / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+    const double ydd = qm * e4 - g0 * yn1 - w0 * w0 * yn0;
+    a.d[bi * S + n + 1] = yn0;
+    a.dd[bi * S + n + 1] = yn1;
+    a.ddd[bi * S + n + 1] = ydd;
+    if (MIXED)
+      a.H32[bi * S + n + 1] =
+          make_float4((float)(yn0 / (q * L)), (float)(yn1 / (q * kC)), (float)(ydd * dt / (q * kC)), 0.f);
+    if (a.Ed) a.Ed[bi * S + n + 1] = e4;
+    if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
+    if (fabs(yn1) * vfac > a.v_max) {
+      set_status(a.status, PC_ERR_VELOCITY);
+      *stop = 1;
+      break;
+    }
+    y0 = yn0;
+    y1 = yn1;
+  }
+  Es[0] = Es[2 * kb];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -625,11 +720,17 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
   const size_t nbn = (size_t)dp->B * dp->N;
   const bool mixed = opts->precision == PC_MIXED;
   if (mixed && S > ((int64_t)1 << 30)) return PC_ERR_ARG;
-  // scratch: stage fields, the float32 mirror (mixed), kinetic energies for the fit
-  const size_t es_bytes = nbn * (2 * pc::kMaxBlock + 1) * sizeof(double);
-  const size_t h_bytes = mixed ? nbn * S * sizeof(float4) : 0;
-  const size_t ke_bytes = opts->fit ? nbn * S * sizeof(double) : 0;
-  if (ctx->run_scratch.reserve(es_bytes + h_bytes + ke_bytes) != cudaSuccess) return PC_ERR_CUDA;
+  // scratch: stage fields, float32 mirror (mixed), dipole records, pair delays (mixed), block
+  // lengths, kinetic energies for the fit
+  auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const size_t es_bytes = al(nbn * (2 * pc::kMaxBlock + 1) * sizeof(double));
+  const size_t h_bytes = mixed ? al(nbn * S * sizeof(float4)) : 0;
+  const size_t f_bytes = al(nbn * pc::kDipF * sizeof(float));
+  const size_t dl_bytes = mixed ? al(nbn * dp->N * sizeof(int2)) : 0;
+  const size_t k_bytes = al(dp->B * sizeof(int));
+  const size_t ke_bytes = opts->fit ? al(nbn * S * sizeof(double)) : 0;
+  if (ctx->run_scratch.reserve(es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes + ke_bytes) != cudaSuccess)
+    return PC_ERR_CUDA;
   char *scr = (char *)ctx->run_scratch.ptr;
   pc::RunArgs a;
   a.B = dp->B;
@@ -652,11 +753,47 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
   a.Ed = out->Ed;
   a.Es = (double *)scr;
   a.H32 = mixed ? (float4 *)(scr + es_bytes) : nullptr;
+  a.dipf = (float *)(scr + es_bytes + h_bytes);
+  a.delay = mixed ? (int2 *)(scr + es_bytes + h_bytes + f_bytes) : nullptr;
+  a.kblock = (int *)(scr + es_bytes + h_bytes + f_bytes + dl_bytes);
   a.status = ctx->d_status;
-  if (mixed) pc::lo_run_kernel<true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
-  else pc::lo_run_kernel<false><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
+  char *ke_base = scr + es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes;
+  pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
+  if (dp->N <= pc::kSmallN) {
+    // small configurations: one persistent CTA each, the time loop inside
+    if (mixed) pc::lo_run_kernel<true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
+    else pc::lo_run_kernel<false><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
+  } else {
+    // large configurations: grid-wide phases, one drive and one RK4 launch per causal block of the
+    // shortest block length over the batch
+    std::vector<int> kb(dp->B);
+    if (cudaMemcpyAsync(kb.data(), a.kblock, dp->B * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return PC_ERR_CUDA;
+    int K = pc::kMaxBlock;
+    for (int v : kb) K = std::min(K, v);
+    const dim3 dgrid((unsigned)((dp->N + pc::kRunWarps - 1) / pc::kRunWarps), (unsigned)dp->B);
+    const unsigned rgrid = (unsigned)((nbn + 127) / 128);
+    if (mixed) {
+      pc::lo_init_kernel<true><<<rgrid, 128, 0, st>>>(a);
+      pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
+      for (int64_t n0 = 0; n0 < n_steps; n0 += K) {
+        const int k = (int)std::min((int64_t)K, n_steps - n0);
+        pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * k);
+        pc::lo_rk4_kernel<true><<<rgrid, 128, 0, st>>>(a, n0, k);
+      }
+    } else {
+      pc::lo_init_kernel<false><<<rgrid, 128, 0, st>>>(a);
+      pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
+      for (int64_t n0 = 0; n0 < n_steps; n0 += K) {
+        const int k = (int)std::min((int64_t)K, n_steps - n0);
+        pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * k);
+        pc::lo_rk4_kernel<false><<<rgrid, 128, 0, st>>>(a, n0, k);
+      }
+    }
+  }
   if (opts->fit) {
-    double *ke = (double *)(scr + es_bytes + h_bytes);
+    double *ke = (double *)ke_base;
     pc::ke_series_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, ke);
     pc_status ls = pc::launch_fit(ctx, ke, (int)nbn, S, dt, opts->first_index, out->gamma, out->omega, nullptr,
                                   nullptr, st);

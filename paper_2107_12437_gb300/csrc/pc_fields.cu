@@ -25,8 +25,10 @@ namespace pc {
 constexpr int kMaxT = 32;        // times per launch (the host splits longer lists)
 constexpr int kMixThreads = 256; // points per CTA in the mixed path
 constexpr int kChunk = 64;       // sources staged in shared memory at a time
-// dipoles closer than this many c*dt to a point are summed in float64 (see the kernel comment)
-constexpr float kNearL = 320.f;
+// a dipole closer than kNearL c*dt to a point whose near field there cancels by more than kCancel
+// (dipole_cancellation) is summed in float64 instead
+constexpr float kNearL = 400.f;
+constexpr float kCancel = 6.f;
 
 struct Points {
   const double *list;  // [P][3] or null for a plane
@@ -276,65 +278,36 @@ __device__ __forceinline__ ff ff_from_double(double x) {
   return {hi, (float)(x - (double)hi)};
 }
 
-// Both charges of dipole j in float64 (plain per-charge evaluation), added to the float32
-// accumulators in their units.  Used for points within kNearL of the dipole, where the float32
-// difference form loses accuracy: there the sampled position X and velocity V at the retarded
-// time combine as X + R V, which nearly vanishes whenever the dipole's instantaneous moment
-// crosses zero.
+// Both charges of dipole j in float64, added to the float32 accumulators in their units.  Used for
+// points within kNearL of the dipole, where the float32 difference form loses accuracy: there the
+// sampled position X and velocity V at the retarded time combine as X + R V, which nearly vanishes
+// whenever the dipole's instantaneous moment crosses zero.  Exact per-charge roots (no segment
+// extension), the same difference form in double.
 template <int KIND>
-__device__ __forceinline__ int near_dipole_f64(const Sources &s, int j, double r0, double r1, double r2, double u,
-                                            long long kg, double r_excl, double invE, double invP, float *part,
-                                            uint8_t *mask) {
-  const double r[3] = {r0, r1, r2};
-  const double cdt = kC * s.dtd;
-  TrajF64 tr;
-  tr.dipole = true;
-  tr.d = s.d + (size_t)j * s.Sd;
-  tr.dd = s.dd + (size_t)j * s.Sd;
-  tr.ddd = s.ddd + (size_t)j * s.Sd;
-  for (int i = 0; i < 3; ++i) {
-    tr.R[i] = s.origin[3 * j + i];
-    tr.ax[i] = s.axis[3 * j + i];
-  }
+__device__ __noinline__ int near_dipole_f64(const Sources &s, int j, const double r[3], double u, double Ld,
+                                               double r_excl, float *part, uint8_t *mask) {
   const double q = s.qd[j], m1 = s.m1[j], m2 = s.m2[j];
-  double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, A[3] = {0, 0, 0}, phi = 0.0;
-  for (int sg = 0; sg < 2; ++sg) {
-    tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
-    int64_t k;
-    double th;
-    int e = solve_f64(tr, s.Sd, 1, r, u, cdt, (int64_t)kg, &k, &th);
-    if (e) return e;
-    double p0[3], v[3], a[3];
-    if (k < 0 || (k == 0 && th == 0.0)) {
-      tr.p(0, p0);
-      v[0] = v[1] = v[2] = 0.0;
-      a[0] = a[1] = a[2] = 0.0;
-    } else {
-      double p1[3], v1[3], a1[3];
-      tr.p(k, p0);
-      tr.p(k + 1, p1);
-      tr.va(k, v, a);
-      tr.va(k + 1, v1, a1);
-      for (int i = 0; i < 3; ++i) {
-        p0[i] += th * (p1[i] - p0[i]);
-        v[i] += th * (v1[i] - v[i]);
-        a[i] += th * (a1[i] - a[i]);
-      }
-    }
-    double av[3] = {r[0] - p0[0], r[1] - p0[1], r[2] - p0[2]};
-    lw_add_f64<KIND>(sg == 0 ? q : -q, av, v, a, r_excl, E, B, &phi, A, mask);
-  }
-  const double invB = invE * kC, invA = invP * kC;
-  part[0] += (float)(E[0] * invE);
-  part[1] += (float)(E[1] * invE);
-  part[2] += (float)(E[2] * invE);
-  part[3] += (float)(B[0] * invB);
-  part[4] += (float)(B[1] * invB);
-  part[5] += (float)(B[2] * invB);
-  part[6] += (float)(phi * invP);
-  part[7] += (float)(A[0] * invA);
-  part[8] += (float)(A[1] * invA);
-  part[9] += (float)(A[2] * invA);
+  const double rx = (r[0] - s.origin[3 * j]) / Ld, ry = (r[1] - s.origin[3 * j + 1]) / Ld,
+               rz = (r[2] - s.origin[3 * j + 2]) / Ld;
+  const double rn = sqrt(rx * rx + ry * ry + rz * rz);
+  const double px = s.axis[3 * j], py = s.axis[3 * j + 1], pz = s.axis[3 * j + 2];
+  const double rp = rx * px + ry * py + rz * pz;
+  const double x = u - rn;
+  const double fl = floor(x);
+  HistF64 H;
+  H.d = s.d + (size_t)j * s.Sd;
+  H.dd = s.dd + (size_t)j * s.Sd;
+  H.ddd = s.ddd + (size_t)j * s.Sd;
+  H.sx = 1.0 / (q * Ld);
+  H.sv = 1.0 / (q * kC);
+  H.sa = s.dtd / (q * kC);
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int e = dipole_net<KIND, double, HistF64>(H, (int)s.Sd, (int)fl, x - fl, rx, ry, rz, rn, px, py, pz, rp,
+                                                  m2 / (m1 + m2), m1 / (m1 + m2), q / kE, r_excl / Ld, true, acc,
+                                                  *mask);
+  if (e) return e;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) part[i] += (float)acc[i];
   return 0;
 }
 
@@ -379,19 +352,27 @@ __device__ __forceinline__ void charge_mixed(float ax, float ay, float az, float
   acc[9] += qs * i1 * vz;
 }
 
-__device__ __forceinline__ void kahan_add(float *sum, float *comp, const float *part) {
+// Kahan-compensated running sums of the ten outputs; each thread's sums live in shared memory,
+// strided by the block size (they are touched once per group of eight sources).
+struct KahanSmem {
+  float *sum, *comp;  // [10][kMixThreads], thread column tid
+  __device__ __forceinline__ void add(const float *part) const {
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    float y = part[i] - comp[i];
-    float t = sum[i] + y;
-    comp[i] = (t - sum[i]) - y;
-    sum[i] = t;
+    for (int i = 0; i < 10; ++i) {
+      const float s0 = sum[i * kMixThreads], c0 = comp[i * kMixThreads];
+      const float y = part[i] - c0;
+      const float t = s0 + y;
+      comp[i * kMixThreads] = (t - s0) - y;
+      sum[i * kMixThreads] = t;
+    }
   }
-}
+  __device__ __forceinline__ float get(int i) const { return sum[i * kMixThreads] - comp[i * kMixThreads]; }
+};
 
 template <int KIND, bool LIST>
-__global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
+__global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
   __shared__ double s_anchor[3];
+  __shared__ float s_kahan[2][10][kMixThreads];
   __shared__ float4 s_geo[kChunk];   // rho_a (x,y,z), |rho_a|
   __shared__ float4 s_geo_lo[kChunk]; // low parts of rho_a and |rho_a| (list mode)
   __shared__ float4 s_ax[kChunk];    // axis (x,y,z), q/e
@@ -431,9 +412,12 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
   double r[3];
   point_at(L.pts, active ? p : 0, r);
   const double t = L.times[f];
-  float sum[10], comp[10];
+  const KahanSmem acc{&s_kahan[0][0][tid], &s_kahan[1][0][tid]};
 #pragma unroll
-  for (int i = 0; i < 10; ++i) sum[i] = comp[i] = 0.f;
+  for (int i = 0; i < 10; ++i) {
+    s_kahan[0][i][tid] = 0.f;
+    s_kahan[1][i][tid] = 0.f;
+  }
   uint8_t mask = 0;
   int err = 0;
   // lengths of the two source groups (c dt) and scale of group g relative to the output unit
@@ -449,7 +433,6 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
     const float dr2 = drx * drx + dry * dry + drz * drz;
     const double u = (t - s.t0d) / s.dtd;
     const float rex = (float)(L.r_excl / Ld);
-    const double invE = Lref * Lref / (kKe * kE), invP = Lref / (kKe * kE);
     const int Sd32 = (int)s.Sd;
     for (int base = 0; base < s.N; base += kChunk) {
       const int nch = min(kChunk, s.N - base);
@@ -506,39 +489,36 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
           xc = (x.hi - (float)fl) + x.lo;
         }
         const float rp = rx * ax.x + ry * ax.y + rz * ax.z;
-        if (rn < kNearL) {
-          near_mask |= 1ull << jj;  // evaluated in float64 after this chunk
-          continue;
-        }
-        const float4 *H = L.Hd + (size_t)(base + jj) * s.Sd;
+        const HistF32 H{L.Hd + (size_t)(base + jj) * s.Sd};
         float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
-        int e1 = dip_charge_solve(H, Sd32, kb, xc, rn, rp, mu.x, Xp, Vp, Ap, dp);
-        int e2 = dip_charge_solve(H, Sd32, kb, xc, rn, rp, -mu.y, Xm, Vm, Am, dm);
-        if (e1 | e2) {
-          err = e1 ? e1 : e2;
+        const int e = dipole_states<float, HistF32>(H, Sd32, kb, xc, rn, rp, mu.x, mu.y, false, Xp, Vp, Ap, dp, Xm, Vm,
+                                                    Am, dm);
+        if (e) {
+          err = e;
           break;
         }
-        dipole_pair_mixed<KIND>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm, Am,
-                                dm, rex, part, mask);
+        if (rn < kNearL && dipole_cancellation<float>(rn, mu.x, mu.y, Xp, Vp, Ap, Xm, Vm, Am) > kCancel) {
+          near_mask |= 1ull << jj;  // ill-conditioned in float32: evaluated in float64 after this chunk
+          continue;
+        }
+        dipole_pair<KIND, float>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm, Am, dm,
+                                 rex, part, mask);
         if ((jj & 7) == 7) {
-          kahan_add(sum, comp, part);
+          acc.add(part);
 #pragma unroll
           for (int i = 0; i < 10; ++i) part[i] = 0.f;
         }
       }
-      kahan_add(sum, comp, part);
+      acc.add(part);
       // near pairs of this chunk, in float64
       while (near_mask && !err) {
         const int jj = __ffsll((long long)near_mask) - 1;
         near_mask &= near_mask - 1ull;
 #pragma unroll
         for (int i = 0; i < 10; ++i) part[i] = 0.f;
-        const int j = base + jj;
-        const double dx = r[0] - s.origin[3 * j], dy = r[1] - s.origin[3 * j + 1], dz = r[2] - s.origin[3 * j + 2];
-        const long long kg = (long long)floor(u - sqrt(dx * dx + dy * dy + dz * dz) / Ld);
-        const int e = near_dipole_f64<KIND>(s, j, r[0], r[1], r[2], u, kg, L.r_excl, invE, invP, part, &mask);
+        const int e = near_dipole_f64<KIND>(s, base + jj, r, u, Ld, L.r_excl, part, &mask);
         if (e) err = e;
-        kahan_add(sum, comp, part);
+        acc.add(part);
       }
     }
   }
@@ -617,7 +597,7 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
           const float A = 1.f - (wx * wx + wy * wy + wz * wz);
           const float B = rn - ((rx - ocx) * wx + (ry - ocy) * wy + (rz - ocz) * wz);
           const float C = ocx * (2.f * rx - ocx) + ocy * (2.f * ry - ocy) + ocz * (2.f * rz - ocz);
-          const float sq = fsqrt_approx(fmaxf(B * B - A * C, 0.f));
+          const float sq = Num<float>::sqrt0(fmaxf(B * B - A * C, 0.f));
           const float dl = (B > 0.f) ? -__fdividef(C, B + sq) : __fdividef(-B + sq, A);
           float th = thc - dl;
           const bool ok = (j < 0) ? ((float)j + th <= 1e-4f)
@@ -667,12 +647,12 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
 #pragma unroll
         for (int i = 6; i < 10; ++i) part[i] += sP * c10[i];
         if ((cc & 7) == 7) {
-          kahan_add(sum, comp, part);
+          acc.add(part);
 #pragma unroll
           for (int i = 0; i < 10; ++i) part[i] = 0.f;
         }
       }
-      kahan_add(sum, comp, part);
+      acc.add(part);
     }
   }
   if (!active) return;
@@ -686,22 +666,22 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed_kernel(const Laun
   const int64_t o = (L.frame0 + f) * L.pts.P + p;
   if (L.out.E) {
     float *e = (float *)L.out.E + 3 * o;
-    e[0] = fE * (sum[0] - comp[0]);
-    e[1] = fE * (sum[1] - comp[1]);
-    e[2] = fE * (sum[2] - comp[2]);
+    e[0] = fE * acc.get(0);
+    e[1] = fE * acc.get(1);
+    e[2] = fE * acc.get(2);
   }
   if (L.out.B) {
     float *b = (float *)L.out.B + 3 * o;
-    b[0] = fB * (sum[3] - comp[3]);
-    b[1] = fB * (sum[4] - comp[4]);
-    b[2] = fB * (sum[5] - comp[5]);
+    b[0] = fB * acc.get(3);
+    b[1] = fB * acc.get(4);
+    b[2] = fB * acc.get(5);
   }
-  if (L.out.phi) ((float *)L.out.phi)[o] = fP * (sum[6] - comp[6]);
+  if (L.out.phi) ((float *)L.out.phi)[o] = fP * acc.get(6);
   if (L.out.A) {
     float *a = (float *)L.out.A + 3 * o;
-    a[0] = fA * (sum[7] - comp[7]);
-    a[1] = fA * (sum[8] - comp[8]);
-    a[2] = fA * (sum[9] - comp[9]);
+    a[0] = fA * acc.get(7);
+    a[1] = fA * acc.get(8);
+    a[2] = fA * acc.get(9);
   }
   if (L.out.mask) L.out.mask[o] = mask;
 }

@@ -1,8 +1,9 @@
-// float32 device helpers shared by the field sum and the oscillator run: the retarded state of
-// one dipole charge from the float32 history mirror (Eq. ret_t on a linear segment, solved as a
-// quadratic in offsets from the dipole centre) and the net field of a dipole's two charges in
-// difference form (Eqs. E, B, V, A in Griffiths' form with v and a along the dipole axis).
-// Lengths in units of c*dt, times in samples, velocities in units of c.
+// Device helpers for the net field of a dipole's two charges in difference form, shared by the
+// field sum and the oscillator run, instantiated in float (the mixed path) and in double (pairs
+// near a dipole).  Eq. ret_t on a linear history segment is a quadratic in the offset of a charge
+// from its dipole centre; the Lienard-Wiechert fields (Eqs. E, B, V, A, Griffiths' form with v and
+// a along the dipole axis) are written with scalar coefficients whose +/- differences carry no
+// cancellation.  Lengths in units of c*dt, times in samples, velocities in units of c.
 #pragma once
 #include "pc_internal.cuh"
 
@@ -10,164 +11,306 @@ namespace pc {
 
 // a root up to this many samples past the last sample is taken at the last sample
 constexpr float kEndTol = 1e-3f;
+// both charges are evaluated on their centre's segment, extended linearly, when their own
+// retarded times lie within this many samples of it (the extension error is second order)
+constexpr float kExtrap = 0.1f;
 
-__device__ __forceinline__ float fsqrt_approx(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+template <typename T>
+struct Num;
+template <>
+struct Num<float> {
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float sqrt0(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+  static __device__ __forceinline__ int floor_int(float x) { return __float2int_rd(x); }
+};
+template <>
+struct Num<double> {
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double sqrt0(double x) { return x > 0.0 ? sqrt(x) : 0.0; }
+  static __device__ __forceinline__ int floor_int(double x) { return (int)floor(x); }
+};
 
-// Sample j of a dipole history; before the first sample the dipole rests with moment d[0].
-// Sample indices are 32-bit in the float32 path: conversions to 64-bit integers run on the
-// float64 unit, which is the narrowest pipe of this GPU.
-__device__ __forceinline__ float4 dip_sample(const float4 *H, int j) {
-  if (j >= 0) return __ldg(H + j);
-  float4 h0 = __ldg(H);
-  return make_float4(h0.x, 0.f, 0.f, 0.f);
-}
+// Dipole history samples (X = d/(qL), V = d'/(qc), A = d'' dt/(qc)); before the first sample the
+// dipole rests at X[0].  Sample indices are 32-bit: conversions to 64-bit integers run on the
+// float64 unit, the narrowest pipe of this GPU.
+struct HistF32 {
+  const float4 *H;
+  __device__ __forceinline__ void get(int j, float &x, float &v, float &a) const {
+    float4 h = __ldg(H + (j >= 0 ? j : 0));
+    x = h.x;
+    v = j >= 0 ? h.y : 0.f;
+    a = j >= 0 ? h.z : 0.f;
+  }
+};
+struct HistF64 {
+  const double *d, *dd, *ddd;
+  double sx, sv, sa;  // 1/(qL), 1/(qc), dt/(qc)
+  __device__ __forceinline__ void get(int j, double &x, double &v, double &a) const {
+    const int k = j >= 0 ? j : 0;
+    x = d[k] * sx;
+    v = j >= 0 ? dd[k] * sv : 0.0;
+    a = j >= 0 ? ddd[k] * sa : 0.0;
+  }
+};
 
-// Retarded state of one dipole charge at offset smu*X along the axis from the dipole centre.
+// Retarded state of one dipole charge at offset smu*X along the axis from the dipole centre, found
+// exactly on the piecewise-linear history.
 //   kb + xc: retarded time of the centre, in samples (xc small)
-//   rn = |rho|, rp = rho . axis (units of c dt)
-// Out: X, V, Ac interpolated at the charge's own retarded time; delta = its distance minus rn.
-__device__ __forceinline__ int dip_charge_solve(const float4 *H, int S, int kb, float xc, float rn, float rp,
-                                                float smu, float &X, float &V, float &Ac, float &delta) {
-  if (!(fabsf(xc) < 1e8f)) return PC_ERR_NOCONV;
-  int kc = __float2int_rd(xc);
-  float thc = xc - (float)kc;
+//   rn = |rho|, rp = rho . axis
+// Out: X, V, Ac at the charge's own retarded time; delta = its distance minus rn.
+template <typename T, typename Hist>
+__device__ __forceinline__ int dip_charge_solve(const Hist &H, int S, int kb, T xc, T rn, T rp, T smu, T &X, T &V,
+                                                T &Ac, T &delta) {
+  if (!(fabs(xc) < T(1e8))) return PC_ERR_NOCONV;
+  int kc = Num<T>::floor_int(xc);
+  T thc = xc - (T)kc;
   int j = kb + kc;
   // first-order estimate of the charge's delay offset picks its segment
   {
-    float4 h = dip_sample(H, j < S ? j : S - 1);
-    float d0 = (rn > 0.f) ? -smu * h.x * __fdividef(rp, rn) : 0.f;
-    int st = __float2int_rd(thc - d0);
+    T hx, hv, ha;
+    H.get(j < S ? j : S - 1, hx, hv, ha);
+    T d0 = (rn > T(0)) ? -smu * hx * Num<T>::div(rp, rn) : T(0);
+    int st = Num<T>::floor_int(thc - d0);
     j += st;
-    thc -= (float)st;
+    thc -= (T)st;
   }
   for (int it = 0; it < 6; ++it) {
     if (j > S - 2) {
       // past the end: solve on the last segment extended; a root up to kEndTol past the last
       // sample is clamped to it, a later one is a history error
-      thc += (float)(j - (S - 2));
+      thc += (T)(j - (S - 2));
       j = S - 2;
     }
-    float4 h0 = dip_sample(H, j), h1 = dip_sample(H, j + 1);
-    if (j < 0) h1 = h0;  // static segment
-    float dx = h1.x - h0.x;
-    float sc = smu * (h0.x + thc * dx);
-    float w = smu * dx;
-    float A = 1.f - w * w;
-    float B = rn - w * (rp - sc);
-    float C = sc * (2.f * rp - sc);
-    float sq = fsqrt_approx(fmaxf(B * B - A * C, 0.f));
-    float dl = (B > 0.f) ? -__fdividef(C, B + sq) : __fdividef(-B + sq, A);
-    float th = thc - dl;
-    bool ok = (j < 0) ? ((float)j + th <= 1e-4f)
-                      : (th >= -1e-4f && (th <= 1.0001f || (j == S - 2 && th <= 1.f + kEndTol)));
+    T x0, v0, a0, x1, v1, a1;
+    H.get(j, x0, v0, a0);
+    if (j < 0) {  // static segment
+      x1 = x0;
+      v1 = v0;
+      a1 = a0;
+    } else {
+      H.get(j + 1, x1, v1, a1);
+    }
+    const T dx = x1 - x0;
+    const T sc = smu * (x0 + thc * dx);
+    const T w = smu * dx;
+    const T A = T(1) - w * w;
+    const T B = rn - w * (rp - sc);
+    const T C = sc * (T(2) * rp - sc);
+    const T sq = Num<T>::sqrt0(fmax(B * B - A * C, T(0)));
+    const T dl = (B > T(0)) ? -Num<T>::div(C, B + sq) : Num<T>::div(-B + sq, A);
+    T th = thc - dl;
+    const bool ok = (j < 0) ? ((T)j + th <= T(1e-4))
+                            : (th >= T(-1e-4) && (th <= T(1.0001) || (j == S - 2 && th <= T(1) + T(kEndTol))));
     if (ok) {
-      th = fminf(fmaxf(th, 0.f), 1.f);
-      X = h0.x + th * dx;
-      V = h0.y + th * (h1.y - h0.y);
-      Ac = h0.z + th * (h1.z - h0.z);
+      th = fmin(fmax(th, T(0)), T(1));
+      X = x0 + th * dx;
+      V = v0 + th * (v1 - v0);
+      Ac = a0 + th * (a1 - a0);
       delta = dl;
       return 0;
     }
-    if (!(fabsf(th) < 1e8f)) return PC_ERR_NOCONV;
-    if (j == S - 2 && th > 1.f) return PC_ERR_HISTORY;
-    int st = __float2int_rd(th);
+    if (!(fabs(th) < T(1e8))) return PC_ERR_NOCONV;
+    if (j == S - 2 && th > T(1)) return PC_ERR_HISTORY;
+    int st = Num<T>::floor_int(th);
     j += st;
-    thc -= (float)st;
+    thc -= (T)st;
   }
   return PC_ERR_NOCONV;
 }
 
-template <int KIND>
-__device__ __forceinline__ void dipole_pair_mixed(float rx, float ry, float rz, float rn, float px, float py, float pz,
-                                                  float rp, float mup, float mum, float qs, float Xp, float Vp,
-                                                  float Ap, float dp, float Xm, float Vm, float Am, float dm,
-                                                  float rex, float *acc, uint8_t &mask) {
+// Both charges of a dipole from their centre's segment j (samples x0.. at j, x1.. at j+1, the
+// centre at fraction thc), the segment extended linearly when a charge's retarded time falls just
+// outside it.  Returns false when an offset exceeds kExtrap samples; the caller then solves each
+// charge with dip_charge_solve.
+// first/last: segment j is the first (0) or the last (S-2) of the history, whose ends may not be
+// extended (the history is static before sample 0 and unknown after the last sample).
+template <typename T>
+__device__ __forceinline__ bool dip_pair_states(T x0, T v0, T a0, T x1, T v1, T a1, T thc, T rn, T rp, T mup, T mum,
+                                                bool first, bool last, T &Xp, T &Vp, T &Ap, T &dp, T &Xm, T &Vm,
+                                                T &Am, T &dm) {
+  const T dx = x1 - x0, dv = v1 - v0, da = a1 - a0;
+  const T Xc = x0 + thc * dx;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const T smu = c == 0 ? mup : -mum;
+    const T sc = smu * Xc, w = smu * dx;
+    const T A = T(1) - w * w;
+    const T B = rn - w * (rp - sc);
+    const T C = sc * (T(2) * rp - sc);
+    const T sq = Num<T>::sqrt0(fmax(B * B - A * C, T(0)));
+    const T dl = (B > T(0)) ? -Num<T>::div(C, B + sq) : Num<T>::div(-B + sq, A);
+    const T th = thc - dl;
+    ok = ok && th >= (first ? T(0) : T(-kExtrap)) && th <= T(1) + (last ? T(kEndTol) : T(kExtrap));
+    const T X = x0 + th * dx, V = v0 + th * dv, Ac = a0 + th * da;
+    if (c == 0) {
+      Xp = X;
+      Vp = V;
+      Ap = Ac;
+      dp = dl;
+    } else {
+      Xm = X;
+      Vm = V;
+      Am = Ac;
+      dm = dl;
+    }
+  }
+  return ok;
+}
+
+// Net field q [F(x+) - F(x-)] of a dipole's two charges, added to acc[10] = (E, B, phi, A), in
+// units of k_e e / L^2 (E), k_e e / (L^2 c) (B), k_e e / L (phi), k_e e / (L c) (A), qs = q / e.
+// Per charge: E = C_a a + C_p p, B = (C_p / R) (rho x p), phi = 1/R_u, A = v p / R_u with
+// a = rho - s p, R_u = R - v a.p, G = 1 - v^2 + alpha a.p, C_a = G / R_u^3,
+// C_p = -R v G / R_u^3 - alpha R / R_u^2; the differences of C_a, C_p, C_p / R, 1/R_u and v/R_u
+// are formed from the differences of their inputs (dR = delta+ - delta-, ds, dv, dalpha).
+template <int KIND, typename T>
+__device__ __forceinline__ void dipole_pair(T rx, T ry, T rz, T rn, T px, T py, T pz, T rp, T mup, T mum, T qs, T Xp,
+                                            T Vp, T Ap, T dp, T Xm, T Vm, T Am, T dm, T rex, T *acc,
+                                            uint8_t &mask) {
   // charge 1 = positive (offset +mup X), charge 0 = negative (offset -mum X)
-  const float s1 = mup * Xp, s0 = -mum * Xm, ds = mup * Xp + mum * Xm;
-  const float v1 = mup * Vp, v0 = -mum * Vm, dv = mup * Vp + mum * Vm;
-  const float a1 = mup * Ap, a0 = -mum * Am, da = mup * Ap + mum * Am;
-  const float R0 = rn + dm, dR = dp - dm, R1 = R0 + dR;
+  const T s1 = mup * Xp, s0 = -mum * Xm, ds = mup * Xp + mum * Xm;
+  const T v1 = mup * Vp, v0 = -mum * Vm, dv = mup * Vp + mum * Vm;
+  const T a1 = mup * Ap, a0 = -mum * Am, da = mup * Ap + mum * Am;
+  const T R0 = rn + dm, dR = dp - dm, R1 = R0 + dR;
   if (R0 <= rex || R1 <= rex) {
     mask = 1;
     // one charge coincides with the point: add the other one alone
     const bool use1 = R1 > rex;
     if (!(R0 > rex) && !use1) return;
-    const float s = use1 ? s1 : s0, v = use1 ? v1 : v0, al = use1 ? a1 : a0, R = use1 ? R1 : R0;
-    const float sign = use1 ? qs : -qs;
-    const float ap = rp - s;
-    const float Ru = R - v * ap;
-    const float i1 = __frcp_rn(Ru);
-    const float i2 = i1 * i1, i3 = i2 * i1;
-    float G = 0.f, Q = 0.f;
-    if (KIND != PC_RADIATION) G += 1.f - v * v;
+    const T s = use1 ? s1 : s0, v = use1 ? v1 : v0, al = use1 ? a1 : a0, R = use1 ? R1 : R0;
+    const T sign = use1 ? qs : -qs;
+    const T ap = rp - s;
+    const T Ru = R - v * ap;
+    const T i1 = Num<T>::rcp(Ru);
+    const T i2 = i1 * i1, i3 = i2 * i1;
+    T G = T(0), Q = T(0);
+    if (KIND != PC_RADIATION) G += T(1) - v * v;
     if (KIND != PC_COULOMB) {
       G += al * ap;
       Q = al;
     }
-    const float Ca = G * i3;
-    const float Cp = -R * v * G * i3 - Q * R * i2;
-    const float Bc = -v * G * i3 - Q * i2;
-    const float ax_ = rx - s * px, ay_ = ry - s * py, az_ = rz - s * pz;
+    const T Ca = G * i3;
+    const T Cp = -R * v * G * i3 - Q * R * i2;
+    const T Bc = -v * G * i3 - Q * i2;
+    const T ax_ = rx - s * px, ay_ = ry - s * py, az_ = rz - s * pz;
     acc[0] += sign * (Ca * ax_ + Cp * px);
     acc[1] += sign * (Ca * ay_ + Cp * py);
     acc[2] += sign * (Ca * az_ + Cp * pz);
-    const float cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
+    const T cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
     acc[3] += sign * Bc * cx;
     acc[4] += sign * Bc * cy;
     acc[5] += sign * Bc * cz;
     acc[6] += sign * i1;
-    const float va = sign * v * i1;
+    const T va = sign * v * i1;
     acc[7] += va * px;
     acc[8] += va * py;
     acc[9] += va * pz;
     return;
   }
-  const float ap0 = rp - s0, ap1 = rp - s1, dap = -ds;
-  const float Ru0 = R0 - v0 * ap0;
-  const float dRu = dR - (dv * ap1 + v0 * dap);
-  const float Ru1 = Ru0 + dRu;
-  const float i0 = __frcp_rn(Ru0), i1 = __frcp_rn(Ru1);
-  const float di = -dRu * i0 * i1;
-  const float i02 = i0 * i0, i12 = i1 * i1;
-  const float i03 = i02 * i0, i13 = i12 * i1;
-  const float di2 = di * (i0 + i1);
-  const float di3 = di * (i12 + i1 * i0 + i02);
-  float G0 = 0.f, dG = 0.f;
+  const T ap0 = rp - s0, ap1 = rp - s1, dap = -ds;
+  const T Ru0 = R0 - v0 * ap0;
+  const T dRu = dR - (dv * ap1 + v0 * dap);
+  const T Ru1 = Ru0 + dRu;
+  const T i0 = Num<T>::rcp(Ru0), i1 = Num<T>::rcp(Ru1);
+  const T di = -dRu * i0 * i1;
+  const T i02 = i0 * i0, i12 = i1 * i1;
+  const T i03 = i02 * i0, i13 = i12 * i1;
+  const T di2 = di * (i0 + i1);
+  const T di3 = di * (i12 + i1 * i0 + i02);
+  T G0 = T(0), dG = T(0);
   if (KIND != PC_RADIATION) {
-    G0 += 1.f - v0 * v0;
+    G0 += T(1) - v0 * v0;
     dG += -dv * (v1 + v0);
   }
   if (KIND != PC_COULOMB) {
     G0 += a0 * ap0;
     dG += da * ap1 + a0 * dap;
   }
-  const float G1 = G0 + dG;
-  const float Ca0 = G0 * i03, Ca1 = G1 * i13;
-  const float dCa = dG * i13 + G0 * di3;
+  const T G1 = G0 + dG;
+  const T Ca0 = G0 * i03, Ca1 = G1 * i13;
+  const T dCa = dG * i13 + G0 * di3;
   // C_p = -R v G i^3 - alpha R i^2 ; B coefficient C_p / R = -v G i^3 - alpha i^2
-  const float P0 = R0 * v0 * G0;
-  const float dP = dR * v1 * G1 + R0 * (dv * G1 + v0 * dG);
-  float dCp = -(dP * i13 + P0 * di3);
-  const float dvG = dv * G1 + v0 * dG;
-  float dBc = -(dvG * i13 + v0 * G0 * di3);
+  const T P0 = R0 * v0 * G0;
+  const T dP = dR * v1 * G1 + R0 * (dv * G1 + v0 * dG);
+  T dCp = -(dP * i13 + P0 * di3);
+  const T dvG = dv * G1 + v0 * dG;
+  T dBc = -(dvG * i13 + v0 * G0 * di3);
   if (KIND != PC_COULOMB) {
-    const float Q0 = a0 * R0, dQ = da * R1 + a0 * dR;
+    const T Q0 = a0 * R0, dQ = da * R1 + a0 * dR;
     dCp -= dQ * i12 + Q0 * di2;
     dBc -= da * i12 + a0 * di2;
   }
-  const float ep = dCp - (Ca1 * s1 - Ca0 * s0);
+  const T ep = dCp - (Ca1 * s1 - Ca0 * s0);
   acc[0] += qs * (dCa * rx + ep * px);
   acc[1] += qs * (dCa * ry + ep * py);
   acc[2] += qs * (dCa * rz + ep * pz);
-  const float cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
+  const T cx = ry * pz - rz * py, cy = rz * px - rx * pz, cz = rx * py - ry * px;
   acc[3] += qs * dBc * cx;
   acc[4] += qs * dBc * cy;
   acc[5] += qs * dBc * cz;
   acc[6] += qs * di;
-  const float dA = qs * (dv * i1 + v0 * di);
+  const T dA = qs * (dv * i1 + v0 * di);
   acc[7] += dA * px;
   acc[8] += dA * py;
   acc[9] += dA * pz;
+}
+
+// Exact per-charge roots of both charges, kept out of line: it only runs for large charge offsets
+// (or near pairs), and inlining it would cost the common path registers.
+template <typename T, typename Hist>
+__device__ __noinline__ int dip_pair_exact(const Hist &H, int S, int kb, T xc, T rn, T rp, T mup, T mum, T &Xp, T &Vp,
+                                           T &Ap, T &dp, T &Xm, T &Vm, T &Am, T &dm) {
+  const int e1 = dip_charge_solve<T>(H, S, kb, xc, rn, rp, mup, Xp, Vp, Ap, dp);
+  const int e2 = dip_charge_solve<T>(H, S, kb, xc, rn, rp, -mum, Xm, Vm, Am, dm);
+  return e1 ? e1 : e2;
+}
+
+// Retarded states of both charges of a dipole: their centre's segment extended when possible,
+// exact per-charge roots otherwise (or when `exact`).  Returns 0 or an error code.
+template <typename T, typename Hist>
+__device__ __forceinline__ int dipole_states(const Hist &H, int S, int kb, T xc, T rn, T rp, T mup, T mum, bool exact,
+                                             T &Xp, T &Vp, T &Ap, T &dp, T &Xm, T &Vm, T &Am, T &dm) {
+  bool done = false;
+  if (!exact && fabs(xc) < T(1e8)) {
+    const int kc = Num<T>::floor_int(xc);
+    const T thc = xc - (T)kc;
+    const int j = kb + kc;
+    if (j >= 0 && j <= S - 2) {
+      T x0, v0, a0, x1, v1, a1;
+      H.get(j, x0, v0, a0);
+      H.get(j + 1, x1, v1, a1);
+      done = dip_pair_states<T>(x0, v0, a0, x1, v1, a1, thc, rn, rp, mup, mum, j == 0, j == S - 2, Xp, Vp, Ap, dp,
+                                Xm, Vm, Am, dm);
+    }
+  }
+  if (!done) return dip_pair_exact<T, Hist>(H, S, kb, xc, rn, rp, mup, mum, Xp, Vp, Ap, dp, Xm, Vm, Am, dm);
+  return 0;
+}
+
+// Cancellation ratio of a dipole's near field: its float32 evaluation works with terms of the size
+// of the moment at the retarded time and its rate and acceleration, (|ds| + R |dv| + R^2 |da|),
+// while the near field follows the moment at the present time, ds + R dv + R^2 da / 2, which
+// passes through zero.  The ratio bounds the loss of relative accuracy of the difference form.
+template <typename T>
+__device__ __forceinline__ T dipole_cancellation(T rn, T mup, T mum, T Xp, T Vp, T Ap, T Xm, T Vm, T Am) {
+  const T ds = mup * Xp + mum * Xm, dv = mup * Vp + mum * Vm, da = mup * Ap + mum * Am;
+  const T num = fabs(ds) + rn * fabs(dv) + rn * rn * fabs(da);
+  const T den = fabs(ds + rn * dv + T(0.5) * rn * rn * da);
+  return Num<T>::div(num, fmax(den, T(1e-30) * num + T(1e-38)));
+}
+
+// Net field of a dipole pair in T precision: retarded states then the difference form.
+template <int KIND, typename T, typename Hist>
+__device__ __forceinline__ int dipole_net(const Hist &H, int S, int kb, T xc, T rx, T ry, T rz, T rn, T px, T py, T pz,
+                                          T rp, T mup, T mum, T qs, T rex, bool exact, T *acc, uint8_t &mask) {
+  T Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
+  const int e = dipole_states<T, Hist>(H, S, kb, xc, rn, rp, mup, mum, exact, Xp, Vp, Ap, dp, Xm, Vm, Am, dm);
+  if (e) return e;
+  dipole_pair<KIND, T>(rx, ry, rz, rn, px, py, pz, rp, mup, mum, qs, Xp, Vp, Ap, dp, Xm, Vm, Am, dm, rex, acc, mask);
+  return 0;
 }
 
 }  // namespace pc

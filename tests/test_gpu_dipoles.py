@@ -115,3 +115,15 @@ def test_ke_fit_synthetic(ctx, gamma):
     assert abs(float(om[0]) / w - 1) < 1e-10
     assert abs(float(g[0]) - gamma) < 1e-6 * max(gamma, 2e7)
     assert abs(float(om[0]) - f["omega"]) / w < 1e-11
+
+
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+def test_cloud_grid_path(ctx, prec):
+    # 96 oscillators in a 150 nm cube (5 nm minimum spacing, random axes): above the size that runs
+    # as one CTA per configuration, so the run takes the grid-wide drive / RK4 launches
+    cfg = W.cfg5(N=96, n_steps=240, side=150e-9, min_spacing=5e-9, seed=7)
+    ref = oracle.dipoles_run(cfg)
+    assert ref["status"] == oracle.OK
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=prec, want_Ed=True)
+    for k in ("d", "d_dot", "Ed"):
+        assert hist_err(out[k][0], ref[k]) < HIST_TOL[prec], k

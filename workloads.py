@@ -255,9 +255,10 @@ def cfg4(N: int = 256, n_steps: int = 20000):
     return lo_batch(origins, axes, om, 1e-11, 1e-18, n_steps, 10000)
 
 
-def cfg5(N: int = 4096, n_steps: int = 20000, side: float = 600e-9, min_spacing: float = 5e-9):
+def cfg5(N: int = 4096, n_steps: int = 20000, side: float = 600e-9, min_spacing: float = 5e-9,
+         seed: int = SEED_CFG5):
     """N LOs at seeded random positions in a cube with a minimum spacing, random axes."""
-    rng = np.random.default_rng(SEED_CFG5)
+    rng = np.random.default_rng(seed)
     pts = np.empty((0, 3))
     cell = min_spacing
     grid = {}
