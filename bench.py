@@ -44,6 +44,17 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
 
+def kernel_source_hash():
+    """sha256 over the sources of the mixed field kernel (pc_fields.cu, pc_lw_f32.cuh, pc_lw_f64.cuh)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("pc_fields.cu", "pc_lw_f32.cuh", "pc_lw_f64.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_12437_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def rank_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
@@ -207,7 +218,7 @@ def main():
     if args.profile:
         if args.profile == "fields_mixed_small":
             pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=512,
-                               nv=2048, times=list(times[:2]), precision=pc.PC_MIXED)
+                               nv=2048, times=[float(times[5]), float(times[11])], precision=pc.PC_MIXED)
         elif args.profile == "fields_f64_small":
             pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=64,
                                nv=2048, times=list(times[:1]), precision=pc.PC_F64)
@@ -286,11 +297,15 @@ def main():
     fp32_fma, fp64_fma = pc.pc_alu_peaks(ctx)
     peak_tflops = 2.0 * N_SM * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     achieved = FLOPS_PER_PAIR * pairs_per_step / (kernel_ms * 1e-3) / 1e12
+    # DRAM bytes of one full launch, scaled from an ncu capture of a smaller case; valid only while
+    # the kernel sources are the ones that capture was taken of
     traffic = None
     prof = os.path.join(ROOT, "profiles", "fields_mixed_traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get("bytes_per_full_launch")
+            rec = json.load(open(prof))
+            if rec.get("source_sha256") == kernel_source_hash():
+                traffic = rec.get("bytes_per_full_launch")
         except Exception:
             traffic = None
 
@@ -337,19 +352,32 @@ def main():
                                           "peak": 2.0 * fp64_fma / 1e12, "unit": "TFLOP/s",
                                           "frac": FLOPS_PER_PAIR * f64_value / (2.0 * fp64_fma),
                                           "peak_basis": "measured float64 FMA rate (pc_alu_peaks)"}}
-        # batched self-consistent pair: 256 separations x 40 000 steps + fit
-        cfg, _ = W.cfg3(B=256, n_steps=40000)
-        lod = pc.lo_config_to_device(cfg, dev)
-        pc.pc_dipoles_run(ctx, lod, cfg.dt, 2000)
-        torch.cuda.synchronize()
-        e0.record(s)
-        pc.pc_dipoles_run(ctx, lod, cfg.dt, cfg.n_steps, fit=True, first_index=cfg.first_index)
-        e1.record(s)
-        torch.cuda.synchronize()
-        lo_ms = e0.elapsed_time(e1)
-        line["dipole_steps"] = {"value": cfg.B * cfg.N * cfg.n_steps / (lo_ms * 1e-3), "unit": "dipole-steps/s",
-                                "workload": "256 separations (1 nm .. 1 um) x 2 oscillators x 40000 RK4 steps "
-                                            "+ KE fit, float64", "ms": lo_ms}
+        # oscillator runs: dipole-steps per second (float64 RK4 state; driving field per precision)
+        def lo_time(cfg, n_steps, prec, fit):
+            lod = pc.lo_config_to_device(cfg, dev)
+            pc.pc_dipoles_run(ctx, lod, cfg.dt, min(n_steps, 64), precision=prec)
+            torch.cuda.synchronize()
+            e0.record(s)
+            pc.pc_dipoles_run(ctx, lod, cfg.dt, n_steps, precision=prec, fit=fit, first_index=cfg.first_index)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            return {"value": cfg.B * cfg.N * n_steps / (ms * 1e-3), "unit": "dipole-steps/s", "ms": ms}
+
+        cfg3, _ = W.cfg3(B=256, n_steps=40000)
+        ds = {}
+        for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
+            r = lo_time(cfg3, cfg3.n_steps, prec, True)
+            r["workload"] = ("batched pairs: 256 separations (1 nm .. 1 um) x 2 oscillators x 40000 RK4 steps, "
+                             "one launch, + KE fit of all 512 dipoles")
+            ds["pairs_" + name] = r
+        cfg5 = W.cfg5()
+        n5 = 1600
+        r = lo_time(cfg5, n5, pc.PC_MIXED, False)
+        r["workload"] = (f"cloud: 4096 oscillators in a 600 nm cube, first {n5} of the 20000 RK4 steps "
+                         "(bounded sample; 100 causal blocks of 16 steps)")
+        ds["cloud_mixed"] = r
+        line["dipole_steps"] = ds
         if rank == 0:
             import oracle
 

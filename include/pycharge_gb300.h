@@ -210,6 +210,34 @@ pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sources *dp, c
                             const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,
                             void *stream);
 
+/* Gradient outputs of pc_dipoles_adjoint (device arrays, overwritten). */
+typedef struct {
+  double *origin; /* [B][N][3] dL/d origin (1/m units of L) */
+  double *omega0; /* [B][N]    dL/d omega0 */
+  double *d0;     /* [B][N]    dL/d d0 (initial dipole moment, C m) */
+} pc_dipole_grads;
+
+/*
+ * pc_dipoles_adjoint -- reverse-mode gradient of L = sum_{b,i} w_{b,i} E_{b,i}(T) through the whole
+ * run of pc_dipoles_run, E the dipole energy of Eq. dipoleE at the last step T = n_steps dt and
+ * w = dL_dEnergyFinal (device [B][N]).  The paper has no adjoint; it differentiates the same
+ * discrete computation as pc_dipoles_run with precision PC_F64 and ed_mode 0: RK4 of
+ * Eq. LO_equation, the Lienard-Wiechert driving field (Eqs. E, r_1, r_2) at the retarded time of
+ * Eq. ret_t on the piecewise-linear history.  The retarded time is differentiated through its
+ * defining equation (implicit-function theorem), the history interpolation exactly; a kink of the
+ * loss where a retarded time crosses a sample is not smoothed.
+ * The call first repeats the forward run, keeping the whole history and the half-step fields in
+ * the context (8 doubles per dipole and step), then sweeps the causal blocks in reverse.
+ *   dp, dt, n_steps, opts   as for pc_dipoles_run; opts->precision must be PC_F64 and
+ *                           opts->ed_mode 0 (PC_ERR_ARG otherwise); the fit is not run
+ *   g                       gradients (device)
+ * Errors: those of pc_dipoles_run; PC_ERR_ARG also when the source windows of one causal block
+ * exceed shared memory (more than about 8 500 steps between the nearest and the farthest
+ * dipole of a configuration); PC_ERR_NOCONV when a retarded time leaves its window.
+ */
+pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
+                             const double *dL_dEnergyFinal, const pc_dipole_grads *g, void *stream);
+
 /*
  * pc_alu_peaks -- measures this GPU's float32 and float64 fused-multiply-add throughput (FMA/s)
  * with dependent-chain kernels; used as roofline denominators.  Writes fp32_fma_per_s,

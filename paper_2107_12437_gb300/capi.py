@@ -62,6 +62,10 @@ class PcRunOut(ctypes.Structure):
                 ("omega", _vp)]
 
 
+class PcDipoleGrads(ctypes.Structure):
+    _fields_ = [("origin", _vp), ("omega0", _vp), ("d0", _vp)]
+
+
 # every entry point of include/pycharge_gb300.h with its argument types
 SIGNATURES = {
     "pc_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
@@ -74,6 +78,8 @@ SIGNATURES = {
                                        ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                       ctypes.POINTER(PcRunOut), _vp]),
+    "pc_dipoles_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
+                                          _vp, ctypes.POINTER(PcDipoleGrads), _vp]),
     "pc_ke_fit": (ctypes.c_int, [_vp, _vp, _i32, _i64, _f64, _i64, _vp, _vp, _vp, _vp, _vp]),
     "pc_alu_peaks": (ctypes.c_int, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _vp]),
     "pc_fields_noalloc": (ctypes.c_int, [ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
@@ -275,6 +281,48 @@ def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_
                                 ctypes.byref(ro), _stream(stream))
     _check(st, "pc_dipoles_run")
     return out
+
+
+def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, stream=None):
+    """pc_dipoles_adjoint: gradients of sum w E(T) (w = dL_dEnergyFinal, [B][N] CUDA float64) with
+    respect to the origins, omega0 and d0; returns (g_origin [B][N][3], g_omega0 [B][N], g_d0 [B][N])."""
+    B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
+    dev = dp.origin.device
+    w = dL_dEnergyFinal.to(device=dev, dtype=torch.float64).contiguous()
+    g_origin = torch.empty((B, N, 3), dtype=torch.float64, device=dev)
+    g_omega0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
+                  m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=PC_F64)
+    g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
+    st = ctx.lib.pc_dipoles_adjoint(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
+                                    _ptr(w), ctypes.byref(g), _stream(stream))
+    _check(st, "pc_dipoles_adjoint")
+    return g_origin, g_omega0, g_d0
+
+
+class FinalEnergy(torch.autograd.Function):
+    """E(T) [B][N] of the float64 oscillator run as a differentiable function of (origin, omega0, d0);
+    the backward pass is pc_dipoles_adjoint.  Other configuration tensors are held fixed."""
+
+    @staticmethod
+    def forward(fctx, origin, omega0, d0, rest, ctx, dt, n_steps, v_max):
+        dp = SimpleNamespace(origin=origin.contiguous(), omega0=omega0.contiguous(), d0=d0.contiguous(),
+                             axis=rest.axis, q=rest.q, m1=rest.m1, m2=rest.m2)
+        out = pc_dipoles_run(ctx, dp, dt, n_steps, v_max=v_max, precision=PC_F64, want_energy=True)
+        fctx.dp, fctx.pc, fctx.dt, fctx.n_steps, fctx.v_max = dp, ctx, dt, n_steps, v_max
+        return out["energy"][:, :, -1].clone()
+
+    @staticmethod
+    def backward(fctx, grad_E):
+        go, gw, gd = pc_dipoles_adjoint(fctx.pc, fctx.dp, fctx.dt, fctx.n_steps, grad_E, v_max=fctx.v_max)
+        return go, gw, gd, None, None, None, None, None
+
+
+def final_energy(ctx, dp, dt, n_steps, v_max=0.0):
+    """Differentiable E(T) [B][N] (Eq. dipoleE at the last step) of pc_dipoles_run in float64."""
+    return FinalEnergy.apply(dp.origin, dp.omega0, dp.d0, dp, ctx, float(dt), int(n_steps), float(v_max))
 
 
 def pc_ke_fit(ctx, ke, dt, first_index, stream=None):

@@ -51,6 +51,7 @@ extern "C" pc_status pc_ctx_destroy(pc_ctx *ctx) {
   ctx->hist_f32.release();
   ctx->charge_ref.release();
   ctx->run_scratch.release();
+  ctx->adj_scratch.release();
   delete ctx;
   return PC_OK;
 }

@@ -14,6 +14,8 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "pc_internal.cuh"
@@ -39,8 +41,9 @@ struct RunArgs {
   int *status;
   // tables built once per run (mixed path): per-dipole float records, per-pair centre delays
   float *dipf;        // [B][N][kDipF]: origin/L as hi+lo (6), axis (3), m2/(m1+m2), m1/(m1+m2), q/e
-  int2 *delay;        // [B][N][N]: |R_i - R_j| / (c dt) = x + y * 2^-30, x integer, y the fraction
+  int2 *delay;        // [B][N][N]: |R_i - R_j| / (c dt) = x + y, x integer, y the fraction (float bits)
   int *kblock;        // [B] causal block length per configuration
+  double *Ehalf;      // [B][N][n_steps] E_d at t_n + dt/2 (kept for the adjoint), or null
 };
 
 constexpr int kDipF = 12;
@@ -123,10 +126,10 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   const float rn = sqrtf(rx * rx + ry * ry + rz * rz);
   const float px = fj[6], py = fj[7], pz = fj[8];
   const float rp = rx * px + ry * py + rz * pz;
-  const HistF32 H{a.H32 + bj * (size_t)(a.n_steps + 1)};
+  const HistF32RW H{a.H32 + bj * (size_t)(a.n_steps + 1)};
   float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   uint8_t mk = 0;
-  const int e = dipole_net<PC_TOTAL, float, HistF32>(H, nvalid, kb, xc, rx, ry, rz, rn, px, py, pz, rp, fj[9], fj[10],
+  const int e = dipole_net<PC_TOTAL, float, HistF32RW>(H, nvalid, kb, xc, rx, ry, rz, rn, px, py, pz, rp, fj[9], fj[10],
                                                      fj[11], 0.f, false, acc, mk);
   if (e) {
     *err = (e == PC_ERR_HISTORY) ? PC_ERR_CAUSALITY : e;
@@ -144,6 +147,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   const int slots = 32 / nst;
   const int s = lane % nst, m = lane / nst;
   const double stage = ns > 0 ? 0.5 * (s + 1) : 0.0;
+  const float stage_f = (float)stage;  // converted once: conversions issue to the float64 unit
   double accd = 0.0;
   float accf = 0.f, comp = 0.f;
   if (m < slots) {
@@ -152,9 +156,10 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       if (MIXED) {
         // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
         const int2 dl = a.delay[(size_t)bidx(a, b, i) * a.N + j];
-        const float xs = (float)stage - (float)dl.y * 0x1p-30f;
-        const int fl = __float2int_rd(xs);
-        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - (float)fl, (int)n0 + 1, err);
+        const float xs = stage_f - __int_as_float(dl.y);
+        float flf;
+        const int fl = Num<float>::floor_int(xs, flf);
+        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, (int)n0 + 1, err);
         // Kahan sum over sources
         const float y = v - comp;
         const float t = accf + y;
@@ -275,7 +280,7 @@ __global__ void lo_tables_kernel(const RunArgs a) {
     if (i != j) rmin = fmin(rmin, r);
     const double x = r / L;
     const double fl = floor(x);
-    if (a.delay) a.delay[(size_t)bi * N + j] = make_int2((int)fl, (int)((x - fl) * 0x1p30));
+    if (a.delay) a.delay[(size_t)bi * N + j] = make_int2((int)fl, __float_as_int((float)(x - fl)));
   }
   s_rmin[threadIdx.x] = rmin;
   s_smax[threadIdx.x] = smax;
@@ -372,6 +377,7 @@ __device__ void rk4_block(const RunArgs &a, int b, int i, int64_t n0, int kb, in
       a.H32[bi * S + n + 1] =
           make_float4((float)(yn0 / (q * L)), (float)(yn1 / (q * kC)), (float)(ydd * dt / (q * kC)), 0.f);
     if (a.Ed) a.Ed[bi * S + n + 1] = e4;
+    if (a.Ehalf) a.Ehalf[bi * a.n_steps + n] = Es[2 * k + 1];
     if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
     if (fabs(yn1) * vfac > a.v_max) {
       set_status(a.status, PC_ERR_VELOCITY);
@@ -437,27 +443,35 @@ struct FitArgs {
   int *status;
 };
 
-// residual/Jacobian pass.  mode 0: cost only; mode 1: cost, J^T J (10), J^T r (4)
+// residual/Jacobian pass.  mode 0: cost only; mode 1: cost, J^T J (10), J^T r (4).
+// Each thread takes a contiguous chunk of samples; sin, cos and exp of the model are evaluated
+// exactly at the chunk start and advanced by rotation and multiplication by the one-sample factors
+// (float64; the chunk is ~1e2 samples, so the recurrence adds ~1e-14 relative).
 __device__ void fit_pass(const double *y, int64_t n, double dt, double T, double Ag, double wg, const double x[4],
                          int mode, double out[15]) {
   for (int k = 0; k < 15; ++k) out[k] = 0.0;
   const double A = Ag * x[0], g = x[1] / T, w = wg + x[2] / T, ph = x[3];
   const int64_t chunk = (n + kFitThreads - 1) / kFitThreads;
   const int64_t i0 = (int64_t)threadIdx.x * chunk, i1 = min(n, i0 + chunk);
+  if (i0 >= i1) return;
+  double s, c, cw, sw;
+  sincos(w * ((double)i0 * dt) + ph, &s, &c);
+  sincos(w * dt, &sw, &cw);
+  double env = exp(-g * ((double)i0 * dt));
+  const double e1 = exp(-g * dt);
+  const double iA = 1.0 / Ag, iT = 1.0 / T;
   for (int64_t i = i0; i < i1; ++i) {
     const double tau = (double)i * dt;
-    double s, c;
-    sincos(w * tau + ph, &s, &c);
-    const double env = exp(-g * tau);
-    const double model = A * env * s * s;
-    const double r = (model - y[i]) / Ag;
+    const double ss = s * s;
+    const double model = A * env * ss;
+    const double r = (model - y[i]) * iA;
     out[0] += r * r;
     if (mode) {
       double J[4];
-      J[0] = env * s * s;
-      J[1] = -tau * A * env * s * s / T / Ag;
-      J[2] = 2.0 * A * env * s * c * tau / T / Ag;
-      J[3] = 2.0 * A * env * s * c / Ag;
+      J[0] = env * ss;
+      J[1] = -tau * model * iT * iA;
+      J[3] = 2.0 * A * env * s * c * iA;
+      J[2] = J[3] * tau * iT;
       int idx = 1;
 #pragma unroll
       for (int p = 0; p < 4; ++p)
@@ -466,6 +480,11 @@ __device__ void fit_pass(const double *y, int64_t n, double dt, double T, double
 #pragma unroll
       for (int p = 0; p < 4; ++p) out[11 + p] += J[p] * r;
     }
+    // advance the phase by w dt and the envelope by exp(-g dt)
+    const double s1 = s * cw + c * sw;
+    c = c * cw - s * sw;
+    s = s1;
+    env *= e1;
   }
 }
 
@@ -702,8 +721,10 @@ extern "C" pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t
   return pc::end_call(ctx, st);
 }
 
-extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
-                                    const pc_run_opts *opts, const pc_run_out *out, void *stream) {
+namespace pc {
+// Forward run (Algorithm 1); Ehalf (or null) receives E_d at the half steps for the adjoint.
+static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
+                          const pc_run_out *out, double *Ehalf, cudaStream_t st, int *k_out = nullptr) {
   if (!ctx || !dp || !opts || !out) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0) || n_steps < 0) return PC_ERR_ARG;
   if (!dp->origin || !dp->axis || !dp->q || !dp->m1 || !dp->m2 || !dp->omega0 || !dp->d0) return PC_ERR_ARG;
@@ -712,10 +733,6 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
   if (opts->precision != PC_F64 && opts->precision != PC_MIXED) return PC_ERR_ARG;
   if (opts->fit && (!out->gamma || !out->omega || opts->first_index < 0 || n_steps + 1 - opts->first_index < 8))
     return PC_ERR_ARG;
-  pc::DeviceGuard g(ctx->device);
-  cudaStream_t st = (cudaStream_t)stream;
-  pc_status bs = pc::begin_call(ctx, st);
-  if (bs != PC_OK) return bs;
   const int64_t S = n_steps + 1;
   const size_t nbn = (size_t)dp->B * dp->N;
   const bool mixed = opts->precision == PC_MIXED;
@@ -756,9 +773,19 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
   a.dipf = (float *)(scr + es_bytes + h_bytes);
   a.delay = mixed ? (int2 *)(scr + es_bytes + h_bytes + f_bytes) : nullptr;
   a.kblock = (int *)(scr + es_bytes + h_bytes + f_bytes + dl_bytes);
+  a.Ehalf = Ehalf;
   a.status = ctx->d_status;
   char *ke_base = scr + es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes;
   pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
+  if (k_out) {
+    // the shortest causal block over the batch, for the caller
+    std::vector<int> kb(dp->B);
+    if (cudaMemcpyAsync(kb.data(), a.kblock, dp->B * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return PC_ERR_CUDA;
+    *k_out = pc::kMaxBlock;
+    for (int v : kb) *k_out = std::min(*k_out, v);
+  }
   if (dp->N <= pc::kSmallN) {
     // small configurations: one persistent CTA each, the time loop inside
     if (mixed) pc::lo_run_kernel<true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
@@ -799,5 +826,430 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
                                   nullptr, st);
     if (ls != PC_OK) return ls;
   }
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+}  // namespace pc
+
+extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
+                                    const pc_run_opts *opts, const pc_run_out *out, void *stream) {
+  if (!ctx) return PC_ERR_ARG;
+  pc::DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, opts, out, nullptr, st);
+  if (rs != PC_OK) return rs;
+  return pc::end_call(ctx, st);
+}
+
+// ================================================================================================
+// Adjoint of the oscillator run (float64): gradients of L = sum_i w_i E_i(T) (Eq. dipoleE at the
+// final step) with respect to the dipole origins, omega0 and the initial moments.
+//
+// The forward run keeps its whole history (it is the trajectory store the retarded fields read)
+// and its half-step driving fields, so the reverse sweep recomputes nothing but the pair geometry.
+// Reverse sweep over the causal blocks, last block first:
+//   (1) per receiver, the reverse of its K RK4 steps: the adjoint of its state, of omega0 and of
+//       the 2K stage driving fields of the block; the adjoint of each history sample (d, d', d'')
+//       is complete by then, since only stages of later blocks read it;
+//   (2) per source dipole (one CTA), the reverse of the retarded Lienard-Wiechert field of its two
+//       charges at every receiver and stage of the block: adjoints of the source's history samples
+//       (accumulated in a shared-memory window), of both origins, and of the retarded time itself
+//       through the implicit-function theorem on c^2 (t - t')^2 = |r - r_s(t')|^2 (Eq. ret_t).
+// ================================================================================================
+namespace pc {
+
+struct AdjArgs {
+  RunArgs f;           // forward arguments; f.d/dd/ddd/Ed/Ehalf hold the forward history
+  const double *wE;    // [B][N] dL / dE_i(T)
+  double *mu;          // [B][N][S][3] adjoints of the history samples (d, d', d'')
+  double *lam;         // [B][N][2] adjoint of the state (d, d') at the current step
+  double *carry;       // [B][N] adjoint of E_d at the current block start (from its first RK4 stage)
+  double *Ebar;        // [B][N][2*kMaxBlock+1] adjoints of the block's stage fields
+  double *w0bar;       // [B][N]
+  double *tau;         // [B][N][2] smallest and largest delay (steps) from a source to its receivers
+  double *g_origin, *g_omega0, *g_d0;
+  int64_t margin;      // samples of slack around the retarded window (charge offsets)
+};
+
+__global__ void adj_init_kernel(const AdjArgs A) {
+  const RunArgs &a = A.f;
+  const int64_t S = a.n_steps + 1;
+  const double L = kC * a.dt;
+  for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < (int64_t)a.B * a.N;
+       bi += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(bi / a.N), i = (int)(bi % a.N);
+    const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
+    const double m = m1 * m2 / (m1 + m2);
+    const double dN = a.d[bi * S + a.n_steps], vN = a.dd[bi * S + a.n_steps];
+    const double w = A.wE[bi];
+    // E = m (w0^2 d^2 + d'^2) / (2 q^2)
+    A.lam[2 * bi] = w * m * w0 * w0 * dN / (q * q);
+    A.lam[2 * bi + 1] = w * m * vN / (q * q);
+    A.w0bar[bi] = w * m * w0 * dN * dN / (q * q);
+    A.carry[bi] = 0.0;
+    for (int c = 0; c < 3; ++c) A.g_origin[3 * bi + c] = 0.0;
+    double tmin = 1e300, tmax = 0.0;
+    for (int jj = 0; jj < a.N; ++jj) {
+      if (jj == i) continue;
+      const size_t bj = bidx(a, b, jj);
+      const double dx = a.origin[3 * bi] - a.origin[3 * bj], dy = a.origin[3 * bi + 1] - a.origin[3 * bj + 1],
+                   dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
+      const double t = sqrt(dx * dx + dy * dy + dz * dz) / L;
+      tmin = fmin(tmin, t);
+      tmax = fmax(tmax, t);
+    }
+    A.tau[2 * bi] = tmin;
+    A.tau[2 * bi + 1] = tmax;
+  }
+}
+
+// (1) reverse RK4 of steps n0 + kb - 1 .. n0 for one receiver; writes the stage-field adjoints of
+// the block to Ebar[1 .. 2 kb] (stage s at time n0 + s/2).
+__global__ void adj_rk4_kernel(const AdjArgs A, int64_t n0, int kb) {
+  const RunArgs &a = A.f;
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= (int64_t)a.B * a.N) return;
+  const int64_t S = a.n_steps + 1;
+  const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
+  const double m = m1 * m2 / (m1 + m2);
+  const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
+  const double qm = q * q / m;
+  const double dt = a.dt, h = 0.5 * dt;
+  double l0 = A.lam[2 * bi], l1 = A.lam[2 * bi + 1];
+  double carry = A.carry[bi];
+  double w0b = 0.0;
+  double *Eb = A.Ebar + bi * (2 * kMaxBlock + 1);
+  for (int k = kb - 1; k >= 0; --k) {
+    const int64_t n = n0 + k;
+    // history sample n+1 = (d, d', d'') with d'' = qm E(n+1) - g0 d' - w0^2 d
+    const double *mu1 = A.mu + (bi * S + n + 1) * 3;
+    const double yN0 = a.d[bi * S + n + 1], yN1 = a.dd[bi * S + n + 1];
+    l0 += mu1[0] - w0 * w0 * mu1[2];
+    l1 += mu1[1] - g0 * mu1[2];
+    double e4b = carry + qm * mu1[2];
+    double g0b = -yN1 * mu1[2], w2b = -yN0 * mu1[2];
+    // forward stages of step n
+    const double y0 = a.d[bi * S + n], y1 = a.dd[bi * S + n];
+    const double e1 = a.Ed[bi * S + n], e2 = a.Ehalf[bi * a.n_steps + n], e4 = a.Ed[bi * S + n + 1];
+    const double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
+    const double y0b = y0 + h * k1a, y1b = y1 + h * k1b;
+    const double k2a = y1b, k2b = -g0 * y1b - w0 * w0 * y0b + qm * e2;
+    const double y0c = y0 + h * k2a, y1c = y1 + h * k2b;
+    const double k3a = y1c, k3b = -g0 * y1c - w0 * w0 * y0c + qm * e2;
+    const double y0d = y0 + dt * k3a, y1d = y1 + dt * k3b;
+    (void)e4;
+    // reverse of y_{n+1} = y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4)
+    double y0bar = l0, y1bar = l1;
+    double k1ab = dt / 6.0 * l0, k2ab = dt / 3.0 * l0, k3ab = dt / 3.0 * l0, k4ab = dt / 6.0 * l0;
+    double k1bb = dt / 6.0 * l1, k2bb = dt / 3.0 * l1, k3bb = dt / 3.0 * l1, k4bb = dt / 6.0 * l1;
+    double e2b = 0.0, e1b = 0.0;
+    // k4 = f(y_d, e4)
+    double y1db = k4ab - g0 * k4bb, y0db = -w0 * w0 * k4bb;
+    e4b += qm * k4bb;
+    g0b += -y1d * k4bb;
+    w2b += -y0d * k4bb;
+    y0bar += y0db;
+    k3ab += dt * y0db;
+    y1bar += y1db;
+    k3bb += dt * y1db;
+    // k3 = f(y_c, e2)
+    double y1cb = k3ab - g0 * k3bb, y0cb = -w0 * w0 * k3bb;
+    e2b += qm * k3bb;
+    g0b += -y1c * k3bb;
+    w2b += -y0c * k3bb;
+    y0bar += y0cb;
+    k2ab += h * y0cb;
+    y1bar += y1cb;
+    k2bb += h * y1cb;
+    // k2 = f(y_b, e2)
+    double y1bb = k2ab - g0 * k2bb, y0bb = -w0 * w0 * k2bb;
+    e2b += qm * k2bb;
+    g0b += -y1b * k2bb;
+    w2b += -y0b * k2bb;
+    y0bar += y0bb;
+    k1ab += h * y0bb;
+    y1bar += y1bb;
+    k1bb += h * y1bb;
+    // k1 = f(y_n, e1)
+    y1bar += k1ab - g0 * k1bb;
+    y0bar += -w0 * w0 * k1bb;
+    e1b += qm * k1bb;
+    g0b += -y1 * k1bb;
+    w2b += -y0 * k1bb;
+    // g0 = q^2 w0^2 / (6 pi eps0 c^3 m), w2 = w0^2
+    w0b += g0b * 2.0 * g0 / w0 + w2b * 2.0 * w0;
+    Eb[2 * k + 2] = e4b;
+    Eb[2 * k + 1] = e2b;
+    carry = e1b;
+    l0 = y0bar;
+    l1 = y1bar;
+  }
+  A.lam[2 * bi] = l0;
+  A.lam[2 * bi + 1] = l1;
+  A.carry[bi] = carry;
+  A.w0bar[bi] += w0b;
+}
+
+// Reverse of the driving-field contribution F = p_i . E of dipole j's two charges at receiver i
+// and time u (steps, history 0..nv).  eb = dL/dF.  Adds to the history adjoints of j (window
+// win[0..W) for samples wlo..), to the receiver's and the source's origin adjoints.
+__device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int64_t nv, double eb, double *win,
+                            int64_t wlo, int W, double Rib[3], double Rjb[3]) {
+  const RunArgs &a = A.f;
+  const int64_t S = a.n_steps + 1;
+  const double cdt = kC * a.dt;
+  const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+  const double *Ri = a.origin + 3 * bi;
+  const double *pi = a.axis + 3 * bi;
+  TrajF64 tr;
+  tr.dipole = true;
+  tr.d = a.d + bj * S;
+  tr.dd = a.dd + bj * S;
+  tr.ddd = a.ddd + bj * S;
+  double pj[3];
+  for (int c = 0; c < 3; ++c) {
+    tr.R[c] = a.origin[3 * bj + c];
+    tr.ax[c] = a.axis[3 * bj + c];
+    pj[c] = tr.ax[c];
+  }
+  const double q = a.q[bj], m1 = a.m1[bj], m2 = a.m2[bj];
+  double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
+  const int64_t kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
+  const double Eb[3] = {eb * pi[0], eb * pi[1], eb * pi[2]};
+  for (int sg = 0; sg < 2; ++sg) {
+    const double w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+    tr.w = w;
+    const double qc = sg == 0 ? q : -q;
+    int64_t k = -1;
+    double th = 0.0;
+    bool stat = true;
+    if (nv > 0) {
+      const int e = solve_f64(tr, nv + 1, 1, Ri, u, cdt, kg, &k, &th);
+      if (e) return e;
+      stat = (k < 0 || (k == 0 && th == 0.0));
+    }
+    double p[3], vel[3] = {0, 0, 0}, acc[3] = {0, 0, 0};
+    double Dd = 0, Dv = 0, Da = 0;
+    if (stat) {
+      tr.p(0, p);
+    } else {
+      double p1[3], v1[3], a1[3];
+      tr.p(k, p);
+      tr.p(k + 1, p1);
+      tr.va(k, vel, acc);
+      tr.va(k + 1, v1, a1);
+      Dd = tr.d[k + 1] - tr.d[k];
+      Dv = tr.dd[k + 1] - tr.dd[k];
+      Da = tr.ddd[k + 1] - tr.ddd[k];
+      for (int c = 0; c < 3; ++c) {
+        p[c] += th * (p1[c] - p[c]);
+        vel[c] += th * (v1[c] - vel[c]);
+        acc[c] += th * (a1[c] - acc[c]);
+      }
+    }
+    const double av[3] = {Ri[0] - p[0], Ri[1] - p[1], Ri[2] - p[2]};
+    double ab[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, accb[3] = {0, 0, 0};
+    lw_E_f64_rev(qc, av, vel, acc, Eb, ab, vb, accb);
+    // a = r - p: receiver origin gets ab, the source position gets -ab
+    for (int c = 0; c < 3; ++c) {
+      Rib[c] += ab[c];
+      Rjb[c] -= ab[c];
+    }
+    const double pb_p = -dot3(ab, pj);  // adjoint of the charge offset along the axis
+    if (stat) {
+      // position R_j + w d[0] p_j: only d[0] (window slot of sample 0)
+      if (wlo != 0) return PC_ERR_NOCONV;
+      atomicAdd(&win[0], w * pb_p);
+      continue;
+    }
+    if (k < wlo || k + 1 >= wlo + W) return PC_ERR_NOCONV;
+    const double Db = w * pb_p, Vb = w * dot3(vb, pj), Ab = w * dot3(accb, pj);
+    double *w0p = win + 3 * (k - wlo), *w1p = w0p + 3;
+    // the fraction th depends on the inputs through G(th) = cdt^2 (u - k - th)^2 - |r - p(th)|^2 = 0
+    const double thb = Db * Dd + Vb * Dv + Ab * Da;
+    const double ap = dot3(av, pj);
+    const double Gth = -2.0 * cdt * cdt * (u - (double)k - th) + 2.0 * w * Dd * ap;
+    const double sfac = -thb / Gth;
+    for (int c = 0; c < 3; ++c) {
+      Rib[c] += sfac * (-2.0 * av[c]);
+      Rjb[c] += sfac * (2.0 * av[c]);
+    }
+    const double dbar = Db + sfac * 2.0 * ap * w;
+    atomicAdd(&w0p[0], (1.0 - th) * dbar);
+    atomicAdd(&w0p[1], (1.0 - th) * Vb);
+    atomicAdd(&w0p[2], (1.0 - th) * Ab);
+    atomicAdd(&w1p[0], th * dbar);
+    atomicAdd(&w1p[1], th * Vb);
+    atomicAdd(&w1p[2], th * Ab);
+  }
+  return 0;
+}
+
+// (2) one CTA per (source j, configuration b): reverse of the block's stage fields at every
+// receiver.  ns == 0 handles the field at t = 0 with the adjoint left in `carry`.  The source
+// samples the block's retarded times reach lie in [n0 + 1/2 - tau_max - margin,
+// n0 + ns/2 - tau_min + margin]; their adjoints are gathered in a shared-memory window.
+__global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t n0, int ns, int wmax) {
+  extern __shared__ double win[];  // [wmax][3]
+  __shared__ double s_rj[3][128];
+  const RunArgs &a = A.f;
+  const int j = blockIdx.x, b = blockIdx.y;
+  const size_t bj = bidx(a, b, j);
+  const int64_t S = a.n_steps + 1;
+  int64_t wlo = 0, whi = 0;
+  if (ns > 0) {
+    const double lo = (double)n0 + 0.5 - A.tau[2 * bj + 1] - (double)A.margin;
+    const double hi = (double)n0 + 0.5 * ns - A.tau[2 * bj] + (double)A.margin + 1.0;
+    wlo = (int64_t)fmax(0.0, floor(lo));
+    whi = (int64_t)fmin((double)n0, ceil(hi));
+    if (whi < wlo) whi = wlo;
+  }
+  const int W = (int)(whi - wlo + 1);
+  if (W > wmax) {
+    if (threadIdx.x == 0) set_status(a.status, PC_ERR_NOCONV);
+    return;
+  }
+  for (int t = threadIdx.x; t < 3 * W; t += blockDim.x) win[t] = 0.0;
+  __syncthreads();
+  double Rjb[3] = {0, 0, 0};
+  int err = 0;
+  for (int i = threadIdx.x; i < a.N && !err; i += blockDim.x) {
+    if (i == j) continue;
+    const size_t bi = bidx(a, b, i);
+    double Rib[3] = {0, 0, 0};
+    const int nst = ns > 0 ? ns : 1;
+    for (int s = 1; s <= nst && !err; ++s) {
+      const double eb = ns > 0 ? A.Ebar[bi * (2 * kMaxBlock + 1) + s] : A.carry[bi];
+      if (eb == 0.0) continue;
+      const double u = ns > 0 ? (double)n0 + 0.5 * s : 0.0;
+      err = pair_rev_f64(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
+    }
+    for (int c = 0; c < 3; ++c)
+      if (Rib[c] != 0.0) atomicAdd(&A.g_origin[3 * bi + c], Rib[c]);
+  }
+  if (err) set_status(a.status, err);
+  for (int c = 0; c < 3; ++c) s_rj[c][threadIdx.x] = Rjb[c];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += s_rj[threadIdx.x][k];
+    atomicAdd(&A.g_origin[3 * bj + threadIdx.x], t);
+  }
+  // the window into the source's history adjoints (this CTA owns source j during the launch)
+  for (int t = threadIdx.x; t < 3 * W; t += blockDim.x) A.mu[(bj * S + wlo) * 3 + t] += win[t];
+}
+
+__global__ void adj_final_kernel(const AdjArgs A) {
+  const RunArgs &a = A.f;
+  const int64_t S = a.n_steps + 1;
+  for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < (int64_t)a.B * a.N;
+       bi += (int64_t)gridDim.x * blockDim.x) {
+    // y_0 = (d0, 0) and the history before and at t = 0 sits at d0
+    A.g_d0[bi] = A.lam[2 * bi] + A.mu[bi * S * 3];
+    A.g_omega0[bi] = A.w0bar[bi];
+  }
+}
+
+}  // namespace pc
+
+extern "C" pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
+                                        const pc_run_opts *opts, const double *dL_dEnergyFinal,
+                                        const pc_dipole_grads *g, void *stream) {
+  if (!ctx || !dp || !opts || !dL_dEnergyFinal || !g || !g->origin || !g->omega0 || !g->d0) return PC_ERR_ARG;
+  if (opts->ed_mode != 0 || opts->precision != PC_F64 || n_steps < 1) return PC_ERR_ARG;
+  if (dp->B < 1 || dp->N < 1 || !(dt > 0.0)) return PC_ERR_ARG;
+  pc::DeviceGuard gd(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  const int64_t S = n_steps + 1;
+  const size_t nbn = (size_t)dp->B * dp->N;
+  auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const size_t hist = al(nbn * S * sizeof(double));
+  const size_t half = al(nbn * n_steps * sizeof(double));
+  const size_t mu_b = al(nbn * S * 3 * sizeof(double));
+  const size_t small = al(nbn * (2 + 1 + (2 * pc::kMaxBlock + 1) + 1 + 2) * sizeof(double));
+  if (ctx->adj_scratch.reserve(4 * hist + half + mu_b + small) != cudaSuccess) return PC_ERR_CUDA;
+  char *p = (char *)ctx->adj_scratch.ptr;
+  double *d = (double *)p, *dd = (double *)(p + hist), *ddd = (double *)(p + 2 * hist), *Ed = (double *)(p + 3 * hist);
+  double *Eh = (double *)(p + 4 * hist);
+  double *mu = (double *)(p + 4 * hist + half);
+  double *sm = (double *)(p + 4 * hist + half + mu_b);
+  // forward run with the full history and the half-step fields
+  pc_run_opts fo = *opts;
+  fo.fit = 0;
+  pc_run_out fw;
+  memset(&fw, 0, sizeof(fw));
+  fw.d = d;
+  fw.d_dot = dd;
+  fw.d_ddot = ddd;
+  fw.Ed = Ed;
+  int K = 1;
+  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K);
+  if (rs != PC_OK) return rs;
+  pc::AdjArgs A;
+  memset(&A, 0, sizeof(A));
+  pc::RunArgs &a = A.f;
+  a.B = dp->B;
+  a.N = dp->N;
+  a.origin = dp->origin;
+  a.axis = dp->axis;
+  a.q = dp->q;
+  a.m1 = dp->m1;
+  a.m2 = dp->m2;
+  a.omega0 = dp->omega0;
+  a.d0 = dp->d0;
+  a.dt = dt;
+  a.n_steps = n_steps;
+  a.d = d;
+  a.dd = dd;
+  a.ddd = ddd;
+  a.Ed = Ed;
+  a.Ehalf = Eh;
+  a.status = ctx->d_status;
+  A.wE = dL_dEnergyFinal;
+  A.mu = mu;
+  A.lam = sm;
+  A.carry = sm + 2 * nbn;
+  A.Ebar = sm + 3 * nbn;
+  A.w0bar = sm + (3 + 2 * pc::kMaxBlock + 1) * nbn;
+  A.tau = A.w0bar + nbn;
+  A.g_origin = g->origin;
+  A.g_omega0 = g->omega0;
+  A.g_d0 = g->d0;
+  if (cudaMemsetAsync(mu, 0, nbn * S * 3 * sizeof(double), st) != cudaSuccess) return PC_ERR_CUDA;
+  const unsigned rgrid = (unsigned)((nbn + 127) / 128);
+  pc::adj_init_kernel<<<rgrid, 128, 0, st>>>(A);
+  // margin for charge offsets: three times the largest initial |r_dip|, in samples, plus one
+  std::vector<double> hq(nbn), hd0(nbn), htau(2 * nbn);
+  if (cudaMemcpyAsync(hq.data(), dp->q, nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(hd0.data(), dp->d0, nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(htau.data(), A.tau, 2 * nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PC_ERR_CUDA;
+  double smax = 0.0, spread = 0.0;
+  for (size_t k = 0; k < nbn; ++k) {
+    smax = std::max(smax, std::fabs(hd0[k] / hq[k]));
+    if (htau[2 * k] <= htau[2 * k + 1]) spread = std::max(spread, htau[2 * k + 1] - htau[2 * k]);
+  }
+  A.margin = (int64_t)std::ceil(3.0 * smax / (pc::kC * dt)) + 2;
+  const int wmax = (int)std::max(1.0, std::min<double>(std::ceil(spread) + K + 2.0 * A.margin + 6.0, (double)S));
+  const size_t smem = (size_t)wmax * 3 * sizeof(double);
+  if (smem > 200 * 1024) return PC_ERR_ARG;  // source windows beyond shared memory
+  if (cudaFuncSetAttribute(pc::adj_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return PC_ERR_CUDA;
+  const dim3 fgrid((unsigned)dp->N, (unsigned)dp->B);
+  const int64_t nblocks = (n_steps + K - 1) / K;
+  for (int64_t bk = nblocks - 1; bk >= 0; --bk) {
+    const int64_t n0 = bk * K;
+    const int kb = (int)std::min((int64_t)K, n_steps - n0);
+    pc::adj_rk4_kernel<<<rgrid, 128, 0, st>>>(A, n0, kb);
+    pc::adj_field_kernel<<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
+  }
+  // the driving field at t = 0 (static configuration) and the final gradients
+  pc::adj_field_kernel<<<fgrid, 128, smem, st>>>(A, 0, 0, wmax);
+  pc::adj_final_kernel<<<rgrid, 128, 0, st>>>(A);
   return pc::end_call(ctx, st);
 }

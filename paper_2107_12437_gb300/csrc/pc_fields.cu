@@ -12,7 +12,7 @@
 //            are evaluated together in difference form: the net field q[E(x+) - E(x-)] is built
 //            from differences of the scalar coefficients of the Lienard-Wiechert field that carry
 //            no cancellation, so the s/R loss of the +-q pair (s = charge separation) does not
-//            appear.  Contributions are summed in groups of eight and the group sums are added
+//            appear.  Contributions are summed in groups of sixteen and the group sums are added
 //            with Kahan compensation.
 #include <stdio.h>
 
@@ -353,7 +353,7 @@ __device__ __forceinline__ void charge_mixed(float ax, float ay, float az, float
 }
 
 // Kahan-compensated running sums of the ten outputs; each thread's sums live in shared memory,
-// strided by the block size (they are touched once per group of eight sources).
+// strided by the block size (they are touched once per group of sixteen sources).
 struct KahanSmem {
   float *sum, *comp;  // [10][kMixThreads], thread column tid
   __device__ __forceinline__ void add(const float *part) const {
@@ -370,15 +370,15 @@ struct KahanSmem {
 };
 
 template <int KIND, bool LIST>
-__global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
+__global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
   __shared__ double s_anchor[3];
   __shared__ float s_kahan[2][10][kMixThreads];
   __shared__ float4 s_geo[kChunk];   // rho_a (x,y,z), |rho_a|
   __shared__ float4 s_geo_lo[kChunk]; // low parts of rho_a and |rho_a| (list mode)
   __shared__ float4 s_ax[kChunk];    // axis (x,y,z), q/e
-  __shared__ float2 s_mu[kChunk];    // m2/(m1+m2), m1/(m1+m2)
-  __shared__ int s_ka[kChunk];
-  __shared__ float s_fa[kChunk];
+  __shared__ float4 s_mix[kChunk];   // m2/(m1+m2), m1/(m1+m2), fraction and integer part of the
+                                     // retarded sample of the anchor (integer as bits)
+  __shared__ const float4 *s_hist[kChunk];
 
   const int tid = threadIdx.x;
   const int f = blockIdx.y;
@@ -450,9 +450,9 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
         s_ax[tid] = make_float4((float)s.axis[3 * j], (float)s.axis[3 * j + 1], (float)s.axis[3 * j + 2],
                                 (float)(s.qd[j] / kE));
         const double m1 = s.m1[j], m2 = s.m2[j];
-        s_mu[tid] = make_float2((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)));
-        s_ka[tid] = (int)kaf;
-        s_fa[tid] = (float)(x - kaf);
+        s_mix[tid] = make_float4((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)), (float)(x - kaf),
+                                 __int_as_float((int)kaf));
+        s_hist[tid] = L.Hd + (size_t)j * s.Sd;
       }
       __syncthreads();
       if (!active || err) continue;
@@ -463,18 +463,20 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
       for (int jj = 0; jj < nch; ++jj) {
         const float4 g = s_geo[jj];
         const float4 ax = s_ax[jj];
-        const float2 mu = s_mu[jj];
+        const float4 mx = s_mix[jj];
+        const float2 mu = make_float2(mx.x, mx.y);
+        const float fa = mx.z;
         const float rx = g.x + drx, ry = g.y + dry, rz = g.z + drz;
         const float rho2 = rx * rx + ry * ry + rz * rz;
         const float irn = rsqrtf(rho2);
         const float rn = rho2 > 0.f ? rho2 * irn : 0.f;
         // retarded time of the dipole centre, in samples: kb + xc with |xc| small
-        int kb = s_ka[jj];
+        int kb = __float_as_int(mx.w);
         float xc;
         if (!LIST) {
           // compact tile: |rho| - |rho_a| from the tile offset without cancellation
           const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
-          xc = s_fa[jj] - corr;
+          xc = fa - corr;
         } else {
           // points of a list tile may lie far apart: |rho| - |rho_a| in float-float, integer part
           // moved into kb so that the fraction keeps its precision
@@ -483,13 +485,14 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
                    pz = ff_add({g.z, gl.z}, {drz, drlz});
           const ff n2 = ff_add(ff_add(ff_mul(px, px), ff_mul(py, py)), ff_mul(pz, pz));
           const ff dn = ff_add(ff_sqrt(n2), {-g.w, -gl.w});
-          const ff x = ff_add({s_fa[jj], 0.f}, {-dn.hi, -dn.lo});
-          const int fl = __float2int_rd(x.hi);
+          const ff x = ff_add({fa, 0.f}, {-dn.hi, -dn.lo});
+          float flf;
+          const int fl = Num<float>::floor_int(x.hi, flf);
           kb += fl;
-          xc = (x.hi - (float)fl) + x.lo;
+          xc = (x.hi - flf) + x.lo;
         }
         const float rp = rx * ax.x + ry * ax.y + rz * ax.z;
-        const HistF32 H{L.Hd + (size_t)(base + jj) * s.Sd};
+        const HistF32 H{s_hist[jj]};
         float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
         const int e = dipole_states<float, HistF32>(H, Sd32, kb, xc, rn, rp, mu.x, mu.y, false, Xp, Vp, Ap, dp, Xm, Vm,
                                                     Am, dm);
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
         }
         dipole_pair<KIND, float>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm, Am, dm,
                                  rex, part, mask);
-        if ((jj & 7) == 7) {
+        if ((jj & 15) == 15) {
           acc.add(part);
 #pragma unroll
           for (int i = 0; i < 10; ++i) part[i] = 0.f;
@@ -542,8 +545,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
         const double kaf = floor(x);
         s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
         s_ax[tid] = make_float4(0.f, 0.f, 0.f, (float)(s.q[c] / kE));
-        s_ka[tid] = (int)kaf;
-        s_fa[tid] = (float)(x - kaf);
+        s_mix[tid] = make_float4(0.f, 0.f, (float)(x - kaf), __int_as_float((int)kaf));
       }
       __syncthreads();
       if (!active || err) continue;
@@ -558,24 +560,26 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
         const float irn = rho2 > 0.f ? rsqrtf(rho2) : 0.f;
         const float rn = rho2 * irn;
         const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
-        const float xc = s_fa[cc] - corr;
-        if (!(fabsf(xc) < 1e8f)) {
+        const float xc = s_mix[cc].z - corr;
+        if (!(fabsf(xc) < 1e6f)) {
           err = PC_ERR_NOCONV;
           break;
         }
         const float4 *H = L.Hc + (size_t)(base + cc) * s.S * 3;
         const int S = (int)s.S;
         // first-order estimate of the charge's delay offset: -rho_hat . o(center time)
-        const int kc = __float2int_rd(xc);
-        float thc = xc - (float)kc;
-        int j = s_ka[cc] + kc;
+        float kcf;
+        const int kc = Num<float>::floor_int(xc, kcf);
+        float thc = xc - kcf;
+        int j = __float_as_int(s_mix[cc].w) + kc;
         {
           int jc = j < 0 ? 0 : (j > S - 1 ? S - 1 : j);
           float4 o = __ldg(H + 3 * jc);
           float d0 = -(rx * o.x + ry * o.y + rz * o.z) * irn;
-          int st = __float2int_rd(thc - d0);
+          float stf;
+          int st = Num<float>::floor_int(thc - d0, stf);
           j += st;
-          thc -= (float)st;
+          thc -= stf;
         }
         float ox = 0, oy = 0, oz = 0, vx = 0, vy = 0, vz = 0, gx = 0, gy = 0, gz = 0;
         bool done = false;
@@ -623,14 +627,15 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
             }
             done = true;
           } else {
-            if (!(fabsf(th) < 1e8f)) break;
+            if (!(fabsf(th) < 1e6f)) break;
             if ((j == S - 2 && th > 1.f) || (j == 0 && th < 0.f && !s.static_before)) {
               err = PC_ERR_HISTORY;
               break;
             }
-            const int st = __float2int_rd(th);
+            float stf;
+            const int st = Num<float>::floor_int(th, stf);
             j += st;
-            thc -= (float)st;
+            thc -= stf;
           }
         }
         if (!done) {
@@ -646,7 +651,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) fields_mixed_kernel(const Laun
         for (int i = 0; i < 6; ++i) part[i] += sE * c10[i];
 #pragma unroll
         for (int i = 6; i < 10; ++i) part[i] += sP * c10[i];
-        if ((cc & 7) == 7) {
+        if ((cc & 15) == 15) {
           acc.add(part);
 #pragma unroll
           for (int i = 0; i < 10; ++i) part[i] = 0.f;

@@ -49,6 +49,7 @@ struct pc_ctx {
   pc::Buf hist_f32;          // float32 mirrors of source histories (mixed path)
   pc::Buf charge_ref;        // per-charge float64 reference positions
   pc::Buf run_scratch;       // LO-run scratch (stage fields, fit work)
+  pc::Buf adj_scratch;       // adjoint: forward history, history adjoints
   int num_sms = 0;
 };
 

@@ -22,7 +22,25 @@ struct Num<float> {
   static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float sqrt0(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
-  static __device__ __forceinline__ int floor_int(float x) { return __float2int_rd(x); }
+  // floor(x) as an integer and as a float, for |x| < 2^22, without conversion instructions (on this
+  // GPU float<->int conversions issue to the float64 unit): adding 1.5 * 2^23 rounds x to an integer
+  // held in the low mantissa bits.
+  static __device__ __forceinline__ int floor_int(float x, float &fl) {
+    const float magic = 12582912.f;
+    const float y = x + magic;
+    float r = y - magic;
+    int i = __float_as_int(y) - 0x4B400000;
+    if (r > x) {
+      r -= 1.f;
+      i -= 1;
+    }
+    fl = r;
+    return i;
+  }
+  static __device__ __forceinline__ int floor_int(float x) {
+    float fl;
+    return floor_int(x, fl);
+  }
 };
 template <>
 struct Num<double> {
@@ -30,20 +48,37 @@ struct Num<double> {
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double sqrt0(double x) { return x > 0.0 ? sqrt(x) : 0.0; }
   static __device__ __forceinline__ int floor_int(double x) { return (int)floor(x); }
+  static __device__ __forceinline__ int floor_int(double x, double &fl) {
+    fl = floor(x);
+    return (int)fl;
+  }
 };
 
 // Dipole history samples (X = d/(qL), V = d'/(qc), A = d'' dt/(qc)); before the first sample the
 // dipole rests at X[0].  Sample indices are 32-bit: conversions to 64-bit integers run on the
 // float64 unit, the narrowest pipe of this GPU.
-struct HistF32 {
+// READ_ONLY: the history does not change while the kernel runs, so loads may use the read-only
+// data cache; the oscillator run appends to the history it reads and uses coherent loads.
+template <bool READ_ONLY>
+struct HistF32T {
   const float4 *H;
+  __device__ __forceinline__ float4 load(int j) const { return READ_ONLY ? __ldg(H + j) : H[j]; }
   __device__ __forceinline__ void get(int j, float &x, float &v, float &a) const {
-    float4 h = __ldg(H + (j >= 0 ? j : 0));
+    float4 h = load(j >= 0 ? j : 0);
     x = h.x;
     v = j >= 0 ? h.y : 0.f;
     a = j >= 0 ? h.z : 0.f;
   }
+  // sample j >= 0 known to exist
+  __device__ __forceinline__ void get_in(int j, float &x, float &v, float &a) const {
+    float4 h = load(j);
+    x = h.x;
+    v = h.y;
+    a = h.z;
+  }
 };
+using HistF32 = HistF32T<true>;
+using HistF32RW = HistF32T<false>;
 struct HistF64 {
   const double *d, *dd, *ddd;
   double sx, sv, sa;  // 1/(qL), 1/(qc), dt/(qc)
@@ -53,6 +88,7 @@ struct HistF64 {
     v = j >= 0 ? dd[k] * sv : 0.0;
     a = j >= 0 ? ddd[k] * sa : 0.0;
   }
+  __device__ __forceinline__ void get_in(int j, double &x, double &v, double &a) const { get(j, x, v, a); }
 };
 
 // Retarded state of one dipole charge at offset smu*X along the axis from the dipole centre, found
@@ -63,23 +99,26 @@ struct HistF64 {
 template <typename T, typename Hist>
 __device__ __forceinline__ int dip_charge_solve(const Hist &H, int S, int kb, T xc, T rn, T rp, T smu, T &X, T &V,
                                                 T &Ac, T &delta) {
-  if (!(fabs(xc) < T(1e8))) return PC_ERR_NOCONV;
-  int kc = Num<T>::floor_int(xc);
-  T thc = xc - (T)kc;
+  if (!(fabs(xc) < T(1e6))) return PC_ERR_NOCONV;
+  T fl;
+  int kc = Num<T>::floor_int(xc, fl);
+  T thc = xc - fl;
   int j = kb + kc;
   // first-order estimate of the charge's delay offset picks its segment
   {
     T hx, hv, ha;
     H.get(j < S ? j : S - 1, hx, hv, ha);
     T d0 = (rn > T(0)) ? -smu * hx * Num<T>::div(rp, rn) : T(0);
-    int st = Num<T>::floor_int(thc - d0);
+    T fs;
+    int st = Num<T>::floor_int(thc - d0, fs);
     j += st;
-    thc -= (T)st;
+    thc -= fs;
   }
   for (int it = 0; it < 6; ++it) {
     if (j > S - 2) {
       // past the end: solve on the last segment extended; a root up to kEndTol past the last
       // sample is clamped to it, a later one is a history error
+      if (j - (S - 2) > 1000) return PC_ERR_HISTORY;
       thc += (T)(j - (S - 2));
       j = S - 2;
     }
@@ -111,11 +150,12 @@ __device__ __forceinline__ int dip_charge_solve(const Hist &H, int S, int kb, T 
       delta = dl;
       return 0;
     }
-    if (!(fabs(th) < T(1e8))) return PC_ERR_NOCONV;
+    if (!(fabs(th) < T(1e6))) return PC_ERR_NOCONV;
     if (j == S - 2 && th > T(1)) return PC_ERR_HISTORY;
-    int st = Num<T>::floor_int(th);
+    T fs;
+    int st = Num<T>::floor_int(th, fs);
     j += st;
-    thc -= (T)st;
+    thc -= fs;
   }
   return PC_ERR_NOCONV;
 }
@@ -274,14 +314,15 @@ template <typename T, typename Hist>
 __device__ __forceinline__ int dipole_states(const Hist &H, int S, int kb, T xc, T rn, T rp, T mup, T mum, bool exact,
                                              T &Xp, T &Vp, T &Ap, T &dp, T &Xm, T &Vm, T &Am, T &dm) {
   bool done = false;
-  if (!exact && fabs(xc) < T(1e8)) {
-    const int kc = Num<T>::floor_int(xc);
-    const T thc = xc - (T)kc;
+  if (!exact && fabs(xc) < T(1e6)) {
+    T fl;
+    const int kc = Num<T>::floor_int(xc, fl);
+    const T thc = xc - fl;
     const int j = kb + kc;
     if (j >= 0 && j <= S - 2) {
       T x0, v0, a0, x1, v1, a1;
-      H.get(j, x0, v0, a0);
-      H.get(j + 1, x1, v1, a1);
+      H.get_in(j, x0, v0, a0);
+      H.get_in(j + 1, x1, v1, a1);
       done = dip_pair_states<T>(x0, v0, a0, x1, v1, a1, thc, rn, rp, mup, mum, j == 0, j == S - 2, Xp, Vp, Ap, dp,
                                 Xm, Vm, Am, dm);
     }

@@ -26,6 +26,7 @@ EPS0 = 8.8541878128e-12
 SEED_CFG2 = 2107
 SEED_CFG4 = 12437
 SEED_CFG5 = 210712437
+SEED_ADJ = 1243721
 
 
 @dataclasses.dataclass
@@ -289,3 +290,30 @@ def cfg5(N: int = 4096, n_steps: int = 20000, side: float = 600e-9, min_spacing:
     pts = np.array(out)[None]
     axes = unit_vectors(rng, N)[None]
     return lo_batch(pts, axes, 2 * math.pi * 200e12, 1e-11, 1e-18, n_steps, 10000)
+
+
+def adjoint_cluster(B: int = 2, N: int = 3, n_steps: int = 3000, spacing: float = 6e-9, seed: int = SEED_ADJ,
+                    margin: float = 0.08) -> LOConfig:
+    """B clusters of N LOs (random axes, omega0 = 2 pi 200 THz +-1%, r_dip0 = 10 pm) for gradient
+    checks.  Pair distances are drawn so that no retarded time sits within `margin` steps of a
+    history sample at the whole- or half-step stage times: a centre-to-centre delay tau (steps)
+    with frac(tau) and frac(tau + 1/2) both farther than `margin` from an integer.  The charges
+    move by at most r_dip0/(c dt) = 0.033 steps, so finite-difference steps of the inputs do not
+    cross the kinks of the piecewise-linear history."""
+    rng = np.random.default_rng(seed)
+    dt = 1e-18
+    L = C * dt
+    origins = np.zeros((B, N, 3))
+    for b in range(B):
+        while True:
+            pts = rng.uniform(0.0, spacing * N ** (1 / 3) * 1.5, size=(N, 3))
+            dist = np.linalg.norm(pts[:, None] - pts[None], axis=-1)[np.triu_indices(N, 1)]
+            if N > 1 and dist.min() < spacing:
+                continue
+            f = np.mod(dist / L, 0.5)
+            if np.all((f > margin) & (f < 0.5 - margin)):
+                break
+        origins[b] = pts
+    axes = unit_vectors(rng, B * N).reshape(B, N, 3)
+    om = 2 * math.pi * 200e12 * (1.0 + rng.uniform(-0.01, 0.01, size=(B, N)))
+    return lo_batch(origins, axes, om, 1e-11, dt, n_steps, 0)
