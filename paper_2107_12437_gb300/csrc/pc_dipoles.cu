@@ -21,6 +21,7 @@
 #include "pc_internal.cuh"
 #include "pc_lw_f32.cuh"
 #include "pc_lw_f64.cuh"
+#include "pc_adjoint.cuh"
 
 namespace pc {
 
