@@ -311,6 +311,27 @@ __device__ __noinline__ int near_dipole_f64(const Sources &s, int j, const doubl
   return 0;
 }
 
+// A dipole pair the inner loop could not take on its fast path (a charge offset beyond the shared
+// segment, a point close to a charge, or an ill-conditioned near field): exact float32 roots of
+// both charges, then the float32 difference form, or the float64 near path where the near field
+// cancels.  Kept out of line so that the inner loop makes no calls.
+template <int KIND>
+__device__ __noinline__ int slow_dipole(const Sources &s, int j, const float4 *hist, int S, int kb, float xc, float rx,
+                                        float ry, float rz, float rn, float4 ax, float mup, float mum, float rex,
+                                        const double r[3], double u, double Ld, double r_excl, float *part,
+                                        uint8_t *mask) {
+  const float rp = rx * ax.x + ry * ax.y + rz * ax.z;
+  const HistF32 H{hist};
+  float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
+  const int e = dipole_states<float, HistF32>(H, S, kb, xc, rn, rp, mup, mum, true, Xp, Vp, Ap, dp, Xm, Vm, Am, dm);
+  if (e) return e;
+  if (rn < kNearL && dipole_cancellation<float>(rn, mup, mum, Xp, Vp, Ap, Xm, Vm, Am) > kCancel)
+    return near_dipole_f64<KIND>(s, j, r, u, Ld, r_excl, part, mask);
+  dipole_pair<KIND, float>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mup, mum, ax.w, Xp, Vp, Ap, dp, Xm, Vm, Am, dm, rex,
+                           part, *mask);
+  return 0;
+}
+
 // Generic charge in float32 (no pairing): Griffiths form with c = 1.
 template <int KIND>
 __device__ __forceinline__ void charge_mixed(float ax, float ay, float az, float vx, float vy, float vz, float gx,
@@ -459,7 +480,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       float part[10];
 #pragma unroll
       for (int i = 0; i < 10; ++i) part[i] = 0.f;
-      unsigned long long near_mask = 0ull;
+      unsigned long long slow_mask = 0ull;
       for (int jj = 0; jj < nch; ++jj) {
         const float4 g = s_geo[jj];
         const float4 ax = s_ax[jj];
@@ -492,16 +513,27 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
           xc = (x.hi - flf) + x.lo;
         }
         const float rp = rx * ax.x + ry * ax.y + rz * ax.z;
-        const HistF32 H{s_hist[jj]};
+        // fast path: both charges on the segment of their centre's retarded time
         float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
-        const int e = dipole_states<float, HistF32>(H, Sd32, kb, xc, rn, rp, mu.x, mu.y, false, Xp, Vp, Ap, dp, Xm, Vm,
-                                                    Am, dm);
-        if (e) {
-          err = e;
-          break;
+        bool fast = false;
+        if (fabsf(xc) < 1e6f) {
+          float fl;
+          const int kc = Num<float>::floor_int(xc, fl);
+          const int j = kb + kc;
+          if (j >= 0 && j <= Sd32 - 2) {
+            const HistF32 H{s_hist[jj]};
+            float x0, v0, a0, x1, v1, a1;
+            H.get_in(j, x0, v0, a0);
+            H.get_in(j + 1, x1, v1, a1);
+            fast = dip_pair_states<float>(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, mu.x, mu.y, j == 0, j == Sd32 - 2,
+                                          Xp, Vp, Ap, dp, Xm, Vm, Am, dm);
+          }
         }
-        if (rn < kNearL && dipole_cancellation<float>(rn, mu.x, mu.y, Xp, Vp, Ap, Xm, Vm, Am) > kCancel) {
-          near_mask |= 1ull << jj;  // ill-conditioned in float32: evaluated in float64 after this chunk
+        // near fields that cancel in float32 also leave the fast path
+        if (fast && rn < kNearL && dipole_cancellation<float>(rn, mu.x, mu.y, Xp, Vp, Ap, Xm, Vm, Am) > kCancel)
+          fast = false;
+        if (!fast) {
+          slow_mask |= 1ull << jj;
           continue;
         }
         dipole_pair<KIND, float>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm, Am, dm,
@@ -513,13 +545,37 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
         }
       }
       acc.add(part);
-      // near pairs of this chunk, in float64
-      while (near_mask && !err) {
-        const int jj = __ffsll((long long)near_mask) - 1;
-        near_mask &= near_mask - 1ull;
+      // the pairs of this chunk that left the fast path
+      while (slow_mask && !err) {
+        const int jj = __ffsll((long long)slow_mask) - 1;
+        slow_mask &= slow_mask - 1ull;
 #pragma unroll
         for (int i = 0; i < 10; ++i) part[i] = 0.f;
-        const int e = near_dipole_f64<KIND>(s, base + jj, r, u, Ld, L.r_excl, part, &mask);
+        const float4 g = s_geo[jj];
+        const float4 ax = s_ax[jj];
+        const float4 mx = s_mix[jj];
+        const float rx = g.x + drx, ry = g.y + dry, rz = g.z + drz;
+        const float rho2 = rx * rx + ry * ry + rz * rz;
+        const float rn = rho2 > 0.f ? rho2 * rsqrtf(rho2) : 0.f;
+        int kb = __float_as_int(mx.w);
+        float xc;
+        if (!LIST) {
+          const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
+          xc = mx.z - corr;
+        } else {
+          const float4 gl = s_geo_lo[jj];
+          const ff px = ff_add({g.x, gl.x}, {drx, drlx}), py = ff_add({g.y, gl.y}, {dry, drly}),
+                   pz = ff_add({g.z, gl.z}, {drz, drlz});
+          const ff n2 = ff_add(ff_add(ff_mul(px, px), ff_mul(py, py)), ff_mul(pz, pz));
+          const ff dn = ff_add(ff_sqrt(n2), {-g.w, -gl.w});
+          const ff x = ff_add({mx.z, 0.f}, {-dn.hi, -dn.lo});
+          float flf;
+          const int fl = Num<float>::floor_int(x.hi, flf);
+          kb += fl;
+          xc = (x.hi - flf) + x.lo;
+        }
+        const int e = slow_dipole<KIND>(s, base + jj, s_hist[jj], Sd32, kb, xc, rx, ry, rz, rn, ax, mx.x, mx.y, rex,
+                                        r, u, Ld, L.r_excl, part, &mask);
         if (e) err = e;
         acc.add(part);
       }

@@ -180,8 +180,20 @@ __device__ __forceinline__ bool dip_pair_states(T x0, T v0, T a0, T x1, T v1, T 
     const T A = T(1) - w * w;
     const T B = rn - w * (rp - sc);
     const T C = sc * (T(2) * rp - sc);
-    const T sq = Num<T>::sqrt0(fmax(B * B - A * C, T(0)));
-    const T dl = (B > T(0)) ? -Num<T>::div(C, B + sq) : Num<T>::div(-B + sq, A);
+    T dl;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // away from the charge |A C| << B^2 and the smaller root -C / (B + sqrt(B^2 - A C)) is
+      // -(C / 2B) (1 + eps/4 + eps^2/8 + O(eps^3)), eps = A C / B^2: below 1e-7 relative for
+      // |eps| < 1e-2; other pairs take the exact per-charge solve
+      const T r = Num<T>::rcp(B);
+      const T h = T(0.5) * C * r;
+      const T eps = A * C * r * r;
+      dl = -(h + h * eps * (T(0.25) + T(0.125) * eps));
+      ok = ok && B > T(0) && fabs(eps) < T(1e-2);
+    } else {
+      const T sq = Num<T>::sqrt0(fmax(B * B - A * C, T(0)));
+      dl = (B > T(0)) ? -Num<T>::div(C, B + sq) : Num<T>::div(-B + sq, A);
+    }
     const T th = thc - dl;
     ok = ok && th >= (first ? T(0) : T(-kExtrap)) && th <= T(1) + (last ? T(kEndTol) : T(kExtrap));
     const T X = x0 + th * dx, V = v0 + th * dv, Ac = a0 + th * da;
