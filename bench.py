@@ -367,10 +367,43 @@ def main():
         cfg3, _ = W.cfg3(B=256, n_steps=40000)
         ds = {}
         for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
-            r = lo_time(cfg3, cfg3.n_steps, prec, True)
+            r = lo_time(cfg3, cfg3.n_steps, prec, False)
             r["workload"] = ("batched pairs: 256 separations (1 nm .. 1 um) x 2 oscillators x 40000 RK4 steps, "
-                             "one launch, + KE fit of all 512 dipoles")
+                             "one launch")
             ds["pairs_" + name] = r
+        # the Eq. KE fit of all 512 kinetic-energy series of that run (30 001 samples each)
+        lod = pc.lo_config_to_device(cfg3, dev)
+        out3 = pc.pc_dipoles_run(ctx, lod, cfg3.dt, cfg3.n_steps, precision=pc.PC_MIXED)
+        m3 = lod.m1 * lod.m2 / (lod.m1 + lod.m2)
+        ke = (m3[..., None] * out3["d_dot"] ** 2 / (2 * lod.q[..., None] ** 2)).reshape(cfg3.B * cfg3.N, -1)
+        pc.pc_ke_fit(ctx, ke, cfg3.dt, cfg3.first_index)
+        torch.cuda.synchronize()
+        e0.record(s)
+        pc.pc_ke_fit(ctx, ke, cfg3.dt, cfg3.first_index)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ds["ke_fit"] = {"value": cfg3.B * cfg3.N / (e0.elapsed_time(e1) * 1e-3), "unit": "series/s",
+                        "ms": e0.elapsed_time(e1), "workload": "512 kinetic-energy series x 30001 samples"}
+        del out3, ke
+        # ring of 256 oscillators (200 nm radius, omega0 +-1 %), 20 000 steps: forward in both
+        # precisions, and the float64 adjoint of sum E(T) (forward repeated inside, then reverse)
+        cfg4 = W.cfg4()
+        for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
+            r = lo_time(cfg4, cfg4.n_steps, prec, False)
+            r["workload"] = "ring: 256 oscillators on a 200 nm ring x 20000 RK4 steps"
+            ds["ring_" + name] = r
+        lod4 = pc.lo_config_to_device(cfg4, dev)
+        w4 = torch.ones((1, cfg4.N), dtype=torch.float64, device=dev)
+        pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, 64, w4)
+        torch.cuda.synchronize()
+        e0.record(s)
+        pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, cfg4.n_steps, w4)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms4 = e0.elapsed_time(e1)
+        ds["ring_adjoint_f64"] = {"value": cfg4.N * cfg4.n_steps / (ms4 * 1e-3), "unit": "dipole-steps/s", "ms": ms4,
+                                  "workload": "gradients of sum E(T) w.r.t. 768 origin coordinates, 256 omega0, "
+                                              "256 d0 of the 256-oscillator ring, 20000 steps (forward + reverse)"}
         cfg5 = W.cfg5()
         n5 = 1600
         r = lo_time(cfg5, n5, pc.PC_MIXED, False)

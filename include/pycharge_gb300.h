@@ -239,6 +239,27 @@ pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64
                              const double *dL_dEnergyFinal, const pc_dipole_grads *g, void *stream);
 
 /*
+ * pc_dipoles_rates_adjoint -- reverse-mode gradient of L = sum_{b,i} (dL_dgamma gamma + dL_domega omega)
+ * where gamma and omega are the Eq. KE fit (Sec. 2.4) of each dipole's kinetic energy
+ * m d'^2/(2 q^2) from first_index on, after the float64 run of pc_dipoles_run (ed_mode 0).  The
+ * paper has no adjoint.  The fit is differentiated through its optimum by the implicit-function
+ * theorem (full Hessian of the least-squares cost, residual term included), which turns
+ * (dL/dgamma, dL/domega) into a cotangent on every d' sample of the fit window; the run is then
+ * reversed as in pc_dipoles_adjoint.  delta omega = omega - omega0 has dL/domega0 one less than
+ * the omega0 gradient returned here.
+ *   dp, dt, n_steps, opts  as for pc_dipoles_run; opts->precision PC_F64, opts->ed_mode 0,
+ *                          opts->first_index the first fitted step
+ *   dL_dgamma, dL_domega   device [B][N] cotangents (either may be NULL, not both)
+ *   gamma, omega           device [B][N] out: the fitted values (or NULL)
+ *   g                      gradients (device)
+ * Errors: those of pc_dipoles_adjoint; PC_ERR_NOCONV when a fit fails (fewer than two
+ * kinetic-energy minima in the window) or its Hessian is singular.
+ */
+pc_status pc_dipoles_rates_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
+                                   const pc_run_opts *opts, const double *dL_dgamma, const double *dL_domega,
+                                   double *gamma, double *omega, const pc_dipole_grads *g, void *stream);
+
+/*
  * pc_alu_peaks -- measures this GPU's float32 and float64 fused-multiply-add throughput (FMA/s)
  * with dependent-chain kernels; used as roofline denominators.  Writes fp32_fma_per_s,
  * fp64_fma_per_s (host pointers).

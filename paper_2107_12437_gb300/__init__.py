@@ -2,7 +2,8 @@
 
 The computation lives in libpycharge_gb300.so (C ABI: include/pycharge_gb300.h); `capi` is its
 thin ctypes binding.  Names follow the header: pc_fields, pc_fields_plane, pc_dipoles_run,
-pc_ke_fit, pc_dipoles_adjoint (with the autograd wrapper final_energy).
+pc_ke_fit, pc_dipoles_adjoint and pc_dipoles_rates_adjoint (with the autograd wrappers final_energy and
+fitted_rates).
 """
 from .capi import (  # noqa: F401
     PC_COULOMB,
@@ -15,10 +16,12 @@ from .capi import (  # noqa: F401
     charges_to_device,
     dipoles_to_device,
     final_energy,
+    fitted_rates,
     lo_config_to_device,
     load,
     pc_alu_peaks,
     pc_dipoles_adjoint,
+    pc_dipoles_rates_adjoint,
     pc_dipoles_run,
     pc_fields,
     pc_fields_plane,

@@ -80,6 +80,9 @@ SIGNATURES = {
                                       ctypes.POINTER(PcRunOut), _vp]),
     "pc_dipoles_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                           _vp, ctypes.POINTER(PcDipoleGrads), _vp]),
+    "pc_dipoles_rates_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64,
+                                                ctypes.POINTER(PcRunOpts), _vp, _vp, _vp, _vp,
+                                                ctypes.POINTER(PcDipoleGrads), _vp]),
     "pc_ke_fit": (ctypes.c_int, [_vp, _vp, _i32, _i64, _f64, _i64, _vp, _vp, _vp, _vp, _vp]),
     "pc_alu_peaks": (ctypes.c_int, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _vp]),
     "pc_fields_noalloc": (ctypes.c_int, [ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
@@ -300,6 +303,60 @@ def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, stream=
                                     _ptr(w), ctypes.byref(g), _stream(stream))
     _check(st, "pc_dipoles_adjoint")
     return g_origin, g_omega0, g_d0
+
+
+def pc_dipoles_rates_adjoint(ctx, dp, dt, n_steps, first_index, dL_dgamma=None, dL_domega=None, v_max=0.0,
+                             stream=None):
+    """pc_dipoles_rates_adjoint: gradients of sum(dL_dgamma gamma + dL_domega omega) of the Eq. KE
+    fit; returns (gamma, omega, g_origin, g_omega0, g_d0)."""
+    B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
+    dev = dp.origin.device
+
+    def cot(x):
+        return None if x is None else x.to(device=dev, dtype=torch.float64).contiguous()
+
+    wg, ww = cot(dL_dgamma), cot(dL_domega)
+    gamma = torch.empty((B, N), dtype=torch.float64, device=dev)
+    omega = torch.empty((B, N), dtype=torch.float64, device=dev)
+    g_origin = torch.empty((B, N, 3), dtype=torch.float64, device=dev)
+    g_omega0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
+                  m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=1, first_index=int(first_index), precision=PC_F64)
+    g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
+    st = ctx.lib.pc_dipoles_rates_adjoint(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
+                                          _ptr(wg), _ptr(ww), _ptr(gamma), _ptr(omega), ctypes.byref(g),
+                                          _stream(stream))
+    _check(st, "pc_dipoles_rates_adjoint")
+    return gamma, omega, g_origin, g_omega0, g_d0
+
+
+class FittedRates(torch.autograd.Function):
+    """(gamma, omega) [B][N] of the Eq. KE fit after the float64 run, differentiable in
+    (origin, omega0, d0); the backward pass is pc_dipoles_rates_adjoint."""
+
+    @staticmethod
+    def forward(fctx, origin, omega0, d0, rest, ctx, dt, n_steps, first_index, v_max):
+        dp = SimpleNamespace(origin=origin.contiguous(), omega0=omega0.contiguous(), d0=d0.contiguous(),
+                             axis=rest.axis, q=rest.q, m1=rest.m1, m2=rest.m2)
+        out = pc_dipoles_run(ctx, dp, dt, n_steps, v_max=v_max, precision=PC_F64, fit=True, first_index=first_index,
+                             want_energy=False)
+        fctx.dp, fctx.pc, fctx.args = dp, ctx, (dt, n_steps, first_index, v_max)
+        return out["gamma"], out["omega"]
+
+    @staticmethod
+    def backward(fctx, grad_gamma, grad_omega):
+        dt, n_steps, first_index, v_max = fctx.args
+        _, _, go, gw, gd = pc_dipoles_rates_adjoint(fctx.pc, fctx.dp, dt, n_steps, first_index, grad_gamma,
+                                                    grad_omega, v_max=v_max)
+        return go, gw, gd, None, None, None, None, None, None
+
+
+def fitted_rates(ctx, dp, dt, n_steps, first_index, v_max=0.0):
+    """Differentiable (gamma, omega) of the Eq. KE fit of pc_dipoles_run in float64."""
+    return FittedRates.apply(dp.origin, dp.omega0, dp.d0, dp, ctx, float(dt), int(n_steps), int(first_index),
+                             float(v_max))
 
 
 class FinalEnergy(torch.autograd.Function):

@@ -52,6 +52,8 @@ extern "C" pc_status pc_ctx_destroy(pc_ctx *ctx) {
   ctx->charge_ref.release();
   ctx->run_scratch.release();
   ctx->adj_scratch.release();
+  if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+  if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
   delete ctx;
   return PC_OK;
 }

@@ -28,6 +28,7 @@ namespace pc {
 constexpr int kRunWarps = 8;   // receivers advanced concurrently by one CTA
 constexpr int kMaxBlock = 16;  // steps per causal block (2K <= 32 stages, one per lane)
 constexpr int kSmallN = 64;    // configurations up to this size run as one persistent CTA each
+constexpr int kMaxSplit = 64;  // source slices per receiver on the grid path
 
 struct RunArgs {
   int B, N;
@@ -45,6 +46,11 @@ struct RunArgs {
   int2 *delay;        // [B][N][N]: |R_i - R_j| / (c dt) = x + y, x integer, y the fraction (float bits)
   int *kblock;        // [B] causal block length per configuration
   double *Ehalf;      // [B][N][n_steps] E_d at t_n + dt/2 (kept for the adjoint), or null
+  // grid path: sources split into nsplit slices whose partial stage fields Epart
+  // [nsplit][B][N][2*kMaxBlock+1] are summed in slice order; blk = {block start, block length}
+  double *Epart;
+  int nsplit;
+  int64_t *blk;
 };
 
 constexpr int kDipF = 12;
@@ -142,7 +148,8 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
 // Phase A for one receiver (one warp): stage fields E_d(n0 + (s+1)/2), s < ns, into Es[1 + s];
 // ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.
 template <bool MIXED>
-__device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err) {
+__device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err,
+                            int j_lo, int j_hi, double *dst) {
   const int lane = threadIdx.x & 31;
   const int nst = ns > 0 ? ns : 1;
   const int slots = 32 / nst;
@@ -152,7 +159,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   double accd = 0.0;
   float accf = 0.f, comp = 0.f;
   if (m < slots) {
-    for (int j = m; j < a.N; j += slots) {
+    for (int j = j_lo + m; j < j_hi; j += slots) {
       if (j == i) continue;
       if (MIXED) {
         // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
@@ -177,7 +184,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   if (lane < nst) {
     double t = 0.0;
     for (int mm = 0; mm < slots; ++mm) t += sh[mm * nst + lane];
-    a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = t;
+    dst[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = t;
   }
   __syncwarp();
 }
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
   // ---- E_d at t = 0 from the static configuration ----
   for (int i = warp; i < N; i += kRunWarps) {
     int err = 0;
-    drive_phase<MIXED>(a, b, i, 0, 0, sh[warp], &err);
+    drive_phase<MIXED>(a, b, i, 0, 0, sh[warp], &err, 0, N, a.Es);
     if (err) {
       set_status(a.status, err);
       s_stop = 1;
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     // phase A: all stage fields of the block
     for (int i = warp; i < N; i += kRunWarps) {
       int err = 0;
-      drive_phase<MIXED>(a, b, i, n0, 2 * kb, sh[warp], &err);
+      drive_phase<MIXED>(a, b, i, n0, 2 * kb, sh[warp], &err, 0, N, a.Es);
       if (err) {
         set_status(a.status, err);
         s_stop = 1;
@@ -297,11 +304,16 @@ __global__ void lo_tables_kernel(const RunArgs a) {
 }
 
 // Grid-wide phases for large configurations: history sample 0, stage fields (one warp per
-// receiver) and RK4 (one thread per receiver), one launch each per causal block.
+// receiver and source slice) and RK4 (one thread per receiver), one launch each per causal block;
+// the block loop runs inside one CUDA graph (a device-side while loop).
 template <bool MIXED>
-__global__ void lo_init_kernel(const RunArgs a) {
+__global__ void lo_init_kernel(const RunArgs a, int K) {
   const int64_t S = a.n_steps + 1;
   const double L = kC * a.dt;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.blk[0] = 0;
+    a.blk[1] = K;
+  }
   for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < (int64_t)a.B * a.N;
        bi += (int64_t)gridDim.x * blockDim.x) {
     a.d[bi * S] = a.d0[bi];
@@ -316,27 +328,70 @@ __global__ void lo_init_kernel(const RunArgs a) {
   }
 }
 
+// Grid path, phase A: one warp per (receiver, source slice).  ns < 0 takes the block from the
+// device cursor a.blk (graph replay); ns == 0 evaluates E_d(0).
 template <bool MIXED>
 __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs a, int64_t n0, int ns) {
   __shared__ double sh[kRunWarps][32];
   if (*((volatile int *)a.status)) return;  // an earlier block failed
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (ns < 0) {
+    n0 = a.blk[0];
+    if (n0 >= a.n_steps) return;
+    ns = 2 * (int)min(a.blk[1], a.n_steps - n0);
+  }
+  const int warp = threadIdx.x >> 5;
   const int b = blockIdx.y;
   const int i = blockIdx.x * kRunWarps + warp;
   if (i >= a.N) return;
+  const int z = blockIdx.z;
+  const int chunk = (a.N + a.nsplit - 1) / a.nsplit;
+  const int j_lo = min(a.N, z * chunk), j_hi = min(a.N, j_lo + chunk);
+  double *dst = a.nsplit > 1 ? a.Epart + (size_t)z * a.B * a.N * (2 * kMaxBlock + 1) : a.Es;
   int err = 0;
-  drive_phase<MIXED>(a, b, i, n0, ns, sh[warp], &err);
+  drive_phase<MIXED>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
   if (err) set_status(a.status, err);
-  if (ns == 0 && lane == 0 && a.Ed) a.Ed[bidx(a, b, i) * (a.n_steps + 1)] = a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)];
+}
+
+// Sum of the slices' partial stage fields (fixed order) into Es[lo..hi].
+__device__ __forceinline__ void sum_slices(const RunArgs &a, size_t bi, int lo, int hi) {
+  if (a.nsplit <= 1) return;
+  const size_t stride = (size_t)a.B * a.N * (2 * kMaxBlock + 1);
+  const double *src = a.Epart + bi * (2 * kMaxBlock + 1);
+  for (int k = lo; k <= hi; ++k) {
+    double t = 0.0;
+    for (int z = 0; z < a.nsplit; ++z) t += src[z * stride + k];
+    a.Es[bi * (2 * kMaxBlock + 1) + k] = t;
+  }
+}
+
+// E_d(0): slice sums and the first driving-field sample.
+__global__ void lo_start_kernel(const RunArgs a) {
+  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= (int64_t)a.B * a.N) return;
+  sum_slices(a, bi, 0, 0);
+  if (a.Ed) a.Ed[bi * (a.n_steps + 1)] = a.Es[bi * (2 * kMaxBlock + 1)];
 }
 
 template <bool MIXED>
 __global__ void lo_rk4_kernel(const RunArgs a, int64_t n0, int kb) {
   if (*((volatile int *)a.status)) return;
+  if (kb < 0) {
+    n0 = a.blk[0];
+    if (n0 >= a.n_steps) return;
+    kb = (int)min(a.blk[1], a.n_steps - n0);
+  }
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= (int64_t)a.B * a.N) return;
+  sum_slices(a, bi, 1, 2 * kb);
   int stop = 0;
   rk4_block<MIXED>(a, (int)(bi / a.N), (int)(bi % a.N), n0, kb, &stop);
+}
+
+// Advances the device cursor by one block and sets the loop condition of the graph.
+__global__ void lo_advance_kernel(const RunArgs a, cudaGraphConditionalHandle loop) {
+  const int64_t n0 = a.blk[0] + a.blk[1];
+  a.blk[0] = n0;
+  cudaGraphSetConditional(loop, (n0 < a.n_steps && *((volatile int *)a.status) == 0) ? 1u : 0u);
 }
 
 // Phase B for receiver i: kb RK4 steps (Eq. LO_equation) from step n0 with the stage fields Es,
@@ -707,6 +762,144 @@ static pc_status launch_fit(pc_ctx *ctx, const double *ke, int K, int64_t S, dou
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
+// Adjoint of the Eq. KE fit through its optimum (implicit-function theorem).  With the fit's scaled
+// parameters x = (A/A_g, gamma T, (omega - omega_g) T, phi) and scaled residuals r_n = (m_n - y_n)/A_g,
+// the optimum solves g(x, y) = sum_n r_n dr_n/dx = 0, so dx/dy_n = H^-1 J_n / A_g with
+// H = sum_n (J_n J_n^T + r_n d2r_n/dx2) the full Hessian of the least-squares cost.  For a loss
+// with cotangents (dL/dgamma, dL/domega), dL/dy_n = z . J_n / A_g with z = H^-1 (0, dL/dgamma / T,
+// dL/domega / T, 0).  The kinetic energy y_n = m d'_n^2 / (2 q^2) (n >= first) then passes
+// dL/dd'_n = dL/dy_n m d'_n / q^2 into the history adjoint of sample n.
+struct FitAdjArgs {
+  const double *ke;            // [K][S] the fitted series
+  int K;
+  int64_t S, first;
+  double dt;
+  const double *gamma, *omega, *amp, *phase;  // the optimum, physical units
+  const double *dL_dgamma, *dL_domega;        // [K]
+  const double *dd, *m1, *m2, *q;             // forward d' history and the dipoles' constants
+  double *mu;                                 // [K][S][3] history adjoints (d' component += ...)
+  int *status;
+};
+
+__global__ void __launch_bounds__(kFitThreads) ke_fit_adjoint_kernel(const FitAdjArgs fa) {
+  __shared__ double sh[16 * (kFitThreads / 32)];
+  __shared__ double s_z[4];
+  __shared__ int s_bad;
+  const int k = blockIdx.x;
+  const double *y = fa.ke + (size_t)k * fa.S + fa.first;
+  const int64_t n = fa.S - fa.first;
+  const double dt = fa.dt, T = (double)(n - 1) * dt;
+  const double A = fa.amp[k], g = fa.gamma[k], w = fa.omega[k], ph = fa.phase[k];
+  const double Ag = A, iA = 1.0 / Ag, iT = 1.0 / T;
+  const int64_t chunk = (n + kFitThreads - 1) / kFitThreads;
+  const int64_t i0 = (int64_t)threadIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s = 0.0, c = 1.0, cw = 1.0, sw = 0.0, env = 1.0, e1 = 1.0;
+  if (i0 < i1) {
+    sincos(w * ((double)i0 * dt) + ph, &s, &c);
+    sincos(w * dt, &sw, &cw);
+    env = exp(-g * ((double)i0 * dt));
+    e1 = exp(-g * dt);
+  }
+  // pass 1: H (upper triangle, 10 values)
+  double h[10];
+  for (int q = 0; q < 10; ++q) h[q] = 0.0;
+  {
+    double ss_ = s, cc_ = c, en = env;
+    for (int64_t i = i0; i < i1; ++i) {
+      const double u = (double)i * dt * iT;  // tau / T
+      const double ss = ss_ * ss_, s2 = 2.0 * ss_ * cc_, c2 = cc_ * cc_ - ss_ * ss_;
+      const double mA = A * en * iA;         // model / (A_g sin^2)
+      const double r = (A * en * ss - y[i]) * iA;
+      double J[4], D[10];
+      J[0] = en * ss;
+      J[1] = -u * mA * ss;
+      J[3] = mA * s2;
+      J[2] = J[3] * u;
+      // second derivatives of r in the scaled parameters (upper triangle, row-major)
+      D[0] = 0.0;
+      D[1] = -u * en * ss;
+      D[2] = en * s2 * u;
+      D[3] = en * s2;
+      D[4] = mA * ss * u * u;
+      D[5] = -mA * s2 * u * u;
+      D[6] = -mA * s2 * u;
+      D[7] = 2.0 * mA * c2 * u * u;
+      D[8] = 2.0 * mA * c2 * u;
+      D[9] = 2.0 * mA * c2;
+      int idx = 0;
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = p; q < 4; ++q, ++idx) h[idx] += J[p] * J[q] + r * D[idx];
+      const double s1 = ss_ * cw + cc_ * sw;
+      cc_ = cc_ * cw - ss_ * sw;
+      ss_ = s1;
+      en *= e1;
+    }
+  }
+  double h16[16];
+  for (int q = 0; q < 10; ++q) h16[q] = h[q];
+  for (int q = 10; q < 16; ++q) h16[q] = 0.0;
+  block_sum<16>(h16, sh);
+  if (threadIdx.x == 0) {
+    double M[4][4], rhs[4] = {0.0, fa.dL_dgamma ? fa.dL_dgamma[k] * iT : 0.0,
+                              fa.dL_domega ? fa.dL_domega[k] * iT : 0.0, 0.0};
+    int idx = 0;
+    for (int p = 0; p < 4; ++p)
+      for (int q = p; q < 4; ++q, ++idx) M[p][q] = M[q][p] = h16[idx];
+    // Gaussian elimination with partial pivoting
+    s_bad = 0;
+    for (int cc = 0; cc < 4; ++cc) {
+      int best = cc;
+      for (int r = cc + 1; r < 4; ++r)
+        if (fabs(M[r][cc]) > fabs(M[best][cc])) best = r;
+      if (best != cc) {
+        for (int q = 0; q < 4; ++q) {
+          const double t = M[cc][q];
+          M[cc][q] = M[best][q];
+          M[best][q] = t;
+        }
+        const double t = rhs[cc];
+        rhs[cc] = rhs[best];
+        rhs[best] = t;
+      }
+      if (!(fabs(M[cc][cc]) > 0.0)) s_bad = 1;
+      for (int r = cc + 1; r < 4 && !s_bad; ++r) {
+        const double f = M[r][cc] / M[cc][cc];
+        for (int q = cc; q < 4; ++q) M[r][q] -= f * M[cc][q];
+        rhs[r] -= f * rhs[cc];
+      }
+    }
+    for (int cc = 3; cc >= 0 && !s_bad; --cc) {
+      double t = rhs[cc];
+      for (int q = cc + 1; q < 4; ++q) t -= M[cc][q] * s_z[q];
+      s_z[cc] = t / M[cc][cc];
+    }
+    if (s_bad) set_status(fa.status, PC_ERR_NOCONV);
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const double z0 = s_z[0], z1 = s_z[1], z2 = s_z[2], z3 = s_z[3];
+  const double m = fa.m1[k] * fa.m2[k] / (fa.m1[k] + fa.m2[k]), qq = fa.q[k];
+  const double kv = m / (qq * qq);
+  const double *ddk = fa.dd + (size_t)k * fa.S + fa.first;
+  double *muk = fa.mu + ((size_t)k * fa.S + fa.first) * 3;
+  // pass 2: dL/dy_n = z . J_n / A_g, into the adjoint of d'_n
+  double ss_ = s, cc_ = c, en = env;
+  for (int64_t i = i0; i < i1; ++i) {
+    const double u = (double)i * dt * iT;
+    const double ss = ss_ * ss_, s2 = 2.0 * ss_ * cc_;
+    const double mA = A * en * iA;
+    const double J0 = en * ss, J1 = -u * mA * ss, J3 = mA * s2, J2 = J3 * u;
+    const double dy = (z0 * J0 + z1 * J1 + z2 * J2 + z3 * J3) * iA;
+    muk[3 * i + 1] += dy * kv * ddk[i];
+    const double s1 = ss_ * cw + cc_ * sw;
+    cc_ = cc_ * cw - ss_ * sw;
+    ss_ = s1;
+    en *= e1;
+  }
+}
+
 }  // namespace pc
 
 extern "C" pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t S, double dt, int64_t first_index,
@@ -723,6 +916,66 @@ extern "C" pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t
 }
 
 namespace pc {
+// The causal-block loop of the grid path as one CUDA graph: a while node whose body is
+// drive -> RK4 -> advance.  The advance kernel moves the device cursor a.blk by one block and
+// clears the loop condition after the last block or after an error, so the loop ends after at
+// most ceil(n_steps / K) passes.  The graph is kept in the context until its next use (every
+// entry point has synchronised its stream by then) or until the context is destroyed.
+static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, dim3 dgrid, unsigned rgrid,
+                                   cudaStream_t st) {
+  if (ctx->loop_exec) {
+    cudaGraphExecDestroy(ctx->loop_exec);
+    ctx->loop_exec = nullptr;
+  }
+  if (ctx->loop_graph) {
+    cudaGraphDestroy(ctx->loop_graph);
+    ctx->loop_graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return PC_ERR_CUDA;
+  ctx->loop_graph = g;
+  cudaGraphConditionalHandle loop;
+  if (cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return PC_ERR_CUDA;
+  // zero-initialised storage: the struct's union has no default constructor
+  alignas(cudaGraphNodeParams) unsigned char cp_mem[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_mem);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  if (cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp) != cudaSuccess) return PC_ERR_CUDA;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  RunArgs args = a;
+  int64_t from_cursor = -1;
+  int from_cursor_i = -1;
+  void *drive_args[] = {&args, &from_cursor, &from_cursor_i};
+  void *rk4_args[] = {&args, &from_cursor, &from_cursor_i};
+  void *adv_args[] = {&args, &loop};
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof(kp));
+  cudaGraphNode_t n1, n2, n3;
+  kp.func = mixed ? (void *)lo_drive_kernel<true> : (void *)lo_drive_kernel<false>;
+  kp.gridDim = dgrid;
+  kp.blockDim = dim3(kRunWarps * 32);
+  kp.kernelParams = drive_args;
+  if (cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp) != cudaSuccess) return PC_ERR_CUDA;
+  kp.func = mixed ? (void *)lo_rk4_kernel<true> : (void *)lo_rk4_kernel<false>;
+  kp.gridDim = dim3(rgrid);
+  kp.blockDim = dim3(128);
+  kp.kernelParams = rk4_args;
+  if (cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp) != cudaSuccess) return PC_ERR_CUDA;
+  kp.func = (void *)lo_advance_kernel;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = adv_args;
+  if (cudaGraphAddKernelNode(&n3, body, &n2, 1, &kp) != cudaSuccess) return PC_ERR_CUDA;
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) return PC_ERR_CUDA;
+  ctx->loop_exec = ex;
+  return cudaGraphLaunch(ex, st) == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+
 // Forward run (Algorithm 1); Ehalf (or null) receives E_d at the half steps for the adjoint.
 static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                           const pc_run_out *out, double *Ehalf, cudaStream_t st, int *k_out = nullptr) {
@@ -747,8 +1000,12 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const size_t dl_bytes = mixed ? al(nbn * dp->N * sizeof(int2)) : 0;
   const size_t k_bytes = al(dp->B * sizeof(int));
   const size_t ke_bytes = opts->fit ? al(nbn * S * sizeof(double)) : 0;
-  if (ctx->run_scratch.reserve(es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes + ke_bytes) != cudaSuccess)
-    return PC_ERR_CUDA;
+  const bool grid = dp->N > pc::kSmallN;
+  const size_t part_bytes = grid ? al((size_t)pc::kMaxSplit * es_bytes) : 0;
+  const size_t blk_bytes = al(2 * sizeof(int64_t));
+  const size_t part_off = es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes + ke_bytes;
+  const size_t blk_off = part_off + part_bytes;
+  if (ctx->run_scratch.reserve(blk_off + blk_bytes) != cudaSuccess) return PC_ERR_CUDA;
   char *scr = (char *)ctx->run_scratch.ptr;
   pc::RunArgs a;
   a.B = dp->B;
@@ -775,6 +1032,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.delay = mixed ? (int2 *)(scr + es_bytes + h_bytes + f_bytes) : nullptr;
   a.kblock = (int *)(scr + es_bytes + h_bytes + f_bytes + dl_bytes);
   a.Ehalf = Ehalf;
+  a.Epart = nullptr;
+  a.nsplit = 1;
+  a.blk = nullptr;
   a.status = ctx->d_status;
   char *ke_base = scr + es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes;
   pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
@@ -800,24 +1060,24 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
       return PC_ERR_CUDA;
     int K = pc::kMaxBlock;
     for (int v : kb) K = std::min(K, v);
-    const dim3 dgrid((unsigned)((dp->N + pc::kRunWarps - 1) / pc::kRunWarps), (unsigned)dp->B);
+    // sources split so that about two resident warps per SM slot are in flight
+    const int64_t target = (int64_t)ctx->num_sms * 64;
+    int nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, (target + (int64_t)nbn - 1) / (int64_t)nbn),
+                                        std::max(1, dp->N / 8));
+    nsplit = std::min(nsplit, kMaxSplit);
+    a.nsplit = nsplit;
+    a.Epart = nsplit > 1 ? (double *)(scr + part_off) : nullptr;
+    a.blk = (int64_t *)(scr + blk_off);
+    const dim3 dgrid((unsigned)((dp->N + pc::kRunWarps - 1) / pc::kRunWarps), (unsigned)dp->B, (unsigned)nsplit);
     const unsigned rgrid = (unsigned)((nbn + 127) / 128);
-    if (mixed) {
-      pc::lo_init_kernel<true><<<rgrid, 128, 0, st>>>(a);
-      pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
-      for (int64_t n0 = 0; n0 < n_steps; n0 += K) {
-        const int k = (int)std::min((int64_t)K, n_steps - n0);
-        pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * k);
-        pc::lo_rk4_kernel<true><<<rgrid, 128, 0, st>>>(a, n0, k);
-      }
-    } else {
-      pc::lo_init_kernel<false><<<rgrid, 128, 0, st>>>(a);
-      pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
-      for (int64_t n0 = 0; n0 < n_steps; n0 += K) {
-        const int k = (int)std::min((int64_t)K, n_steps - n0);
-        pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * k);
-        pc::lo_rk4_kernel<false><<<rgrid, 128, 0, st>>>(a, n0, k);
-      }
+    if (mixed) pc::lo_init_kernel<true><<<rgrid, 128, 0, st>>>(a, K);
+    else pc::lo_init_kernel<false><<<rgrid, 128, 0, st>>>(a, K);
+    if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
+    else pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
+    pc::lo_start_kernel<<<rgrid, 128, 0, st>>>(a);
+    if (n_steps > 0) {
+      pc_status gs = pc::launch_block_loop(ctx, a, mixed, dgrid, rgrid, st);
+      if (gs != PC_OK) return gs;
     }
   }
   if (opts->fit) {
@@ -883,7 +1143,7 @@ __global__ void adj_init_kernel(const AdjArgs A) {
     const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
     const double m = m1 * m2 / (m1 + m2);
     const double dN = a.d[bi * S + a.n_steps], vN = a.dd[bi * S + a.n_steps];
-    const double w = A.wE[bi];
+    const double w = A.wE ? A.wE[bi] : 0.0;
     // E = m (w0^2 d^2 + d'^2) / (2 q^2)
     A.lam[2 * bi] = w * m * w0 * w0 * dN / (q * q);
     A.lam[2 * bi + 1] = w * m * vN / (q * q);
@@ -1154,29 +1414,32 @@ __global__ void adj_final_kernel(const AdjArgs A) {
 
 }  // namespace pc
 
-extern "C" pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
-                                        const pc_run_opts *opts, const double *dL_dEnergyFinal,
-                                        const pc_dipole_grads *g, void *stream) {
-  if (!ctx || !dp || !opts || !dL_dEnergyFinal || !g || !g->origin || !g->omega0 || !g->d0) return PC_ERR_ARG;
+namespace pc {
+// Reverse mode of the float64 run for L = sum w E(T) (wE, or null) plus, when rates is set,
+// sum (dL/dgamma gamma + dL/domega omega) of the Eq. KE fit from first_index on.
+static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
+                              const double *wE, bool rates, const double *dL_dgamma, const double *dL_domega,
+                              double *gamma_out, double *omega_out, const pc_dipole_grads *g, cudaStream_t st) {
+  if (!dp || !opts || !g || !g->origin || !g->omega0 || !g->d0) return PC_ERR_ARG;
   if (opts->ed_mode != 0 || opts->precision != PC_F64 || n_steps < 1) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0)) return PC_ERR_ARG;
-  pc::DeviceGuard gd(ctx->device);
-  cudaStream_t st = (cudaStream_t)stream;
-  pc_status bs = pc::begin_call(ctx, st);
-  if (bs != PC_OK) return bs;
+  if (rates && (opts->first_index < 0 || n_steps + 1 - opts->first_index < 8)) return PC_ERR_ARG;
   const int64_t S = n_steps + 1;
   const size_t nbn = (size_t)dp->B * dp->N;
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   const size_t hist = al(nbn * S * sizeof(double));
   const size_t half = al(nbn * n_steps * sizeof(double));
   const size_t mu_b = al(nbn * S * 3 * sizeof(double));
-  const size_t small = al(nbn * (2 + 1 + (2 * pc::kMaxBlock + 1) + 1 + 2) * sizeof(double));
-  if (ctx->adj_scratch.reserve(4 * hist + half + mu_b + small) != cudaSuccess) return PC_ERR_CUDA;
+  const size_t small = al(nbn * (2 + 1 + (2 * kMaxBlock + 1) + 1 + 2) * sizeof(double));
+  const size_t fit_b = rates ? hist + al(4 * nbn * sizeof(double)) : 0;
+  if (ctx->adj_scratch.reserve(4 * hist + half + mu_b + small + fit_b) != cudaSuccess) return PC_ERR_CUDA;
   char *p = (char *)ctx->adj_scratch.ptr;
   double *d = (double *)p, *dd = (double *)(p + hist), *ddd = (double *)(p + 2 * hist), *Ed = (double *)(p + 3 * hist);
   double *Eh = (double *)(p + 4 * hist);
   double *mu = (double *)(p + 4 * hist + half);
   double *sm = (double *)(p + 4 * hist + half + mu_b);
+  double *ke = rates ? (double *)(p + 4 * hist + half + mu_b + small) : nullptr;
+  double *fpar = rates ? ke + hist / sizeof(double) : nullptr;  // gamma, omega, amp, phase [nbn] each
   // forward run with the full history and the half-step fields
   pc_run_opts fo = *opts;
   fo.fit = 0;
@@ -1187,11 +1450,11 @@ extern "C" pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, doubl
   fw.d_ddot = ddd;
   fw.Ed = Ed;
   int K = 1;
-  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K);
+  pc_status rs = run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K);
   if (rs != PC_OK) return rs;
-  pc::AdjArgs A;
+  AdjArgs A;
   memset(&A, 0, sizeof(A));
-  pc::RunArgs &a = A.f;
+  RunArgs &a = A.f;
   a.B = dp->B;
   a.N = dp->N;
   a.origin = dp->origin;
@@ -1208,20 +1471,51 @@ extern "C" pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, doubl
   a.ddd = ddd;
   a.Ed = Ed;
   a.Ehalf = Eh;
+  a.nsplit = 1;
   a.status = ctx->d_status;
-  A.wE = dL_dEnergyFinal;
+  A.wE = wE;
   A.mu = mu;
   A.lam = sm;
   A.carry = sm + 2 * nbn;
   A.Ebar = sm + 3 * nbn;
-  A.w0bar = sm + (3 + 2 * pc::kMaxBlock + 1) * nbn;
+  A.w0bar = sm + (3 + 2 * kMaxBlock + 1) * nbn;
   A.tau = A.w0bar + nbn;
   A.g_origin = g->origin;
   A.g_omega0 = g->omega0;
   A.g_d0 = g->d0;
   if (cudaMemsetAsync(mu, 0, nbn * S * 3 * sizeof(double), st) != cudaSuccess) return PC_ERR_CUDA;
+  if (rates) {
+    // the fit of the forward run's kinetic energies, then its adjoint into the d' history adjoints
+    ke_series_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, ke);
+    double *fg = fpar, *fw_ = fpar + nbn, *fa_ = fpar + 2 * nbn, *fp = fpar + 3 * nbn;
+    pc_status ls = launch_fit(ctx, ke, (int)nbn, S, dt, opts->first_index, fg, fw_, fa_, fp, st);
+    if (ls != PC_OK) return ls;
+    FitAdjArgs fj;
+    fj.ke = ke;
+    fj.K = (int)nbn;
+    fj.S = S;
+    fj.first = opts->first_index;
+    fj.dt = dt;
+    fj.gamma = fg;
+    fj.omega = fw_;
+    fj.amp = fa_;
+    fj.phase = fp;
+    fj.dL_dgamma = dL_dgamma;
+    fj.dL_domega = dL_domega;
+    fj.dd = dd;
+    fj.m1 = dp->m1;
+    fj.m2 = dp->m2;
+    fj.q = dp->q;
+    fj.mu = mu;
+    fj.status = ctx->d_status;
+    ke_fit_adjoint_kernel<<<(unsigned)nbn, kFitThreads, 0, st>>>(fj);
+    if (gamma_out && cudaMemcpyAsync(gamma_out, fg, nbn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return PC_ERR_CUDA;
+    if (omega_out && cudaMemcpyAsync(omega_out, fw_, nbn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return PC_ERR_CUDA;
+  }
   const unsigned rgrid = (unsigned)((nbn + 127) / 128);
-  pc::adj_init_kernel<<<rgrid, 128, 0, st>>>(A);
+  adj_init_kernel<<<rgrid, 128, 0, st>>>(A);
   // margin for charge offsets: three times the largest initial |r_dip|, in samples, plus one
   std::vector<double> hq(nbn), hd0(nbn), htau(2 * nbn);
   if (cudaMemcpyAsync(hq.data(), dp->q, nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1234,23 +1528,52 @@ extern "C" pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, doubl
     smax = std::max(smax, std::fabs(hd0[k] / hq[k]));
     if (htau[2 * k] <= htau[2 * k + 1]) spread = std::max(spread, htau[2 * k + 1] - htau[2 * k]);
   }
-  A.margin = (int64_t)std::ceil(3.0 * smax / (pc::kC * dt)) + 2;
+  A.margin = (int64_t)std::ceil(3.0 * smax / (kC * dt)) + 2;
   const int wmax = (int)std::max(1.0, std::min<double>(std::ceil(spread) + K + 2.0 * A.margin + 6.0, (double)S));
   const size_t smem = (size_t)wmax * 3 * sizeof(double);
   if (smem > 200 * 1024) return PC_ERR_ARG;  // source windows beyond shared memory
-  if (cudaFuncSetAttribute(pc::adj_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(adj_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PC_ERR_CUDA;
   const dim3 fgrid((unsigned)dp->N, (unsigned)dp->B);
   const int64_t nblocks = (n_steps + K - 1) / K;
   for (int64_t bk = nblocks - 1; bk >= 0; --bk) {
     const int64_t n0 = bk * K;
     const int kb = (int)std::min((int64_t)K, n_steps - n0);
-    pc::adj_rk4_kernel<<<rgrid, 128, 0, st>>>(A, n0, kb);
-    pc::adj_field_kernel<<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
+    adj_rk4_kernel<<<rgrid, 128, 0, st>>>(A, n0, kb);
+    adj_field_kernel<<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
   }
   // the driving field at t = 0 (static configuration) and the final gradients
-  pc::adj_field_kernel<<<fgrid, 128, smem, st>>>(A, 0, 0, wmax);
-  pc::adj_final_kernel<<<rgrid, 128, 0, st>>>(A);
+  adj_field_kernel<<<fgrid, 128, smem, st>>>(A, 0, 0, wmax);
+  adj_final_kernel<<<rgrid, 128, 0, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
+}
+}  // namespace pc
+
+extern "C" pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
+                                        const pc_run_opts *opts, const double *dL_dEnergyFinal,
+                                        const pc_dipole_grads *g, void *stream) {
+  if (!ctx || !dL_dEnergyFinal) return PC_ERR_ARG;
+  pc::DeviceGuard gd(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  pc_status rs = pc::adjoint_core(ctx, dp, dt, n_steps, opts, dL_dEnergyFinal, false, nullptr, nullptr, nullptr,
+                                  nullptr, g, st);
+  if (rs != PC_OK) return rs;
+  return pc::end_call(ctx, st);
+}
+
+extern "C" pc_status pc_dipoles_rates_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
+                                              const pc_run_opts *opts, const double *dL_dgamma,
+                                              const double *dL_domega, double *gamma, double *omega,
+                                              const pc_dipole_grads *g, void *stream) {
+  if (!ctx || (!dL_dgamma && !dL_domega)) return PC_ERR_ARG;
+  pc::DeviceGuard gd(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  pc_status rs = pc::adjoint_core(ctx, dp, dt, n_steps, opts, nullptr, true, dL_dgamma, dL_domega, gamma, omega, g,
+                                  st);
+  if (rs != PC_OK) return rs;
   return pc::end_call(ctx, st);
 }

@@ -374,26 +374,25 @@ __device__ __forceinline__ void charge_mixed(float ax, float ay, float az, float
 }
 
 // Kahan-compensated running sums of the ten outputs; each thread's sums live in shared memory,
-// strided by the block size (they are touched once per group of sixteen sources).
-struct KahanSmem {
-  float *sum, *comp;  // [10][kMixThreads], thread column tid
-  __device__ __forceinline__ void add(const float *part) const {
+// strided by the block size (they are touched once per group of sixteen sources).  Indexed from
+// the thread index directly, so no pointer stays live across the source loop.
+using KahanArr = float[2][10][kMixThreads];
+__device__ __forceinline__ void kahan_add(KahanArr &k, int tid, const float *part) {
 #pragma unroll
-    for (int i = 0; i < 10; ++i) {
-      const float s0 = sum[i * kMixThreads], c0 = comp[i * kMixThreads];
-      const float y = part[i] - c0;
-      const float t = s0 + y;
-      comp[i * kMixThreads] = (t - s0) - y;
-      sum[i * kMixThreads] = t;
-    }
+  for (int i = 0; i < 10; ++i) {
+    const float s0 = k[0][i][tid], c0 = k[1][i][tid];
+    const float y = part[i] - c0;
+    const float t = s0 + y;
+    k[1][i][tid] = (t - s0) - y;
+    k[0][i][tid] = t;
   }
-  __device__ __forceinline__ float get(int i) const { return sum[i * kMixThreads] - comp[i * kMixThreads]; }
-};
+}
+__device__ __forceinline__ float kahan_get(const KahanArr &k, int tid, int i) { return k[0][i][tid] - k[1][i][tid]; }
 
 template <int KIND, bool LIST>
 __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
   __shared__ double s_anchor[3];
-  __shared__ float s_kahan[2][10][kMixThreads];
+  __shared__ KahanArr s_kahan;
   __shared__ float4 s_geo[kChunk];   // rho_a (x,y,z), |rho_a|
   __shared__ float4 s_geo_lo[kChunk]; // low parts of rho_a and |rho_a| (list mode)
   __shared__ float4 s_ax[kChunk];    // axis (x,y,z), q/e
@@ -430,10 +429,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     s_anchor[2] = a[2];
   }
   __syncthreads();
-  double r[3];
-  point_at(L.pts, active ? p : 0, r);
-  const double t = L.times[f];
-  const KahanSmem acc{&s_kahan[0][0][tid], &s_kahan[1][0][tid]};
+  const int64_t pp = active ? p : 0;
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
     s_kahan[0][i][tid] = 0.f;
@@ -447,21 +443,28 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
 
   // ---------------- dipoles ----------------
   if (s.N > 0) {
+    // float64 values used once per chunk or by the rare slow pairs are recomputed there, so that
+    // none of them occupies registers across the source loop
+    double r[3];
+    point_at(L.pts, pp, r);
     const double drxd = (r[0] - s_anchor[0]) / Ld, dryd = (r[1] - s_anchor[1]) / Ld, drzd = (r[2] - s_anchor[2]) / Ld;
     const float drx = (float)drxd, dry = (float)dryd, drz = (float)drzd;
     const float drlx = (float)(drxd - (double)drx), drly = (float)(dryd - (double)dry),
                 drlz = (float)(drzd - (double)drz);
     const float dr2 = drx * drx + dry * dry + drz * drz;
-    const double u = (t - s.t0d) / s.dtd;
     const float rex = (float)(L.r_excl / Ld);
+    const float rex_fast = rex + 1.5f;
     const int Sd32 = (int)s.Sd;
+    const unsigned jlim = Sd32 > 3 ? (unsigned)(Sd32 - 3) : 0u;  // fast segments 1 <= j <= S-3
     for (int base = 0; base < s.N; base += kChunk) {
       const int nch = min(kChunk, s.N - base);
       __syncthreads();
       if (tid < nch) {
         const int j = base + tid;
+        const double Ldc = kC * s.dtd;
+        const double u = (L.times[f] - s.t0d) / s.dtd;
         double ra[3];
-        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - s.origin[3 * j + i]) / Ld;
+        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - s.origin[3 * j + i]) / Ldc;
         const double rna = sqrt(ra[0] * ra[0] + ra[1] * ra[1] + ra[2] * ra[2]);
         const double x = u - rna;
         const double kaf = floor(x);
@@ -481,7 +484,10 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
 #pragma unroll
       for (int i = 0; i < 10; ++i) part[i] = 0.f;
       unsigned long long slow_mask = 0ull;
-      for (int jj = 0; jj < nch; ++jj) {
+      for (int g16 = 0; g16 < nch; g16 += 16) {
+      // groups of sixteen sources summed in float32, the group sums compensated
+      const int gend = min(nch, g16 + 16);
+      for (int jj = g16; jj < gend; ++jj) {
         const float4 g = s_geo[jj];
         const float4 ax = s_ax[jj];
         const float4 mx = s_mix[jj];
@@ -489,8 +495,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
         const float fa = mx.z;
         const float rx = g.x + drx, ry = g.y + dry, rz = g.z + drz;
         const float rho2 = rx * rx + ry * ry + rz * rz;
-        const float irn = rsqrtf(rho2);
-        const float rn = rho2 > 0.f ? rho2 * irn : 0.f;
+        // rho2 == 0 makes rn NaN, which sends the pair to the slow path through the tests below
+        const float rn = rho2 * rsqrtf(rho2);
         // retarded time of the dipole centre, in samples: kb + xc with |xc| small
         int kb = __float_as_int(mx.w);
         float xc;
@@ -513,20 +519,23 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
           xc = (x.hi - flf) + x.lo;
         }
         const float rp = rx * ax.x + ry * ax.y + rz * ax.z;
-        // fast path: both charges on the segment of their centre's retarded time
+        // fast path: both charges on the interior segment of their centre's retarded time, the point
+        // farther than rex + 1.5 samples from the centre (the charges are then farther than rex:
+        // their distances differ from rn by |delta| <= 1.1); a garbage index from a huge or NaN xc
+        // fails the range test before any load
         float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
         bool fast = false;
-        if (fabsf(xc) < 1e6f) {
+        {
           float fl;
           const int kc = Num<float>::floor_int(xc, fl);
           const int j = kb + kc;
-          if (j >= 0 && j <= Sd32 - 2) {
+          if ((unsigned)(j - 1) < jlim && rn > rex_fast) {
             const HistF32 H{s_hist[jj]};
             float x0, v0, a0, x1, v1, a1;
             H.get_in(j, x0, v0, a0);
             H.get_in(j + 1, x1, v1, a1);
-            fast = dip_pair_states<float>(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, mu.x, mu.y, j == 0, j == Sd32 - 2,
-                                          Xp, Vp, Ap, dp, Xm, Vm, Am, dm);
+            fast = dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, mu.x, mu.y, Xp, Vp, Ap, dp, Xm, Vm, Am,
+                                        dm);
           }
         }
         // near fields that cancel in float32 also leave the fast path
@@ -536,21 +545,21 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
           slow_mask |= 1ull << jj;
           continue;
         }
-        dipole_pair<KIND, float>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm, Am, dm,
-                                 rex, part, mask);
-        if ((jj & 15) == 15) {
-          acc.add(part);
-#pragma unroll
-          for (int i = 0; i < 10; ++i) part[i] = 0.f;
-        }
+        dipole_pair<KIND, float, false>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm,
+                                        Am, dm, rex, part, mask);
       }
-      acc.add(part);
+      kahan_add(s_kahan, tid, part);
+#pragma unroll
+      for (int i = 0; i < 10; ++i) part[i] = 0.f;
+      }
       // the pairs of this chunk that left the fast path
       while (slow_mask && !err) {
         const int jj = __ffsll((long long)slow_mask) - 1;
         slow_mask &= slow_mask - 1ull;
-#pragma unroll
-        for (int i = 0; i < 10; ++i) part[i] = 0.f;
+        // the out-of-line call gets arrays of its own: passing the address of part or mask would
+        // keep them in local memory throughout the source loop
+        float sp[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint8_t smask = 0;
         const float4 g = s_geo[jj];
         const float4 ax = s_ax[jj];
         const float4 mx = s_mix[jj];
@@ -574,15 +583,21 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
           kb += fl;
           xc = (x.hi - flf) + x.lo;
         }
+        double rp64[3];
+        point_at(L.pts, pp, rp64);
         const int e = slow_dipole<KIND>(s, base + jj, s_hist[jj], Sd32, kb, xc, rx, ry, rz, rn, ax, mx.x, mx.y, rex,
-                                        r, u, Ld, L.r_excl, part, &mask);
+                                        rp64, (L.times[f] - s.t0d) / s.dtd, kC * s.dtd, L.r_excl, sp, &smask);
         if (e) err = e;
-        acc.add(part);
+        mask |= smask;
+        kahan_add(s_kahan, tid, sp);
       }
     }
   }
   // ---------------- point charges ----------------
   if (s.M > 0) {
+    double r[3];
+    point_at(L.pts, pp, r);
+    const double t = L.times[f];
     const float drx = (float)((r[0] - s_anchor[0]) / Lch), dry = (float)((r[1] - s_anchor[1]) / Lch),
                 drz = (float)((r[2] - s_anchor[2]) / Lch);
     const float dr2 = drx * drx + dry * dry + drz * drz;
@@ -708,12 +723,12 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
 #pragma unroll
         for (int i = 6; i < 10; ++i) part[i] += sP * c10[i];
         if ((cc & 15) == 15) {
-          acc.add(part);
+          kahan_add(s_kahan, tid, part);
 #pragma unroll
           for (int i = 0; i < 10; ++i) part[i] = 0.f;
         }
       }
-      acc.add(part);
+      kahan_add(s_kahan, tid, part);
     }
   }
   if (!active) return;
@@ -727,22 +742,22 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   const int64_t o = (L.frame0 + f) * L.pts.P + p;
   if (L.out.E) {
     float *e = (float *)L.out.E + 3 * o;
-    e[0] = fE * acc.get(0);
-    e[1] = fE * acc.get(1);
-    e[2] = fE * acc.get(2);
+    e[0] = fE * kahan_get(s_kahan, tid, 0);
+    e[1] = fE * kahan_get(s_kahan, tid, 1);
+    e[2] = fE * kahan_get(s_kahan, tid, 2);
   }
   if (L.out.B) {
     float *b = (float *)L.out.B + 3 * o;
-    b[0] = fB * acc.get(3);
-    b[1] = fB * acc.get(4);
-    b[2] = fB * acc.get(5);
+    b[0] = fB * kahan_get(s_kahan, tid, 3);
+    b[1] = fB * kahan_get(s_kahan, tid, 4);
+    b[2] = fB * kahan_get(s_kahan, tid, 5);
   }
-  if (L.out.phi) ((float *)L.out.phi)[o] = fP * acc.get(6);
+  if (L.out.phi) ((float *)L.out.phi)[o] = fP * kahan_get(s_kahan, tid, 6);
   if (L.out.A) {
     float *a = (float *)L.out.A + 3 * o;
-    a[0] = fA * acc.get(7);
-    a[1] = fA * acc.get(8);
-    a[2] = fA * acc.get(9);
+    a[0] = fA * kahan_get(s_kahan, tid, 7);
+    a[1] = fA * kahan_get(s_kahan, tid, 8);
+    a[2] = fA * kahan_get(s_kahan, tid, 9);
   }
   if (L.out.mask) L.out.mask[o] = mask;
 }

@@ -50,6 +50,8 @@ struct pc_ctx {
   pc::Buf charge_ref;        // per-charge float64 reference positions
   pc::Buf run_scratch;       // LO-run scratch (stage fields, fit work)
   pc::Buf adj_scratch;       // adjoint: forward history, history adjoints
+  cudaGraph_t loop_graph = nullptr;     // causal-block loop of the last grid-path run
+  cudaGraphExec_t loop_exec = nullptr;
   int num_sms = 0;
 };
 

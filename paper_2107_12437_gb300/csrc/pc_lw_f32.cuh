@@ -212,13 +212,59 @@ __device__ __forceinline__ bool dip_pair_states(T x0, T v0, T a0, T x1, T v1, T 
   return ok;
 }
 
+// Fast form of dip_pair_states for the float32 inner loop: segment j interior to the history
+// (1 <= j <= S-3, checked by the caller), the series root only, and one combined test.  Returns
+// false when a charge's root leaves [-kExtrap, 1 + kExtrap] of the segment or the series does not
+// apply (|eps| >= 1e-2, which also covers B <= 0: B is positive unless the point lies within about
+// 1e-3 sample of the dipole centre, where |eps| is large); NaN inputs fail the tests as well.
+// The two charges run side by side in the lanes of float2 operations (packed FFMA2/FMUL2/FADD2:
+// one instruction issue for both charges).
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ bool dip_pair_states_fast(float x0, float v0, float a0, float x1, float v1, float a1,
+                                                     float thc, float rn, float rp, float mup, float mum, float &Xp,
+                                                     float &Vp, float &Ap, float &dp, float &Xm, float &Vm,
+                                                     float &Am, float &dm) {
+  const float dx = x1 - x0, dv = v1 - v0, da = a1 - a0;
+  const float Xc = x0 + thc * dx;
+  const float2 smu = make_float2(mup, -mum);  // (positive charge, negative charge)
+  const float2 sc = __fmul2_rn(smu, f2(Xc));
+  const float2 w = __fmul2_rn(smu, f2(dx));
+  const float2 nw = make_float2(-w.x, -w.y), nsc = make_float2(-sc.x, -sc.y);
+  const float2 A = __ffma2_rn(nw, w, f2(1.f));                   // 1 - w^2
+  const float2 B = __ffma2_rn(nw, __fadd2_rn(f2(rp), nsc), f2(rn));  // rn - w (rp - sc)
+  const float2 C = __fmul2_rn(sc, __ffma2_rn(f2(2.f), f2(rp), nsc));  // sc (2 rp - sc)
+  const float2 r = make_float2(__fdividef(1.f, B.x), __fdividef(1.f, B.y));
+  const float2 Cr = __fmul2_rn(C, r);
+  const float2 h = __fmul2_rn(Cr, f2(0.5f));
+  const float2 eps = __fmul2_rn(__fmul2_rn(A, Cr), r);
+  const float2 poly = __ffma2_rn(eps, f2(0.125f), f2(0.25f));
+  const float2 ndl = __ffma2_rn(h, __fmul2_rn(eps, poly), h);  // -delta
+  const float2 th = __fadd2_rn(f2(thc), ndl);
+  const float2 X = __ffma2_rn(th, f2(dx), f2(x0));
+  const float2 V = __ffma2_rn(th, f2(dv), f2(v0));
+  const float2 Ac = __ffma2_rn(th, f2(da), f2(a0));
+  Xp = X.x;
+  Xm = X.y;
+  Vp = V.x;
+  Vm = V.y;
+  Ap = Ac.x;
+  Am = Ac.y;
+  dp = -ndl.x;
+  dm = -ndl.y;
+  const float2 td = __fadd2_rn(th, f2(-0.5f));
+  const float tdev = fmaxf(fabsf(td.x), fabsf(td.y));
+  const float edev = fmaxf(fabsf(eps.x), fabsf(eps.y));
+  return tdev <= 0.5f + kExtrap && edev < 1e-2f;
+}
+
 // Net field q [F(x+) - F(x-)] of a dipole's two charges, added to acc[10] = (E, B, phi, A), in
 // units of k_e e / L^2 (E), k_e e / (L^2 c) (B), k_e e / L (phi), k_e e / (L c) (A), qs = q / e.
 // Per charge: E = C_a a + C_p p, B = (C_p / R) (rho x p), phi = 1/R_u, A = v p / R_u with
 // a = rho - s p, R_u = R - v a.p, G = 1 - v^2 + alpha a.p, C_a = G / R_u^3,
 // C_p = -R v G / R_u^3 - alpha R / R_u^2; the differences of C_a, C_p, C_p / R, 1/R_u and v/R_u
 // are formed from the differences of their inputs (dR = delta+ - delta-, ds, dv, dalpha).
-template <int KIND, typename T>
+// CHECK_REX = false: the caller guarantees both charges farther than rex from the point.
+template <int KIND, typename T, bool CHECK_REX = true>
 __device__ __forceinline__ void dipole_pair(T rx, T ry, T rz, T rn, T px, T py, T pz, T rp, T mup, T mum, T qs, T Xp,
                                             T Vp, T Ap, T dp, T Xm, T Vm, T Am, T dm, T rex, T *acc,
                                             uint8_t &mask) {
@@ -227,7 +273,7 @@ __device__ __forceinline__ void dipole_pair(T rx, T ry, T rz, T rn, T px, T py, 
   const T v1 = mup * Vp, v0 = -mum * Vm, dv = mup * Vp + mum * Vm;
   const T a1 = mup * Ap, a0 = -mum * Am, da = mup * Ap + mum * Am;
   const T R0 = rn + dm, dR = dp - dm, R1 = R0 + dR;
-  if (R0 <= rex || R1 <= rex) {
+  if (CHECK_REX && (R0 <= rex || R1 <= rex)) {
     mask = 1;
     // one charge coincides with the point: add the other one alone
     const bool use1 = R1 > rex;

@@ -132,3 +132,100 @@ def test_adjoint_argument_errors(ctx):
         pc.pc_dipoles_adjoint(ctx, dp, cfg.dt, 0, w)
     with pytest.raises(pc.PcError):
         pc.pc_dipoles_adjoint(ctx, dp, -1.0, 50, w)
+
+
+# ---- gradients of the fitted decay rate and frequency (Eq. KE fit after the run) ----
+
+def _rates_cfg(B, seed=W.SEED_ADJ + 7):
+    # strongly coupled enough (q = 10e, >= 30 nm) that the fitted rates move with the geometry;
+    # 8000 steps, fit from step 1000 (two kinetic-energy minima per period of 5000 steps)
+    return W.adjoint_cluster(B=B, N=2, n_steps=8000, spacing=30e-9, charge=10.0, first_index=1000, seed=seed)
+
+
+def _rates_loss_gpu(ctx, cfg, wg, ww):
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=pc.PC_F64, fit=True,
+                            first_index=cfg.first_index, want_energy=False)
+    return float((out["gamma"].cpu().numpy() * wg).sum() + (out["omega"].cpu().numpy() * ww).sum())
+
+
+def _rates_loss_oracle(cfg, wg, ww):
+    from oracle import fit
+
+    tot = 0.0
+    for b in range(cfg.B):
+        r = oracle.dipoles_run(cfg, b=b)
+        assert r["status"] == oracle.OK
+        for i in range(cfg.N):
+            m = cfg.m1[b, i] * cfg.m2[b, i] / (cfg.m1[b, i] + cfg.m2[b, i])
+            ke = m * r["d_dot"][i] ** 2 / (2 * cfg.q[b, i] ** 2)
+            f = fit.ke_fit(ke, cfg.dt, cfg.first_index)
+            tot += wg[b, i] * f["gamma"] + ww[b, i] * f["omega"]
+    return tot
+
+
+def _rates_weights(cfg, seed):
+    rng = np.random.default_rng(seed)
+    from oracle import theory as th
+
+    g0 = th.gamma0(cfg.q[0, 0], cfg.m1[0, 0] / 2, cfg.omega0[0, 0])
+    # cotangents that weigh gamma and omega alike in units of gamma0
+    return rng.uniform(0.5, 1.5, size=(cfg.B, cfg.N)) / g0, rng.uniform(-1.5, 1.5, size=(cfg.B, cfg.N)) / g0
+
+
+def _rates_adjoint(ctx, cfg, wg, ww):
+    dp = pc.lo_config_to_device(cfg)
+    gam, om, go, gw, gd = pc.pc_dipoles_rates_adjoint(ctx, dp, cfg.dt, cfg.n_steps, cfg.first_index,
+                                                      torch.tensor(wg, device="cuda"),
+                                                      torch.tensor(ww, device="cuda"))
+    return {"origin": go.cpu().numpy(), "omega0": gw.cpu().numpy(), "d0": gd.cpu().numpy()}, gam, om
+
+
+def _rates_steps(cfg):
+    return {"origin": 6e-13, "omega0": 1e-7 * float(cfg.omega0.mean()), "d0": 1e-6 * float(cfg.d0.mean())}
+
+
+def test_rates_adjoint_vs_gpu_finite_differences(ctx):
+    cfg = _rates_cfg(B=2)
+    wg, ww = _rates_weights(cfg, 11)
+    g, gam, om = _rates_adjoint(ctx, cfg, wg, ww)
+    # the fitted values returned by the adjoint are those of the plain run with fit
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=pc.PC_F64, fit=True,
+                            first_index=cfg.first_index, want_energy=False)
+    assert torch.equal(gam, out["gamma"]) and torch.equal(om, out["omega"])
+    hs = _rates_steps(cfg)
+    for name in ("origin", "omega0", "d0"):
+        arr = getattr(cfg, name)
+        fd = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            h = hs[name]
+            fd[idx] = (_rates_loss_gpu(ctx, _perturbed(cfg, name, idx, h), wg, ww) -
+                       _rates_loss_gpu(ctx, _perturbed(cfg, name, idx, -h), wg, ww)) / (2 * h)
+        _check(g[name], fd, 1e-4)
+
+
+def test_rates_adjoint_vs_oracle_finite_differences(ctx):
+    cfg = _rates_cfg(B=1, seed=W.SEED_ADJ + 8)
+    wg, ww = _rates_weights(cfg, 12)
+    g, _, _ = _rates_adjoint(ctx, cfg, wg, ww)
+    hs = _rates_steps(cfg)
+    for name in ("origin", "omega0", "d0"):
+        arr = getattr(cfg, name)
+        fd = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            h = hs[name]
+            fd[idx] = (_rates_loss_oracle(_perturbed(cfg, name, idx, h), wg, ww) -
+                       _rates_loss_oracle(_perturbed(cfg, name, idx, -h), wg, ww)) / (2 * h)
+        _check(g[name], fd, 1e-4)
+
+
+def test_fitted_rates_autograd(ctx):
+    cfg = _rates_cfg(B=1, seed=W.SEED_ADJ + 9)
+    dp = pc.lo_config_to_device(cfg)
+    for t in (dp.origin, dp.omega0, dp.d0):
+        t.requires_grad_(True)
+    gam, om = pc.fitted_rates(ctx, dp, cfg.dt, cfg.n_steps, cfg.first_index)
+    wg, ww = _rates_weights(cfg, 13)
+    (gam * torch.tensor(wg, device="cuda") + om * torch.tensor(ww, device="cuda")).sum().backward()
+    g, _, _ = _rates_adjoint(ctx, cfg, wg, ww)
+    assert np.allclose(dp.origin.grad.cpu().numpy(), g["origin"], rtol=1e-12, atol=0)
+    assert np.allclose(dp.omega0.grad.cpu().numpy(), g["omega0"], rtol=1e-12, atol=0)

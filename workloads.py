@@ -293,13 +293,14 @@ def cfg5(N: int = 4096, n_steps: int = 20000, side: float = 600e-9, min_spacing:
 
 
 def adjoint_cluster(B: int = 2, N: int = 3, n_steps: int = 3000, spacing: float = 6e-9, seed: int = SEED_ADJ,
-                    margin: float = 0.08) -> LOConfig:
+                    margin: float = 0.08, charge: float = 1.0, first_index: int = 0) -> LOConfig:
     """B clusters of N LOs (random axes, omega0 = 2 pi 200 THz +-1%, r_dip0 = 10 pm) for gradient
     checks.  Pair distances are drawn so that no retarded time sits within `margin` steps of a
     history sample at the whole- or half-step stage times: a centre-to-centre delay tau (steps)
     with frac(tau) and frac(tau + 1/2) both farther than `margin` from an integer.  The charges
     move by at most r_dip0/(c dt) = 0.033 steps, so finite-difference steps of the inputs do not
-    cross the kinks of the piecewise-linear history."""
+    cross the kinks of the piecewise-linear history.  charge scales q (in units of e; the
+    radiative decay rate grows as q^2), first_index is the first fitted step."""
     rng = np.random.default_rng(seed)
     dt = 1e-18
     L = C * dt
@@ -316,4 +317,4 @@ def adjoint_cluster(B: int = 2, N: int = 3, n_steps: int = 3000, spacing: float 
         origins[b] = pts
     axes = unit_vectors(rng, B * N).reshape(B, N, 3)
     om = 2 * math.pi * 200e12 * (1.0 + rng.uniform(-0.01, 0.01, size=(B, N)))
-    return lo_batch(origins, axes, om, 1e-11, dt, n_steps, 0)
+    return lo_batch(origins, axes, om, 1e-11, dt, n_steps, first_index, q=charge * E_CHARGE)
