@@ -188,3 +188,20 @@ def lienard_power_circular(q, speed, accel):
     """Lienard's generalisation for v perpendicular to a: P = q^2 gamma^4 a^2 / (6 pi eps0 c^3)."""
     g2 = 1.0 / (1.0 - (speed / C) ** 2)
     return q * q * g2 * g2 * accel * accel / (6.0 * math.pi * EPS0 * C ** 3)
+
+
+def populations(t, gamma0, gamma12, delta12):
+    """Excited-state populations (rho_aa, rho_bb) of two identical coupled dipoles, dipole a
+    excited at t = 0 (App. A, Eqs. rho_aa and rho_bb): a quarter of the sum of the superradiant
+    and subradiant decays, plus (a) or minus (b) their beating 2 cos(2 delta12 t) exp(-gamma0 t)."""
+    t = np.asarray(t, dtype=np.float64)
+    slow = np.exp(-(gamma0 - gamma12) * t)
+    fast = np.exp(-(gamma0 + gamma12) * t)
+    beat = 2.0 * np.cos(2.0 * delta12 * t) * np.exp(-gamma0 * t)
+    return 0.25 * (slow + fast + beat), 0.25 * (slow + fast - beat)
+
+
+def normalized_energy(energy):
+    """n_e(t) = E(t) / max E over both dipoles (Eq. ne_energy), energy [N][S]."""
+    e = np.asarray(energy, dtype=np.float64)
+    return e / np.max(e)

@@ -544,6 +544,94 @@ __device__ void fit_pass(const double *y, int64_t n, double dt, double T, double
   }
 }
 
+// Full-Hessian pass in the fit's scaled parameters x (A = A_g x0, gamma = x1 / T,
+// omega = omega_g + x2 / T, phi = x3; residuals r = (model - y) / A_g): out[0] = sum r^2,
+// out[1..10] = H = sum (J J^T + r d2r/dx2) (upper triangle, row-major), out[11..14] = J^T r.
+__device__ void fit_newton_pass(const double *y, int64_t n, double dt, double T, double Ag, double wg,
+                                const double x[4], double out[15]) {
+  for (int k = 0; k < 15; ++k) out[k] = 0.0;
+  const double A = Ag * x[0], g = x[1] / T, w = wg + x[2] / T, ph = x[3];
+  const double iA = 1.0 / Ag, iT = 1.0 / T;
+  const int64_t chunk = (n + kFitThreads - 1) / kFitThreads;
+  const int64_t i0 = (int64_t)threadIdx.x * chunk, i1 = min(n, i0 + chunk);
+  if (i0 >= i1) return;
+  double s, c, cw, sw;
+  sincos(w * ((double)i0 * dt) + ph, &s, &c);
+  sincos(w * dt, &sw, &cw);
+  double en = exp(-g * ((double)i0 * dt));
+  const double e1 = exp(-g * dt);
+  for (int64_t i = i0; i < i1; ++i) {
+    const double u = (double)i * dt * iT;  // tau / T
+    const double ss = s * s, s2 = 2.0 * s * c, c2 = c * c - s * s;
+    const double mA = A * en * iA;
+    const double r = (A * en * ss - y[i]) * iA;
+    double J[4], D[10];
+    J[0] = en * ss;
+    J[1] = -u * mA * ss;
+    J[3] = mA * s2;
+    J[2] = J[3] * u;
+    D[0] = 0.0;
+    D[1] = -u * en * ss;
+    D[2] = en * s2 * u;
+    D[3] = en * s2;
+    D[4] = mA * ss * u * u;
+    D[5] = -mA * s2 * u * u;
+    D[6] = -mA * s2 * u;
+    D[7] = 2.0 * mA * c2 * u * u;
+    D[8] = 2.0 * mA * c2 * u;
+    D[9] = 2.0 * mA * c2;
+    out[0] += r * r;
+    int idx = 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = p; q < 4; ++q, ++idx) out[1 + idx] += J[p] * J[q] + r * D[idx];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) out[11 + p] += J[p] * r;
+    const double s1 = s * cw + c * sw;
+    c = c * cw - s * sw;
+    s = s1;
+    en *= e1;
+  }
+}
+
+// Solves M z = rhs (4x4, M given as the upper triangle h[10] of a symmetric matrix) by Gaussian
+// elimination with partial pivoting; returns false for a singular matrix.
+__device__ bool solve4_sym(const double *h, const double *rhs_in, double *z) {
+  double M[4][4], rhs[4];
+  int idx = 0;
+  for (int p = 0; p < 4; ++p)
+    for (int q = p; q < 4; ++q, ++idx) M[p][q] = M[q][p] = h[idx];
+  for (int p = 0; p < 4; ++p) rhs[p] = rhs_in[p];
+  for (int cc = 0; cc < 4; ++cc) {
+    int best = cc;
+    for (int r = cc + 1; r < 4; ++r)
+      if (fabs(M[r][cc]) > fabs(M[best][cc])) best = r;
+    if (best != cc) {
+      for (int q = 0; q < 4; ++q) {
+        const double t = M[cc][q];
+        M[cc][q] = M[best][q];
+        M[best][q] = t;
+      }
+      const double t = rhs[cc];
+      rhs[cc] = rhs[best];
+      rhs[best] = t;
+    }
+    if (!(fabs(M[cc][cc]) > 0.0)) return false;
+    for (int r = cc + 1; r < 4; ++r) {
+      const double f = M[r][cc] / M[cc][cc];
+      for (int q = cc; q < 4; ++q) M[r][q] -= f * M[cc][q];
+      rhs[r] -= f * rhs[cc];
+    }
+  }
+  for (int cc = 3; cc >= 0; --cc) {
+    double t = rhs[cc];
+    for (int q = cc + 1; q < 4; ++q) t -= M[cc][q] * z[q];
+    z[cc] = t / M[cc][cc];
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kFitThreads) ke_fit_kernel(const FitArgs fa) {
   __shared__ double sh[16 * (kFitThreads / 32)];
   __shared__ double s_x[4], s_xt[4], s_par[4];
@@ -736,6 +824,33 @@ __global__ void __launch_bounds__(kFitThreads) ke_fit_kernel(const FitArgs fa) {
     __syncthreads();
     if (stop) break;
   }
+  // Newton steps with the full Hessian polish the optimum where LM slows down (the decay rate is
+  // weakly determined when gamma T is small): the gradient of the cost then vanishes to rounding,
+  // as the implicit-function derivative of the fit assumes
+  for (int it = 0; it < 2; ++it) {
+    double x[4] = {s_x[0], s_x[1], s_x[2], s_x[3]};
+    double hp[15];
+    fit_newton_pass(y, n, dt, T, Ag, wg, x, hp);
+    double h16[16];
+    for (int q = 0; q < 15; ++q) h16[q] = hp[q];
+    h16[15] = 0.0;
+    block_sum<16>(h16, sh);
+    if (threadIdx.x == 0) {
+      const double rhs[4] = {-h16[11], -h16[12], -h16[13], -h16[14]};
+      double dx[4];
+      s_flag = solve4_sym(h16 + 1, rhs, dx) ? 0 : 1;
+      for (int p = 0; p < 4; ++p) s_xt[p] = s_flag ? s_x[p] : s_x[p] + dx[p];
+    }
+    __syncthreads();
+    double xt[4] = {s_xt[0], s_xt[1], s_xt[2], s_xt[3]};
+    double c1[15];
+    fit_pass(y, n, dt, T, Ag, wg, xt, 0, c1);
+    double cc[1] = {c1[0]};
+    block_sum<1>(cc, sh);
+    if (threadIdx.x == 0 && !s_flag && cc[0] <= h16[0] * (1.0 + 1e-12) && cc[0] == cc[0])
+      for (int p = 0; p < 4; ++p) s_x[p] = s_xt[p];
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     const double A = Ag * s_x[0], g = s_x[1] / T, w = wg + s_x[2] / T, ph = s_x[3];
     if (fa.gamma) fa.gamma[k] = g;
@@ -790,91 +905,21 @@ __global__ void __launch_bounds__(kFitThreads) ke_fit_adjoint_kernel(const FitAd
   const int64_t n = fa.S - fa.first;
   const double dt = fa.dt, T = (double)(n - 1) * dt;
   const double A = fa.amp[k], g = fa.gamma[k], w = fa.omega[k], ph = fa.phase[k];
+  // scaled about the optimum itself: A_g = A, omega_g = omega, so x = (1, gamma T, 0, phi)
   const double Ag = A, iA = 1.0 / Ag, iT = 1.0 / T;
-  const int64_t chunk = (n + kFitThreads - 1) / kFitThreads;
-  const int64_t i0 = (int64_t)threadIdx.x * chunk, i1 = min(n, i0 + chunk);
-  double s = 0.0, c = 1.0, cw = 1.0, sw = 0.0, env = 1.0, e1 = 1.0;
-  if (i0 < i1) {
-    sincos(w * ((double)i0 * dt) + ph, &s, &c);
-    sincos(w * dt, &sw, &cw);
-    env = exp(-g * ((double)i0 * dt));
-    e1 = exp(-g * dt);
-  }
-  // pass 1: H (upper triangle, 10 values)
-  double h[10];
-  for (int q = 0; q < 10; ++q) h[q] = 0.0;
-  {
-    double ss_ = s, cc_ = c, en = env;
-    for (int64_t i = i0; i < i1; ++i) {
-      const double u = (double)i * dt * iT;  // tau / T
-      const double ss = ss_ * ss_, s2 = 2.0 * ss_ * cc_, c2 = cc_ * cc_ - ss_ * ss_;
-      const double mA = A * en * iA;         // model / (A_g sin^2)
-      const double r = (A * en * ss - y[i]) * iA;
-      double J[4], D[10];
-      J[0] = en * ss;
-      J[1] = -u * mA * ss;
-      J[3] = mA * s2;
-      J[2] = J[3] * u;
-      // second derivatives of r in the scaled parameters (upper triangle, row-major)
-      D[0] = 0.0;
-      D[1] = -u * en * ss;
-      D[2] = en * s2 * u;
-      D[3] = en * s2;
-      D[4] = mA * ss * u * u;
-      D[5] = -mA * s2 * u * u;
-      D[6] = -mA * s2 * u;
-      D[7] = 2.0 * mA * c2 * u * u;
-      D[8] = 2.0 * mA * c2 * u;
-      D[9] = 2.0 * mA * c2;
-      int idx = 0;
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = p; q < 4; ++q, ++idx) h[idx] += J[p] * J[q] + r * D[idx];
-      const double s1 = ss_ * cw + cc_ * sw;
-      cc_ = cc_ * cw - ss_ * sw;
-      ss_ = s1;
-      en *= e1;
-    }
-  }
+  const double x[4] = {1.0, g * T, 0.0, ph};
+  double hp[15];
+  fit_newton_pass(y, n, dt, T, Ag, w, x, hp);
   double h16[16];
-  for (int q = 0; q < 10; ++q) h16[q] = h[q];
-  for (int q = 10; q < 16; ++q) h16[q] = 0.0;
+  for (int q = 0; q < 15; ++q) h16[q] = hp[q];
+  h16[15] = 0.0;
   block_sum<16>(h16, sh);
   if (threadIdx.x == 0) {
-    double M[4][4], rhs[4] = {0.0, fa.dL_dgamma ? fa.dL_dgamma[k] * iT : 0.0,
-                              fa.dL_domega ? fa.dL_domega[k] * iT : 0.0, 0.0};
-    int idx = 0;
-    for (int p = 0; p < 4; ++p)
-      for (int q = p; q < 4; ++q, ++idx) M[p][q] = M[q][p] = h16[idx];
-    // Gaussian elimination with partial pivoting
-    s_bad = 0;
-    for (int cc = 0; cc < 4; ++cc) {
-      int best = cc;
-      for (int r = cc + 1; r < 4; ++r)
-        if (fabs(M[r][cc]) > fabs(M[best][cc])) best = r;
-      if (best != cc) {
-        for (int q = 0; q < 4; ++q) {
-          const double t = M[cc][q];
-          M[cc][q] = M[best][q];
-          M[best][q] = t;
-        }
-        const double t = rhs[cc];
-        rhs[cc] = rhs[best];
-        rhs[best] = t;
-      }
-      if (!(fabs(M[cc][cc]) > 0.0)) s_bad = 1;
-      for (int r = cc + 1; r < 4 && !s_bad; ++r) {
-        const double f = M[r][cc] / M[cc][cc];
-        for (int q = cc; q < 4; ++q) M[r][q] -= f * M[cc][q];
-        rhs[r] -= f * rhs[cc];
-      }
-    }
-    for (int cc = 3; cc >= 0 && !s_bad; --cc) {
-      double t = rhs[cc];
-      for (int q = cc + 1; q < 4; ++q) t -= M[cc][q] * s_z[q];
-      s_z[cc] = t / M[cc][cc];
-    }
+    const double rhs[4] = {0.0, fa.dL_dgamma ? fa.dL_dgamma[k] * iT : 0.0, fa.dL_domega ? fa.dL_domega[k] * iT : 0.0,
+                           0.0};
+    double z[4];
+    s_bad = solve4_sym(h16 + 1, rhs, z) ? 0 : 1;
+    for (int p = 0; p < 4; ++p) s_z[p] = s_bad ? 0.0 : z[p];
     if (s_bad) set_status(fa.status, PC_ERR_NOCONV);
   }
   __syncthreads();
@@ -884,18 +929,25 @@ __global__ void __launch_bounds__(kFitThreads) ke_fit_adjoint_kernel(const FitAd
   const double kv = m / (qq * qq);
   const double *ddk = fa.dd + (size_t)k * fa.S + fa.first;
   double *muk = fa.mu + ((size_t)k * fa.S + fa.first) * 3;
-  // pass 2: dL/dy_n = z . J_n / A_g, into the adjoint of d'_n
-  double ss_ = s, cc_ = c, en = env;
+  // dL/dy_n = z . J_n / A_g, into the adjoint of d'_n
+  const int64_t chunk = (n + kFitThreads - 1) / kFitThreads;
+  const int64_t i0 = (int64_t)threadIdx.x * chunk, i1 = min(n, i0 + chunk);
+  if (i0 >= i1) return;
+  double sn, cs, cw, sw;
+  sincos(w * ((double)i0 * dt) + ph, &sn, &cs);
+  sincos(w * dt, &sw, &cw);
+  double en = exp(-g * ((double)i0 * dt));
+  const double e1 = exp(-g * dt);
   for (int64_t i = i0; i < i1; ++i) {
     const double u = (double)i * dt * iT;
-    const double ss = ss_ * ss_, s2 = 2.0 * ss_ * cc_;
+    const double ss = sn * sn, s2 = 2.0 * sn * cs;
     const double mA = A * en * iA;
     const double J0 = en * ss, J1 = -u * mA * ss, J3 = mA * s2, J2 = J3 * u;
     const double dy = (z0 * J0 + z1 * J1 + z2 * J2 + z3 * J3) * iA;
     muk[3 * i + 1] += dy * kv * ddk[i];
-    const double s1 = ss_ * cw + cc_ * sw;
-    cc_ = cc_ * cw - ss_ * sw;
-    ss_ = s1;
+    const double s1 = sn * cw + cs * sw;
+    cs = cs * cw - sn * sw;
+    sn = s1;
     en *= e1;
   }
 }

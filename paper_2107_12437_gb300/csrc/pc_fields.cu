@@ -374,20 +374,36 @@ __device__ __forceinline__ void charge_mixed(float ax, float ay, float az, float
 }
 
 // Kahan-compensated running sums of the ten outputs; each thread's sums live in shared memory,
-// strided by the block size (they are touched once per group of sixteen sources).  Indexed from
-// the thread index directly, so no pointer stays live across the source loop.
-using KahanArr = float[2][10][kMixThreads];
-__device__ __forceinline__ void kahan_add(KahanArr &k, int tid, const float *part) {
+// strided by the block size (they are touched once per group of sixteen sources), as five packed
+// pairs: 0 (E_x, E_y), 1 (B_x, B_y), 2 (A_x, A_y), 3 (E_z, B_z), 4 (A_z, phi).  Indexed from the
+// thread index directly, so no pointer stays live across the source loop.
+using KahanArr = float2[2][5][kMixThreads];
+__device__ __forceinline__ void kahan_add(KahanArr &k, int tid, const float2 *P) {
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    const float s0 = k[0][i][tid], c0 = k[1][i][tid];
-    const float y = part[i] - c0;
-    const float t = s0 + y;
-    k[1][i][tid] = (t - s0) - y;
+  for (int i = 0; i < 5; ++i) {
+    const float2 s0 = k[0][i][tid], c0 = k[1][i][tid];
+    const float2 y = __fadd2_rn(P[i], make_float2(-c0.x, -c0.y));
+    const float2 t = __fadd2_rn(s0, y);
+    const float2 d = __fadd2_rn(t, make_float2(-s0.x, -s0.y));
+    k[1][i][tid] = __fadd2_rn(d, make_float2(-y.x, -y.y));
     k[0][i][tid] = t;
   }
 }
-__device__ __forceinline__ float kahan_get(const KahanArr &k, int tid, int i) { return k[0][i][tid] - k[1][i][tid]; }
+// the ten outputs in their natural order (E, B, phi, A) into the packed slots
+__device__ __forceinline__ void pack_outputs(const float *part, float2 (&P)[5]) {
+  P[0] = make_float2(part[0], part[1]);
+  P[1] = make_float2(part[3], part[4]);
+  P[2] = make_float2(part[7], part[8]);
+  P[3] = make_float2(part[2], part[5]);
+  P[4] = make_float2(part[9], part[6]);
+}
+__device__ __forceinline__ float kahan_get(const KahanArr &k, int tid, int i) {
+  // natural index -> (slot, lane)
+  const int slot[10] = {0, 0, 3, 1, 1, 3, 4, 2, 2, 4};
+  const int hi[10] = {0, 1, 0, 0, 1, 1, 1, 0, 1, 0};
+  const float2 sv = k[0][slot[i]][tid], cv = k[1][slot[i]][tid];
+  return hi[i] ? sv.y - cv.y : sv.x - cv.x;
+}
 
 template <int KIND, bool LIST>
 __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
@@ -431,9 +447,9 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   __syncthreads();
   const int64_t pp = active ? p : 0;
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    s_kahan[0][i][tid] = 0.f;
-    s_kahan[1][i][tid] = 0.f;
+  for (int i = 0; i < 5; ++i) {
+    s_kahan[0][i][tid] = make_float2(0.f, 0.f);
+    s_kahan[1][i][tid] = make_float2(0.f, 0.f);
   }
   uint8_t mask = 0;
   int err = 0;
@@ -480,9 +496,9 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       }
       __syncthreads();
       if (!active || err) continue;
-      float part[10];
+      float2 P[5];
 #pragma unroll
-      for (int i = 0; i < 10; ++i) part[i] = 0.f;
+      for (int i = 0; i < 5; ++i) P[i] = make_float2(0.f, 0.f);
       unsigned long long slow_mask = 0ull;
       for (int g16 = 0; g16 < nch; g16 += 16) {
       // groups of sixteen sources summed in float32, the group sums compensated
@@ -523,7 +539,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
         // farther than rex + 1.5 samples from the centre (the charges are then farther than rex:
         // their distances differ from rn by |delta| <= 1.1); a garbage index from a huge or NaN xc
         // fails the range test before any load
-        float Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
+        float2 X, V, Ac, dl;
         bool fast = false;
         {
           float fl;
@@ -534,23 +550,23 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
             float x0, v0, a0, x1, v1, a1;
             H.get_in(j, x0, v0, a0);
             H.get_in(j + 1, x1, v1, a1);
-            fast = dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, mu.x, mu.y, Xp, Vp, Ap, dp, Xm, Vm, Am,
-                                        dm);
+            fast = dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, mu.x, mu.y, X, V, Ac, dl);
           }
         }
         // near fields that cancel in float32 also leave the fast path
-        if (fast && rn < kNearL && dipole_cancellation<float>(rn, mu.x, mu.y, Xp, Vp, Ap, Xm, Vm, Am) > kCancel)
+        if (fast && rn < kNearL &&
+            dipole_cancellation<float>(rn, mu.x, mu.y, X.x, V.x, Ac.x, X.y, V.y, Ac.y) > kCancel)
           fast = false;
         if (!fast) {
           slow_mask |= 1ull << jj;
           continue;
         }
-        dipole_pair<KIND, float, false>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mu.x, mu.y, ax.w, Xp, Vp, Ap, dp, Xm, Vm,
-                                        Am, dm, rex, part, mask);
+        dipole_pair_fast<KIND>(make_float2(rx, ry), rz, rn, make_float2(ax.x, ax.y), ax.z, rp, mu.x, mu.y, ax.w, X, V,
+                               Ac, dl, P);
       }
-      kahan_add(s_kahan, tid, part);
+      kahan_add(s_kahan, tid, P);
 #pragma unroll
-      for (int i = 0; i < 10; ++i) part[i] = 0.f;
+      for (int i = 0; i < 5; ++i) P[i] = make_float2(0.f, 0.f);
       }
       // the pairs of this chunk that left the fast path
       while (slow_mask && !err) {
@@ -589,7 +605,9 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
                                         rp64, (L.times[f] - s.t0d) / s.dtd, kC * s.dtd, L.r_excl, sp, &smask);
         if (e) err = e;
         mask |= smask;
-        kahan_add(s_kahan, tid, sp);
+        float2 SP[5];
+        pack_outputs(sp, SP);
+        kahan_add(s_kahan, tid, SP);
       }
     }
   }
@@ -723,12 +741,16 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
 #pragma unroll
         for (int i = 6; i < 10; ++i) part[i] += sP * c10[i];
         if ((cc & 15) == 15) {
-          kahan_add(s_kahan, tid, part);
+          float2 PP[5];
+          pack_outputs(part, PP);
+          kahan_add(s_kahan, tid, PP);
 #pragma unroll
           for (int i = 0; i < 10; ++i) part[i] = 0.f;
         }
       }
-      kahan_add(s_kahan, tid, part);
+      float2 PP[5];
+      pack_outputs(part, PP);
+      kahan_add(s_kahan, tid, PP);
     }
   }
   if (!active) return;

@@ -221,16 +221,15 @@ __device__ __forceinline__ bool dip_pair_states(T x0, T v0, T a0, T x1, T v1, T 
 // one instruction issue for both charges).
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 __device__ __forceinline__ bool dip_pair_states_fast(float x0, float v0, float a0, float x1, float v1, float a1,
-                                                     float thc, float rn, float rp, float mup, float mum, float &Xp,
-                                                     float &Vp, float &Ap, float &dp, float &Xm, float &Vm,
-                                                     float &Am, float &dm) {
+                                                     float thc, float rn, float rp, float mup, float mum, float2 &X,
+                                                     float2 &V, float2 &Ac, float2 &dl) {
   const float dx = x1 - x0, dv = v1 - v0, da = a1 - a0;
   const float Xc = x0 + thc * dx;
   const float2 smu = make_float2(mup, -mum);  // (positive charge, negative charge)
   const float2 sc = __fmul2_rn(smu, f2(Xc));
   const float2 w = __fmul2_rn(smu, f2(dx));
   const float2 nw = make_float2(-w.x, -w.y), nsc = make_float2(-sc.x, -sc.y);
-  const float2 A = __ffma2_rn(nw, w, f2(1.f));                   // 1 - w^2
+  const float2 A = __ffma2_rn(nw, w, f2(1.f));                       // 1 - w^2
   const float2 B = __ffma2_rn(nw, __fadd2_rn(f2(rp), nsc), f2(rn));  // rn - w (rp - sc)
   const float2 C = __fmul2_rn(sc, __ffma2_rn(f2(2.f), f2(rp), nsc));  // sc (2 rp - sc)
   const float2 r = make_float2(__fdividef(1.f, B.x), __fdividef(1.f, B.y));
@@ -240,21 +239,75 @@ __device__ __forceinline__ bool dip_pair_states_fast(float x0, float v0, float a
   const float2 poly = __ffma2_rn(eps, f2(0.125f), f2(0.25f));
   const float2 ndl = __ffma2_rn(h, __fmul2_rn(eps, poly), h);  // -delta
   const float2 th = __fadd2_rn(f2(thc), ndl);
-  const float2 X = __ffma2_rn(th, f2(dx), f2(x0));
-  const float2 V = __ffma2_rn(th, f2(dv), f2(v0));
-  const float2 Ac = __ffma2_rn(th, f2(da), f2(a0));
-  Xp = X.x;
-  Xm = X.y;
-  Vp = V.x;
-  Vm = V.y;
-  Ap = Ac.x;
-  Am = Ac.y;
-  dp = -ndl.x;
-  dm = -ndl.y;
+  X = __ffma2_rn(th, f2(dx), f2(x0));
+  V = __ffma2_rn(th, f2(dv), f2(v0));
+  Ac = __ffma2_rn(th, f2(da), f2(a0));
+  dl = make_float2(-ndl.x, -ndl.y);
   const float2 td = __fadd2_rn(th, f2(-0.5f));
   const float tdev = fmaxf(fabsf(td.x), fabsf(td.y));
   const float edev = fmaxf(fabsf(eps.x), fabsf(eps.y));
   return tdev <= 0.5f + kExtrap && edev < 1e-2f;
+}
+
+// dipole_pair (CHECK_REX = false) for the float32 fast path with both charges in float2 lanes,
+// (positive, negative), and the ten outputs in five packed accumulators:
+//   P[0] = (E_x, E_y), P[1] = (B_x, B_y), P[2] = (A_x, A_y), P[3] = (E_z, B_z), P[4] = (A_z, phi).
+// Same algebra and units as dipole_pair.
+template <int KIND>
+__device__ __forceinline__ void dipole_pair_fast(float2 rxy, float rz, float rn, float2 pxy, float pz, float rp,
+                                                 float mup, float mum, float qs, float2 X, float2 V, float2 Ac,
+                                                 float2 dl, float2 (&P)[5]) {
+  const float2 mu2 = make_float2(mup, -mum);
+  const float2 s = __fmul2_rn(mu2, X);   // (s1, s0): charge offsets along the axis
+  const float2 v = __fmul2_rn(mu2, V);   // (v1, v0)
+  const float2 al = __fmul2_rn(mu2, Ac);  // (a1, a0)
+  const float ds = mup * X.x + mum * X.y, dv = mup * V.x + mum * V.y, da = mup * Ac.x + mum * Ac.y;
+  const float2 R = __fadd2_rn(f2(rn), dl);  // (R1, R0)
+  const float dR = dl.x - dl.y;
+  const float2 ap = __fadd2_rn(f2(rp), make_float2(-s.x, -s.y));  // (ap1, ap0)
+  const float2 Ru = __ffma2_rn(make_float2(-v.x, -v.y), ap, R);   // (Ru1, Ru0)
+  const float dRu = dR - (dv * ap.x - v.y * ds);
+  const float2 i = make_float2(__fdividef(1.f, Ru.x), __fdividef(1.f, Ru.y));  // (i1, i0)
+  const float2 i2 = __fmul2_rn(i, i);
+  const float2 i3 = __fmul2_rn(i2, i);
+  const float di = -dRu * i.y * i.x;
+  const float di2 = di * (i.x + i.y);
+  const float di3 = di * (i2.x + i.x * i.y + i2.y);
+  const float v0 = v.y, a0 = al.y, ap0 = ap.y, R0 = R.y;
+  float G0 = 0.f, dG = 0.f;
+  if (KIND != PC_RADIATION) {
+    G0 += 1.f - v0 * v0;
+    dG += -dv * (v.x + v0);
+  }
+  if (KIND != PC_COULOMB) {
+    G0 += a0 * ap0;
+    dG += da * ap.x - a0 * ds;
+  }
+  const float G1 = G0 + dG;
+  const float2 Ca = __fmul2_rn(make_float2(G1, G0), i3);  // (Ca1, Ca0)
+  const float dCa = dG * i3.x + G0 * di3;
+  const float P0 = R0 * v0 * G0;
+  const float dvG = dv * G1 + v0 * dG;
+  const float dP = dR * v.x * G1 + R0 * dvG;
+  float dCp = -(dP * i3.x + P0 * di3);
+  float dBc = -(dvG * i3.x + v0 * G0 * di3);
+  if (KIND != PC_COULOMB) {
+    const float Q0 = a0 * R0, dQ = da * R.x + a0 * dR;
+    dCp -= dQ * i2.x + Q0 * di2;
+    dBc -= da * i2.x + a0 * di2;
+  }
+  const float2 Cs = __fmul2_rn(Ca, s);
+  const float ep = dCp - (Cs.x - Cs.y);
+  const float cE = qs * dCa, cP = qs * ep, cB = qs * dBc;
+  const float cx = rxy.y * pz - rz * pxy.y, cy = rz * pxy.x - rxy.x * pz, cz = rxy.x * pxy.y - rxy.y * pxy.x;
+  const float dA = qs * (dv * i.x + v0 * di);
+  P[0] = __ffma2_rn(f2(cE), rxy, P[0]);
+  P[0] = __ffma2_rn(f2(cP), pxy, P[0]);
+  P[1] = __ffma2_rn(f2(cB), make_float2(cx, cy), P[1]);
+  P[2] = __ffma2_rn(f2(dA), pxy, P[2]);
+  P[3] = __ffma2_rn(make_float2(cE, cB), make_float2(rz, cz), P[3]);
+  P[3].x = fmaf(cP, pz, P[3].x);
+  P[4] = __ffma2_rn(make_float2(dA, qs), make_float2(pz, di), P[4]);
 }
 
 // Net field q [F(x+) - F(x-)] of a dipole's two charges, added to acc[10] = (E, B, phi, A), in

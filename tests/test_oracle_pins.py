@@ -494,3 +494,32 @@ def test_scale_outputs_bound_the_superposition():
     orad = oracle.fields(pts1, [1e-14], charges=ch1, kind=oracle.RADIATION)
     ecr = np.linalg.norm(oc["E"][0], axis=-1) + np.linalg.norm(orad["E"][0], axis=-1)
     assert np.allclose(o1["scale_charge"]["E"][0], ecr, rtol=1e-14)
+
+
+def test_populations_solve_the_density_matrix_equations():
+    # Eq. DM in the dressed basis, integrated numerically from rho_aa(0) = 1: rho_++ = rho_-- =
+    # rho_+- = rho_-+ = 1/2 (|+-> = (|e_a g_b> +- |g_a e_b>)/sqrt 2), and
+    # rho_aa = <sigma_a^+ sigma_a^-> = (rho_++ + rho_-- + rho_+- + rho_-+)/2,
+    # rho_bb = (rho_++ + rho_-- - rho_+- - rho_-+)/2
+    from scipy.integrate import solve_ivp
+
+    g0, g12, d12 = 1.0, 0.83, 7.3
+
+    def rhs(t, y):
+        pp, mm, pm_re, pm_im = y
+        pm = pm_re + 1j * pm_im
+        dpm = -(g0 + 2j * d12) * pm
+        return [-(g0 + g12) * pp, -(g0 - g12) * mm, dpm.real, dpm.imag]
+
+    ts = np.linspace(0.0, 3.0, 61)
+    sol = solve_ivp(rhs, (0.0, 3.0), [0.5, 0.5, 0.5, 0.0], t_eval=ts, rtol=1e-12, atol=1e-14)
+    pp, mm, pm_re = sol.y[0], sol.y[1], sol.y[2]
+    raa_num = 0.5 * (pp + mm + 2.0 * pm_re)
+    rbb_num = 0.5 * (pp + mm - 2.0 * pm_re)
+    raa, rbb = th.populations(ts, g0, g12, d12)
+    assert np.max(np.abs(raa - raa_num)) < 1e-9
+    assert np.max(np.abs(rbb - rbb_num)) < 1e-9
+    assert raa[0] == pytest.approx(1.0) and rbb[0] == pytest.approx(0.0, abs=1e-15)
+    # the limit of very small separations, gamma12 -> gamma0 (App. A)
+    raa0, _ = th.populations(ts, g0, g0, d12)
+    assert np.allclose(raa0, 0.25 * (1 + np.exp(-2 * g0 * ts) + 2 * np.cos(2 * d12 * ts) * np.exp(-g0 * ts)))

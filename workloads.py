@@ -318,3 +318,13 @@ def adjoint_cluster(B: int = 2, N: int = 3, n_steps: int = 3000, spacing: float 
     axes = unit_vectors(rng, B * N).reshape(B, N, 3)
     om = 2 * math.pi * 200e12 * (1.0 + rng.uniform(-0.01, 0.01, size=(B, N)))
     return lo_batch(origins, axes, om, 1e-11, dt, n_steps, first_index, q=charge * E_CHARGE)
+
+
+def population_pair(n_steps: int = 2_100_000, dt: float = 1e-17, r_dip: float = 1e-11, sep: float = 80e-9):
+    """Two s dipoles (moments along y, separated along x by 80 nm), q = 20 e, m1 = m2 = m_e,
+    omega0 = 2 pi 200 THz; dipole a starts with moment q r_dip, dipole b at rest with none."""
+    origins = np.array([[[0.0, 0.0, 0.0], [sep, 0.0, 0.0]]])
+    axes = np.array([[[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]])
+    cfg = lo_batch(origins, axes, 2 * math.pi * 200e12, r_dip, dt, n_steps, 0, q=20 * E_CHARGE)
+    cfg.d0[0, 1] = 0.0
+    return cfg
