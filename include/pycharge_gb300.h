@@ -175,6 +175,26 @@ typedef struct {
 pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                          const pc_run_out *out, void *stream);
 
+/* Moving dipoles (Sec. 4.3): the origin of every dipole as a function of time, sampled at the half
+ * steps t = h dt / 2, h = 0 .. 2 n_steps, device [B][N][2 n_steps + 1][3] each (m, m/s, m/s^2). */
+typedef struct {
+  const double *pos, *vel, *acc;
+} pc_dipole_motion;
+
+/*
+ * pc_dipoles_run_moving -- pc_dipoles_run with moving origins (Sec. 4.3), float64 only.
+ * The driving field of each RK4 stage is evaluated at the receiver's origin at that stage's time
+ * (half-step samples 2n, 2n+1, 2n+2); each source charge sits at its origin plus its offset along
+ * the axis, with the origin's whole-step samples (even h) joining the moment in the linearly
+ * interpolated history (Sec. 3.1) and adding its velocity and acceleration to the charge's; for
+ * t <= 0 the origins rest at their first sample.  dp->origin holds the origins at t = 0 (the
+ * first samples of pos); the causal block length accounts for the closest approach of the origins
+ * over the run and their largest speed.
+ * Errors: those of pc_dipoles_run; PC_ERR_ARG for opts->precision other than PC_F64.
+ */
+pc_status pc_dipoles_run_moving(pc_ctx *ctx, const pc_dipoles *dp, const pc_dipole_motion *motion, double dt,
+                                int64_t n_steps, const pc_run_opts *opts, const pc_run_out *out, void *stream);
+
 /*
  * pc_ke_fit -- Levenberg-Marquardt fit of Eq. KE (Sec. 2.4) to K series of kinetic energies.
  *   ke        device [K][S] samples at spacing dt; samples first_index..S-1 are fitted

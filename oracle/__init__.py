@@ -51,6 +51,7 @@ class _Sources(ctypes.Structure):
         ("N", ctypes.c_int32), ("Sd", ctypes.c_int64), ("t0d", ctypes.c_double), ("dtd", ctypes.c_double),
         ("origin", _P), ("axis", _P), ("qd", _P), ("m1", _P), ("m2", _P),
         ("d", _P), ("d_dot", _P), ("d_ddot", _P), ("last_valid", ctypes.c_int64),
+        ("org_pos", _P), ("org_vel", _P), ("org_acc", _P),
     ]
 
 
@@ -66,6 +67,7 @@ def lib():
         _lib.orc_fields.restype = ctypes.c_int
         _lib.orc_retarded_delay.restype = ctypes.c_int
         _lib.orc_dipoles_run.restype = ctypes.c_int
+        _lib.orc_dipoles_run_moving.restype = ctypes.c_int
     return _lib
 
 
@@ -166,10 +168,11 @@ def lw_griffiths(q, aR, v, acc):
     return E, B
 
 
-def dipoles_run(cfg, b=0, n_steps=None, ed_mode=0, v_max=None, nthreads=0):
+def dipoles_run(cfg, b=0, n_steps=None, ed_mode=0, v_max=None, nthreads=0, motion=None):
     """Algorithm 1 for configuration b of a workloads.LOConfig.
 
-    Returns dict d, d_dot, d_ddot, energy, Ed [N][n_steps+1] and status.
+    motion: optional (pos, vel, acc) [B][N][2 n_steps + 1][3] origin trajectories at the half steps
+    (moving dipoles, Sec. 4.3).  Returns dict d, d_dot, d_ddot, energy, Ed [N][n_steps+1] and status.
     """
     from workloads import C as _c
 
@@ -183,9 +186,14 @@ def dipoles_run(cfg, b=0, n_steps=None, ed_mode=0, v_max=None, nthreads=0):
     ddd = np.zeros((N, S))
     en = np.zeros((N, S))
     Ed = np.zeros((N, S))
-    st = lib().orc_dipoles_run(
+    mo = [None, None, None]
+    if motion is not None:
+        H = 2 * n_steps + 1
+        mo = [keep(np.asarray(x)[b, :, :H]) for x in motion]
+    st = lib().orc_dipoles_run_moving(
         ctypes.c_int32(N), _ptr(keep(cfg.origin[b])), _ptr(keep(cfg.axis[b])), _ptr(keep(cfg.q[b])),
         _ptr(keep(cfg.m1[b])), _ptr(keep(cfg.m2[b])), _ptr(keep(cfg.omega0[b])), _ptr(keep(cfg.d0[b])),
+        _ptr(mo[0]), _ptr(mo[1]), _ptr(mo[2]),
         ctypes.c_double(cfg.dt), ctypes.c_int64(n_steps), ctypes.c_double(v_max), ctypes.c_int32(ed_mode),
         _ptr(d), _ptr(dd), _ptr(ddd), _ptr(en), _ptr(Ed), ctypes.c_int32(nthreads))
     return dict(d=d, d_dot=dd, d_ddot=ddd, energy=en, Ed=Ed, status=st)

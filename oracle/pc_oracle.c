@@ -66,6 +66,9 @@ typedef struct {
   const double *qd, *m1, *m2;  /* [N] charge magnitude and the two masses */
   const double *d, *d_dot, *d_ddot; /* [N][Sd] moment along axis, C m, and its derivatives */
   int64_t last_valid;          /* dipole samples 0..last_valid are known; -1 = all */
+  /* moving dipoles (Sec. 4.3): origin position, velocity and acceleration at the half steps
+   * t0d + h dtd / 2, h = 0 .. 2 Sd - 2, [N][2 Sd - 1][3]; NULL for fixed origins */
+  const double *org_pos, *org_vel, *org_acc;
 } orc_sources;
 
 static inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -121,6 +124,14 @@ static int charge_state(const orc_sources *s, int c, double tp, double *qc, doub
   const double *D = s->d + (int64_t)j * s->Sd;
   const double *DV = s->d_dot + (int64_t)j * s->Sd;
   const double *DA = s->d_ddot + (int64_t)j * s->Sd;
+  /* a moving origin: the history holds the whole-step samples (even half-step indices), linearly
+   * interpolated like every other history (Sec. 3.1); at rest at its first position for t <= t0 */
+  double Rm[3] = {R[0], R[1], R[2]}, Rv[3] = {0.0, 0.0, 0.0}, Ra[3] = {0.0, 0.0, 0.0};
+  const int64_t H = 2 * s->Sd - 1;
+  if (s->org_pos) {
+    const double *OP = s->org_pos + (int64_t)j * H * 3;
+    for (int i = 0; i < 3; ++i) Rm[i] = OP[i];
+  }
   if (x <= 0.0) {
     /* stationary dipole moment for t <= t0 (Sec. 3.2) */
     dd = D[0]; dv = 0.0; da = 0.0;
@@ -136,14 +147,24 @@ static int charge_state(const orc_sources *s, int c, double tp, double *qc, doub
     dd = D[k] + th * (D[k + 1] - D[k]);
     dv = DV[k] + th * (DV[k + 1] - DV[k]);
     da = DA[k] + th * (DA[k + 1] - DA[k]);
+    if (s->org_pos) {
+      const double *OP = s->org_pos + ((int64_t)j * H + 2 * k) * 3;
+      const double *OV = s->org_vel + ((int64_t)j * H + 2 * k) * 3;
+      const double *OA = s->org_acc + ((int64_t)j * H + 2 * k) * 3;
+      for (int i = 0; i < 3; ++i) {
+        Rm[i] = OP[i] + th * (OP[6 + i] - OP[i]);
+        Rv[i] = OV[i] + th * (OV[6 + i] - OV[i]);
+        Ra[i] = OA[i] + th * (OA[6 + i] - OA[i]);
+      }
+    }
   }
   /* r_dip = d / q along the axis; r_1 = R + m2/(m1+m2) r_dip, r_2 = R - m1/(m1+m2) r_dip */
   double w = neg ? -m1 / (m1 + m2) : m2 / (m1 + m2);
   *qc = neg ? -q : q;
   for (int i = 0; i < 3; ++i) {
-    p[i] = R[i] + w * (dd / q) * u[i];
-    v[i] = w * (dv / q) * u[i];
-    a[i] = w * (da / q) * u[i];
+    p[i] = Rm[i] + w * (dd / q) * u[i];
+    v[i] = Rv[i] + w * (dv / q) * u[i];
+    a[i] = Ra[i] + w * (da / q) * u[i];
   }
   return ORC_OK;
 }
@@ -392,17 +413,41 @@ int orc_fields(const orc_sources *s, const double *points, int64_t P, const doub
  *
  * Outputs d, dd, ddd, energy, Ed: [N][n_steps + 1] (Ed may be NULL).
  */
+int orc_dipoles_run_moving(int32_t N, const double *origin, const double *axis, const double *q, const double *m1,
+                           const double *m2, const double *omega0, const double *d0, const double *org_pos,
+                           const double *org_vel, const double *org_acc, double dt, int64_t n_steps, double v_max,
+                           int32_t ed_mode, double *d, double *dd, double *ddd, double *energy, double *Ed,
+                           int32_t nthreads);
+
 int orc_dipoles_run(int32_t N, const double *origin, const double *axis, const double *q, const double *m1,
                     const double *m2, const double *omega0, const double *d0, double dt, int64_t n_steps,
                     double v_max, int32_t ed_mode, double *d, double *dd, double *ddd, double *energy, double *Ed,
                     int32_t nthreads) {
+  return orc_dipoles_run_moving(N, origin, axis, q, m1, m2, omega0, d0, NULL, NULL, NULL, dt, n_steps, v_max, ed_mode,
+                                d, dd, ddd, energy, Ed, nthreads);
+}
+
+/*
+ * Moving dipoles (Sec. 4.3): the origin of dipole i follows a prescribed trajectory, given at the
+ * half steps (org_pos/org_vel/org_acc [N][2 n_steps + 1][3], NULL for fixed origins).  The driving
+ * field of each RK4 stage is taken at the origin's position at that stage's time (half-step
+ * index 2n, 2n + 1, 2n + 2); the sources' retarded positions follow the whole-step history.
+ */
+int orc_dipoles_run_moving(int32_t N, const double *origin, const double *axis, const double *q, const double *m1,
+                           const double *m2, const double *omega0, const double *d0, const double *org_pos,
+                           const double *org_vel, const double *org_acc, double dt, int64_t n_steps, double v_max,
+                           int32_t ed_mode, double *d, double *dd, double *ddd, double *energy, double *Ed,
+                           int32_t nthreads) {
   if (N <= 0 || n_steps < 0 || !(dt > 0.0)) return ORC_ERR_ARG;
+  if (org_pos && (!org_vel || !org_acc)) return ORC_ERR_ARG;
   int64_t S = n_steps + 1;
+  const int64_t Hn = 2 * S - 1;
   orc_sources s;
   memset(&s, 0, sizeof(s));
   s.N = N; s.Sd = S; s.t0d = 0.0; s.dtd = dt;
   s.origin = origin; s.axis = axis; s.qd = q; s.m1 = m1; s.m2 = m2;
   s.d = d; s.d_dot = dd; s.d_ddot = ddd;
+  s.org_pos = org_pos; s.org_vel = org_vel; s.org_acc = org_acc;
   double *ed_now = (double *)calloc((size_t)N, sizeof(double));
   double *ed_half = (double *)calloc((size_t)N, sizeof(double));
   double *ed_next = (double *)calloc((size_t)N, sizeof(double));
@@ -428,17 +473,21 @@ int orc_dipoles_run(int32_t N, const double *origin, const double *axis, const d
       uint8_t mk;
       int st = ORC_OK;
       const double *p = axis + 3 * i;
+      /* receiver position at the half steps 2n, 2n + 1, 2n + 2 */
+      const double *r0 = org_pos ? org_pos + ((int64_t)i * Hn + 2 * n) * 3 : origin + 3 * i;
+      const double *r1 = org_pos ? r0 + 3 : r0;
+      const double *r2 = org_pos ? r0 + 6 : r0;
       if (n == 0) {
-        st = fields_at(&s, origin + 3 * i, t, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
+        st = fields_at(&s, r0, t, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
         ed_now[i] = dot3(p, E);
         if (Ed) Ed[(int64_t)i * S] = ed_now[i];
       }
       if (!st) {
-        st = fields_at(&s, origin + 3 * i, t + 0.5 * dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
+        st = fields_at(&s, r1, t + 0.5 * dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
         ed_half[i] = dot3(p, E);
       }
       if (!st) {
-        st = fields_at(&s, origin + 3 * i, t + dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
+        st = fields_at(&s, r2, t + dt, ORC_TOTAL, 0.0, i, E, B, &ph, A, &mk, NULL);
         ed_next[i] = dot3(p, E);
       }
       if (st) {

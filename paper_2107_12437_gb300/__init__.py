@@ -23,6 +23,7 @@ from .capi import (  # noqa: F401
     pc_dipoles_adjoint,
     pc_dipoles_rates_adjoint,
     pc_dipoles_run,
+    pc_dipoles_run_moving,
     pc_fields,
     pc_fields_plane,
     pc_ke_fit,

@@ -62,6 +62,10 @@ class PcRunOut(ctypes.Structure):
                 ("omega", _vp)]
 
 
+class PcDipoleMotion(ctypes.Structure):
+    _fields_ = [("pos", _vp), ("vel", _vp), ("acc", _vp)]
+
+
 class PcDipoleGrads(ctypes.Structure):
     _fields_ = [("origin", _vp), ("omega0", _vp), ("d0", _vp)]
 
@@ -78,6 +82,8 @@ SIGNATURES = {
                                        ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                       ctypes.POINTER(PcRunOut), _vp]),
+    "pc_dipoles_run_moving": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), ctypes.POINTER(PcDipoleMotion), _f64,
+                                             _i64, ctypes.POINTER(PcRunOpts), ctypes.POINTER(PcRunOut), _vp]),
     "pc_dipoles_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                           _vp, ctypes.POINTER(PcDipoleGrads), _vp]),
     "pc_dipoles_rates_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64,
@@ -380,6 +386,40 @@ class FinalEnergy(torch.autograd.Function):
 def final_energy(ctx, dp, dt, n_steps, v_max=0.0):
     """Differentiable E(T) [B][N] (Eq. dipoleE at the last step) of pc_dipoles_run in float64."""
     return FinalEnergy.apply(dp.origin, dp.omega0, dp.d0, dp, ctx, float(dt), int(n_steps), float(v_max))
+
+
+def pc_dipoles_run_moving(ctx, dp, motion, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_index=0,
+                          want_energy=True, want_Ed=False, stream=None):
+    """pc_dipoles_run_moving: motion = (pos, vel, acc) CUDA float64 tensors [B][N][2 n_steps + 1][3]."""
+    B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
+    S = int(n_steps) + 1
+    dev = dp.origin.device
+    out = dict(d=torch.empty((B, N, S), dtype=torch.float64, device=dev),
+               d_dot=torch.empty((B, N, S), dtype=torch.float64, device=dev),
+               d_ddot=torch.empty((B, N, S), dtype=torch.float64, device=dev))
+    if want_energy:
+        out["energy"] = torch.empty((B, N, S), dtype=torch.float64, device=dev)
+    if want_Ed:
+        out["Ed"] = torch.empty((B, N, S), dtype=torch.float64, device=dev)
+    if fit:
+        out["gamma"] = torch.empty((B, N), dtype=torch.float64, device=dev)
+        out["omega"] = torch.empty((B, N), dtype=torch.float64, device=dev)
+    pos, vel, acc = (x.to(device=dev, dtype=torch.float64).contiguous() for x in motion)
+    for x in (pos, vel, acc):
+        if tuple(x.shape) != (B, N, 2 * S - 1, 3):
+            raise ValueError("motion arrays must be [B][N][2 n_steps + 1][3]")
+    d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
+                  m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+    mo = PcDipoleMotion(pos=_ptr(pos), vel=_ptr(vel), acc=_ptr(acc))
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=int(ed_mode), fit=int(bool(fit)), first_index=int(first_index),
+                     precision=PC_F64)
+    ro = PcRunOut(d=_ptr(out["d"]), d_dot=_ptr(out["d_dot"]), d_ddot=_ptr(out["d_ddot"]),
+                  energy=_ptr(out.get("energy")), Ed=_ptr(out.get("Ed")), gamma=_ptr(out.get("gamma")),
+                  omega=_ptr(out.get("omega")))
+    st = ctx.lib.pc_dipoles_run_moving(ctx.handle, ctypes.byref(d), ctypes.byref(mo), float(dt), int(n_steps),
+                                       ctypes.byref(opts), ctypes.byref(ro), _stream(stream))
+    _check(st, "pc_dipoles_run_moving")
+    return out
 
 
 def pc_ke_fit(ctx, ke, dt, first_index, stream=None):

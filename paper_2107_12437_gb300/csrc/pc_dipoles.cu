@@ -51,6 +51,9 @@ struct RunArgs {
   double *Epart;
   int nsplit;
   int64_t *blk;
+  // moving dipoles (float64 path): origin position, velocity, acceleration at the half steps,
+  // [B][N][2 n_steps + 1][3], or null for fixed origins
+  const double *org_pos, *org_vel, *org_acc;
 };
 
 constexpr int kDipF = 12;
@@ -66,7 +69,10 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
   const int64_t S = a.n_steps + 1;
   const double cdt = kC * a.dt;
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
-  const double *Ri = a.origin + 3 * bi;
+  // receiver at its origin; a moving origin at the stage time (half-step index 2u)
+  const int64_t H = 2 * S - 1;
+  const int64_t hh = (int64_t)llrint(2.0 * u);
+  const double *Ri = a.org_pos ? a.org_pos + (bi * H + hh) * 3 : a.origin + 3 * bi;
   const double *pi = a.axis + 3 * bi;
   TrajF64 tr;
   tr.dipole = true;
@@ -76,6 +82,12 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
   for (int k = 0; k < 3; ++k) {
     tr.R[k] = a.origin[3 * bj + k];
     tr.ax[k] = a.axis[3 * bj + k];
+  }
+  if (a.org_pos) {
+    tr.Rp = a.org_pos + bj * H * 3;
+    tr.Rv = a.org_vel + bj * H * 3;
+    tr.Ra = a.org_acc + bj * H * 3;
+    for (int k = 0; k < 3; ++k) tr.R[k] = tr.Rp[6 * nv + k];  // the source now, for the first guess
   }
   const double q = a.q[bj], m1 = a.m1[bj], m2 = a.m2[bj];
   double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
@@ -261,7 +273,7 @@ __global__ void lo_tables_kernel(const RunArgs a) {
   const int b = blockIdx.x;
   const int N = a.N;
   const double L = kC * a.dt;
-  __shared__ double s_rmin[256], s_smax[256];
+  __shared__ double s_rmin[256], s_smax[256], s_vmax[256];
   double rmin = 1e300, smax = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const size_t bi = bidx(a, b, i);
@@ -279,6 +291,8 @@ __global__ void lo_tables_kernel(const RunArgs a) {
     f[11] = (float)(a.q[bi] / kE);
     smax = fmax(smax, fabs(a.d0[bi] / a.q[bi]));
   }
+  double vmax = 0.0;  // largest origin speed (moving dipoles)
+  const int64_t H = 2 * a.n_steps + 1;
   for (int64_t ij = threadIdx.x; ij < (int64_t)N * N; ij += blockDim.x) {
     const int i = (int)(ij / N), j = (int)(ij % N);
     const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
@@ -286,19 +300,32 @@ __global__ void lo_tables_kernel(const RunArgs a) {
                  dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
     if (i != j) rmin = fmin(rmin, r);
+    if (a.org_pos && i != j) {
+      // closest approach of the two origins over the run, and the origins' speeds
+      for (int64_t h = 0; h < H; ++h) {
+        const double *pi_ = a.org_pos + (bi * H + h) * 3, *pj_ = a.org_pos + (bj * H + h) * 3;
+        const double ex = pi_[0] - pj_[0], ey = pi_[1] - pj_[1], ez = pi_[2] - pj_[2];
+        rmin = fmin(rmin, sqrt(ex * ex + ey * ey + ez * ez));
+        const double *vi = a.org_vel + (bi * H + h) * 3;
+        vmax = fmax(vmax, sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+      }
+    }
     const double x = r / L;
     const double fl = floor(x);
     if (a.delay) a.delay[(size_t)bi * N + j] = make_int2((int)fl, __float_as_int((float)(x - fl)));
   }
   s_rmin[threadIdx.x] = rmin;
   s_smax[threadIdx.x] = smax;
+  s_vmax[threadIdx.x] = vmax;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int t = 1; t < blockDim.x; ++t) {
       rmin = fmin(rmin, s_rmin[t]);
       smax = fmax(smax, s_smax[t]);
+      vmax = fmax(vmax, s_vmax[t]);
     }
-    const double kk = floor((rmin - 3.0 * smax) / L);
+    // within a block of K steps a source origin moves at most vmax K dt closer
+    const double kk = floor((rmin - 3.0 * smax) / (L * (1.0 + vmax / kC)));
     a.kblock[b] = (int)fmax(1.0, fmin((double)kMaxBlock, kk));
   }
 }
@@ -1030,7 +1057,8 @@ static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, di
 
 // Forward run (Algorithm 1); Ehalf (or null) receives E_d at the half steps for the adjoint.
 static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
-                          const pc_run_out *out, double *Ehalf, cudaStream_t st, int *k_out = nullptr) {
+                          const pc_run_out *out, double *Ehalf, cudaStream_t st, int *k_out = nullptr,
+                          const pc_dipole_motion *motion = nullptr) {
   if (!ctx || !dp || !opts || !out) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0) || n_steps < 0) return PC_ERR_ARG;
   if (!dp->origin || !dp->axis || !dp->q || !dp->m1 || !dp->m2 || !dp->omega0 || !dp->d0) return PC_ERR_ARG;
@@ -1042,6 +1070,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const int64_t S = n_steps + 1;
   const size_t nbn = (size_t)dp->B * dp->N;
   const bool mixed = opts->precision == PC_MIXED;
+  if (motion && (mixed || !motion->pos || !motion->vel || !motion->acc)) return PC_ERR_ARG;
   if (mixed && S > ((int64_t)1 << 30)) return PC_ERR_ARG;
   // scratch: stage fields, float32 mirror (mixed), dipole records, pair delays (mixed), block
   // lengths, kinetic energies for the fit
@@ -1087,6 +1116,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.Epart = nullptr;
   a.nsplit = 1;
   a.blk = nullptr;
+  a.org_pos = motion ? motion->pos : nullptr;
+  a.org_vel = motion ? motion->vel : nullptr;
+  a.org_acc = motion ? motion->acc : nullptr;
   a.status = ctx->d_status;
   char *ke_base = scr + es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes;
   pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
@@ -1142,6 +1174,19 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 }  // namespace pc
+
+extern "C" pc_status pc_dipoles_run_moving(pc_ctx *ctx, const pc_dipoles *dp, const pc_dipole_motion *motion,
+                                           double dt, int64_t n_steps, const pc_run_opts *opts, const pc_run_out *out,
+                                           void *stream) {
+  if (!ctx || !motion) return PC_ERR_ARG;
+  pc::DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, opts, out, nullptr, st, nullptr, motion);
+  if (rs != PC_OK) return rs;
+  return pc::end_call(ctx, st);
+}
 
 extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
                                     const pc_run_opts *opts, const pc_run_out *out, void *stream) {

@@ -17,6 +17,9 @@ struct TrajF64 {
   const double *d, *dd, *ddd;  // dipole: [S]
   double R[3], ax[3], w;       // dipole: origin, axis, signed weight / q
   bool dipole;
+  // moving dipole origin (or null): position, velocity, acceleration at the half steps, [2 S - 1][3];
+  // the history holds the whole steps (half-step index 2k)
+  const double *Rp = nullptr, *Rv = nullptr, *Ra = nullptr;
   __device__ void p(int64_t k, double o[3]) const {
     if (!dipole) {
       o[0] = pos[3 * k];
@@ -24,9 +27,10 @@ struct TrajF64 {
       o[2] = pos[3 * k + 2];
     } else {
       double s = w * d[k];
-      o[0] = R[0] + s * ax[0];
-      o[1] = R[1] + s * ax[1];
-      o[2] = R[2] + s * ax[2];
+      const double *c = Rp ? Rp + 6 * k : R;
+      o[0] = c[0] + s * ax[0];
+      o[1] = c[1] + s * ax[1];
+      o[2] = c[2] + s * ax[2];
     }
   }
   __device__ void va(int64_t k, double v[3], double a[3]) const {
@@ -38,8 +42,8 @@ struct TrajF64 {
     } else {
       double sv = w * dd[k], sa = w * ddd[k];
       for (int i = 0; i < 3; ++i) {
-        v[i] = sv * ax[i];
-        a[i] = sa * ax[i];
+        v[i] = (Rv ? Rv[6 * k + i] : 0.0) + sv * ax[i];
+        a[i] = (Ra ? Ra[6 * k + i] : 0.0) + sa * ax[i];
       }
     }
   }

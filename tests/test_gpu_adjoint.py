@@ -181,7 +181,11 @@ def _rates_adjoint(ctx, cfg, wg, ww):
 
 
 def _rates_steps(cfg):
-    return {"origin": 6e-13, "omega0": 1e-7 * float(cfg.omega0.mean()), "d0": 1e-6 * float(cfg.d0.mean())}
+    # the fitted rates bend faster with the geometry than the final energy: 1.5e-13 m keeps the
+    # central difference's h^2 term below 2e-5 (6e-13 m gave 2.6e-4, a quarter of it 2e-5, so the
+    # gap was truncation); the rates depend on d0 only through amplitude ratios, so its step is
+    # larger to lift the quotient above the fit's rounding
+    return {"origin": 1.5e-13, "omega0": 1e-7 * float(cfg.omega0.mean()), "d0": 1e-4 * float(cfg.d0.mean())}
 
 
 def test_rates_adjoint_vs_gpu_finite_differences(ctx):
@@ -201,6 +205,11 @@ def test_rates_adjoint_vs_gpu_finite_differences(ctx):
             fd[idx] = (_rates_loss_gpu(ctx, _perturbed(cfg, name, idx, h), wg, ww) -
                        _rates_loss_gpu(ctx, _perturbed(cfg, name, idx, -h), wg, ww)) / (2 * h)
         _check(g[name], fd, 1e-4)
+    # rates are nearly invariant under a common scaling of all moments of a configuration: the
+    # run is linear in d0 up to the finite charge separation (multipole terms of relative size
+    # r_dip / R ~ 3e-4), so sum_i d0_i dL/dd0_i nearly cancels per configuration
+    euler = (cfg.d0 * g["d0"]).sum(axis=1)
+    assert np.all(np.abs(euler) <= 1e-2 * np.abs(cfg.d0 * g["d0"]).sum(axis=1))
 
 
 def test_rates_adjoint_vs_oracle_finite_differences(ctx):

@@ -1,0 +1,76 @@
+"""Moving dipoles (Sec. 4.3): pc_dipoles_run_moving (CUDA, float64, through the C ABI) against the
+FP64 oracle with the same half-step origin trajectories."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2107_12437_gb300 as pc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pc.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(motion):
+    return tuple(torch.tensor(np.ascontiguousarray(x), device="cuda") for x in motion)
+
+
+def _err(g, ref):
+    g = g.cpu().numpy()
+    return float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+
+
+def test_moving_pair_matches_oracle(ctx):
+    origins = np.array([[[0.0, 0.0, 0.0], [20e-9, 0.0, 0.0]], [[0.0, 0.0, 0.0], [0.0, 35e-9, 0.0]]])
+    axes = np.array([[[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]], [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]])
+    cfg = W.lo_batch(origins, axes, 2 * math.pi * 200e12, 1e-11, 1e-18, 4000, 0, q=10 * W.E_CHARGE)
+    motion = W.oscillating_origins(cfg, np.array([[1e-10, 0.0], [2e-10, 5e-11]]), 2 * math.pi * 20e12)
+    out = pc.pc_dipoles_run_moving(ctx, pc.lo_config_to_device(cfg), _dev(motion), cfg.dt, cfg.n_steps, want_Ed=True)
+    for b in range(cfg.B):
+        ref = oracle.dipoles_run(cfg, b=b, motion=motion)
+        assert ref["status"] == oracle.OK
+        for k in ("d", "d_dot", "d_ddot", "energy", "Ed"):
+            assert _err(out[k][b], ref[k]) < 1e-10, (b, k)
+    # the motion changes the run: without it the histories differ
+    still = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=pc.PC_F64)
+    assert _err(still["d"][0], out["d"][0].cpu().numpy()) > 1e-8
+
+
+def test_moving_cloud_grid_path_matches_oracle(ctx):
+    # more than 64 dipoles: the grid-wide drive and graph loop with moving origins
+    cfg = W.cfg5(N=80, n_steps=160, side=200e-9, min_spacing=12e-9, seed=W.SEED_CFG5 + 3)
+    rng = np.random.default_rng(5)
+    motion = W.oscillating_origins(cfg, rng.uniform(0.0, 2e-10, size=(1, 80)), 2 * math.pi * 30e12,
+                                   direction=(1.0, 1.0, 0.0))
+    out = pc.pc_dipoles_run_moving(ctx, pc.lo_config_to_device(cfg), _dev(motion), cfg.dt, cfg.n_steps, want_Ed=True)
+    ref = oracle.dipoles_run(cfg, motion=motion)
+    assert ref["status"] == oracle.OK
+    for k in ("d", "d_dot", "Ed"):
+        assert _err(out[k][0], ref[k]) < 1e-10, k
+
+
+def test_moving_rejects_mixed_precision(ctx):
+    cfg = W.adjoint_cluster(B=1, N=2, n_steps=20)
+    motion = _dev(W.oscillating_origins(cfg, 1e-10, 1e13))
+    dp = pc.lo_config_to_device(cfg)
+    d = pc.capi.PcDipoles(B=1, N=2, origin=pc.capi._ptr(dp.origin), axis=pc.capi._ptr(dp.axis), q=pc.capi._ptr(dp.q),
+                          m1=pc.capi._ptr(dp.m1), m2=pc.capi._ptr(dp.m2), omega0=pc.capi._ptr(dp.omega0),
+                          d0=pc.capi._ptr(dp.d0))
+    mo = pc.capi.PcDipoleMotion(pos=pc.capi._ptr(motion[0]), vel=pc.capi._ptr(motion[1]), acc=pc.capi._ptr(motion[2]))
+    opts = pc.capi.PcRunOpts(v_max=0.0, ed_mode=0, fit=0, first_index=0, precision=pc.PC_MIXED)
+    outs = [torch.empty((1, 2, 21), dtype=torch.float64, device="cuda") for _ in range(3)]
+    ro = pc.capi.PcRunOut(d=pc.capi._ptr(outs[0]), d_dot=pc.capi._ptr(outs[1]), d_ddot=pc.capi._ptr(outs[2]))
+    import ctypes
+
+    st = ctx.lib.pc_dipoles_run_moving(ctx.handle, ctypes.byref(d), ctypes.byref(mo), cfg.dt, 20, ctypes.byref(opts),
+                                       ctypes.byref(ro), None)
+    assert st == 1  # PC_ERR_ARG

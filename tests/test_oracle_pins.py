@@ -523,3 +523,51 @@ def test_populations_solve_the_density_matrix_equations():
     # the limit of very small separations, gamma12 -> gamma0 (App. A)
     raa0, _ = th.populations(ts, g0, g0, d12)
     assert np.allclose(raa0, 0.25 * (1 + np.exp(-2 * g0 * ts) + 2 * np.cos(2 * d12 * ts) * np.exp(-g0 * ts)))
+
+
+def _moving_cfg(n_steps=600):
+    # two s dipoles 20 nm apart; dipole 0's origin oscillates along x (0.1 nm, 2 pi 20 THz: up to
+    # 1.3e4 m/s), dipole 1 rests
+    origins = np.array([[[0.0, 0.0, 0.0], [20e-9, 0.0, 0.0]]])
+    axes = np.array([[[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]]])
+    cfg = W.lo_batch(origins, axes, 2 * math.pi * 200e12, 1e-11, 1e-18, n_steps, 0, q=10 * W.E_CHARGE)
+    motion = W.oscillating_origins(cfg, np.array([[1e-10, 0.0]]), 2 * math.pi * 20e12)
+    return cfg, motion
+
+
+def test_moving_dipoles_without_motion_match_fixed_run():
+    cfg, _ = _moving_cfg(300)
+    still = W.oscillating_origins(cfg, 0.0, 1.0)
+    a = oracle.dipoles_run(cfg)
+    b = oracle.dipoles_run(cfg, motion=still)
+    assert a["status"] == oracle.OK and b["status"] == oracle.OK
+    for k in ("d", "d_dot", "d_ddot", "Ed"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_moving_dipole_driving_field_equals_point_charge_field():
+    # the driving field of the moving run at whole steps against the generic point-charge path
+    # (pinned on its own) fed with the same dipole's two charges written out as sampled trajectories
+    cfg, motion = _moving_cfg(600)
+    r = oracle.dipoles_run(cfg, motion=motion)
+    assert r["status"] == oracle.OK
+    pos, vel, acc = motion
+    S = cfg.n_steps + 1
+    # source the moving dipole and receiver the fixed one, then the reverse
+    for src, rcv in ((0, 1), (1, 0)):
+        m1, m2, q = cfg.m1[0, src], cfg.m2[0, src], cfg.q[0, src]
+        u = cfg.axis[0, src]
+        P, V, A = pos[0, src, ::2], vel[0, src, ::2], acc[0, src, ::2]
+        cp, cv, ca = [], [], []
+        for w in (m2 / (m1 + m2), -m1 / (m1 + m2)):
+            cp.append(P + (w * r["d"][src] / q)[:, None] * u)
+            cv.append(V + (w * r["d_dot"][src] / q)[:, None] * u)
+            ca.append(A + (w * r["d_ddot"][src] / q)[:, None] * u)
+        ch = W.Charges(q=np.array([q, -q]), pos=np.stack(cp), vel=np.stack(cv), acc=np.stack(ca), t0=0.0,
+                       dt=cfg.dt, static_before=1)
+        for n in (50, 301, 600):
+            pt = pos[0, rcv, 2 * n][None]
+            f = oracle.fields(pt, [n * cfg.dt], charges=ch)
+            assert f["status"] == oracle.OK
+            ed = float(f["E"][0, 0] @ cfg.axis[0, rcv])
+            assert abs(ed - r["Ed"][rcv, n]) <= 1e-12 * abs(ed), (src, n, ed, r["Ed"][rcv, n])

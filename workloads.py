@@ -328,3 +328,21 @@ def population_pair(n_steps: int = 2_100_000, dt: float = 1e-17, r_dip: float = 
     cfg = lo_batch(origins, axes, 2 * math.pi * 200e12, r_dip, dt, n_steps, 0, q=20 * E_CHARGE)
     cfg.d0[0, 1] = 0.0
     return cfg
+
+
+def oscillating_origins(cfg: LOConfig, amp, Omega, direction=(1.0, 0.0, 0.0), n_steps=None):
+    """Origin trajectories R(t) = R0 + amp (cos(Omega t) - 1) u for every dipole (moving dipoles,
+    Sec. 4.3: an origin oscillating along x as in the paper's listing, shifted so that R(0) = R0),
+    sampled at the half steps t = h dt / 2, h = 0 .. 2 n_steps: (pos, vel, acc)
+    [B][N][2 n_steps + 1][3].  amp may be an array [B][N] (0 for fixed dipoles)."""
+    n_steps = cfg.n_steps if n_steps is None else n_steps
+    B, N = cfg.B, cfg.N
+    amp = np.broadcast_to(np.asarray(amp, dtype=np.float64), (B, N))
+    u = np.asarray(direction, dtype=np.float64)
+    u = u / np.linalg.norm(u)
+    t = np.arange(2 * n_steps + 1) * (cfg.dt / 2)
+    c, s = np.cos(Omega * t), np.sin(Omega * t)
+    pos = cfg.origin[:, :, None, :] + amp[:, :, None, None] * (c - 1.0)[None, None, :, None] * u
+    vel = -amp[:, :, None, None] * Omega * s[None, None, :, None] * u
+    acc = -amp[:, :, None, None] * Omega ** 2 * c[None, None, :, None] * u
+    return pos, vel, np.ascontiguousarray(acc)
