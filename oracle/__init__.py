@@ -68,6 +68,7 @@ def lib():
         _lib.orc_retarded_delay.restype = ctypes.c_int
         _lib.orc_dipoles_run.restype = ctypes.c_int
         _lib.orc_dipoles_run_moving.restype = ctypes.c_int
+        _lib.orc_fields_param.restype = ctypes.c_int
     return _lib
 
 
@@ -197,3 +198,25 @@ def dipoles_run(cfg, b=0, n_steps=None, ed_mode=0, v_max=None, nthreads=0, motio
         ctypes.c_double(cfg.dt), ctypes.c_int64(n_steps), ctypes.c_double(v_max), ctypes.c_int32(ed_mode),
         _ptr(d), _ptr(dd), _ptr(ddd), _ptr(en), _ptr(Ed), ctypes.c_int32(nthreads))
     return dict(d=d, d_dot=dd, d_ddot=ddd, energy=en, Ed=Ed, status=st)
+
+
+def fields_param(points, times, kind, q, par, fkind=TOTAL, r_excl=0.0, nthreads=0):
+    """E, B, A [T][P][3], phi [T][P], mask [T][P] of point charges on analytic trajectories
+    (kind [M] in 0..3, q [M], par [M][12]; the layouts are those of orc_fields_param)."""
+    keep = _Keep()
+    pts = keep(np.asarray(points).reshape(-1, 3))
+    tms = keep(np.atleast_1d(times))
+    P, T = pts.shape[0], tms.shape[0]
+    kd = np.ascontiguousarray(kind, dtype=np.int32)
+    qq = keep(q)
+    pr = keep(np.asarray(par).reshape(-1, 12))
+    E = np.zeros((T, P, 3))
+    B = np.zeros((T, P, 3))
+    A = np.zeros((T, P, 3))
+    phi = np.zeros((T, P))
+    mask = np.zeros((T, P), dtype=np.uint8)
+    st = lib().orc_fields_param(
+        ctypes.c_int32(kd.size), kd.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(qq), _ptr(pr), _ptr(pts),
+        ctypes.c_int64(P), _ptr(tms), ctypes.c_int32(T), ctypes.c_int32(fkind), ctypes.c_double(r_excl), _ptr(E),
+        _ptr(B), _ptr(phi), _ptr(A), mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.c_int32(nthreads))
+    return dict(E=E, B=B, A=A, phi=phi, mask=mask, status=st)

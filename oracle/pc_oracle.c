@@ -396,6 +396,120 @@ int orc_fields(const orc_sources *s, const double *points, int64_t P, const doub
 }
 
 /*
+ * Point charges on analytic trajectories r(t) (Sec. 2.2 and Sec. 3.1: the predefined trajectories
+ * of the paper's stationary, oscillating, orbiting and linearly accelerating charges), with exact
+ * velocity and acceleration.  par[12] per charge:
+ *   0 stationary:   r0[3]
+ *   1 oscillating:  r0[3], u[3] (unit), A, w, phi:        r = r0 + A cos(w t + phi) u
+ *   2 circular:     c[3], e1[3], e2[3] (orthonormal), a, w, phi:  r = c + a (cos(w t + phi) e1 + sin(w t + phi) e2)
+ *   3 accelerating: r0[3], v0[3], acc[3], ta:              r = r0 + v0 s + acc s^2 / 2 for s = t - ta >= 0,
+ *                                                          r0 + v0 s before (uniform motion)
+ */
+static void param_state(int kind, const double *p, double t, double r[3], double v[3], double a[3]) {
+  for (int i = 0; i < 3; ++i) { r[i] = p[i]; v[i] = 0.0; a[i] = 0.0; }
+  if (kind == 1) {
+    double ph = p[7] * t + p[8];
+    for (int i = 0; i < 3; ++i) {
+      r[i] = p[i] + p[6] * cos(ph) * p[3 + i];
+      v[i] = -p[6] * p[7] * sin(ph) * p[3 + i];
+      a[i] = -p[6] * p[7] * p[7] * cos(ph) * p[3 + i];
+    }
+  } else if (kind == 2) {
+    double ph = p[10] * t + p[11], rad = p[9], w = p[10];
+    for (int i = 0; i < 3; ++i) {
+      r[i] = p[i] + rad * (cos(ph) * p[3 + i] + sin(ph) * p[6 + i]);
+      v[i] = rad * w * (-sin(ph) * p[3 + i] + cos(ph) * p[6 + i]);
+      a[i] = -rad * w * w * (cos(ph) * p[3 + i] + sin(ph) * p[6 + i]);
+    }
+  } else if (kind == 3) {
+    double sdt = t - p[9];
+    int on = sdt >= 0.0;
+    for (int i = 0; i < 3; ++i) {
+      r[i] = p[i] + p[3 + i] * sdt + (on ? 0.5 * p[6 + i] * sdt * sdt : 0.0);
+      v[i] = p[3 + i] + (on ? p[6 + i] * sdt : 0.0);
+      a[i] = on ? p[6 + i] : 0.0;
+    }
+  }
+}
+
+/* retarded time of a parametric charge: bisection on g(t') = c (t - t') - |r - r(t')| (Eq. ret_t),
+   the lower end pushed back until g >= 0 */
+static int param_retarded_time(int kind, const double *p, double t, const double r[3], double *tp_out) {
+  double rc[3], v[3], a[3];
+  param_state(kind, p, t, rc, v, a);
+  double D[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
+  double hi = t, lo = t - sqrt(dot3(D, D)) / ORC_C;
+  double span = t - lo + 1e-30;
+  for (int it = 0;; ++it) {
+    param_state(kind, p, lo, rc, v, a);
+    double E[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
+    if (ORC_C * (t - lo) - sqrt(dot3(E, E)) >= 0.0) break;
+    if (it >= 200) return ORC_ERR_NOCONV;
+    span *= 2.0;
+    lo = t - span;
+  }
+  for (int it = 0; it < 4000; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    param_state(kind, p, mid, rc, v, a);
+    double E[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
+    if (ORC_C * (t - mid) - sqrt(dot3(E, E)) >= 0.0) lo = mid;
+    else hi = mid;
+  }
+  *tp_out = 0.5 * (lo + hi);
+  return ORC_OK;
+}
+
+int orc_fields_param(int32_t M, const int32_t *kind, const double *q, const double *par, const double *points,
+                     int64_t P, const double *times, int32_t T, int32_t fkind, double r_excl, double *E, double *B,
+                     double *phi, double *A, uint8_t *mask, int32_t nthreads) {
+  if (fkind < 0 || fkind > 2 || P < 0 || T < 0 || M < 0) return ORC_ERR_ARG;
+  for (int c = 0; c < M; ++c)
+    if (kind[c] < 0 || kind[c] > 3) return ORC_ERR_ARG;
+  int status = ORC_OK;
+  int64_t total = P * (int64_t)T;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+#endif
+  for (int64_t idx = 0; idx < total; ++idx) {
+    int64_t f = idx / P, pidx = idx % P;
+    const double *r = points + 3 * pidx;
+    double t = times[f];
+    double *e = E + 3 * idx, *b = B + 3 * idx, *aa = A + 3 * idx;
+    for (int i = 0; i < 3; ++i) { e[i] = 0.0; b[i] = 0.0; aa[i] = 0.0; }
+    phi[idx] = 0.0;
+    mask[idx] = 0;
+    for (int c = 0; c < M; ++c) {
+      double tp;
+      int st = param_retarded_time(kind[c], par + 12 * c, t, r, &tp);
+      if (st) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        if (status == ORC_OK) status = st;
+        break;
+      }
+      double pc_[3], v[3], ac[3];
+      param_state(kind[c], par + 12 * c, tp, pc_, v, ac);
+      double aR[3] = {r[0] - pc_[0], r[1] - pc_[1], r[2] - pc_[2]};
+      double R = sqrt(dot3(aR, aR));
+      if (R <= r_excl) { mask[idx] = 1; continue; }
+      double Ec[3], Er[3], ph, Ac[3];
+      lw_jackson(q[c], aR, v, ac, Ec, Er, &ph, Ac);
+      double Ek[3], n[3] = {aR[0] / R, aR[1] / R, aR[2] / R}, nE[3];
+      for (int i = 0; i < 3; ++i)
+        Ek[i] = (fkind == ORC_COULOMB) ? Ec[i] : (fkind == ORC_RADIATION) ? Er[i] : Ec[i] + Er[i];
+      cross3(n, Ek, nE);
+      for (int i = 0; i < 3; ++i) { e[i] += Ek[i]; b[i] += nE[i] / ORC_C; aa[i] += Ac[i]; }
+      phi[idx] += ph;
+    }
+  }
+  (void)nthreads;
+  return status;
+}
+
+/*
  * Lorentz-oscillator run, Algorithm 1, for one configuration of N dipoles.
  *
  * Dipole i: origin R_i, unit axis p_i, charges +-q_i with masses m1_i (positive) and m2_i

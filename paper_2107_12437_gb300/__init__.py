@@ -25,6 +25,7 @@ from .capi import (  # noqa: F401
     pc_dipoles_run,
     pc_dipoles_run_moving,
     pc_fields,
+    pc_fields_param,
     pc_fields_plane,
     pc_ke_fit,
 )

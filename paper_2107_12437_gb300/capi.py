@@ -62,6 +62,13 @@ class PcRunOut(ctypes.Structure):
                 ("omega", _vp)]
 
 
+class PcParamCharges(ctypes.Structure):
+    _fields_ = [("M", _i32), ("kind", _vp), ("q", _vp), ("par", _vp)]
+
+
+PC_TRAJ_STATIONARY, PC_TRAJ_OSCILLATING, PC_TRAJ_CIRCULAR, PC_TRAJ_ACCELERATING = 0, 1, 2, 3
+
+
 class PcDipoleMotion(ctypes.Structure):
     _fields_ = [("pos", _vp), ("vel", _vp), ("acc", _vp)]
 
@@ -82,6 +89,8 @@ SIGNATURES = {
                                        ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                       ctypes.POINTER(PcRunOut), _vp]),
+    "pc_fields_param": (ctypes.c_int, [_vp, ctypes.POINTER(PcParamCharges), _vp, _i64, ctypes.POINTER(_f64), _i32,
+                                       _i32, _f64, ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run_moving": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), ctypes.POINTER(PcDipoleMotion), _f64,
                                              _i64, ctypes.POINTER(PcRunOpts), ctypes.POINTER(PcRunOut), _vp]),
     "pc_dipoles_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
@@ -253,6 +262,25 @@ def pc_fields_plane(ctx, charges=None, dipoles=None, origin=(0, 0, 0), eu=(1, 0,
                                  ctypes.byref(_out_struct(o)), _stream(stream))
     _check(st, "pc_fields_plane")
     return o
+
+
+def pc_fields_param(ctx, kind, q, par, points, times=(0.0,), field_kind=PC_TOTAL, r_excl=0.0, out=None, stream=None):
+    """pc_fields_param: charges on analytic trajectories (kind [M] int32, q [M], par [M][12]);
+    returns float64 E, B, A [T][P][3], phi [T][P], mask [T][P]."""
+    dev = points.device if isinstance(points, torch.Tensor) else torch.device("cuda")
+    kd = torch.as_tensor(kind, dtype=torch.int32, device=dev).contiguous()
+    qq = torch.as_tensor(q, dtype=torch.float64, device=dev).contiguous()
+    pr = torch.as_tensor(par, dtype=torch.float64, device=dev).reshape(-1, 12).contiguous()
+    pts = torch.as_tensor(points, dtype=torch.float64, device=dev).reshape(-1, 3).contiguous()
+    P, T = int(pts.shape[0]), len(times)
+    if out is None:
+        out = alloc_field_out(P, T, PC_F64, dev)
+    ch = PcParamCharges(M=int(kd.numel()), kind=_ptr(kd), q=_ptr(qq), par=_ptr(pr))
+    tarr = (_f64 * T)(*[float(t) for t in times])
+    st = ctx.lib.pc_fields_param(ctx.handle, ctypes.byref(ch), _ptr(pts), P, tarr, T, int(field_kind), float(r_excl),
+                                 ctypes.byref(_out_struct(out)), _stream(stream))
+    _check(st, "pc_fields_param")
+    return out
 
 
 def lo_config_to_device(cfg, device="cuda"):

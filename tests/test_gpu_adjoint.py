@@ -180,12 +180,10 @@ def _rates_adjoint(ctx, cfg, wg, ww):
     return {"origin": go.cpu().numpy(), "omega0": gw.cpu().numpy(), "d0": gd.cpu().numpy()}, gam, om
 
 
-def _rates_steps(cfg):
-    # the fitted rates bend faster with the geometry than the final energy: 1.5e-13 m keeps the
-    # central difference's h^2 term below 2e-5 (6e-13 m gave 2.6e-4, a quarter of it 2e-5, so the
-    # gap was truncation); the rates depend on d0 only through amplitude ratios, so its step is
-    # larger to lift the quotient above the fit's rounding
-    return {"origin": 1.5e-13, "omega0": 1e-7 * float(cfg.omega0.mean()), "d0": 1e-4 * float(cfg.d0.mean())}
+def _rates_steps(cfg, h_origin):
+    # the rates depend on d0 only through amplitude ratios, so its step is larger to lift the
+    # quotient above the fit's rounding
+    return {"origin": h_origin, "omega0": 1e-7 * float(cfg.omega0.mean()), "d0": 1e-4 * float(cfg.d0.mean())}
 
 
 def test_rates_adjoint_vs_gpu_finite_differences(ctx):
@@ -196,7 +194,9 @@ def test_rates_adjoint_vs_gpu_finite_differences(ctx):
     out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=pc.PC_F64, fit=True,
                             first_index=cfg.first_index, want_energy=False)
     assert torch.equal(gam, out["gamma"]) and torch.equal(om, out["omega"])
-    hs = _rates_steps(cfg)
+    # the fitted rates bend faster with the geometry than the final energy: on this configuration
+    # 6e-13 m left an h^2 error of 2.6e-4 and a quarter of it 2e-5
+    hs = _rates_steps(cfg, 1.5e-13)
     for name in ("origin", "omega0", "d0"):
         arr = getattr(cfg, name)
         fd = np.zeros_like(arr)
@@ -216,7 +216,9 @@ def test_rates_adjoint_vs_oracle_finite_differences(ctx):
     cfg = _rates_cfg(B=1, seed=W.SEED_ADJ + 8)
     wg, ww = _rates_weights(cfg, 12)
     g, _, _ = _rates_adjoint(ctx, cfg, wg, ww)
-    hs = _rates_steps(cfg)
+    # the oracle's fit stops at SciPy's tolerances, which a smaller step would amplify; on this
+    # configuration 6e-13 m leaves an h^2 error near 1e-5
+    hs = _rates_steps(cfg, 6e-13)
     for name in ("origin", "omega0", "d0"):
         arr = getattr(cfg, name)
         fd = np.zeros_like(arr)

@@ -571,3 +571,86 @@ def test_moving_dipole_driving_field_equals_point_charge_field():
             assert f["status"] == oracle.OK
             ed = float(f["E"][0, 0] @ cfg.axis[0, rcv])
             assert abs(ed - r["Ed"][rcv, n]) <= 1e-12 * abs(ed), (src, n, ed, r["Ed"][rcv, n])
+
+
+# ---- point charges on analytic trajectories ----
+
+def _par(*vals):
+    p = np.zeros(12)
+    flat = np.concatenate([np.atleast_1d(np.asarray(v, dtype=np.float64)) for v in vals])
+    p[:flat.size] = flat
+    return p
+
+
+@pytest.mark.parametrize("beta", [0.1, 0.5, 0.9])
+def test_param_uniform_motion_heaviside_feynman(beta):
+    v = beta * W.C * np.array([0.0, 0.6, 0.8])
+    r0 = np.array([0.0, -20e-9, 3e-9])
+    T = 2.5e-15
+    rng = np.random.default_rng(3)
+    pts = r0 + T * v + rng.uniform(-60e-9, 60e-9, size=(50, 3))
+    # accelerating kind with zero acceleration, clock started at t = 0
+    out = oracle.fields_param(pts, [T], [3], [-W.E_CHARGE], [_par(r0, v, [0, 0, 0], 0.0)])
+    assert out["status"] == oracle.OK
+    E, B, phi, A = th.uniform_motion(-W.E_CHARGE, r0 + v * T, v, pts)
+    assert rel(out["E"][0], E) < 1e-12
+    assert rel(out["B"][0], B) < 1e-12
+    assert np.max(np.abs(out["phi"][0] - phi) / np.abs(phi)) < 1e-12
+    assert rel(out["A"][0], A) < 1e-12
+
+
+def test_param_stationary_is_coulomb():
+    pts = np.random.default_rng(4).uniform(-5e-9, 5e-9, size=(30, 3))
+    out = oracle.fields_param(pts, [1e-15], [0], [W.E_CHARGE], [_par([1e-9, -2e-9, 0.5e-9])])
+    E, phi = th.coulomb_static(W.E_CHARGE, [1e-9, -2e-9, 0.5e-9], pts)
+    assert rel(out["E"][0], E) < 1e-13
+    assert np.max(np.abs(out["phi"][0] - phi) / np.abs(phi)) < 1e-14
+
+
+def test_param_oscillating_pair_is_hertzian_dipole():
+    # Sec. 4.1 / App. E: +-q oscillating in antiphase, amplitude sep/2 each, d = q sep cos(w t);
+    # no sampling, so only the (sep/z)^2 departure of the physical dipole remains
+    w = 7e16
+    q = 1e5 * W.E_CHARGE
+    sep = 4e-14
+    lam = 2 * math.pi * W.C / w
+    zs = np.array([0.05, 0.1, 0.3, 0.7, 1.0, 1.6, 2.5]) * lam
+    t_eval = 3.0 * lam / W.C + 0.37e-16
+    pts = np.stack([np.zeros_like(zs), np.zeros_like(zs), zs], axis=1)
+    ux = [1.0, 0.0, 0.0]
+    pars = [_par([0, 0, 0], ux, sep / 2, w, 0.0), _par([0, 0, 0], ux, -sep / 2, w, 0.0)]
+    out = oracle.fields_param(pts, [t_eval], [1, 1], [q, -q], pars)
+    assert out["status"] == oracle.OK
+    E_th, B_th = th.hertzian_dipole([q * sep, 0, 0], w, pts, t_eval)
+    errE = np.linalg.norm(out["E"][0] - E_th, axis=1) / np.linalg.norm(E_th, axis=1)
+    errB = np.linalg.norm(out["B"][0] - B_th, axis=1) / np.linalg.norm(B_th, axis=1)
+    assert np.all(errE < 1e-9) and np.all(errB < 1e-9)
+
+
+def test_param_circular_orbit_lienard_power():
+    radius, beta = 1e-9, 0.1
+    w = beta * W.C / radius
+    r_s = 2e-4
+    Tp = 2 * math.pi / w
+    times = r_s / W.C + np.arange(8) * Tp / 8
+    x, wq = np.polynomial.legendre.leggauss(32)
+    n_ph = 32
+    phis = np.arange(n_ph) * 2 * math.pi / n_ph
+    st = np.sqrt(1 - x * x)
+    pts = np.concatenate([np.stack([r_s * st * math.cos(p), r_s * st * math.sin(p), r_s * x], axis=1) for p in phis])
+    wts = np.concatenate([wq * (2 * math.pi / n_ph) for _ in phis])
+    par = _par([0, 0, 0], [1, 0, 0], [0, 1, 0], radius, w, 0.0)
+    out = oracle.fields_param(pts, times, [2], [W.E_CHARGE], [par], fkind=oracle.RADIATION)
+    assert out["status"] == oracle.OK
+    S_ = np.cross(out["E"], out["B"]) / th.MU0
+    flux = r_s ** 2 * np.sum(np.sum(S_ * (pts / r_s)[None], axis=2) * wts[None, :], axis=1)
+    P = th.lienard_power_circular(W.E_CHARGE, beta * W.C, beta * W.C * w)
+    assert np.max(np.abs(flux / P - 1)) < 1e-4
+    # at the orbit's centre the retarded time is exactly t - radius / c
+    c0 = oracle.fields_param(np.zeros((1, 3)), [times[0]], [2], [W.E_CHARGE], [par])
+    tp = times[0] - radius / W.C
+    p = radius * np.array([math.cos(w * tp), math.sin(w * tp), 0.0])
+    v = radius * w * np.array([-math.sin(w * tp), math.cos(w * tp), 0.0])
+    a = -w * w * p
+    Ec, Er, _, _ = oracle.lw_jackson(W.E_CHARGE, -p, v, a)
+    assert rel(c0["E"][0], (Ec + Er)[None]) < 1e-12

@@ -346,3 +346,43 @@ def oscillating_origins(cfg: LOConfig, amp, Omega, direction=(1.0, 0.0, 0.0), n_
     vel = -amp[:, :, None, None] * Omega * s[None, None, :, None] * u
     acc = -amp[:, :, None, None] * Omega ** 2 * c[None, None, :, None] * u
     return pos, vel, np.ascontiguousarray(acc)
+
+
+def param_charges(seed: int = 41):
+    """A mixed set of point charges on analytic trajectories (stationary, oscillating, circular,
+    accelerating; par layout of pc_fields_param) within a few nm of the origin, speeds up to 0.5 c,
+    and random observation points 5-60 nm away."""
+    rng = np.random.default_rng(seed)
+    kind, q, par = [], [], []
+
+    def unit():
+        v = rng.standard_normal(3)
+        return v / np.linalg.norm(v)
+
+    for k in range(12):
+        kd = k % 4
+        p = np.zeros(12)
+        p[:3] = rng.uniform(-3e-9, 3e-9, 3)
+        if kd == 1:
+            p[3:6] = unit()
+            p[6], p[7], p[8] = rng.uniform(0.2e-9, 1e-9), rng.uniform(1e15, 5e16), rng.uniform(0, 2 * math.pi)
+            p[7] = min(p[7], 0.5 * C / p[6])
+        elif kd == 2:
+            e1 = unit()
+            e2 = np.cross(e1, unit())
+            e2 /= np.linalg.norm(e2)
+            p[3:6], p[6:9] = e1, e2
+            p[9] = rng.uniform(0.5e-9, 2e-9)
+            p[10] = rng.uniform(0.05, 0.4) * C / p[9]
+            p[11] = rng.uniform(0, 2 * math.pi)
+        elif kd == 3:
+            p[3:6] = rng.uniform(-0.1, 0.1, 3) * C
+            p[6:9] = rng.uniform(-1, 1, 3) * 1e22
+            p[9] = rng.uniform(-5e-15, 5e-15)
+        kind.append(kd)
+        q.append(E_CHARGE * (1 if k % 3 else -1) * (1 + k % 2))
+        par.append(p)
+    d = rng.standard_normal((256, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts = d * rng.uniform(5e-9, 60e-9, size=(256, 1))
+    return np.array(kind, dtype=np.int32), np.array(q), np.array(par), pts
