@@ -146,6 +146,26 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   const float px = fj[6], py = fj[7], pz = fj[8];
   const float rp = rx * px + ry * py + rz * pz;
   const HistF32RW H{a.H32 + bj * (size_t)(a.n_steps + 1)};
+  // fast path: both charges on the segment of the centre's retarded time (packed solve), then only
+  // the driving-field projection p_i . E of the pair
+  {
+    float fl;
+    const int kc = Num<float>::floor_int(xc, fl);
+    const int k = kb + kc;
+    if (k >= 0 && k <= nvalid - 2) {
+      float x0, v0, a0, x1, v1, a1;
+      H.get_in(k, x0, v0, a0);
+      H.get_in(k + 1, x1, v1, a1);
+      // the first segment may not be extended backwards, the last one only by kEndTol
+      const float lo = (k == 0) ? 0.f : -kExtrap, hi = 1.f + ((k == nvalid - 2) ? kEndTol : kExtrap);
+      float2 X, V, Ac, dl;
+      if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, fj[9], fj[10], X, V, Ac, dl, 0.5f * (lo + hi),
+                               0.5f * (hi - lo))) {
+        const float rpi = rx * fi[6] + ry * fi[7] + rz * fi[8], ppi = px * fi[6] + py * fi[7] + pz * fi[8];
+        return dipole_drive_fast(rn, rp, fj[9], fj[10], fj[11], X, V, Ac, dl, rpi, ppi);
+      }
+    }
+  }
   float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   uint8_t mk = 0;
   const int e = dipole_net<PC_TOTAL, float, HistF32RW>(H, nvalid, kb, xc, rx, ry, rz, rn, px, py, pz, rp, fj[9], fj[10],

@@ -220,9 +220,12 @@ __device__ __forceinline__ bool dip_pair_states(T x0, T v0, T a0, T x1, T v1, T 
 // The two charges run side by side in the lanes of float2 operations (packed FFMA2/FMUL2/FADD2:
 // one instruction issue for both charges).
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+// th_mid, th_half: the roots must lie within th_mid +- th_half of the segment (the field kernel's
+// interior segments: 0.5 +- (0.5 + kExtrap)).  The tests are written so that a NaN fails them.
 __device__ __forceinline__ bool dip_pair_states_fast(float x0, float v0, float a0, float x1, float v1, float a1,
                                                      float thc, float rn, float rp, float mup, float mum, float2 &X,
-                                                     float2 &V, float2 &Ac, float2 &dl) {
+                                                     float2 &V, float2 &Ac, float2 &dl, float th_mid = 0.5f,
+                                                     float th_half = 0.5f + kExtrap) {
   const float dx = x1 - x0, dv = v1 - v0, da = a1 - a0;
   const float Xc = x0 + thc * dx;
   const float2 smu = make_float2(mup, -mum);  // (positive charge, negative charge)
@@ -243,10 +246,43 @@ __device__ __forceinline__ bool dip_pair_states_fast(float x0, float v0, float a
   V = __ffma2_rn(th, f2(dv), f2(v0));
   Ac = __ffma2_rn(th, f2(da), f2(a0));
   dl = make_float2(-ndl.x, -ndl.y);
-  const float2 td = __fadd2_rn(th, f2(-0.5f));
-  const float tdev = fmaxf(fabsf(td.x), fabsf(td.y));
-  const float edev = fmaxf(fabsf(eps.x), fabsf(eps.y));
-  return tdev <= 0.5f + kExtrap && edev < 1e-2f;
+  const float2 td = __fadd2_rn(th, f2(-th_mid));
+  return fabsf(td.x) <= th_half && fabsf(td.y) <= th_half && fabsf(eps.x) + fabsf(eps.y) < 1e-2f;
+}
+
+// The driving-field part of dipole_pair_fast: p_i . E of the pair, given r . p_i (rpi) and
+// p_j . p_i (ppi), in the units of dipole_pair (E = C_a a + C_p p_j summed over the two charges).
+__device__ __forceinline__ float dipole_drive_fast(float rn, float rp, float mup, float mum, float qs, float2 X,
+                                                   float2 V, float2 Ac, float2 dl, float rpi, float ppi) {
+  const float2 mu2 = make_float2(mup, -mum);
+  const float2 s = __fmul2_rn(mu2, X);
+  const float2 v = __fmul2_rn(mu2, V);
+  const float2 al = __fmul2_rn(mu2, Ac);
+  const float ds = mup * X.x + mum * X.y, dv = mup * V.x + mum * V.y, da = mup * Ac.x + mum * Ac.y;
+  const float2 R = __fadd2_rn(f2(rn), dl);
+  const float dR = dl.x - dl.y;
+  const float2 ap = __fadd2_rn(f2(rp), make_float2(-s.x, -s.y));
+  const float2 Ru = __ffma2_rn(make_float2(-v.x, -v.y), ap, R);
+  const float dRu = dR - (dv * ap.x - v.y * ds);
+  const float2 i = make_float2(__fdividef(1.f, Ru.x), __fdividef(1.f, Ru.y));
+  const float2 i2 = __fmul2_rn(i, i);
+  const float2 i3 = __fmul2_rn(i2, i);
+  const float di = -dRu * i.y * i.x;
+  const float di2 = di * (i.x + i.y);
+  const float di3 = di * (i2.x + i.x * i.y + i2.y);
+  const float v0 = v.y, a0 = al.y, R0 = R.y;
+  const float G0 = 1.f - v0 * v0 + a0 * ap.y;
+  const float dG = -dv * (v.x + v0) + da * ap.x - a0 * ds;
+  const float G1 = G0 + dG;
+  const float2 Ca = __fmul2_rn(make_float2(G1, G0), i3);
+  const float dCa = dG * i3.x + G0 * di3;
+  const float P0 = R0 * v0 * G0;
+  const float dP = dR * v.x * G1 + R0 * (dv * G1 + v0 * dG);
+  const float Q0 = a0 * R0, dQ = da * R.x + a0 * dR;
+  const float dCp = -(dP * i3.x + P0 * di3) - (dQ * i2.x + Q0 * di2);
+  const float2 Cs = __fmul2_rn(Ca, s);
+  const float ep = dCp - (Cs.x - Cs.y);
+  return qs * (dCa * rpi + ep * ppi);
 }
 
 // dipole_pair (CHECK_REX = false) for the float32 fast path with both charges in float2 lanes,
