@@ -54,14 +54,118 @@ struct RunArgs {
   // moving dipoles (float64 path): origin position, velocity, acceleration at the half steps,
   // [B][N][2 n_steps + 1][3], or null for fixed origins
   const double *org_pos, *org_vel, *org_acc;
+  // per dipole: the RK4 step as an affine map y' = M y + c1 e1 + c2 e2 + c4 e4, as
+  // [B][N][kTab]: M^1 .. M^kMaxBlock (row-major 2x2 each), then c1, c2, c4
+  double *rk4tab;
 };
+
+constexpr int kTab = 4 * 16 + 6;
 
 constexpr int kDipF = 12;
 
 __device__ __forceinline__ size_t bidx(const RunArgs &a, int b, int i) { return (size_t)b * a.N + i; }
 
+// One RK4 step of d'' + g0 d' + w2 d = qm E (Eq. LO_equation) on y = (d, d') with stage fields
+// e1 (t), e2 (t + dt/2, both middle stages) and e4 (t + dt).
+__device__ __forceinline__ void rk4_step(double y0, double y1, double e1, double e2, double e4, double g0, double w2,
+                                         double qm, double dt, double &n0, double &n1) {
+  const double k1a = y1, k1b = -g0 * y1 - w2 * y0 + qm * e1;
+  const double y0b = y0 + 0.5 * dt * k1a, y1b = y1 + 0.5 * dt * k1b;
+  const double k2a = y1b, k2b = -g0 * y1b - w2 * y0b + qm * e2;
+  const double y0c = y0 + 0.5 * dt * k2a, y1c = y1 + 0.5 * dt * k2b;
+  const double k3a = y1c, k3b = -g0 * y1c - w2 * y0c + qm * e2;
+  const double y0d = y0 + dt * k3a, y1d = y1 + dt * k3b;
+  const double k4a = y1d, k4b = -g0 * y1d - w2 * y0d + qm * e4;
+  n0 = y0 + dt / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
+  n1 = y1 + dt / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
+}
+
+// The step is linear in (y, e1, e2, e4): its matrix M and stage responses c1, c2, c4 are the step
+// applied to unit inputs; the table holds M^1 .. M^16 for the block scan.
+__device__ void rk4_table(const RunArgs &a, size_t bi) {
+  const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
+  const double m = m1 * m2 / (m1 + m2);
+  const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
+  const double qm = q * q / m, w2 = w0 * w0, dt = a.dt;
+  double M[4], c[6];
+  rk4_step(1.0, 0.0, 0.0, 0.0, 0.0, g0, w2, qm, dt, M[0], M[2]);
+  rk4_step(0.0, 1.0, 0.0, 0.0, 0.0, g0, w2, qm, dt, M[1], M[3]);
+  rk4_step(0.0, 0.0, 1.0, 0.0, 0.0, g0, w2, qm, dt, c[0], c[1]);
+  rk4_step(0.0, 0.0, 0.0, 1.0, 0.0, g0, w2, qm, dt, c[2], c[3]);
+  rk4_step(0.0, 0.0, 0.0, 0.0, 1.0, g0, w2, qm, dt, c[4], c[5]);
+  double *T = a.rk4tab + bi * kTab;
+  double P[4] = {M[0], M[1], M[2], M[3]};
+  for (int j = 0; j < 16; ++j) {
+    for (int e = 0; e < 4; ++e) T[4 * j + e] = P[e];
+    const double Q[4] = {M[0] * P[0] + M[1] * P[2], M[0] * P[1] + M[1] * P[3], M[2] * P[0] + M[3] * P[2],
+                         M[2] * P[1] + M[3] * P[3]};
+    for (int e = 0; e < 4; ++e) P[e] = Q[e];
+  }
+  for (int e = 0; e < 6; ++e) T[64 + e] = c[e];
+}
+
+// The kb steps of a causal block at once, one lane per step: with every stage field of the block
+// known, y_{k+1} = M^(k+1) y_0 + sum_{m <= k} M^(k-m) b_m, b_m = c1 e1_m + c2 e2_m + c4 e4_m, an
+// inclusive scan over the lanes (log2 kb shuffle rounds) instead of kb dependent steps.  Called by
+// all 32 lanes of a warp; appends d, d', d'' (and the float32 mirror, energy, E_d, the half-step
+// fields) to the history exactly as the stepwise form.
 template <bool MIXED>
-__device__ void rk4_block(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop);
+__device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop) {
+  const int lane = threadIdx.x & 31;
+  const int64_t S = a.n_steps + 1;
+  const double L = kC * a.dt;
+  const size_t bi = bidx(a, b, i);
+  double *Es = a.Es + bi * (2 * kMaxBlock + 1);
+  const double *T = a.rk4tab + bi * kTab;
+  const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
+  const double m = m1 * m2 / (m1 + m2);
+  const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
+  const double qm = q * q / m;
+  const double vfac = fmax(m1, m2) / (m1 + m2) / q;
+  const double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
+  double vx = 0.0, vy = 0.0, e2 = 0.0, e4 = 0.0;
+  if (lane < kb) {
+    const double e1 = Es[2 * lane];
+    e2 = Es[2 * lane + 1];
+    e4 = Es[2 * lane + 2];
+    const double f2 = (a.ed_mode == 1) ? e1 : e2, f4 = (a.ed_mode == 1) ? e1 : e4;
+    vx = T[64] * e1 + T[66] * f2 + T[68] * f4;
+    vy = T[65] * e1 + T[67] * f2 + T[69] * f4;
+  }
+  for (int off = 1; off < kb; off <<= 1) {
+    const double ox = __shfl_up_sync(0xffffffffu, vx, off), oy = __shfl_up_sync(0xffffffffu, vy, off);
+    if (lane >= off) {
+      const double *P = T + 4 * (off - 1);  // M^off
+      vx += P[0] * ox + P[1] * oy;
+      vy += P[2] * ox + P[3] * oy;
+    }
+  }
+  int bad = 0;
+  if (lane < kb) {
+    const double *P = T + 4 * lane;  // M^(lane+1)
+    const double yn0 = P[0] * y0 + P[1] * y1 + vx;
+    const double yn1 = P[2] * y0 + P[3] * y1 + vy;
+    const int64_t n = n0 + lane;
+    const double ydd = qm * e4 - g0 * yn1 - w0 * w0 * yn0;
+    a.d[bi * S + n + 1] = yn0;
+    a.dd[bi * S + n + 1] = yn1;
+    a.ddd[bi * S + n + 1] = ydd;
+    if (MIXED)
+      a.H32[bi * S + n + 1] =
+          make_float4((float)(yn0 / (q * L)), (float)(yn1 / (q * kC)), (float)(ydd * a.dt / (q * kC)), 0.f);
+    if (a.Ed) a.Ed[bi * S + n + 1] = e4;
+    if (a.Ehalf) a.Ehalf[bi * a.n_steps + n] = e2;
+    if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
+    bad = fabs(yn1) * vfac > a.v_max;
+  }
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) set_status(a.status, PC_ERR_VELOCITY);
+    *stop = 1;
+  }
+  __syncwarp();
+  if (lane == 0) Es[0] = Es[2 * kb];
+  __syncwarp();
+}
 
 // Contribution of dipole j to the driving field of receiver i at time u (steps), history 0..nv.
 // float64: both charges per charge (Eqs. r_1, r_2, E); returns p_i . E.
@@ -152,6 +256,24 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
     float fl;
     const int kc = Num<float>::floor_int(xc, fl);
     const int k = kb + kc;
+    const float rpi = rx * fi[6] + ry * fi[7] + rz * fi[8], ppi = px * fi[6] + py * fi[7] + pz * fi[8];
+    if (k < -1) {
+      // the centre's retarded time lies a sample or more before t = 0; when both charges' offsets
+      // (at most |s| samples) keep them there too, they rest at their first position with no
+      // velocity or acceleration (Sec. 3.2), and their distances are exact without a solve:
+      // R_c = |rho - s_c p|, delta_c = R_c - rn = s_c (s_c - 2 rp) / (R_c + rn)
+      float x0, v0, a0;
+      H.get_in(0, x0, v0, a0);
+      const float sp = fj[9] * x0, sm = -fj[10] * x0;
+      if ((float)kb + xc + fmaxf(fabsf(sp), fabsf(sm)) < -0.01f) {
+        const float Rp = sqrtf(fmaxf(rn * rn + sp * (sp - 2.f * rp), 0.f));
+        const float Rm = sqrtf(fmaxf(rn * rn + sm * (sm - 2.f * rp), 0.f));
+        const float2 dl = make_float2(__fdividef(sp * (sp - 2.f * rp), Rp + rn), __fdividef(sm * (sm - 2.f * rp), Rm + rn));
+        const float2 zero = make_float2(0.f, 0.f);
+        if (Rp > 0.f && Rm > 0.f)
+          return dipole_drive_fast(rn, rp, fj[9], fj[10], fj[11], make_float2(x0, x0), zero, zero, dl, rpi, ppi);
+      }
+    }
     if (k >= 0 && k <= nvalid - 2) {
       float x0, v0, a0, x1, v1, a1;
       H.get_in(k, x0, v0, a0);
@@ -160,10 +282,8 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
       const float lo = (k == 0) ? 0.f : -kExtrap, hi = 1.f + ((k == nvalid - 2) ? kEndTol : kExtrap);
       float2 X, V, Ac, dl;
       if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, fj[9], fj[10], X, V, Ac, dl, 0.5f * (lo + hi),
-                               0.5f * (hi - lo))) {
-        const float rpi = rx * fi[6] + ry * fi[7] + rz * fi[8], ppi = px * fi[6] + py * fi[7] + pz * fi[8];
+                               0.5f * (hi - lo)))
         return dipole_drive_fast(rn, rp, fj[9], fj[10], fj[11], X, V, Ac, dl, rpi, ppi);
-      }
     }
   }
   float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -274,12 +394,11 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     }
     __syncthreads();
     if (s_stop) break;
-    // phase B: kb RK4 steps per receiver (lane 0 of its warp)
+    // phase B: the kb RK4 steps of each receiver, one warp per receiver, one lane per step
     for (int i = warp; i < N; i += kRunWarps) {
-      if (lane != 0) continue;
       int stop = 0;
-      rk4_block<MIXED>(a, b, i, n0, kb, &stop);
-      if (stop) s_stop = 1;
+      rk4_block_warp<MIXED>(a, b, i, n0, kb, &stop);
+      if (stop && lane == 0) s_stop = 1;
     }
     __syncthreads();
   }
@@ -305,6 +424,7 @@ __global__ void lo_tables_kernel(const RunArgs a) {
       f[3 + c] = (float)(x - (double)hi);
       f[6 + c] = (float)a.axis[3 * bi + c];
     }
+    rk4_table(a, bi);
     const double m1 = a.m1[bi], m2 = a.m2[bi];
     f[9] = (float)(m2 / (m1 + m2));
     f[10] = (float)(m1 / (m1 + m2));
@@ -427,11 +547,14 @@ __global__ void lo_rk4_kernel(const RunArgs a, int64_t n0, int kb) {
     if (n0 >= a.n_steps) return;
     kb = (int)min(a.blk[1], a.n_steps - n0);
   }
-  const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per receiver
+  const int64_t bi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (bi >= (int64_t)a.B * a.N) return;
-  sum_slices(a, bi, 1, 2 * kb);
+  const int lane = threadIdx.x & 31;
+  if (a.nsplit > 1 && lane < 2 * kb) sum_slices(a, bi, 1 + lane, 1 + lane);
+  __syncwarp();
   int stop = 0;
-  rk4_block<MIXED>(a, (int)(bi / a.N), (int)(bi % a.N), n0, kb, &stop);
+  rk4_block_warp<MIXED>(a, (int)(bi / a.N), (int)(bi % a.N), n0, kb, &stop);
 }
 
 // Advances the device cursor by one block and sets the loop condition of the graph.
@@ -439,58 +562,6 @@ __global__ void lo_advance_kernel(const RunArgs a, cudaGraphConditionalHandle lo
   const int64_t n0 = a.blk[0] + a.blk[1];
   a.blk[0] = n0;
   cudaGraphSetConditional(loop, (n0 < a.n_steps && *((volatile int *)a.status) == 0) ? 1u : 0u);
-}
-
-// Phase B for receiver i: kb RK4 steps (Eq. LO_equation) from step n0 with the stage fields Es,
-// appending d, d', d'' (and the float32 mirror, energy, E_d) to the history.
-template <bool MIXED>
-__device__ void rk4_block(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop) {
-  const int64_t S = a.n_steps + 1;
-  const double L = kC * a.dt;
-  const size_t bi = bidx(a, b, i);
-  double *Es = a.Es + bi * (2 * kMaxBlock + 1);
-  const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
-  const double m = m1 * m2 / (m1 + m2);
-  const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
-  const double qm = q * q / m;
-  const double dt = a.dt;
-  const double vfac = fmax(m1, m2) / (m1 + m2) / q;
-  double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
-  for (int k = 0; k < kb; ++k) {
-    const int64_t n = n0 + k;
-    const double e1 = Es[2 * k];
-    const double f2 = (a.ed_mode == 1) ? e1 : Es[2 * k + 1];
-    const double e4 = Es[2 * k + 2];
-    const double f4 = (a.ed_mode == 1) ? e1 : e4;
-    // RK4 on (d, d') with d'' = -gamma0 d' - omega0^2 d + (q^2/m) E_d(t)
-    const double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
-    const double y0b = y0 + 0.5 * dt * k1a, y1b = y1 + 0.5 * dt * k1b;
-    const double k2a = y1b, k2b = -g0 * y1b - w0 * w0 * y0b + qm * f2;
-    const double y0c = y0 + 0.5 * dt * k2a, y1c = y1 + 0.5 * dt * k2b;
-    const double k3a = y1c, k3b = -g0 * y1c - w0 * w0 * y0c + qm * f2;
-    const double y0d = y0 + dt * k3a, y1d = y1 + dt * k3b;
-    const double k4a = y1d, k4b = -g0 * y1d - w0 * w0 * y0d + qm * f4;
-    const double yn0 = y0 + dt / 6.0 * (k1a + 2.0 * k2a + 2.0 * k3a + k4a);
-    const double yn1 = y1 + dt / 6.0 * (k1b + 2.0 * k2b + 2.0 * k3b + k4b);
-    const double ydd = qm * e4 - g0 * yn1 - w0 * w0 * yn0;
-    a.d[bi * S + n + 1] = yn0;
-    a.dd[bi * S + n + 1] = yn1;
-    a.ddd[bi * S + n + 1] = ydd;
-    if (MIXED)
-      a.H32[bi * S + n + 1] =
-          make_float4((float)(yn0 / (q * L)), (float)(yn1 / (q * kC)), (float)(ydd * dt / (q * kC)), 0.f);
-    if (a.Ed) a.Ed[bi * S + n + 1] = e4;
-    if (a.Ehalf) a.Ehalf[bi * a.n_steps + n] = Es[2 * k + 1];
-    if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
-    if (fabs(yn1) * vfac > a.v_max) {
-      set_status(a.status, PC_ERR_VELOCITY);
-      *stop = 1;
-      break;
-    }
-    y0 = yn0;
-    y1 = yn1;
-  }
-  Es[0] = Es[2 * kb];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1060,7 +1131,7 @@ static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, di
   kp.kernelParams = drive_args;
   if (cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp) != cudaSuccess) return PC_ERR_CUDA;
   kp.func = mixed ? (void *)lo_rk4_kernel<true> : (void *)lo_rk4_kernel<false>;
-  kp.gridDim = dim3(rgrid);
+  kp.gridDim = dim3((unsigned)(((size_t)a.B * a.N * 32 + 127) / 128));  // one warp per receiver
   kp.blockDim = dim3(128);
   kp.kernelParams = rk4_args;
   if (cudaGraphAddKernelNode(&n2, body, &n1, 1, &kp) != cudaSuccess) return PC_ERR_CUDA;
@@ -1104,9 +1175,11 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const bool grid = dp->N > pc::kSmallN;
   const size_t part_bytes = grid ? al((size_t)pc::kMaxSplit * es_bytes) : 0;
   const size_t blk_bytes = al(2 * sizeof(int64_t));
+  const size_t tab_bytes = al(nbn * pc::kTab * sizeof(double));
   const size_t part_off = es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes + ke_bytes;
   const size_t blk_off = part_off + part_bytes;
-  if (ctx->run_scratch.reserve(blk_off + blk_bytes) != cudaSuccess) return PC_ERR_CUDA;
+  const size_t tab_off = blk_off + blk_bytes;
+  if (ctx->run_scratch.reserve(tab_off + tab_bytes) != cudaSuccess) return PC_ERR_CUDA;
   char *scr = (char *)ctx->run_scratch.ptr;
   pc::RunArgs a;
   a.B = dp->B;
@@ -1136,6 +1209,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.Epart = nullptr;
   a.nsplit = 1;
   a.blk = nullptr;
+  a.rk4tab = (double *)(scr + tab_off);
   a.org_pos = motion ? motion->pos : nullptr;
   a.org_vel = motion ? motion->vel : nullptr;
   a.org_acc = motion ? motion->acc : nullptr;

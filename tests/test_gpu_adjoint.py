@@ -194,16 +194,19 @@ def test_rates_adjoint_vs_gpu_finite_differences(ctx):
     out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=pc.PC_F64, fit=True,
                             first_index=cfg.first_index, want_energy=False)
     assert torch.equal(gam, out["gamma"]) and torch.equal(om, out["omega"])
-    # the fitted rates bend faster with the geometry than the final energy: on this configuration
-    # 6e-13 m left an h^2 error of 2.6e-4 and a quarter of it 2e-5
-    hs = _rates_steps(cfg, 1.5e-13)
+    # the fitted rates bend faster with the geometry than the final energy (on this configuration
+    # a 6e-13 m central difference carries an h^2 error of 2.6e-4) and the fit amplifies the run's
+    # rounding, so small steps are noisy: Richardson extrapolation of the central differences at
+    # h and 2h cancels the h^2 term and keeps the step large
+    hs = _rates_steps(cfg, 6e-13)
     for name in ("origin", "omega0", "d0"):
         arr = getattr(cfg, name)
         fd = np.zeros_like(arr)
         for idx in np.ndindex(arr.shape):
             h = hs[name]
-            fd[idx] = (_rates_loss_gpu(ctx, _perturbed(cfg, name, idx, h), wg, ww) -
-                       _rates_loss_gpu(ctx, _perturbed(cfg, name, idx, -h), wg, ww)) / (2 * h)
+            d1, d2 = [(_rates_loss_gpu(ctx, _perturbed(cfg, name, idx, k * h), wg, ww) -
+                       _rates_loss_gpu(ctx, _perturbed(cfg, name, idx, -k * h), wg, ww)) / (2 * k * h) for k in (1, 2)]
+            fd[idx] = (4.0 * d1 - d2) / 3.0
         _check(g[name], fd, 1e-4)
     # rates are nearly invariant under a common scaling of all moments of a configuration: the
     # run is linear in d0 up to the finite charge separation (multipole terms of relative size
