@@ -11,7 +11,8 @@ dipole-steps/s, the end-to-end number through the C ABI with host buffers, the r
 field kernel, clocks sampled during the timed region and the FP64 CPU oracle on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --profile fields_mixed_small|fields_f64_small|lo_small   (one small run for ncu)
+  python bench.py --profile fields_mixed_small|fields_f64_small|lo_small|ring_small|adj_small
+                                                     (one small run for ncu)
 Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own copy of the workload
 (independent problems, no data-path collective), so scaling is weak.
 """
@@ -189,7 +190,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", default=None, choices=["fields_mixed_small", "fields_f64_small", "lo_small"])
+    ap.add_argument("--profile", default=None,
+                    choices=["fields_mixed_small", "fields_f64_small", "lo_small", "ring_small", "adj_small"])
     ap.add_argument("--no-extra", action="store_true", help="skip the float64, oscillator and CPU legs")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -222,9 +224,19 @@ def main():
         elif args.profile == "fields_f64_small":
             pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=64,
                                nv=2048, times=list(times[:1]), precision=pc.PC_F64)
-        else:
+        elif args.profile == "lo_small":
+            # batched pairs, mixed: one persistent launch over 2000 steps
             cfg, _ = W.cfg3(B=256, n_steps=2000)
-            pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps)
+            pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=pc.PC_MIXED)
+        elif args.profile == "ring_small":
+            # 256-oscillator ring, mixed, grid path: 200 steps (13 causal blocks)
+            cfg = W.cfg4(n_steps=200)
+            pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=pc.PC_MIXED)
+        else:
+            # adjoint of the ring's float64 run over 200 steps
+            cfg = W.cfg4(n_steps=200)
+            w = torch.ones((1, cfg.N), dtype=torch.float64, device=dev)
+            pc.pc_dipoles_adjoint(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, w)
         torch.cuda.synchronize()
         return 0
 
