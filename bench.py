@@ -56,6 +56,23 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of a per-rank scalar over all ranks (the slowest rank sets the job time)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_per_rank, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` replicas that each process units_per_rank: the total units
+    over the slowest rank's time (weak scaling, no data-path collective)."""
+    return world * units_per_rank / max_over_ranks(seconds_per_rank, dist, device)
+
+
 def rank_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
@@ -265,12 +282,8 @@ def main():
         if dist:
             dist.barrier()
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * pairs_per_step * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(ms), dist, dev)
+    value = whole_job_rate(pairs_per_step * args.steps, total_ms * 1e-3, world)
     kernel_ms = min(ms)  # dominant kernel: fields_mixed_kernel (prep kernel < 0.1 % of the step)
     avg_ms = total_ms / args.steps
 
@@ -299,11 +312,7 @@ def main():
     for _ in range(n_e2e):
         e2e_step()
     e2e_sec = (time.perf_counter() - t0) / n_e2e
-    if dist:
-        t = torch.tensor([e2e_sec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
-    e2e_value = world * pairs_per_step / e2e_sec
+    e2e_value = whole_job_rate(pairs_per_step, e2e_sec, world, dist, dev)
 
     # ---- roofline of the field kernel (float32 ALU) ----
     fp32_fma, fp64_fma = pc.pc_alu_peaks(ctx)

@@ -57,9 +57,14 @@ struct RunArgs {
   // per dipole: the RK4 step as an affine map y' = M y + c1 e1 + c2 e2 + c4 e4, as
   // [B][N][kTab]: M^1 .. M^kMaxBlock (row-major 2x2 each), then c1, c2, c4
   double *rk4tab;
+  double e_unit;  // k_e e / (c dt)^2: the float32 driving field's unit (V/m)
 };
 
-constexpr int kTab = 4 * 16 + 6;
+// then the dipole's constants, so that no block recomputes them (float64 divisions are costly on
+// this GPU): gamma0, omega0^2, q^2/m, the largest charge-speed factor, 1/(q L), 1/(q c), dt/(q c),
+// m/(2 q^2), and the charges' signed offsets per unit moment m2/((m1+m2) q), -m1/((m1+m2) q)
+constexpr int kTabC = 4 * 16 + 6;
+constexpr int kTab = kTabC + 10;
 
 constexpr int kDipF = 12;
 
@@ -102,6 +107,17 @@ __device__ void rk4_table(const RunArgs &a, size_t bi) {
     for (int e = 0; e < 4; ++e) P[e] = Q[e];
   }
   for (int e = 0; e < 6; ++e) T[64 + e] = c[e];
+  const double L = kC * dt;
+  T[kTabC + 0] = g0;
+  T[kTabC + 1] = w2;
+  T[kTabC + 2] = qm;
+  T[kTabC + 3] = fmax(m1, m2) / (m1 + m2) / q;
+  T[kTabC + 4] = 1.0 / (q * L);
+  T[kTabC + 5] = 1.0 / (q * kC);
+  T[kTabC + 6] = dt / (q * kC);
+  T[kTabC + 7] = m / (2.0 * q * q);
+  T[kTabC + 8] = m2 / (m1 + m2) / q;
+  T[kTabC + 9] = -m1 / (m1 + m2) / q;
 }
 
 // The kb steps of a causal block at once, one lane per step: with every stage field of the block
@@ -113,15 +129,10 @@ template <bool MIXED>
 __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop) {
   const int lane = threadIdx.x & 31;
   const int64_t S = a.n_steps + 1;
-  const double L = kC * a.dt;
   const size_t bi = bidx(a, b, i);
   double *Es = a.Es + bi * (2 * kMaxBlock + 1);
   const double *T = a.rk4tab + bi * kTab;
-  const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
-  const double m = m1 * m2 / (m1 + m2);
-  const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
-  const double qm = q * q / m;
-  const double vfac = fmax(m1, m2) / (m1 + m2) / q;
+  const double g0 = T[kTabC + 0], w2 = T[kTabC + 1], qm = T[kTabC + 2], vfac = T[kTabC + 3];
   const double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
   double vx = 0.0, vy = 0.0, e2 = 0.0, e4 = 0.0;
   if (lane < kb) {
@@ -146,16 +157,16 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
     const double yn0 = P[0] * y0 + P[1] * y1 + vx;
     const double yn1 = P[2] * y0 + P[3] * y1 + vy;
     const int64_t n = n0 + lane;
-    const double ydd = qm * e4 - g0 * yn1 - w0 * w0 * yn0;
+    const double ydd = qm * e4 - g0 * yn1 - w2 * yn0;
     a.d[bi * S + n + 1] = yn0;
     a.dd[bi * S + n + 1] = yn1;
     a.ddd[bi * S + n + 1] = ydd;
     if (MIXED)
       a.H32[bi * S + n + 1] =
-          make_float4((float)(yn0 / (q * L)), (float)(yn1 / (q * kC)), (float)(ydd * a.dt / (q * kC)), 0.f);
+          make_float4((float)(yn0 * T[kTabC + 4]), (float)(yn1 * T[kTabC + 5]), (float)(ydd * T[kTabC + 6]), 0.f);
     if (a.Ed) a.Ed[bi * S + n + 1] = e4;
     if (a.Ehalf) a.Ehalf[bi * a.n_steps + n] = e2;
-    if (a.energy) a.energy[bi * S + n + 1] = m * (w0 * w0 * yn0 * yn0 + yn1 * yn1) / (2.0 * q * q);
+    if (a.energy) a.energy[bi * S + n + 1] = T[kTabC + 7] * (w2 * yn0 * yn0 + yn1 * yn1);
     bad = fabs(yn1) * vfac > a.v_max;
   }
   if (__any_sync(0xffffffffu, bad)) {
@@ -193,12 +204,13 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
     tr.Ra = a.org_acc + bj * H * 3;
     for (int k = 0; k < 3; ++k) tr.R[k] = tr.Rp[6 * nv + k];  // the source now, for the first guess
   }
-  const double q = a.q[bj], m1 = a.m1[bj], m2 = a.m2[bj];
+  const double q = a.q[bj];
+  const double *Tj = a.rk4tab + bj * kTab;
   double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
   const int64_t kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
   double E[3] = {0.0, 0.0, 0.0};
   for (int sg = 0; sg < 2; ++sg) {
-    tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+    tr.w = Tj[kTabC + 8 + sg];
     double p0[3], v[3] = {0, 0, 0}, ac[3] = {0, 0, 0};
     if (nv == 0) {
       // only the static pre-history exists: the root must precede t = 0
@@ -330,7 +342,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       }
     }
   }
-  double mine = MIXED ? (double)accf * (kKe * kE / ((kC * a.dt) * (kC * a.dt))) : accd;
+  double mine = MIXED ? (double)accf * a.e_unit : accd;
   sh[lane] = (m < slots) ? mine : 0.0;
   __syncwarp();
   if (lane < nst) {
@@ -1210,6 +1222,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.nsplit = 1;
   a.blk = nullptr;
   a.rk4tab = (double *)(scr + tab_off);
+  a.e_unit = pc::kKe * pc::kE / ((pc::kC * dt) * (pc::kC * dt));
   a.org_pos = motion ? motion->pos : nullptr;
   a.org_vel = motion ? motion->vel : nullptr;
   a.org_acc = motion ? motion->acc : nullptr;
