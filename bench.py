@@ -295,14 +295,14 @@ def main():
     d2h = sum(v.numel() * v.element_size() for v in out.values())
 
     def e2e_step():
+        # host inputs to the device, then the library's host-output entry point: it computes the
+        # frames in chunks and copies each chunk back while the next one computes
         dev_in = {k: v.to(dev, non_blocking=True) for k, v in pin_in.items()}
         from types import SimpleNamespace
 
         dps = SimpleNamespace(t0=dp.t0, dt=dp.dt, **dev_in)
-        pc.pc_fields_plane(ctx, dipoles=dps, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=NU, nv=NV,
-                           times=list(times), precision=pc.PC_MIXED, out=out)
-        for k in out:
-            pin_out[k].copy_(out[k], non_blocking=True)
+        pc.pc_fields_plane_to_host(ctx, dipoles=dps, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=NU,
+                                   nv=NV, times=list(times), precision=pc.PC_MIXED, out=pin_out)
         torch.cuda.current_stream(dev).synchronize()
 
     e2e_step()

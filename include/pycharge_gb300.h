@@ -154,6 +154,23 @@ pc_status pc_fields_param(pc_ctx *ctx, const pc_param_charges *ch, const double 
                           const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,
                           void *stream);
 
+/*
+ * pc_fields_to_host / pc_fields_plane_to_host -- pc_fields / pc_fields_plane with the outputs
+ * delivered to HOST memory: out_host holds host pointers ([T][P][...] as in pc_field_out).  The
+ * frames are computed in chunks of about 256 MB of outputs into two alternating device buffers
+ * owned by the context, and each chunk is copied to the host on a second stream while the next
+ * chunk computes, so the copies overlap the computation.  For the copies to run asynchronously the
+ * host buffers must be page-locked (cudaHostAlloc / cudaHostRegister); pageable buffers still
+ * work, with the copies serialized.  The call returns when every copy has landed.  Sources and
+ * points stay on the device.  Errors: those of pc_fields.
+ */
+pc_status pc_fields_to_host(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const double *points,
+                            int64_t P, const double *times, int32_t T, int32_t kind, int32_t precision,
+                            double r_excl, const pc_field_out *out_host, void *stream);
+pc_status pc_fields_plane_to_host(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,
+                                  const pc_plane *grid, const double *times, int32_t T, int32_t kind,
+                                  int32_t precision, double r_excl, const pc_field_out *out_host, void *stream);
+
 /* pc_fields on a plane grid (P = nu*nv points generated on the device); same semantics. */
 pc_status pc_fields_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const pc_plane *grid,
                           const double *times, int32_t T, int32_t kind, int32_t precision, double r_excl,

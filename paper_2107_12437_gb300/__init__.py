@@ -27,5 +27,6 @@ from .capi import (  # noqa: F401
     pc_fields,
     pc_fields_param,
     pc_fields_plane,
+    pc_fields_plane_to_host,
     pc_ke_fit,
 )

@@ -89,6 +89,12 @@ SIGNATURES = {
                                        ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                       ctypes.POINTER(PcRunOut), _vp]),
+    "pc_fields_to_host": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
+                                         ctypes.POINTER(_f64), _i32, _i32, _i32, _f64, ctypes.POINTER(PcFieldOut),
+                                         _vp]),
+    "pc_fields_plane_to_host": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources),
+                                               ctypes.POINTER(PcPlane), ctypes.POINTER(_f64), _i32, _i32, _i32, _f64,
+                                               ctypes.POINTER(PcFieldOut), _vp]),
     "pc_fields_param": (ctypes.c_int, [_vp, ctypes.POINTER(PcParamCharges), _vp, _i64, ctypes.POINTER(_f64), _i32,
                                        _i32, _f64, ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run_moving": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), ctypes.POINTER(PcDipoleMotion), _f64,
@@ -226,6 +232,18 @@ def alloc_field_out(P, T, precision, device="cuda", which=("E", "B", "phi", "A",
     return o
 
 
+def _hptr(t):
+    if t is None:
+        return None
+    assert not t.is_cuda and t.is_contiguous(), "host outputs must be contiguous CPU tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_out_struct(o):
+    return PcFieldOut(E=_hptr(o.get("E")), B=_hptr(o.get("B")), phi=_hptr(o.get("phi")), A=_hptr(o.get("A")),
+                      mask=_hptr(o.get("mask")))
+
+
 def _out_struct(o):
     return PcFieldOut(E=_ptr(o.get("E")), B=_ptr(o.get("B")), phi=_ptr(o.get("phi")), A=_ptr(o.get("A")),
                       mask=_ptr(o.get("mask")))
@@ -261,6 +279,30 @@ def pc_fields_plane(ctx, charges=None, dipoles=None, origin=(0, 0, 0), eu=(1, 0,
                                  ctypes.byref(pl), tarr, T, kind, precision, float(r_excl),
                                  ctypes.byref(_out_struct(o)), _stream(stream))
     _check(st, "pc_fields_plane")
+    return o
+
+
+def alloc_host_field_out(P, T, precision, which=("E", "B", "phi", "A", "mask")):
+    """Page-locked host outputs for pc_fields_plane_to_host / pc_fields_to_host."""
+    dt = torch.float64 if precision == PC_F64 else torch.float32
+    shapes = {"E": (T, P, 3), "B": (T, P, 3), "phi": (T, P), "A": (T, P, 3), "mask": (T, P)}
+    return {k: torch.empty(shapes[k], dtype=torch.uint8 if k == "mask" else dt, pin_memory=True) for k in which}
+
+
+def pc_fields_plane_to_host(ctx, charges=None, dipoles=None, origin=(0, 0, 0), eu=(1, 0, 0), ev=(0, 1, 0), nu=1,
+                            nv=1, times=(0.0,), kind=PC_TOTAL, precision=PC_F64, r_excl=0.0, out=None, stream=None):
+    """pc_fields_plane_to_host: sources on the device, outputs (page-locked host tensors) on the host."""
+    T = len(times)
+    o = alloc_host_field_out(nu * nv, T, precision) if out is None else out
+    pl = PcPlane(origin=(_f64 * 3)(*origin), eu=(_f64 * 3)(*eu), ev=(_f64 * 3)(*ev), nu=nu, nv=nv)
+    tarr = (_f64 * T)(*[float(t) for t in times])
+    chs = _charges_struct(charges)
+    dps = _dipoles_struct(dipoles)
+    st = ctx.lib.pc_fields_plane_to_host(ctx.handle, ctypes.byref(chs) if chs else None,
+                                         ctypes.byref(dps) if dps else None, ctypes.byref(pl), tarr, T, kind,
+                                         precision, float(r_excl), ctypes.byref(_host_out_struct(o)),
+                                         _stream(stream))
+    _check(st, "pc_fields_plane_to_host")
     return o
 
 

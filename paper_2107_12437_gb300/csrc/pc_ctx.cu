@@ -54,6 +54,10 @@ extern "C" pc_status pc_ctx_destroy(pc_ctx *ctx) {
   ctx->adj_scratch.release();
   if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
   if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
+  ctx->out_chunks.release();
+  for (int k = 0; k < 4; ++k)
+    if (ctx->pipe_ev[k]) cudaEventDestroy(ctx->pipe_ev[k]);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   delete ctx;
   return PC_OK;
 }

@@ -16,6 +16,8 @@
 //            with Kahan compensation.
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "pc_internal.cuh"
 #include "pc_lw_f32.cuh"
 #include "pc_lw_f64.cuh"
@@ -789,9 +791,18 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
 // ================================================================================================
 static bool finite3(const double *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
 
+// Host outputs: frames are computed in chunks into two device buffers that alternate, and each
+// chunk is copied to the host on a second stream while the next chunk computes.
+struct HostPipe {
+  bool on = false;
+  int32_t frames = 1;        // frames per chunk
+  size_t bytes_frame = 0;    // device bytes of one frame of every requested output
+};
+
 static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const double *list,
                              const pc_plane *plane, int64_t P, const double *times, int32_t T, int32_t kind,
-                             int32_t precision, double r_excl, const pc_field_out *out, void *stream) {
+                             int32_t precision, double r_excl, const pc_field_out *out, void *stream,
+                             bool to_host = false) {
   if (!ctx || !out || !times || T < 1 || P < 0) return PC_ERR_ARG;
   if (kind < PC_TOTAL || kind > PC_RADIATION || (precision != PC_F64 && precision != PC_MIXED)) return PC_ERR_ARG;
   if (!(r_excl >= 0.0)) return PC_ERR_ARG;
@@ -883,10 +894,51 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
       prep_charges_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hc, (double *)ctx->charge_ref.ptr);
     }
   }
-  for (int32_t f0 = 0; f0 < T; f0 += kMaxT) {
-    L.T = min(kMaxT, T - f0);
+  // host outputs: chunk sizes, device buffers, the copy stream and its events
+  const size_t elt = precision == PC_F64 ? sizeof(double) : sizeof(float);
+  const size_t b_vec = (size_t)P * 3 * elt, b_sca = (size_t)P * elt, b_msk = (size_t)P;
+  HostPipe hp;
+  char *slot_base[2] = {nullptr, nullptr};
+  if (to_host) {
+    hp.on = true;
+    hp.bytes_frame = (out->E ? b_vec : 0) + (out->B ? b_vec : 0) + (out->A ? b_vec : 0) + (out->phi ? b_sca : 0) +
+                     (out->mask ? b_msk : 0);
+    if (hp.bytes_frame == 0) return end_call(ctx, st);
+    const size_t target = (size_t)256 << 20;  // about 256 MB per chunk
+    hp.frames = (int32_t)std::max<size_t>(1, std::min<size_t>((size_t)kMaxT, target / hp.bytes_frame));
+    const size_t slot = hp.bytes_frame * hp.frames;
+    if (ctx->out_chunks.reserve(2 * slot) != cudaSuccess) return PC_ERR_CUDA;
+    slot_base[0] = (char *)ctx->out_chunks.ptr;
+    slot_base[1] = slot_base[0] + slot;
+    if (!ctx->copy_stream) {
+      if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return PC_ERR_CUDA;
+      for (int k = 0; k < 4; ++k)
+        if (cudaEventCreateWithFlags(&ctx->pipe_ev[k], cudaEventDisableTiming) != cudaSuccess) return PC_ERR_CUDA;
+    }
+  }
+  const int32_t step = hp.on ? hp.frames : kMaxT;
+  int chunk = 0;
+  for (int32_t f0 = 0; f0 < T; f0 += step, ++chunk) {
+    L.T = min(step, T - f0);
     L.frame0 = f0;
     for (int i = 0; i < L.T; ++i) L.times[i] = times[f0 + i];
+    const int sl = chunk & 1;
+    if (hp.on) {
+      // this chunk's device slot: wait until the copy of the chunk before last has left it
+      if (chunk >= 2 && cudaStreamWaitEvent(st, ctx->pipe_ev[2 + sl], 0) != cudaSuccess) return PC_ERR_CUDA;
+      char *c = slot_base[sl];
+      const size_t nf = (size_t)L.T;
+      L.out.E = out->E ? (void *)c : nullptr;
+      c += out->E ? nf * b_vec : 0;
+      L.out.B = out->B ? (void *)c : nullptr;
+      c += out->B ? nf * b_vec : 0;
+      L.out.A = out->A ? (void *)c : nullptr;
+      c += out->A ? nf * b_vec : 0;
+      L.out.phi = out->phi ? (void *)c : nullptr;
+      c += out->phi ? nf * b_sca : 0;
+      L.out.mask = out->mask ? (uint8_t *)c : nullptr;
+      L.frame0 = 0;
+    }
     if (precision == PC_F64) {
       dim3 grid((unsigned)((P + 127) / 128), (unsigned)L.T);
       if (kind == PC_TOTAL) fields_f64_kernel<PC_TOTAL><<<grid, 128, 0, st>>>(L);
@@ -912,6 +964,29 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
         else fields_mixed_kernel<PC_RADIATION, false><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
       }
     }
+    if (hp.on) {
+      // copy the chunk to the host on the copy stream once its kernel is done
+      cudaStream_t cs = ctx->copy_stream;
+      if (cudaEventRecord(ctx->pipe_ev[sl], st) != cudaSuccess || cudaStreamWaitEvent(cs, ctx->pipe_ev[sl], 0) != cudaSuccess)
+        return PC_ERR_CUDA;
+      const size_t nf = (size_t)L.T;
+      const size_t o = (size_t)f0;
+      bool ok = true;
+      if (out->E) ok = ok && cudaMemcpyAsync((char *)out->E + o * b_vec, L.out.E, nf * b_vec, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+      if (out->B) ok = ok && cudaMemcpyAsync((char *)out->B + o * b_vec, L.out.B, nf * b_vec, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+      if (out->A) ok = ok && cudaMemcpyAsync((char *)out->A + o * b_vec, L.out.A, nf * b_vec, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+      if (out->phi)
+        ok = ok && cudaMemcpyAsync((char *)out->phi + o * b_sca, L.out.phi, nf * b_sca, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+      if (out->mask)
+        ok = ok && cudaMemcpyAsync(out->mask + o * b_msk, L.out.mask, nf * b_msk, cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+      if (!ok || cudaEventRecord(ctx->pipe_ev[2 + sl], cs) != cudaSuccess) return PC_ERR_CUDA;
+    }
+  }
+  if (hp.on) {
+    // the caller's stream ends after the last copy, so the status read-back below covers them all
+    if (cudaEventRecord(ctx->pipe_ev[2], ctx->copy_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(st, ctx->pipe_ev[2], 0) != cudaSuccess)
+      return PC_ERR_CUDA;
   }
   return end_call(ctx, st);
 }
@@ -923,6 +998,22 @@ extern "C" pc_status pc_fields(pc_ctx *ctx, const pc_charges *ch, const pc_dipol
                                double r_excl, const pc_field_out *out, void *stream) {
   if (P > 0 && !points) return PC_ERR_ARG;
   return pc::fields_impl(ctx, ch, dp, points, nullptr, P, times, T, kind, precision, r_excl, out, stream);
+}
+
+extern "C" pc_status pc_fields_to_host(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,
+                                       const double *points, int64_t P, const double *times, int32_t T, int32_t kind,
+                                       int32_t precision, double r_excl, const pc_field_out *out_host, void *stream) {
+  if (P > 0 && !points) return PC_ERR_ARG;
+  return pc::fields_impl(ctx, ch, dp, points, nullptr, P, times, T, kind, precision, r_excl, out_host, stream, true);
+}
+
+extern "C" pc_status pc_fields_plane_to_host(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,
+                                             const pc_plane *grid, const double *times, int32_t T, int32_t kind,
+                                             int32_t precision, double r_excl, const pc_field_out *out_host,
+                                             void *stream) {
+  if (!grid || grid->nu < 0 || grid->nv < 0) return PC_ERR_ARG;
+  return pc::fields_impl(ctx, ch, dp, nullptr, grid, grid->nu * grid->nv, times, T, kind, precision, r_excl,
+                         out_host, stream, true);
 }
 
 extern "C" pc_status pc_fields_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,

@@ -241,3 +241,23 @@ def test_many_frames_split_launches(ctx):
     out = pc.pc_fields(ctx, charges=pc.charges_to_device(ch), points=torch.as_tensor(sel, device="cuda"),
                        times=list(times), r_excl=R_EXCL)
     compare(out, ref, pc.PC_F64, ("E", "phi"))
+
+
+def test_plane_to_host_matches_device_outputs(ctx):
+    # 1024 x 2048 points, 5 frames: 86 MB of float32 outputs per frame, so the host pipeline runs
+    # three chunks (two frames each, the last one short) through its two alternating buffers
+    dp, g, z, times = W.cfg2()
+    dpd = pc.dipoles_to_device(dp)
+    step = float(g[1] - g[0])
+    kw = dict(dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=1024, nv=2048,
+              times=[float(t) for t in times[:5]], precision=pc.PC_MIXED)
+    dev = pc.pc_fields_plane(ctx, **kw)
+    host = pc.pc_fields_plane_to_host(ctx, **kw)
+    for k in ("E", "B", "phi", "A", "mask"):
+        assert torch.equal(host[k], dev[k].cpu()), k
+    # float64 outputs and a subset of outputs
+    kw64 = dict(kw, nu=64, precision=pc.PC_F64)
+    dev64 = pc.pc_fields_plane(ctx, **kw64)
+    out = pc.capi.alloc_host_field_out(64 * 2048, 5, pc.PC_F64, which=("E", "phi"))
+    host64 = pc.pc_fields_plane_to_host(ctx, out=out, **kw64)
+    assert torch.equal(host64["E"], dev64["E"].cpu()) and torch.equal(host64["phi"], dev64["phi"].cpu())
