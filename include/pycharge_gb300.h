@@ -148,7 +148,8 @@ typedef struct {
  * acceleration, so no history interpolation enters; `kind` selects Eq. E, ECoulomb or Eradiation.
  * The charges must stay slower than light.
  *   points  device [P][3];  times host [T];  r_excl, out as for pc_fields (PC_F64 layout)
- * Errors: PC_ERR_ARG, PC_ERR_NOCONV (no bracket or no convergence), PC_ERR_CUDA.
+ * Errors: PC_ERR_ARG (also for a kind outside PC_TRAJ_*, found on the device), PC_ERR_NOCONV (no
+ * bracket or no convergence), PC_ERR_CUDA.
  */
 pc_status pc_fields_param(pc_ctx *ctx, const pc_param_charges *ch, const double *points, int64_t P,
                           const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,

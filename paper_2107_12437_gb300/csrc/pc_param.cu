@@ -118,6 +118,10 @@ __global__ void __launch_bounds__(128) fields_param_kernel(const ParamLaunch L) 
   uint8_t mask = 0;
   for (int c = 0; c < L.M; ++c) {
     const int kd = __ldg(L.kind + c);
+    if (kd < PC_TRAJ_STATIONARY || kd > PC_TRAJ_ACCELERATING) {
+      set_status(L.status, PC_ERR_ARG);
+      return;
+    }
     const double *p = L.par + 12 * c;
     double tp;
     const int e = param_retarded(kd, p, t, r, &tp);

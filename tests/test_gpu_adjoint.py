@@ -249,3 +249,16 @@ def test_fitted_rates_autograd(ctx):
     g, _, _ = _rates_adjoint(ctx, cfg, wg, ww)
     assert np.allclose(dp.origin.grad.cpu().numpy(), g["origin"], rtol=1e-12, atol=0)
     assert np.allclose(dp.omega0.grad.cpu().numpy(), g["omega0"], rtol=1e-12, atol=0)
+
+
+def test_adjoint_grid_path_configuration(ctx):
+    # more than 64 dipoles: the forward runs on the grid path (source slices, graph loop); the
+    # adjoint of two d0 components and one origin coordinate against central differences
+    cfg = W.cfg5(N=72, n_steps=120, side=160e-9, min_spacing=14e-9, seed=W.SEED_CFG5 + 11)
+    w = _weights(cfg, seed=21)
+    g = _adjoint(ctx, cfg, w)
+    for name, idx, h in (("d0", (0, 3), 1e-6 * cfg.d0[0, 3]), ("d0", (0, 40), 1e-6 * cfg.d0[0, 40]),
+                         ("origin", (0, 7, 1), 5e-13)):
+        fd = (_loss_gpu(ctx, _perturbed(cfg, name, idx, h), w) - _loss_gpu(ctx, _perturbed(cfg, name, idx, -h), w)) / (2 * h)
+        scale = np.abs(g[name]).max()
+        assert abs(g[name][idx] - fd) <= 1e-4 * scale, (name, idx, g[name][idx], fd)

@@ -261,3 +261,18 @@ def test_plane_to_host_matches_device_outputs(ctx):
     out = pc.capi.alloc_host_field_out(64 * 2048, 5, pc.PC_F64, which=("E", "phi"))
     host64 = pc.pc_fields_plane_to_host(ctx, out=out, **kw64)
     assert torch.equal(host64["E"], dev64["E"].cpu()) and torch.equal(host64["phi"], dev64["phi"].cpu())
+
+
+def test_plane_to_host_many_frames_and_empty(ctx):
+    # more frames than one launch takes and a grid with no points
+    dp, g, z, times = W.cfg2()
+    dpd = pc.dipoles_to_device(dp)
+    step = float(g[1] - g[0])
+    tt = [float(t) for t in np.linspace(times[0], times[-1], 40)]
+    kw = dict(dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=16, nv=256, times=tt,
+              precision=pc.PC_MIXED)
+    dev = pc.pc_fields_plane(ctx, **kw)
+    host = pc.pc_fields_plane_to_host(ctx, **kw)
+    assert torch.equal(host["E"], dev["E"].cpu()) and torch.equal(host["mask"], dev["mask"].cpu())
+    empty = pc.pc_fields_plane_to_host(ctx, **dict(kw, nu=0))
+    assert empty["E"].shape == (40, 0, 3)

@@ -70,3 +70,16 @@ def test_param_removes_interpolation_error(ctx):
     es = np.linalg.norm(s["E"].cpu().numpy() - exact["E"], axis=-1) / np.linalg.norm(exact["E"], axis=-1)
     assert ea.max() < 1e-12
     assert es.max() > 1e3 * ea.max()  # interpolation error of the sampled history
+
+
+def test_param_many_frames_and_empty(ctx):
+    kind, q, par, pts = W.param_charges()
+    times = list(np.linspace(0.0, 2e-14, 37))  # more frames than one launch takes
+    out = pc.pc_fields_param(ctx, kind, q, par, torch.tensor(pts[:40], device="cuda"), times)
+    ref = oracle.fields_param(pts[:40], times, kind, q, par)
+    err = np.linalg.norm(out["E"].cpu().numpy() - ref["E"], axis=-1) / np.linalg.norm(ref["E"], axis=-1)
+    assert err.max() < 1e-9
+    empty = pc.pc_fields_param(ctx, kind, q, par, torch.zeros((0, 3), dtype=torch.float64, device="cuda"), times)
+    assert empty["E"].shape == (37, 0, 3)
+    with pytest.raises(pc.PcError):
+        pc.pc_fields_param(ctx, [7], [1.0], np.zeros((1, 12)), torch.tensor(pts[:4], device="cuda"), [0.0])
