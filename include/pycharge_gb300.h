@@ -328,6 +328,29 @@ pc_status pc_dipoles_rates_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt,
                                    double *gamma, double *omega, const pc_dipole_grads *g, void *stream);
 
 /*
+ * pc_dipoles_fields_adjoint -- reverse-mode gradient of a loss on the fields of the oscillators
+ * themselves: L = sum over configurations, frames and points of <cE, E> + <cB, B> + cphi phi +
+ * <cA, A>, where E, B, phi, A are the fields of configuration b's dipoles (Sec. 2.2, Eqs. E, B,
+ * V, A, both charges of every dipole) at the points and times, on the history of the float64 run
+ * of pc_dipoles_run from t = 0 (the moments rest at d0 before).  The paper has no adjoint.  Each
+ * field term is reversed through the Lienard-Wiechert expressions, the interpolation and the
+ * retarded time (implicit-function theorem); the resulting adjoints of the dipoles' history
+ * samples and origins seed the reverse sweep of pc_dipoles_adjoint, which carries them to the
+ * origins, omega0 and d0.
+ *   dp, dt, n_steps, opts   as for pc_dipoles_adjoint (PC_F64, ed_mode 0)
+ *   points                  device [P][3]; times host [T], 0 <= t (retarded times must fall
+ *                           inside the run's samples)
+ *   cot                     device float64 cotangents [B][T][P][3] (E, B, A) and [B][T][P] (phi),
+ *                           any may be NULL; cot->mask must be NULL
+ *   g                       gradients (device)
+ * Errors: those of pc_dipoles_adjoint; PC_ERR_HISTORY for times past the run; PC_ERR_NOCONV when
+ * the points' delays from a source span more than 8 500 samples.
+ */
+pc_status pc_dipoles_fields_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
+                                    const pc_run_opts *opts, const double *points, int64_t P, const double *times,
+                                    int32_t T, const pc_field_out *cot, const pc_dipole_grads *g, void *stream);
+
+/*
  * pc_alu_peaks -- measures this GPU's float32 and float64 fused-multiply-add throughput (FMA/s)
  * with dependent-chain kernels; used as roofline denominators.  Writes fp32_fma_per_s,
  * fp64_fma_per_s (host pointers).

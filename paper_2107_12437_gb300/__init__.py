@@ -21,6 +21,7 @@ from .capi import (  # noqa: F401
     load,
     pc_alu_peaks,
     pc_dipoles_adjoint,
+    pc_dipoles_fields_adjoint,
     pc_dipoles_rates_adjoint,
     pc_dipoles_run,
     pc_dipoles_run_moving,

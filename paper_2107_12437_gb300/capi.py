@@ -104,6 +104,9 @@ SIGNATURES = {
     "pc_dipoles_rates_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64,
                                                 ctypes.POINTER(PcRunOpts), _vp, _vp, _vp, _vp,
                                                 ctypes.POINTER(PcDipoleGrads), _vp]),
+    "pc_dipoles_fields_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64,
+                                                 ctypes.POINTER(PcRunOpts), _vp, _i64, ctypes.POINTER(_f64), _i32,
+                                                 ctypes.POINTER(PcFieldOut), ctypes.POINTER(PcDipoleGrads), _vp]),
     "pc_ke_fit": (ctypes.c_int, [_vp, _vp, _i32, _i64, _f64, _i64, _vp, _vp, _vp, _vp, _vp]),
     "pc_alu_peaks": (ctypes.c_int, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _vp]),
     "pc_fields_noalloc": (ctypes.c_int, [ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
@@ -406,6 +409,35 @@ def pc_dipoles_rates_adjoint(ctx, dp, dt, n_steps, first_index, dL_dgamma=None, 
                                           _stream(stream))
     _check(st, "pc_dipoles_rates_adjoint")
     return gamma, omega, g_origin, g_omega0, g_d0
+
+
+def pc_dipoles_fields_adjoint(ctx, dp, dt, n_steps, points, times, cE=None, cB=None, cphi=None, cA=None, v_max=0.0,
+                              stream=None):
+    """pc_dipoles_fields_adjoint: gradients of sum <c, field> of the oscillators' own fields at the
+    points and times; cotangents [B][T][P][3] / [B][T][P] CUDA float64 (any may be None).
+    Returns (g_origin, g_omega0, g_d0)."""
+    B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
+    dev = dp.origin.device
+    pts = torch.as_tensor(points, dtype=torch.float64, device=dev).reshape(-1, 3).contiguous()
+    P, T = int(pts.shape[0]), len(times)
+
+    def c(x):
+        return None if x is None else torch.as_tensor(x, dtype=torch.float64, device=dev).contiguous()
+
+    cot = {k: c(v) for k, v in (("E", cE), ("B", cB), ("phi", cphi), ("A", cA))}
+    g_origin = torch.empty((B, N, 3), dtype=torch.float64, device=dev)
+    g_omega0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
+                  m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=PC_F64)
+    g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
+    tarr = (_f64 * T)(*[float(t) for t in times])
+    st = ctx.lib.pc_dipoles_fields_adjoint(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
+                                           _ptr(pts), P, tarr, T, ctypes.byref(_out_struct(cot)), ctypes.byref(g),
+                                           _stream(stream))
+    _check(st, "pc_dipoles_fields_adjoint")
+    return g_origin, g_omega0, g_d0
 
 
 class FittedRates(torch.autograd.Function):

@@ -1605,6 +1605,159 @@ __global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t
   for (int t = threadIdx.x; t < 3 * W; t += blockDim.x) A.mu[(bj * S + wlo) * 3 + t] += win[t];
 }
 
+// Field-loss seed of the adjoint: L = sum over configurations b, frames f and points p of
+// <cE, E> + <cB, B> + cphi phi + <cA, A> of the configuration's dipoles at the points (Sec. 2.2,
+// Eqs. E, B, V, A on the run's own history).  One CTA per (source dipole, frame, configuration)
+// reverses the field of the source's two charges at every point: the adjoints of its history
+// samples collect in a shared-memory window spanning the points' retarded times (then added to
+// the global history adjoints by atomics, several frames hitting the same samples), the adjoint of
+// its origin by a block sum, and the retarded time is differentiated through its defining equation.
+struct FieldSeed {
+  const double *pts;   // [P][3]
+  int64_t P;
+  int32_t T;
+  const double *times;  // device [T]
+  const double *cE, *cB, *cphi, *cA;  // [B][T][P][3] / [B][T][P], any may be null
+};
+
+__device__ int field_rev_charge(const AdjArgs &A, const TrajF64 &tr, double qc, const double r[3], double u,
+                                int64_t kg, const double *cE, const double *cB, double cphi, const double *cA,
+                                double *win, int64_t wlo, int W, double Rjb[3]) {
+  const RunArgs &a = A.f;
+  const int64_t S = a.n_steps + 1;
+  const double cdt = kC * a.dt;
+  int64_t k = -1;
+  double th = 0.0;
+  const int e = solve_f64(tr, S, 1, r, u, cdt, kg, &k, &th);
+  if (e) return e;
+  const bool stat = k < 0;
+  double p[3], vel[3] = {0, 0, 0}, acc[3] = {0, 0, 0};
+  double Dd = 0, Dv = 0, Da = 0;
+  if (stat) {
+    tr.p(0, p);
+  } else {
+    double p1[3], v1[3], a1[3];
+    tr.p(k, p);
+    tr.p(k + 1, p1);
+    tr.va(k, vel, acc);
+    tr.va(k + 1, v1, a1);
+    Dd = tr.d[k + 1] - tr.d[k];
+    Dv = tr.dd[k + 1] - tr.dd[k];
+    Da = tr.ddd[k + 1] - tr.ddd[k];
+    for (int c = 0; c < 3; ++c) {
+      p[c] += th * (p1[c] - p[c]);
+      vel[c] += th * (v1[c] - vel[c]);
+      acc[c] += th * (a1[c] - acc[c]);
+    }
+  }
+  const double av[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+  double ab[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, accb[3] = {0, 0, 0};
+  lw_full_f64_rev(qc, av, vel, acc, cE, cB, cphi, cA, ab, vb, accb);
+  for (int c = 0; c < 3; ++c) Rjb[c] -= ab[c];  // a = r - p, p = R_j + w d axis
+  const double w = tr.w;
+  const double pb_p = -dot3(ab, tr.ax);
+  if (stat) {
+    if (wlo != 0) return PC_ERR_NOCONV;
+    atomicAdd(&win[0], w * pb_p);
+    return 0;
+  }
+  if (k < wlo || k + 1 >= wlo + W) return PC_ERR_NOCONV;
+  const double Db = w * pb_p, Vb = w * dot3(vb, tr.ax), Ab = w * dot3(accb, tr.ax);
+  const double thb = Db * Dd + Vb * Dv + Ab * Da;
+  const double ap = dot3(av, tr.ax);
+  const double Gth = -2.0 * cdt * cdt * (u - (double)k - th) + 2.0 * w * Dd * ap;
+  const double sfac = -thb / Gth;
+  for (int c = 0; c < 3; ++c) Rjb[c] += sfac * 2.0 * av[c];
+  const double dbar = Db + sfac * 2.0 * ap * w;
+  double *w0p = win + 3 * (k - wlo), *w1p = w0p + 3;
+  atomicAdd(&w0p[0], (1.0 - th) * dbar);
+  atomicAdd(&w0p[1], (1.0 - th) * Vb);
+  atomicAdd(&w0p[2], (1.0 - th) * Ab);
+  atomicAdd(&w1p[0], th * dbar);
+  atomicAdd(&w1p[1], th * Vb);
+  atomicAdd(&w1p[2], th * Ab);
+  return 0;
+}
+
+__global__ void __launch_bounds__(128) fields_adj_kernel(const AdjArgs A, const FieldSeed F, int wmax) {
+  extern __shared__ double win[];  // [wmax][3]
+  __shared__ double s_red[3][128];
+  __shared__ double s_lo[128], s_hi[128];
+  const RunArgs &a = A.f;
+  const int j = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
+  const size_t bj = bidx(a, b, j);
+  const int64_t S = a.n_steps + 1;
+  const double L = kC * a.dt;
+  const double t = F.times[f];
+  const double u = t / a.dt;
+  TrajF64 tr;
+  tr.dipole = true;
+  tr.d = a.d + bj * S;
+  tr.dd = a.dd + bj * S;
+  tr.ddd = a.ddd + bj * S;
+  for (int c = 0; c < 3; ++c) {
+    tr.R[c] = a.origin[3 * bj + c];
+    tr.ax[c] = a.axis[3 * bj + c];
+  }
+  // retarded-sample window of the points
+  double lo = 1e300, hi = -1e300;
+  for (int64_t p = threadIdx.x; p < F.P; p += blockDim.x) {
+    const double dx = F.pts[3 * p] - tr.R[0], dy = F.pts[3 * p + 1] - tr.R[1], dz = F.pts[3 * p + 2] - tr.R[2];
+    const double dist = sqrt(dx * dx + dy * dy + dz * dz) / L;
+    lo = fmin(lo, dist);
+    hi = fmax(hi, dist);
+  }
+  s_lo[threadIdx.x] = lo;
+  s_hi[threadIdx.x] = hi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)blockDim.x; ++q) {
+      lo = fmin(lo, s_lo[q]);
+      hi = fmax(hi, s_hi[q]);
+    }
+    s_lo[0] = lo;
+    s_hi[0] = hi;
+  }
+  __syncthreads();
+  const int64_t wlo = (int64_t)fmax(0.0, floor(u - s_hi[0] - (double)A.margin));
+  int64_t whi = (int64_t)fmin((double)(S - 1), ceil(u - s_lo[0] + (double)A.margin) + 1.0);
+  if (whi < wlo) whi = wlo;
+  const int W = (int)(whi - wlo + 1);
+  if (W > wmax) {
+    if (threadIdx.x == 0) set_status(a.status, PC_ERR_NOCONV);
+    return;
+  }
+  for (int q = threadIdx.x; q < 3 * W; q += blockDim.x) win[q] = 0.0;
+  __syncthreads();
+  const double q = a.q[bj], m1 = a.m1[bj], m2 = a.m2[bj];
+  double Rjb[3] = {0, 0, 0};
+  int err = 0;
+  const size_t base = ((size_t)b * F.T + f) * (size_t)F.P;
+  for (int64_t p = threadIdx.x; p < F.P && !err; p += blockDim.x) {
+    const double r[3] = {F.pts[3 * p], F.pts[3 * p + 1], F.pts[3 * p + 2]};
+    const double *cE = F.cE ? F.cE + 3 * (base + p) : nullptr;
+    const double *cB = F.cB ? F.cB + 3 * (base + p) : nullptr;
+    const double *cA = F.cA ? F.cA + 3 * (base + p) : nullptr;
+    const double cphi = F.cphi ? F.cphi[base + p] : 0.0;
+    const double dv[3] = {r[0] - tr.R[0], r[1] - tr.R[1], r[2] - tr.R[2]};
+    const int64_t kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / L);
+    for (int sg = 0; sg < 2 && !err; ++sg) {
+      tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+      err = field_rev_charge(A, tr, sg == 0 ? q : -q, r, u, kg, cE, cB, cphi, cA, win, wlo, W, Rjb);
+    }
+  }
+  if (err) set_status(a.status, err);
+  for (int c = 0; c < 3; ++c) s_red[c][threadIdx.x] = Rjb[c];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double tt = 0.0;
+    for (int q2 = 0; q2 < (int)blockDim.x; ++q2) tt += s_red[threadIdx.x][q2];
+    atomicAdd(&A.g_origin[3 * bj + threadIdx.x], tt);
+  }
+  for (int q2 = threadIdx.x; q2 < 3 * W; q2 += blockDim.x)
+    if (win[q2] != 0.0) atomicAdd(&A.mu[(bj * S + wlo) * 3 + q2], win[q2]);
+}
+
 __global__ void adj_final_kernel(const AdjArgs A) {
   const RunArgs &a = A.f;
   const int64_t S = a.n_steps + 1;
@@ -1623,7 +1776,8 @@ namespace pc {
 // sum (dL/dgamma gamma + dL/domega omega) of the Eq. KE fit from first_index on.
 static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                               const double *wE, bool rates, const double *dL_dgamma, const double *dL_domega,
-                              double *gamma_out, double *omega_out, const pc_dipole_grads *g, cudaStream_t st) {
+                              double *gamma_out, double *omega_out, const pc_dipole_grads *g, cudaStream_t st,
+                              const FieldSeed *fseed = nullptr) {
   if (!dp || !opts || !g || !g->origin || !g->omega0 || !g->d0) return PC_ERR_ARG;
   if (opts->ed_mode != 0 || opts->precision != PC_F64 || n_steps < 1) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0)) return PC_ERR_ARG;
@@ -1738,6 +1892,15 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   if (smem > 200 * 1024) return PC_ERR_ARG;  // source windows beyond shared memory
   if (cudaFuncSetAttribute(adj_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PC_ERR_CUDA;
+  if (fseed && fseed->P > 0) {
+    // the field loss seeds the history adjoints and the origin gradients before the sweep; its
+    // window spans the points' delays from each source, at most 8 500 samples
+    const int fw = 8500;
+    const size_t fsm = (size_t)fw * 3 * sizeof(double);
+    if (cudaFuncSetAttribute(fields_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess)
+      return PC_ERR_CUDA;
+    fields_adj_kernel<<<dim3((unsigned)dp->N, (unsigned)fseed->T, (unsigned)dp->B), 128, fsm, st>>>(A, *fseed, fw);
+  }
   const dim3 fgrid((unsigned)dp->N, (unsigned)dp->B);
   const int64_t nblocks = (n_steps + K - 1) / K;
   for (int64_t bk = nblocks - 1; bk >= 0; --bk) {
@@ -1778,6 +1941,38 @@ extern "C" pc_status pc_dipoles_rates_adjoint(pc_ctx *ctx, const pc_dipoles *dp,
   if (bs != PC_OK) return bs;
   pc_status rs = pc::adjoint_core(ctx, dp, dt, n_steps, opts, nullptr, true, dL_dgamma, dL_domega, gamma, omega, g,
                                   st);
+  if (rs != PC_OK) return rs;
+  return pc::end_call(ctx, st);
+}
+
+extern "C" pc_status pc_dipoles_fields_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,
+                                               const pc_run_opts *opts, const double *points, int64_t P,
+                                               const double *times, int32_t T, const pc_field_out *cot,
+                                               const pc_dipole_grads *g, void *stream) {
+  if (!ctx || !cot || !times || T < 1 || P < 0 || (P > 0 && !points)) return PC_ERR_ARG;
+  if (cot->mask) return PC_ERR_ARG;  // the mask has no cotangent
+  for (int i = 0; i < T; ++i)
+    if (!isfinite(times[i]) || times[i] < 0.0) return PC_ERR_ARG;
+  pc::DeviceGuard gd(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  // the frame times on the device (context scratch of the field outputs)
+  if (ctx->out_chunks.reserve((size_t)T * sizeof(double)) != cudaSuccess) return PC_ERR_CUDA;
+  double *tdev = (double *)ctx->out_chunks.ptr;
+  if (cudaMemcpyAsync(tdev, times, (size_t)T * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return PC_ERR_CUDA;
+  pc::FieldSeed fs;
+  fs.pts = points;
+  fs.P = P;
+  fs.T = T;
+  fs.times = tdev;
+  fs.cE = (const double *)cot->E;
+  fs.cB = (const double *)cot->B;
+  fs.cphi = (const double *)cot->phi;
+  fs.cA = (const double *)cot->A;
+  pc_status rs = pc::adjoint_core(ctx, dp, dt, n_steps, opts, nullptr, false, nullptr, nullptr, nullptr, nullptr, g,
+                                  st, &fs);
   if (rs != PC_OK) return rs;
   return pc::end_call(ctx, st);
 }

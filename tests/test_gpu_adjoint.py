@@ -262,3 +262,51 @@ def test_adjoint_grid_path_configuration(ctx):
         fd = (_loss_gpu(ctx, _perturbed(cfg, name, idx, h), w) - _loss_gpu(ctx, _perturbed(cfg, name, idx, -h), w)) / (2 * h)
         scale = np.abs(g[name]).max()
         assert abs(g[name][idx] - fd) <= 1e-4 * scale, (name, idx, g[name][idx], fd)
+
+
+# ---- gradients of a loss on the oscillators' own fields ----
+
+def _field_cfg():
+    cfg = W.adjoint_cluster(B=1, N=3, n_steps=1500, seed=W.SEED_ADJ + 21)
+    times = [1300 * cfg.dt, 1500 * cfg.dt]
+    pts = W.kink_free_points(cfg, times)
+    return cfg, times, pts
+
+
+def _field_loss(ctx, cfg, times, pts, cot):
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=pc.PC_F64)
+    src = W.Dipoles(origin=cfg.origin[0], axis=cfg.axis[0], q=cfg.q[0], m1=cfg.m1[0], m2=cfg.m2[0],
+                    d=out["d"][0].cpu().numpy(), d_dot=out["d_dot"][0].cpu().numpy(),
+                    d_ddot=out["d_ddot"][0].cpu().numpy(), t0=0.0, dt=cfg.dt)
+    f = pc.pc_fields(ctx, dipoles=pc.dipoles_to_device(src), points=torch.tensor(pts, device="cuda"), times=times,
+                     precision=pc.PC_F64)
+    return sum(float((f[k].cpu().numpy() * cot[k][0]).sum()) for k in ("E", "B", "phi", "A"))
+
+
+def test_fields_adjoint_vs_finite_differences(ctx):
+    cfg, times, pts = _field_cfg()
+    rng = np.random.default_rng(31)
+    T, P = len(times), len(pts)
+    # cotangents scaled by each field's typical size, so that E, B, phi and A contribute alike
+    ones = {k: np.ones((1, T, P, 3) if k != "phi" else (1, T, P)) for k in ("E", "B", "phi", "A")}
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=pc.PC_F64)
+    src = W.Dipoles(origin=cfg.origin[0], axis=cfg.axis[0], q=cfg.q[0], m1=cfg.m1[0], m2=cfg.m2[0],
+                    d=out["d"][0].cpu().numpy(), d_dot=out["d_dot"][0].cpu().numpy(),
+                    d_ddot=out["d_ddot"][0].cpu().numpy(), t0=0.0, dt=cfg.dt)
+    f0 = pc.pc_fields(ctx, dipoles=pc.dipoles_to_device(src), points=torch.tensor(pts, device="cuda"), times=times,
+                      precision=pc.PC_F64)
+    cot = {k: rng.standard_normal(ones[k].shape) / float(np.sqrt(np.mean(f0[k].cpu().numpy() ** 2)))
+           for k in ones}
+    dp = pc.lo_config_to_device(cfg)
+    go, gw, gd = pc.pc_dipoles_fields_adjoint(ctx, dp, cfg.dt, cfg.n_steps, pts, times, cE=cot["E"], cB=cot["B"],
+                                              cphi=cot["phi"], cA=cot["A"])
+    g = {"origin": go.cpu().numpy(), "omega0": gw.cpu().numpy(), "d0": gd.cpu().numpy()}
+    hs = {"origin": 3e-13, "omega0": 1e-7 * float(cfg.omega0.mean()), "d0": 1e-6 * float(cfg.d0.mean())}
+    for name in ("origin", "omega0", "d0"):
+        arr = getattr(cfg, name)
+        fd = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            h = hs[name]
+            fd[idx] = (_field_loss(ctx, _perturbed(cfg, name, idx, h), times, pts, cot) -
+                       _field_loss(ctx, _perturbed(cfg, name, idx, -h), times, pts, cot)) / (2 * h)
+        _check(g[name], fd, 1e-4)

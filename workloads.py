@@ -386,3 +386,27 @@ def param_charges(seed: int = 41):
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     pts = d * rng.uniform(5e-9, 60e-9, size=(256, 1))
     return np.array(kind, dtype=np.int32), np.array(q), np.array(par), pts
+
+
+def kink_free_points(cfg: LOConfig, times, n: int = 8, r_min: float = 15e-9, r_max: float = 60e-9,
+                     margin: float = 0.08, seed: int = 77):
+    """n observation points around configuration 0 of cfg whose retarded times from every dipole
+    centre, at every one of `times`, sit at least `margin` samples from a history sample (so
+    finite-difference steps of the inputs do not cross the kinks of the piecewise-linear history)."""
+    rng = np.random.default_rng(seed)
+    L = C * cfg.dt
+    centre = cfg.origin[0].mean(axis=0)
+    out = []
+    while len(out) < n:
+        d = rng.standard_normal(3)
+        p = centre + d / np.linalg.norm(d) * rng.uniform(r_min, r_max)
+        ok = True
+        for t in times:
+            x = t / cfg.dt - np.linalg.norm(cfg.origin[0] - p, axis=1) / L
+            f = x - np.floor(x)
+            if np.any((f < margin) | (f > 1 - margin)):
+                ok = False
+                break
+        if ok:
+            out.append(p)
+    return np.array(out)
