@@ -156,6 +156,19 @@ pc_status pc_fields_param(pc_ctx *ctx, const pc_param_charges *ch, const double 
                           void *stream);
 
 /*
+ * pc_autotune_plane -- picks the tile shape of the PC_MIXED plane evaluation for this workload and
+ * keeps it in the context for later pc_fields_plane / pc_fields_plane_to_host calls: tiles of 256
+ * points as 8 x 32, 16 x 16 (the default) or 32 x 8 rows x columns, each run once to warm up and
+ * once timed on the given arguments (which are those of pc_fields_plane with PC_MIXED; `out`
+ * receives the fields of the last run).  Writes the chosen rows per tile to *tile_rows (or NULL).
+ * The results of every shape agree to float32 rounding (the tile anchor enters the delays).
+ * Errors: those of pc_fields_plane.
+ */
+pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const pc_plane *grid,
+                            const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,
+                            int32_t *tile_rows, void *stream);
+
+/*
  * pc_fields_to_host / pc_fields_plane_to_host -- pc_fields / pc_fields_plane with the outputs
  * delivered to HOST memory: out_host holds host pointers ([T][P][...] as in pc_field_out).  The
  * frames are computed in chunks of about 256 MB of outputs into two alternating device buffers

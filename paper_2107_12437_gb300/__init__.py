@@ -20,6 +20,7 @@ from .capi import (  # noqa: F401
     lo_config_to_device,
     load,
     pc_alu_peaks,
+    pc_autotune_plane,
     pc_dipoles_adjoint,
     pc_dipoles_fields_adjoint,
     pc_dipoles_rates_adjoint,

@@ -84,6 +84,7 @@ struct Launch {
   const float4 *Hd;     // [N][Sd] (d/(qL), d'/(qc), d'' dt/(qc), 0)
   const float4 *Hc;     // [M][S][3]: offset/L, v/c, a dt/c
   const double *cref;   // [M][3] reference position (sample 0)
+  int32_t tile_shift;   // plane tiles of (256 >> tile_shift) rows x (1 << tile_shift) columns
 };
 
 // ================================================================================================
@@ -427,7 +428,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     p = (int64_t)blockIdx.x * kMixThreads + tid;
   } else {
     int64_t tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
-    int64_t iu = tu * 16 + (tid >> 4), iv = tv * 16 + (tid & 15);
+    const int sh = L.tile_shift, cols = 1 << sh, rows = kMixThreads >> sh;
+    int64_t iu = tu * rows + (tid >> sh), iv = tv * cols + (tid & (cols - 1));
     p = (iu < L.pts.nu && iv < L.pts.nv) ? iu * L.pts.nv + iv : L.pts.P;
   }
   const bool active = p < L.pts.P;
@@ -439,7 +441,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       point_at(L.pts, pa, a);
     } else {
       int64_t tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
-      double iu = (double)(tu * 16) + 7.5, iv = (double)(tv * 16) + 7.5;
+      const int sh = L.tile_shift, cols = 1 << sh, rows = kMixThreads >> sh;
+      double iu = (double)(tu * rows) + 0.5 * (rows - 1), iv = (double)(tv * cols) + 0.5 * (cols - 1);
       for (int i = 0; i < 3; ++i) a[i] = L.pts.o[i] + iu * L.pts.eu[i] + iv * L.pts.ev[i];
     }
     s_anchor[0] = a[0];
@@ -873,6 +876,7 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
   L.out.mask = out->mask;
   L.r_excl = r_excl;
   L.status = ctx->d_status;
+  L.tile_shift = ctx->tile_shift;
 
   if (precision == PC_MIXED) {
     // the float32 path indexes samples with 32-bit integers
@@ -949,8 +953,9 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
       if (list) {
         tiles = (P + kMixThreads - 1) / kMixThreads;
       } else {
-        int64_t tu = (L.pts.nu + 15) / 16;
-        tiles_v = (L.pts.nv + 15) / 16;
+        const int64_t cols = (int64_t)1 << L.tile_shift, rows = kMixThreads / cols;
+        int64_t tu = (L.pts.nu + rows - 1) / rows;
+        tiles_v = (L.pts.nv + cols - 1) / cols;
         tiles = tu * tiles_v;
       }
       dim3 grid((unsigned)tiles, (unsigned)L.T);
@@ -1148,4 +1153,45 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PC_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PC_ERR_CUDA;
   return (pc_status)h;
+}
+
+// ================================================================================================
+// Tile-shape autotuning of the mixed plane evaluation: 256-point tiles of 8 x 32, 16 x 16 or 32 x 8
+// (rows x columns) trade the spread of the points' delays within a tile (the history gathers'
+// locality) against the width of the output rows each warp stores.  Each candidate runs the
+// caller's workload once to warm up and once timed; the fastest is kept in the context for the
+// plane calls that follow.
+// ================================================================================================
+extern "C" pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,
+                                       const pc_plane *grid, const double *times, int32_t T, int32_t kind,
+                                       double r_excl, const pc_field_out *out, int32_t *tile_rows, void *stream) {
+  if (!ctx || !grid || !out) return PC_ERR_ARG;
+  pc::DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int shifts[3] = {5, 4, 3};  // 32, 16, 8 columns
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PC_ERR_CUDA;
+  float best = 1e30f;
+  int best_shift = ctx->tile_shift;
+  pc_status rs = PC_OK;
+  for (int c = 0; c < 3 && rs == PC_OK; ++c) {
+    ctx->tile_shift = shifts[c];
+    rs = pc_fields_plane(ctx, ch, dp, grid, times, T, kind, PC_MIXED, r_excl, out, stream);
+    if (rs != PC_OK) break;
+    cudaEventRecord(e0, st);
+    rs = pc_fields_plane(ctx, ch, dp, grid, times, T, kind, PC_MIXED, r_excl, out, stream);
+    cudaEventRecord(e1, st);
+    if (rs != PC_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_shift = shifts[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tile_shift = best_shift;
+  if (tile_rows) *tile_rows = pc::kMixThreads >> best_shift;
+  return rs;
 }

@@ -276,3 +276,19 @@ def test_plane_to_host_many_frames_and_empty(ctx):
     assert torch.equal(host["E"], dev["E"].cpu()) and torch.equal(host["mask"], dev["mask"].cpu())
     empty = pc.pc_fields_plane_to_host(ctx, **dict(kw, nu=0))
     assert empty["E"].shape == (40, 0, 3)
+
+
+def test_autotuned_tile_shape_keeps_parity(ctx):
+    # the tuner times the three tile shapes on a config-2 strip and keeps the fastest; every shape
+    # gives the same fields to float32 rounding
+    dp, g, z, times = W.cfg2()
+    dpd = pc.dipoles_to_device(dp)
+    step = float(g[1] - g[0])
+    kw = dict(dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=96, nv=512,
+              times=[float(times[3])])
+    ref = pc.pc_fields_plane(ctx, precision=pc.PC_MIXED, **kw)["E"].double()
+    rows = pc.pc_autotune_plane(ctx, **kw)
+    assert rows in (8, 16, 32)
+    tuned = pc.pc_fields_plane(ctx, precision=pc.PC_MIXED, **kw)["E"].double()
+    scale = torch.linalg.norm(ref, dim=-1).max()
+    assert float(torch.linalg.norm(tuned - ref, dim=-1).max() / scale) < 1e-5
