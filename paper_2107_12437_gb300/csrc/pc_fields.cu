@@ -85,7 +85,22 @@ struct Launch {
   const float4 *Hc;     // [M][S][3]: offset/L, v/c, a dt/c
   const double *cref;   // [M][3] reference position (sample 0)
   int32_t tile_shift;   // plane tiles of (256 >> tile_shift) rows x (1 << tile_shift) columns
+  // mixed path, set on the host: each frame's time in dipole samples, 1/(c dt) of the dipole
+  // history, and per dipole two float4 records (axis x, y, z, q/e), (m2/(m1+m2), m1/(m1+m2), 0, 0)
+  double uf[kMaxT];
+  double iLd;
+  const float4 *srcf;
 };
+
+// the frames of one launch: their times and, for the dipoles, the times in samples
+__host__ inline void set_frames(Launch &L, const double *times, int32_t f0, int32_t n) {
+  L.T = n;
+  L.frame0 = f0;
+  for (int i = 0; i < n; ++i) {
+    L.times[i] = times[f0 + i];
+    L.uf[i] = L.src.N > 0 ? (times[f0 + i] - L.src.t0d) / L.src.dtd : 0.0;
+  }
+}
 
 // ================================================================================================
 // float64 path
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(128) fields_f64_kernel(const Launch L) {
 // ================================================================================================
 // mixed path
 // ================================================================================================
-__global__ void prep_dipoles_f32(const Sources s, float4 *H) {
+__global__ void prep_dipoles_f32(const Sources s, float4 *H, float4 *srcf) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t n = (int64_t)s.N * s.Sd;
   if (i >= n) return;
@@ -227,6 +242,11 @@ __global__ void prep_dipoles_f32(const Sources s, float4 *H) {
   const double Lc = kC * s.dtd;
   H[i] = make_float4((float)(s.d[i] / (q * Lc)), (float)(s.dd[i] / (q * kC)), (float)(s.ddd[i] * s.dtd / (q * kC)),
                      0.f);
+  if (i % s.Sd == 0) {
+    const double m1 = s.m1[j], m2 = s.m2[j];
+    srcf[2 * j] = make_float4((float)s.axis[3 * j], (float)s.axis[3 * j + 1], (float)s.axis[3 * j + 2], (float)(q / kE));
+    srcf[2 * j + 1] = make_float4((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)), 0.f, 0.f);
+  }
 }
 
 __global__ void prep_charges_f32(const Sources s, float4 *H, double *cref) {
@@ -468,12 +488,13 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     // none of them occupies registers across the source loop
     double r[3];
     point_at(L.pts, pp, r);
-    const double drxd = (r[0] - s_anchor[0]) / Ld, dryd = (r[1] - s_anchor[1]) / Ld, drzd = (r[2] - s_anchor[2]) / Ld;
+    const double iLd = L.iLd;  // float64 divisions would stall the CTA on this GPU's narrow float64 unit
+    const double drxd = (r[0] - s_anchor[0]) * iLd, dryd = (r[1] - s_anchor[1]) * iLd, drzd = (r[2] - s_anchor[2]) * iLd;
     const float drx = (float)drxd, dry = (float)dryd, drz = (float)drzd;
     const float drlx = (float)(drxd - (double)drx), drly = (float)(dryd - (double)dry),
                 drlz = (float)(drzd - (double)drz);
     const float dr2 = drx * drx + dry * dry + drz * drz;
-    const float rex = (float)(L.r_excl / Ld);
+    const float rex = (float)(L.r_excl * iLd);
     const float rex_fast = rex + 1.5f;
     const int Sd32 = (int)s.Sd;
     const unsigned jlim = Sd32 > 3 ? (unsigned)(Sd32 - 3) : 0u;  // fast segments 1 <= j <= S-3
@@ -481,22 +502,21 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       const int nch = min(kChunk, s.N - base);
       __syncthreads();
       if (tid < nch) {
+        // the tile anchor's distance to the source in float64 (the integer sample index and a
+        // fraction kept to ~1e-7), everything else from the per-call records
         const int j = base + tid;
-        const double Ldc = kC * s.dtd;
-        const double u = (L.times[f] - s.t0d) / s.dtd;
         double ra[3];
-        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - s.origin[3 * j + i]) / Ldc;
+        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - s.origin[3 * j + i]) * L.iLd;
         const double rna = sqrt(ra[0] * ra[0] + ra[1] * ra[1] + ra[2] * ra[2]);
-        const double x = u - rna;
+        const double x = L.uf[f] - rna;
         const double kaf = floor(x);
         s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
-        s_geo_lo[tid] = make_float4((float)(ra[0] - (double)(float)ra[0]), (float)(ra[1] - (double)(float)ra[1]),
-                                    (float)(ra[2] - (double)(float)ra[2]), (float)(rna - (double)(float)rna));
-        s_ax[tid] = make_float4((float)s.axis[3 * j], (float)s.axis[3 * j + 1], (float)s.axis[3 * j + 2],
-                                (float)(s.qd[j] / kE));
-        const double m1 = s.m1[j], m2 = s.m2[j];
-        s_mix[tid] = make_float4((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)), (float)(x - kaf),
-                                 __int_as_float((int)kaf));
+        if (LIST)
+          s_geo_lo[tid] = make_float4((float)(ra[0] - (double)(float)ra[0]), (float)(ra[1] - (double)(float)ra[1]),
+                                      (float)(ra[2] - (double)(float)ra[2]), (float)(rna - (double)(float)rna));
+        s_ax[tid] = L.srcf[2 * j];
+        const float4 mm = L.srcf[2 * j + 1];
+        s_mix[tid] = make_float4(mm.x, mm.y, (float)(x - kaf), __int_as_float((int)kaf));
         s_hist[tid] = L.Hd + (size_t)j * s.Sd;
       }
       __syncthreads();
@@ -882,16 +902,19 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
     // the float32 path indexes samples with 32-bit integers
     if ((has_dp && s.Sd > (int64_t)1 << 30) || (has_ch && s.S > (int64_t)1 << 30)) return PC_ERR_ARG;
     size_t nd = has_dp ? (size_t)s.N * s.Sd : 0, nc = has_ch ? (size_t)s.M * s.S * 3 : 0;
-    if (ctx->hist_f32.reserve((nd + nc) * sizeof(float4)) != cudaSuccess) return PC_ERR_CUDA;
+    const size_t ns = has_dp ? 2 * (size_t)s.N : 0;
+    if (ctx->hist_f32.reserve((nd + nc + ns) * sizeof(float4)) != cudaSuccess) return PC_ERR_CUDA;
     if (has_ch && ctx->charge_ref.reserve((size_t)s.M * 3 * sizeof(double)) != cudaSuccess) return PC_ERR_CUDA;
     float4 *Hd = (float4 *)ctx->hist_f32.ptr;
     float4 *Hc = Hd + nd;
     L.Hd = Hd;
     L.Hc = Hc;
     L.cref = (const double *)ctx->charge_ref.ptr;
+    L.srcf = Hc + nc;
+    L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;
     if (has_dp) {
       int64_t n = (int64_t)nd;
-      prep_dipoles_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hd);
+      prep_dipoles_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hd, Hc + nc);
     }
     if (has_ch) {
       int64_t n = (int64_t)s.M * s.S;
@@ -923,9 +946,7 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
   const int32_t step = hp.on ? hp.frames : kMaxT;
   int chunk = 0;
   for (int32_t f0 = 0; f0 < T; f0 += step, ++chunk) {
-    L.T = min(step, T - f0);
-    L.frame0 = f0;
-    for (int i = 0; i < L.T; ++i) L.times[i] = times[f0 + i];
+    set_frames(L, times, f0, min(step, T - f0));
     const int sl = chunk & 1;
     if (hp.on) {
       // this chunk's device slot: wait until the copy of the chunk before last has left it
@@ -1071,7 +1092,8 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   // the scratch must hold the float32 mirrors and the reference positions
   const size_t nd = has_dp ? (size_t)dp->N * (size_t)dp->S : 0;
   const size_t nc = has_ch ? (size_t)ch->M * (size_t)ch->S * 3 : 0;
-  const size_t need = (nd + nc) * sizeof(float4) + (has_ch ? (size_t)ch->M * 3 * sizeof(double) : 0);
+  const size_t ns = has_dp ? 2 * (size_t)dp->N : 0;
+  const size_t need = (nd + nc + ns) * sizeof(float4) + (has_ch ? (size_t)ch->M * 3 * sizeof(double) : 0);
   if (need > kStaticScratchBytes) return PC_ERR_ARG;
   if ((has_dp && dp->S > (int64_t)1 << 30) || (has_ch && ch->S > (int64_t)1 << 30)) return PC_ERR_ARG;
 
@@ -1085,7 +1107,8 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   int *status = (int *)base;
   float4 *Hd = (float4 *)(base + kStaticHeader);
   float4 *Hc = Hd + nd;
-  double *cref = (double *)(Hc + nc);
+  float4 *srcf = Hc + nc;
+  double *cref = (double *)(srcf + ns);
 
   cudaStream_t st = (cudaStream_t)stream;
   cudaGetLastError();
@@ -1132,17 +1155,17 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   L.Hd = Hd;
   L.Hc = Hc;
   L.cref = cref;
+  L.srcf = srcf;
+  L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;
   // the mirrors are rewritten in full by every call
-  if (has_dp) prep_dipoles_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(s, Hd);
+  if (has_dp) prep_dipoles_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(s, Hd, srcf);
   if (has_ch) {
     const int64_t n = (int64_t)s.M * s.S;
     prep_charges_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hc, cref);
   }
   const int64_t tiles = (P + kMixThreads - 1) / kMixThreads;
   for (int32_t f0 = 0; f0 < T; f0 += kMaxT) {
-    L.T = min(kMaxT, T - f0);
-    L.frame0 = f0;
-    for (int i = 0; i < L.T; ++i) L.times[i] = times[f0 + i];
+    set_frames(L, times, f0, min(kMaxT, T - f0));
     dim3 grid((unsigned)tiles, (unsigned)L.T);
     if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, true><<<grid, kMixThreads, 0, st>>>(L, 1);
     else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, true><<<grid, kMixThreads, 0, st>>>(L, 1);
