@@ -277,7 +277,7 @@ pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t S, double 
  * Scratch: the float32 history mirrors, the point-charge reference positions and the status word
  * live in one static device array of 16 MiB (plus a 256-byte header) that the library reserves on
  * every GPU that loads it and keeps until the process exits.  The sources must fit it:
- *   16 * N * S_dipoles + 32 * N + 48 * M * S_charges + 24 * M  <=  16 MiB  (bytes),
+ *   16 * N * S_dipoles + 64 * N + 48 * M * S_charges + 24 * M  <=  16 MiB  (bytes),
  * otherwise the call returns PC_ERR_ARG without touching the device.
  * Set-up: the first call on a device resolves the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  The device used is

@@ -88,7 +88,9 @@ struct Launch {
   // mixed path, set on the host: each frame's time in dipole samples, 1/(c dt) of the dipole
   // history, and per dipole two float4 records (axis x, y, z, q/e), (m2/(m1+m2), m1/(m1+m2), 0, 0)
   double uf[kMaxT];
+  float uf_hi[kMaxT], uf_lo[kMaxT];  // the same as float-float
   double iLd;
+  float eu_L[3], ev_L[3];            // plane steps in units of c dt (dipole history)
   const float4 *srcf;
 };
 
@@ -99,6 +101,8 @@ __host__ inline void set_frames(Launch &L, const double *times, int32_t f0, int3
   for (int i = 0; i < n; ++i) {
     L.times[i] = times[f0 + i];
     L.uf[i] = L.src.N > 0 ? (times[f0 + i] - L.src.t0d) / L.src.dtd : 0.0;
+    L.uf_hi[i] = (float)L.uf[i];
+    L.uf_lo[i] = (float)(L.uf[i] - (double)L.uf_hi[i]);
   }
 }
 
@@ -244,8 +248,16 @@ __global__ void prep_dipoles_f32(const Sources s, float4 *H, float4 *srcf) {
                      0.f);
   if (i % s.Sd == 0) {
     const double m1 = s.m1[j], m2 = s.m2[j];
-    srcf[2 * j] = make_float4((float)s.axis[3 * j], (float)s.axis[3 * j + 1], (float)s.axis[3 * j + 2], (float)(q / kE));
-    srcf[2 * j + 1] = make_float4((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)), 0.f, 0.f);
+    srcf[4 * j] = make_float4((float)s.axis[3 * j], (float)s.axis[3 * j + 1], (float)s.axis[3 * j + 2], (float)(q / kE));
+    srcf[4 * j + 1] = make_float4((float)(m2 / (m1 + m2)), (float)(m1 / (m1 + m2)), 0.f, 0.f);
+    float hi[3], lo[3];
+    for (int c = 0; c < 3; ++c) {
+      const double x = s.origin[3 * j + c] / Lc;
+      hi[c] = (float)x;
+      lo[c] = (float)(x - (double)hi[c]);
+    }
+    srcf[4 * j + 2] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    srcf[4 * j + 3] = make_float4(lo[0], lo[1], lo[2], 0.f);
   }
 }
 
@@ -431,6 +443,7 @@ __device__ __forceinline__ float kahan_get(const KahanArr &k, int tid, int i) {
 template <int KIND, bool LIST>
 __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
   __shared__ double s_anchor[3];
+  __shared__ float s_anc_hi[3], s_anc_lo[3];  // the anchor / (c dt) of the dipoles as float-float
   __shared__ KahanArr s_kahan;
   __shared__ float4 s_geo[kChunk];   // rho_a (x,y,z), |rho_a|
   __shared__ float4 s_geo_lo[kChunk]; // low parts of rho_a and |rho_a| (list mode)
@@ -468,6 +481,11 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     s_anchor[0] = a[0];
     s_anchor[1] = a[1];
     s_anchor[2] = a[2];
+    for (int i = 0; i < 3; ++i) {
+      const double x = a[i] * L.iLd;
+      s_anc_hi[i] = (float)x;
+      s_anc_lo[i] = (float)(x - (double)s_anc_hi[i]);
+    }
   }
   __syncthreads();
   const int64_t pp = active ? p : 0;
@@ -486,13 +504,28 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   if (s.N > 0) {
     // float64 values used once per chunk or by the rare slow pairs are recomputed there, so that
     // none of them occupies registers across the source loop
-    double r[3];
-    point_at(L.pts, pp, r);
     const double iLd = L.iLd;  // float64 divisions would stall the CTA on this GPU's narrow float64 unit
-    const double drxd = (r[0] - s_anchor[0]) * iLd, dryd = (r[1] - s_anchor[1]) * iLd, drzd = (r[2] - s_anchor[2]) * iLd;
-    const float drx = (float)drxd, dry = (float)dryd, drz = (float)drzd;
-    const float drlx = (float)(drxd - (double)drx), drly = (float)(dryd - (double)dry),
-                drlz = (float)(drzd - (double)drz);
+    float drx, dry, drz, drlx = 0.f, drly = 0.f, drlz = 0.f;
+    if (!LIST) {
+      // a plane point sits a whole number of grid steps from the tile anchor: the offset in float
+      // from those small integers (no float64 on the way)
+      const int sh = L.tile_shift, cols = 1 << sh, rows = kMixThreads >> sh;
+      const float du = (float)(tid >> sh) - 0.5f * (float)(rows - 1), dv = (float)(tid & (cols - 1)) - 0.5f * (float)(cols - 1);
+      drx = du * L.eu_L[0] + dv * L.ev_L[0];
+      dry = du * L.eu_L[1] + dv * L.ev_L[1];
+      drz = du * L.eu_L[2] + dv * L.ev_L[2];
+    } else {
+      double r[3];
+      point_at(L.pts, pp, r);
+      const double drxd = (r[0] - s_anchor[0]) * iLd, dryd = (r[1] - s_anchor[1]) * iLd,
+                   drzd = (r[2] - s_anchor[2]) * iLd;
+      drx = (float)drxd;
+      dry = (float)dryd;
+      drz = (float)drzd;
+      drlx = (float)(drxd - (double)drx);
+      drly = (float)(dryd - (double)dry);
+      drlz = (float)(drzd - (double)drz);
+    }
     const float dr2 = drx * drx + dry * dry + drz * drz;
     const float rex = (float)(L.r_excl * iLd);
     const float rex_fast = rex + 1.5f;
@@ -504,19 +537,22 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       if (tid < nch) {
         // the tile anchor's distance to the source in float64 (the integer sample index and a
         // fraction kept to ~1e-7), everything else from the per-call records
+        // in float-float (~1e-14 relative) on the float32 pipes: rho_a = anchor - origin in units of
+        // c dt, |rho_a|, and the centre's retarded sample u - |rho_a| split into integer and fraction
         const int j = base + tid;
-        double ra[3];
-        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - s.origin[3 * j + i]) * L.iLd;
-        const double rna = sqrt(ra[0] * ra[0] + ra[1] * ra[1] + ra[2] * ra[2]);
-        const double x = L.uf[f] - rna;
-        const double kaf = floor(x);
-        s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
-        if (LIST)
-          s_geo_lo[tid] = make_float4((float)(ra[0] - (double)(float)ra[0]), (float)(ra[1] - (double)(float)ra[1]),
-                                      (float)(ra[2] - (double)(float)ra[2]), (float)(rna - (double)(float)rna));
-        s_ax[tid] = L.srcf[2 * j];
-        const float4 mm = L.srcf[2 * j + 1];
-        s_mix[tid] = make_float4(mm.x, mm.y, (float)(x - kaf), __int_as_float((int)kaf));
+        const float4 oh = L.srcf[4 * j + 2], ol = L.srcf[4 * j + 3];
+        const ff rax = ff_add({s_anc_hi[0], s_anc_lo[0]}, {-oh.x, -ol.x});
+        const ff ray = ff_add({s_anc_hi[1], s_anc_lo[1]}, {-oh.y, -ol.y});
+        const ff raz = ff_add({s_anc_hi[2], s_anc_lo[2]}, {-oh.z, -ol.z});
+        const ff rna = ff_sqrt(ff_add(ff_add(ff_mul(rax, rax), ff_mul(ray, ray)), ff_mul(raz, raz)));
+        const ff x = ff_add({L.uf_hi[f], L.uf_lo[f]}, {-rna.hi, -rna.lo});
+        float kaf;
+        const int kai = Num<float>::floor_int(x.hi, kaf);
+        s_geo[tid] = make_float4(rax.hi, ray.hi, raz.hi, rna.hi);
+        if (LIST) s_geo_lo[tid] = make_float4(rax.lo, ray.lo, raz.lo, rna.lo);
+        s_ax[tid] = L.srcf[4 * j];
+        const float4 mm = L.srcf[4 * j + 1];
+        s_mix[tid] = make_float4(mm.x, mm.y, (x.hi - kaf) + x.lo, __int_as_float(kai));
         s_hist[tid] = L.Hd + (size_t)j * s.Sd;
       }
       __syncthreads();
@@ -902,7 +938,7 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
     // the float32 path indexes samples with 32-bit integers
     if ((has_dp && s.Sd > (int64_t)1 << 30) || (has_ch && s.S > (int64_t)1 << 30)) return PC_ERR_ARG;
     size_t nd = has_dp ? (size_t)s.N * s.Sd : 0, nc = has_ch ? (size_t)s.M * s.S * 3 : 0;
-    const size_t ns = has_dp ? 2 * (size_t)s.N : 0;
+    const size_t ns = has_dp ? 4 * (size_t)s.N : 0;
     if (ctx->hist_f32.reserve((nd + nc + ns) * sizeof(float4)) != cudaSuccess) return PC_ERR_CUDA;
     if (has_ch && ctx->charge_ref.reserve((size_t)s.M * 3 * sizeof(double)) != cudaSuccess) return PC_ERR_CUDA;
     float4 *Hd = (float4 *)ctx->hist_f32.ptr;
@@ -912,6 +948,10 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
     L.cref = (const double *)ctx->charge_ref.ptr;
     L.srcf = Hc + nc;
     L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;
+    for (int i = 0; i < 3; ++i) {
+      L.eu_L[i] = (float)(L.pts.eu[i] * L.iLd);
+      L.ev_L[i] = (float)(L.pts.ev[i] * L.iLd);
+    }
     if (has_dp) {
       int64_t n = (int64_t)nd;
       prep_dipoles_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, Hd, Hc + nc);
@@ -1092,7 +1132,7 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   // the scratch must hold the float32 mirrors and the reference positions
   const size_t nd = has_dp ? (size_t)dp->N * (size_t)dp->S : 0;
   const size_t nc = has_ch ? (size_t)ch->M * (size_t)ch->S * 3 : 0;
-  const size_t ns = has_dp ? 2 * (size_t)dp->N : 0;
+  const size_t ns = has_dp ? 4 * (size_t)dp->N : 0;
   const size_t need = (nd + nc + ns) * sizeof(float4) + (has_ch ? (size_t)ch->M * 3 * sizeof(double) : 0);
   if (need > kStaticScratchBytes) return PC_ERR_ARG;
   if ((has_dp && dp->S > (int64_t)1 << 30) || (has_ch && ch->S > (int64_t)1 << 30)) return PC_ERR_ARG;
