@@ -92,7 +92,19 @@ struct Launch {
   double iLd;
   float eu_L[3], ev_L[3];            // plane steps in units of c dt (dipole history)
   const float4 *srcf;
+  float unit[4];                     // SI units of the float32 sums of E, B, phi, A
 };
+
+// the float32 outputs' units: E in k_e e / L^2, B in k_e e / (L^2 c), phi in k_e e / L,
+// A in k_e e / (L c), L = c dt of the dipoles (of the point charges when there are no dipoles)
+__host__ inline void set_units(Launch &L) {
+  const double Lref = (L.src.N > 0) ? kC * L.src.dtd : kC * L.src.dt;
+  const double kE2 = kKe * kE / (Lref * Lref), kP = kKe * kE / Lref;
+  L.unit[0] = (float)kE2;
+  L.unit[1] = (float)(kE2 / kC);
+  L.unit[2] = (float)kP;
+  L.unit[3] = (float)(kP / kC);
+}
 
 // the frames of one launch: their times and, for the dipoles, the times in samples
 __host__ inline void set_frames(Launch &L, const double *times, int32_t f0, int32_t n) {
@@ -820,8 +832,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     return;
   }
   // units: E in k_e e / L^2, B in k_e e / (L^2 c), phi in k_e e / L, A in k_e e / (L c)
-  const double kE2 = kKe * kE / (Lref * Lref), kP = kKe * kE / Lref;
-  const float fE = (float)kE2, fB = (float)(kE2 / kC), fP = (float)kP, fA = (float)(kP / kC);
+  const float fE = L.unit[0], fB = L.unit[1], fP = L.unit[2], fA = L.unit[3];
   const int64_t o = (L.frame0 + f) * L.pts.P + p;
   if (L.out.E) {
     float *e = (float *)L.out.E + 3 * o;
@@ -948,6 +959,7 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
     L.cref = (const double *)ctx->charge_ref.ptr;
     L.srcf = Hc + nc;
     L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;
+    set_units(L);
     for (int i = 0; i < 3; ++i) {
       L.eu_L[i] = (float)(L.pts.eu[i] * L.iLd);
       L.ev_L[i] = (float)(L.pts.ev[i] * L.iLd);
@@ -1197,6 +1209,7 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   L.cref = cref;
   L.srcf = srcf;
   L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;
+  set_units(L);
   // the mirrors are rewritten in full by every call
   if (has_dp) prep_dipoles_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(s, Hd, srcf);
   if (has_ch) {
