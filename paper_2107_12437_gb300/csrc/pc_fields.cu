@@ -93,6 +93,11 @@ struct Launch {
   float eu_L[3], ev_L[3];            // plane steps in units of c dt (dipole history)
   const float4 *srcf;
   float unit[4];                     // SI units of the float32 sums of E, B, phi, A
+  // point charges: each frame's time in their samples, 1/(c dt) of their history, and the scales
+  // of their float32 terms to the output unit (E, phi)
+  double ufc[kMaxT];
+  double iLc;
+  float sE, sP;
 };
 
 // the float32 outputs' units: E in k_e e / L^2, B in k_e e / (L^2 c), phi in k_e e / L,
@@ -104,6 +109,12 @@ __host__ inline void set_units(Launch &L) {
   L.unit[1] = (float)(kE2 / kC);
   L.unit[2] = (float)kP;
   L.unit[3] = (float)(kP / kC);
+  if (L.src.M > 0) {
+    const double Lch = kC * L.src.dt;
+    L.iLc = 1.0 / Lch;
+    L.sE = (float)((Lref / Lch) * (Lref / Lch));
+    L.sP = (float)(Lref / Lch);
+  }
 }
 
 // the frames of one launch: their times and, for the dipoles, the times in samples
@@ -113,6 +124,7 @@ __host__ inline void set_frames(Launch &L, const double *times, int32_t f0, int3
   for (int i = 0; i < n; ++i) {
     L.times[i] = times[f0 + i];
     L.uf[i] = L.src.N > 0 ? (times[f0 + i] - L.src.t0d) / L.src.dtd : 0.0;
+    L.ufc[i] = L.src.M > 0 ? (times[f0 + i] - L.src.t0) / L.src.dt : 0.0;
     L.uf_hi[i] = (float)L.uf[i];
     L.uf_lo[i] = (float)(L.uf[i] - (double)L.uf_hi[i]);
   }
@@ -508,9 +520,6 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   }
   uint8_t mask = 0;
   int err = 0;
-  // lengths of the two source groups (c dt) and scale of group g relative to the output unit
-  const double Ld = kC * s.dtd, Lch = kC * s.dt;
-  const double Lref = (s.N > 0) ? Ld : Lch;
 
   // ---------------- dipoles ----------------
   if (s.N > 0) {
@@ -688,25 +697,25 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   if (s.M > 0) {
     double r[3];
     point_at(L.pts, pp, r);
-    const double t = L.times[f];
-    const float drx = (float)((r[0] - s_anchor[0]) / Lch), dry = (float)((r[1] - s_anchor[1]) / Lch),
-                drz = (float)((r[2] - s_anchor[2]) / Lch);
+    const double iLc = L.iLc;  // no float64 division on the way (the float64 unit is narrow here)
+    const float drx = (float)((r[0] - s_anchor[0]) * iLc), dry = (float)((r[1] - s_anchor[1]) * iLc),
+                drz = (float)((r[2] - s_anchor[2]) * iLc);
     const float dr2 = drx * drx + dry * dry + drz * drz;
-    const double u = (t - s.t0) / s.dt;
-    const float rex = (float)(L.r_excl / Lch);
-    const float sE = (float)((Lref / Lch) * (Lref / Lch)), sP = (float)(Lref / Lch);
+    const double u = L.ufc[f];
+    const float rex = (float)(L.r_excl * iLc);
+    const float sE = L.sE, sP = L.sP;
     for (int base = 0; base < s.M; base += kChunk) {
       const int nch = min(kChunk, s.M - base);
       __syncthreads();
       if (tid < nch) {
         const int c = base + tid;
         double ra[3];
-        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - L.cref[3 * c + i]) / Lch;
+        for (int i = 0; i < 3; ++i) ra[i] = (s_anchor[i] - L.cref[3 * c + i]) * iLc;
         const double rna = sqrt(ra[0] * ra[0] + ra[1] * ra[1] + ra[2] * ra[2]);
         const double x = u - rna;
         const double kaf = floor(x);
         s_geo[tid] = make_float4((float)ra[0], (float)ra[1], (float)ra[2], (float)rna);
-        s_ax[tid] = make_float4(0.f, 0.f, 0.f, (float)(s.q[c] / kE));
+        s_ax[tid] = make_float4(0.f, 0.f, 0.f, (float)(s.q[c] * (1.0 / kE)));
         s_mix[tid] = make_float4(0.f, 0.f, (float)(x - kaf), __int_as_float((int)kaf));
       }
       __syncthreads();
