@@ -127,3 +127,20 @@ def test_cloud_grid_path(ctx, prec):
     out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=prec, want_Ed=True)
     for k in ("d", "d_dot", "Ed"):
         assert hist_err(out[k][0], ref[k]) < HIST_TOL[prec], k
+
+
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+def test_frozen_field_reading_and_unequal_masses(ctx, prec):
+    # E_d held at its value at t over each step (the alternative reading of Algorithm 1) and
+    # dipoles with unequal charge masses, against the oracle with the same reading
+    origins = np.array([[[0.0, 0.0, 0.0], [30e-9, 0.0, 0.0], [0.0, 22e-9, 9e-9]]])
+    axes = np.array([[[0.0, 1.0, 0.0], [0.6, 0.8, 0.0], [0.0, 0.0, 1.0]]])
+    cfg = W.lo_batch(origins, axes, 2 * math.pi * 200e12, 1e-11, 1e-18, 6000, 0, q=5 * W.E_CHARGE)
+    cfg.m1[0] = W.M_E * np.array([1.0, 3.0, 1836.0])
+    cfg.m2[0] = W.M_E * np.array([1.0, 0.7, 1.0])
+    ref = oracle.dipoles_run(cfg, ed_mode=1)
+    assert ref["status"] == oracle.OK
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, ed_mode=1, want_Ed=True,
+                            precision=prec)
+    for k in ("d", "d_dot", "d_ddot", "energy", "Ed"):
+        assert hist_err(out[k][0], ref[k]) < HIST_TOL[prec], k

@@ -292,3 +292,23 @@ def test_autotuned_tile_shape_keeps_parity(ctx):
     tuned = pc.pc_fields_plane(ctx, precision=pc.PC_MIXED, **kw)["E"].double()
     scale = torch.linalg.norm(ref, dim=-1).max()
     assert float(torch.linalg.norm(tuned - ref, dim=-1).max() / scale) < 1e-5
+
+
+@pytest.mark.parametrize("kind", [pc.PC_COULOMB, pc.PC_RADIATION])
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+def test_unequal_masses_and_field_kinds(ctx, prec, kind):
+    # dipoles whose two charges have different masses sit off-centre (Eqs. r_1, r_2); the Coulomb
+    # and radiation parts of Eq. E separately
+    dp, g, z, times = W.cfg2()
+    rng = np.random.default_rng(17)
+    dp.m1 = W.M_E * rng.uniform(0.5, 2000.0, size=dp.N)
+    dp.m2 = W.M_E * rng.uniform(0.5, 2.0, size=dp.N)
+    iu = np.arange(3, 2048, 71)[:24]
+    iv = np.arange(11, 2048, 67)[:21]
+    pts = W.plane_grid(g[iu], g[iv], z)
+    tsel = times[[2, 9]]
+    ref = oracle.fields(pts, tsel, dipoles=dp, kind=kind)
+    assert ref["status"] == oracle.OK
+    out = pc.pc_fields(ctx, dipoles=pc.dipoles_to_device(dp), points=torch.as_tensor(pts, device="cuda"),
+                       times=list(tsel), kind=kind, precision=prec)
+    compare(out, ref, prec)
