@@ -11,7 +11,8 @@ dipole-steps/s, the end-to-end number through the C ABI with host buffers, the r
 field kernel, clocks sampled during the timed region and the FP64 CPU oracle on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --profile fields_mixed_small|fields_f64_small|lo_small|ring_small|adj_small
+  python bench.py --profile fields_mixed_small|fields_mixed2_small|fields_f64_small|lo_small|ring_small|
+                            cloud_small|adj_small
                                                      (one small run for ncu)
 Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own copy of the workload
 (independent problems, no data-path collective), so scaling is weak.
@@ -46,11 +47,11 @@ SM_MAX_MHZ = 2070.0
 
 
 def kernel_source_hash():
-    """sha256 over the sources of the mixed field kernel (pc_fields.cu, pc_lw_f32.cuh, pc_lw_f64.cuh)."""
+    """sha256 over the sources of the mixed field kernels (pc_fields.cu and the headers it includes)."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("pc_fields.cu", "pc_lw_f32.cuh", "pc_lw_f64.cuh"):
+    for f in ("pc_fields.cu", "pc_lw_f32.cuh", "pc_lw_f32x2.cuh", "pc_lw_f64.cuh"):
         with open(os.path.join(ROOT, "paper_2107_12437_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -166,6 +167,46 @@ def oracle_lo_sample(threads=0):
                 sample="1 of 256 separations (2 oscillators) x 4000 steps")
 
 
+def compare_cloud(pc, ctx, dev, n_steps):
+    """The 4096-oscillator cloud (600 nm cube, 5 nm minimum spacing, random axes) over n_steps in
+    both precisions with the Eq. KE fit: run times, and the mixed path's total-energy trace,
+    moment histories and fitted gamma, omega against the all-float64 GPU path."""
+    import torch
+
+    cfg = W.cfg5(n_steps=n_steps)
+    lod = pc.lo_config_to_device(cfg, dev)
+    s = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res, outs = {"workload": f"cloud: 4096 oscillators in a 600 nm cube, {n_steps} RK4 steps, fit from step "
+                             f"{cfg.first_index}"}, {}
+    for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
+        pc.pc_dipoles_run(ctx, lod, cfg.dt, 64, precision=prec)
+        torch.cuda.synchronize()
+        e0.record(s)
+        o = pc.pc_dipoles_run(ctx, lod, cfg.dt, n_steps, precision=prec, fit=True, first_index=cfg.first_index)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"ms": ms, "dipole_steps_per_s": cfg.N * n_steps / (ms * 1e-3)}
+        outs[name] = {k: o[k][0] for k in ("d", "d_dot", "energy", "gamma", "omega")}
+        del o
+    m, f = outs["mixed"], outs["f64"]
+    et_m, et_f = m["energy"].sum(0), f["energy"].sum(0)
+    mass = cfg.m1[0] * cfg.m2[0] / (cfg.m1[0] + cfg.m2[0])
+    g0 = torch.as_tensor(cfg.q[0] ** 2 * cfg.omega0[0] ** 2 / (6 * math.pi * W.EPS0 * W.C ** 3 * mass), device=dev)
+    w0 = torch.as_tensor(cfg.omega0[0], device=dev)
+    res["mixed_over_f64"] = res["f64"]["ms"] / res["mixed"]["ms"]
+    res["energy_trace_max_rel_err"] = float((et_m - et_f).abs().max() / et_f.abs().max())
+    for k in ("d", "d_dot"):
+        res[k + "_max_err_rel_to_peak"] = float(((m[k] - f[k]).abs().amax(-1) / f[k].abs().amax(-1)).max())
+    res["gamma_max_abs_err_over_gamma0"] = float(((m["gamma"] - f["gamma"]).abs() / g0).max())
+    res["omega_max_rel_err"] = float(((m["omega"] - f["omega"]).abs() / w0).max())
+    res["gamma_over_gamma0_f64_range"] = [float((f["gamma"] / g0).min()), float((f["gamma"] / g0).max())]
+    res["delta_omega_over_gamma0_f64_range"] = [float(((f["omega"] - w0) / g0).min()),
+                                                 float(((f["omega"] - w0) / g0).max())]
+    return res
+
+
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
@@ -208,8 +249,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", default=None,
-                    choices=["fields_mixed_small", "fields_f64_small", "lo_small", "ring_small", "adj_small"])
+                    choices=["fields_mixed_small", "fields_mixed2_small", "fields_f64_small", "lo_small",
+                             "ring_small", "cloud_small", "adj_small"])
     ap.add_argument("--no-extra", action="store_true", help="skip the float64, oscillator and CPU legs")
+    ap.add_argument("--compare-cloud", type=int, default=0, metavar="STEPS",
+                    help="run the 4096-oscillator cloud for STEPS steps in both precisions and compare them")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -235,7 +279,9 @@ def main():
     pairs_per_step = NU * NV * T * 2 * dp.N
 
     if args.profile:
-        if args.profile == "fields_mixed_small":
+        if args.profile in ("fields_mixed_small", "fields_mixed2_small"):
+            # 512 rows of the grid, frames 5 and 11; one point per thread (16 x 16 tiles) or two
+            pc.pc_set_plane_tiling(ctx, *((16, 16) if args.profile == "fields_mixed_small" else (32, 16)))
             pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=512,
                                nv=2048, times=[float(times[5]), float(times[11])], precision=pc.PC_MIXED)
         elif args.profile == "fields_f64_small":
@@ -245,9 +291,12 @@ def main():
             # batched pairs, mixed: one persistent launch over 2000 steps
             cfg, _ = W.cfg3(B=256, n_steps=2000)
             pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=pc.PC_MIXED)
-        elif args.profile == "ring_small":
-            # 256-oscillator ring, mixed, grid path: 200 steps (13 causal blocks)
-            cfg = W.cfg4(n_steps=200)
+        elif args.profile in ("ring_small", "cloud_small"):
+            # grid path, mixed, block loop launched from the host so that the profiler sees every
+            # launch: the 256-oscillator ring over 200 steps (13 causal blocks), or the 4096-oscillator
+            # cloud over 64 steps (4 blocks)
+            os.environ["PYCHARGE_GB300_HOST_LOOP"] = "1"
+            cfg = W.cfg4(n_steps=200) if args.profile == "ring_small" else W.cfg5(n_steps=64)
             pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=pc.PC_MIXED)
         else:
             # adjoint of the ring's float64 run over 200 steps
@@ -255,6 +304,11 @@ def main():
             w = torch.ones((1, cfg.N), dtype=torch.float64, device=dev)
             pc.pc_dipoles_adjoint(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, w)
         torch.cuda.synchronize()
+        return 0
+
+    if args.compare_cloud:
+        print(json.dumps(compare_cloud(pc, ctx, dev, args.compare_cloud)), flush=True)
+        ctx.close()
         return 0
 
     out = pc.capi.alloc_field_out(NU * NV, T, pc.PC_MIXED, dev)
@@ -265,8 +319,8 @@ def main():
                            times=list(times), precision=pc.PC_MIXED, out=out)
 
     # plan: the tile shape of the mixed plane kernel, tuned on this workload before the timed steps
-    tile_rows = pc.pc_autotune_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=NU,
-                                     nv=NV, times=list(times), out=out)
+    tile_rows, tile_cols = pc.pc_autotune_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0),
+                                                ev=(0, step, 0), nu=NU, nv=NV, times=list(times), out=out)
     for _ in range(args.warmup):
         step_fn()
     torch.cuda.synchronize()
@@ -341,14 +395,15 @@ def main():
                                "w0 = 2 pi 200 THz, origins in a 1 um cube, seed 2107), 2048x2048 plane at "
                                "z = 0.5 um, 16 frames t = 10 fs + f 5/16 fs, mixed precision, float32 outputs",
                    "pairs_per_step": pairs_per_step, "parallelism": f"replicas x{world}",
-                   "tile": f"{tile_rows} x {256 // tile_rows} points (autotuned)",
+                   "tile": f"{tile_rows} x {tile_cols} points, {tile_rows * tile_cols // 256} per thread (autotuned)",
                    "l2": "flushed between steps (256 MB write); outputs 2.7 GB > L2"},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": "LW pair evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "fields_mixed_kernel", "flops_per_pair": FLOPS_PER_PAIR,
+                     "kernel": "fields_mixed2_kernel" if tile_rows * tile_cols > 256 else "fields_mixed_kernel",
+                     "flops_per_pair": FLOPS_PER_PAIR,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
                      "measured_fp32_fma_per_s": fp32_fma, "measured_fp64_fma_per_s": fp64_fma},
     }
@@ -430,12 +485,65 @@ def main():
                                   "workload": "gradients of sum E(T) w.r.t. 768 origin coordinates, 256 omega0, "
                                               "256 d0 of the 256-oscillator ring, 20000 steps (forward + reverse)"}
         cfg5 = W.cfg5()
-        n5 = 1600
-        r = lo_time(cfg5, n5, pc.PC_MIXED, False)
-        r["workload"] = (f"cloud: 4096 oscillators in a 600 nm cube, first {n5} of the 20000 RK4 steps "
-                         "(bounded sample; 100 causal blocks of 16 steps)")
+        r = lo_time(cfg5, cfg5.n_steps, pc.PC_MIXED, False)
+        r["workload"] = "cloud: 4096 oscillators in a 600 nm cube x 20000 RK4 steps (1250 causal blocks of 16 steps)"
         ds["cloud_mixed"] = r
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(s)
+            fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        # gradients of the fitted decay rates (Eq. KE fit) of the batched pairs: forward, fit, fit
+        # adjoint and reverse sweep, float64
+        lod3 = pc.lo_config_to_device(cfg3, dev)
+        wg3 = torch.ones((cfg3.B, cfg3.N), dtype=torch.float64, device=dev)
+        ms = timed(lambda: pc.pc_dipoles_rates_adjoint(ctx, lod3, cfg3.dt, cfg3.n_steps, cfg3.first_index,
+                                                       dL_dgamma=wg3))
+        ds["pairs_rates_adjoint_f64"] = {
+            "value": cfg3.B * cfg3.N * cfg3.n_steps / (ms * 1e-3), "unit": "dipole-steps/s", "ms": ms,
+            "workload": "gradients of sum gamma of the 256 x 2 batched pairs (40000 steps) w.r.t. origins, "
+                        "omega0, d0 (forward + fit + reverse)"}
+        # moving dipoles (Sec. 4.3): the ring with every origin oscillating along x (1 A, 20 THz)
+        cfg4m = W.cfg4(n_steps=4000)
+        mot = tuple(torch.from_numpy(x).to(dev)
+                    for x in W.oscillating_origins(cfg4m, 1e-10, 2 * math.pi * 20e12))
+        lod4m = pc.lo_config_to_device(cfg4m, dev)
+        ms = timed(lambda: pc.pc_dipoles_run_moving(ctx, lod4m, mot, cfg4m.dt, cfg4m.n_steps))
+        ds["ring_moving_f64"] = {"value": cfg4m.N * cfg4m.n_steps / (ms * 1e-3), "unit": "dipole-steps/s", "ms": ms,
+                                 "workload": "ring of 256 oscillators, origins oscillating along x "
+                                             "(1e-10 m, 20 THz), 4000 RK4 steps, float64"}
+        del mot
+        # population dynamics (App. A): one excited and one unexcited dipole, q = 20 e, 80 nm,
+        # one beating period (2.1e6 steps of 10 as)
+        cfgp = W.population_pair()
+        lodp = pc.lo_config_to_device(cfgp, dev)
+        for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
+            ms = timed(lambda: pc.pc_dipoles_run(ctx, lodp, cfgp.dt, cfgp.n_steps, precision=prec))
+            ds["populations_" + name] = {"value": cfgp.B * cfgp.N * cfgp.n_steps / (ms * 1e-3),
+                                         "unit": "dipole-steps/s", "ms": ms,
+                                         "workload": "two dipoles, 80 nm, q = 20 e, 2.1e6 RK4 steps of 10 as"}
         line["dipole_steps"] = ds
+        # charges on analytic trajectories (no history samples): the orbiting pair (static +e, -e on
+        # a 1 nm circle at 0.1 c) on a 2048 x 2048 grid over +-50 nm, 4 frames, float64
+        ng = 2048
+        gx = torch.linspace(-50e-9, 50e-9, ng, dtype=torch.float64, device=dev)
+        pts = torch.stack([gx[:, None].expand(ng, ng), gx[None, :].expand(ng, ng),
+                           torch.zeros((ng, ng), dtype=torch.float64, device=dev)], dim=-1).reshape(-1, 3)
+        par = np.zeros((2, 12))
+        par[1, 3], par[1, 7], par[1, 9], par[1, 10] = 1.0, 1.0, 1e-9, 0.1 * W.C / 1e-9
+        kinds = [pc.PC_TRAJ_STATIONARY, pc.PC_TRAJ_CIRCULAR]
+        tp = [10e-15 + f * 50e-18 for f in range(4)]
+        pout = pc.capi.alloc_field_out(ng * ng, len(tp), pc.PC_F64, dev)
+        ms = timed(lambda: pc.pc_fields_param(ctx, kinds, [W.E_CHARGE, -W.E_CHARGE], par, pts, tp, out=pout))
+        line["param_fields_f64"] = {"value": ng * ng * len(tp) * 2 / (ms * 1e-3), "unit": "LW pair evals/s",
+                                    "ms": ms, "workload": "static +e and -e on a 1 nm circle at 0.1 c, analytic "
+                                                          "trajectories, 2048 x 2048 grid over +-50 nm, 4 frames"}
+        del pout, pts
         if rank == 0:
             import oracle
 

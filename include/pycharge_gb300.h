@@ -158,15 +158,27 @@ pc_status pc_fields_param(pc_ctx *ctx, const pc_param_charges *ch, const double 
 /*
  * pc_autotune_plane -- picks the tile shape of the PC_MIXED plane evaluation for this workload and
  * keeps it in the context for later pc_fields_plane / pc_fields_plane_to_host calls: tiles of 256
- * points as 8 x 32, 16 x 16 (the default) or 32 x 8 rows x columns, each run once to warm up and
- * once timed on the given arguments (which are those of pc_fields_plane with PC_MIXED; `out`
- * receives the fields of the last run).  Writes the chosen rows per tile to *tile_rows (or NULL).
- * The results of every shape agree to float32 rounding (the tile anchor enters the delays).
+ * points as 8 x 32, 16 x 16 (the default) or 32 x 8 rows x columns with one point per thread, and,
+ * for grids of dipoles alone, tiles of 512 points as 16 x 32, 32 x 16 or 64 x 8 with two points per
+ * thread (each thread's two points in rows r and r + rows/2 of the tile, evaluated together in the
+ * lanes of packed float32 registers).  Each shape runs once to warm up and once timed on the given
+ * arguments (those of pc_fields_plane with PC_MIXED; `out` receives the fields of the last run).
+ * Writes the chosen tile's rows and columns to *tile_rows, *tile_cols (either may be NULL).  The
+ * results of every shape agree to float32 rounding (the tile anchor enters the delays).
  * Errors: those of pc_fields_plane.
  */
 pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const pc_plane *grid,
                             const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,
-                            int32_t *tile_rows, void *stream);
+                            int32_t *tile_rows, int32_t *tile_cols, void *stream);
+
+/*
+ * pc_set_plane_tiling -- sets the PC_MIXED plane tile shape directly (what pc_autotune_plane
+ * chooses): tile_rows x tile_cols = 256 points (one per thread) or 512 (two per thread; used for
+ * plane grids of dipoles alone, other calls take the one-point tile of the same columns),
+ * tile_cols a power of two up to 256.
+ * Errors: PC_ERR_ARG for any other shape.
+ */
+pc_status pc_set_plane_tiling(pc_ctx *ctx, int32_t tile_rows, int32_t tile_cols);
 
 /*
  * pc_fields_to_host / pc_fields_plane_to_host -- pc_fields / pc_fields_plane with the outputs
@@ -230,8 +242,12 @@ typedef struct {
  * each step d'' is set from the equation of motion at the step end.  Optionally the kinetic energy
  * m d'^2/(2 q^2) from first_index on is fitted to Eq. KE (Levenberg-Marquardt), giving gamma and
  * omega per dipole.
- * Errors: PC_ERR_ARG, PC_ERR_CAUSALITY (two dipoles closer than c dt), PC_ERR_VELOCITY,
- * PC_ERR_NOCONV, PC_ERR_CUDA.
+ * Configurations of more than 64 dipoles run as grid-wide launches per causal block, the block
+ * loop one CUDA graph with a device-side while node; where that node is unavailable, or when the
+ * environment variable PYCHARGE_GB300_HOST_LOOP is "1" (for profilers that do not descend into
+ * conditional graph nodes), the same launches are issued from the host, with identical results.
+ * Errors: PC_ERR_ARG (also B > 65535 with N > 64), PC_ERR_CAUSALITY (two dipoles closer than
+ * c dt), PC_ERR_VELOCITY, PC_ERR_NOCONV, PC_ERR_CUDA.
  */
 pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                          const pc_run_out *out, void *stream);

@@ -11,6 +11,10 @@ from .capi import (  # noqa: F401
     PC_MIXED,
     PC_RADIATION,
     PC_TOTAL,
+    PC_TRAJ_ACCELERATING,
+    PC_TRAJ_CIRCULAR,
+    PC_TRAJ_OSCILLATING,
+    PC_TRAJ_STATIONARY,
     Context,
     PcError,
     charges_to_device,
@@ -28,6 +32,7 @@ from .capi import (  # noqa: F401
     pc_dipoles_run_moving,
     pc_fields,
     pc_fields_param,
+    pc_set_plane_tiling,
     pc_fields_plane,
     pc_fields_plane_to_host,
     pc_ke_fit,

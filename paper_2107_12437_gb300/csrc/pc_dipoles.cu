@@ -14,6 +14,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -44,6 +45,11 @@ struct RunArgs {
   // tables built once per run (mixed path): per-dipole float records, per-pair centre delays
   float *dipf;        // [B][N][kDipF]: origin/L as hi+lo (6), axis (3), m2/(m1+m2), m1/(m1+m2), q/e
   int2 *delay;        // [B][N][N]: |R_i - R_j| / (c dt) = x + y, x integer, y the fraction (float bits)
+  // [B][N][N] (mixed path): rho = (R_i - R_j) / (c dt) as (|rho|, rho . p_j, rho . p_i, p_j . p_i)
+  float4 *pgeo;
+  // [B][2]: closest distance of two origins (over the run for moving ones) and largest origin
+  // speed, as the bits of non-negative doubles (ordered like the values under integer min / max)
+  unsigned long long *rstat;
   int *kblock;        // [B] causal block length per configuration
   double *Ehalf;      // [B][N][n_steps] E_d at t_n + dt/2 (kept for the adjoint), or null
   // grid path: sources split into nsplit slices whose partial stage fields Epart
@@ -180,7 +186,8 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
 
 // Contribution of dipole j to the driving field of receiver i at time u (steps), history 0..nv.
 // float64: both charges per charge (Eqs. r_1, r_2, E); returns p_i . E.
-__device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int *err) {
+__device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int64_t kg_fixed,
+                                 int *err) {
   const int64_t S = a.n_steps + 1;
   const double cdt = kC * a.dt;
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
@@ -206,8 +213,12 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
   }
   const double q = a.q[bj];
   const double *Tj = a.rk4tab + bj * kTab;
-  double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
-  const int64_t kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
+  // first guess of the retarded sample: the centre delay (from the pair table for fixed origins)
+  int64_t kg = kg_fixed;
+  if (a.org_pos) {
+    double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
+    kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
+  }
   double E[3] = {0.0, 0.0, 0.0};
   for (int sg = 0; sg < 2; ++sg) {
     tr.w = Tj[kTabC + 8 + sg];
@@ -251,16 +262,13 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
 
 // float32: the dipole pair in difference form from the float32 mirror; returns p_i . E in units
 // of k_e e / (c dt)^2.  kb + xc is the retarded time of dipole j's centre.
-__device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, float xc, int nvalid, int *err) {
+__device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, float xc, const float4 g, int nvalid,
+                                int *err) {
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
-  const float *fi = a.dipf + bi * kDipF, *fj = a.dipf + bj * kDipF;
-  // origin offsets from hi + lo parts: the hi difference of nearby origins is exact
-  const float rx = (fi[0] - fj[0]) + (fi[3] - fj[3]);
-  const float ry = (fi[1] - fj[1]) + (fi[4] - fj[4]);
-  const float rz = (fi[2] - fj[2]) + (fi[5] - fj[5]);
-  const float rn = sqrtf(rx * rx + ry * ry + rz * rz);
-  const float px = fj[6], py = fj[7], pz = fj[8];
-  const float rp = rx * px + ry * py + rz * pz;
+  const float *fj = a.dipf + bj * kDipF;
+  // pair geometry from the table (fixed origins); the source's charge split and charge
+  const float rn = g.x, rp = g.y, rpi = g.z, ppi = g.w;
+  const float4 cj = *reinterpret_cast<const float4 *>(fj + 8);  // (p_z, mu+, mu-, q/e)
   const HistF32RW H{a.H32 + bj * (size_t)(a.n_steps + 1)};
   // fast path: both charges on the segment of the centre's retarded time (packed solve), then only
   // the driving-field projection p_i . E of the pair
@@ -268,7 +276,6 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
     float fl;
     const int kc = Num<float>::floor_int(xc, fl);
     const int k = kb + kc;
-    const float rpi = rx * fi[6] + ry * fi[7] + rz * fi[8], ppi = px * fi[6] + py * fi[7] + pz * fi[8];
     if (k < -1) {
       // the centre's retarded time lies a sample or more before t = 0; when both charges' offsets
       // (at most |s| samples) keep them there too, they rest at their first position with no
@@ -276,14 +283,14 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
       // R_c = |rho - s_c p|, delta_c = R_c - rn = s_c (s_c - 2 rp) / (R_c + rn)
       float x0, v0, a0;
       H.get_in(0, x0, v0, a0);
-      const float sp = fj[9] * x0, sm = -fj[10] * x0;
+      const float sp = cj.y * x0, sm = -cj.z * x0;
       if ((float)kb + xc + fmaxf(fabsf(sp), fabsf(sm)) < -0.01f) {
         const float Rp = sqrtf(fmaxf(rn * rn + sp * (sp - 2.f * rp), 0.f));
         const float Rm = sqrtf(fmaxf(rn * rn + sm * (sm - 2.f * rp), 0.f));
         const float2 dl = make_float2(__fdividef(sp * (sp - 2.f * rp), Rp + rn), __fdividef(sm * (sm - 2.f * rp), Rm + rn));
         const float2 zero = make_float2(0.f, 0.f);
         if (Rp > 0.f && Rm > 0.f)
-          return dipole_drive_fast(rn, rp, fj[9], fj[10], fj[11], make_float2(x0, x0), zero, zero, dl, rpi, ppi);
+          return dipole_drive_fast(rn, rp, cj.y, cj.z, cj.w, make_float2(x0, x0), zero, zero, dl, rpi, ppi);
       }
     }
     if (k >= 0 && k <= nvalid - 2) {
@@ -293,15 +300,24 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
       // the first segment may not be extended backwards, the last one only by kEndTol
       const float lo = (k == 0) ? 0.f : -kExtrap, hi = 1.f + ((k == nvalid - 2) ? kEndTol : kExtrap);
       float2 X, V, Ac, dl;
-      if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, fj[9], fj[10], X, V, Ac, dl, 0.5f * (lo + hi),
+      if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, cj.y, cj.z, X, V, Ac, dl, 0.5f * (lo + hi),
                                0.5f * (hi - lo)))
-        return dipole_drive_fast(rn, rp, fj[9], fj[10], fj[11], X, V, Ac, dl, rpi, ppi);
+        return dipole_drive_fast(rn, rp, cj.y, cj.z, cj.w, X, V, Ac, dl, rpi, ppi);
     }
   }
+  // general case: the geometry again from the float records (origin offsets from hi + lo parts: the
+  // hi difference of nearby origins is exact)
+  const float *fi = a.dipf + bi * kDipF;
+  const float rx = (fi[0] - fj[0]) + (fi[3] - fj[3]);
+  const float ry = (fi[1] - fj[1]) + (fi[4] - fj[4]);
+  const float rz = (fi[2] - fj[2]) + (fi[5] - fj[5]);
+  const float rn2 = sqrtf(rx * rx + ry * ry + rz * rz);
+  const float px = fj[6], py = fj[7], pz = fj[8];
+  const float rp2 = rx * px + ry * py + rz * pz;
   float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   uint8_t mk = 0;
-  const int e = dipole_net<PC_TOTAL, float, HistF32RW>(H, nvalid, kb, xc, rx, ry, rz, rn, px, py, pz, rp, fj[9], fj[10],
-                                                     fj[11], 0.f, false, acc, mk);
+  const int e = dipole_net<PC_TOTAL, float, HistF32RW>(H, nvalid, kb, xc, rx, ry, rz, rn2, px, py, pz, rp2, cj.y, cj.z,
+                                                     cj.w, 0.f, false, acc, mk);
   if (e) {
     *err = (e == PC_ERR_HISTORY) ? PC_ERR_CAUSALITY : e;
     return 0.f;
@@ -327,18 +343,22 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       if (j == i) continue;
       if (MIXED) {
         // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
-        const int2 dl = a.delay[(size_t)bidx(a, b, i) * a.N + j];
+        const size_t ij = (size_t)bidx(a, b, i) * a.N + j;
+        const int2 dl = a.delay[ij];
         const float xs = stage_f - __int_as_float(dl.y);
         float flf;
         const int fl = Num<float>::floor_int(xs, flf);
-        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, (int)n0 + 1, err);
+        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, a.pgeo[ij], (int)n0 + 1, err);
         // Kahan sum over sources
         const float y = v - comp;
         const float t = accf + y;
         comp = (t - accf) - y;
         accf = t;
       } else {
-        accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, err);
+        // first guess: the sample of the centre's retarded time, n0 + stage - delay
+        const int2 dl = a.delay[(size_t)bidx(a, b, i) * a.N + j];
+        const int kg = (int)n0 - dl.x + Num<float>::floor_int(stage_f - __int_as_float(dl.y));
+        accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, kg, err);
       }
     }
   }
@@ -424,8 +444,8 @@ __global__ void lo_tables_kernel(const RunArgs a) {
   const int b = blockIdx.x;
   const int N = a.N;
   const double L = kC * a.dt;
-  __shared__ double s_rmin[256], s_smax[256], s_vmax[256];
-  double rmin = 1e300, smax = 0.0;
+  __shared__ double s_smax[256];
+  double smax = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const size_t bi = bidx(a, b, i);
     float *f = a.dipf + bi * kDipF;
@@ -443,42 +463,89 @@ __global__ void lo_tables_kernel(const RunArgs a) {
     f[11] = (float)(a.q[bi] / kE);
     smax = fmax(smax, fabs(a.d0[bi] / a.q[bi]));
   }
-  double vmax = 0.0;  // largest origin speed (moving dipoles)
-  const int64_t H = 2 * a.n_steps + 1;
-  for (int64_t ij = threadIdx.x; ij < (int64_t)N * N; ij += blockDim.x) {
-    const int i = (int)(ij / N), j = (int)(ij % N);
-    const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
-    const double dx = a.origin[3 * bi] - a.origin[3 * bj], dy = a.origin[3 * bi + 1] - a.origin[3 * bj + 1],
-                 dz = a.origin[3 * bi + 2] - a.origin[3 * bj + 2];
-    const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    if (i != j) rmin = fmin(rmin, r);
-    if (a.org_pos && i != j) {
-      // closest approach of the two origins over the run, and the origins' speeds
-      for (int64_t h = 0; h < H; ++h) {
-        const double *pi_ = a.org_pos + (bi * H + h) * 3, *pj_ = a.org_pos + (bj * H + h) * 3;
-        const double ex = pi_[0] - pj_[0], ey = pi_[1] - pj_[1], ez = pi_[2] - pj_[2];
-        rmin = fmin(rmin, sqrt(ex * ex + ey * ey + ez * ez));
-        const double *vi = a.org_vel + (bi * H + h) * 3;
-        vmax = fmax(vmax, sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
-      }
-    }
-    const double x = r / L;
-    const double fl = floor(x);
-    if (a.delay) a.delay[(size_t)bi * N + j] = make_int2((int)fl, __float_as_int((float)(x - fl)));
-  }
-  s_rmin[threadIdx.x] = rmin;
   s_smax[threadIdx.x] = smax;
-  s_vmax[threadIdx.x] = vmax;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int t = 1; t < blockDim.x; ++t) {
-      rmin = fmin(rmin, s_rmin[t]);
-      smax = fmax(smax, s_smax[t]);
-      vmax = fmax(vmax, s_vmax[t]);
-    }
+    for (int t = 1; t < blockDim.x; ++t) smax = fmax(smax, s_smax[t]);
+    const double rmin = __longlong_as_double((long long)a.rstat[2 * b]);
+    const double vmax = __longlong_as_double((long long)a.rstat[2 * b + 1]);
     // within a block of K steps a source origin moves at most vmax K dt closer
     const double kk = floor((rmin - 3.0 * smax) / (L * (1.0 + vmax / kC)));
     a.kblock[b] = (int)fmax(1.0, fmin((double)kMaxBlock, kk));
+  }
+}
+
+// Presets a.rstat to (a large distance, 0): 0x7f7f... is about 1.4e306 as a double.
+__global__ void lo_rstat_init_kernel(const RunArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  a.rstat[2 * b] = 0x7f7f7f7f7f7f7f7full;
+  a.rstat[2 * b + 1] = 0ull;
+}
+
+// Per pair (i, j) of a configuration: the centre delay |R_i - R_j| / (c dt) (the first guess of
+// the retarded-time solves; its integer part capped at 2^30, beyond every history), the float32
+// pair geometry of the mixed drive, and the configuration's closest origin distance (over the run
+// for moving origins) and largest origin speed, for the causal block length.  Grid: x over pair
+// blocks, y over configurations.
+__global__ void __launch_bounds__(256) lo_pairs_kernel(const RunArgs a) {
+  __shared__ double s_r[256], s_v[256];
+  const int N = a.N;
+  const int64_t NN = (int64_t)N * N;
+  const double L = kC * a.dt;
+  const int64_t H = 2 * a.n_steps + 1;
+  for (int b = blockIdx.y; b < a.B; b += gridDim.y) {
+    double rmin = 1e300, vmax = 0.0;
+    for (int64_t ij = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ij < NN;
+         ij += (int64_t)gridDim.x * blockDim.x) {
+      const int i = (int)(ij / N), j = (int)(ij % N);
+      const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+      const double *Ri = a.origin + 3 * bi, *Rj = a.origin + 3 * bj;
+      const double dx = Ri[0] - Rj[0], dy = Ri[1] - Rj[1], dz = Ri[2] - Rj[2];
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      if (i != j) {
+        rmin = fmin(rmin, r);
+        if (a.org_pos) {
+          // closest approach of the two origins over the run
+          for (int64_t h = 0; h < H; ++h) {
+            const double *pi_ = a.org_pos + (bi * H + h) * 3, *pj_ = a.org_pos + (bj * H + h) * 3;
+            const double ex = pi_[0] - pj_[0], ey = pi_[1] - pj_[1], ez = pi_[2] - pj_[2];
+            rmin = fmin(rmin, sqrt(ex * ex + ey * ey + ez * ez));
+          }
+        }
+      } else if (a.org_pos) {
+        for (int64_t h = 0; h < H; ++h) {
+          const double *vi = a.org_vel + (bi * H + h) * 3;
+          vmax = fmax(vmax, sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+        }
+      }
+      const double x = r / L;
+      const double fl = floor(x);
+      a.delay[bi * N + j] = make_int2((int)fmin(fl, 1073741824.0), __float_as_int((float)(x - fl)));
+      if (a.pgeo) {
+        const double *pi_ = a.axis + 3 * bi, *pj_ = a.axis + 3 * bj;
+        const double rx = dx / L, ry = dy / L, rz = dz / L;
+        a.pgeo[bi * N + j] =
+            make_float4((float)x, (float)(rx * pj_[0] + ry * pj_[1] + rz * pj_[2]),
+                        (float)(rx * pi_[0] + ry * pi_[1] + rz * pi_[2]),
+                        (float)(pj_[0] * pi_[0] + pj_[1] * pi_[1] + pj_[2] * pi_[2]));
+      }
+    }
+    s_r[threadIdx.x] = rmin;
+    s_v[threadIdx.x] = vmax;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) {
+        s_r[threadIdx.x] = fmin(s_r[threadIdx.x], s_r[threadIdx.x + w]);
+        s_v[threadIdx.x] = fmax(s_v[threadIdx.x], s_v[threadIdx.x + w]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      atomicMin(a.rstat + 2 * b, (unsigned long long)__double_as_longlong(s_r[0]));
+      atomicMax(a.rstat + 2 * b + 1, (unsigned long long)__double_as_longlong(s_v[0]));
+    }
+    __syncthreads();
   }
 }
 
@@ -1175,13 +1242,16 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const bool mixed = opts->precision == PC_MIXED;
   if (motion && (mixed || !motion->pos || !motion->vel || !motion->acc)) return PC_ERR_ARG;
   if (mixed && S > ((int64_t)1 << 30)) return PC_ERR_ARG;
+  if (dp->N > pc::kSmallN && dp->B > 65535) return PC_ERR_ARG;  // grid path: configurations on grid y
   // scratch: stage fields, float32 mirror (mixed), dipole records, pair delays (mixed), block
   // lengths, kinetic energies for the fit
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   const size_t es_bytes = al(nbn * (2 * pc::kMaxBlock + 1) * sizeof(double));
   const size_t h_bytes = mixed ? al(nbn * S * sizeof(float4)) : 0;
   const size_t f_bytes = al(nbn * pc::kDipF * sizeof(float));
-  const size_t dl_bytes = mixed ? al(nbn * dp->N * sizeof(int2)) : 0;
+  const size_t dl_bytes = al(nbn * dp->N * sizeof(int2));
+  const size_t geo_bytes = mixed ? al(nbn * dp->N * sizeof(float4)) : 0;
+  const size_t rs_bytes = al(2 * (size_t)dp->B * sizeof(unsigned long long));
   const size_t k_bytes = al(dp->B * sizeof(int));
   const size_t ke_bytes = opts->fit ? al(nbn * S * sizeof(double)) : 0;
   const bool grid = dp->N > pc::kSmallN;
@@ -1191,7 +1261,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const size_t part_off = es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes + ke_bytes;
   const size_t blk_off = part_off + part_bytes;
   const size_t tab_off = blk_off + blk_bytes;
-  if (ctx->run_scratch.reserve(tab_off + tab_bytes) != cudaSuccess) return PC_ERR_CUDA;
+  const size_t geo_off = tab_off + tab_bytes;
+  const size_t rs_off = geo_off + geo_bytes;
+  if (ctx->run_scratch.reserve(rs_off + rs_bytes) != cudaSuccess) return PC_ERR_CUDA;
   char *scr = (char *)ctx->run_scratch.ptr;
   pc::RunArgs a;
   a.B = dp->B;
@@ -1215,7 +1287,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.Es = (double *)scr;
   a.H32 = mixed ? (float4 *)(scr + es_bytes) : nullptr;
   a.dipf = (float *)(scr + es_bytes + h_bytes);
-  a.delay = mixed ? (int2 *)(scr + es_bytes + h_bytes + f_bytes) : nullptr;
+  a.delay = (int2 *)(scr + es_bytes + h_bytes + f_bytes);
+  a.pgeo = mixed ? (float4 *)(scr + geo_off) : nullptr;
+  a.rstat = (unsigned long long *)(scr + rs_off);
   a.kblock = (int *)(scr + es_bytes + h_bytes + f_bytes + dl_bytes);
   a.Ehalf = Ehalf;
   a.Epart = nullptr;
@@ -1228,6 +1302,14 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.org_acc = motion ? motion->acc : nullptr;
   a.status = ctx->d_status;
   char *ke_base = scr + es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes;
+  {
+    // pair tables and the per-configuration distance / speed extremes, then the per-dipole tables
+    const int64_t NN = (int64_t)dp->N * dp->N;
+    const unsigned gx = (unsigned)std::min<int64_t>((NN + 255) / 256, 2048);
+    const unsigned gy = (unsigned)std::min(dp->B, 65535);
+    pc::lo_rstat_init_kernel<<<(dp->B + 255) / 256, 256, 0, st>>>(a);
+    pc::lo_pairs_kernel<<<dim3(gx, gy), 256, 0, st>>>(a);
+  }
   pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
   if (k_out) {
     // the shortest causal block over the batch, for the caller
@@ -1267,8 +1349,24 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     else pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
     pc::lo_start_kernel<<<rgrid, 128, 0, st>>>(a);
     if (n_steps > 0) {
-      pc_status gs = pc::launch_block_loop(ctx, a, mixed, dgrid, rgrid, st);
-      if (gs != PC_OK) return gs;
+      // the block loop runs as one graph with a device-side while node; the host-driven loop (one
+      // drive and one RK4 launch per block, same kernels and order) serves where that node is not
+      // available, and on request through PYCHARGE_GB300_HOST_LOOP=1 (profilers that do not
+      // descend into conditional graph nodes see every launch)
+      const char *hl = getenv("PYCHARGE_GB300_HOST_LOOP");
+      pc_status gs = (hl && hl[0] == '1') ? PC_ERR_CUDA : pc::launch_block_loop(ctx, a, mixed, dgrid, rgrid, st);
+      if (gs != PC_OK) {
+        cudaGetLastError();
+        for (int64_t n0 = 0; n0 < n_steps; n0 += K) {
+          const int kb = (int)std::min<int64_t>(K, n_steps - n0);
+          if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
+          else pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
+          const unsigned wgrid = (unsigned)((nbn * 32 + 127) / 128);
+          if (mixed) pc::lo_rk4_kernel<true><<<wgrid, 128, 0, st>>>(a, n0, kb);
+          else pc::lo_rk4_kernel<false><<<wgrid, 128, 0, st>>>(a, n0, kb);
+        }
+        if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
+      }
     }
   }
   if (opts->fit) {
@@ -1579,19 +1677,52 @@ __global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t
   __syncthreads();
   double Rjb[3] = {0, 0, 0};
   int err = 0;
-  for (int i = threadIdx.x; i < a.N && !err; i += blockDim.x) {
-    if (i == j) continue;
-    const size_t bi = bidx(a, b, i);
-    double Rib[3] = {0, 0, 0};
-    const int nst = ns > 0 ? ns : 1;
-    for (int s = 1; s <= nst && !err; ++s) {
-      const double eb = ns > 0 ? A.Ebar[bi * (2 * kMaxBlock + 1) + s] : A.carry[bi];
-      if (eb == 0.0) continue;
-      const double u = ns > 0 ? (double)n0 + 0.5 * s : 0.0;
-      err = pair_rev_f64(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
+  const int nst = ns > 0 ? ns : 1;
+  if (a.N >= (int)blockDim.x) {
+    // many receivers: one thread per receiver, its stages in order, its origin adjoint in registers
+    for (int i = threadIdx.x; i < a.N && !err; i += blockDim.x) {
+      if (i == j) continue;
+      const size_t bi = bidx(a, b, i);
+      double Rib[3] = {0, 0, 0};
+      for (int s = 1; s <= nst && !err; ++s) {
+        const double eb = ns > 0 ? A.Ebar[bi * (2 * kMaxBlock + 1) + s] : A.carry[bi];
+        if (eb == 0.0) continue;
+        const double u = ns > 0 ? (double)n0 + 0.5 * s : 0.0;
+        err = pair_rev_f64(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
+      }
+      for (int c = 0; c < 3; ++c)
+        if (Rib[c] != 0.0) atomicAdd(&A.g_origin[3 * bi + c], Rib[c]);
     }
-    for (int c = 0; c < 3; ++c)
-      if (Rib[c] != 0.0) atomicAdd(&A.g_origin[3 * bi + c], Rib[c]);
+  } else {
+    // few receivers: each warp takes 32 / nst receivers at a time, one lane per (receiver, stage),
+    // and a receiver's origin adjoint is summed over its stages in shared memory (fixed order)
+    // before one atomic per component
+    __shared__ double s_rib[4][32][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slots = 32 / nst;
+    const int m = lane / nst, s = 1 + lane % nst;
+    for (int i0 = 0; i0 < a.N; i0 += 4 * slots) {
+      const int i = i0 + warp * slots + m;
+      double Rib[3] = {0, 0, 0};
+      if (m < slots && i < a.N && i != j && !err) {
+        const size_t bi = bidx(a, b, i);
+        const double eb = ns > 0 ? A.Ebar[bi * (2 * kMaxBlock + 1) + s] : A.carry[bi];
+        if (eb != 0.0) {
+          const double u = ns > 0 ? (double)n0 + 0.5 * s : 0.0;
+          err = pair_rev_f64(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
+        }
+      }
+      for (int c = 0; c < 3; ++c) s_rib[warp][lane][c] = Rib[c];
+      __syncwarp();
+      if (m < slots && s == 1 && i < a.N) {
+        for (int c = 0; c < 3; ++c) {
+          double t = 0.0;
+          for (int q = 0; q < nst; ++q) t += s_rib[warp][lane + q][c];
+          if (t != 0.0) atomicAdd(&A.g_origin[3 * bidx(a, b, i) + c], t);
+        }
+      }
+      __syncwarp();
+    }
   }
   if (err) set_status(a.status, err);
   for (int c = 0; c < 3; ++c) s_rj[c][threadIdx.x] = Rjb[c];

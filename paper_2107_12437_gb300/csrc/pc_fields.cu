@@ -20,6 +20,7 @@
 
 #include "pc_internal.cuh"
 #include "pc_lw_f32.cuh"
+#include "pc_lw_f32x2.cuh"
 #include "pc_lw_f64.cuh"
 
 namespace pc {
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(128) fields_f64_kernel(const Launch L) {
       double pr[3];
       tr.p(kr, pr);
       double dv[3] = {r[0] - pr[0], r[1] - pr[1], r[2] - pr[2]};
-      double tau0 = sqrt(dot3(dv, dv)) / cdt;
+      double tau0 = sqrt(dot3(dv, dv)) * L.iLc;
       int64_t k;
       double th;
       err = solve_f64(tr, s.S, s.static_before, r, u, cdt, (int64_t)floor(u - tau0), &k, &th);
@@ -199,11 +200,12 @@ __global__ void __launch_bounds__(128) fields_f64_kernel(const Launch L) {
         tr.ax[i] = s.axis[3 * j + i];
       }
       const double q = s.qd[j], m1 = s.m1[j], m2 = s.m2[j];
+      const double iw = 1.0 / ((m1 + m2) * q);  // the one float64 division per dipole
       double dv[3] = {r[0] - tr.R[0], r[1] - tr.R[1], r[2] - tr.R[2]};
-      double tau0 = sqrt(dot3(dv, dv)) / cdt;
+      double tau0 = sqrt(dot3(dv, dv)) * L.iLd;
       int64_t kg = (int64_t)floor(u - tau0);
       for (int sg = 0; sg < 2 && !err; ++sg) {
-        tr.w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+        tr.w = (sg == 0) ? m2 * iw : -m1 * iw;
         int64_t k;
         double th;
         err = solve_f64(tr, s.Sd, 1, r, u, cdt, kg, &k, &th);
@@ -865,6 +867,255 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   if (L.out.mask) L.out.mask[o] = mask;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Two points per thread (plane grids of dipoles): the thread's points sit in rows r and r + rows of
+// a tile of 2 rows x cols points, and the fast path evaluates both at once in the lanes of float2
+// registers (pc_lw_f32x2.cuh), which packs the per-point scalar part of the pair algebra too.  The
+// per-source work staged in shared memory serves twice as many points.  Slow pairs take the
+// one-point slow path of their point.
+// ------------------------------------------------------------------------------------------------
+using KahanArr2 = float2[2][10][kMixThreads];  // [sum, compensation][output][thread], lanes = points
+
+__device__ __forceinline__ void kahan2_add(KahanArr2 &k, int tid, const V2 *P) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const float2 s0 = k[0][i][tid], c0 = k[1][i][tid];
+    const float2 y = __fadd2_rn(P[i].v, make_float2(-c0.x, -c0.y));
+    const float2 t = __fadd2_rn(s0, y);
+    const float2 d = __fadd2_rn(t, make_float2(-s0.x, -s0.y));
+    k[1][i][tid] = __fadd2_rn(d, make_float2(-y.x, -y.y));
+    k[0][i][tid] = t;
+  }
+}
+
+// the slow pairs of one point (lane 0 = A, 1 = B) of the chunk, into that point's Kahan lane
+template <int KIND>
+__device__ __forceinline__ int slow_pairs2(const Launch &L, int f, int base, unsigned long long bits, int lane,
+                                           float drx, float dry, float drz, float dr2, int64_t p, int Sd32,
+                                           float rex, const float4 *s_geo, const float4 *s_ax, const float4 *s_mix,
+                                           const float4 *const *s_hist, KahanArr2 &kh, int tid, uint8_t &mask) {
+  const Sources &s = L.src;
+  int err = 0;
+  while (bits && !err) {
+    const int jj = __ffsll((long long)bits) - 1;
+    bits &= bits - 1ull;
+    float sp[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    uint8_t smask = 0;
+    const float4 g = s_geo[jj];
+    const float4 ax = s_ax[jj];
+    const float4 mx = s_mix[jj];
+    const float rx = g.x + drx, ry = g.y + dry, rz = g.z + drz;
+    const float rho2 = rx * rx + ry * ry + rz * rz;
+    const float rn = rho2 > 0.f ? rho2 * rsqrtf(rho2) : 0.f;
+    const int kb = __float_as_int(mx.w);
+    const float corr = __fdividef(2.f * (g.x * drx + g.y * dry + g.z * drz) + dr2, rn + g.w);
+    const float xc = mx.z - corr;
+    double rp64[3];
+    point_at(L.pts, p, rp64);
+    err = slow_dipole<KIND>(s, base + jj, s_hist[jj], Sd32, kb, xc, rx, ry, rz, rn, ax, mx.x, mx.y, rex, rp64,
+                            (L.times[f] - s.t0d) / s.dtd, kC * s.dtd, L.r_excl, sp, &smask);
+    mask |= smask;
+    V2 SP[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) SP[i] = lane == 0 ? V2(sp[i], 0.f) : V2(0.f, sp[i]);
+    kahan2_add(kh, tid, SP);
+  }
+  return err;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Launch L, int64_t tiles_v) {
+  __shared__ float s_anc_hi[3], s_anc_lo[3];  // the tile anchor / (c dt) as float-float
+  __shared__ KahanArr2 s_kahan;
+  __shared__ float4 s_geo[kChunk];  // rho_a (x,y,z), |rho_a|
+  __shared__ float4 s_ax[kChunk];   // axis (x,y,z), q/e
+  __shared__ float4 s_mix[kChunk];  // m2/(m1+m2), m1/(m1+m2), fraction and integer part (bits) of the
+                                    // retarded sample of the anchor
+  __shared__ const float4 *s_hist[kChunk];
+
+  const int tid = threadIdx.x;
+  const int f = blockIdx.y;
+  const Sources &s = L.src;
+  const int sh = L.tile_shift, cols = 1 << sh, rows = kMixThreads >> sh;
+  const int64_t tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
+  const int64_t iuA = tu * 2 * rows + (tid >> sh), iuB = iuA + rows, iv = tv * cols + (tid & (cols - 1));
+  const bool actA = iuA < L.pts.nu && iv < L.pts.nv, actB = iuB < L.pts.nu && iv < L.pts.nv;
+  const int64_t pA = iuA * L.pts.nv + iv, pB = iuB * L.pts.nv + iv;
+  if (tid == 0) {
+    const double iu = (double)(tu * 2 * rows) + 0.5 * (2 * rows - 1), ivc = (double)(tv * cols) + 0.5 * (cols - 1);
+    for (int i = 0; i < 3; ++i) {
+      const double x = (L.pts.o[i] + iu * L.pts.eu[i] + ivc * L.pts.ev[i]) * L.iLd;
+      s_anc_hi[i] = (float)x;
+      s_anc_lo[i] = (float)(x - (double)s_anc_hi[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    s_kahan[0][i][tid] = make_float2(0.f, 0.f);
+    s_kahan[1][i][tid] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  uint8_t maskA = 0, maskB = 0;
+  int err = 0;
+  // offsets of the two points from the anchor, from whole grid steps (no float64 on the way)
+  const float duA = (float)(tid >> sh) - 0.5f * (float)(2 * rows - 1), duB = duA + (float)rows;
+  const float dvv = (float)(tid & (cols - 1)) - 0.5f * (float)(cols - 1);
+  const V2 drx(duA * L.eu_L[0] + dvv * L.ev_L[0], duB * L.eu_L[0] + dvv * L.ev_L[0]);
+  const V2 dry(duA * L.eu_L[1] + dvv * L.ev_L[1], duB * L.eu_L[1] + dvv * L.ev_L[1]);
+  const V2 drz(duA * L.eu_L[2] + dvv * L.ev_L[2], duB * L.eu_L[2] + dvv * L.ev_L[2]);
+  const V2 dr2 = fma2(drz, drz, fma2(dry, dry, drx * drx));
+  const float rex = (float)(L.r_excl * L.iLd);
+  const float rex_fast = rex + 1.5f;
+  const int Sd32 = (int)s.Sd;
+  const unsigned jlim = Sd32 > 3 ? (unsigned)(Sd32 - 3) : 0u;  // fast segments 1 <= j <= S-3
+  const bool any = actA || actB;
+  for (int base = 0; base < s.N; base += kChunk) {
+    const int nch = min(kChunk, s.N - base);
+    __syncthreads();
+    if (tid < nch) {
+      // the anchor's distance to the source and the centre's retarded sample in float-float
+      const int j = base + tid;
+      const float4 oh = L.srcf[4 * j + 2], ol = L.srcf[4 * j + 3];
+      const ff rax = ff_add({s_anc_hi[0], s_anc_lo[0]}, {-oh.x, -ol.x});
+      const ff ray = ff_add({s_anc_hi[1], s_anc_lo[1]}, {-oh.y, -ol.y});
+      const ff raz = ff_add({s_anc_hi[2], s_anc_lo[2]}, {-oh.z, -ol.z});
+      const ff rna = ff_sqrt(ff_add(ff_add(ff_mul(rax, rax), ff_mul(ray, ray)), ff_mul(raz, raz)));
+      const ff x = ff_add({L.uf_hi[f], L.uf_lo[f]}, {-rna.hi, -rna.lo});
+      float kaf;
+      const int kai = Num<float>::floor_int(x.hi, kaf);
+      s_geo[tid] = make_float4(rax.hi, ray.hi, raz.hi, rna.hi);
+      s_ax[tid] = L.srcf[4 * j];
+      const float4 mm = L.srcf[4 * j + 1];
+      s_mix[tid] = make_float4(mm.x, mm.y, (x.hi - kaf) + x.lo, __int_as_float(kai));
+      s_hist[tid] = L.Hd + (size_t)j * s.Sd;
+    }
+    __syncthreads();
+    if (!any || err) continue;
+    V2 P[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) P[i] = V2(0.f);
+    unsigned long long slowA = 0ull, slowB = 0ull;
+    for (int g16 = 0; g16 < nch; g16 += 16) {
+      // groups of sixteen sources summed in float32, the group sums compensated
+      const int gend = min(nch, g16 + 16);
+      for (int jj = g16; jj < gend; ++jj) {
+        const float4 g = s_geo[jj];
+        const float4 ax = s_ax[jj];
+        const float4 mx = s_mix[jj];
+        V2 rx = V2(g.x) + drx, ry = V2(g.y) + dry, rz = V2(g.z) + drz;
+        const V2 rho2 = fma2(rz, rz, fma2(ry, ry, rx * rx));
+        // rho2 == 0 makes rn NaN, which fails the tests below
+        V2 rn = rho2 * V2(rsqrtf(rho2.v.x), rsqrtf(rho2.v.y));
+        const V2 num = fma2(V2(2.f), fma2(V2(g.z), drz, fma2(V2(g.y), dry, V2(g.x) * drx)), dr2);
+        V2 xc = V2(mx.z) - num * rcp2(rn + V2(g.w));
+        const int kb = __float_as_int(mx.w);
+        float flA, flB;
+        const int jA = kb + Num<float>::floor_int(xc.v.x, flA), jB = kb + Num<float>::floor_int(xc.v.y, flB);
+        bool fA = actA && (unsigned)(jA - 1) < jlim && rn.v.x > rex_fast;
+        bool fB = actB && (unsigned)(jB - 1) < jlim && rn.v.y > rex_fast;
+        if (!(fA && fB)) {
+          if (actA && !fA) slowA |= 1ull << jj;
+          if (actB && !fB) slowB |= 1ull << jj;
+          if (!fA && !fB) continue;
+          // the point off the fast path takes the other point's geometry: finite values whose
+          // results are dropped
+          if (!fA) {
+            rx.v.x = rx.v.y;
+            ry.v.x = ry.v.y;
+            rz.v.x = rz.v.y;
+            rn.v.x = rn.v.y;
+            xc.v.x = xc.v.y;
+            flA = flB;
+          } else {
+            rx.v.y = rx.v.x;
+            ry.v.y = ry.v.x;
+            rz.v.y = rz.v.x;
+            rn.v.y = rn.v.x;
+            xc.v.y = xc.v.x;
+            flB = flA;
+          }
+        }
+        const V2 rp = fma2(rz, V2(ax.z), fma2(ry, V2(ax.y), rx * V2(ax.x)));
+        const HistF32 H{s_hist[jj]};
+        const int ja = fA ? jA : jB, jb = fB ? jB : jA;
+        const float4 hA0 = H.load(ja), hA1 = H.load(ja + 1), hB0 = H.load(jb), hB1 = H.load(jb + 1);
+        const V2 x0(hA0.x, hB0.x), v0(hA0.y, hB0.y), a0(hA0.z, hB0.z);
+        const V2 dx = V2(hA1.x, hB1.x) - x0, dv = V2(hA1.y, hB1.y) - v0, da = V2(hA1.z, hB1.z) - a0;
+        const V2 thc = xc - V2(flA, flB);
+        const V2 Xc = fma2(thc, dx, x0);
+        Ch2 cp, cm;
+        V2 ep, em;
+        const V2 tp = charge2_state(mx.x, x0, dx, v0, dv, a0, da, Xc, thc, rn, rp, cp, ep);
+        const V2 tm = charge2_state(-mx.y, x0, dx, v0, dv, a0, da, Xc, thc, rn, rp, cm, em);
+        // both charges on interior segments (0.5 +- (0.5 + kExtrap)), the series converged
+        const float thh = 0.5f + kExtrap;
+        fA = fA && fabsf(tp.v.x - 0.5f) <= thh && fabsf(tm.v.x - 0.5f) <= thh && fabsf(ep.v.x) + fabsf(em.v.x) < 1e-2f;
+        fB = fB && fabsf(tp.v.y - 0.5f) <= thh && fabsf(tm.v.y - 0.5f) <= thh && fabsf(ep.v.y) + fabsf(em.v.y) < 1e-2f;
+        // near fields that cancel in float32 also leave the fast path
+        if (fA && rn.v.x < kNearL &&
+            dipole_cancellation<float>(rn.v.x, mx.x, mx.y, cp.X.v.x, cp.V.v.x, cp.Ac.v.x, cm.X.v.x, cm.V.v.x,
+                                       cm.Ac.v.x) > kCancel)
+          fA = false;
+        if (fB && rn.v.y < kNearL &&
+            dipole_cancellation<float>(rn.v.y, mx.x, mx.y, cp.X.v.y, cp.V.v.y, cp.Ac.v.y, cm.X.v.y, cm.V.v.y,
+                                       cm.Ac.v.y) > kCancel)
+          fB = false;
+        if (actA && !fA) slowA |= 1ull << jj;
+        if (actB && !fB) slowB |= 1ull << jj;
+        if (!fA && !fB) continue;
+        dipole2_fast<KIND>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mx.x, mx.y, ax.w, cp, cm, fA, fB, P);
+      }
+      kahan2_add(s_kahan, tid, P);
+#pragma unroll
+      for (int i = 0; i < 10; ++i) P[i] = V2(0.f);
+    }
+    // the pairs of this chunk that left the fast path, per point
+    const V2 d2 = dr2;
+    if (slowA)
+      err = slow_pairs2<KIND>(L, f, base, slowA, 0, drx.v.x, dry.v.x, drz.v.x, d2.v.x, pA, Sd32, rex, s_geo, s_ax,
+                              s_mix, s_hist, s_kahan, tid, maskA);
+    if (slowB && !err)
+      err = slow_pairs2<KIND>(L, f, base, slowB, 1, drx.v.y, dry.v.y, drz.v.y, d2.v.y, pB, Sd32, rex, s_geo, s_ax,
+                              s_mix, s_hist, s_kahan, tid, maskB);
+  }
+  if (!any) return;
+  if (err) {
+    set_status(L.status, err);
+    return;
+  }
+  const float uE = L.unit[0], uB = L.unit[1], uP = L.unit[2], uA = L.unit[3];
+  for (int lane = 0; lane < 2; ++lane) {
+    if (!(lane == 0 ? actA : actB)) continue;
+    const int64_t o = (L.frame0 + f) * L.pts.P + (lane == 0 ? pA : pB);
+    float val[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      const float2 sv = s_kahan[0][i][tid], cv = s_kahan[1][i][tid];
+      val[i] = lane == 0 ? sv.x - cv.x : sv.y - cv.y;
+    }
+    if (L.out.E) {
+      float *e = (float *)L.out.E + 3 * o;
+      e[0] = uE * val[0];
+      e[1] = uE * val[1];
+      e[2] = uE * val[2];
+    }
+    if (L.out.B) {
+      float *b = (float *)L.out.B + 3 * o;
+      b[0] = uB * val[3];
+      b[1] = uB * val[4];
+      b[2] = uB * val[5];
+    }
+    if (L.out.phi) ((float *)L.out.phi)[o] = uP * val[6];
+    if (L.out.A) {
+      float *a = (float *)L.out.A + 3 * o;
+      a[0] = uA * val[7];
+      a[1] = uA * val[8];
+      a[2] = uA * val[9];
+    }
+    if (L.out.mask) L.out.mask[o] = lane == 0 ? maskA : maskB;
+  }
+}
+
 // ================================================================================================
 // host side
 // ================================================================================================
@@ -954,6 +1205,8 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
   L.status = ctx->d_status;
   L.tile_shift = ctx->tile_shift;
 
+  L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;  // 1/(c dt): first guesses without a division
+  L.iLc = has_ch ? 1.0 / (kC * s.dt) : 0.0;
   if (precision == PC_MIXED) {
     // the float32 path indexes samples with 32-bit integers
     if ((has_dp && s.Sd > (int64_t)1 << 30) || (has_ch && s.S > (int64_t)1 << 30)) return PC_ERR_ARG;
@@ -1031,17 +1284,23 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
       else if (kind == PC_COULOMB) fields_f64_kernel<PC_COULOMB><<<grid, 128, 0, st>>>(L);
       else fields_f64_kernel<PC_RADIATION><<<grid, 128, 0, st>>>(L);
     } else {
+      // plane grids of dipoles alone may take two points per thread (the tuned choice)
+      const bool two = !list && !has_ch && ctx->pts_per_thread == 2;
       int64_t tiles, tiles_v = 1;
       if (list) {
         tiles = (P + kMixThreads - 1) / kMixThreads;
       } else {
-        const int64_t cols = (int64_t)1 << L.tile_shift, rows = kMixThreads / cols;
+        const int64_t cols = (int64_t)1 << L.tile_shift, rows = (two ? 2 : 1) * (kMixThreads / cols);
         int64_t tu = (L.pts.nu + rows - 1) / rows;
         tiles_v = (L.pts.nv + cols - 1) / cols;
         tiles = tu * tiles_v;
       }
       dim3 grid((unsigned)tiles, (unsigned)L.T);
-      if (list) {
+      if (two) {
+        if (kind == PC_TOTAL) fields_mixed2_kernel<PC_TOTAL><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+        else if (kind == PC_COULOMB) fields_mixed2_kernel<PC_COULOMB><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+        else fields_mixed2_kernel<PC_RADIATION><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+      } else if (list) {
         if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
         else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
         else fields_mixed_kernel<PC_RADIATION, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
@@ -1247,20 +1506,37 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
 // caller's workload once to warm up and once timed; the fastest is kept in the context for the
 // plane calls that follow.
 // ================================================================================================
+extern "C" pc_status pc_set_plane_tiling(pc_ctx *ctx, int32_t tile_rows, int32_t tile_cols) {
+  if (!ctx || tile_rows < 1 || tile_cols < 1 || tile_cols > pc::kMixThreads) return PC_ERR_ARG;
+  if (tile_cols & (tile_cols - 1)) return PC_ERR_ARG;  // a power of two
+  const int64_t pts = (int64_t)tile_rows * tile_cols;
+  if (pts != pc::kMixThreads && pts != 2 * pc::kMixThreads) return PC_ERR_ARG;
+  int sh = 0;
+  while ((1 << sh) < tile_cols) ++sh;
+  ctx->tile_shift = sh;
+  ctx->pts_per_thread = pts == pc::kMixThreads ? 1 : 2;
+  return PC_OK;
+}
+
 extern "C" pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,
                                        const pc_plane *grid, const double *times, int32_t T, int32_t kind,
-                                       double r_excl, const pc_field_out *out, int32_t *tile_rows, void *stream) {
+                                       double r_excl, const pc_field_out *out, int32_t *tile_rows,
+                                       int32_t *tile_cols, void *stream) {
   if (!ctx || !grid || !out) return PC_ERR_ARG;
   pc::DeviceGuard g(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
-  const int shifts[3] = {5, 4, 3};  // 32, 16, 8 columns
+  // (points per thread, log2 columns): 8 x 32, 16 x 16, 32 x 8 tiles of one point per thread, and
+  // 16 x 32, 32 x 16, 64 x 8 of two (plane grids of dipoles alone)
+  const int cand[6][2] = {{1, 5}, {1, 4}, {1, 3}, {2, 5}, {2, 4}, {2, 3}};
+  const int ncand = (ch && ch->M > 0) ? 3 : 6;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PC_ERR_CUDA;
   float best = 1e30f;
-  int best_shift = ctx->tile_shift;
+  int best_c = -1;
   pc_status rs = PC_OK;
-  for (int c = 0; c < 3 && rs == PC_OK; ++c) {
-    ctx->tile_shift = shifts[c];
+  for (int c = 0; c < ncand && rs == PC_OK; ++c) {
+    ctx->pts_per_thread = cand[c][0];
+    ctx->tile_shift = cand[c][1];
     rs = pc_fields_plane(ctx, ch, dp, grid, times, T, kind, PC_MIXED, r_excl, out, stream);
     if (rs != PC_OK) break;
     cudaEventRecord(e0, st);
@@ -1271,12 +1547,15 @@ extern "C" pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const 
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      best_shift = shifts[c];
+      best_c = c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx->tile_shift = best_shift;
-  if (tile_rows) *tile_rows = pc::kMixThreads >> best_shift;
+  if (best_c < 0) best_c = 1;
+  ctx->pts_per_thread = cand[best_c][0];
+  ctx->tile_shift = cand[best_c][1];
+  if (tile_rows) *tile_rows = ctx->pts_per_thread * (pc::kMixThreads >> ctx->tile_shift);
+  if (tile_cols) *tile_cols = 1 << ctx->tile_shift;
   return rs;
 }

@@ -116,12 +116,15 @@ __device__ __forceinline__ void lw_add_f64(double q, const double a[3], const do
                                            double r_excl, double E[3], double B[3], double *phi, double A[3],
                                            uint8_t *mask) {
   const double c = kC;
-  double R = sqrt(dot3(a, a));
-  if (R <= r_excl) {
+  // 1/R and R from one reciprocal square root (float64 division and square root are long
+  // sequences on this GPU's narrow float64 unit)
+  const double R2 = dot3(a, a);
+  const double iR = rsqrt(R2);
+  const double R = R2 * iR;
+  if (!(R > r_excl)) {
     *mask = 1;
     return;
   }
-  double iR = 1.0 / R;
   double n[3] = {a[0] * iR, a[1] * iR, a[2] * iR};
   double u[3] = {c * n[0] - v[0], c * n[1] - v[1], c * n[2] - v[2]};
   double Ru = c * R - dot3(a, v);
@@ -164,8 +167,9 @@ namespace pc {
 __device__ __forceinline__ void lw_E_f64(double q, const double a[3], const double v[3], const double acc[3],
                                          double E[3]) {
   const double c = kC;
-  double R = sqrt(dot3(a, a));
-  double iR = 1.0 / R;
+  const double R2 = dot3(a, a);
+  const double iR = rsqrt(R2);
+  const double R = R2 * iR;
   double u[3] = {c * a[0] * iR - v[0], c * a[1] * iR - v[1], c * a[2] * iR - v[2]};
   double Ru = c * R - dot3(a, v);
   double iRu = 1.0 / Ru;

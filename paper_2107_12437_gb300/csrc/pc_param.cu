@@ -65,46 +65,98 @@ __device__ __forceinline__ void param_state(int kind, const double *p, double t,
   }
 }
 
-// Root of g(t') = c (t - t') - |r - r(t')| (decreasing while the charge is slower than light):
-// a bracket [lo, t] with g(lo) >= 0 by doubling the look-back, then Newton steps with
-// g'(t') = -c + n.v, any step that leaves the bracket replaced by bisection.
-__device__ int param_retarded(int kind, const double *p, double t, const double r[3], double *tp) {
-  double rc[3], v[3], a[3];
+// Root of g(t') = c (t - t') - |r - r(t')| (decreasing while the charge is slower than light) by
+// Newton steps with g'(t') = -c + n.v inside a bracket [lo, hi] (g(lo) >= 0 >= g(hi)); a step that
+// leaves the bracket is replaced by the false-position point of the bracket (bisection if that
+// rounds onto an end).  First guess: the retarded time of a charge that keeps its velocity at t
+// (exact for uniform motion).  Converged when the Newton step is below 1e-15 (|t| + |t - t'|), a
+// few units in the last place (g itself is only known to rounding, and a tighter test would chase
+// that noise); that last step is then taken, so the root is exact to rounding.  Returns the root
+// and the state there.
+__device__ int param_retarded(int kind, const double *p, double t, const double r[3], double *tp, double rc[3],
+                              double v[3], double a[3]) {
+  constexpr double kTol = 1e-15;
   param_state(kind, p, t, rc, v, a);
-  double D[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
-  double span = sqrt(dot3(D, D)) / kC;
-  double lo = t - span, hi = t;
-  bool found = false;
-  for (int it = 0; it < 64; ++it) {
-    param_state(kind, p, lo, rc, v, a);
-    const double E[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
-    if (kC * (t - lo) - sqrt(dot3(E, E)) >= 0.0) {
-      found = true;
+  const double D[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
+  const double R0 = sqrt(dot3(D, D));
+  // c^2 tau^2 = |D + v tau|^2: (c^2 - v^2) tau^2 - 2 (D.v) tau - R0^2 = 0, the positive root in
+  // the form without cancellation
+  const double Dv = dot3(D, v), c2v2 = kC * kC - dot3(v, v);
+  double tau = R0 / kC;
+  if (c2v2 > 0.0) {
+    const double sq = sqrt(Dv * Dv + c2v2 * R0 * R0);
+    tau = Dv >= 0.0 ? (Dv + sq) / c2v2 : (R0 * R0) / (sq - Dv);
+  }
+  double x = t - tau;
+  param_state(kind, p, x, rc, v, a);
+  double E[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
+  double R = sqrt(dot3(E, E));
+  double g = kC * (t - x) - R;
+  double lo = x, hi = t, glo = g, ghi = -R0;
+  if (g < 0.0) {
+    hi = x;
+    ghi = g;
+    if (R > 0.0) {
+      const double step = g / (-kC + dot3(E, v) / R);
+      if (fabs(step) <= kTol * (fabs(t) + fabs(t - x))) {
+        // the guess is within one small Newton step of the root
+        *tp = x - step;
+        param_state(kind, p, *tp, rc, v, a);
+        return 0;
+      }
+    }
+    // the root lies further back: double the look-back until g >= 0
+    double span = fmax(2.0 * tau, R0 / kC) + 1e-30;
+    bool found = false;
+    for (int it = 0; it < 64; ++it) {
+      x = t - span;
+      param_state(kind, p, x, rc, v, a);
+      for (int i = 0; i < 3; ++i) E[i] = r[i] - rc[i];
+      R = sqrt(dot3(E, E));
+      g = kC * (t - x) - R;
+      if (g >= 0.0) {
+        found = true;
+        break;
+      }
+      hi = x;
+      ghi = g;
+      span *= 2.0;
+    }
+    if (!found) return PC_ERR_NOCONV;
+    lo = x;
+    glo = g;
+  }
+  for (int it = 0;; ++it) {
+    if (g >= 0.0) {
+      lo = x;
+      glo = g;
+    } else {
+      hi = x;
+      ghi = g;
+    }
+    if (!(R > 0.0)) break;  // the point sits on the charge at x (masked by the field sum)
+    const double step = g / (-kC + dot3(E, v) / R);
+    const double tol = kTol * (fabs(t) + fabs(t - x)) + 1e-300;
+    if (fabs(step) <= tol) {
+      x -= step;
+      param_state(kind, p, x, rc, v, a);
       break;
     }
-    span = 2.0 * span + 1e-30;
-    lo = t - span;
-  }
-  if (!found) return PC_ERR_NOCONV;
-  double x = lo;
-  for (int it = 0; it < 100; ++it) {
-    param_state(kind, p, x, rc, v, a);
-    const double E[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
-    const double R = sqrt(dot3(E, E));
-    const double g = kC * (t - x) - R;
-    if (g >= 0.0) lo = x;
-    else hi = x;
-    const double dg = -kC + dot3(E, v) / R;
-    double xn = x - g / dg;
-    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    const double tol = 2e-16 * (fabs(t) + fabs(t - x)) + 1e-300;
-    if (fabs(xn - x) <= tol || !(hi - lo > tol)) {
-      *tp = xn;
-      return 0;
+    if (!(hi - lo > tol)) break;
+    if (it == 100) return PC_ERR_NOCONV;
+    double xn = x - step;
+    if (!(xn > lo && xn < hi)) {
+      xn = lo + (hi - lo) * (glo / (glo - ghi));
+      if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
     }
     x = xn;
+    param_state(kind, p, x, rc, v, a);
+    for (int i = 0; i < 3; ++i) E[i] = r[i] - rc[i];
+    R = sqrt(dot3(E, E));
+    g = kC * (t - x) - R;
   }
-  return PC_ERR_NOCONV;
+  *tp = x;
+  return 0;
 }
 
 template <int KIND>
@@ -123,14 +175,12 @@ __global__ void __launch_bounds__(128) fields_param_kernel(const ParamLaunch L) 
       return;
     }
     const double *p = L.par + 12 * c;
-    double tp;
-    const int e = param_retarded(kd, p, t, r, &tp);
+    double tp, rc[3], v[3], a[3];
+    const int e = param_retarded(kd, p, t, r, &tp, rc, v, a);
     if (e) {
       set_status(L.status, e);
       return;
     }
-    double rc[3], v[3], a[3];
-    param_state(kd, p, tp, rc, v, a);
     const double av[3] = {r[0] - rc[0], r[1] - rc[1], r[2] - rc[2]};
     lw_add_f64<KIND>(__ldg(L.q + c), av, v, a, L.r_excl, E, B, &phi, A, &mask);
   }

@@ -130,6 +130,20 @@ def test_cloud_grid_path(ctx, prec):
 
 
 @pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+def test_grid_path_host_loop_matches_graph(ctx, prec, monkeypatch):
+    # the causal-block loop launched from the host (one drive and one RK4 launch per block) runs the
+    # same kernels in the same order as the device-side graph loop: identical results, also when
+    # the last block is shorter than the others
+    cfg = W.cfg5(N=96, n_steps=203, side=150e-9, min_spacing=5e-9, seed=7)
+    dp = pc.lo_config_to_device(cfg)
+    g = pc.pc_dipoles_run(ctx, dp, cfg.dt, cfg.n_steps, precision=prec, want_Ed=True)
+    monkeypatch.setenv("PYCHARGE_GB300_HOST_LOOP", "1")
+    h = pc.pc_dipoles_run(ctx, dp, cfg.dt, cfg.n_steps, precision=prec, want_Ed=True)
+    for k in ("d", "d_dot", "d_ddot", "energy", "Ed"):
+        assert torch.equal(g[k], h[k]), k
+
+
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
 def test_frozen_field_reading_and_unequal_masses(ctx, prec):
     # E_d held at its value at t over each step (the alternative reading of Algorithm 1) and
     # dipoles with unequal charge masses, against the oracle with the same reading

@@ -173,12 +173,18 @@ def test_cfg2_plane_tiles(ctx, prec):
     compare(out, ref, prec)
 
 
-def test_cfg2_full_size_sampled(ctx):
-    # the launch the benchmark times: 2048 x 2048 plane, 16 frames, mixed precision, float32 outputs
+@pytest.mark.parametrize("tiling", [(16, 16), (32, 16)])
+def test_cfg2_full_size_sampled(ctx, tiling):
+    # the launch the benchmark times: 2048 x 2048 plane, 16 frames, mixed precision, float32 outputs,
+    # with one and with two points per thread
     dp, g, z, times = W.cfg2()
     step = g[1] - g[0]
-    out = pc.pc_fields_plane(ctx, dipoles=pc.dipoles_to_device(dp), origin=(0.0, 0.0, z), eu=(step, 0, 0),
-                             ev=(0, step, 0), nu=2048, nv=2048, times=list(times), precision=pc.PC_MIXED)
+    pc.pc_set_plane_tiling(ctx, *tiling)
+    try:
+        out = pc.pc_fields_plane(ctx, dipoles=pc.dipoles_to_device(dp), origin=(0.0, 0.0, z), eu=(step, 0, 0),
+                                 ev=(0, step, 0), nu=2048, nv=2048, times=list(times), precision=pc.PC_MIXED)
+    finally:
+        pc.pc_set_plane_tiling(ctx, 16, 16)
     for k in ("E", "B", "phi", "A"):
         assert torch.isfinite(out[k]).all()
     rng = np.random.default_rng(99)
@@ -287,11 +293,63 @@ def test_autotuned_tile_shape_keeps_parity(ctx):
     kw = dict(dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=96, nv=512,
               times=[float(times[3])])
     ref = pc.pc_fields_plane(ctx, precision=pc.PC_MIXED, **kw)["E"].double()
-    rows = pc.pc_autotune_plane(ctx, **kw)
-    assert rows in (8, 16, 32)
+    shape = pc.pc_autotune_plane(ctx, **kw)
+    assert shape in ((8, 32), (16, 16), (32, 8), (16, 32), (32, 16), (64, 8))
     tuned = pc.pc_fields_plane(ctx, precision=pc.PC_MIXED, **kw)["E"].double()
+    pc.pc_set_plane_tiling(ctx, 16, 16)
     scale = torch.linalg.norm(ref, dim=-1).max()
     assert float(torch.linalg.norm(tuned - ref, dim=-1).max() / scale) < 1e-5
+
+
+@pytest.mark.parametrize("tiling", [(16, 16), (8, 32), (32, 16), (16, 32), (64, 8)])
+@pytest.mark.parametrize("kind", [pc.PC_TOTAL, pc.PC_COULOMB, pc.PC_RADIATION])
+def test_cfg2_plane_tilings(ctx, tiling, kind):
+    # every tile shape of the mixed plane kernels (256 points with one per thread, 512 with two per
+    # thread) on a contiguous 70 x 45 block with ragged edges in both directions (threads with
+    # both, one or none of their points inside the grid), unequal charge masses, one frame in the
+    # run and one at t = 1 fs where most retarded times fall before the first sample (the static
+    # pre-history of the slow path), against the oracle
+    dp, g, z, times = W.cfg2()
+    rng = np.random.default_rng(29)
+    dp.m1 = W.M_E * rng.uniform(0.5, 3.0, size=dp.N)
+    u0, v0, nu, nv = 1000, 610, 70, 45
+    pts = W.plane_grid(g[u0:u0 + nu], g[v0:v0 + nv], z)
+    tsel = np.array([1e-15, times[6]])
+    ref = oracle.fields(pts, tsel, dipoles=dp, kind=kind)
+    assert ref["status"] == oracle.OK
+    step = g[1] - g[0]
+    pc.pc_set_plane_tiling(ctx, *tiling)
+    try:
+        out = pc.pc_fields_plane(ctx, dipoles=pc.dipoles_to_device(dp), origin=(g[u0], g[v0], z), eu=(step, 0, 0),
+                                 ev=(0, step, 0), nu=nu, nv=nv, times=list(tsel), kind=kind, precision=pc.PC_MIXED)
+    finally:
+        pc.pc_set_plane_tiling(ctx, 16, 16)
+    compare(out, ref, pc.PC_MIXED, ("E", "B", "phi", "A") if kind == pc.PC_TOTAL else ("E", "B"))
+
+
+def test_two_point_tiles_near_sources_and_errors(ctx):
+    # dipoles placed within a few c dt of grid points and of the plane (near pairs, cancellation,
+    # points on the slow path next to points on the fast one) with two points per thread; and the
+    # tiling setter's argument checks
+    dp, g, z, times = W.cfg2()
+    step = g[1] - g[0]
+    u0, v0, nu, nv = 300, 900, 33, 29
+    dp.origin[0] = [g[u0 + 5], g[v0 + 7], z + 0.4e-9]
+    dp.origin[1] = [g[u0 + 6] + 0.3 * step, g[v0 + 20], z - 2e-9]
+    dp.origin[2] = [g[u0 + 30], g[v0 + 3] + 0.5 * step, z + 7e-9]
+    pts = W.plane_grid(g[u0:u0 + nu], g[v0:v0 + nv], z)
+    ref = oracle.fields(pts, times[[4]], dipoles=dp)
+    assert ref["status"] == oracle.OK
+    pc.pc_set_plane_tiling(ctx, 32, 16)
+    try:
+        out = pc.pc_fields_plane(ctx, dipoles=pc.dipoles_to_device(dp), origin=(g[u0], g[v0], z), eu=(step, 0, 0),
+                                 ev=(0, step, 0), nu=nu, nv=nv, times=[times[4]], precision=pc.PC_MIXED)
+    finally:
+        pc.pc_set_plane_tiling(ctx, 16, 16)
+    compare(out, ref, pc.PC_MIXED)
+    for bad in ((16, 17), (3, 64), (0, 16), (1, 512), (24, 16)):
+        with pytest.raises(pc.PcError):
+            pc.pc_set_plane_tiling(ctx, *bad)
 
 
 @pytest.mark.parametrize("kind", [pc.PC_COULOMB, pc.PC_RADIATION])
