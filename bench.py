@@ -319,7 +319,7 @@ def main():
                            times=list(times), precision=pc.PC_MIXED, out=out)
 
     # plan: the tile shape of the mixed plane kernel, tuned on this workload before the timed steps
-    tile_rows, tile_cols = pc.pc_autotune_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0),
+    tile_rows, tile_cols, tile_stage = pc.pc_autotune_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0),
                                                 ev=(0, step, 0), nu=NU, nv=NV, times=list(times), out=out)
     for _ in range(args.warmup):
         step_fn()
@@ -395,7 +395,8 @@ def main():
                                "w0 = 2 pi 200 THz, origins in a 1 um cube, seed 2107), 2048x2048 plane at "
                                "z = 0.5 um, 16 frames t = 10 fs + f 5/16 fs, mixed precision, float32 outputs",
                    "pairs_per_step": pairs_per_step, "parallelism": f"replicas x{world}",
-                   "tile": f"{tile_rows} x {tile_cols} points, {tile_rows * tile_cols // 256} per thread (autotuned)",
+                   "tile": f"{tile_rows} x {tile_cols} points, {tile_rows * tile_cols // 256} per thread, "
+                           f"{tile_stage} sources per shared-memory stage (autotuned)",
                    "l2": "flushed between steps (256 MB write); outputs 2.7 GB > L2"},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),

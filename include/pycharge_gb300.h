@@ -155,30 +155,35 @@ pc_status pc_fields_param(pc_ctx *ctx, const pc_param_charges *ch, const double 
                           const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,
                           void *stream);
 
+/* Tile shape of the PC_MIXED plane evaluation: tile_rows x tile_cols points (256 with one point
+ * per thread, or 512 with two per thread: each thread's points in rows r and r + tile_rows/2,
+ * evaluated together in the lanes of packed float32 registers; used for grids of dipoles alone,
+ * other calls take the one-point tile of the same columns), tile_cols a power of two up to 256;
+ * sources_per_stage = 32 or 64 sources staged in shared memory at a time. */
+typedef struct {
+  int32_t tile_rows, tile_cols, sources_per_stage;
+} pc_plane_tiling;
+
 /*
  * pc_autotune_plane -- picks the tile shape of the PC_MIXED plane evaluation for this workload and
- * keeps it in the context for later pc_fields_plane / pc_fields_plane_to_host calls: tiles of 256
- * points as 8 x 32, 16 x 16 (the default) or 32 x 8 rows x columns with one point per thread, and,
- * for grids of dipoles alone, tiles of 512 points as 16 x 32, 32 x 16 or 64 x 8 with two points per
- * thread (each thread's two points in rows r and r + rows/2 of the tile, evaluated together in the
- * lanes of packed float32 registers).  Each shape runs once to warm up and once timed on the given
- * arguments (those of pc_fields_plane with PC_MIXED; `out` receives the fields of the last run).
- * Writes the chosen tile's rows and columns to *tile_rows, *tile_cols (either may be NULL).  The
- * results of every shape agree to float32 rounding (the tile anchor enters the delays).
+ * keeps it in the context for later pc_fields_plane / pc_fields_plane_to_host calls: one-point tiles
+ * of 8 x 32, 16 x 16 (the default) or 32 x 8 rows x columns, two-point tiles of 16 x 32, 32 x 16 or
+ * 64 x 8 (grids of dipoles alone), each with 64 (the default) and with 32 sources per stage.  Each
+ * shape runs once to warm up and once timed on the given arguments (those of pc_fields_plane with
+ * PC_MIXED; `out` receives the fields of the last run).  Writes the chosen shape to *chosen (or
+ * NULL).  The results of every shape agree to float32 rounding (the tile anchor enters the delays).
  * Errors: those of pc_fields_plane.
  */
 pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const pc_plane *grid,
                             const double *times, int32_t T, int32_t kind, double r_excl, const pc_field_out *out,
-                            int32_t *tile_rows, int32_t *tile_cols, void *stream);
+                            pc_plane_tiling *chosen, void *stream);
 
 /*
  * pc_set_plane_tiling -- sets the PC_MIXED plane tile shape directly (what pc_autotune_plane
- * chooses): tile_rows x tile_cols = 256 points (one per thread) or 512 (two per thread; used for
- * plane grids of dipoles alone, other calls take the one-point tile of the same columns),
- * tile_cols a power of two up to 256.
- * Errors: PC_ERR_ARG for any other shape.
+ * chooses).
+ * Errors: PC_ERR_ARG for a shape outside those described at pc_plane_tiling.
  */
-pc_status pc_set_plane_tiling(pc_ctx *ctx, int32_t tile_rows, int32_t tile_cols);
+pc_status pc_set_plane_tiling(pc_ctx *ctx, const pc_plane_tiling *tiling);
 
 /*
  * pc_fields_to_host / pc_fields_plane_to_host -- pc_fields / pc_fields_plane with the outputs

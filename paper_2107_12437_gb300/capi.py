@@ -73,6 +73,10 @@ class PcDipoleMotion(ctypes.Structure):
     _fields_ = [("pos", _vp), ("vel", _vp), ("acc", _vp)]
 
 
+class PcPlaneTiling(ctypes.Structure):
+    _fields_ = [("tile_rows", _i32), ("tile_cols", _i32), ("sources_per_stage", _i32)]
+
+
 class PcDipoleGrads(ctypes.Structure):
     _fields_ = [("origin", _vp), ("omega0", _vp), ("d0", _vp)]
 
@@ -97,9 +101,8 @@ SIGNATURES = {
                                                ctypes.POINTER(PcFieldOut), _vp]),
     "pc_autotune_plane": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources),
                                          ctypes.POINTER(PcPlane), ctypes.POINTER(_f64), _i32, _i32, _f64,
-                                         ctypes.POINTER(PcFieldOut), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
-                                         _vp]),
-    "pc_set_plane_tiling": (ctypes.c_int, [_vp, _i32, _i32]),
+                                         ctypes.POINTER(PcFieldOut), ctypes.POINTER(PcPlaneTiling), _vp]),
+    "pc_set_plane_tiling": (ctypes.c_int, [_vp, ctypes.POINTER(PcPlaneTiling)]),
     "pc_fields_param": (ctypes.c_int, [_vp, ctypes.POINTER(PcParamCharges), _vp, _i64, ctypes.POINTER(_f64), _i32,
                                        _i32, _f64, ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run_moving": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), ctypes.POINTER(PcDipoleMotion), _f64,
@@ -293,24 +296,26 @@ def pc_fields_plane(ctx, charges=None, dipoles=None, origin=(0, 0, 0), eu=(1, 0,
 def pc_autotune_plane(ctx, charges=None, dipoles=None, origin=(0, 0, 0), eu=(1, 0, 0), ev=(0, 1, 0), nu=1, nv=1,
                       times=(0.0,), kind=PC_TOTAL, r_excl=0.0, out=None, stream=None, device="cuda"):
     """pc_autotune_plane: times the tile shapes on this mixed plane workload, keeps the fastest in
-    the context and returns its (rows, columns)."""
+    the context and returns it as (rows, columns, sources per stage)."""
     T = len(times)
     o = alloc_field_out(nu * nv, T, PC_MIXED, device) if out is None else out
     pl = PcPlane(origin=(_f64 * 3)(*origin), eu=(_f64 * 3)(*eu), ev=(_f64 * 3)(*ev), nu=nu, nv=nv)
     tarr = (_f64 * T)(*[float(t) for t in times])
     chs = _charges_struct(charges)
     dps = _dipoles_struct(dipoles)
-    rows, cols = _i32(0), _i32(0)
+    t = PcPlaneTiling()
     st = ctx.lib.pc_autotune_plane(ctx.handle, ctypes.byref(chs) if chs else None, ctypes.byref(dps) if dps else None,
                                    ctypes.byref(pl), tarr, T, kind, float(r_excl), ctypes.byref(_out_struct(o)),
-                                   ctypes.byref(rows), ctypes.byref(cols), _stream(stream))
+                                   ctypes.byref(t), _stream(stream))
     _check(st, "pc_autotune_plane")
-    return rows.value, cols.value
+    return t.tile_rows, t.tile_cols, t.sources_per_stage
 
 
-def pc_set_plane_tiling(ctx, tile_rows, tile_cols):
-    """pc_set_plane_tiling: the mixed plane tile shape (256 points, or 512 with two per thread)."""
-    _check(ctx.lib.pc_set_plane_tiling(ctx.handle, int(tile_rows), int(tile_cols)), "pc_set_plane_tiling")
+def pc_set_plane_tiling(ctx, tile_rows, tile_cols, sources_per_stage=64):
+    """pc_set_plane_tiling: the mixed plane tile shape (256 points, or 512 with two per thread) and
+    the sources per shared-memory stage (32 or 64)."""
+    t = PcPlaneTiling(tile_rows=int(tile_rows), tile_cols=int(tile_cols), sources_per_stage=int(sources_per_stage))
+    _check(ctx.lib.pc_set_plane_tiling(ctx.handle, ctypes.byref(t)), "pc_set_plane_tiling")
 
 
 def alloc_host_field_out(P, T, precision, which=("E", "B", "phi", "A", "mask")):

@@ -17,6 +17,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "pc_internal.cuh"
 #include "pc_lw_f32.cuh"
@@ -27,7 +28,17 @@ namespace pc {
 
 constexpr int kMaxT = 32;        // times per launch (the host splits longer lists)
 constexpr int kMixThreads = 256; // points per CTA in the mixed path
-constexpr int kChunk = 64;       // sources staged in shared memory at a time
+constexpr int kChunk = 64;       // sources staged in shared memory at a time (the largest stage)
+// per-chunk bit mask of the pairs that left the fast path: 32 or 64 sources per stage
+template <int CH>
+struct SlowMask {
+  using T = typename std::conditional<(CH <= 32), unsigned, unsigned long long>::type;
+  static __device__ __forceinline__ T bit(int j) { return (T)1 << j; }
+  static __device__ __forceinline__ int first(T m) {
+    if constexpr (CH <= 32) return __ffs((int)m) - 1;
+    else return __ffsll((long long)m) - 1;
+  }
+};
 // a dipole closer than kNearL c*dt to a point whose near field there cancels by more than kCancel
 // (dipole_cancellation) is summed in float64 instead
 constexpr float kNearL = 400.f;
@@ -466,17 +477,17 @@ __device__ __forceinline__ float kahan_get(const KahanArr &k, int tid, int i) {
   return hi[i] ? sv.y - cv.y : sv.x - cv.x;
 }
 
-template <int KIND, bool LIST>
+template <int KIND, bool LIST, int CH>
 __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
   __shared__ double s_anchor[3];
   __shared__ float s_anc_hi[3], s_anc_lo[3];  // the anchor / (c dt) of the dipoles as float-float
   __shared__ KahanArr s_kahan;
-  __shared__ float4 s_geo[kChunk];   // rho_a (x,y,z), |rho_a|
-  __shared__ float4 s_geo_lo[kChunk]; // low parts of rho_a and |rho_a| (list mode)
-  __shared__ float4 s_ax[kChunk];    // axis (x,y,z), q/e
-  __shared__ float4 s_mix[kChunk];   // m2/(m1+m2), m1/(m1+m2), fraction and integer part of the
+  __shared__ float4 s_geo[CH];   // rho_a (x,y,z), |rho_a|
+  __shared__ float4 s_geo_lo[CH]; // low parts of rho_a and |rho_a| (list mode)
+  __shared__ float4 s_ax[CH];    // axis (x,y,z), q/e
+  __shared__ float4 s_mix[CH];   // m2/(m1+m2), m1/(m1+m2), fraction and integer part of the
                                      // retarded sample of the anchor (integer as bits)
-  __shared__ const float4 *s_hist[kChunk];
+  __shared__ const float4 *s_hist[CH];
 
   const int tid = threadIdx.x;
   const int f = blockIdx.y;
@@ -554,8 +565,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     const float rex_fast = rex + 1.5f;
     const int Sd32 = (int)s.Sd;
     const unsigned jlim = Sd32 > 3 ? (unsigned)(Sd32 - 3) : 0u;  // fast segments 1 <= j <= S-3
-    for (int base = 0; base < s.N; base += kChunk) {
-      const int nch = min(kChunk, s.N - base);
+    for (int base = 0; base < s.N; base += CH) {
+      const int nch = min(CH, s.N - base);
       __syncthreads();
       if (tid < nch) {
         // the tile anchor's distance to the source in float64 (the integer sample index and a
@@ -583,7 +594,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       float2 P[5];
 #pragma unroll
       for (int i = 0; i < 5; ++i) P[i] = make_float2(0.f, 0.f);
-      unsigned long long slow_mask = 0ull;
+      typename SlowMask<CH>::T slow_mask = 0;
       for (int g16 = 0; g16 < nch; g16 += 16) {
       // groups of sixteen sources summed in float32, the group sums compensated
       const int gend = min(nch, g16 + 16);
@@ -642,7 +653,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
             dipole_cancellation<float>(rn, mu.x, mu.y, X.x, V.x, Ac.x, X.y, V.y, Ac.y) > kCancel)
           fast = false;
         if (!fast) {
-          slow_mask |= 1ull << jj;
+          slow_mask |= SlowMask<CH>::bit(jj);
           continue;
         }
         dipole_pair_fast<KIND>(make_float2(rx, ry), rz, rn, make_float2(ax.x, ax.y), ax.z, rp, mu.x, mu.y, ax.w, X, V,
@@ -654,8 +665,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       }
       // the pairs of this chunk that left the fast path
       while (slow_mask && !err) {
-        const int jj = __ffsll((long long)slow_mask) - 1;
-        slow_mask &= slow_mask - 1ull;
+        const int jj = SlowMask<CH>::first(slow_mask);
+        slow_mask &= slow_mask - 1;
         // the out-of-line call gets arrays of its own: passing the address of part or mask would
         // keep them in local memory throughout the source loop
         float sp[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -706,8 +717,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     const double u = L.ufc[f];
     const float rex = (float)(L.r_excl * iLc);
     const float sE = L.sE, sP = L.sP;
-    for (int base = 0; base < s.M; base += kChunk) {
-      const int nch = min(kChunk, s.M - base);
+    for (int base = 0; base < s.M; base += CH) {
+      const int nch = min(CH, s.M - base);
       __syncthreads();
       if (tid < nch) {
         const int c = base + tid;
@@ -889,16 +900,16 @@ __device__ __forceinline__ void kahan2_add(KahanArr2 &k, int tid, const V2 *P) {
 }
 
 // the slow pairs of one point (lane 0 = A, 1 = B) of the chunk, into that point's Kahan lane
-template <int KIND>
-__device__ __forceinline__ int slow_pairs2(const Launch &L, int f, int base, unsigned long long bits, int lane,
+template <int KIND, int CH>
+__device__ __forceinline__ int slow_pairs2(const Launch &L, int f, int base, typename SlowMask<CH>::T bits, int lane,
                                            float drx, float dry, float drz, float dr2, int64_t p, int Sd32,
                                            float rex, const float4 *s_geo, const float4 *s_ax, const float4 *s_mix,
                                            const float4 *const *s_hist, KahanArr2 &kh, int tid, uint8_t &mask) {
   const Sources &s = L.src;
   int err = 0;
   while (bits && !err) {
-    const int jj = __ffsll((long long)bits) - 1;
-    bits &= bits - 1ull;
+    const int jj = SlowMask<CH>::first(bits);
+    bits &= bits - 1;
     float sp[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     uint8_t smask = 0;
     const float4 g = s_geo[jj];
@@ -923,15 +934,15 @@ __device__ __forceinline__ int slow_pairs2(const Launch &L, int f, int base, uns
   return err;
 }
 
-template <int KIND>
+template <int KIND, int CH>
 __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Launch L, int64_t tiles_v) {
   __shared__ float s_anc_hi[3], s_anc_lo[3];  // the tile anchor / (c dt) as float-float
   __shared__ KahanArr2 s_kahan;
-  __shared__ float4 s_geo[kChunk];  // rho_a (x,y,z), |rho_a|
-  __shared__ float4 s_ax[kChunk];   // axis (x,y,z), q/e
-  __shared__ float4 s_mix[kChunk];  // m2/(m1+m2), m1/(m1+m2), fraction and integer part (bits) of the
+  __shared__ float4 s_geo[CH];  // rho_a (x,y,z), |rho_a|
+  __shared__ float4 s_ax[CH];   // axis (x,y,z), q/e
+  __shared__ float4 s_mix[CH];  // m2/(m1+m2), m1/(m1+m2), fraction and integer part (bits) of the
                                     // retarded sample of the anchor
-  __shared__ const float4 *s_hist[kChunk];
+  __shared__ const float4 *s_hist[CH];
 
   const int tid = threadIdx.x;
   const int f = blockIdx.y;
@@ -969,8 +980,8 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Lau
   const int Sd32 = (int)s.Sd;
   const unsigned jlim = Sd32 > 3 ? (unsigned)(Sd32 - 3) : 0u;  // fast segments 1 <= j <= S-3
   const bool any = actA || actB;
-  for (int base = 0; base < s.N; base += kChunk) {
-    const int nch = min(kChunk, s.N - base);
+  for (int base = 0; base < s.N; base += CH) {
+    const int nch = min(CH, s.N - base);
     __syncthreads();
     if (tid < nch) {
       // the anchor's distance to the source and the centre's retarded sample in float-float
@@ -994,7 +1005,7 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Lau
     V2 P[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) P[i] = V2(0.f);
-    unsigned long long slowA = 0ull, slowB = 0ull;
+    typename SlowMask<CH>::T slowA = 0, slowB = 0;
     for (int g16 = 0; g16 < nch; g16 += 16) {
       // groups of sixteen sources summed in float32, the group sums compensated
       const int gend = min(nch, g16 + 16);
@@ -1014,8 +1025,8 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Lau
         bool fA = actA && (unsigned)(jA - 1) < jlim && rn.v.x > rex_fast;
         bool fB = actB && (unsigned)(jB - 1) < jlim && rn.v.y > rex_fast;
         if (!(fA && fB)) {
-          if (actA && !fA) slowA |= 1ull << jj;
-          if (actB && !fB) slowB |= 1ull << jj;
+          if (actA && !fA) slowA |= SlowMask<CH>::bit(jj);
+          if (actB && !fB) slowB |= SlowMask<CH>::bit(jj);
           if (!fA && !fB) continue;
           // the point off the fast path takes the other point's geometry: finite values whose
           // results are dropped
@@ -1060,8 +1071,8 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Lau
             dipole_cancellation<float>(rn.v.y, mx.x, mx.y, cp.X.v.y, cp.V.v.y, cp.Ac.v.y, cm.X.v.y, cm.V.v.y,
                                        cm.Ac.v.y) > kCancel)
           fB = false;
-        if (actA && !fA) slowA |= 1ull << jj;
-        if (actB && !fB) slowB |= 1ull << jj;
+        if (actA && !fA) slowA |= SlowMask<CH>::bit(jj);
+        if (actB && !fB) slowB |= SlowMask<CH>::bit(jj);
         if (!fA && !fB) continue;
         dipole2_fast<KIND>(rx, ry, rz, rn, ax.x, ax.y, ax.z, rp, mx.x, mx.y, ax.w, cp, cm, fA, fB, P);
       }
@@ -1072,10 +1083,10 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Lau
     // the pairs of this chunk that left the fast path, per point
     const V2 d2 = dr2;
     if (slowA)
-      err = slow_pairs2<KIND>(L, f, base, slowA, 0, drx.v.x, dry.v.x, drz.v.x, d2.v.x, pA, Sd32, rex, s_geo, s_ax,
+      err = slow_pairs2<KIND, CH>(L, f, base, slowA, 0, drx.v.x, dry.v.x, drz.v.x, d2.v.x, pA, Sd32, rex, s_geo, s_ax,
                               s_mix, s_hist, s_kahan, tid, maskA);
     if (slowB && !err)
-      err = slow_pairs2<KIND>(L, f, base, slowB, 1, drx.v.y, dry.v.y, drz.v.y, d2.v.y, pB, Sd32, rex, s_geo, s_ax,
+      err = slow_pairs2<KIND, CH>(L, f, base, slowB, 1, drx.v.y, dry.v.y, drz.v.y, d2.v.y, pB, Sd32, rex, s_geo, s_ax,
                               s_mix, s_hist, s_kahan, tid, maskB);
   }
   if (!any) return;
@@ -1120,6 +1131,26 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Lau
 // host side
 // ================================================================================================
 static bool finite3(const double *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+// mixed-path launches: plane tiles with CH sources per shared-memory stage, one or two points per
+// thread; point lists with the full stage
+template <int CH>
+static void launch_mixed_plane(const Launch &L, dim3 grid, int64_t tiles_v, bool two, int kind, cudaStream_t st) {
+  if (two) {
+    if (kind == PC_TOTAL) fields_mixed2_kernel<PC_TOTAL, CH><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+    else if (kind == PC_COULOMB) fields_mixed2_kernel<PC_COULOMB, CH><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+    else fields_mixed2_kernel<PC_RADIATION, CH><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+  } else {
+    if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, false, CH><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+    else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, false, CH><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+    else fields_mixed_kernel<PC_RADIATION, false, CH><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
+  }
+}
+static void launch_mixed_list(const Launch &L, dim3 grid, int kind, cudaStream_t st) {
+  if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, true, kChunk><<<grid, kMixThreads, 0, st>>>(L, 1);
+  else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, true, kChunk><<<grid, kMixThreads, 0, st>>>(L, 1);
+  else fields_mixed_kernel<PC_RADIATION, true, kChunk><<<grid, kMixThreads, 0, st>>>(L, 1);
+}
 
 // Host outputs: frames are computed in chunks into two device buffers that alternate, and each
 // chunk is copied to the host on a second stream while the next chunk computes.
@@ -1296,19 +1327,9 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
         tiles = tu * tiles_v;
       }
       dim3 grid((unsigned)tiles, (unsigned)L.T);
-      if (two) {
-        if (kind == PC_TOTAL) fields_mixed2_kernel<PC_TOTAL><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-        else if (kind == PC_COULOMB) fields_mixed2_kernel<PC_COULOMB><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-        else fields_mixed2_kernel<PC_RADIATION><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-      } else if (list) {
-        if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-        else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-        else fields_mixed_kernel<PC_RADIATION, true><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-      } else {
-        if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, false><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-        else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, false><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-        else fields_mixed_kernel<PC_RADIATION, false><<<grid, kMixThreads, 0, st>>>(L, tiles_v);
-      }
+      if (list) launch_mixed_list(L, grid, kind, st);
+      else if (ctx->src_chunk == 32) launch_mixed_plane<32>(L, grid, tiles_v, two, kind, st);
+      else launch_mixed_plane<kChunk>(L, grid, tiles_v, two, kind, st);
     }
     if (hp.on) {
       // copy the chunk to the host on the copy stream once its kernel is done
@@ -1488,9 +1509,7 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   for (int32_t f0 = 0; f0 < T; f0 += kMaxT) {
     set_frames(L, times, f0, min(kMaxT, T - f0));
     dim3 grid((unsigned)tiles, (unsigned)L.T);
-    if (kind == PC_TOTAL) fields_mixed_kernel<PC_TOTAL, true><<<grid, kMixThreads, 0, st>>>(L, 1);
-    else if (kind == PC_COULOMB) fields_mixed_kernel<PC_COULOMB, true><<<grid, kMixThreads, 0, st>>>(L, 1);
-    else fields_mixed_kernel<PC_RADIATION, true><<<grid, kMixThreads, 0, st>>>(L, 1);
+    launch_mixed_list(L, grid, kind, st);
   }
   if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
   int h = 0;  // pageable host word: the copy completes before cudaMemcpyAsync returns to the stream order
@@ -1506,37 +1525,43 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
 // caller's workload once to warm up and once timed; the fastest is kept in the context for the
 // plane calls that follow.
 // ================================================================================================
-extern "C" pc_status pc_set_plane_tiling(pc_ctx *ctx, int32_t tile_rows, int32_t tile_cols) {
-  if (!ctx || tile_rows < 1 || tile_cols < 1 || tile_cols > pc::kMixThreads) return PC_ERR_ARG;
-  if (tile_cols & (tile_cols - 1)) return PC_ERR_ARG;  // a power of two
-  const int64_t pts = (int64_t)tile_rows * tile_cols;
+extern "C" pc_status pc_set_plane_tiling(pc_ctx *ctx, const pc_plane_tiling *t) {
+  if (!ctx || !t) return PC_ERR_ARG;
+  const int32_t rows = t->tile_rows, cols = t->tile_cols;
+  if (rows < 1 || cols < 1 || cols > pc::kMixThreads || (cols & (cols - 1))) return PC_ERR_ARG;
+  const int64_t pts = (int64_t)rows * cols;
   if (pts != pc::kMixThreads && pts != 2 * pc::kMixThreads) return PC_ERR_ARG;
+  if (t->sources_per_stage != 32 && t->sources_per_stage != pc::kChunk) return PC_ERR_ARG;
   int sh = 0;
-  while ((1 << sh) < tile_cols) ++sh;
+  while ((1 << sh) < cols) ++sh;
   ctx->tile_shift = sh;
   ctx->pts_per_thread = pts == pc::kMixThreads ? 1 : 2;
+  ctx->src_chunk = t->sources_per_stage;
   return PC_OK;
 }
 
 extern "C" pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp,
                                        const pc_plane *grid, const double *times, int32_t T, int32_t kind,
-                                       double r_excl, const pc_field_out *out, int32_t *tile_rows,
-                                       int32_t *tile_cols, void *stream) {
+                                       double r_excl, const pc_field_out *out, pc_plane_tiling *chosen,
+                                       void *stream) {
   if (!ctx || !grid || !out) return PC_ERR_ARG;
   pc::DeviceGuard g(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   // (points per thread, log2 columns): 8 x 32, 16 x 16, 32 x 8 tiles of one point per thread, and
-  // 16 x 32, 32 x 16, 64 x 8 of two (plane grids of dipoles alone)
+  // 16 x 32, 32 x 16, 64 x 8 of two (plane grids of dipoles alone); each with 64 and with 32
+  // sources per shared-memory stage
   const int cand[6][2] = {{1, 5}, {1, 4}, {1, 3}, {2, 5}, {2, 4}, {2, 3}};
-  const int ncand = (ch && ch->M > 0) ? 3 : 6;
+  const int nshape = (ch && ch->M > 0) ? 3 : 6;
+  const int chunks[2] = {pc::kChunk, 32};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PC_ERR_CUDA;
   float best = 1e30f;
   int best_c = -1;
   pc_status rs = PC_OK;
-  for (int c = 0; c < ncand && rs == PC_OK; ++c) {
-    ctx->pts_per_thread = cand[c][0];
-    ctx->tile_shift = cand[c][1];
+  for (int c = 0; c < 2 * nshape && rs == PC_OK; ++c) {
+    ctx->pts_per_thread = cand[c % nshape][0];
+    ctx->tile_shift = cand[c % nshape][1];
+    ctx->src_chunk = chunks[c / nshape];
     rs = pc_fields_plane(ctx, ch, dp, grid, times, T, kind, PC_MIXED, r_excl, out, stream);
     if (rs != PC_OK) break;
     cudaEventRecord(e0, st);
@@ -1553,9 +1578,13 @@ extern "C" pc_status pc_autotune_plane(pc_ctx *ctx, const pc_charges *ch, const 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best_c < 0) best_c = 1;
-  ctx->pts_per_thread = cand[best_c][0];
-  ctx->tile_shift = cand[best_c][1];
-  if (tile_rows) *tile_rows = ctx->pts_per_thread * (pc::kMixThreads >> ctx->tile_shift);
-  if (tile_cols) *tile_cols = 1 << ctx->tile_shift;
+  ctx->pts_per_thread = cand[best_c % nshape][0];
+  ctx->tile_shift = cand[best_c % nshape][1];
+  ctx->src_chunk = chunks[best_c / nshape];
+  if (chosen) {
+    chosen->tile_rows = ctx->pts_per_thread * (pc::kMixThreads >> ctx->tile_shift);
+    chosen->tile_cols = 1 << ctx->tile_shift;
+    chosen->sources_per_stage = ctx->src_chunk;
+  }
   return rs;
 }
