@@ -11,8 +11,9 @@ namespace pc {
 __device__ __forceinline__ void lw_E_f64_rev(double q, const double a[3], const double v[3], const double acc[3],
                                              const double Eb[3], double ab[3], double vb[3], double accb[3]) {
   const double c = kC;
-  const double R = sqrt(dot3(a, a));
-  const double iR = 1.0 / R;
+  const double R2 = dot3(a, a);
+  const double iR = rsqrt(R2);  // 1/R and R from one reciprocal square root
+  const double R = R2 * iR;
   const double u[3] = {c * a[0] * iR - v[0], c * a[1] * iR - v[1], c * a[2] * iR - v[2]};
   const double Ru = c * R - dot3(a, v);
   const double iRu = 1.0 / Ru;
@@ -65,8 +66,9 @@ __device__ inline void lw_full_f64_rev(double q, const double a[3], const double
                                        const double *Eb, const double *Bb, double phib, const double *Ab, double ab[3],
                                        double vb[3], double accb[3]) {
   const double c = kC;
-  const double R = sqrt(dot3(a, a));
-  const double iR = 1.0 / R;
+  const double R2 = dot3(a, a);
+  const double iR = rsqrt(R2);  // 1/R and R from one reciprocal square root
+  const double R = R2 * iR;
   const double n[3] = {a[0] * iR, a[1] * iR, a[2] * iR};
   const double u[3] = {c * n[0] - v[0], c * n[1] - v[1], c * n[2] - v[2]};
   const double Ru = c * R - dot3(a, v);

@@ -1228,7 +1228,7 @@ static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, di
 // Forward run (Algorithm 1); Ehalf (or null) receives E_d at the half steps for the adjoint.
 static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                           const pc_run_out *out, double *Ehalf, cudaStream_t st, int *k_out = nullptr,
-                          const pc_dipole_motion *motion = nullptr) {
+                          const pc_dipole_motion *motion = nullptr, const int2 **delay_out = nullptr) {
   if (!ctx || !dp || !opts || !out) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0) || n_steps < 0) return PC_ERR_ARG;
   if (!dp->origin || !dp->axis || !dp->q || !dp->m1 || !dp->m2 || !dp->omega0 || !dp->d0) return PC_ERR_ARG;
@@ -1290,6 +1290,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.delay = (int2 *)(scr + es_bytes + h_bytes + f_bytes);
   a.pgeo = mixed ? (float4 *)(scr + geo_off) : nullptr;
   a.rstat = (unsigned long long *)(scr + rs_off);
+  if (delay_out) *delay_out = a.delay;  // valid until the context's next run
   a.kblock = (int *)(scr + es_bytes + h_bytes + f_bytes + dl_bytes);
   a.Ehalf = Ehalf;
   a.Epart = nullptr;
@@ -1431,6 +1432,8 @@ struct AdjArgs {
   double *Ebar;        // [B][N][2*kMaxBlock+1] adjoints of the block's stage fields
   double *w0bar;       // [B][N]
   double *tau;         // [B][N][2] smallest and largest delay (steps) from a source to its receivers
+  double *wts;         // [B][N][2] offsets of the charges per unit moment, m2/((m1+m2) q), -m1/((m1+m2) q)
+  const int2 *delay;   // [B][N][N] centre delays of the forward run (first guesses of the solves)
   double *g_origin, *g_omega0, *g_d0;
   int64_t margin;      // samples of slack around the retarded window (charge offsets)
 };
@@ -1446,6 +1449,8 @@ __global__ void adj_init_kernel(const AdjArgs A) {
     const double m = m1 * m2 / (m1 + m2);
     const double dN = a.d[bi * S + a.n_steps], vN = a.dd[bi * S + a.n_steps];
     const double w = A.wE ? A.wE[bi] : 0.0;
+    A.wts[2 * bi] = m2 / (m1 + m2) / q;
+    A.wts[2 * bi + 1] = -m1 / (m1 + m2) / q;
     // E = m (w0^2 d^2 + d'^2) / (2 q^2)
     A.lam[2 * bi] = w * m * w0 * w0 * dN / (q * q);
     A.lam[2 * bi + 1] = w * m * vN / (q * q);
@@ -1576,12 +1581,13 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
     tr.ax[c] = a.axis[3 * bj + c];
     pj[c] = tr.ax[c];
   }
-  const double q = a.q[bj], m1 = a.m1[bj], m2 = a.m2[bj];
-  double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
-  const int64_t kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
+  const double q = a.q[bj];
+  // first guess: the sample of the centre's retarded time, u - delay (u - nv is a half-integer)
+  const int2 dl = A.delay[bi * a.N + j];
+  const int64_t kg = nv - dl.x + Num<float>::floor_int((float)(u - (double)nv) - __int_as_float(dl.y));
   const double Eb[3] = {eb * pi[0], eb * pi[1], eb * pi[2]};
   for (int sg = 0; sg < 2; ++sg) {
-    const double w = (sg == 0) ? m2 / (m1 + m2) / q : -m1 / (m1 + m2) / q;
+    const double w = A.wts[2 * bj + sg];
     tr.w = w;
     const double qc = sg == 0 ? q : -q;
     int64_t k = -1;
@@ -1919,7 +1925,7 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   const size_t hist = al(nbn * S * sizeof(double));
   const size_t half = al(nbn * n_steps * sizeof(double));
   const size_t mu_b = al(nbn * S * 3 * sizeof(double));
-  const size_t small = al(nbn * (2 + 1 + (2 * kMaxBlock + 1) + 1 + 2) * sizeof(double));
+  const size_t small = al(nbn * (2 + 1 + (2 * kMaxBlock + 1) + 1 + 2 + 2) * sizeof(double));
   const size_t fit_b = rates ? hist + al(4 * nbn * sizeof(double)) : 0;
   if (ctx->adj_scratch.reserve(4 * hist + half + mu_b + small + fit_b) != cudaSuccess) return PC_ERR_CUDA;
   char *p = (char *)ctx->adj_scratch.ptr;
@@ -1939,7 +1945,8 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   fw.d_ddot = ddd;
   fw.Ed = Ed;
   int K = 1;
-  pc_status rs = run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K);
+  const int2 *delay = nullptr;
+  pc_status rs = run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K, nullptr, &delay);
   if (rs != PC_OK) return rs;
   AdjArgs A;
   memset(&A, 0, sizeof(A));
@@ -1969,6 +1976,8 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   A.Ebar = sm + 3 * nbn;
   A.w0bar = sm + (3 + 2 * kMaxBlock + 1) * nbn;
   A.tau = A.w0bar + nbn;
+  A.wts = A.tau + 2 * nbn;
+  A.delay = delay;
   A.g_origin = g->origin;
   A.g_omega0 = g->omega0;
   A.g_d0 = g->d0;
