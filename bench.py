@@ -485,6 +485,16 @@ def main():
         ds["ring_adjoint_f64"] = {"value": cfg4.N * cfg4.n_steps / (ms4 * 1e-3), "unit": "dipole-steps/s", "ms": ms4,
                                   "workload": "gradients of sum E(T) w.r.t. 768 origin coordinates, 256 omega0, "
                                               "256 d0 of the 256-oscillator ring, 20000 steps (forward + reverse)"}
+        pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, 64, w4, precision=pc.PC_MIXED)
+        torch.cuda.synchronize()
+        e0.record(s)
+        pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, cfg4.n_steps, w4, precision=pc.PC_MIXED)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms4m = e0.elapsed_time(e1)
+        ds["ring_adjoint_mixed_forward"] = {"value": cfg4.N * cfg4.n_steps / (ms4m * 1e-3), "unit": "dipole-steps/s",
+                                            "ms": ms4m, "workload": "the same gradients with the forward run's "
+                                                                    "driving field mixed, the reverse float64"}
         cfg5 = W.cfg5()
         r = lo_time(cfg5, cfg5.n_steps, pc.PC_MIXED, False)
         r["workload"] = "cloud: 4096 oscillators in a 600 nm cube x 20000 RK4 steps (1250 causal blocks of 16 steps)"

@@ -329,9 +329,13 @@ typedef struct {
  * defining equation (implicit-function theorem), the history interpolation exactly; a kink of the
  * loss where a retarded time crosses a sample is not smoothed.
  * The call first repeats the forward run, keeping the whole history and the half-step fields in
- * the context (8 doubles per dipole and step), then sweeps the causal blocks in reverse.
- *   dp, dt, n_steps, opts   as for pc_dipoles_run; opts->precision must be PC_F64 and
- *                           opts->ed_mode 0 (PC_ERR_ARG otherwise); the fit is not run
+ * the context (8 doubles per dipole and step), then sweeps the causal blocks in reverse.  With
+ * opts->precision PC_MIXED the forward run takes the mixed driving field (as pc_dipoles_run with
+ * PC_MIXED, about 30 times faster on large configurations) and the float64 reverse differentiates
+ * along that trajectory; its moment histories agree with the float64 run's to about 1e-8, and so
+ * do the gradients.
+ *   dp, dt, n_steps, opts   as for pc_dipoles_run; opts->precision PC_F64 or PC_MIXED (the
+ *                           forward), opts->ed_mode 0 (PC_ERR_ARG otherwise); the fit is not run
  *   g                       gradients (device)
  * Errors: those of pc_dipoles_run; PC_ERR_ARG also when the source windows of one causal block
  * exceed shared memory (more than about 8 500 steps between the nearest and the farthest
@@ -371,7 +375,7 @@ pc_status pc_dipoles_rates_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt,
  * retarded time (implicit-function theorem); the resulting adjoints of the dipoles' history
  * samples and origins seed the reverse sweep of pc_dipoles_adjoint, which carries them to the
  * origins, omega0 and d0.
- *   dp, dt, n_steps, opts   as for pc_dipoles_adjoint (PC_F64, ed_mode 0)
+ *   dp, dt, n_steps, opts   as for pc_dipoles_adjoint (PC_F64 or PC_MIXED forward, ed_mode 0)
  *   points                  device [P][3]; times host [T], 0 <= t (retarded times must fall
  *                           inside the run's samples)
  *   cot                     device float64 cotangents [B][T][P][3] (E, B, A) and [B][T][P] (phi),

@@ -398,9 +398,10 @@ def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_
     return out
 
 
-def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, stream=None):
+def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, precision=PC_F64, stream=None):
     """pc_dipoles_adjoint: gradients of sum w E(T) (w = dL_dEnergyFinal, [B][N] CUDA float64) with
-    respect to the origins, omega0 and d0; returns (g_origin [B][N][3], g_omega0 [B][N], g_d0 [B][N])."""
+    respect to the origins, omega0 and d0; returns (g_origin [B][N][3], g_omega0 [B][N], g_d0 [B][N]).
+    precision selects the forward run's driving field (the reverse is float64)."""
     B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
     dev = dp.origin.device
     w = dL_dEnergyFinal.to(device=dev, dtype=torch.float64).contiguous()
@@ -409,7 +410,7 @@ def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, stream=
     g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
     d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
                   m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
-    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=PC_F64)
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=int(precision))
     g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
     st = ctx.lib.pc_dipoles_adjoint(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
                                     _ptr(w), ctypes.byref(g), _stream(stream))
@@ -445,7 +446,7 @@ def pc_dipoles_rates_adjoint(ctx, dp, dt, n_steps, first_index, dL_dgamma=None, 
 
 
 def pc_dipoles_fields_adjoint(ctx, dp, dt, n_steps, points, times, cE=None, cB=None, cphi=None, cA=None, v_max=0.0,
-                              stream=None):
+                              precision=PC_F64, stream=None):
     """pc_dipoles_fields_adjoint: gradients of sum <c, field> of the oscillators' own fields at the
     points and times; cotangents [B][T][P][3] / [B][T][P] CUDA float64 (any may be None).
     Returns (g_origin, g_omega0, g_d0)."""
@@ -463,7 +464,7 @@ def pc_dipoles_fields_adjoint(ctx, dp, dt, n_steps, points, times, cE=None, cB=N
     g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
     d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
                   m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
-    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=PC_F64)
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=int(precision))
     g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
     tarr = (_f64 * T)(*[float(t) for t in times])
     st = ctx.lib.pc_dipoles_fields_adjoint(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),

@@ -1916,7 +1916,10 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
                               double *gamma_out, double *omega_out, const pc_dipole_grads *g, cudaStream_t st,
                               const FieldSeed *fseed = nullptr) {
   if (!dp || !opts || !g || !g->origin || !g->omega0 || !g->d0) return PC_ERR_ARG;
-  if (opts->ed_mode != 0 || opts->precision != PC_F64 || n_steps < 1) return PC_ERR_ARG;
+  // the forward may run its driving field in either precision (the reverse is float64 throughout);
+  // the fitted rates' adjoint keeps the float64 forward
+  if (opts->ed_mode != 0 || n_steps < 1) return PC_ERR_ARG;
+  if (opts->precision != PC_F64 && (rates || opts->precision != PC_MIXED)) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0)) return PC_ERR_ARG;
   if (rates && (opts->first_index < 0 || n_steps + 1 - opts->first_index < 8)) return PC_ERR_ARG;
   const int64_t S = n_steps + 1;

@@ -1,5 +1,7 @@
 """Gradients of the float64 oscillator run (pc_dipoles_adjoint, CUDA through the C ABI) against
 central finite differences of the GPU forward and of the FP64 oracle."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -95,6 +97,37 @@ def test_adjoint_vs_oracle_finite_differences(ctx):
             fd[idx] = (_loss_oracle(_perturbed(cfg, name, idx, h), w) -
                        _loss_oracle(_perturbed(cfg, name, idx, -h), w)) / (2 * h)
         _check(g[name], fd, 1e-5 if name != "origin" else 1e-4)
+
+
+def test_mixed_forward_adjoint(ctx):
+    # the forward run with the mixed driving field, the reverse in float64: its moment histories
+    # agree with the float64 run's to ~1e-8, and its gradients with the float64 adjoint's to
+    # within 1e-6 of each group's largest entry (and so with finite differences, as above); the
+    # ring of 256 oscillators takes the grid path, the cluster the one-CTA path
+    for cfg in (W.adjoint_cluster(B=2, N=3, n_steps=3000), W.cfg4(n_steps=400)):
+        w = _weights(cfg) if cfg.N < 10 else np.ones((cfg.B, cfg.N))
+        dp = pc.lo_config_to_device(cfg)
+        wt = torch.tensor(w, device="cuda")
+        g64 = pc.pc_dipoles_adjoint(ctx, dp, cfg.dt, cfg.n_steps, wt)
+        gmx = pc.pc_dipoles_adjoint(ctx, dp, cfg.dt, cfg.n_steps, wt, precision=pc.PC_MIXED)
+        for a, b in zip(g64, gmx):
+            scale = float(a.abs().max())
+            assert scale > 0
+            assert float((a - b).abs().max()) / scale < 1e-6
+    # the fitted rates' adjoint keeps the float64 forward: PC_MIXED is an argument error there
+    with pytest.raises(pc.PcError):
+        dp = pc.lo_config_to_device(cfg)
+        opts = pc.capi.PcRunOpts(v_max=0.0, ed_mode=0, fit=1, first_index=100, precision=pc.PC_MIXED)
+        z = torch.zeros((cfg.B, cfg.N), dtype=torch.float64, device="cuda")
+        d = pc.capi.PcDipoles(B=cfg.B, N=cfg.N, origin=pc.capi._ptr(dp.origin), axis=pc.capi._ptr(dp.axis),
+                              q=pc.capi._ptr(dp.q), m1=pc.capi._ptr(dp.m1), m2=pc.capi._ptr(dp.m2),
+                              omega0=pc.capi._ptr(dp.omega0), d0=pc.capi._ptr(dp.d0))
+        gr = [torch.empty((cfg.B, cfg.N, 3), dtype=torch.float64, device="cuda"), z.clone(), z.clone()]
+        g = pc.capi.PcDipoleGrads(origin=pc.capi._ptr(gr[0]), omega0=pc.capi._ptr(gr[1]), d0=pc.capi._ptr(gr[2]))
+        st = ctx.lib.pc_dipoles_rates_adjoint(ctx.handle, ctypes.byref(d), float(cfg.dt), int(cfg.n_steps),
+                                              ctypes.byref(opts), pc.capi._ptr(z), None, None, None,
+                                              ctypes.byref(g), None)
+        pc.capi._check(st, "pc_dipoles_rates_adjoint")
 
 
 def test_isolated_dipole_gradient_closed_form(ctx):
