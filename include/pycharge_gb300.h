@@ -344,6 +344,30 @@ typedef struct {
 pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                              const double *dL_dEnergyFinal, const pc_dipole_grads *g, void *stream);
 
+/* Gradients of the origin samples of a moving run, device [B][N][2 n_steps + 1][3] each (any may
+ * be NULL: not wanted), laid out as pc_dipole_motion. */
+typedef struct {
+  double *pos, *vel, *acc;
+} pc_dipole_motion_grads;
+
+/*
+ * pc_dipoles_adjoint_moving -- pc_dipoles_adjoint for the run of pc_dipoles_run_moving (Sec. 4.3,
+ * origins on given trajectories): gradients of L = sum w E(T) with respect to every origin sample
+ * (position, velocity, acceleration at the half steps), omega0 and d0.  The paper has no adjoint.
+ * A receiver's origin enters at its stage time (its half-step sample), a source's origin through
+ * the linear interpolation of its whole-step samples at the charge's retarded time, whose
+ * dependence on the origin samples is taken through its defining equation (Eq. ret_t, implicit-
+ * function theorem) as in pc_dipoles_adjoint.  g->origin receives zeros: the static origins do not
+ * enter a moving run.
+ *   dp, motion, dt, n_steps, opts   as for pc_dipoles_run_moving (PC_F64, ed_mode 0)
+ *   dL_dEnergyFinal                  device [B][N]
+ *   g, gm                            gradients (device); the call clears gm's arrays first
+ * Errors: those of pc_dipoles_adjoint and of pc_dipoles_run_moving.
+ */
+pc_status pc_dipoles_adjoint_moving(pc_ctx *ctx, const pc_dipoles *dp, const pc_dipole_motion *motion, double dt,
+                                    int64_t n_steps, const pc_run_opts *opts, const double *dL_dEnergyFinal,
+                                    const pc_dipole_grads *g, const pc_dipole_motion_grads *gm, void *stream);
+
 /*
  * pc_dipoles_rates_adjoint -- reverse-mode gradient of L = sum_{b,i} (dL_dgamma gamma + dL_domega omega)
  * where gamma and omega are the Eq. KE fit (Sec. 2.4) of each dipole's kinetic energy

@@ -26,6 +26,7 @@ from .capi import (  # noqa: F401
     pc_alu_peaks,
     pc_autotune_plane,
     pc_dipoles_adjoint,
+    pc_dipoles_adjoint_moving,
     pc_dipoles_fields_adjoint,
     pc_dipoles_rates_adjoint,
     pc_dipoles_run,

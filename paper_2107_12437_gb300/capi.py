@@ -107,6 +107,9 @@ SIGNATURES = {
                                        _i32, _f64, ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run_moving": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), ctypes.POINTER(PcDipoleMotion), _f64,
                                              _i64, ctypes.POINTER(PcRunOpts), ctypes.POINTER(PcRunOut), _vp]),
+    "pc_dipoles_adjoint_moving": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), ctypes.POINTER(PcDipoleMotion),
+                                                 _f64, _i64, ctypes.POINTER(PcRunOpts), _vp,
+                                                 ctypes.POINTER(PcDipoleGrads), ctypes.POINTER(PcDipoleMotion), _vp]),
     "pc_dipoles_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                           _vp, ctypes.POINTER(PcDipoleGrads), _vp]),
     "pc_dipoles_rates_adjoint": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64,
@@ -556,6 +559,35 @@ def pc_dipoles_run_moving(ctx, dp, motion, dt, n_steps, v_max=0.0, ed_mode=0, fi
                                        ctypes.byref(opts), ctypes.byref(ro), _stream(stream))
     _check(st, "pc_dipoles_run_moving")
     return out
+
+
+def pc_dipoles_adjoint_moving(ctx, dp, motion, dt, n_steps, dL_dEnergyFinal, v_max=0.0, stream=None):
+    """pc_dipoles_adjoint_moving: gradients of sum w E(T) of a moving run (motion = (pos, vel, acc)
+    CUDA float64 [B][N][2 n_steps + 1][3]); returns (g_origin (zeros), g_omega0, g_d0, g_pos, g_vel,
+    g_acc)."""
+    B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
+    dev = dp.origin.device
+    H = 2 * int(n_steps) + 1
+    pos, vel, acc = (x.to(device=dev, dtype=torch.float64).contiguous() for x in motion)
+    for x in (pos, vel, acc):
+        if tuple(x.shape) != (B, N, H, 3):
+            raise ValueError("motion arrays must be [B][N][2 n_steps + 1][3]")
+    w = dL_dEnergyFinal.to(device=dev, dtype=torch.float64).contiguous()
+    g_origin = torch.empty((B, N, 3), dtype=torch.float64, device=dev)
+    g_omega0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    gm = [torch.empty((B, N, H, 3), dtype=torch.float64, device=dev) for _ in range(3)]
+    d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
+                  m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+    mo = PcDipoleMotion(pos=_ptr(pos), vel=_ptr(vel), acc=_ptr(acc))
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=PC_F64)
+    g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
+    gmo = PcDipoleMotion(pos=_ptr(gm[0]), vel=_ptr(gm[1]), acc=_ptr(gm[2]))
+    st = ctx.lib.pc_dipoles_adjoint_moving(ctx.handle, ctypes.byref(d), ctypes.byref(mo), float(dt), int(n_steps),
+                                           ctypes.byref(opts), _ptr(w), ctypes.byref(g), ctypes.byref(gmo),
+                                           _stream(stream))
+    _check(st, "pc_dipoles_adjoint_moving")
+    return (g_origin, g_omega0, g_d0, *gm)
 
 
 def pc_ke_fit(ctx, ke, dt, first_index, stream=None):

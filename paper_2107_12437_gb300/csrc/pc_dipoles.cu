@@ -1434,6 +1434,10 @@ struct AdjArgs {
   double *tau;         // [B][N][2] smallest and largest delay (steps) from a source to its receivers
   double *wts;         // [B][N][2] offsets of the charges per unit moment, m2/((m1+m2) q), -m1/((m1+m2) q)
   const int2 *delay;   // [B][N][N] centre delays of the forward run (first guesses of the solves)
+  // moving origins (f.org_pos set): gradients of the origin samples, [B][N][2 n_steps + 1][3] each
+  // (null: not wanted), and per dipole the largest origin displacement from its first sample (samples)
+  double *gpos, *gvel, *gacc;
+  double *disp;
   double *g_origin, *g_omega0, *g_d0;
   int64_t margin;      // samples of slack around the retarded window (charge offsets)
 };
@@ -1451,6 +1455,17 @@ __global__ void adj_init_kernel(const AdjArgs A) {
     const double w = A.wE ? A.wE[bi] : 0.0;
     A.wts[2 * bi] = m2 / (m1 + m2) / q;
     A.wts[2 * bi + 1] = -m1 / (m1 + m2) / q;
+    double dmax = 0.0;
+    if (a.org_pos) {
+      const int64_t H = 2 * a.n_steps + 1;
+      const double *P0 = a.org_pos + bi * H * 3;
+      for (int64_t h = 1; h < H; ++h) {
+        const double *Ph = P0 + 3 * h;
+        const double ex = Ph[0] - P0[0], ey = Ph[1] - P0[1], ez = Ph[2] - P0[2];
+        dmax = fmax(dmax, sqrt(ex * ex + ey * ey + ez * ez));
+      }
+    }
+    A.disp[bi] = dmax / L;
     // E = m (w0^2 d^2 + d'^2) / (2 q^2)
     A.lam[2 * bi] = w * m * w0 * w0 * dN / (q * q);
     A.lam[2 * bi + 1] = w * m * vN / (q * q);
@@ -1562,6 +1577,7 @@ __global__ void adj_rk4_kernel(const AdjArgs A, int64_t n0, int kb) {
 // Reverse of the driving-field contribution F = p_i . E of dipole j's two charges at receiver i
 // and time u (steps, history 0..nv).  eb = dL/dF.  Adds to the history adjoints of j (window
 // win[0..W) for samples wlo..), to the receiver's and the source's origin adjoints.
+template <bool MOV>
 __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int64_t nv, double eb, double *win,
                             int64_t wlo, int W, double Rib[3], double Rjb[3]) {
   const RunArgs &a = A.f;
@@ -1582,9 +1598,25 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
     pj[c] = tr.ax[c];
   }
   const double q = a.q[bj];
-  // first guess: the sample of the centre's retarded time, u - delay (u - nv is a half-integer)
-  const int2 dl = A.delay[bi * a.N + j];
-  const int64_t kg = nv - dl.x + Num<float>::floor_int((float)(u - (double)nv) - __int_as_float(dl.y));
+  // moving origins: the receiver at its origin of the stage time (half-step index 2u), the source
+  // charges on the interpolated origin history; their adjoints go to the origin samples
+  constexpr bool mov = MOV;  // moving origins (a.org_pos set): a separate instantiation
+  const int64_t H = 2 * S - 1;
+  const int64_t hh = mov ? (int64_t)llrint(2.0 * u) : 0;
+  int64_t kg;
+  if (mov) {
+    Ri = a.org_pos + (bi * H + hh) * 3;
+    tr.Rp = a.org_pos + bj * H * 3;
+    tr.Rv = a.org_vel + bj * H * 3;
+    tr.Ra = a.org_acc + bj * H * 3;
+    for (int c = 0; c < 3; ++c) tr.R[c] = tr.Rp[6 * nv + c];  // the source now, for the first guess
+    const double dv[3] = {Ri[0] - tr.R[0], Ri[1] - tr.R[1], Ri[2] - tr.R[2]};
+    kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
+  } else {
+    // first guess: the sample of the centre's retarded time, u - delay (u - nv is a half-integer)
+    const int2 dl = A.delay[bi * a.N + j];
+    kg = nv - dl.x + Num<float>::floor_int((float)(u - (double)nv) - __int_as_float(dl.y));
+  }
   const double Eb[3] = {eb * pi[0], eb * pi[1], eb * pi[2]};
   for (int sg = 0; sg < 2; ++sg) {
     const double w = A.wts[2 * bj + sg];
@@ -1621,28 +1653,68 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
     double ab[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, accb[3] = {0, 0, 0};
     lw_E_f64_rev(qc, av, vel, acc, Eb, ab, vb, accb);
     // a = r - p: receiver origin gets ab, the source position gets -ab
+    double *gr = mov && A.gpos ? A.gpos + (bi * H + hh) * 3 : nullptr;  // receiver's origin sample
     for (int c = 0; c < 3; ++c) {
-      Rib[c] += ab[c];
-      Rjb[c] -= ab[c];
+      if (mov) {
+        if (gr) atomicAdd(gr + c, ab[c]);
+      } else {
+        Rib[c] += ab[c];
+        Rjb[c] -= ab[c];
+      }
     }
     const double pb_p = -dot3(ab, pj);  // adjoint of the charge offset along the axis
     if (stat) {
-      // position R_j + w d[0] p_j: only d[0] (window slot of sample 0)
+      // position R_j + w d[0] p_j: only d[0] (window slot of sample 0) and the first origin sample
       if (wlo != 0) return PC_ERR_NOCONV;
       atomicAdd(&win[0], w * pb_p);
+      if (mov && A.gpos)
+        for (int c = 0; c < 3; ++c) atomicAdd(A.gpos + bj * H * 3 + c, -ab[c]);
       continue;
     }
     if (k < wlo || k + 1 >= wlo + W) return PC_ERR_NOCONV;
     const double Db = w * pb_p, Vb = w * dot3(vb, pj), Ab = w * dot3(accb, pj);
     double *w0p = win + 3 * (k - wlo), *w1p = w0p + 3;
     // the fraction th depends on the inputs through G(th) = cdt^2 (u - k - th)^2 - |r - p(th)|^2 = 0
-    const double thb = Db * Dd + Vb * Dv + Ab * Da;
+    double thb = Db * Dd + Vb * Dv + Ab * Da;
     const double ap = dot3(av, pj);
-    const double Gth = -2.0 * cdt * cdt * (u - (double)k - th) + 2.0 * w * Dd * ap;
+    double Gth = -2.0 * cdt * cdt * (u - (double)k - th) + 2.0 * w * Dd * ap;
+    double dRp[3] = {0, 0, 0};
+    if (mov) {
+      // the origin's interpolated position, velocity and acceleration move with th too
+      const double *P0 = tr.Rp + 6 * k, *V0 = tr.Rv + 6 * k, *A0 = tr.Ra + 6 * k;
+      for (int c = 0; c < 3; ++c) {
+        dRp[c] = P0[6 + c] - P0[c];
+        thb += -ab[c] * dRp[c] + vb[c] * (V0[6 + c] - V0[c]) + accb[c] * (A0[6 + c] - A0[c]);
+      }
+      Gth += 2.0 * dot3(av, dRp);
+    }
     const double sfac = -thb / Gth;
-    for (int c = 0; c < 3; ++c) {
-      Rib[c] += sfac * (-2.0 * av[c]);
-      Rjb[c] += sfac * (2.0 * av[c]);
+    if (mov) {
+      // origin samples 2k and 2k + 2 carry the source's position (with the retarded-time term),
+      // velocity and acceleration adjoints with weights 1 - th and th; the receiver's sample the
+      // retarded-time term of r
+      const size_t o0 = (bj * H + 2 * k) * 3, o1 = o0 + 6;
+      for (int c = 0; c < 3; ++c) {
+        const double pbv = -ab[c] + sfac * 2.0 * av[c];
+        if (A.gpos) {
+          atomicAdd(A.gpos + o0 + c, (1.0 - th) * pbv);
+          atomicAdd(A.gpos + o1 + c, th * pbv);
+          atomicAdd(gr + c, sfac * (-2.0 * av[c]));
+        }
+        if (A.gvel) {
+          atomicAdd(A.gvel + o0 + c, (1.0 - th) * vb[c]);
+          atomicAdd(A.gvel + o1 + c, th * vb[c]);
+        }
+        if (A.gacc) {
+          atomicAdd(A.gacc + o0 + c, (1.0 - th) * accb[c]);
+          atomicAdd(A.gacc + o1 + c, th * accb[c]);
+        }
+      }
+    } else {
+      for (int c = 0; c < 3; ++c) {
+        Rib[c] += sfac * (-2.0 * av[c]);
+        Rjb[c] += sfac * (2.0 * av[c]);
+      }
     }
     const double dbar = Db + sfac * 2.0 * ap * w;
     atomicAdd(&w0p[0], (1.0 - th) * dbar);
@@ -1659,6 +1731,7 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
 // receiver.  ns == 0 handles the field at t = 0 with the adjoint left in `carry`.  The source
 // samples the block's retarded times reach lie in [n0 + 1/2 - tau_max - margin,
 // n0 + ns/2 - tau_min + margin]; their adjoints are gathered in a shared-memory window.
+template <bool MOV>
 __global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t n0, int ns, int wmax) {
   extern __shared__ double win[];  // [wmax][3]
   __shared__ double s_rj[3][128];
@@ -1694,7 +1767,7 @@ __global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t
         const double eb = ns > 0 ? A.Ebar[bi * (2 * kMaxBlock + 1) + s] : A.carry[bi];
         if (eb == 0.0) continue;
         const double u = ns > 0 ? (double)n0 + 0.5 * s : 0.0;
-        err = pair_rev_f64(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
+        err = pair_rev_f64<MOV>(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
       }
       for (int c = 0; c < 3; ++c)
         if (Rib[c] != 0.0) atomicAdd(&A.g_origin[3 * bi + c], Rib[c]);
@@ -1715,7 +1788,7 @@ __global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t
         const double eb = ns > 0 ? A.Ebar[bi * (2 * kMaxBlock + 1) + s] : A.carry[bi];
         if (eb != 0.0) {
           const double u = ns > 0 ? (double)n0 + 0.5 * s : 0.0;
-          err = pair_rev_f64(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
+          err = pair_rev_f64<MOV>(A, b, i, j, u, n0, eb, win, wlo, W, Rib, Rjb);
         }
       }
       for (int c = 0; c < 3; ++c) s_rib[warp][lane][c] = Rib[c];
@@ -1914,8 +1987,12 @@ namespace pc {
 static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                               const double *wE, bool rates, const double *dL_dgamma, const double *dL_domega,
                               double *gamma_out, double *omega_out, const pc_dipole_grads *g, cudaStream_t st,
-                              const FieldSeed *fseed = nullptr) {
+                              const FieldSeed *fseed = nullptr, const pc_dipole_motion *motion = nullptr,
+                              const pc_dipole_motion_grads *gm = nullptr) {
   if (!dp || !opts || !g || !g->origin || !g->omega0 || !g->d0) return PC_ERR_ARG;
+  // moving origins: the energy loss with the float64 forward only
+  if (motion && (rates || fseed || opts->precision != PC_F64 || !motion->pos || !motion->vel || !motion->acc))
+    return PC_ERR_ARG;
   // the forward may run its driving field in either precision (the reverse is float64 throughout);
   // the fitted rates' adjoint keeps the float64 forward
   if (opts->ed_mode != 0 || n_steps < 1) return PC_ERR_ARG;
@@ -1928,7 +2005,7 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   const size_t hist = al(nbn * S * sizeof(double));
   const size_t half = al(nbn * n_steps * sizeof(double));
   const size_t mu_b = al(nbn * S * 3 * sizeof(double));
-  const size_t small = al(nbn * (2 + 1 + (2 * kMaxBlock + 1) + 1 + 2 + 2) * sizeof(double));
+  const size_t small = al(nbn * (2 + 1 + (2 * kMaxBlock + 1) + 1 + 2 + 2 + 1) * sizeof(double));
   const size_t fit_b = rates ? hist + al(4 * nbn * sizeof(double)) : 0;
   if (ctx->adj_scratch.reserve(4 * hist + half + mu_b + small + fit_b) != cudaSuccess) return PC_ERR_CUDA;
   char *p = (char *)ctx->adj_scratch.ptr;
@@ -1949,8 +2026,12 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   fw.Ed = Ed;
   int K = 1;
   const int2 *delay = nullptr;
-  pc_status rs = run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K, nullptr, &delay);
+  pc_status rs = run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K, motion, &delay);
   if (rs != PC_OK) return rs;
+  const size_t hs = (size_t)(2 * n_steps + 1) * 3 * sizeof(double);
+  if (motion && gm)
+    for (double *gp : {gm->pos, gm->vel, gm->acc})
+      if (gp && cudaMemsetAsync(gp, 0, nbn * hs, st) != cudaSuccess) return PC_ERR_CUDA;
   AdjArgs A;
   memset(&A, 0, sizeof(A));
   RunArgs &a = A.f;
@@ -1980,7 +2061,18 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   A.w0bar = sm + (3 + 2 * kMaxBlock + 1) * nbn;
   A.tau = A.w0bar + nbn;
   A.wts = A.tau + 2 * nbn;
+  A.disp = A.wts + 2 * nbn;
   A.delay = delay;
+  if (motion) {
+    a.org_pos = motion->pos;
+    a.org_vel = motion->vel;
+    a.org_acc = motion->acc;
+    if (gm) {
+      A.gpos = gm->pos;
+      A.gvel = gm->vel;
+      A.gacc = gm->acc;
+    }
+  }
   A.g_origin = g->origin;
   A.g_omega0 = g->omega0;
   A.g_d0 = g->d0;
@@ -2018,10 +2110,11 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   const unsigned rgrid = (unsigned)((nbn + 127) / 128);
   adj_init_kernel<<<rgrid, 128, 0, st>>>(A);
   // margin for charge offsets: three times the largest initial |r_dip|, in samples, plus one
-  std::vector<double> hq(nbn), hd0(nbn), htau(2 * nbn);
+  std::vector<double> hq(nbn), hd0(nbn), htau(2 * nbn), hdisp(nbn);
   if (cudaMemcpyAsync(hq.data(), dp->q, nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(hd0.data(), dp->d0, nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(htau.data(), A.tau, 2 * nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(hdisp.data(), A.disp, nbn * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return PC_ERR_CUDA;
   double smax = 0.0, spread = 0.0;
@@ -2029,11 +2122,16 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
     smax = std::max(smax, std::fabs(hd0[k] / hq[k]));
     if (htau[2 * k] <= htau[2 * k + 1]) spread = std::max(spread, htau[2 * k + 1] - htau[2 * k]);
   }
-  A.margin = (int64_t)std::ceil(3.0 * smax / (kC * dt)) + 2;
+  // moving origins: delays drift by up to the two origins' displacements
+  double dmax = 0.0;
+  for (double v : hdisp) dmax = std::max(dmax, v);
+  A.margin = (int64_t)std::ceil(3.0 * smax / (kC * dt) + 2.0 * dmax) + 2;
   const int wmax = (int)std::max(1.0, std::min<double>(std::ceil(spread) + K + 2.0 * A.margin + 6.0, (double)S));
   const size_t smem = (size_t)wmax * 3 * sizeof(double);
   if (smem > 200 * 1024) return PC_ERR_ARG;  // source windows beyond shared memory
-  if (cudaFuncSetAttribute(adj_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  const bool mov = motion != nullptr;
+  if (cudaFuncSetAttribute(mov ? adj_field_kernel<true> : adj_field_kernel<false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PC_ERR_CUDA;
   if (fseed && fseed->P > 0) {
     // the field loss seeds the history adjoints and the origin gradients before the sweep; its
@@ -2050,10 +2148,12 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
     const int64_t n0 = bk * K;
     const int kb = (int)std::min((int64_t)K, n_steps - n0);
     adj_rk4_kernel<<<rgrid, 128, 0, st>>>(A, n0, kb);
-    adj_field_kernel<<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
+    if (mov) adj_field_kernel<true><<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
+    else adj_field_kernel<false><<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
   }
   // the driving field at t = 0 (static configuration) and the final gradients
-  adj_field_kernel<<<fgrid, 128, smem, st>>>(A, 0, 0, wmax);
+  if (mov) adj_field_kernel<true><<<fgrid, 128, smem, st>>>(A, 0, 0, wmax);
+  else adj_field_kernel<false><<<fgrid, 128, smem, st>>>(A, 0, 0, wmax);
   adj_final_kernel<<<rgrid, 128, 0, st>>>(A);
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
@@ -2069,6 +2169,21 @@ extern "C" pc_status pc_dipoles_adjoint(pc_ctx *ctx, const pc_dipoles *dp, doubl
   if (bs != PC_OK) return bs;
   pc_status rs = pc::adjoint_core(ctx, dp, dt, n_steps, opts, dL_dEnergyFinal, false, nullptr, nullptr, nullptr,
                                   nullptr, g, st);
+  if (rs != PC_OK) return rs;
+  return pc::end_call(ctx, st);
+}
+
+extern "C" pc_status pc_dipoles_adjoint_moving(pc_ctx *ctx, const pc_dipoles *dp, const pc_dipole_motion *motion,
+                                               double dt, int64_t n_steps, const pc_run_opts *opts,
+                                               const double *dL_dEnergyFinal, const pc_dipole_grads *g,
+                                               const pc_dipole_motion_grads *gm, void *stream) {
+  if (!ctx || !motion || !dL_dEnergyFinal) return PC_ERR_ARG;
+  pc::DeviceGuard gd(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  pc_status rs = pc::adjoint_core(ctx, dp, dt, n_steps, opts, dL_dEnergyFinal, false, nullptr, nullptr, nullptr,
+                                  nullptr, g, st, nullptr, motion, gm);
   if (rs != PC_OK) return rs;
   return pc::end_call(ctx, st);
 }

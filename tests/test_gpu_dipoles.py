@@ -104,6 +104,29 @@ def test_causality_and_velocity_errors(ctx):
     assert ei.value.status == pc.capi.PC_ERR_VELOCITY
 
 
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+@pytest.mark.parametrize("N", [2, 80])
+def test_zero_steps_and_argument_errors(ctx, prec, N):
+    # n_steps = 0 (the one-CTA and the grid path): the history is the initial state alone, d0 at
+    # rest, with its energy m w0^2 d0^2 / (2 q^2) (Eq. dipoleE); malformed calls are argument errors
+    cfg = W.cfg5(N=N, n_steps=0, side=150e-9, min_spacing=8e-9, seed=3)
+    dp = pc.lo_config_to_device(cfg)
+    out = pc.pc_dipoles_run(ctx, dp, cfg.dt, 0, precision=prec)
+    m = cfg.m1 * cfg.m2 / (cfg.m1 + cfg.m2)
+    e0 = m * cfg.omega0 ** 2 * cfg.d0 ** 2 / (2 * cfg.q ** 2)
+    assert out["d"].shape == (1, N, 1)
+    assert np.array_equal(out["d"][..., 0].cpu().numpy(), cfg.d0)
+    assert not out["d_dot"].any() and not out["d_ddot"].any()
+    assert np.allclose(out["energy"][..., 0].cpu().numpy(), e0, rtol=1e-14, atol=0)
+    for kw in (dict(ed_mode=2), dict(fit=True, first_index=0)):
+        with pytest.raises(pc.PcError) as ei:
+            pc.pc_dipoles_run(ctx, dp, cfg.dt, 4, precision=prec, **kw)
+        assert ei.value.status == pc.capi.PC_ERR_ARG
+    with pytest.raises(pc.PcError) as ei:
+        pc.pc_dipoles_run(ctx, dp, -cfg.dt, 4, precision=prec)
+    assert ei.value.status == pc.capi.PC_ERR_ARG
+
+
 @pytest.mark.parametrize("gamma", [0.0, 2e7, 3e10])
 def test_ke_fit_synthetic(ctx, gamma):
     dt = 1e-18

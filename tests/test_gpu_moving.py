@@ -74,3 +74,79 @@ def test_moving_rejects_mixed_precision(ctx):
     st = ctx.lib.pc_dipoles_run_moving(ctx.handle, ctypes.byref(d), ctypes.byref(mo), cfg.dt, 20, ctypes.byref(opts),
                                        ctypes.byref(ro), None)
     assert st == 1  # PC_ERR_ARG
+
+
+def _weights(cfg, seed=5):
+    rng = np.random.default_rng(seed)
+    e0 = 0.5 * (W.M_E / 2) * float(cfg.omega0.mean()) ** 2 * (1e-11) ** 2
+    return rng.uniform(0.5, 1.5, size=(cfg.B, cfg.N)) / e0
+
+
+def test_moving_adjoint_without_motion_matches_static(ctx):
+    # origins that stay put: the gradient of a rigid shift of a dipole's whole trajectory (the sum
+    # over its position samples) is the static adjoint's origin gradient, and omega0, d0 agree
+    cfg = W.adjoint_cluster(B=2, N=3, n_steps=2000)
+    motion = W.oscillating_origins(cfg, 0.0, 1e13)
+    w = torch.tensor(_weights(cfg), device="cuda")
+    dp = pc.lo_config_to_device(cfg)
+    st = pc.pc_dipoles_adjoint(ctx, dp, cfg.dt, cfg.n_steps, w)
+    mv = pc.pc_dipoles_adjoint_moving(ctx, dp, _dev(motion), cfg.dt, cfg.n_steps, w)
+    assert not mv[0].any()
+    shift = mv[3].sum(dim=2)
+    assert float((shift - st[0]).abs().max() / st[0].abs().max()) < 1e-9
+    for a, b in ((st[1], mv[1]), (st[2], mv[2])):
+        assert float((a - b).abs().max() / a.abs().max()) < 1e-12
+    for gv in mv[4:]:
+        assert torch.isfinite(gv).all() and gv.abs().max() > 0
+
+
+def test_moving_adjoint_vs_finite_differences(ctx):
+    # gradients of sum w E(T) of a moving run against central differences of the GPU forward:
+    # omega0 and d0 of every dipole; rigid shifts of each dipole's trajectory; and shifts of its
+    # position, velocity and acceleration samples inside one time window
+    cfg = W.adjoint_cluster(B=1, N=3, n_steps=2000)
+    motion = W.oscillating_origins(cfg, np.array([[1e-10, 0.0, 5e-11]]), 2 * math.pi * 20e12,
+                                   direction=(1.0, 0.5, 0.0))
+    wn = _weights(cfg)
+    w = torch.tensor(wn, device="cuda")
+    g = pc.pc_dipoles_adjoint_moving(ctx, pc.lo_config_to_device(cfg), _dev(motion), cfg.dt, cfg.n_steps, w)
+    g = [x.cpu().numpy() for x in g]
+
+    def loss(c, m):
+        out = pc.pc_dipoles_run_moving(ctx, pc.lo_config_to_device(c), _dev(m), c.dt, c.n_steps)
+        return float((out["energy"][:, :, -1].cpu().numpy() * wn).sum())
+
+    import copy
+
+    def check(adj, fd, tol):
+        adj, fd = np.asarray(adj), np.asarray(fd)
+        scale = np.max(np.abs(fd))
+        assert scale > 0
+        assert np.max(np.abs(adj - fd)) / scale < tol, (adj, fd)
+
+    for name, rel in (("omega0", 1e-6), ("d0", 1e-6)):
+        fd = []
+        for i in range(cfg.N):
+            h = rel * float(getattr(cfg, name)[0, i])
+            cp, cm = copy.deepcopy(cfg), copy.deepcopy(cfg)
+            getattr(cp, name)[0, i] += h
+            getattr(cm, name)[0, i] -= h
+            fd.append((loss(cp, motion) - loss(cm, motion)) / (2 * h))
+        check(g[1 if name == "omega0" else 2][0], fd, 1e-5)
+    win = slice(1200, 1601)
+    L0 = loss(cfg, motion)
+    for arr, gi, h, sl in ((0, 3, 6e-13, slice(None)), (0, 3, 6e-13, win), (1, 4, None, win), (2, 5, None, win)):
+        adj, fd = [], []
+        if h is None:
+            # velocity and acceleration samples: a step that moves the loss by ~1e-7 of itself, far
+            # above its rounding and still in the linear range
+            h = 1e-7 * abs(L0) / max(abs(g[gi][0, i, sl, c].sum()) for i in range(cfg.N) for c in range(3))
+        for i in range(cfg.N):
+            for c in range(3):
+                mp = [x.copy() for x in motion]
+                mm = [x.copy() for x in motion]
+                mp[arr][0, i, sl, c] += h
+                mm[arr][0, i, sl, c] -= h
+                fd.append((loss(cfg, mp) - loss(cfg, mm)) / (2 * h))
+                adj.append(g[gi][0, i, sl, c].sum())
+        check(adj, fd, 1e-4)
