@@ -136,7 +136,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # CPU oracle legs
 # ------------------------------------------------------------------------------------------------
-def oracle_sample(n_side=160, threads=0):
+def oracle_sample(n_side=720, threads=0):
     """The FP64 oracle on one frame of a strided n_side x n_side sub-grid of the field-grid workload."""
     import oracle
 
@@ -154,17 +154,20 @@ def oracle_sample(n_side=160, threads=0):
                        f"({pairs:.3g} pair evals, {sec:.2f} s wall)")
 
 
-def oracle_lo_sample(threads=0):
-    """The FP64 oracle on two coupled oscillators (one separation of the batched run), 4000 steps."""
+def oracle_lo_sample(threads=0, n_sep=12):
+    """The FP64 oracle on n_sep separations of the batched run (two coupled oscillators each) over
+    all 40 000 steps, one configuration after another."""
     import oracle
 
-    cfg, _ = W.cfg3(B=256, n_steps=4000)
+    cfg, _ = W.cfg3(B=256, n_steps=40000)
+    bs = np.linspace(0, cfg.B - 1, n_sep).astype(int)
     t0 = time.perf_counter()
-    r = oracle.dipoles_run(cfg, b=128, nthreads=threads or 1)
+    for b in bs:
+        r = oracle.dipoles_run(cfg, b=int(b), nthreads=threads or 1)
+        assert r["status"] == oracle.OK
     sec = time.perf_counter() - t0
-    assert r["status"] == oracle.OK
-    return dict(value=2 * 4000 / sec, unit="dipole-steps/s", cores=threads or 1, kind="oracle",
-                sample="1 of 256 separations (2 oscillators) x 4000 steps")
+    return dict(value=n_sep * 2 * cfg.n_steps / sec, unit="dipole-steps/s", cores=threads or 1, kind="oracle",
+                sample=f"{n_sep} of the 256 separations (2 oscillators each) x 40000 steps ({sec:.1f} s wall)")
 
 
 def compare_cloud(pc, ctx, dev, n_steps):
