@@ -437,12 +437,13 @@ def main():
                                           "frac": FLOPS_PER_PAIR * f64_value / (2.0 * fp64_fma),
                                           "peak_basis": "measured float64 FMA rate (pc_alu_peaks)"}}
         # oscillator runs: dipole-steps per second (float64 RK4 state; driving field per precision)
-        def lo_time(cfg, n_steps, prec, fit):
+        def lo_time(cfg, n_steps, prec, fit, near_f64=0.0):
             lod = pc.lo_config_to_device(cfg, dev)
-            pc.pc_dipoles_run(ctx, lod, cfg.dt, min(n_steps, 64), precision=prec)
+            pc.pc_dipoles_run(ctx, lod, cfg.dt, min(n_steps, 64), precision=prec, near_f64=near_f64)
             torch.cuda.synchronize()
             e0.record(s)
-            pc.pc_dipoles_run(ctx, lod, cfg.dt, n_steps, precision=prec, fit=fit, first_index=cfg.first_index)
+            pc.pc_dipoles_run(ctx, lod, cfg.dt, n_steps, precision=prec, fit=fit, first_index=cfg.first_index,
+                              near_f64=near_f64)
             e1.record(s)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
@@ -455,6 +456,10 @@ def main():
             r["workload"] = ("batched pairs: 256 separations (1 nm .. 1 um) x 2 oscillators x 40000 RK4 steps, "
                              "one launch")
             ds["pairs_" + name] = r
+        r = lo_time(cfg3, cfg3.n_steps, pc.PC_MIXED, False, near_f64=10e-9)
+        r["workload"] = ("the same, mixed with the sources within 10 nm summed in float64 (decay rates of the "
+                         "closest pairs resolved)")
+        ds["pairs_mixed_near_f64"] = r
         # the Eq. KE fit of all 512 kinetic-energy series of that run (30 001 samples each)
         lod = pc.lo_config_to_device(cfg3, dev)
         out3 = pc.pc_dipoles_run(ctx, lod, cfg3.dt, cfg3.n_steps, precision=pc.PC_MIXED)

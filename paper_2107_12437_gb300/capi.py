@@ -54,7 +54,8 @@ class PcDipoles(ctypes.Structure):
 
 
 class PcRunOpts(ctypes.Structure):
-    _fields_ = [("v_max", _f64), ("ed_mode", _i32), ("fit", _i32), ("first_index", _i64), ("precision", _i32)]
+    _fields_ = [("v_max", _f64), ("ed_mode", _i32), ("fit", _i32), ("first_index", _i64), ("precision", _i32),
+                ("near_f64", _f64)]
 
 
 class PcRunOut(ctypes.Structure):
@@ -372,7 +373,7 @@ def lo_config_to_device(cfg, device="cuda"):
 
 
 def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_index=0, precision=PC_F64,
-                   want_energy=True, want_Ed=False, out=None, stream=None):
+                   want_energy=True, want_Ed=False, out=None, near_f64=0.0, stream=None):
     """pc_dipoles_run: dp holds [B][N] / [B][N][3] CUDA tensors; returns the dict of outputs."""
     B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
     S = int(n_steps) + 1
@@ -391,7 +392,7 @@ def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_
     d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
                   m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
     opts = PcRunOpts(v_max=float(v_max), ed_mode=int(ed_mode), fit=int(bool(fit)), first_index=int(first_index),
-                     precision=int(precision))
+                     precision=int(precision), near_f64=float(near_f64))
     ro = PcRunOut(d=_ptr(out["d"]), d_dot=_ptr(out["d_dot"]), d_ddot=_ptr(out["d_ddot"]),
                   energy=_ptr(out.get("energy")), Ed=_ptr(out.get("Ed")), gamma=_ptr(out.get("gamma")),
                   omega=_ptr(out.get("omega")))

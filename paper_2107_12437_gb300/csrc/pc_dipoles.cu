@@ -64,6 +64,7 @@ struct RunArgs {
   // [B][N][kTab]: M^1 .. M^kMaxBlock (row-major 2x2 each), then c1, c2, c4
   double *rk4tab;
   double e_unit;  // k_e e / (c dt)^2: the float32 driving field's unit (V/m)
+  float near_L;   // mixed drive: sources whose centre is closer than this (units of c dt) go float64
 };
 
 // then the dipole's constants, so that no block recomputes them (float64 divisions are costly on
@@ -327,7 +328,7 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
 
 // Phase A for one receiver (one warp): stage fields E_d(n0 + (s+1)/2), s < ns, into Es[1 + s];
 // ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.
-template <bool MIXED>
+template <bool MIXED, bool NEAR = false>
 __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err,
                             int j_lo, int j_hi, double *dst) {
   const int lane = threadIdx.x & 31;
@@ -345,10 +346,16 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
         // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
         const size_t ij = (size_t)bidx(a, b, i) * a.N + j;
         const int2 dl = a.delay[ij];
+        const float4 geo = a.pgeo[ij];
         const float xs = stage_f - __int_as_float(dl.y);
         float flf;
         const int fl = Num<float>::floor_int(xs, flf);
-        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, a.pgeo[ij], (int)n0 + 1, err);
+        if (NEAR && geo.x < a.near_L) {
+          // a near source whose radiative coupling float32 cannot resolve: the float64 pair
+          accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, (int)n0 - dl.x + fl, err);
+          continue;
+        }
+        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, geo, (int)n0 + 1, err);
         // Kahan sum over sources
         const float y = v - comp;
         const float t = accf + y;
@@ -362,7 +369,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       }
     }
   }
-  double mine = MIXED ? (double)accf * a.e_unit : accd;
+  double mine = MIXED ? (double)accf * a.e_unit + accd : accd;
   sh[lane] = (m < slots) ? mine : 0.0;
   __syncwarp();
   if (lane < nst) {
@@ -373,7 +380,9 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   __syncwarp();
 }
 
-template <bool MIXED>
+// NEAR: the mixed drive sums its near sources in float64 (near_f64 > 0), a separate instantiation
+// so that the float32 source loop of the default one keeps its registers
+template <bool MIXED, bool NEAR = false>
 __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a) {
   const int b = blockIdx.x;
   const int N = a.N;
@@ -404,7 +413,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
   // ---- E_d at t = 0 from the static configuration ----
   for (int i = warp; i < N; i += kRunWarps) {
     int err = 0;
-    drive_phase<MIXED>(a, b, i, 0, 0, sh[warp], &err, 0, N, a.Es);
+    drive_phase<MIXED, NEAR>(a, b, i, 0, 0, sh[warp], &err, 0, N, a.Es);
     if (err) {
       set_status(a.status, err);
       s_stop = 1;
@@ -418,7 +427,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     // phase A: all stage fields of the block
     for (int i = warp; i < N; i += kRunWarps) {
       int err = 0;
-      drive_phase<MIXED>(a, b, i, n0, 2 * kb, sh[warp], &err, 0, N, a.Es);
+      drive_phase<MIXED, NEAR>(a, b, i, n0, 2 * kb, sh[warp], &err, 0, N, a.Es);
       if (err) {
         set_status(a.status, err);
         s_stop = 1;
@@ -576,7 +585,7 @@ __global__ void lo_init_kernel(const RunArgs a, int K) {
 
 // Grid path, phase A: one warp per (receiver, source slice).  ns < 0 takes the block from the
 // device cursor a.blk (graph replay); ns == 0 evaluates E_d(0).
-template <bool MIXED>
+template <bool MIXED, bool NEAR = false>
 __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs a, int64_t n0, int ns) {
   __shared__ double sh[kRunWarps][32];
   if (*((volatile int *)a.status)) return;  // an earlier block failed
@@ -594,7 +603,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs 
   const int j_lo = min(a.N, z * chunk), j_hi = min(a.N, j_lo + chunk);
   double *dst = a.nsplit > 1 ? a.Epart + (size_t)z * a.B * a.N * (2 * kMaxBlock + 1) : a.Es;
   int err = 0;
-  drive_phase<MIXED>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
+  drive_phase<MIXED, NEAR>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
   if (err) set_status(a.status, err);
 }
 
@@ -1204,7 +1213,8 @@ static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, di
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof(kp));
   cudaGraphNode_t n1, n2, n3;
-  kp.func = mixed ? (void *)lo_drive_kernel<true> : (void *)lo_drive_kernel<false>;
+  kp.func = !mixed ? (void *)lo_drive_kernel<false>
+                    : (a.near_L > 0.f ? (void *)lo_drive_kernel<true, true> : (void *)lo_drive_kernel<true>);
   kp.gridDim = dgrid;
   kp.blockDim = dim3(kRunWarps * 32);
   kp.kernelParams = drive_args;
@@ -1235,6 +1245,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   if (!out->d || !out->d_dot || !out->d_ddot) return PC_ERR_ARG;
   if (opts->ed_mode != 0 && opts->ed_mode != 1) return PC_ERR_ARG;
   if (opts->precision != PC_F64 && opts->precision != PC_MIXED) return PC_ERR_ARG;
+  if (!(opts->near_f64 >= 0.0) || !std::isfinite(opts->near_f64)) return PC_ERR_ARG;
   if (opts->fit && (!out->gamma || !out->omega || opts->first_index < 0 || n_steps + 1 - opts->first_index < 8))
     return PC_ERR_ARG;
   const int64_t S = n_steps + 1;
@@ -1298,6 +1309,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.blk = nullptr;
   a.rk4tab = (double *)(scr + tab_off);
   a.e_unit = pc::kKe * pc::kE / ((pc::kC * dt) * (pc::kC * dt));
+  a.near_L = mixed ? (float)(opts->near_f64 / (pc::kC * dt)) : 0.f;
   a.org_pos = motion ? motion->pos : nullptr;
   a.org_vel = motion ? motion->vel : nullptr;
   a.org_acc = motion ? motion->acc : nullptr;
@@ -1323,7 +1335,8 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   }
   if (dp->N <= pc::kSmallN) {
     // small configurations: one persistent CTA each, the time loop inside
-    if (mixed) pc::lo_run_kernel<true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
+    if (mixed && a.near_L > 0.f) pc::lo_run_kernel<true, true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
+    else if (mixed) pc::lo_run_kernel<true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
     else pc::lo_run_kernel<false><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
   } else {
     // large configurations: grid-wide phases, one drive and one RK4 launch per causal block of the
@@ -1346,7 +1359,8 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     const unsigned rgrid = (unsigned)((nbn + 127) / 128);
     if (mixed) pc::lo_init_kernel<true><<<rgrid, 128, 0, st>>>(a, K);
     else pc::lo_init_kernel<false><<<rgrid, 128, 0, st>>>(a, K);
-    if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
+    if (mixed && a.near_L > 0.f) pc::lo_drive_kernel<true, true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
+    else if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
     else pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
     pc::lo_start_kernel<<<rgrid, 128, 0, st>>>(a);
     if (n_steps > 0) {
@@ -1360,7 +1374,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
         cudaGetLastError();
         for (int64_t n0 = 0; n0 < n_steps; n0 += K) {
           const int kb = (int)std::min<int64_t>(K, n_steps - n0);
-          if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
+          if (mixed && a.near_L > 0.f)
+            pc::lo_drive_kernel<true, true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
+          else if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
           else pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
           const unsigned wgrid = (unsigned)((nbn * 32 + 127) / 128);
           if (mixed) pc::lo_rk4_kernel<true><<<wgrid, 128, 0, st>>>(a, n0, kb);
