@@ -170,6 +170,21 @@ def oracle_lo_sample(threads=0, n_sep=12):
                 sample=f"{n_sep} of the 256 separations (2 oscillators each) x 40000 steps ({sec:.1f} s wall)")
 
 
+def oracle_cloud_sample(threads=0):
+    """The FP64 oracle on the 4096-oscillator cloud for one RK4 step (4096 dipole-steps), all host
+    cores (the receivers split across threads)."""
+    import oracle
+
+    threads = threads or len(os.sched_getaffinity(0))
+    cfg = W.cfg5(n_steps=1)
+    t0 = time.perf_counter()
+    r = oracle.dipoles_run(cfg, n_steps=1, nthreads=threads)
+    sec = time.perf_counter() - t0
+    assert r["status"] == oracle.OK
+    return dict(value=cfg.N / sec, unit="dipole-steps/s", cores=threads, kind="oracle",
+                sample=f"4096-oscillator cloud, 1 of its 20000 steps ({sec:.1f} s wall)")
+
+
 def compare_cloud(pc, ctx, dev, n_steps):
     """The 4096-oscillator cloud (600 nm cube, 5 nm minimum spacing, random axes) over n_steps in
     both precisions with the Eq. KE fit: run times, and the mixed path's total-energy trace,
@@ -569,6 +584,7 @@ def main():
             oracle.build()
             line["cpu_baseline"] = oracle_sample()
             line["cpu_baseline_lo"] = oracle_lo_sample()
+            line["cpu_baseline_cloud"] = oracle_cloud_sample()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
