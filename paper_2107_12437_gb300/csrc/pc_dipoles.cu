@@ -77,6 +77,20 @@ constexpr int kDipF = 12;
 
 __device__ __forceinline__ size_t bidx(const RunArgs &a, int b, int i) { return (size_t)b * a.N + i; }
 
+// double -> float rounded to nearest (ties away from zero) from the bits, on the integer units: the
+// conversion instruction issues to this GPU's narrow float64 unit, the bottleneck of the per-step
+// path of small configurations.  Magnitudes below the float range flush to zero, above it go to
+// infinity (the scaled history values stay far from both).
+__device__ __forceinline__ float dbl2flt(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return __int_as_float((int)sign);
+  if (e >= 255) return __int_as_float((int)(sign | 0x7f800000u));
+  const unsigned m = (unsigned)((b >> 29) & 0x7fffffu), r = (unsigned)((b >> 28) & 1u);
+  return __int_as_float((int)((sign | ((unsigned)e << 23) | m) + r));
+}
+
 // One RK4 step of d'' + g0 d' + w2 d = qm E (Eq. LO_equation) on y = (d, d') with stage fields
 // e1 (t), e2 (t + dt/2, both middle stages) and e4 (t + dt).
 __device__ __forceinline__ void rk4_step(double y0, double y1, double e1, double e2, double e4, double g0, double w2,
@@ -170,7 +184,7 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
     a.ddd[bi * S + n + 1] = ydd;
     if (MIXED)
       a.H32[bi * S + n + 1] =
-          make_float4((float)(yn0 * T[kTabC + 4]), (float)(yn1 * T[kTabC + 5]), (float)(ydd * T[kTabC + 6]), 0.f);
+          make_float4(dbl2flt(yn0 * T[kTabC + 4]), dbl2flt(yn1 * T[kTabC + 5]), dbl2flt(ydd * T[kTabC + 6]), 0.f);
     if (a.Ed) a.Ed[bi * S + n + 1] = e4;
     if (a.Ehalf) a.Ehalf[bi * a.n_steps + n] = e2;
     if (a.energy) a.energy[bi * S + n + 1] = T[kTabC + 7] * (w2 * yn0 * yn0 + yn1 * yn1);
@@ -335,8 +349,10 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   const int nst = ns > 0 ? ns : 1;
   const int slots = 32 / nst;
   const int s = lane % nst, m = lane / nst;
-  const double stage = ns > 0 ? 0.5 * (s + 1) : 0.0;
-  const float stage_f = (float)stage;  // converted once: conversions issue to the float64 unit
+  const double stage = ns > 0 ? 0.5 * (s + 1) : 0.0;  // the float64 drive's
+  // float(s + 1) from the bits (exact below 2^23): conversion instructions issue to the narrow
+  // float64 unit
+  const float stage_f = ns > 0 ? 0.5f * (__int_as_float(0x4B000000 | (s + 1)) - 8388608.f) : 0.f;
   double accd = 0.0;
   float accf = 0.f, comp = 0.f;
   if (m < slots) {
@@ -369,13 +385,26 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       }
     }
   }
-  double mine = MIXED ? (double)accf * a.e_unit + accd : accd;
-  sh[lane] = (m < slots) ? mine : 0.0;
-  __syncwarp();
-  if (lane < nst) {
-    double t = 0.0;
-    for (int mm = 0; mm < slots; ++mm) t += sh[mm * nst + lane];
-    dst[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = t;
+  if (MIXED && !NEAR) {
+    // the slots' float32 sums added in float32, one conversion per stage (conversions and float64
+    // arithmetic issue to the narrow float64 unit)
+    float *shf = reinterpret_cast<float *>(sh);
+    shf[lane] = (m < slots) ? accf : 0.f;
+    __syncwarp();
+    if (lane < nst) {
+      float t = 0.f;
+      for (int mm = 0; mm < slots; ++mm) t += shf[mm * nst + lane];
+      dst[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = (double)t * a.e_unit;
+    }
+  } else {
+    double mine = MIXED ? (double)accf * a.e_unit + accd : accd;
+    sh[lane] = (m < slots) ? mine : 0.0;
+    __syncwarp();
+    if (lane < nst) {
+      double t = 0.0;
+      for (int mm = 0; mm < slots; ++mm) t += sh[mm * nst + lane];
+      dst[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = t;
+    }
   }
   __syncwarp();
 }
