@@ -71,7 +71,7 @@ struct RunArgs {
 // this GPU): gamma0, omega0^2, q^2/m, the largest charge-speed factor, 1/(q L), 1/(q c), dt/(q c),
 // m/(2 q^2), and the charges' signed offsets per unit moment m2/((m1+m2) q), -m1/((m1+m2) q)
 constexpr int kTabC = 4 * 16 + 6;
-constexpr int kTab = kTabC + 10;
+constexpr int kTab = kTabC + 11;
 
 constexpr int kDipF = 12;
 
@@ -139,6 +139,7 @@ __device__ void rk4_table(const RunArgs &a, size_t bi) {
   T[kTabC + 7] = m / (2.0 * q * q);
   T[kTabC + 8] = m2 / (m1 + m2) / q;
   T[kTabC + 9] = -m1 / (m1 + m2) / q;
+  T[kTabC + 10] = a.v_max / T[kTabC + 3];  // the largest |d'| the velocity guard allows
 }
 
 // The kb steps of a causal block at once, one lane per step: with every stage field of the block
@@ -153,7 +154,7 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
   const size_t bi = bidx(a, b, i);
   double *Es = a.Es + bi * (2 * kMaxBlock + 1);
   const double *T = a.rk4tab + bi * kTab;
-  const double g0 = T[kTabC + 0], w2 = T[kTabC + 1], qm = T[kTabC + 2], vfac = T[kTabC + 3];
+  const double g0 = T[kTabC + 0], w2 = T[kTabC + 1], qm = T[kTabC + 2];
   const double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
   double vx = 0.0, vy = 0.0, e2 = 0.0, e4 = 0.0;
   if (lane < kb) {
@@ -183,12 +184,13 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
     a.dd[bi * S + n + 1] = yn1;
     a.ddd[bi * S + n + 1] = ydd;
     if (MIXED)
-      a.H32[bi * S + n + 1] =
-          make_float4(dbl2flt(yn0 * T[kTabC + 4]), dbl2flt(yn1 * T[kTabC + 5]), dbl2flt(ydd * T[kTabC + 6]), 0.f);
+      // the float32 mirror scaled in float32 (one rounding more than scaling in float64: below the
+      // mirror's own rounding budget), the values converted on the integer units
+      a.H32[bi * S + n + 1] = make_float4(dbl2flt(yn0) * dbl2flt(T[kTabC + 4]), dbl2flt(yn1) * dbl2flt(T[kTabC + 5]),
+                                          dbl2flt(ydd) * dbl2flt(T[kTabC + 6]), 0.f);
     if (a.Ed) a.Ed[bi * S + n + 1] = e4;
     if (a.Ehalf) a.Ehalf[bi * a.n_steps + n] = e2;
-    if (a.energy) a.energy[bi * S + n + 1] = T[kTabC + 7] * (w2 * yn0 * yn0 + yn1 * yn1);
-    bad = fabs(yn1) * vfac > a.v_max;
+    bad = fabs(yn1) > T[kTabC + 10];
   }
   if (__any_sync(0xffffffffu, bad)) {
     if (lane == 0) set_status(a.status, PC_ERR_VELOCITY);
@@ -684,6 +686,18 @@ __global__ void lo_advance_kernel(const RunArgs a, cudaGraphConditionalHandle lo
 // ------------------------------------------------------------------------------------------------
 // kinetic-energy series for the fit
 // ------------------------------------------------------------------------------------------------
+// Eq. dipoleE of every history sample, E = m (w0^2 d^2 + d'^2) / (2 q^2), after the run (off the
+// per-block path of the time loop)
+__global__ void energy_kernel(const RunArgs a) {
+  const int64_t S = a.n_steps + 1;
+  const int64_t n = (int64_t)a.B * a.N * S;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const double *T = a.rk4tab + (idx / S) * kTab;
+    const double x = a.d[idx], v = a.dd[idx];
+    a.energy[idx] = T[kTabC + 7] * (T[kTabC + 1] * x * x + v * v);
+  }
+}
+
 __global__ void ke_series_kernel(const RunArgs a, double *ke) {
   const int64_t S = a.n_steps + 1;
   const int64_t n = (int64_t)a.B * a.N * S;
@@ -1415,6 +1429,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
       }
     }
   }
+  if (a.energy) pc::energy_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a);
   if (opts->fit) {
     double *ke = (double *)ke_base;
     pc::ke_series_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, ke);
