@@ -125,6 +125,20 @@ def test_zero_steps_and_argument_errors(ctx, prec, N):
     with pytest.raises(pc.PcError) as ei:
         pc.pc_dipoles_run(ctx, dp, -cfg.dt, 4, precision=prec)
     assert ei.value.status == pc.capi.PC_ERR_ARG
+    if prec == pc.PC_MIXED:
+        # 32-bit sample indices of the mixed drive: a run of 2^30 steps or more is an argument
+        # error before anything is touched (the output arrays here are short)
+        import ctypes
+
+        buf = [torch.empty((1, N, 1), dtype=torch.float64, device="cuda") for _ in range(3)]
+        d = pc.capi.PcDipoles(B=1, N=N, origin=pc.capi._ptr(dp.origin), axis=pc.capi._ptr(dp.axis),
+                              q=pc.capi._ptr(dp.q), m1=pc.capi._ptr(dp.m1), m2=pc.capi._ptr(dp.m2),
+                              omega0=pc.capi._ptr(dp.omega0), d0=pc.capi._ptr(dp.d0))
+        opts = pc.capi.PcRunOpts(v_max=0.0, ed_mode=0, fit=0, first_index=0, precision=pc.PC_MIXED)
+        ro = pc.capi.PcRunOut(d=pc.capi._ptr(buf[0]), d_dot=pc.capi._ptr(buf[1]), d_ddot=pc.capi._ptr(buf[2]))
+        st = ctx.lib.pc_dipoles_run(ctx.handle, ctypes.byref(d), float(cfg.dt), 1 << 30, ctypes.byref(opts),
+                                    ctypes.byref(ro), None)
+        assert st == pc.capi.PC_ERR_ARG
 
 
 @pytest.mark.parametrize("gamma", [0.0, 2e7, 3e10])

@@ -238,6 +238,24 @@ def test_bad_arguments(ctx, cfg1_data):
         pc.pc_fields(ctx, points=ptd, times=[1e-14])  # no sources
 
 
+def test_mixed_rejects_histories_beyond_32bit_indices(ctx):
+    # the mixed kernels index history samples with 32-bit integers: a history longer than 2^30
+    # samples is an argument error before anything is read (the arrays here are short: the call
+    # must not touch them)
+    import ctypes
+
+    dp, g, z, times = W.cfg2(n_grid=8, n_frames=1)
+    dpd = pc.dipoles_to_device(dp)
+    pts = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    out = pc.capi.alloc_field_out(4, 1, pc.PC_MIXED)
+    dps = pc.capi._dipoles_struct(dpd)
+    dps.S = (1 << 30) + 1
+    tarr = (ctypes.c_double * 1)(float(times[0]))
+    st = ctx.lib.pc_fields(ctx.handle, None, ctypes.byref(dps), pc.capi._ptr(pts), 4, tarr, 1, pc.PC_TOTAL,
+                           pc.PC_MIXED, 0.0, ctypes.byref(pc.capi._out_struct(out)), None)
+    assert st == pc.capi.PC_ERR_ARG
+
+
 def test_many_frames_split_launches(ctx):
     # more than 32 times per call: the host splits the launch; frames stay in order
     ch, pts, _ = W.cfg1()
