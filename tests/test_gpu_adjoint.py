@@ -130,6 +130,25 @@ def test_mixed_forward_adjoint(ctx):
         pc.capi._check(st, "pc_dipoles_rates_adjoint")
 
 
+def test_ring_full_size_vs_finite_differences(ctx):
+    # the 256-oscillator ring at full length (20 000 steps): adjoint gradients of the summed final
+    # energies against central differences of the float64 forward for sampled parameters (two
+    # omega0, two d0 at 1e-6 relative; two origin coordinates at 1e-7 relative, which keeps the
+    # delays from crossing history samples)
+    cfg = W.cfg4()
+    w = np.ones((cfg.B, cfg.N)) / (0.5 * (W.M_E / 2) * float(cfg.omega0.mean()) ** 2 * 1e-22)
+    g = _adjoint(ctx, cfg, w)
+    for name, idxs, rel in (("omega0", ((0, 3), (0, 200)), 1e-6), ("d0", ((0, 17), (0, 128)), 1e-6),
+                            ("origin", ((0, 5, 0), (0, 90, 1)), 1e-7)):
+        adj, fd = [], []
+        for idx in idxs:
+            h = rel * (float(np.abs(getattr(cfg, name)[idx])) if name != "origin" else 200e-9)
+            fd.append((_loss_gpu(ctx, _perturbed(cfg, name, idx, h), w) -
+                       _loss_gpu(ctx, _perturbed(cfg, name, idx, -h), w)) / (2 * h))
+            adj.append(g[name][idx])
+        _check(np.array(adj), np.array(fd), 1e-4)
+
+
 def test_isolated_dipole_gradient_closed_form(ctx):
     # a single LO decays freely: E(T) from the RK4 recurrence alone; d0 enters linearly in d(T),
     # so dE(T)/dd0 = 2 E(T)/d0 exactly
