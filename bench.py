@@ -74,6 +74,23 @@ def whole_job_rate(units_per_rank, seconds_per_rank, world, dist=None, device="c
     return world * units_per_rank / max_over_ranks(seconds_per_rank, dist, device)
 
 
+def gpu_local_cpus(dev):
+    """The host CPUs attached to the GPU's PCI device (sysfs local_cpulist), or None."""
+    import torch
+
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (pr.pci_domain_id, pr.pci_bus_id,
+                                                                       pr.pci_device_id)
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        return cpus & set(os.sched_getaffinity(0)) or None
+    except Exception:
+        return None
+
+
 def rank_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
@@ -363,9 +380,17 @@ def main():
     avg_ms = total_ms / args.steps
 
     # ---- end to end through the C ABI with host buffers ----
+    # the page-locked buffers are placed (first touch) on the memory of the CPUs attached to the
+    # GPU: run on those CPUs while allocating and copying, as a caller would
+    cpus_all = set(os.sched_getaffinity(0))
+    cpus_gpu = gpu_local_cpus(dev)
+    if cpus_gpu:
+        os.sched_setaffinity(0, cpus_gpu)
     host_in = {k: getattr(dp, k).copy() for k in ("origin", "axis", "q", "m1", "m2", "d", "d_dot", "d_ddot")}
     pin_in = {k: torch.from_numpy(v).pin_memory() for k, v in host_in.items()}
     pin_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    for v in pin_out.values():
+        v.zero_()  # first touch by the bound thread
     h2d = sum(v.numel() * v.element_size() for v in pin_in.values())
     d2h = sum(v.numel() * v.element_size() for v in out.values())
 
@@ -388,6 +413,8 @@ def main():
         e2e_step()
     e2e_sec = (time.perf_counter() - t0) / n_e2e
     e2e_value = whole_job_rate(pairs_per_step, e2e_sec, world, dist, dev)
+    os.sched_setaffinity(0, cpus_all)
+    del pin_out, pin_in
 
     # ---- roofline of the field kernel (float32 ALU) ----
     fp32_fma, fp64_fma = pc.pc_alu_peaks(ctx)
@@ -418,7 +445,8 @@ def main():
                    "l2": "flushed between steps (256 MB write); outputs 2.7 GB > L2"},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
-        "e2e": {"value": e2e_value, "unit": "LW pair evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "LW pair evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "host_cpus": f"{len(cpus_gpu)} GPU-local" if cpus_gpu else "unbound"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": "fields_mixed2_kernel" if tile_rows * tile_cols > 256 else "fields_mixed_kernel",
