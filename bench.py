@@ -395,8 +395,8 @@ def main():
     d2h = sum(v.numel() * v.element_size() for v in out.values())
 
     def e2e_step():
-        # host inputs to the device, then the library's host-output entry point: it computes the
-        # frames in chunks and copies each chunk back while the next one computes
+        # host inputs to the device, then the library's host-output entry point: the outputs are
+        # page-locked, so the kernels store the fields into host memory as they compute them
         dev_in = {k: v.to(dev, non_blocking=True) for k, v in pin_in.items()}
         from types import SimpleNamespace
 

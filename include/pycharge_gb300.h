@@ -187,13 +187,15 @@ pc_status pc_set_plane_tiling(pc_ctx *ctx, const pc_plane_tiling *tiling);
 
 /*
  * pc_fields_to_host / pc_fields_plane_to_host -- pc_fields / pc_fields_plane with the outputs
- * delivered to HOST memory: out_host holds host pointers ([T][P][...] as in pc_field_out).  The
- * frames are computed in chunks of about 256 MB of outputs into two alternating device buffers
+ * delivered to HOST memory: out_host holds host pointers ([T][P][...] as in pc_field_out), each
+ * covering its whole array.  When every requested output is page-locked (cudaHostAlloc,
+ * cudaHostRegister) and mapped for the device (always so under unified addressing), the kernels
+ * store the fields into them directly, so the transfer runs inside the computation.  Otherwise
+ * the frames are computed in chunks of about 256 MB of outputs into two alternating device buffers
  * owned by the context, and each chunk is copied to the host on a second stream while the next
- * chunk computes, so the copies overlap the computation.  For the copies to run asynchronously the
- * host buffers must be page-locked (cudaHostAlloc / cudaHostRegister); pageable buffers still
- * work, with the copies serialized.  The call returns when every copy has landed.  Sources and
- * points stay on the device.  Errors: those of pc_fields.
+ * chunk computes; with pageable buffers those copies are serialized.  The results are identical
+ * in both modes.  The call returns when every output has landed.  Sources and points stay on the
+ * device.  Errors: those of pc_fields.
  */
 pc_status pc_fields_to_host(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_sources *dp, const double *points,
                             int64_t P, const double *times, int32_t T, int32_t kind, int32_t precision,

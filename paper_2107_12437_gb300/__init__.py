@@ -36,5 +36,6 @@ from .capi import (  # noqa: F401
     pc_set_plane_tiling,
     pc_fields_plane,
     pc_fields_plane_to_host,
+    pc_fields_to_host,
     pc_ke_fit,
 )

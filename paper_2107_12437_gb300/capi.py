@@ -322,16 +322,34 @@ def pc_set_plane_tiling(ctx, tile_rows, tile_cols, sources_per_stage=64):
     _check(ctx.lib.pc_set_plane_tiling(ctx.handle, ctypes.byref(t)), "pc_set_plane_tiling")
 
 
-def alloc_host_field_out(P, T, precision, which=("E", "B", "phi", "A", "mask")):
-    """Page-locked host outputs for pc_fields_plane_to_host / pc_fields_to_host."""
+def alloc_host_field_out(P, T, precision, which=("E", "B", "phi", "A", "mask"), pinned=True):
+    """Host outputs for pc_fields_plane_to_host / pc_fields_to_host: page-locked (the kernels store
+    into them directly) or, with pinned=False, pageable (filled by chunked copies)."""
     dt = torch.float64 if precision == PC_F64 else torch.float32
     shapes = {"E": (T, P, 3), "B": (T, P, 3), "phi": (T, P), "A": (T, P, 3), "mask": (T, P)}
-    return {k: torch.empty(shapes[k], dtype=torch.uint8 if k == "mask" else dt, pin_memory=True) for k in which}
+    return {k: torch.empty(shapes[k], dtype=torch.uint8 if k == "mask" else dt, pin_memory=pinned) for k in which}
+
+
+def pc_fields_to_host(ctx, charges=None, dipoles=None, points=None, times=(0.0,), kind=PC_TOTAL, precision=PC_F64,
+                      r_excl=0.0, out=None, stream=None):
+    """pc_fields_to_host: points [P][3] float64 CUDA tensor, outputs host tensors (page-locked by
+    default)."""
+    P = int(points.shape[0])
+    T = len(times)
+    o = alloc_host_field_out(P, T, precision) if out is None else out
+    tarr = (_f64 * T)(*[float(t) for t in times])
+    chs = _charges_struct(charges)
+    dps = _dipoles_struct(dipoles)
+    st = ctx.lib.pc_fields_to_host(ctx.handle, ctypes.byref(chs) if chs else None,
+                                   ctypes.byref(dps) if dps else None, _ptr(points), P, tarr, T, kind, precision,
+                                   float(r_excl), ctypes.byref(_host_out_struct(o)), _stream(stream))
+    _check(st, "pc_fields_to_host")
+    return o
 
 
 def pc_fields_plane_to_host(ctx, charges=None, dipoles=None, origin=(0, 0, 0), eu=(1, 0, 0), ev=(0, 1, 0), nu=1,
                             nv=1, times=(0.0,), kind=PC_TOTAL, precision=PC_F64, r_excl=0.0, out=None, stream=None):
-    """pc_fields_plane_to_host: sources on the device, outputs (page-locked host tensors) on the host."""
+    """pc_fields_plane_to_host: sources on the device, outputs host tensors (page-locked by default)."""
     T = len(times)
     o = alloc_host_field_out(nu * nv, T, precision) if out is None else out
     pl = PcPlane(origin=(_f64 * 3)(*origin), eu=(_f64 * 3)(*eu), ev=(_f64 * 3)(*ev), nu=nu, nv=nv)

@@ -1152,8 +1152,33 @@ static void launch_mixed_list(const Launch &L, dim3 grid, int kind, cudaStream_t
   else fields_mixed_kernel<PC_RADIATION, true, kChunk><<<grid, kMixThreads, 0, st>>>(L, 1);
 }
 
-// Host outputs: frames are computed in chunks into two device buffers that alternate, and each
-// chunk is copied to the host on a second stream while the next chunk computes.
+// Host outputs that are page-locked are mapped into the device's address space (unified
+// addressing): the kernels store into them directly and the stores reach host memory while the
+// computation runs.  Returns false (leaving `dev` as it was) if any requested output is not
+// page-locked host memory the device can address.
+static bool mapped_host_outputs(const pc_field_out *out, Outs &dev) {
+  const void *h[5] = {out->E, out->B, out->phi, out->A, out->mask};
+  void *d[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int k = 0; k < 5; ++k) {
+    if (!h[k]) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h[k]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    d[k] = a.devicePointer;
+  }
+  dev.E = d[0];
+  dev.B = d[1];
+  dev.phi = d[2];
+  dev.A = d[3];
+  dev.mask = (uint8_t *)d[4];
+  return true;
+}
+
+// Other host outputs: frames are computed in chunks into two device buffers that alternate, and
+// each chunk is copied to the host on a second stream while the next chunk computes.
 struct HostPipe {
   bool on = false;
   int32_t frames = 1;        // frames per chunk
@@ -1271,11 +1296,11 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
   const size_t b_vec = (size_t)P * 3 * elt, b_sca = (size_t)P * elt, b_msk = (size_t)P;
   HostPipe hp;
   char *slot_base[2] = {nullptr, nullptr};
-  if (to_host) {
+  if (to_host && !out->E && !out->B && !out->A && !out->phi && !out->mask) return end_call(ctx, st);
+  if (to_host && !mapped_host_outputs(out, L.out)) {
     hp.on = true;
     hp.bytes_frame = (out->E ? b_vec : 0) + (out->B ? b_vec : 0) + (out->A ? b_vec : 0) + (out->phi ? b_sca : 0) +
                      (out->mask ? b_msk : 0);
-    if (hp.bytes_frame == 0) return end_call(ctx, st);
     const size_t target = (size_t)256 << 20;  // about 256 MB per chunk
     hp.frames = (int32_t)std::max<size_t>(1, std::min<size_t>((size_t)kMaxT, target / hp.bytes_frame));
     const size_t slot = hp.bytes_frame * hp.frames;

@@ -268,23 +268,31 @@ def test_many_frames_split_launches(ctx):
 
 
 def test_plane_to_host_matches_device_outputs(ctx):
-    # 1024 x 2048 points, 5 frames: 86 MB of float32 outputs per frame, so the host pipeline runs
-    # three chunks (two frames each, the last one short) through its two alternating buffers
+    # 1024 x 2048 points, 5 frames, 86 MB of float32 outputs per frame.  Page-locked outputs are
+    # stored by the kernels directly; pageable ones go through the chunked copies (three chunks
+    # of two frames each, the last one short, through the two alternating device buffers)
     dp, g, z, times = W.cfg2()
     dpd = pc.dipoles_to_device(dp)
     step = float(g[1] - g[0])
     kw = dict(dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=1024, nv=2048,
               times=[float(t) for t in times[:5]], precision=pc.PC_MIXED)
     dev = pc.pc_fields_plane(ctx, **kw)
-    host = pc.pc_fields_plane_to_host(ctx, **kw)
-    for k in ("E", "B", "phi", "A", "mask"):
-        assert torch.equal(host[k], dev[k].cpu()), k
-    # float64 outputs and a subset of outputs
+    for pinned in (True, False):
+        out = pc.capi.alloc_host_field_out(1024 * 2048, 5, pc.PC_MIXED, pinned=pinned)
+        for v in out.values():
+            v.fill_(7)  # nothing of the previous contents may survive
+        host = pc.pc_fields_plane_to_host(ctx, out=out, **kw)
+        for k in ("E", "B", "phi", "A", "mask"):
+            assert torch.equal(host[k], dev[k].cpu()), (k, pinned)
+    # float64 outputs and a subset of outputs; one page-locked and one pageable output take the
+    # chunked copies for both
     kw64 = dict(kw, nu=64, precision=pc.PC_F64)
     dev64 = pc.pc_fields_plane(ctx, **kw64)
-    out = pc.capi.alloc_host_field_out(64 * 2048, 5, pc.PC_F64, which=("E", "phi"))
-    host64 = pc.pc_fields_plane_to_host(ctx, out=out, **kw64)
-    assert torch.equal(host64["E"], dev64["E"].cpu()) and torch.equal(host64["phi"], dev64["phi"].cpu())
+    for pins in ((True, True), (False, False), (True, False)):
+        out = {k: pc.capi.alloc_host_field_out(64 * 2048, 5, pc.PC_F64, which=(k,), pinned=p)[k]
+               for k, p in zip(("E", "phi"), pins)}
+        host64 = pc.pc_fields_plane_to_host(ctx, out=out, **kw64)
+        assert torch.equal(host64["E"], dev64["E"].cpu()) and torch.equal(host64["phi"], dev64["phi"].cpu()), pins
 
 
 def test_plane_to_host_many_frames_and_empty(ctx):
@@ -296,10 +304,31 @@ def test_plane_to_host_many_frames_and_empty(ctx):
     kw = dict(dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=16, nv=256, times=tt,
               precision=pc.PC_MIXED)
     dev = pc.pc_fields_plane(ctx, **kw)
-    host = pc.pc_fields_plane_to_host(ctx, **kw)
-    assert torch.equal(host["E"], dev["E"].cpu()) and torch.equal(host["mask"], dev["mask"].cpu())
+    for pinned in (True, False):
+        out = pc.capi.alloc_host_field_out(16 * 256, 40, pc.PC_MIXED, pinned=pinned)
+        host = pc.pc_fields_plane_to_host(ctx, out=out, **kw)
+        assert torch.equal(host["E"], dev["E"].cpu()) and torch.equal(host["mask"], dev["mask"].cpu()), pinned
     empty = pc.pc_fields_plane_to_host(ctx, **dict(kw, nu=0))
     assert empty["E"].shape == (40, 0, 3)
+
+
+def test_list_to_host_matches_device_outputs(ctx):
+    # point lists with host outputs, both precisions, page-locked and pageable, 20 frames (two
+    # launches of the mixed path) on a ragged 1000 points
+    dp, g, z, times = W.cfg2()
+    dpd = pc.dipoles_to_device(dp)
+    rng = np.random.default_rng(5)
+    pts = torch.tensor(np.c_[rng.uniform(0, 1e-6, (1000, 2)), np.full(1000, z)], dtype=torch.float64,
+                       device="cuda")
+    tt = [float(t) for t in np.linspace(times[0], times[-1], 20)]
+    for prec in (pc.PC_MIXED, pc.PC_F64):
+        kw = dict(dipoles=dpd, points=pts, times=tt, precision=prec)
+        dev = pc.pc_fields(ctx, **kw)
+        for pinned in (True, False):
+            out = pc.capi.alloc_host_field_out(1000, 20, prec, pinned=pinned)
+            host = pc.pc_fields_to_host(ctx, out=out, **kw)
+            for k in ("E", "B", "phi", "A", "mask"):
+                assert torch.equal(host[k], dev[k].cpu()), (k, prec, pinned)
 
 
 def test_autotuned_tile_shape_keeps_parity(ctx):
