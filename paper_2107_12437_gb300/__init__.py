@@ -32,6 +32,7 @@ from .capi import (  # noqa: F401
     pc_dipoles_run,
     pc_dipoles_run_moving,
     pc_fields,
+    pc_fields_noalloc,
     pc_fields_param,
     pc_set_plane_tiling,
     pc_fields_plane,
