@@ -202,9 +202,10 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
 }
 
 // Contribution of dipole j to the driving field of receiver i at time u (steps), history 0..nv.
-// float64: both charges per charge (Eqs. r_1, r_2, E); returns p_i . E.
+// float64: charge by charge (Eqs. r_1, r_2, E), charges sg0 .. sg1 - 1 (0 = +q, 1 = -q); returns
+// p_i . E.
 __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int64_t kg_fixed,
-                                 int *err) {
+                                 int *err, int sg0 = 0, int sg1 = 2) {
   const int64_t S = a.n_steps + 1;
   const double cdt = kC * a.dt;
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
@@ -237,7 +238,7 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
     kg = (int64_t)floor(u - sqrt(dot3(dv, dv)) / cdt);
   }
   double E[3] = {0.0, 0.0, 0.0};
-  for (int sg = 0; sg < 2; ++sg) {
+  for (int sg = sg0; sg < sg1; ++sg) {
     tr.w = Tj[kTabC + 8 + sg];
     double p0[3], v[3] = {0, 0, 0}, ac[3] = {0, 0, 0};
     if (nv == 0) {
@@ -357,33 +358,48 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   const float stage_f = ns > 0 ? 0.5f * (__int_as_float(0x4B000000 | (s + 1)) - 8388608.f) : 0.f;
   double accd = 0.0;
   float accf = 0.f, comp = 0.f;
+  // fewer float64 sources than half the slots (small configurations): the two charges of each
+  // take two slots, which halves the serial float64 chain of a slot
+  const bool split = (!MIXED || NEAR) && 2 * (j_hi - j_lo) <= slots;
+  // source j's charges sg0 .. sg1 - 1
+  auto source = [&](int j, int sg0, int sg1) {
+    if (j == i) return;
+    if (MIXED) {
+      // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
+      const size_t ij = (size_t)bidx(a, b, i) * a.N + j;
+      const int2 dl = a.delay[ij];
+      const float4 geo = a.pgeo[ij];
+      const float xs = stage_f - __int_as_float(dl.y);
+      float flf;
+      const int fl = Num<float>::floor_int(xs, flf);
+      if (NEAR && geo.x < a.near_L) {
+        // a near source whose radiative coupling float32 cannot resolve: the float64 pair
+        accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, (int)n0 - dl.x + fl, err, sg0, sg1);
+        return;
+      }
+      if (sg0 == 1) return;  // the float32 pair takes both charges at once
+      const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, geo, (int)n0 + 1, err);
+      // Kahan sum over sources
+      const float y = v - comp;
+      const float t = accf + y;
+      comp = (t - accf) - y;
+      accf = t;
+    } else {
+      // first guess: the sample of the centre's retarded time, n0 + stage - delay
+      const int2 dl = a.delay[(size_t)bidx(a, b, i) * a.N + j];
+      const int kg = (int)n0 - dl.x + Num<float>::floor_int(stage_f - __int_as_float(dl.y));
+      accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, kg, err, sg0, sg1);
+    }
+  };
   if (m < slots) {
-    for (int j = j_lo + m; j < j_hi; j += slots) {
-      if (j == i) continue;
-      if (MIXED) {
-        // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
-        const size_t ij = (size_t)bidx(a, b, i) * a.N + j;
-        const int2 dl = a.delay[ij];
-        const float4 geo = a.pgeo[ij];
-        const float xs = stage_f - __int_as_float(dl.y);
-        float flf;
-        const int fl = Num<float>::floor_int(xs, flf);
-        if (NEAR && geo.x < a.near_L) {
-          // a near source whose radiative coupling float32 cannot resolve: the float64 pair
-          accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, (int)n0 - dl.x + fl, err);
-          continue;
-        }
-        const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, geo, (int)n0 + 1, err);
-        // Kahan sum over sources
-        const float y = v - comp;
-        const float t = accf + y;
-        comp = (t - accf) - y;
-        accf = t;
-      } else {
-        // first guess: the sample of the centre's retarded time, n0 + stage - delay
-        const int2 dl = a.delay[(size_t)bidx(a, b, i) * a.N + j];
-        const int kg = (int)n0 - dl.x + Num<float>::floor_int(stage_f - __int_as_float(dl.y));
-        accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, kg, err);
+    if constexpr (MIXED && !NEAR) {
+      for (int j = j_lo + m; j < j_hi; j += slots) source(j, 0, 2);
+    } else {
+      // one loop, so that the float64 pair is inlined once
+      const int nh = split ? 2 * (j_hi - j_lo) : j_hi - j_lo;
+      for (int h = m; h < nh; h += slots) {
+        const int sg0 = split ? h & 1 : 0;
+        source(j_lo + (split ? h >> 1 : h), sg0, split ? sg0 + 1 : 2);
       }
     }
   }
