@@ -347,7 +347,7 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
 // ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.
 template <bool MIXED, bool NEAR = false>
 __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err,
-                            int j_lo, int j_hi, double *dst) {
+                            int j_lo, int j_hi, double *dst, int sgsel = -1) {
   const int lane = threadIdx.x & 31;
   const int nst = ns > 0 ? ns : 1;
   const int slots = 32 / nst;
@@ -360,7 +360,8 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   float accf = 0.f, comp = 0.f;
   // fewer float64 sources than half the slots (small configurations): the two charges of each
   // take two slots, which halves the serial float64 chain of a slot
-  const bool split = (!MIXED || NEAR) && 2 * (j_hi - j_lo) <= slots;
+  // (sgsel = 0 or 1: only that charge of every float64 source, the other taken by another warp)
+  const bool split = sgsel < 0 && (!MIXED || NEAR) && 2 * (j_hi - j_lo) <= slots;
   // source j's charges sg0 .. sg1 - 1
   auto source = [&](int j, int sg0, int sg1) {
     if (j == i) return;
@@ -398,8 +399,8 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       // one loop, so that the float64 pair is inlined once
       const int nh = split ? 2 * (j_hi - j_lo) : j_hi - j_lo;
       for (int h = m; h < nh; h += slots) {
-        const int sg0 = split ? h & 1 : 0;
-        source(j_lo + (split ? h >> 1 : h), sg0, split ? sg0 + 1 : 2);
+        const int sg0 = split ? h & 1 : (sgsel < 0 ? 0 : sgsel);
+        source(j_lo + (split ? h >> 1 : h), sg0, (split || sgsel >= 0) ? sg0 + 1 : 2);
       }
     }
   }
@@ -471,10 +472,16 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
   for (int64_t n0 = 0; n0 < a.n_steps; n0 += K) {
     if (s_stop) break;
     const int kb = (int)min((int64_t)K, a.n_steps - n0);
-    // phase A: all stage fields of the block
-    for (int i = warp; i < N; i += kRunWarps) {
+    // phase A: all stage fields of the block.  A float64 drive whose lanes are all taken while
+    // warps are idle (2 N <= kRunWarps < 2 N * 32 / (2 kb)) gives each charge of the sources its own
+    // warp: warp 2i + h sums charge h of receiver i's sources, h = 1 into Epart, added after (not
+    // in the mixed instantiations, whose registers it would raise)
+    const int nst = 2 * kb;
+    const bool xsplit = !MIXED && 2 * N <= kRunWarps && 2 * N > 32 / nst;
+    for (int w = warp; w < (xsplit ? 2 * N : N); w += kRunWarps) {
       int err = 0;
-      drive_phase<MIXED, NEAR>(a, b, i, n0, 2 * kb, sh[warp], &err, 0, N, a.Es);
+      drive_phase<MIXED, NEAR>(a, b, xsplit ? w >> 1 : w, n0, nst, sh[warp], &err, 0, N,
+                               (xsplit && (w & 1)) ? a.Epart : a.Es, xsplit ? w & 1 : -1);
       if (err) {
         set_status(a.status, err);
         s_stop = 1;
@@ -482,6 +489,13 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     }
     __syncthreads();
     if (s_stop) break;
+    if (xsplit) {
+      for (int t = threadIdx.x; t < N * nst; t += blockDim.x) {
+        const size_t o = bidx(a, b, t / nst) * (2 * kMaxBlock + 1) + 1 + t % nst;
+        a.Es[o] += a.Epart[o];
+      }
+      __syncthreads();
+    }
     // phase B: the kb RK4 steps of each receiver, one warp per receiver, one lane per step
     for (int i = warp; i < N; i += kRunWarps) {
       int stop = 0;
@@ -1325,7 +1339,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const size_t k_bytes = al(dp->B * sizeof(int));
   const size_t ke_bytes = opts->fit ? al(nbn * S * sizeof(double)) : 0;
   const bool grid = dp->N > pc::kSmallN;
-  const size_t part_bytes = grid ? al((size_t)pc::kMaxSplit * es_bytes) : 0;
+  // grid path: the source slices' partial stage fields; one configuration per CTA: the second
+  // charge's partial sums when the two charges run on two warps
+  const size_t part_bytes = grid ? al((size_t)pc::kMaxSplit * es_bytes) : es_bytes;
   const size_t blk_bytes = al(2 * sizeof(int64_t));
   const size_t tab_bytes = al(nbn * pc::kTab * sizeof(double));
   const size_t part_off = es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes + ke_bytes;
@@ -1363,7 +1379,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   if (delay_out) *delay_out = a.delay;  // valid until the context's next run
   a.kblock = (int *)(scr + es_bytes + h_bytes + f_bytes + dl_bytes);
   a.Ehalf = Ehalf;
-  a.Epart = nullptr;
+  a.Epart = (double *)(scr + part_off);
   a.nsplit = 1;
   a.blk = nullptr;
   a.rk4tab = (double *)(scr + tab_off);
