@@ -11,8 +11,8 @@ dipole-steps/s, the end-to-end number through the C ABI with host buffers, the r
 field kernel, clocks sampled during the timed region and the FP64 CPU oracle on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --profile fields_mixed_small|fields_mixed2_small|fields_f64_small|lo_small|ring_small|
-                            cloud_small|adj_small
+  python bench.py --profile fields_mixed_small|fields_mixed2_small|fields_f64_small|lo_small|lo_f64_small|
+                            ring_small|cloud_small|adj_small
                                                      (one small run for ncu)
 Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own copy of the workload
 (independent problems, no data-path collective), so scaling is weak.
@@ -285,7 +285,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", default=None,
                     choices=["fields_mixed_small", "fields_mixed2_small", "fields_f64_small", "lo_small",
-                             "ring_small", "cloud_small", "adj_small"])
+                             "lo_f64_small", "ring_small", "cloud_small", "adj_small"])
     ap.add_argument("--no-extra", action="store_true", help="skip the float64, oscillator and CPU legs")
     ap.add_argument("--compare-cloud", type=int, default=0, metavar="STEPS",
                     help="run the 4096-oscillator cloud for STEPS steps in both precisions and compare them")
@@ -322,10 +322,11 @@ def main():
         elif args.profile == "fields_f64_small":
             pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=64,
                                nv=2048, times=list(times[:1]), precision=pc.PC_F64)
-        elif args.profile == "lo_small":
-            # batched pairs, mixed: one persistent launch over 2000 steps
+        elif args.profile in ("lo_small", "lo_f64_small"):
+            # batched pairs, mixed or float64: one persistent launch over 2000 steps
             cfg, _ = W.cfg3(B=256, n_steps=2000)
-            pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=pc.PC_MIXED)
+            prec = pc.PC_MIXED if args.profile == "lo_small" else pc.PC_F64
+            pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=prec)
         elif args.profile in ("ring_small", "cloud_small"):
             # grid path, mixed, block loop launched from the host so that the profiler sees every
             # launch: the 256-oscillator ring over 200 steps (13 causal blocks), or the 4096-oscillator
