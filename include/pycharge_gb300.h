@@ -32,7 +32,9 @@ typedef enum {
   PC_ERR_VELOCITY = 4,  /* a dipole charge exceeded v_max (Sec. 3.2, default c/100) */
   PC_ERR_CAUSALITY = 5, /* dt exceeds a light-crossing time between dipoles (Sec. 3.2) */
   PC_ERR_NOCONV = 6,    /* the retarded-time solve or the energy fit did not converge */
-  PC_ERR_TIMEOUT = 7    /* a device-side wait exceeded its iteration limit */
+  PC_ERR_TIMEOUT = 7    /* reserved: no kernel of this library waits on another (every ordering
+                           between blocks goes through kernel or graph-node boundaries), so no
+                           call returns it */
 } pc_status;
 
 /* field kind, Sec. 3.2 (calculate_E / calculate_B select total, Coulomb or radiation field) */
@@ -72,7 +74,7 @@ typedef struct {
  */
 typedef struct {
   int32_t N;                /* number of dipoles (0 = none) */
-  int64_t S;                /* samples per dipole, >= 2 */
+  int64_t S;                /* samples per dipole, 2 <= S <= 2^30 */
   double t0, dt;
   const double *origin;     /* device [N][3] (m) */
   const double *axis;       /* device [N][3] unit vectors */
@@ -309,8 +311,9 @@ pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t S, double 
  *   16 * N * S_dipoles + 64 * N + 48 * M * S_charges + 24 * M  <=  16 MiB  (bytes),
  * otherwise the call returns PC_ERR_ARG without touching the device.
  * Set-up: the first call on a device resolves the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  The device used is
- * the caller's current device.
+ * with that device current; make that first call before any stream capture.  A failed lookup
+ * returns PC_ERR_CUDA and is retried by the next call.  The device used is the caller's current
+ * device; `points` must be device memory of that device (PC_ERR_ARG otherwise).
  * Every call shares the one array and leaves its contents behind: each call clears the status word
  * and rewrites the mirrors it reads, so calls in sequence are independent, but calls that overlap
  * on the GPU (other streams, other host threads) race on the array and must not be issued.

@@ -5,12 +5,13 @@ package.  It shares no code with the CUDA library (paper_2107_12437_gb300); both
 from workloads.py, which holds no method arithmetic.
 
   * pc_oracle.c     retarded-time bisection, Lienard-Wiechert fields (Jackson and Griffiths forms),
-                    superposition, dipole charges, Lorentz-oscillator run (Algorithm 1, RK4)
+                    superposition, dipole charges, Lorentz-oscillator run (Algorithm 1, RK4); the
+                    field sum once more in binary128 (fields_x) for points where dipoles cancel
   * theory.py       closed forms used as pins: Coulomb, uniform motion, Hertzian dipole, Larmor,
                     free-space Green's function rates (App. A), exact classical pole
   * fit.py          Levenberg-Marquardt fit of the kinetic energy to Eq. KE
 
-Every function is FP64.  Parity pins live in tests/test_oracle_*.py.
+Every function is FP64 except fields_x (binary128 throughout).  Parity pins live in tests/test_oracle_*.py.
 """
 from __future__ import annotations
 
@@ -65,6 +66,7 @@ def lib():
         _lib.orc_sources_size.restype = ctypes.c_int64
         assert _lib.orc_sources_size() == ctypes.sizeof(_Sources), "oracle struct layout mismatch"
         _lib.orc_fields.restype = ctypes.c_int
+        _lib.orc_fields_x.restype = ctypes.c_int
         _lib.orc_retarded_delay.restype = ctypes.c_int
         _lib.orc_dipoles_run.restype = ctypes.c_int
         _lib.orc_dipoles_run_moving.restype = ctypes.c_int
@@ -137,6 +139,26 @@ def fields(points, times, charges=None, dipoles=None, kind=TOTAL, r_excl=0.0, nt
     return dict(E=E, B=B, A=A, phi=phi, mask=mask, status=st,
                 scale_charge=dict(E=scale[..., 0], B=scale[..., 1], phi=scale[..., 2], A=scale[..., 3]),
                 scale_source=dict(E=scale[..., 4], B=scale[..., 5], phi=scale[..., 6], A=scale[..., 7]))
+
+
+def fields_x(points, times, charges=None, dipoles=None, kind=TOTAL, r_excl=0.0, nthreads=0):
+    """fields() with every intermediate in binary128 (orc_fields_x): E, B, A [T][P][3], phi [T][P],
+    mask [T][P] and the status.  The +-q pair of a dipole no longer costs digits, so these are the
+    fields of the discrete history to float64 rounding.  Fixed dipole origins only."""
+    keep = _Keep()
+    s = _sources(charges, dipoles, keep)
+    pts = keep(np.asarray(points).reshape(-1, 3))
+    tms = keep(np.atleast_1d(times))
+    P, T = pts.shape[0], tms.shape[0]
+    E = np.zeros((T, P, 3))
+    B = np.zeros((T, P, 3))
+    A = np.zeros((T, P, 3))
+    phi = np.zeros((T, P))
+    mask = np.zeros((T, P), dtype=np.uint8)
+    st = lib().orc_fields_x(ctypes.byref(s), _ptr(pts), ctypes.c_int64(P), _ptr(tms), ctypes.c_int32(T),
+                            ctypes.c_int32(kind), ctypes.c_double(r_excl), _ptr(E), _ptr(B), _ptr(phi), _ptr(A),
+                            mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.c_int32(nthreads))
+    return dict(E=E, B=B, A=A, phi=phi, mask=mask, status=st)
 
 
 def retarded_delay(c, t, r, charges=None, dipoles=None):

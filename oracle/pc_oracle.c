@@ -17,6 +17,8 @@
  *   - superposition over all charges (Sec. 2.2);
  *   - dipole charges from the dipole moment (Sec. 2.3, Eqs. eff_mass, r_1, r_2), static for t <= 0
  *     (Sec. 3.2);
+ *   - the same field sum with every intermediate in binary128 (orc_fields_x), the reference for
+ *     points where the +-q charges of dipoles cancel by many digits;
  *   - the Lorentz-oscillator run of Algorithm 1 with the equation of motion Eq. LO_equation,
  *     RK4 in time, driving field E_d = p . E at the dipole origin from all other dipoles (Sec. 2.3,
  *     Sec. 3.2), energy Eq. dipoleE, velocity guard (Sec. 3.2, default c/100).
@@ -646,6 +648,231 @@ int orc_dipoles_run_moving(int32_t N, const double *origin, const double *axis, 
     }
   }
   free(ed_now); free(ed_half); free(ed_next);
+  return status;
+}
+
+/*
+ * ---------------------------------------------------------------------------------------------
+ * Extended precision: the same retarded-time bisection, linear interpolation of the history
+ * (Sec. 3.1), Jackson form (Eqs. V, A, E, B) and superposition (Sec. 2.2) as fields_at, with every
+ * intermediate in IEEE binary128 (113-bit significand; libgcc's software arithmetic on both the
+ * x86-64 and the aarch64 build).  The inputs are the same float64 samples, read exactly; the sums
+ * are rounded to float64 only at the end.  A dipole's two charges cancel by R/s in the sum (up to
+ * 1e7 near a dipole whose moment crosses zero), which costs the float64 evaluation that many
+ * digits; here the loss leaves ~1e-27 relative, so the result is the field of the discrete
+ * history to float64 rounding.  Fixed origins only.
+ * ---------------------------------------------------------------------------------------------
+ */
+typedef _Float128 xreal;
+
+/* square root: float64 estimate, then two Newton steps (each doubles the correct bits: 53 -> 106
+ * -> beyond the 113 of the format) */
+static xreal xsqrt(xreal a) {
+  if (!(a > 0)) return 0;
+  xreal x = (xreal)sqrt((double)a);
+  x = 0.5 * (x + a / x);
+  x = 0.5 * (x + a / x);
+  return x;
+}
+
+static xreal xdot3(const xreal *a, const xreal *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void xcross3(const xreal *a, const xreal *b, xreal *o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* charge_state in binary128: linear interpolation between the float64 samples (Sec. 3.1), dipole
+ * charges at R +- w (d/q) p (Eqs. r_1, r_2), at rest before the first sample (Sec. 3.2) */
+static int xcharge_state(const orc_sources *s, int c, xreal tp, xreal *qc, xreal p[3], xreal v[3], xreal a[3]) {
+  if (c < s->M) {
+    const double *P = s->pos + (int64_t)c * s->S * 3;
+    const double *V = s->vel + (int64_t)c * s->S * 3;
+    const double *A = s->acc + (int64_t)c * s->S * 3;
+    *qc = s->q[c];
+    xreal x = (tp - (xreal)s->t0) / (xreal)s->dt;
+    if (x < 0 && x > -1e-9) x = 0;
+    if (x > (xreal)(s->S - 1) && x < (xreal)(s->S - 1) + (xreal)1e-9) x = (xreal)(s->S - 1);
+    if (x < 0) {
+      if (!s->static_before) return ORC_ERR_HISTORY;
+      for (int i = 0; i < 3; ++i) { p[i] = P[i]; v[i] = 0; a[i] = 0; }
+      return ORC_OK;
+    }
+    int64_t k = (int64_t)x;
+    if (k >= s->S - 1) {
+      if (x > (xreal)(s->S - 1)) return ORC_ERR_HISTORY;
+      k = s->S - 2;
+    }
+    xreal th = x - (xreal)k;
+    for (int i = 0; i < 3; ++i) {
+      p[i] = (xreal)P[k * 3 + i] + th * ((xreal)P[(k + 1) * 3 + i] - (xreal)P[k * 3 + i]);
+      v[i] = (xreal)V[k * 3 + i] + th * ((xreal)V[(k + 1) * 3 + i] - (xreal)V[k * 3 + i]);
+      a[i] = (xreal)A[k * 3 + i] + th * ((xreal)A[(k + 1) * 3 + i] - (xreal)A[k * 3 + i]);
+    }
+    return ORC_OK;
+  }
+  int j = (c - s->M) / 2;
+  int neg = (c - s->M) % 2;
+  xreal m1 = s->m1[j], m2 = s->m2[j], q = s->qd[j];
+  const double *u = s->axis + 3 * j;
+  const double *R = s->origin + 3 * j;
+  const double *D = s->d + (int64_t)j * s->Sd;
+  const double *DV = s->d_dot + (int64_t)j * s->Sd;
+  const double *DA = s->d_ddot + (int64_t)j * s->Sd;
+  xreal dd, dv, da;
+  xreal x = (tp - (xreal)s->t0d) / (xreal)s->dtd;
+  if (x <= 0) {
+    dd = D[0]; dv = 0; da = 0;
+  } else {
+    int64_t last = s->Sd - 1;
+    if (x > (xreal)last && x < (xreal)last + (xreal)1e-9) x = (xreal)last;
+    int64_t k = (int64_t)x;
+    if (k >= last) {
+      if (x > (xreal)last) return ORC_ERR_HISTORY;
+      k = last - 1;
+    }
+    xreal th = x - (xreal)k;
+    dd = (xreal)D[k] + th * ((xreal)D[k + 1] - (xreal)D[k]);
+    dv = (xreal)DV[k] + th * ((xreal)DV[k + 1] - (xreal)DV[k]);
+    da = (xreal)DA[k] + th * ((xreal)DA[k + 1] - (xreal)DA[k]);
+  }
+  xreal w = neg ? -m1 / (m1 + m2) : m2 / (m1 + m2);
+  *qc = neg ? -q : q;
+  for (int i = 0; i < 3; ++i) {
+    p[i] = (xreal)R[i] + w * (dd / q) * (xreal)u[i];
+    v[i] = w * (dv / q) * (xreal)u[i];
+    a[i] = w * (da / q) * (xreal)u[i];
+  }
+  return ORC_OK;
+}
+
+static xreal xg_at(const orc_sources *s, int c, xreal t, const xreal r[3], xreal tp, int *st) {
+  xreal qc, p[3], v[3], a[3];
+  *st = xcharge_state(s, c, tp, &qc, p, v, a);
+  xreal D[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+  return (xreal)ORC_C * (t - tp) - xsqrt(xdot3(D, D));
+}
+
+/* bisection of g(t') = c (t - t') - |r - r_c(t')| (Eq. ret_t) as orc_retarded_time, to the
+ * resolution of binary128 */
+static int xretarded_time(const orc_sources *s, int c, xreal t, const xreal r[3], xreal *tp_out) {
+  int st;
+  int sampled = (c < s->M);
+  xreal t_first = sampled ? s->t0 : s->t0d;
+  xreal t_last = sampled ? (xreal)s->t0 + (xreal)(s->S - 1) * (xreal)s->dt
+                         : (xreal)s->t0d + (xreal)(s->Sd - 1) * (xreal)s->dtd;
+  xreal hi = (t < t_last) ? t : t_last;
+  xreal lo;
+  if (sampled && !s->static_before) {
+    lo = t_first;
+    if (lo > hi) return ORC_ERR_HISTORY;
+    xreal g = xg_at(s, c, t, r, lo, &st);
+    if (st) return st;
+    if (g < 0) return ORC_ERR_HISTORY;
+  } else {
+    xreal qc, p[3], v[3], a[3];
+    st = xcharge_state(s, c, (t < t_first) ? t : t_first, &qc, p, v, a);
+    if (st) return st;
+    xreal D[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+    lo = t - xsqrt(xdot3(D, D)) / (xreal)ORC_C * ((xreal)1 + (xreal)1e-12) - (xreal)1e-30;
+    if (lo > t_first) lo = t_first;
+    if (lo > hi) lo = hi;
+  }
+  if (hi < t) {
+    xreal g = xg_at(s, c, t, r, hi, &st);
+    if (st) return st;
+    if (g > 0) return ORC_ERR_HISTORY;
+    if (g == 0) { *tp_out = hi; return ORC_OK; }
+  }
+  for (int it = 0; it < 16000; ++it) {
+    xreal mid = (xreal)0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    xreal g = xg_at(s, c, t, r, mid, &st);
+    if (st) return st;
+    if (g >= 0) lo = mid; else hi = mid;
+  }
+  *tp_out = (xreal)0.5 * (lo + hi);
+  return ORC_OK;
+}
+
+/* lw_jackson in binary128 (Eqs. V, A, E, ECoulomb, Eradiation; A read as (v/c^2) phi) */
+static void xlw_jackson(xreal q, const xreal aR[3], const xreal v[3], const xreal acc[3], xreal Ec[3], xreal Er[3],
+                        xreal *phi, xreal A[3]) {
+  const xreal c = ORC_C, eps0 = ORC_EPS0, pi = ORC_PI;
+  xreal R = xsqrt(xdot3(aR, aR));
+  xreal n[3] = {aR[0] / R, aR[1] / R, aR[2] / R};
+  xreal beta[3] = {v[0] / c, v[1] / c, v[2] / c};
+  xreal bdot[3] = {acc[0] / c, acc[1] / c, acc[2] / c};
+  xreal kappa = 1 - xdot3(n, beta);
+  xreal b2 = xdot3(beta, beta);
+  xreal k = q / (4 * pi * eps0);
+  xreal nb[3] = {n[0] - beta[0], n[1] - beta[1], n[2] - beta[2]};
+  xreal k3 = kappa * kappa * kappa;
+  for (int i = 0; i < 3; ++i) Ec[i] = k * nb[i] * (1 - b2) / (k3 * R * R);
+  xreal w[3], nw[3];
+  xcross3(nb, bdot, w);
+  xcross3(n, w, nw);
+  for (int i = 0; i < 3; ++i) Er[i] = k * nw[i] / (c * k3 * R);
+  *phi = k / (kappa * R);
+  xreal mu0 = 1 / (eps0 * c * c);
+  for (int i = 0; i < 3; ++i) A[i] = mu0 * q * c / (4 * pi) * beta[i] / (kappa * R);
+}
+
+/*
+ * Fields on P points at T times as orc_fields (outputs rounded to float64), every step in binary128.
+ * Charges closer than r_excl at their retarded position are skipped and masked.
+ */
+int orc_fields_x(const orc_sources *s, const double *points, int64_t P, const double *times, int32_t T, int32_t kind,
+                 double r_excl, double *E, double *B, double *phi, double *A, uint8_t *mask, int32_t nthreads) {
+  if (kind < 0 || kind > 2 || P < 0 || T < 0 || s->org_pos || s->last_valid >= 0) return ORC_ERR_ARG;
+  int status = ORC_OK;
+  int64_t total = P * (int64_t)T;
+  int nc = orc_n_charges(s);
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int64_t idx = 0; idx < total; ++idx) {
+    int64_t f = idx / P, pidx = idx % P;
+    const xreal r[3] = {points[3 * pidx], points[3 * pidx + 1], points[3 * pidx + 2]};
+    const xreal t = times[f];
+    xreal e[3] = {0, 0, 0}, b[3] = {0, 0, 0}, aa[3] = {0, 0, 0}, ph = 0;
+    uint8_t mk = 0;
+    int st = ORC_OK;
+    for (int c = 0; c < nc && !st; ++c) {
+      xreal tp;
+      st = xretarded_time(s, c, t, r, &tp);
+      if (st) break;
+      xreal qc, p[3], v[3], ac[3];
+      st = xcharge_state(s, c, tp, &qc, p, v, ac);
+      if (st) break;
+      xreal aR[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+      xreal R = xsqrt(xdot3(aR, aR));
+      if (R <= (xreal)r_excl) { mk = 1; continue; }
+      xreal Ec[3], Er[3], phc, Ac[3], Ek[3], nE[3];
+      xlw_jackson(qc, aR, v, ac, Ec, Er, &phc, Ac);
+      for (int i = 0; i < 3; ++i)
+        Ek[i] = (kind == ORC_COULOMB) ? Ec[i] : (kind == ORC_RADIATION) ? Er[i] : Ec[i] + Er[i];
+      xreal n[3] = {aR[0] / R, aR[1] / R, aR[2] / R};
+      xcross3(n, Ek, nE);
+      for (int i = 0; i < 3; ++i) { e[i] += Ek[i]; b[i] += nE[i] / (xreal)ORC_C; aa[i] += Ac[i]; }
+      ph += phc;
+    }
+    for (int i = 0; i < 3; ++i) {
+      E[3 * idx + i] = (double)e[i];
+      B[3 * idx + i] = (double)b[i];
+      A[3 * idx + i] = (double)aa[i];
+    }
+    phi[idx] = (double)ph;
+    mask[idx] = mk;
+    if (st) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      if (status == ORC_OK) status = st;
+    }
+  }
+  (void)nthreads;
   return status;
 }
 

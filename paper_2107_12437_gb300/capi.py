@@ -630,21 +630,46 @@ def pc_alu_peaks(ctx, stream=None):
     return a.value, b.value
 
 
+def _check_noalloc_out(o, P, T, device):
+    """The caller's outputs of pc_fields_noalloc: float32 [T][P][3] / [T][P], uint8 mask [T][P],
+    contiguous, on the points' device."""
+    shapes = {"E": (T, P, 3), "B": (T, P, 3), "phi": (T, P), "A": (T, P, 3), "mask": (T, P)}
+    for k, t in o.items():
+        if k not in shapes or t is None:
+            continue
+        want = torch.uint8 if k == "mask" else torch.float32
+        if t.dtype != want or tuple(t.shape) != shapes[k] or not t.is_contiguous() or t.device != device:
+            raise ValueError(f"pc_fields_noalloc: output {k} must be a contiguous {want} tensor of shape "
+                             f"{shapes[k]} on {device}")
+
+
 def pc_fields_noalloc(charges=None, dipoles=None, points=None, times=(0.0,), kind=PC_TOTAL, r_excl=0.0, out=None,
                       stream=None):
-    """pc_fields_noalloc on the current device: mixed precision, no allocation inside the library.
+    """pc_fields_noalloc on the points' device: mixed precision, no allocation inside the library.
 
     `out` (float32 tensors, see alloc_field_out) should be allocated by the caller ahead of time.
+    Every source tensor must sit on the points' device.
     """
     lib = load()
+    dev = points.device
+    if dev.type != "cuda":
+        raise ValueError("pc_fields_noalloc: points must be a CUDA tensor")
+    for src in (charges, dipoles):
+        if src is None:
+            continue
+        for name, t in vars(src).items():
+            if isinstance(t, torch.Tensor) and t.device != dev:
+                raise ValueError(f"pc_fields_noalloc: source tensor {name} is on {t.device}, points on {dev}")
     P = int(points.shape[0])
     T = len(times)
-    o = alloc_field_out(P, T, PC_MIXED, points.device) if out is None else out
-    tarr = (_f64 * T)(*[float(t) for t in times])
-    chs = _charges_struct(charges)
-    dps = _dipoles_struct(dipoles)
-    st = lib.pc_fields_noalloc(ctypes.byref(chs) if chs else None, ctypes.byref(dps) if dps else None,
-                               _ptr(points), P, tarr, T, kind, float(r_excl), ctypes.byref(_out_struct(o)),
-                               _stream(stream))
+    with torch.cuda.device(dev):
+        o = alloc_field_out(P, T, PC_MIXED, dev) if out is None else out
+        _check_noalloc_out(o, P, T, dev)
+        tarr = (_f64 * T)(*[float(t) for t in times])
+        chs = _charges_struct(charges)
+        dps = _dipoles_struct(dipoles)
+        st = lib.pc_fields_noalloc(ctypes.byref(chs) if chs else None, ctypes.byref(dps) if dps else None,
+                                   _ptr(points), P, tarr, T, kind, float(r_excl), ctypes.byref(_out_struct(o)),
+                                   _stream(stream))
     _check(st, "pc_fields_noalloc")
     return o

@@ -71,7 +71,7 @@ extern "C" const char *pc_status_string(pc_status s) {
     case PC_ERR_VELOCITY: return "dipole charge exceeded the maximum velocity";
     case PC_ERR_CAUSALITY: return "time step exceeds a light-crossing time between dipoles";
     case PC_ERR_NOCONV: return "solver did not converge";
-    case PC_ERR_TIMEOUT: return "device wait exceeded its iteration limit";
+    case PC_ERR_TIMEOUT: return "reserved (no call returns it)";
   }
   return "unknown status";
 }

@@ -4,7 +4,8 @@
 //   PC_F64   one thread per (point, time); every charge's retarded time is found by solving, on one
 //            segment of its piecewise-linear history, the quadratic c^2 (t - t')^2 = |r - r_s(t')|^2
 //            (Eq. ret_t with linear interpolation, Sec. 3.1), moving to the segment the root points
-//            to until it lies inside; fields from Griffiths' form of Eqs. E, B, V, A in float64.
+//            to until it lies inside; fields from Griffiths' form of Eqs. E, B, V, A in float64, a
+//            dipole's two charges together in the difference form of the mixed path (below).
 //   PC_MIXED a CTA owns a tile of points.  Per (tile, source) the float64 distance from the tile's
 //            anchor point to the source reference gives the integer part of the retarded sample
 //            index; per (point, source) everything else runs in float32 on offsets (lengths in
@@ -197,52 +198,49 @@ __global__ void __launch_bounds__(128) fields_f64_kernel(const Launch L) {
       lw_add_f64<KIND>(s.q[c], av, v, a, L.r_excl, E, B, &phi, A, &mask);
     }
   }
-  // ---- dipoles: two charges each (Eqs. r_1, r_2) ----
+  // ---- dipoles: the two charges of each (Eqs. r_1, r_2) in difference form ----
+  // Each charge's retarded time is the exact root on its own history segment (offsets from the
+  // dipole centre in units of c dt, times in samples); the net field q [F(x+) - F(x-)] is formed
+  // from differences of the Lienard-Wiechert coefficients (pc_lw_f32.cuh, dipole_pair), so the
+  // R/s cancellation of the +-q pair costs no digits.
   if (s.N > 0 && !err) {
-    const double u = (t - s.t0d) / s.dtd, cdt = kC * s.dtd;
+    const double u = (t - s.t0d) / s.dtd, iLd = L.iLd;
+    const double rex = L.r_excl * iLd;
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = 0; j < s.N && !err; ++j) {
-      TrajF64 tr;
-      tr.dipole = true;
-      tr.d = s.d + (size_t)j * s.Sd;
-      tr.dd = s.dd + (size_t)j * s.Sd;
-      tr.ddd = s.ddd + (size_t)j * s.Sd;
-      for (int i = 0; i < 3; ++i) {
-        tr.R[i] = s.origin[3 * j + i];
-        tr.ax[i] = s.axis[3 * j + i];
-      }
       const double q = s.qd[j], m1 = s.m1[j], m2 = s.m2[j];
-      const double iw = 1.0 / ((m1 + m2) * q);  // the one float64 division per dipole
-      double dv[3] = {r[0] - tr.R[0], r[1] - tr.R[1], r[2] - tr.R[2]};
-      double tau0 = sqrt(dot3(dv, dv)) * L.iLd;
-      int64_t kg = (int64_t)floor(u - tau0);
-      for (int sg = 0; sg < 2 && !err; ++sg) {
-        tr.w = (sg == 0) ? m2 * iw : -m1 * iw;
-        int64_t k;
-        double th;
-        err = solve_f64(tr, s.Sd, 1, r, u, cdt, kg, &k, &th);
-        if (err) break;
-        double p0[3], v[3], a[3];
-        if (k < 0 || (k == 0 && th == 0.0)) {
-          // at rest with moment d[0] for t <= t0 (Sec. 3.2)
-          tr.p(0, p0);
-          v[0] = v[1] = v[2] = 0.0;
-          a[0] = a[1] = a[2] = 0.0;
-        } else {
-          double p1[3], v1[3], a1[3];
-          tr.p(k, p0);
-          tr.p(k + 1, p1);
-          tr.va(k, v, a);
-          tr.va(k + 1, v1, a1);
-          for (int i = 0; i < 3; ++i) {
-            p0[i] += th * (p1[i] - p0[i]);
-            v[i] += th * (v1[i] - v[i]);
-            a[i] += th * (a1[i] - a[i]);
-          }
-        }
-        double av[3] = {r[0] - p0[0], r[1] - p0[1], r[2] - p0[2]};
-        lw_add_f64<KIND>(sg == 0 ? q : -q, av, v, a, L.r_excl, E, B, &phi, A, &mask);
-      }
+      const double rx = (r[0] - s.origin[3 * j]) * iLd, ry = (r[1] - s.origin[3 * j + 1]) * iLd,
+                   rz = (r[2] - s.origin[3 * j + 2]) * iLd;
+      const double rn = sqrt(rx * rx + ry * ry + rz * rz);
+      const double px = s.axis[3 * j], py = s.axis[3 * j + 1], pz = s.axis[3 * j + 2];
+      const double rp = rx * px + ry * py + rz * pz;
+      const double x = u - rn;
+      const double fl = floor(x);
+      HistF64 H;
+      H.d = s.d + (size_t)j * s.Sd;
+      H.dd = s.dd + (size_t)j * s.Sd;
+      H.ddd = s.ddd + (size_t)j * s.Sd;
+      const double iq = 1.0 / q, imm = 1.0 / (m1 + m2);
+      H.sx = iq * iLd;
+      H.sv = iq * (1.0 / kC);
+      H.sa = iq * (s.dtd / kC);
+      double Xp, Vp, Ap, dp, Xm, Vm, Am, dm;
+      const double mup = m2 * imm, mum = m1 * imm;
+      err = dip_pair_exact<double, HistF64>(H, (int)s.Sd, (int)fl, x - fl, rn, rp, mup, mum, Xp, Vp, Ap, dp, Xm, Vm,
+                                           Am, dm, 1e-9);
+      if (err) break;
+      dipole_pair<KIND, double>(rx, ry, rz, rn, px, py, pz, rp, mup, mum, q * (1.0 / kE), Xp, Vp, Ap, dp, Xm, Vm, Am,
+                                dm, rex, acc, mask);
     }
+    // units of the difference form: E in k_e e / L^2, B in k_e e / (L^2 c), phi in k_e e / L,
+    // A in k_e e / (L c), L = c dt of the dipole history
+    const double uP = kKe * kE * iLd, uE = uP * iLd;
+    for (int i = 0; i < 3; ++i) {
+      E[i] += uE * acc[i];
+      B[i] += uE * (1.0 / kC) * acc[3 + i];
+      A[i] += uP * (1.0 / kC) * acc[7 + i];
+    }
+    phi += uP * acc[6];
   }
   if (err) {
     set_status(L.status, err);
@@ -1263,6 +1261,8 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
 
   L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;  // 1/(c dt): first guesses without a division
   L.iLc = has_ch ? 1.0 / (kC * s.dt) : 0.0;
+  // dipole sample indices are 32-bit integers in both paths (the difference form's solves)
+  if (has_dp && s.Sd > (int64_t)1 << 30) return PC_ERR_ARG;
   if (precision == PC_MIXED) {
     // the float32 path indexes samples with 32-bit integers
     if ((has_dp && s.Sd > (int64_t)1 << 30) || (has_ch && s.S > (int64_t)1 << 30)) return PC_ERR_ARG;
@@ -1431,9 +1431,8 @@ constexpr size_t kStaticHeader = 256;                     // status word, padded
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticHeader + kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-static void *g_noalloc_addr[kMaxDevices];
-static cudaError_t g_noalloc_err[kMaxDevices];
-static std::once_flag g_noalloc_once[kMaxDevices];
+static void *g_noalloc_addr[kMaxDevices];  // the array's device address per device, once resolved
+static std::mutex g_noalloc_mu;            // guards g_noalloc_addr
 
 }  // namespace pc
 
@@ -1463,13 +1462,33 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   if (need > kStaticScratchBytes) return PC_ERR_ARG;
   if ((has_dp && dp->S > (int64_t)1 << 30) || (has_ch && ch->S > (int64_t)1 << 30)) return PC_ERR_ARG;
 
-  // once per device, with that device current: the device address of the static scratch
+  // once per device, with that device current: the device address of the static scratch.  Only a
+  // resolved address is kept, so a failed first lookup is retried by the next call.
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PC_ERR_CUDA;
-  std::call_once(g_noalloc_once[dev],
-                 [dev] { g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch); });
-  if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev]) return PC_ERR_CUDA;
-  unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
+  // the points must live on the current device: the kernels run there
+  {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, points) != cudaSuccess) {
+      cudaGetLastError();
+      return PC_ERR_ARG;
+    }
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) return PC_ERR_ARG;
+    if (pa.device != dev) return PC_ERR_ARG;
+  }
+  unsigned char *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void *a = nullptr;
+      if (cudaGetSymbolAddress(&a, g_noalloc_scratch) != cudaSuccess || !a) {
+        cudaGetLastError();
+        return PC_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = a;
+    }
+    base = (unsigned char *)g_noalloc_addr[dev];
+  }
   int *status = (int *)base;
   float4 *Hd = (float4 *)(base + kStaticHeader);
   float4 *Hc = Hd + nd;

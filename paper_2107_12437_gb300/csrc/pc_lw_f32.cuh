@@ -96,9 +96,10 @@ struct HistF64 {
 //   kb + xc: retarded time of the centre, in samples (xc small)
 //   rn = |rho|, rp = rho . axis
 // Out: X, V, Ac at the charge's own retarded time; delta = its distance minus rn.
+// end_tol: a root up to this many samples past the last sample is taken at the last sample.
 template <typename T, typename Hist>
 __device__ __forceinline__ int dip_charge_solve(const Hist &H, int S, int kb, T xc, T rn, T rp, T smu, T &X, T &V,
-                                                T &Ac, T &delta) {
+                                                T &Ac, T &delta, T end_tol = T(kEndTol)) {
   if (!(fabs(xc) < T(1e6))) return PC_ERR_NOCONV;
   T fl;
   int kc = Num<T>::floor_int(xc, fl);
@@ -140,8 +141,13 @@ __device__ __forceinline__ int dip_charge_solve(const Hist &H, int S, int kb, T 
     const T sq = Num<T>::sqrt0(fmax(B * B - A * C, T(0)));
     const T dl = (B > T(0)) ? -Num<T>::div(C, B + sq) : Num<T>::div(-B + sq, A);
     T th = thc - dl;
-    const bool ok = (j < 0) ? ((T)j + th <= T(1e-4))
-                            : (th >= T(-1e-4) && (th <= T(1.0001) || (j == S - 2 && th <= T(1) + T(kEndTol))));
+    // a root this far outside the segment is taken at its end (the neighbouring segment's value
+    // there differs by that fraction of a sample times the history's second difference); float32
+    // roots carry ~1e-6 sample of rounding, float64 ones ~1e-12
+    const T edge = sizeof(T) == sizeof(float) ? T(1e-4) : T(1e-12);
+    const bool ok = (j < 0) ? ((T)j + th <= edge)
+                            : (th >= -edge && (th <= T(1) + edge || (j == S - 2 && th <= T(1) + end_tol)) &&
+                               (j < S - 2 || th <= T(1) + end_tol));
     if (ok) {
       th = fmin(fmax(th, T(0)), T(1));
       X = x0 + th * dx;
@@ -449,9 +455,9 @@ __device__ __forceinline__ void dipole_pair(T rx, T ry, T rz, T rn, T px, T py, 
 // (or near pairs), and inlining it would cost the common path registers.
 template <typename T, typename Hist>
 __device__ __noinline__ int dip_pair_exact(const Hist &H, int S, int kb, T xc, T rn, T rp, T mup, T mum, T &Xp, T &Vp,
-                                           T &Ap, T &dp, T &Xm, T &Vm, T &Am, T &dm) {
-  const int e1 = dip_charge_solve<T>(H, S, kb, xc, rn, rp, mup, Xp, Vp, Ap, dp);
-  const int e2 = dip_charge_solve<T>(H, S, kb, xc, rn, rp, -mum, Xm, Vm, Am, dm);
+                                           T &Ap, T &dp, T &Xm, T &Vm, T &Am, T &dm, T end_tol = T(kEndTol)) {
+  const int e1 = dip_charge_solve<T>(H, S, kb, xc, rn, rp, mup, Xp, Vp, Ap, dp, end_tol);
+  const int e2 = dip_charge_solve<T>(H, S, kb, xc, rn, rp, -mum, Xm, Vm, Am, dm, end_tol);
   return e1 ? e1 : e2;
 }
 

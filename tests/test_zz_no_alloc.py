@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2107_12437_gb300 as pc
 import workloads as W
 from paper_2107_12437_gb300 import capi
@@ -62,3 +63,64 @@ def test_noalloc_rejects_sources_beyond_its_scratch():
     with pytest.raises(pc.PcError) as ei:
         capi.pc_fields_noalloc(dipoles=pc.dipoles_to_device(big), points=ptd, times=[1e-14])
     assert ei.value.status == capi.PC_ERR_ARG
+
+
+def test_noalloc_point_charges_and_dipoles_many_frames():
+    # point charges (the orbiting pair: their mirrors and reference positions sit after the
+    # dipoles' in the static array) together with 32 dipoles, at 33 times (two launches of at most
+    # 32 frames); against pc_fields (PC_MIXED) everywhere and against the oracle on a few points
+    ctx = pc.Context(0)
+    ch, _, _ = W.cfg1()
+    dp, _, _, _ = W.cfg2()
+    srcs = _sub_dipoles(dp, np.arange(32))
+    g = np.linspace(-60e-9, 60e-9, 23)
+    pts = np.concatenate([W.plane_grid(g, g[::3], 2e-9), W.plane_grid(g[::2] + 5e-7, g[::4] + 4e-7, 5e-7)])
+    ptd = torch.as_tensor(pts, device="cuda")
+    times = [float(t) for t in np.linspace(8.0e-15, 9.9e-15, 33)]
+    chd, dpd = pc.charges_to_device(ch), pc.dipoles_to_device(srcs)
+    ref = pc.pc_fields(ctx, charges=chd, dipoles=dpd, points=ptd, times=times, precision=pc.PC_MIXED)
+    for _ in range(2):
+        out = capi.alloc_field_out(ptd.shape[0], len(times), pc.PC_MIXED, "cuda")
+        for v in out.values():
+            v.fill_(7)
+        capi.pc_fields_noalloc(charges=chd, dipoles=dpd, points=ptd, times=times, out=out)
+        torch.cuda.synchronize()
+        assert torch.equal(out["mask"], ref["mask"])
+        for k in ("E", "B", "phi", "A"):
+            assert _rel(out[k], ref[k]) <= MIX_TOL, k
+    # the oracle on every 17th point at the first and the last frame: the mixed-path metric,
+    # |dF| <= 1e-5 of the sum over sources of |F_j| (B at that sum of |E_j| / c)
+    sel = np.arange(0, pts.shape[0], 17)
+    fr = [0, 32]
+    orc = oracle.fields(pts[sel], [times[f] for f in fr], charges=ch, dipoles=srcs)
+    assert orc["status"] == oracle.OK
+    for k in ("E", "B", "phi", "A"):
+        got = out[k][fr][:, sel].double().cpu().numpy()
+        num = np.abs(got - orc[k]) if got.ndim == 2 else np.linalg.norm(got - orc[k], axis=-1)
+        scale = orc["scale_source"]["E"] / W.C if k == "B" else orc["scale_source"][k]
+        assert float(np.max(num / scale)) <= MIX_TOL, k
+    ctx.close()
+
+
+def test_noalloc_rejects_outputs_and_points_it_cannot_use():
+    dp, g, z, times = W.cfg2()
+    dpd = pc.dipoles_to_device(_sub_dipoles(dp, np.arange(4)))
+    ptd = torch.zeros((5, 3), dtype=torch.float64, device="cuda")
+    # a float64 output or one of the wrong length is refused before the call
+    bad = capi.alloc_field_out(5, 1, pc.PC_MIXED, "cuda")
+    bad["E"] = torch.empty((1, 5, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        capi.pc_fields_noalloc(dipoles=dpd, points=ptd, times=[float(times[0])], out=bad)
+    short = capi.alloc_field_out(4, 1, pc.PC_MIXED, "cuda")
+    with pytest.raises(ValueError):
+        capi.pc_fields_noalloc(dipoles=dpd, points=ptd, times=[float(times[0])], out=short)
+    # points in host memory are an argument error of the C entry point itself
+    import ctypes
+
+    hpts = torch.zeros((5, 3), dtype=torch.float64)
+    out = capi.alloc_field_out(5, 1, pc.PC_MIXED, "cuda")
+    tarr = (ctypes.c_double * 1)(float(times[0]))
+    st = capi.load().pc_fields_noalloc(None, ctypes.byref(capi._dipoles_struct(dpd)),
+                                       ctypes.c_void_p(hpts.data_ptr()), 5, tarr, 1, pc.PC_TOTAL, 0.0,
+                                       ctypes.byref(capi._out_struct(out)), None)
+    assert st == capi.PC_ERR_ARG
