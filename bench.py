@@ -36,14 +36,46 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "LW pair evals/s & dipole-steps/s at 1 GB300, mixed vs plain FP64 GPU path"
-# Algorithmic floating-point operations of one retarded pair evaluation (point, charge, time):
-# segment quadratic for the retarded time (34), interpolation of position, velocity and
-# acceleration (30), Lienard-Wiechert E, B, phi, A in Griffiths' form (78), accumulation (10);
-# an add, multiply, divide or square root counts 1, a fused multiply-add 2.
-FLOPS_PER_PAIR = 152
-N_SM = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+# Algorithmic floating-point operations of one retarded pair evaluation (point, charge, time) of the
+# plain per-charge method: the retarded time as the root of a quadratic on one linear history
+# segment, linear interpolation of the charge's state there, and Griffiths' form of the
+# Lienard-Wiechert E, B, phi, A added to the sums.  An add, subtract, multiply, divide, square root or
+# reciprocal (square root) counts 1 flop; a dot product of 3-vectors 5; a fused multiply-add 2.
+FLOP_TALLY = {
+    "retarded time (quadratic on one segment)": {
+        "a = r - p_k, D = p_k+1 - p_k, T = u - k": 7,
+        "A = (c dt)^2 - D.D": 6,
+        "B = a.D - (c dt)^2 T": 7,
+        "C = (c dt)^2 T^2 - a.a": 8,
+        "B^2 - A C": 3,
+        "square root": 1,
+        "root C / (sqrt - B)": 2,
+    },
+    "interpolation at the root": {
+        "position p_k + th D": 6,
+        "velocity v_k + th (v_k+1 - v_k)": 9,
+        "acceleration a_k + th (a_k+1 - a_k)": 9,
+        "separation r - p": 3,
+    },
+    "Lienard-Wiechert fields (Griffiths)": {
+        "R^2, 1/R, R": 7,
+        "n = a / R": 3,
+        "u = c n - v": 6,
+        "R u = c R - a.v": 7,
+        "1 / (R u)": 1,
+        "f = k q R / (R u)^3": 4,
+        "g = f (c^2 - v.v)": 7,
+        "velocity field g u": 3,
+        "a.acc": 5,
+        "radiation field f (u (a.acc) - acc (R u))": 15,
+        "E +=": 3,
+        "B += n x E / c": 15,
+        "phi += k q c / (R u)": 2,
+        "A += (phi / c^2) v": 7,
+    },
+}
+FLOPS_PER_PAIR = sum(sum(v.values()) for v in FLOP_TALLY.values())
+FP32_LANES_PER_SM = 128  # compute capability 10.x: 128 float32 FMA lanes per SM
 
 
 def kernel_source_hash():
@@ -87,6 +119,16 @@ def gpu_local_cpus(dev):
             lo, _, hi = part.partition("-")
             cpus.update(range(int(lo), int(hi or lo) + 1))
         return cpus & set(os.sched_getaffinity(0)) or None
+    except Exception:
+        return None
+
+
+def max_sm_clock_mhz(gpu_index):
+    """The GPU's maximum SM clock (MHz) as nvidia-smi reports it (clocks.max.sm), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=30)
+        return float(out.stdout.strip().splitlines()[0])
     except Exception:
         return None
 
@@ -239,6 +281,79 @@ def compare_cloud(pc, ctx, dev, n_steps):
     res["gamma_over_gamma0_f64_range"] = [float((f["gamma"] / g0).min()), float((f["gamma"] / g0).max())]
     res["delta_omega_over_gamma0_f64_range"] = [float(((f["omega"] - w0) / g0).min()),
                                                  float(((f["omega"] - w0) / g0).max())]
+    return res
+
+
+def field_errors(out_mixed, out_f64, dp, g, z, times, n_per_frame=64):
+    """Per-output errors of both GPU paths on a strided sample of the whole step (n_per_frame
+    points in each of the 16 frames) against the binary128 oracle: plain relative error |dF| / |F|
+    (max, 99th percentile, fraction above the target: 1e-10 float64, 1e-5 mixed) and, for the mixed
+    path, the error over the source scale sum_j |F_j| (from the float64 oracle)."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(2107)
+    nfr = len(times)
+    idx = np.stack([rng.choice(g.size * g.size, n_per_frame, replace=False) for _ in range(nfr)])
+    step = float(g[1] - g[0])
+    res = {"sample": f"{n_per_frame} random points in each of the {nfr} frames of the 2048^2 grid",
+           "reference": "oracle in binary128 (fields_x)"}
+    acc = {p: {k: [] for k in ("E", "B", "phi", "A")} for p in ("f64", "mixed")}
+    srcs = {k: [] for k in ("E", "B", "phi", "A")}
+    for f in range(nfr):
+        pts = np.stack([(idx[f] // g.size) * step, (idx[f] % g.size) * step, np.full(n_per_frame, z)], axis=1)
+        ref = oracle.fields_x(pts, [times[f]], dipoles=dp)
+        r64 = oracle.fields(pts, [times[f]], dipoles=dp)
+        for k in ("E", "B", "phi", "A"):
+            den = np.abs(ref[k][0]) if ref[k].ndim == 2 else np.linalg.norm(ref[k][0], axis=-1)
+            for p, o in (("f64", out_f64), ("mixed", out_mixed)):
+                got = o[k][f, idx[f]].double().cpu().numpy()
+                num = np.abs(got - ref[k][0]) if got.ndim == 1 else np.linalg.norm(got - ref[k][0], axis=-1)
+                acc[p][k].append(np.stack([num, den], axis=1))
+            srcs[k].append(r64["scale_source"]["E"][0] / W.C if k == "B" else r64["scale_source"][k][0])
+    for p, tol in (("f64", 1e-10), ("mixed", 1e-5)):
+        res[p] = {}
+        for k in ("E", "B", "phi", "A"):
+            a = np.concatenate(acc[p][k])
+            rel = a[:, 0] / a[:, 1]
+            e = {"plain_max": float(rel.max()), "plain_p99": float(np.percentile(rel, 99)),
+                 "plain_frac_above_target": float(np.mean(rel > tol))}
+            if p == "mixed":
+                sc = np.concatenate(srcs[k])
+                e["source_scale_max"] = float(np.max(a[:, 0] / sc))
+            res[p][k] = e
+    return res
+
+
+def pair_theory(pc, ctx, dev):
+    """The batched pairs (256 separations, 40 000 steps, Eq. KE fit) for s and p dipoles, float64 and
+    mixed with near sources in float64: fitted delta_12 and gamma_+ against the exact classical pole
+    of the pair (oracle/theory.py), the largest relative errors per separation range."""
+    from oracle import theory as th
+
+    res = {"reference": "exact classical pole w^2 + i g0 w - w0^2 + (q^2/m eps0) p.G(R, w/c).p = 0"}
+    bands = [(1e-9, 3e-9), (3e-9, 10e-9), (10e-9, 100e-9), (100e-9, 1.01e-6)]
+    for orient in ("s", "p"):
+        cfg, sep = W.cfg3(B=256, n_steps=40000, orientation=orient)
+        w0 = float(cfg.omega0[0, 0])
+        m = W.M_E / 2
+        g0 = th.gamma0(W.E_CHARGE, m, w0)
+        d_ex, g_ex = np.zeros(cfg.B), np.zeros(cfg.B)
+        for b, R in enumerate(sep):
+            vec = [0.0, R, 0.0] if orient == "s" else [R, 0.0, 0.0]
+            _, dl, g = th.exact_pair_pole(vec, [1.0, 0.0, 0.0], w0, W.E_CHARGE, m)
+            d_ex[b], g_ex[b] = dl / g0, g / g0
+        for name, prec, near in (("f64", pc.PC_F64, 0.0), ("mixed_near_f64", pc.PC_MIXED, 10e-9)):
+            out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, fit=True,
+                                    first_index=cfg.first_index, precision=prec, near_f64=near, want_energy=False)
+            df = (out["omega"][:, 0].cpu().numpy() - w0) / g0
+            gf = out["gamma"][:, 0].cpu().numpy() / g0
+            rd = np.abs(df - d_ex) / np.maximum(np.abs(d_ex), 1e-30)
+            rg = np.abs(gf - g_ex) / g_ex
+            res[f"{orient}_{name}"] = {
+                f"{lo * 1e9:g}-{hi * 1e9:g} nm": {"delta_max_rel_err": float(rd[(sep >= lo) & (sep < hi)].max()),
+                                                 "gamma_max_rel_err": float(rg[(sep >= lo) & (sep < hi)].max())}
+                for lo, hi in bands}
     return res
 
 
@@ -420,8 +535,15 @@ def main():
     del pin_out, pin_in
 
     # ---- roofline of the field kernel (float32 ALU) ----
+    # peak = SMs x float32 FMA lanes x 2 flop x maximum SM clock, the SM count and the clock read
+    # from this device; the measured FMA rate (dependent-chain kernels) is reported beside it
     fp32_fma, fp64_fma = pc.pc_alu_peaks(ctx)
-    peak_tflops = 2.0 * N_SM * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = max_sm_clock_mhz(dev.index)
+    clk_basis = "maximum SM clock from nvidia-smi"
+    if not sm_max:
+        sm_max, clk_basis = 2070.0, "maximum SM clock of the GB300 data sheet (nvidia-smi unavailable)"
+    peak_tflops = 2.0 * n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     achieved = FLOPS_PER_PAIR * pairs_per_step / (kernel_ms * 1e-3) / 1e12
     # DRAM bytes of one full launch, scaled from an ncu capture of a smaller case; valid only while
     # the kernel sources are the ones that capture was taken of
@@ -454,34 +576,42 @@ def main():
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": "fields_mixed2_kernel" if tile_rows * tile_cols > 256 else "fields_mixed_kernel",
                      "flops_per_pair": FLOPS_PER_PAIR,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
-                     "measured_fp32_fma_per_s": fp32_fma, "measured_fp64_fma_per_s": fp64_fma},
+                     "flops_per_pair_basis": "itemized tally of the per-charge method (bench.FLOP_TALLY)",
+                     "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                                   f"({clk_basis})",
+                     "measured_fp32_fma_per_s": fp32_fma, "measured_fp64_fma_per_s": fp64_fma,
+                     "frac_of_measured_fp32_fma": achieved * 1e12 / (2.0 * fp32_fma)},
     }
 
     if not args.no_extra:
-        # plain float64 GPU path on a bounded sample (64 rows x 2048 x 1 frame), per pair evaluation
+        # the plain float64 GPU path on the whole step (2048 x 2048 plane, 16 frames): one untimed
+        # call, then one timed
+        out64 = pc.capi.alloc_field_out(NU * NV, T, pc.PC_F64, dev)
+
         def f64_step():
-            pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=64,
-                               nv=NV, times=[float(times[0])], precision=pc.PC_F64)
+            pc.pc_fields_plane(ctx, dipoles=dpd, origin=(0.0, 0.0, z), eu=(step, 0, 0), ev=(0, step, 0), nu=NU,
+                               nv=NV, times=list(times), precision=pc.PC_F64, out=out64)
 
         f64_step()
         torch.cuda.synchronize()
+        flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        for _ in range(3):
-            f64_step()
+        f64_step()
         e1.record(s)
         torch.cuda.synchronize()
-        f64_ms = e0.elapsed_time(e1) / 3
-        f64_pairs = 64 * NV * 2 * dp.N
-        f64_value = f64_pairs / (f64_ms * 1e-3)
-        line["fp64_path"] = {"value": f64_value, "unit": "LW pair evals/s",
-                             "sample": "64 rows x 2048 x 1 frame of the same grid, float64 path",
+        f64_ms = e0.elapsed_time(e1)
+        f64_value = pairs_per_step / (f64_ms * 1e-3)
+        line["fp64_path"] = {"value": f64_value, "unit": "LW pair evals/s", "ms": f64_ms,
+                             "sample": "the whole step (2048 x 2048 x 16 frames), float64 path",
                              "mixed_over_fp64": value / world / f64_value,
                              "roofline": {"bound": "alu", "achieved": FLOPS_PER_PAIR * f64_value / 1e12,
                                           "peak": 2.0 * fp64_fma / 1e12, "unit": "TFLOP/s",
                                           "frac": FLOPS_PER_PAIR * f64_value / (2.0 * fp64_fma),
                                           "peak_basis": "measured float64 FMA rate (pc_alu_peaks)"}}
+        if rank == 0:
+            line["errors"] = field_errors(out, out64, dp, g, z, times)
+        del out64
         # oscillator runs: dipole-steps per second (float64 RK4 state; driving field per precision)
         def lo_time(cfg, n_steps, prec, fit, near_f64=0.0):
             lod = pc.lo_config_to_device(cfg, dev)
@@ -506,6 +636,8 @@ def main():
         r["workload"] = ("the same, mixed with the sources within 10 nm summed in float64 (decay rates of the "
                          "closest pairs resolved)")
         ds["pairs_mixed_near_f64"] = r
+        if rank == 0:
+            line["pair_theory"] = pair_theory(pc, ctx, dev)
         # the Eq. KE fit of all 512 kinetic-energy series of that run (30 001 samples each)
         lod = pc.lo_config_to_device(cfg3, dev)
         out3 = pc.pc_dipoles_run(ctx, lod, cfg3.dt, cfg3.n_steps, precision=pc.PC_MIXED)
@@ -553,6 +685,14 @@ def main():
         r = lo_time(cfg5, cfg5.n_steps, pc.PC_MIXED, False)
         r["workload"] = "cloud: 4096 oscillators in a 600 nm cube x 20000 RK4 steps (1250 causal blocks of 16 steps)"
         ds["cloud_mixed"] = r
+        # the all-float64 GPU path on the same cloud over its first 1000 steps (the whole run takes
+        # ~7 minutes in float64), and the mixed path over the same steps for a like-for-like factor
+        cfg5s = W.cfg5(n_steps=1000)
+        for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
+            r = lo_time(cfg5s, cfg5s.n_steps, prec, False)
+            r["workload"] = "cloud: 4096 oscillators in a 600 nm cube x the first 1000 RK4 steps"
+            ds["cloud_1000_" + name] = r
+        ds["cloud_1000_mixed_over_f64"] = ds["cloud_1000_f64"]["ms"] / ds["cloud_1000_mixed"]["ms"]
 
         def timed(fn):
             fn()

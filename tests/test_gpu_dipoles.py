@@ -294,3 +294,37 @@ def test_cloud_full_size_past_static_block(ctx, prec):
         st = oracle.fields(org[i][None], [steps[-1] * cfg.dt], dipoles=still)
         moved += int(abs(ed[-1] - st["E"][0, 0] @ cfg.axis[0, i]) > 1e-3 * scale[-1])
     assert moved >= len(recv) // 2
+
+
+def test_cloud_mixed_against_f64():
+    # Config 5 in both precisions (the mixed path against the all-float64 GPU path).
+    # (1) The 4096-oscillator cloud over its first 1000 steps: total-energy trace within 1e-10 of its
+    #     largest value, moment histories d, d' within 1e-7 of each dipole's peak.
+    # (2) A cloud of the same density (1024 oscillators in a 378 nm cube, 5 nm minimum spacing) over
+    #     6000 steps with the Eq. KE fit from step 1000: fitted omega within 1e-9 relative and gamma
+    #     within 2e-3 gamma0 per dipole (at 5 nm spacing the energies beat rather than decay: the
+    #     comparison is of the same fit applied to both runs).
+    ctx = pc.Context(0)
+    cfg = W.cfg5(n_steps=1000)
+    lod = pc.lo_config_to_device(cfg)
+    o = {p: pc.pc_dipoles_run(ctx, lod, cfg.dt, cfg.n_steps, precision=p) for p in (pc.PC_MIXED, pc.PC_F64)}
+    m, f = o[pc.PC_MIXED], o[pc.PC_F64]
+    et_m, et_f = m["energy"][0].sum(0), f["energy"][0].sum(0)
+    assert float((et_m - et_f).abs().max() / et_f.abs().max()) < 1e-10
+    for k in ("d", "d_dot"):
+        err = ((m[k][0] - f[k][0]).abs().amax(-1) / f[k][0].abs().amax(-1)).max()
+        assert float(err) < 1e-7, k
+    del o, m, f
+    cfg = W.cfg5(N=1024, side=378e-9, n_steps=6000)
+    cfg.first_index = 1000
+    lod = pc.lo_config_to_device(cfg)
+    o = {p: pc.pc_dipoles_run(ctx, lod, cfg.dt, cfg.n_steps, precision=p, fit=True, first_index=cfg.first_index,
+                              want_energy=False) for p in (pc.PC_MIXED, pc.PC_F64)}
+    mass = cfg.m1[0] * cfg.m2[0] / (cfg.m1[0] + cfg.m2[0])
+    g0 = th.gamma0(cfg.q[0], mass, cfg.omega0[0])
+    gm, gf = o[pc.PC_MIXED]["gamma"][0].cpu().numpy(), o[pc.PC_F64]["gamma"][0].cpu().numpy()
+    wm, wf = o[pc.PC_MIXED]["omega"][0].cpu().numpy(), o[pc.PC_F64]["omega"][0].cpu().numpy()
+    assert np.all(np.isfinite(gf)) and np.all(np.isfinite(wf))
+    assert float(np.max(np.abs(wm - wf) / wf)) < 1e-9
+    assert float(np.max(np.abs(gm - gf) / g0)) < 2e-3
+    ctx.close()
