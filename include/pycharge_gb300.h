@@ -235,12 +235,24 @@ typedef struct {
                         * the near field, which float32 rounding swamps: with PC_MIXED alone the
                         * fitted gamma of a pair is off by ~0.3 gamma0 at 1 nm and 1e-3 gamma0 at
                         * 6 nm (omega0 = 2 pi 200 THz); 10e-9 keeps it below 1e-4 gamma0 */
+  const double *state_in; /* device, or NULL: resume from this state (written by an earlier call's
+                           * state_out for the same dipoles and dt); the call then advances from the
+                           * state's step s to s + n_steps, its outputs' sample 0 being step s */
+  double *state_out;      /* device, or NULL: receives the state at the call's last step;
+                           * pc_dipoles_state_size gives its length */
+  int64_t checkpoint_every; /* adjoints (pc_dipoles_adjoint, pc_dipoles_rates_adjoint): 0 keeps the
+                           * whole forward history; K > 0 keeps the run's state every K steps and
+                           * recomputes each segment of K steps during the reverse sweep */
 } pc_run_opts;
 
-/* Outputs of pc_dipoles_run; layout [B][N][n_steps+1] (time fastest). d, d_dot, d_ddot are
- * required: they are the trajectory history the run reads back at retarded times. */
+/* Outputs of pc_dipoles_run; layout [B][N][n_steps+1] (time fastest); every pointer may be NULL
+ * (not wanted).  When d, d_dot and d_ddot are all given (and the run does not resume a state) they
+ * are also the history store the run reads back at retarded times; otherwise the run keeps its
+ * history in a ring of the context holding only the samples a causal block can still reach
+ * (2^k >= D + 18 slots per dipole, D the largest delay between two dipoles in samples plus a margin),
+ * so that its memory does not grow with n_steps. */
 typedef struct {
-  double *d, *d_dot, *d_ddot; /* device, required */
+  double *d, *d_dot, *d_ddot; /* device */
   double *energy;             /* device [B][N][n_steps+1] Eq. dipoleE, or NULL */
   double *Ed;                 /* device [B][N][n_steps+1] driving field at t_n (V/m), or NULL */
   double *gamma;              /* device [B][N] fitted energy decay rate (1/s), or NULL */
@@ -266,6 +278,17 @@ typedef struct {
  */
 pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
                          const pc_run_out *out, void *stream);
+
+/*
+ * pc_dipoles_state_size -- the length (float64 values) of a run state of these dipoles at this dt
+ * (pc_run_opts.state_in / state_out): a header (step, depth D, B N), E_d of every dipole at the state's
+ * step and d, d', d'' of its last D + 1 samples, D the deepest sample a causal block can reach behind
+ * its start (Algorithm 1 needs the retarded history, not only the present state, to continue).
+ * A state resumes the run exactly: the continued run equals the uninterrupted one bit for bit when
+ * the state's step is a multiple of the causal block length, and to rounding otherwise.
+ * Errors: PC_ERR_ARG, PC_ERR_CUDA.
+ */
+pc_status pc_dipoles_state_size(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t *n_doubles, void *stream);
 
 /* Moving dipoles (Sec. 4.3): the origin of every dipole as a function of time, sampled at the half
  * steps t = h dt / 2, h = 0 .. 2 n_steps, device [B][N][2 n_steps + 1][3] each (m, m/s, m/s^2). */

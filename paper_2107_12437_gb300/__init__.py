@@ -31,6 +31,7 @@ from .capi import (  # noqa: F401
     pc_dipoles_rates_adjoint,
     pc_dipoles_run,
     pc_dipoles_run_moving,
+    pc_dipoles_state_size,
     pc_fields,
     pc_fields_noalloc,
     pc_fields_param,

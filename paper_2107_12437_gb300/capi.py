@@ -55,7 +55,7 @@ class PcDipoles(ctypes.Structure):
 
 class PcRunOpts(ctypes.Structure):
     _fields_ = [("v_max", _f64), ("ed_mode", _i32), ("fit", _i32), ("first_index", _i64), ("precision", _i32),
-                ("near_f64", _f64)]
+                ("near_f64", _f64), ("state_in", _vp), ("state_out", _vp), ("checkpoint_every", _i64)]
 
 
 class PcRunOut(ctypes.Structure):
@@ -94,6 +94,7 @@ SIGNATURES = {
                                        ctypes.POINTER(PcFieldOut), _vp]),
     "pc_dipoles_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                       ctypes.POINTER(PcRunOut), _vp]),
+    "pc_dipoles_state_size": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, ctypes.POINTER(_i64), _vp]),
     "pc_fields_to_host": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
                                          ctypes.POINTER(_f64), _i32, _i32, _i32, _f64, ctypes.POINTER(PcFieldOut),
                                          _vp]),
@@ -390,16 +391,36 @@ def lo_config_to_device(cfg, device="cuda"):
                            d0=_dev(cfg.d0, device))
 
 
+def _dipoles(dp):
+    return PcDipoles(B=int(dp.origin.shape[0]), N=int(dp.origin.shape[1]), origin=_ptr(dp.origin), axis=_ptr(dp.axis),
+                     q=_ptr(dp.q), m1=_ptr(dp.m1), m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+
+
+def pc_dipoles_state_size(ctx, dp, dt, stream=None):
+    """pc_dipoles_state_size: the number of float64 values of a run state of these dipoles."""
+    n = _i64(0)
+    _check(ctx.lib.pc_dipoles_state_size(ctx.handle, ctypes.byref(_dipoles(dp)), float(dt), ctypes.byref(n),
+                                         _stream(stream)), "pc_dipoles_state_size")
+    return int(n.value)
+
+
 def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_index=0, precision=PC_F64,
-                   want_energy=True, want_Ed=False, out=None, near_f64=0.0, stream=None):
-    """pc_dipoles_run: dp holds [B][N] / [B][N][3] CUDA tensors; returns the dict of outputs."""
+                   want_energy=True, want_Ed=False, out=None, near_f64=0.0, want_history=True, state_in=None,
+                   state_out=None, stream=None):
+    """pc_dipoles_run: dp holds [B][N] / [B][N][3] CUDA tensors; returns the dict of outputs.
+
+    want_history=False leaves out d, d_dot, d_ddot (the run then keeps its history in a ring of the
+    context, memory independent of n_steps).  state_in / state_out: float64 CUDA tensors of
+    pc_dipoles_state_size values (resume from / save the state at the last step)."""
     B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
     S = int(n_steps) + 1
     dev = dp.origin.device
     if out is None:
-        out = dict(d=torch.empty((B, N, S), dtype=torch.float64, device=dev),
-                   d_dot=torch.empty((B, N, S), dtype=torch.float64, device=dev),
-                   d_ddot=torch.empty((B, N, S), dtype=torch.float64, device=dev))
+        out = {}
+        if want_history:
+            out.update(d=torch.empty((B, N, S), dtype=torch.float64, device=dev),
+                       d_dot=torch.empty((B, N, S), dtype=torch.float64, device=dev),
+                       d_ddot=torch.empty((B, N, S), dtype=torch.float64, device=dev))
         if want_energy:
             out["energy"] = torch.empty((B, N, S), dtype=torch.float64, device=dev)
         if want_Ed:
@@ -407,11 +428,11 @@ def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_
         if fit:
             out["gamma"] = torch.empty((B, N), dtype=torch.float64, device=dev)
             out["omega"] = torch.empty((B, N), dtype=torch.float64, device=dev)
-    d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
-                  m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+    d = _dipoles(dp)
     opts = PcRunOpts(v_max=float(v_max), ed_mode=int(ed_mode), fit=int(bool(fit)), first_index=int(first_index),
-                     precision=int(precision), near_f64=float(near_f64))
-    ro = PcRunOut(d=_ptr(out["d"]), d_dot=_ptr(out["d_dot"]), d_ddot=_ptr(out["d_ddot"]),
+                     precision=int(precision), near_f64=float(near_f64), state_in=_ptr(state_in),
+                     state_out=_ptr(state_out))
+    ro = PcRunOut(d=_ptr(out.get("d")), d_dot=_ptr(out.get("d_dot")), d_ddot=_ptr(out.get("d_ddot")),
                   energy=_ptr(out.get("energy")), Ed=_ptr(out.get("Ed")), gamma=_ptr(out.get("gamma")),
                   omega=_ptr(out.get("omega")))
     st = ctx.lib.pc_dipoles_run(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
@@ -420,10 +441,12 @@ def pc_dipoles_run(ctx, dp, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_
     return out
 
 
-def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, precision=PC_F64, stream=None):
+def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, precision=PC_F64, checkpoint_every=0,
+                       stream=None):
     """pc_dipoles_adjoint: gradients of sum w E(T) (w = dL_dEnergyFinal, [B][N] CUDA float64) with
     respect to the origins, omega0 and d0; returns (g_origin [B][N][3], g_omega0 [B][N], g_d0 [B][N]).
-    precision selects the forward run's driving field (the reverse is float64)."""
+    precision selects the forward run's driving field (the reverse is float64); checkpoint_every > 0
+    keeps the run's state every that many steps and recomputes each segment in the reverse sweep."""
     B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
     dev = dp.origin.device
     w = dL_dEnergyFinal.to(device=dev, dtype=torch.float64).contiguous()
@@ -432,7 +455,8 @@ def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, precisi
     g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
     d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
                   m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
-    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=int(precision))
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=int(precision),
+                     checkpoint_every=int(checkpoint_every))
     g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
     st = ctx.lib.pc_dipoles_adjoint(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
                                     _ptr(w), ctypes.byref(g), _stream(stream))
@@ -441,7 +465,7 @@ def pc_dipoles_adjoint(ctx, dp, dt, n_steps, dL_dEnergyFinal, v_max=0.0, precisi
 
 
 def pc_dipoles_rates_adjoint(ctx, dp, dt, n_steps, first_index, dL_dgamma=None, dL_domega=None, v_max=0.0,
-                             stream=None):
+                             checkpoint_every=0, stream=None):
     """pc_dipoles_rates_adjoint: gradients of sum(dL_dgamma gamma + dL_domega omega) of the Eq. KE
     fit; returns (gamma, omega, g_origin, g_omega0, g_d0)."""
     B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
@@ -458,7 +482,8 @@ def pc_dipoles_rates_adjoint(ctx, dp, dt, n_steps, first_index, dL_dgamma=None, 
     g_d0 = torch.empty((B, N), dtype=torch.float64, device=dev)
     d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
                   m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
-    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=1, first_index=int(first_index), precision=PC_F64)
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=1, first_index=int(first_index), precision=PC_F64,
+                     checkpoint_every=int(checkpoint_every))
     g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
     st = ctx.lib.pc_dipoles_rates_adjoint(ctx.handle, ctypes.byref(d), float(dt), int(n_steps), ctypes.byref(opts),
                                           _ptr(wg), _ptr(ww), _ptr(gamma), _ptr(omega), ctypes.byref(g),

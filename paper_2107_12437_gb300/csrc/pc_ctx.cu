@@ -51,6 +51,7 @@ extern "C" pc_status pc_ctx_destroy(pc_ctx *ctx) {
   ctx->hist_f32.release();
   ctx->charge_ref.release();
   ctx->run_scratch.release();
+  ctx->run_store.release();
   ctx->adj_scratch.release();
   if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
   if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);

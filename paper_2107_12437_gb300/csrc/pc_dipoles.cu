@@ -35,11 +35,29 @@ struct RunArgs {
   int B, N;
   const double *origin, *axis, *q, *m1, *m2, *omega0, *d0;
   double dt;
-  int64_t n_steps;
+  int64_t n_begin;    // the call's first step (absolute: 0, or the step of the state it resumes from)
+  int64_t n_steps;    // the call's last step (absolute): steps n_begin .. n_steps - 1 are advanced
   double v_max;
   int ed_mode;
-  double *d, *dd, *ddd, *energy, *Ed;
-  float4 *H32;        // [B][N][S] float32 mirror (mixed path)
+  // history store: sample n of dipole bi at bi * hs + (n & wm); wm = -1 when the store holds every
+  // sample at its index (the caller's full outputs), W - 1 for a ring of W slots (a power of two at
+  // least the deepest retarded reach of a causal block)
+  double *d, *dd, *ddd;
+  float4 *H32;        // the float32 mirror of the store (mixed path), same slots
+  int64_t hs, wm;
+  // outputs [B][N][So], So = n_steps - n_begin + 1, sample n at index n - n_begin (null: not wanted;
+  // the store's own rows when it is the caller's full outputs)
+  double *od, *odd, *oddd, *energy, *Ed;
+  int energy_loop;    // energies written per step (no full history to take them from afterwards)
+  // kinetic energies m d'^2 / (2 q^2) (and d') for the fit, per step from relative step ke_first,
+  // [B][N][So - ke_first] (null: taken from the full history after the run)
+  double *ke, *kdd;
+  int64_t ke_first, ke_len;  // absolute first step and row length of ke / kdd
+  // resume (null: a fresh run at rest with moment d0 for t <= 0): the state at step n_begin, see
+  // state layout below; state_out receives the state at step n_steps (or null)
+  const double *state_in;
+  double *state_out;
+  int64_t state_D;    // samples of history a state keeps before its step
   double *Es;         // scratch [B][N][2*kMaxBlock+1] stage fields
   int *status;
   // tables built once per run (mixed path): per-dipole float records, per-pair centre delays
@@ -47,11 +65,13 @@ struct RunArgs {
   int2 *delay;        // [B][N][N]: |R_i - R_j| / (c dt) = x + y, x integer, y the fraction (float bits)
   // [B][N][N] (mixed path): rho = (R_i - R_j) / (c dt) as (|rho|, rho . p_j, rho . p_i, p_j . p_i)
   float4 *pgeo;
-  // [B][2]: closest distance of two origins (over the run for moving ones) and largest origin
-  // speed, as the bits of non-negative doubles (ordered like the values under integer min / max)
+  // [B][3]: closest distance of two origins (over the run for moving ones), largest origin speed
+  // and largest distance of two origins, as the bits of non-negative doubles (ordered like the
+  // values under integer min / max)
   unsigned long long *rstat;
   int *kblock;        // [B] causal block length per configuration
-  double *Ehalf;      // [B][N][n_steps] E_d at t_n + dt/2 (kept for the adjoint), or null
+  int *reach;         // [B] deepest retarded reach of a block behind its start (samples): the state depth
+  double *Ehalf;      // [B][N][So - 1] E_d at t_n + dt/2 (kept for the adjoint), or null
   // grid path: sources split into nsplit slices whose partial stage fields Epart
   // [nsplit][B][N][2*kMaxBlock+1] are summed in slice order; blk = {block start, block length}
   double *Epart;
@@ -66,6 +86,13 @@ struct RunArgs {
   double e_unit;  // k_e e / (c dt)^2: the float32 driving field's unit (V/m)
   float near_L;   // mixed drive: sources whose centre is closer than this (units of c dt) go float64
 };
+
+// State of a run at step s (pc_run_opts.state_in / state_out), float64 on the device:
+//   [0] kStateMagic, [1] s, [2] D, [3] B N;  [4 .. 4 + B N) E_d(s) of each dipole;
+//   then [B][N][D + 1][3]: d, d', d'' of samples s - D .. s (oldest first; samples before 0 are the
+//   rest state d0, 0, 0).  D covers every sample a causal block starting at s can reach.
+constexpr double kStateMagic = 20547.0625;
+__host__ __device__ inline int64_t state_doubles(int64_t nbn, int64_t D) { return 4 + nbn + 3 * nbn * (D + 1); }
 
 // then the dipole's constants, so that no block recomputes them (float64 divisions are costly on
 // this GPU): gamma0, omega0^2, q^2/m, the largest charge-speed factor, 1/(q L), 1/(q c), dt/(q c),
@@ -150,12 +177,13 @@ __device__ void rk4_table(const RunArgs &a, size_t bi) {
 template <bool MIXED>
 __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop) {
   const int lane = threadIdx.x & 31;
-  const int64_t S = a.n_steps + 1;
+  const int64_t So = a.n_steps - a.n_begin + 1;
   const size_t bi = bidx(a, b, i);
   double *Es = a.Es + bi * (2 * kMaxBlock + 1);
   const double *T = a.rk4tab + bi * kTab;
   const double g0 = T[kTabC + 0], w2 = T[kTabC + 1], qm = T[kTabC + 2];
-  const double y0 = a.d[bi * S + n0], y1 = a.dd[bi * S + n0];
+  const size_t row = bi * (size_t)a.hs;
+  const double y0 = a.d[row + (n0 & a.wm)], y1 = a.dd[row + (n0 & a.wm)];
   double vx = 0.0, vy = 0.0, e2 = 0.0, e4 = 0.0;
   if (lane < kb) {
     const double e1 = Es[2 * lane];
@@ -180,16 +208,27 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
     const double yn1 = P[2] * y0 + P[3] * y1 + vy;
     const int64_t n = n0 + lane;
     const double ydd = qm * e4 - g0 * yn1 - w2 * yn0;
-    a.d[bi * S + n + 1] = yn0;
-    a.dd[bi * S + n + 1] = yn1;
-    a.ddd[bi * S + n + 1] = ydd;
+    const size_t sl = row + ((n + 1) & a.wm);
+    a.d[sl] = yn0;
+    a.dd[sl] = yn1;
+    a.ddd[sl] = ydd;
     if (MIXED)
       // the float32 mirror scaled in float32 (one rounding more than scaling in float64: below the
       // mirror's own rounding budget), the values converted on the integer units
-      a.H32[bi * S + n + 1] = make_float4(dbl2flt(yn0) * dbl2flt(T[kTabC + 4]), dbl2flt(yn1) * dbl2flt(T[kTabC + 5]),
-                                          dbl2flt(ydd) * dbl2flt(T[kTabC + 6]), 0.f);
-    if (a.Ed) a.Ed[bi * S + n + 1] = e4;
-    if (a.Ehalf) a.Ehalf[bi * a.n_steps + n] = e2;
+      a.H32[sl] = make_float4(dbl2flt(yn0) * dbl2flt(T[kTabC + 4]), dbl2flt(yn1) * dbl2flt(T[kTabC + 5]),
+                              dbl2flt(ydd) * dbl2flt(T[kTabC + 6]), 0.f);
+    const size_t o = bi * So + (size_t)(n + 1 - a.n_begin);
+    if (a.od) a.od[o] = yn0;
+    if (a.odd) a.odd[o] = yn1;
+    if (a.oddd) a.oddd[o] = ydd;
+    if (a.Ed) a.Ed[o] = e4;
+    if (a.Ehalf) a.Ehalf[bi * (So - 1) + (size_t)(n - a.n_begin)] = e2;
+    if (a.energy_loop) a.energy[o] = T[kTabC + 7] * (w2 * yn0 * yn0 + yn1 * yn1);
+    if (a.ke && n + 1 >= a.ke_first && n + 1 < a.ke_first + a.ke_len) {
+      const size_t kk = bi * (size_t)a.ke_len + (size_t)(n + 1 - a.ke_first);
+      a.ke[kk] = T[kTabC + 7] * yn1 * yn1;
+      if (a.kdd) a.kdd[kk] = yn1;
+    }
     bad = fabs(yn1) > T[kTabC + 10];
   }
   if (__any_sync(0xffffffffu, bad)) {
@@ -206,19 +245,20 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
 // p_i . E.
 __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int64_t kg_fixed,
                                  int *err, int sg0 = 0, int sg1 = 2) {
-  const int64_t S = a.n_steps + 1;
   const double cdt = kC * a.dt;
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
-  // receiver at its origin; a moving origin at the stage time (half-step index 2u)
-  const int64_t H = 2 * S - 1;
+  // receiver at its origin; a moving origin at the stage time (half-step index 2u; moving runs start
+  // at step 0 and keep every sample, so the index is absolute)
+  const int64_t H = 2 * a.n_steps + 1;
   const int64_t hh = (int64_t)llrint(2.0 * u);
   const double *Ri = a.org_pos ? a.org_pos + (bi * H + hh) * 3 : a.origin + 3 * bi;
   const double *pi = a.axis + 3 * bi;
   TrajF64 tr;
   tr.dipole = true;
-  tr.d = a.d + bj * S;
-  tr.dd = a.dd + bj * S;
-  tr.ddd = a.ddd + bj * S;
+  tr.d = a.d + bj * a.hs;
+  tr.dd = a.dd + bj * a.hs;
+  tr.ddd = a.ddd + bj * a.hs;
+  tr.wm = a.wm;
   for (int k = 0; k < 3; ++k) {
     tr.R[k] = a.origin[3 * bj + k];
     tr.ax[k] = a.axis[3 * bj + k];
@@ -280,6 +320,9 @@ __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u
 
 // float32: the dipole pair in difference form from the float32 mirror; returns p_i . E in units
 // of k_e e / (c dt)^2.  kb + xc is the retarded time of dipole j's centre.
+// RING: the store is a ring (slot j & wm); otherwise it holds every sample at its index and the mask
+// folds away at compile time (the mixed drive issues every instruction it executes)
+template <bool RING>
 __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, float xc, const float4 g, int nvalid,
                                 int *err) {
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
@@ -287,7 +330,7 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   // pair geometry from the table (fixed origins); the source's charge split and charge
   const float rn = g.x, rp = g.y, rpi = g.z, ppi = g.w;
   const float4 cj = *reinterpret_cast<const float4 *>(fj + 8);  // (p_z, mu+, mu-, q/e)
-  const HistF32RW H{a.H32 + bj * (size_t)(a.n_steps + 1)};
+  const HistF32Ring H{a.H32 + bj * (size_t)a.hs, RING ? (int)a.wm : -1};
   // fast path: both charges on the segment of the centre's retarded time (packed solve), then only
   // the driving-field projection p_i . E of the pair
   {
@@ -334,7 +377,7 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   const float rp2 = rx * px + ry * py + rz * pz;
   float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   uint8_t mk = 0;
-  const int e = dipole_net<PC_TOTAL, float, HistF32RW>(H, nvalid, kb, xc, rx, ry, rz, rn2, px, py, pz, rp2, cj.y, cj.z,
+  const int e = dipole_net<PC_TOTAL, float, HistF32Ring>(H, nvalid, kb, xc, rx, ry, rz, rn2, px, py, pz, rp2, cj.y, cj.z,
                                                      cj.w, 0.f, false, acc, mk);
   if (e) {
     *err = (e == PC_ERR_HISTORY) ? PC_ERR_CAUSALITY : e;
@@ -345,7 +388,7 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
 
 // Phase A for one receiver (one warp): stage fields E_d(n0 + (s+1)/2), s < ns, into Es[1 + s];
 // ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.
-template <bool MIXED, bool NEAR = false>
+template <bool MIXED, bool NEAR = false, bool RING = true>
 __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err,
                             int j_lo, int j_hi, double *dst, int sgsel = -1) {
   const int lane = threadIdx.x & 31;
@@ -379,7 +422,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
         return;
       }
       if (sg0 == 1) return;  // the float32 pair takes both charges at once
-      const float v = pair_drive_f32(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, geo, (int)n0 + 1, err);
+      const float v = pair_drive_f32<RING>(a, b, i, j, (int)n0 - dl.x + fl, xs - flf, geo, (int)n0 + 1, err);
       // Kahan sum over sources
       const float y = v - comp;
       const float t = accf + y;
@@ -430,46 +473,35 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
 
 // NEAR: the mixed drive sums its near sources in float64 (near_f64 > 0), a separate instantiation
 // so that the float32 source loop of the default one keeps its registers
-template <bool MIXED, bool NEAR = false>
+template <bool MIXED, bool NEAR = false, bool RING = true>
 __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a) {
   const int b = blockIdx.x;
   const int N = a.N;
-  const int64_t S = a.n_steps + 1;
+  const int64_t So = a.n_steps - a.n_begin + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double sh[kRunWarps][32];
   __shared__ int s_stop, s_K;
-  const double L = kC * a.dt;
   if (threadIdx.x == 0) {
     s_K = a.kblock[b];
     s_stop = 0;
   }
-  // ---- history sample 0: at rest with moment d0 (Sec. 3.2) ----
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const size_t bi = bidx(a, b, i);
-    a.d[bi * S] = a.d0[bi];
-    a.dd[bi * S] = 0.0;
-    a.ddd[bi * S] = 0.0;
-    if (MIXED) a.H32[bi * S] = make_float4((float)(a.d0[bi] / (a.q[bi] * L)), 0.f, 0.f, 0.f);
-    if (a.energy) {
-      const double m = a.m1[bi] * a.m2[bi] / (a.m1[bi] + a.m2[bi]);
-      const double w0 = a.omega0[bi], q = a.q[bi], x = a.d0[bi];
-      a.energy[bi * S] = m * w0 * w0 * x * x / (2.0 * q * q);
-    }
-  }
+  // (the first sample and, when resuming, the earlier ones are in the store: lo_first_kernel)
   __syncthreads();
   const int K = s_K;
-  // ---- E_d at t = 0 from the static configuration ----
+  // ---- E_d at the first step: the resumed state's, or that of the static configuration ----
   for (int i = warp; i < N; i += kRunWarps) {
-    int err = 0;
-    drive_phase<MIXED, NEAR>(a, b, i, 0, 0, sh[warp], &err, 0, N, a.Es);
-    if (err) {
-      set_status(a.status, err);
-      s_stop = 1;
+    if (!a.state_in) {
+      int err = 0;
+      drive_phase<MIXED, NEAR, RING>(a, b, i, a.n_begin, 0, sh[warp], &err, 0, N, a.Es);
+      if (err) {
+        set_status(a.status, err);
+        s_stop = 1;
+      }
     }
-    if (lane == 0 && a.Ed) a.Ed[bidx(a, b, i) * S] = a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)];
+    if (lane == 0 && a.Ed) a.Ed[bidx(a, b, i) * So] = a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)];
   }
   __syncthreads();
-  for (int64_t n0 = 0; n0 < a.n_steps; n0 += K) {
+  for (int64_t n0 = a.n_begin; n0 < a.n_steps; n0 += K) {
     if (s_stop) break;
     const int kb = (int)min((int64_t)K, a.n_steps - n0);
     // phase A: all stage fields of the block.  A float64 drive whose lanes are all taken while
@@ -480,7 +512,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     const bool xsplit = !MIXED && 2 * N <= kRunWarps && 2 * N > 32 / nst;
     for (int w = warp; w < (xsplit ? 2 * N : N); w += kRunWarps) {
       int err = 0;
-      drive_phase<MIXED, NEAR>(a, b, xsplit ? w >> 1 : w, n0, nst, sh[warp], &err, 0, N,
+      drive_phase<MIXED, NEAR, RING>(a, b, xsplit ? w >> 1 : w, n0, nst, sh[warp], &err, 0, N,
                                (xsplit && (w & 1)) ? a.Epart : a.Es, xsplit ? w & 1 : -1);
       if (err) {
         set_status(a.status, err);
@@ -503,6 +535,87 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
       if (stop && lane == 0) s_stop = 1;
     }
     __syncthreads();
+  }
+}
+
+// The first sample of the call (step n_begin) into the store and the outputs: at rest with moment d0
+// (Sec. 3.2) for a fresh run; for a resumed one, the state's samples n_begin - D .. n_begin into the
+// store's slots and its E_d(n_begin) into the stage fields.  Grid-stride over the dipoles; runs after
+// lo_tables_kernel (the mirror's scales).
+template <bool MIXED>
+__global__ void lo_first_kernel(const RunArgs a) {
+  const int64_t nbn = (int64_t)a.B * a.N;
+  const int64_t So = a.n_steps - a.n_begin + 1;
+  const double L = kC * a.dt;
+  for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < nbn; bi += (int64_t)gridDim.x * blockDim.x) {
+    const double *T = a.rk4tab + bi * kTab;
+    const size_t row = (size_t)bi * a.hs;
+    if (!a.state_in) {
+      const size_t sl = row + (a.n_begin & a.wm);
+      a.d[sl] = a.d0[bi];
+      a.dd[sl] = 0.0;
+      a.ddd[sl] = 0.0;
+      if (MIXED) a.H32[sl] = make_float4((float)(a.d0[bi] / (a.q[bi] * L)), 0.f, 0.f, 0.f);
+    } else {
+      const int64_t D = (int64_t)a.state_in[2];
+      const double *smp = a.state_in + 4 + nbn + (size_t)bi * (D + 1) * 3;
+      for (int64_t t = 0; t <= D; ++t) {
+        const int64_t k = a.n_begin - D + t;
+        if (k < 0) continue;
+        const size_t sl = row + (k & a.wm);
+        const double x = smp[3 * t], v = smp[3 * t + 1], ac = smp[3 * t + 2];
+        a.d[sl] = x;
+        a.dd[sl] = v;
+        a.ddd[sl] = ac;
+        if (MIXED)
+          a.H32[sl] = (k == 0) ? make_float4((float)(x / (a.q[bi] * L)), 0.f, 0.f, 0.f)
+                               : make_float4(dbl2flt(x) * dbl2flt(T[kTabC + 4]), dbl2flt(v) * dbl2flt(T[kTabC + 5]),
+                                             dbl2flt(ac) * dbl2flt(T[kTabC + 6]), 0.f);
+      }
+      a.Es[bi * (2 * kMaxBlock + 1)] = a.state_in[4 + bi];
+    }
+    const size_t sl = row + (a.n_begin & a.wm);
+    const double x = a.d[sl], v = a.dd[sl], ac = a.ddd[sl];
+    const size_t o = (size_t)bi * So;
+    if (a.od) a.od[o] = x;
+    if (a.odd) a.odd[o] = v;
+    if (a.oddd) a.oddd[o] = ac;
+    if (a.energy) a.energy[o] = T[kTabC + 7] * (T[kTabC + 1] * x * x + v * v);
+    if (a.ke && a.n_begin >= a.ke_first && a.n_begin < a.ke_first + a.ke_len) {
+      const size_t kk = (size_t)bi * a.ke_len + (size_t)(a.n_begin - a.ke_first);
+      a.ke[kk] = T[kTabC + 7] * v * v;
+      if (a.kdd) a.kdd[kk] = v;
+    }
+  }
+}
+
+// The state at step n_steps (the call's last) from the store and the stage fields: see the state
+// layout above.  Grid-stride over the dipoles and their samples.
+__global__ void lo_save_kernel(const RunArgs a, int64_t D) {
+  const int64_t nbn = (int64_t)a.B * a.N;
+  double *st = a.state_out;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st[0] = kStateMagic;
+    st[1] = (double)a.n_steps;
+    st[2] = (double)D;
+    st[3] = (double)nbn;
+  }
+  const int64_t tot = nbn * (D + 1);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bi = idx / (D + 1), t = idx % (D + 1);
+    const int64_t k = a.n_steps - D + t;
+    double *o = st + 4 + nbn + 3 * idx;
+    if (k < 0) {
+      o[0] = a.d0[bi];
+      o[1] = 0.0;
+      o[2] = 0.0;
+    } else {
+      const size_t sl = (size_t)bi * a.hs + (k & a.wm);
+      o[0] = a.d[sl];
+      o[1] = a.dd[sl];
+      o[2] = a.ddd[sl];
+    }
+    if (t == 0) st[4 + bi] = a.Es[bi * (2 * kMaxBlock + 1)];
   }
 }
 
@@ -537,20 +650,26 @@ __global__ void lo_tables_kernel(const RunArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int t = 1; t < blockDim.x; ++t) smax = fmax(smax, s_smax[t]);
-    const double rmin = __longlong_as_double((long long)a.rstat[2 * b]);
-    const double vmax = __longlong_as_double((long long)a.rstat[2 * b + 1]);
+    const double rmin = __longlong_as_double((long long)a.rstat[3 * b]);
+    const double vmax = __longlong_as_double((long long)a.rstat[3 * b + 1]);
+    const double rmax = __longlong_as_double((long long)a.rstat[3 * b + 2]);
     // within a block of K steps a source origin moves at most vmax K dt closer
     const double kk = floor((rmin - 3.0 * smax) / (L * (1.0 + vmax / kC)));
     a.kblock[b] = (int)fmax(1.0, fmin((double)kMaxBlock, kk));
+    // the oldest sample a block's retarded times reach, behind the block's start: the largest
+    // centre delay, the charges' offsets (three times the initial amplitude) and a few samples of
+    // the solves' search
+    a.reach[b] = (int)fmin(ceil(rmax / L) + ceil(3.0 * smax / L) + 8.0, 1073741824.0);
   }
 }
 
-// Presets a.rstat to (a large distance, 0): 0x7f7f... is about 1.4e306 as a double.
+// Presets a.rstat to (a large distance, 0, 0): 0x7f7f... is about 1.4e306 as a double.
 __global__ void lo_rstat_init_kernel(const RunArgs a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.B) return;
-  a.rstat[2 * b] = 0x7f7f7f7f7f7f7f7full;
-  a.rstat[2 * b + 1] = 0ull;
+  a.rstat[3 * b] = 0x7f7f7f7f7f7f7f7full;
+  a.rstat[3 * b + 1] = 0ull;
+  a.rstat[3 * b + 2] = 0ull;
 }
 
 // Per pair (i, j) of a configuration: the centre delay |R_i - R_j| / (c dt) (the first guess of
@@ -559,13 +678,13 @@ __global__ void lo_rstat_init_kernel(const RunArgs a) {
 // for moving origins) and largest origin speed, for the causal block length.  Grid: x over pair
 // blocks, y over configurations.
 __global__ void __launch_bounds__(256) lo_pairs_kernel(const RunArgs a) {
-  __shared__ double s_r[256], s_v[256];
+  __shared__ double s_r[256], s_v[256], s_x[256];
   const int N = a.N;
   const int64_t NN = (int64_t)N * N;
   const double L = kC * a.dt;
   const int64_t H = 2 * a.n_steps + 1;
   for (int b = blockIdx.y; b < a.B; b += gridDim.y) {
-    double rmin = 1e300, vmax = 0.0;
+    double rmin = 1e300, vmax = 0.0, rmax = 0.0;
     for (int64_t ij = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ij < NN;
          ij += (int64_t)gridDim.x * blockDim.x) {
       const int i = (int)(ij / N), j = (int)(ij % N);
@@ -575,6 +694,7 @@ __global__ void __launch_bounds__(256) lo_pairs_kernel(const RunArgs a) {
       const double r = sqrt(dx * dx + dy * dy + dz * dz);
       if (i != j) {
         rmin = fmin(rmin, r);
+        rmax = fmax(rmax, r);
         if (a.org_pos) {
           // closest approach of the two origins over the run
           for (int64_t h = 0; h < H; ++h) {
@@ -603,17 +723,20 @@ __global__ void __launch_bounds__(256) lo_pairs_kernel(const RunArgs a) {
     }
     s_r[threadIdx.x] = rmin;
     s_v[threadIdx.x] = vmax;
+    s_x[threadIdx.x] = rmax;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
       if ((int)threadIdx.x < w) {
         s_r[threadIdx.x] = fmin(s_r[threadIdx.x], s_r[threadIdx.x + w]);
         s_v[threadIdx.x] = fmax(s_v[threadIdx.x], s_v[threadIdx.x + w]);
+        s_x[threadIdx.x] = fmax(s_x[threadIdx.x], s_x[threadIdx.x + w]);
       }
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      atomicMin(a.rstat + 2 * b, (unsigned long long)__double_as_longlong(s_r[0]));
-      atomicMax(a.rstat + 2 * b + 1, (unsigned long long)__double_as_longlong(s_v[0]));
+      atomicMin(a.rstat + 3 * b, (unsigned long long)__double_as_longlong(s_r[0]));
+      atomicMax(a.rstat + 3 * b + 1, (unsigned long long)__double_as_longlong(s_v[0]));
+      atomicMax(a.rstat + 3 * b + 2, (unsigned long long)__double_as_longlong(s_x[0]));
     }
     __syncthreads();
   }
@@ -622,31 +745,17 @@ __global__ void __launch_bounds__(256) lo_pairs_kernel(const RunArgs a) {
 // Grid-wide phases for large configurations: history sample 0, stage fields (one warp per
 // receiver and source slice) and RK4 (one thread per receiver), one launch each per causal block;
 // the block loop runs inside one CUDA graph (a device-side while loop).
-template <bool MIXED>
+// Grid path: the block cursor starts at the call's first step.
 __global__ void lo_init_kernel(const RunArgs a, int K) {
-  const int64_t S = a.n_steps + 1;
-  const double L = kC * a.dt;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.blk[0] = 0;
+    a.blk[0] = a.n_begin;
     a.blk[1] = K;
-  }
-  for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < (int64_t)a.B * a.N;
-       bi += (int64_t)gridDim.x * blockDim.x) {
-    a.d[bi * S] = a.d0[bi];
-    a.dd[bi * S] = 0.0;
-    a.ddd[bi * S] = 0.0;
-    if (MIXED) a.H32[bi * S] = make_float4((float)(a.d0[bi] / (a.q[bi] * L)), 0.f, 0.f, 0.f);
-    if (a.energy) {
-      const double m = a.m1[bi] * a.m2[bi] / (a.m1[bi] + a.m2[bi]);
-      const double w0 = a.omega0[bi], q = a.q[bi], x = a.d0[bi];
-      a.energy[bi * S] = m * w0 * w0 * x * x / (2.0 * q * q);
-    }
   }
 }
 
 // Grid path, phase A: one warp per (receiver, source slice).  ns < 0 takes the block from the
 // device cursor a.blk (graph replay); ns == 0 evaluates E_d(0).
-template <bool MIXED, bool NEAR = false>
+template <bool MIXED, bool NEAR = false, bool RING = true>
 __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs a, int64_t n0, int ns) {
   __shared__ double sh[kRunWarps][32];
   if (*((volatile int *)a.status)) return;  // an earlier block failed
@@ -664,7 +773,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs 
   const int j_lo = min(a.N, z * chunk), j_hi = min(a.N, j_lo + chunk);
   double *dst = a.nsplit > 1 ? a.Epart + (size_t)z * a.B * a.N * (2 * kMaxBlock + 1) : a.Es;
   int err = 0;
-  drive_phase<MIXED, NEAR>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
+  drive_phase<MIXED, NEAR, RING>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
   if (err) set_status(a.status, err);
 }
 
@@ -680,12 +789,13 @@ __device__ __forceinline__ void sum_slices(const RunArgs &a, size_t bi, int lo, 
   }
 }
 
-// E_d(0): slice sums and the first driving-field sample.
+// E_d at the first step: slice sums (a fresh run; a resumed one has it from its state) and the first
+// driving-field sample.
 __global__ void lo_start_kernel(const RunArgs a) {
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= (int64_t)a.B * a.N) return;
-  sum_slices(a, bi, 0, 0);
-  if (a.Ed) a.Ed[bi * (a.n_steps + 1)] = a.Es[bi * (2 * kMaxBlock + 1)];
+  if (!a.state_in) sum_slices(a, bi, 0, 0);
+  if (a.Ed) a.Ed[bi * (a.n_steps - a.n_begin + 1)] = a.Es[bi * (2 * kMaxBlock + 1)];
 }
 
 template <bool MIXED>
@@ -718,6 +828,7 @@ __global__ void lo_advance_kernel(const RunArgs a, cudaGraphConditionalHandle lo
 // ------------------------------------------------------------------------------------------------
 // Eq. dipoleE of every history sample, E = m (w0^2 d^2 + d'^2) / (2 q^2), after the run (off the
 // per-block path of the time loop)
+// (full store only: hs = n_steps + 1, n_begin = 0)
 __global__ void energy_kernel(const RunArgs a) {
   const int64_t S = a.n_steps + 1;
   const int64_t n = (int64_t)a.B * a.N * S;
@@ -728,14 +839,15 @@ __global__ void energy_kernel(const RunArgs a) {
   }
 }
 
+// kinetic energies m d'^2 / (2 q^2) of the full store (the same expression as the per-step ones of
+// rk4_block_warp, so that both stores give the fit the same series)
 __global__ void ke_series_kernel(const RunArgs a, double *ke) {
   const int64_t S = a.n_steps + 1;
   const int64_t n = (int64_t)a.B * a.N * S;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t bi = idx / S;
-    const double m = a.m1[bi] * a.m2[bi] / (a.m1[bi] + a.m2[bi]);
-    const double q = a.q[bi], v = a.dd[idx];
-    ke[idx] = m * v * v / (2.0 * q * q);
+    const double *T = a.rk4tab + (idx / S) * kTab;
+    const double v = a.dd[idx];
+    ke[idx] = T[kTabC + 7] * v * v;
   }
 }
 
@@ -1170,8 +1282,8 @@ struct FitAdjArgs {
   double dt;
   const double *gamma, *omega, *amp, *phase;  // the optimum, physical units
   const double *dL_dgamma, *dL_domega;        // [K]
-  const double *dd, *m1, *m2, *q;             // forward d' history and the dipoles' constants
-  double *mu;                                 // [K][S][3] history adjoints (d' component += ...)
+  const double *dd, *m1, *m2, *q;             // forward d' ([K][S] like ke) and the dipoles' constants
+  double *seed;                               // [K][S - first] out: the cotangent of d'_n, n >= first
   int *status;
 };
 
@@ -1207,7 +1319,7 @@ __global__ void __launch_bounds__(kFitThreads) ke_fit_adjoint_kernel(const FitAd
   const double m = fa.m1[k] * fa.m2[k] / (fa.m1[k] + fa.m2[k]), qq = fa.q[k];
   const double kv = m / (qq * qq);
   const double *ddk = fa.dd + (size_t)k * fa.S + fa.first;
-  double *muk = fa.mu + ((size_t)k * fa.S + fa.first) * 3;
+  double *sk = fa.seed + (size_t)k * (fa.S - fa.first);
   // dL/dy_n = z . J_n / A_g, into the adjoint of d'_n
   const int64_t chunk = (n + kFitThreads - 1) / kFitThreads;
   const int64_t i0 = (int64_t)threadIdx.x * chunk, i1 = min(n, i0 + chunk);
@@ -1223,7 +1335,7 @@ __global__ void __launch_bounds__(kFitThreads) ke_fit_adjoint_kernel(const FitAd
     const double mA = A * en * iA;
     const double J0 = en * ss, J1 = -u * mA * ss, J3 = mA * s2, J2 = J3 * u;
     const double dy = (z0 * J0 + z1 * J1 + z2 * J2 + z3 * J3) * iA;
-    muk[3 * i + 1] += dy * kv * ddk[i];
+    sk[i] = dy * kv * ddk[i];
     const double s1 = sn * cw + cs * sw;
     cs = cs * cw - sn * sw;
     sn = s1;
@@ -1247,6 +1359,33 @@ extern "C" pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t
 }
 
 namespace pc {
+// The instantiation of the drive for a run: float64, or mixed with or without near float64 sources,
+// the mixed ones specialised for a full-history store (no slot mask)
+static void *drive_kernel_for(const RunArgs &a, bool mixed) {
+  if (!mixed) return (void *)lo_drive_kernel<false>;
+  const bool ring = a.wm >= 0;
+  if (a.near_L > 0.f)
+    return ring ? (void *)lo_drive_kernel<true, true, true> : (void *)lo_drive_kernel<true, true, false>;
+  return ring ? (void *)lo_drive_kernel<true, false, true> : (void *)lo_drive_kernel<true, false, false>;
+}
+static void *run_kernel_for(const RunArgs &a, bool mixed) {
+  if (!mixed) return (void *)lo_run_kernel<false>;
+  const bool ring = a.wm >= 0;
+  if (a.near_L > 0.f)
+    return ring ? (void *)lo_run_kernel<true, true, true> : (void *)lo_run_kernel<true, true, false>;
+  return ring ? (void *)lo_run_kernel<true, false, true> : (void *)lo_run_kernel<true, false, false>;
+}
+static cudaError_t launch_run_args(void *fn, dim3 grid, dim3 block, const RunArgs &a, cudaStream_t st) {
+  RunArgs aa = a;
+  void *args[] = {&aa};
+  return cudaLaunchKernel(fn, grid, block, args, 0, st);
+}
+static cudaError_t launch_drive(void *fn, dim3 grid, const RunArgs &a, int64_t n0, int ns, cudaStream_t st) {
+  RunArgs aa = a;
+  void *args[] = {&aa, &n0, &ns};
+  return cudaLaunchKernel(fn, grid, dim3(kRunWarps * 32), args, 0, st);
+}
+
 // The causal-block loop of the grid path as one CUDA graph: a while node whose body is
 // drive -> RK4 -> advance.  The advance kernel moves the device cursor a.blk by one block and
 // clears the loop condition after the last block or after an error, so the loop ends after at
@@ -1286,8 +1425,7 @@ static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, di
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof(kp));
   cudaGraphNode_t n1, n2, n3;
-  kp.func = !mixed ? (void *)lo_drive_kernel<false>
-                    : (a.near_L > 0.f ? (void *)lo_drive_kernel<true, true> : (void *)lo_drive_kernel<true>);
+  kp.func = drive_kernel_for(a, mixed);
   kp.gridDim = dgrid;
   kp.blockDim = dim3(kRunWarps * 32);
   kp.kernelParams = drive_args;
@@ -1308,50 +1446,90 @@ static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, di
   return cudaGraphLaunch(ex, st) == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
-// Forward run (Algorithm 1); Ehalf (or null) receives E_d at the half steps for the adjoint.
+// Internal knobs of run_impl beyond pc_run_opts (the adjoint's and the state-size query's).
+struct RunPlan {
+  double *Ehalf = nullptr;                  // [B][N][n_steps] E_d at the half steps, or null
+  int *k_out = nullptr;                     // the shortest causal block over the batch
+  const pc_dipole_motion *motion = nullptr;
+  const int2 **delay_out = nullptr;         // the pair delay table (valid until the context's next run)
+  const double **rk4tab_out = nullptr;      // the per-dipole tables (idem)
+  // a history store supplied by the caller of run_impl, [B][N][shs] with sample n at slot n & swm
+  // (null: the caller's full outputs, or a ring of the context)
+  double *sd = nullptr, *sdd = nullptr, *sddd = nullptr;
+  int64_t shs = 0, swm = -1;
+  // per-step kinetic energies and d' over absolute steps [ke_first, ke_first + ke_len), or null
+  double *ke = nullptr, *kdd = nullptr;
+  int64_t ke_first = 0, ke_len = 0;
+  int64_t *reach_out = nullptr;             // the state depth D of this geometry
+  bool tables_only = false;                 // stop after the tables (the state-size query)
+};
+
+static int64_t pow2_at_least(int64_t x) {
+  int64_t w = 1;
+  while (w < x) w <<= 1;
+  return w;
+}
+
+// Forward run (Algorithm 1) over steps n_begin .. n_begin + n_steps, n_begin = 0 or the step of the
+// resumed state.  The history the retarded fields read is kept in one of three stores: the caller's
+// full d, d', d'' outputs (all three given, no resume), a store supplied through the plan (the
+// adjoint's segment ring), or a ring of the context of W = 2^k >= D + 16 + 2 slots per dipole, D the
+// deepest retarded reach of a causal block (largest origin distance / (c dt) plus the charges'
+// offsets and a margin): memory O(B N D) whatever the number of steps.
 static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps, const pc_run_opts *opts,
-                          const pc_run_out *out, double *Ehalf, cudaStream_t st, int *k_out = nullptr,
-                          const pc_dipole_motion *motion = nullptr, const int2 **delay_out = nullptr) {
+                          const pc_run_out *out, cudaStream_t st, const RunPlan &pl = RunPlan()) {
   if (!ctx || !dp || !opts || !out) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0) || n_steps < 0) return PC_ERR_ARG;
   if (!dp->origin || !dp->axis || !dp->q || !dp->m1 || !dp->m2 || !dp->omega0 || !dp->d0) return PC_ERR_ARG;
-  if (!out->d || !out->d_dot || !out->d_ddot) return PC_ERR_ARG;
   if (opts->ed_mode != 0 && opts->ed_mode != 1) return PC_ERR_ARG;
   if (opts->precision != PC_F64 && opts->precision != PC_MIXED) return PC_ERR_ARG;
   if (!(opts->near_f64 >= 0.0) || !std::isfinite(opts->near_f64)) return PC_ERR_ARG;
   if (opts->fit && (!out->gamma || !out->omega || opts->first_index < 0 || n_steps + 1 - opts->first_index < 8))
     return PC_ERR_ARG;
-  const int64_t S = n_steps + 1;
+  const pc_dipole_motion *motion = pl.motion;
   const size_t nbn = (size_t)dp->B * dp->N;
   const bool mixed = opts->precision == PC_MIXED;
   if (motion && (mixed || !motion->pos || !motion->vel || !motion->acc)) return PC_ERR_ARG;
-  if (mixed && S > ((int64_t)1 << 30)) return PC_ERR_ARG;
   if (dp->N > pc::kSmallN && dp->B > 65535) return PC_ERR_ARG;  // grid path: configurations on grid y
-  // scratch: stage fields, float32 mirror (mixed), dipole records, pair delays (mixed), block
-  // lengths, kinetic energies for the fit
+  // the resumed state's step (and a check of its header)
+  int64_t n_begin = 0, D_in = 0;
+  if (opts->state_in) {
+    if (motion) return PC_ERR_ARG;  // moving origins run from t = 0 with every sample kept
+    double hdr[4];
+    if (cudaMemcpyAsync(hdr, opts->state_in, sizeof(hdr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return PC_ERR_CUDA;
+    if (hdr[0] != kStateMagic || hdr[3] != (double)nbn || !(hdr[1] >= 0.0) || hdr[1] != std::floor(hdr[1]) ||
+        !(hdr[2] >= 1.0) || hdr[1] > 9.0e15)
+      return PC_ERR_ARG;
+    n_begin = (int64_t)hdr[1];
+    D_in = (int64_t)hdr[2];
+  }
+  const int64_t So = n_steps + 1;
+  const int64_t n_end = n_begin + n_steps;
+  if (mixed && n_end + 1 > ((int64_t)1 << 30)) return PC_ERR_ARG;  // 32-bit sample indices
+  const bool full_store = !pl.sd && !opts->state_in && out->d && out->d_dot && out->d_ddot;
+  if (motion && !full_store) return PC_ERR_ARG;
+  // ---- phase 1: per-run tables (pair delays and geometry, dipole records, RK4 powers, block
+  // lengths, reach) in the run scratch ----
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const bool grid = dp->N > pc::kSmallN;
   const size_t es_bytes = al(nbn * (2 * pc::kMaxBlock + 1) * sizeof(double));
-  const size_t h_bytes = mixed ? al(nbn * S * sizeof(float4)) : 0;
   const size_t f_bytes = al(nbn * pc::kDipF * sizeof(float));
   const size_t dl_bytes = al(nbn * dp->N * sizeof(int2));
   const size_t geo_bytes = mixed ? al(nbn * dp->N * sizeof(float4)) : 0;
-  const size_t rs_bytes = al(2 * (size_t)dp->B * sizeof(unsigned long long));
-  const size_t k_bytes = al(dp->B * sizeof(int));
-  const size_t ke_bytes = opts->fit ? al(nbn * S * sizeof(double)) : 0;
-  const bool grid = dp->N > pc::kSmallN;
-  // grid path: the source slices' partial stage fields; one configuration per CTA: the second
-  // charge's partial sums when the two charges run on two warps
+  const size_t rs_bytes = al(3 * (size_t)dp->B * sizeof(unsigned long long));
+  const size_t k_bytes = al(2 * (size_t)dp->B * sizeof(int));
   const size_t part_bytes = grid ? al((size_t)pc::kMaxSplit * es_bytes) : es_bytes;
   const size_t blk_bytes = al(2 * sizeof(int64_t));
   const size_t tab_bytes = al(nbn * pc::kTab * sizeof(double));
-  const size_t part_off = es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes + ke_bytes;
-  const size_t blk_off = part_off + part_bytes;
-  const size_t tab_off = blk_off + blk_bytes;
-  const size_t geo_off = tab_off + tab_bytes;
-  const size_t rs_off = geo_off + geo_bytes;
+  const size_t f_off = es_bytes, dl_off = f_off + f_bytes, k_off = dl_off + dl_bytes;
+  const size_t part_off = k_off + k_bytes, blk_off = part_off + part_bytes, tab_off = blk_off + blk_bytes;
+  const size_t geo_off = tab_off + tab_bytes, rs_off = geo_off + geo_bytes;
   if (ctx->run_scratch.reserve(rs_off + rs_bytes) != cudaSuccess) return PC_ERR_CUDA;
   char *scr = (char *)ctx->run_scratch.ptr;
   pc::RunArgs a;
+  memset(&a, 0, sizeof(a));
   a.B = dp->B;
   a.N = dp->N;
   a.origin = dp->origin;
@@ -1362,23 +1540,18 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.omega0 = dp->omega0;
   a.d0 = dp->d0;
   a.dt = dt;
-  a.n_steps = n_steps;
+  a.n_begin = n_begin;
+  a.n_steps = n_end;
   a.v_max = opts->v_max > 0.0 ? opts->v_max : pc::kC / 100.0;
   a.ed_mode = opts->ed_mode;
-  a.d = out->d;
-  a.dd = out->d_dot;
-  a.ddd = out->d_ddot;
-  a.energy = out->energy;
-  a.Ed = out->Ed;
   a.Es = (double *)scr;
-  a.H32 = mixed ? (float4 *)(scr + es_bytes) : nullptr;
-  a.dipf = (float *)(scr + es_bytes + h_bytes);
-  a.delay = (int2 *)(scr + es_bytes + h_bytes + f_bytes);
+  a.dipf = (float *)(scr + f_off);
+  a.delay = (int2 *)(scr + dl_off);
+  a.kblock = (int *)(scr + k_off);
+  a.reach = a.kblock + dp->B;
   a.pgeo = mixed ? (float4 *)(scr + geo_off) : nullptr;
   a.rstat = (unsigned long long *)(scr + rs_off);
-  if (delay_out) *delay_out = a.delay;  // valid until the context's next run
-  a.kblock = (int *)(scr + es_bytes + h_bytes + f_bytes + dl_bytes);
-  a.Ehalf = Ehalf;
+  a.Ehalf = pl.Ehalf;
   a.Epart = (double *)(scr + part_off);
   a.nsplit = 1;
   a.blk = nullptr;
@@ -1389,7 +1562,8 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.org_vel = motion ? motion->vel : nullptr;
   a.org_acc = motion ? motion->acc : nullptr;
   a.status = ctx->d_status;
-  char *ke_base = scr + es_bytes + h_bytes + f_bytes + dl_bytes + k_bytes;
+  if (pl.delay_out) *pl.delay_out = a.delay;
+  if (pl.rk4tab_out) *pl.rk4tab_out = a.rk4tab;
   {
     // pair tables and the per-configuration distance / speed extremes, then the per-dipole tables
     const int64_t NN = (int64_t)dp->N * dp->N;
@@ -1399,30 +1573,93 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     pc::lo_pairs_kernel<<<dim3(gx, gy), 256, 0, st>>>(a);
   }
   pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
-  if (k_out) {
-    // the shortest causal block over the batch, for the caller
-    std::vector<int> kb(dp->B);
-    if (cudaMemcpyAsync(kb.data(), a.kblock, dp->B * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return PC_ERR_CUDA;
-    *k_out = pc::kMaxBlock;
-    for (int v : kb) *k_out = std::min(*k_out, v);
+  // block lengths and reaches back on the host
+  std::vector<int> kr(2 * (size_t)dp->B);
+  if (cudaMemcpyAsync(kr.data(), a.kblock, kr.size() * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PC_ERR_CUDA;
+  int K = pc::kMaxBlock;
+  int64_t D = 1;
+  for (int b = 0; b < dp->B; ++b) {
+    K = std::min(K, kr[b]);
+    D = std::max<int64_t>(D, kr[dp->B + b]);
   }
+  if (pl.k_out) *pl.k_out = K;
+  if (pl.reach_out) *pl.reach_out = D;
+  if (pl.tables_only) return PC_OK;
+  if (opts->state_in && D_in < D) return PC_ERR_ARG;  // a state of another geometry
+  // ---- phase 2: the history store, its mirror and the per-step fit inputs ----
+  const int64_t W = pow2_at_least(D + pc::kMaxBlock + 2);
+  int64_t hs, wm;
+  if (full_store) {
+    hs = So;
+    wm = -1;
+  } else if (pl.sd) {
+    hs = pl.shs;
+    wm = pl.swm;
+    if (wm >= 0 && wm + 1 < W) return PC_ERR_ARG;
+  } else {
+    hs = W;
+    wm = W - 1;
+  }
+  const bool own_ring = !full_store && !pl.sd;
+  const size_t ring_b = own_ring ? al(nbn * (size_t)hs * sizeof(double)) : 0;
+  const size_t h_bytes = mixed ? al(nbn * (size_t)hs * sizeof(float4)) : 0;
+  // the fit's kinetic energies: after the run from the full store, or per step into their own rows
+  const int64_t first = opts->fit ? opts->first_index : 0;
+  const size_t ke_b = opts->fit ? al(nbn * (size_t)(full_store ? So : So - first) * sizeof(double)) : 0;
+  if (ctx->run_store.reserve(3 * ring_b + h_bytes + ke_b) != cudaSuccess) return PC_ERR_CUDA;
+  char *sto = (char *)ctx->run_store.ptr;
+  a.hs = hs;
+  a.wm = wm;
+  if (full_store) {
+    a.d = out->d;
+    a.dd = out->d_dot;
+    a.ddd = out->d_ddot;
+  } else if (pl.sd) {
+    a.d = pl.sd;
+    a.dd = pl.sdd;
+    a.ddd = pl.sddd;
+  } else {
+    a.d = (double *)sto;
+    a.dd = (double *)(sto + ring_b);
+    a.ddd = (double *)(sto + 2 * ring_b);
+  }
+  if (!full_store) {
+    a.od = out->d;
+    a.odd = out->d_dot;
+    a.oddd = out->d_ddot;
+  }
+  a.H32 = mixed ? (float4 *)(sto + 3 * ring_b) : nullptr;
+  a.energy = out->energy;
+  a.energy_loop = (out->energy && !full_store) ? 1 : 0;
+  a.Ed = out->Ed;
+  double *ke_fit = opts->fit ? (double *)(sto + 3 * ring_b + h_bytes) : nullptr;
+  if (pl.ke) {
+    a.ke = pl.ke;
+    a.kdd = pl.kdd;
+    a.ke_first = pl.ke_first;
+    a.ke_len = pl.ke_len;
+  } else if (opts->fit && !full_store) {
+    a.ke = ke_fit;
+    a.ke_first = n_begin + first;
+    a.ke_len = So - first;
+  }
+  a.state_in = opts->state_in;
+  a.state_out = opts->state_out;
+  a.state_D = D;
+  const unsigned rgrid = (unsigned)((nbn + 127) / 128);
+  if (mixed) pc::lo_first_kernel<true><<<rgrid, 128, 0, st>>>(a);
+  else pc::lo_first_kernel<false><<<rgrid, 128, 0, st>>>(a);
   if (dp->N <= pc::kSmallN) {
     // small configurations: one persistent CTA each, the time loop inside
-    if (mixed && a.near_L > 0.f) pc::lo_run_kernel<true, true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
-    else if (mixed) pc::lo_run_kernel<true><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
-    else pc::lo_run_kernel<false><<<dp->B, pc::kRunWarps * 32, 0, st>>>(a);
+    if (pc::launch_run_args(pc::run_kernel_for(a, mixed), dim3(dp->B), dim3(pc::kRunWarps * 32), a, st) !=
+        cudaSuccess)
+      return PC_ERR_CUDA;
   } else {
     // large configurations: grid-wide phases, one drive and one RK4 launch per causal block of the
-    // shortest block length over the batch
-    std::vector<int> kb(dp->B);
-    if (cudaMemcpyAsync(kb.data(), a.kblock, dp->B * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return PC_ERR_CUDA;
-    int K = pc::kMaxBlock;
-    for (int v : kb) K = std::min(K, v);
-    // sources split so that about two resident warps per SM slot are in flight
+    // shortest block length over the batch; sources split so that about two resident warps per SM
+    // slot are in flight
     const int64_t target = (int64_t)ctx->num_sms * 64;
     int nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, (target + (int64_t)nbn - 1) / (int64_t)nbn),
                                         std::max(1, dp->N / 8));
@@ -1431,12 +1668,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     a.Epart = nsplit > 1 ? (double *)(scr + part_off) : nullptr;
     a.blk = (int64_t *)(scr + blk_off);
     const dim3 dgrid((unsigned)((dp->N + pc::kRunWarps - 1) / pc::kRunWarps), (unsigned)dp->B, (unsigned)nsplit);
-    const unsigned rgrid = (unsigned)((nbn + 127) / 128);
-    if (mixed) pc::lo_init_kernel<true><<<rgrid, 128, 0, st>>>(a, K);
-    else pc::lo_init_kernel<false><<<rgrid, 128, 0, st>>>(a, K);
-    if (mixed && a.near_L > 0.f) pc::lo_drive_kernel<true, true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
-    else if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
-    else pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, 0, 0);
+    pc::lo_init_kernel<<<1, 32, 0, st>>>(a, K);
+    void *drive = pc::drive_kernel_for(a, mixed);
+    if (!opts->state_in && pc::launch_drive(drive, dgrid, a, n_begin, 0, st) != cudaSuccess) return PC_ERR_CUDA;
     pc::lo_start_kernel<<<rgrid, 128, 0, st>>>(a);
     if (n_steps > 0) {
       // the block loop runs as one graph with a device-side while node; the host-driven loop (one
@@ -1447,12 +1681,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
       pc_status gs = (hl && hl[0] == '1') ? PC_ERR_CUDA : pc::launch_block_loop(ctx, a, mixed, dgrid, rgrid, st);
       if (gs != PC_OK) {
         cudaGetLastError();
-        for (int64_t n0 = 0; n0 < n_steps; n0 += K) {
-          const int kb = (int)std::min<int64_t>(K, n_steps - n0);
-          if (mixed && a.near_L > 0.f)
-            pc::lo_drive_kernel<true, true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
-          else if (mixed) pc::lo_drive_kernel<true><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
-          else pc::lo_drive_kernel<false><<<dgrid, pc::kRunWarps * 32, 0, st>>>(a, n0, 2 * kb);
+        for (int64_t n0 = n_begin; n0 < n_end; n0 += K) {
+          const int kb = (int)std::min<int64_t>(K, n_end - n0);
+          pc::launch_drive(drive, dgrid, a, n0, 2 * kb, st);
           const unsigned wgrid = (unsigned)((nbn * 32 + 127) / 128);
           if (mixed) pc::lo_rk4_kernel<true><<<wgrid, 128, 0, st>>>(a, n0, kb);
           else pc::lo_rk4_kernel<false><<<wgrid, 128, 0, st>>>(a, n0, kb);
@@ -1461,12 +1692,12 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
       }
     }
   }
-  if (a.energy) pc::energy_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a);
+  if (opts->state_out) pc::lo_save_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, D);
+  if (a.energy && !a.energy_loop) pc::energy_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a);
   if (opts->fit) {
-    double *ke = (double *)ke_base;
-    pc::ke_series_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, ke);
-    pc_status ls = pc::launch_fit(ctx, ke, (int)nbn, S, dt, opts->first_index, out->gamma, out->omega, nullptr,
-                                  nullptr, st);
+    if (full_store) pc::ke_series_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, ke_fit);
+    pc_status ls = pc::launch_fit(ctx, ke_fit, (int)nbn, full_store ? So : So - first, dt,
+                                  full_store ? first : 0, out->gamma, out->omega, nullptr, nullptr, st);
     if (ls != PC_OK) return ls;
   }
   return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ERR_CUDA;
@@ -1481,8 +1712,31 @@ extern "C" pc_status pc_dipoles_run_moving(pc_ctx *ctx, const pc_dipoles *dp, co
   cudaStream_t st = (cudaStream_t)stream;
   pc_status bs = pc::begin_call(ctx, st);
   if (bs != PC_OK) return bs;
-  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, opts, out, nullptr, st, nullptr, motion);
+  pc::RunPlan pl;
+  pl.motion = motion;
+  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, opts, out, st, pl);
   if (rs != PC_OK) return rs;
+  return pc::end_call(ctx, st);
+}
+
+extern "C" pc_status pc_dipoles_state_size(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t *n_doubles,
+                                           void *stream) {
+  if (!ctx || !n_doubles) return PC_ERR_ARG;
+  pc::DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status bs = pc::begin_call(ctx, st);
+  if (bs != PC_OK) return bs;
+  pc_run_opts o;
+  memset(&o, 0, sizeof(o));
+  pc_run_out none;
+  memset(&none, 0, sizeof(none));
+  pc::RunPlan pl;
+  int64_t D = 0;
+  pl.reach_out = &D;
+  pl.tables_only = true;
+  pc_status rs = pc::run_impl(ctx, dp, dt, 0, &o, &none, st, pl);
+  if (rs != PC_OK) return rs;
+  *n_doubles = pc::state_doubles((int64_t)dp->B * dp->N, D);
   return pc::end_call(ctx, st);
 }
 
@@ -1493,7 +1747,7 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
   cudaStream_t st = (cudaStream_t)stream;
   pc_status bs = pc::begin_call(ctx, st);
   if (bs != PC_OK) return bs;
-  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, opts, out, nullptr, st);
+  pc_status rs = pc::run_impl(ctx, dp, dt, n_steps, opts, out, st);
   if (rs != PC_OK) return rs;
   return pc::end_call(ctx, st);
 }
@@ -1516,9 +1770,14 @@ extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt
 namespace pc {
 
 struct AdjArgs {
-  RunArgs f;           // forward arguments; f.d/dd/ddd/Ed/Ehalf hold the forward history
+  RunArgs f;           // forward arguments; f.d/dd/ddd (store slots), f.Ed/Ehalf (steps f.n_begin ..
+                       // f.n_steps) hold the forward history the reverse reads
   const double *wE;    // [B][N] dL / dE_i(T)
-  double *mu;          // [B][N][S][3] adjoints of the history samples (d, d', d'')
+  double *mu;          // [B][N][f.hs][3] adjoints of the history samples (d, d', d''), sample n at
+                       // slot n & f.wm; a slot is cleared once its sample's adjoint is consumed
+  // the fitted rates' cotangent on d' over absolute steps [seed_first, seed_first + seed_len), or null
+  const double *dseed;
+  int64_t seed_first, seed_len;
   double *lam;         // [B][N][2] adjoint of the state (d, d') at the current step
   double *carry;       // [B][N] adjoint of E_d at the current block start (from its first RK4 stage)
   double *Ebar;        // [B][N][2*kMaxBlock+1] adjoints of the block's stage fields
@@ -1536,14 +1795,14 @@ struct AdjArgs {
 
 __global__ void adj_init_kernel(const AdjArgs A) {
   const RunArgs &a = A.f;
-  const int64_t S = a.n_steps + 1;
   const double L = kC * a.dt;
   for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < (int64_t)a.B * a.N;
        bi += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(bi / a.N), i = (int)(bi % a.N);
     const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
     const double m = m1 * m2 / (m1 + m2);
-    const double dN = a.d[bi * S + a.n_steps], vN = a.dd[bi * S + a.n_steps];
+    const size_t sN = (size_t)bi * a.hs + (a.n_steps & a.wm);
+    const double dN = a.d[sN], vN = a.dd[sN];
     const double w = A.wE ? A.wE[bi] : 0.0;
     A.wts[2 * bi] = m2 / (m1 + m2) / q;
     A.wts[2 * bi + 1] = -m1 / (m1 + m2) / q;
@@ -1585,7 +1844,8 @@ __global__ void adj_rk4_kernel(const AdjArgs A, int64_t n0, int kb) {
   const RunArgs &a = A.f;
   const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= (int64_t)a.B * a.N) return;
-  const int64_t S = a.n_steps + 1;
+  const int64_t So = a.n_steps - a.n_begin + 1;
+  const size_t row = (size_t)bi * a.hs;
   const double m1 = a.m1[bi], m2 = a.m2[bi], q = a.q[bi], w0 = a.omega0[bi];
   const double m = m1 * m2 / (m1 + m2);
   const double g0 = q * q * w0 * w0 / (6.0 * kPi * kEps0 * kC * kC * kC * m);
@@ -1597,16 +1857,26 @@ __global__ void adj_rk4_kernel(const AdjArgs A, int64_t n0, int kb) {
   double *Eb = A.Ebar + bi * (2 * kMaxBlock + 1);
   for (int k = kb - 1; k >= 0; --k) {
     const int64_t n = n0 + k;
-    // history sample n+1 = (d, d', d'') with d'' = qm E(n+1) - g0 d' - w0^2 d
-    const double *mu1 = A.mu + (bi * S + n + 1) * 3;
-    const double yN0 = a.d[bi * S + n + 1], yN1 = a.dd[bi * S + n + 1];
-    l0 += mu1[0] - w0 * w0 * mu1[2];
-    l1 += mu1[1] - g0 * mu1[2];
-    double e4b = carry + qm * mu1[2];
-    double g0b = -yN1 * mu1[2], w2b = -yN0 * mu1[2];
+    // history sample n+1 = (d, d', d'') with d'' = qm E(n+1) - g0 d' - w0^2 d; its adjoint is
+    // complete (only later blocks read the sample) and is consumed here, its slot cleared for reuse
+    double *mu1 = A.mu + (row + ((n + 1) & a.wm)) * 3;
+    const double m0 = mu1[0], m2v = mu1[2];
+    double m1v = mu1[1];
+    if (A.dseed && n + 1 >= A.seed_first && n + 1 < A.seed_first + A.seed_len)
+      m1v += A.dseed[(size_t)bi * A.seed_len + (size_t)(n + 1 - A.seed_first)];
+    mu1[0] = 0.0;
+    mu1[1] = 0.0;
+    mu1[2] = 0.0;
+    const size_t sN = row + ((n + 1) & a.wm), s0 = row + (n & a.wm);
+    const double yN0 = a.d[sN], yN1 = a.dd[sN];
+    l0 += m0 - w0 * w0 * m2v;
+    l1 += m1v - g0 * m2v;
+    double e4b = carry + qm * m2v;
+    double g0b = -yN1 * m2v, w2b = -yN0 * m2v;
     // forward stages of step n
-    const double y0 = a.d[bi * S + n], y1 = a.dd[bi * S + n];
-    const double e1 = a.Ed[bi * S + n], e2 = a.Ehalf[bi * a.n_steps + n], e4 = a.Ed[bi * S + n + 1];
+    const double y0 = a.d[s0], y1 = a.dd[s0];
+    const size_t o = (size_t)bi * So + (size_t)(n - a.n_begin);
+    const double e1 = a.Ed[o], e2 = a.Ehalf[(size_t)bi * (So - 1) + (size_t)(n - a.n_begin)], e4 = a.Ed[o + 1];
     const double k1a = y1, k1b = -g0 * y1 - w0 * w0 * y0 + qm * e1;
     const double y0b = y0 + h * k1a, y1b = y1 + h * k1b;
     const double k2a = y1b, k2b = -g0 * y1b - w0 * w0 * y0b + qm * e2;
@@ -1673,16 +1943,16 @@ template <bool MOV>
 __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int64_t nv, double eb, double *win,
                             int64_t wlo, int W, double Rib[3], double Rjb[3]) {
   const RunArgs &a = A.f;
-  const int64_t S = a.n_steps + 1;
   const double cdt = kC * a.dt;
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
   const double *Ri = a.origin + 3 * bi;
   const double *pi = a.axis + 3 * bi;
   TrajF64 tr;
   tr.dipole = true;
-  tr.d = a.d + bj * S;
-  tr.dd = a.dd + bj * S;
-  tr.ddd = a.ddd + bj * S;
+  tr.d = a.d + bj * a.hs;
+  tr.dd = a.dd + bj * a.hs;
+  tr.ddd = a.ddd + bj * a.hs;
+  tr.wm = a.wm;
   double pj[3];
   for (int c = 0; c < 3; ++c) {
     tr.R[c] = a.origin[3 * bj + c];
@@ -1692,8 +1962,8 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
   const double q = a.q[bj];
   // moving origins: the receiver at its origin of the stage time (half-step index 2u), the source
   // charges on the interpolated origin history; their adjoints go to the origin samples
-  constexpr bool mov = MOV;  // moving origins (a.org_pos set): a separate instantiation
-  const int64_t H = 2 * S - 1;
+  constexpr bool mov = MOV;  // moving origins (a.org_pos set, every sample kept): a separate instantiation
+  const int64_t H = 2 * a.n_steps + 1;
   const int64_t hh = mov ? (int64_t)llrint(2.0 * u) : 0;
   int64_t kg;
   if (mov) {
@@ -1732,9 +2002,9 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
       tr.p(k + 1, p1);
       tr.va(k, vel, acc);
       tr.va(k + 1, v1, a1);
-      Dd = tr.d[k + 1] - tr.d[k];
-      Dv = tr.dd[k + 1] - tr.dd[k];
-      Da = tr.ddd[k + 1] - tr.ddd[k];
+      Dd = tr.dk(k + 1) - tr.dk(k);
+      Dv = tr.ddk(k + 1) - tr.ddk(k);
+      Da = tr.dddk(k + 1) - tr.dddk(k);
       for (int c = 0; c < 3; ++c) {
         p[c] += th * (p1[c] - p[c]);
         vel[c] += th * (v1[c] - vel[c]);
@@ -1830,7 +2100,6 @@ __global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t
   const RunArgs &a = A.f;
   const int j = blockIdx.x, b = blockIdx.y;
   const size_t bj = bidx(a, b, j);
-  const int64_t S = a.n_steps + 1;
   int64_t wlo = 0, whi = 0;
   if (ns > 0) {
     const double lo = (double)n0 + 0.5 - A.tau[2 * bj + 1] - (double)A.margin;
@@ -1904,7 +2173,8 @@ __global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t
     atomicAdd(&A.g_origin[3 * bj + threadIdx.x], t);
   }
   // the window into the source's history adjoints (this CTA owns source j during the launch)
-  for (int t = threadIdx.x; t < 3 * W; t += blockDim.x) A.mu[(bj * S + wlo) * 3 + t] += win[t];
+  for (int t = threadIdx.x; t < 3 * W; t += blockDim.x)
+    A.mu[(bj * a.hs + ((wlo + t / 3) & a.wm)) * 3 + t % 3] += win[t];
 }
 
 // Field-loss seed of the adjoint: L = sum over configurations b, frames f and points p of
@@ -1943,9 +2213,9 @@ __device__ int field_rev_charge(const AdjArgs &A, const TrajF64 &tr, double qc, 
     tr.p(k + 1, p1);
     tr.va(k, vel, acc);
     tr.va(k + 1, v1, a1);
-    Dd = tr.d[k + 1] - tr.d[k];
-    Dv = tr.dd[k + 1] - tr.dd[k];
-    Da = tr.ddd[k + 1] - tr.ddd[k];
+    Dd = tr.dk(k + 1) - tr.dk(k);
+    Dv = tr.ddk(k + 1) - tr.ddk(k);
+    Da = tr.dddk(k + 1) - tr.dddk(k);
     for (int c = 0; c < 3; ++c) {
       p[c] += th * (p1[c] - p[c]);
       vel[c] += th * (v1[c] - vel[c]);
@@ -1994,9 +2264,10 @@ __global__ void __launch_bounds__(128) fields_adj_kernel(const AdjArgs A, const 
   const double u = t / a.dt;
   TrajF64 tr;
   tr.dipole = true;
-  tr.d = a.d + bj * S;
-  tr.dd = a.dd + bj * S;
-  tr.ddd = a.ddd + bj * S;
+  tr.d = a.d + bj * a.hs;  // (the field-loss seed runs on the full store: hs = S, wm = -1)
+  tr.dd = a.dd + bj * a.hs;
+  tr.ddd = a.ddd + bj * a.hs;
+  tr.wm = a.wm;
   for (int c = 0; c < 3; ++c) {
     tr.R[c] = a.origin[3 * bj + c];
     tr.ax[c] = a.axis[3 * bj + c];
@@ -2057,16 +2328,15 @@ __global__ void __launch_bounds__(128) fields_adj_kernel(const AdjArgs A, const 
     atomicAdd(&A.g_origin[3 * bj + threadIdx.x], tt);
   }
   for (int q2 = threadIdx.x; q2 < 3 * W; q2 += blockDim.x)
-    if (win[q2] != 0.0) atomicAdd(&A.mu[(bj * S + wlo) * 3 + q2], win[q2]);
+    if (win[q2] != 0.0) atomicAdd(&A.mu[(bj * a.hs + wlo) * 3 + q2], win[q2]);
 }
 
 __global__ void adj_final_kernel(const AdjArgs A) {
   const RunArgs &a = A.f;
-  const int64_t S = a.n_steps + 1;
   for (int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; bi < (int64_t)a.B * a.N;
        bi += (int64_t)gridDim.x * blockDim.x) {
     // y_0 = (d0, 0) and the history before and at t = 0 sits at d0
-    A.g_d0[bi] = A.lam[2 * bi] + A.mu[bi * S * 3];
+    A.g_d0[bi] = A.lam[2 * bi] + A.mu[((size_t)bi * a.hs + (0 & a.wm)) * 3];
     A.g_omega0[bi] = A.w0bar[bi];
   }
 }
@@ -2091,35 +2361,106 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   if (opts->precision != PC_F64 && (rates || opts->precision != PC_MIXED)) return PC_ERR_ARG;
   if (dp->B < 1 || dp->N < 1 || !(dt > 0.0)) return PC_ERR_ARG;
   if (rates && (opts->first_index < 0 || n_steps + 1 - opts->first_index < 8)) return PC_ERR_ARG;
+  if (opts->state_in || opts->state_out || opts->checkpoint_every < 0) return PC_ERR_ARG;
+  // checkpointing: the energy and rate losses of fixed origins (a field loss or moving origins read
+  // the whole history)
+  const int64_t Cask = opts->checkpoint_every;
+  if (Cask > 0 && (fseed || motion)) return PC_ERR_ARG;
   const int64_t S = n_steps + 1;
   const size_t nbn = (size_t)dp->B * dp->N;
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
-  const size_t hist = al(nbn * S * sizeof(double));
-  const size_t half = al(nbn * n_steps * sizeof(double));
-  const size_t mu_b = al(nbn * S * 3 * sizeof(double));
-  const size_t small = al(nbn * (2 + 1 + (2 * kMaxBlock + 1) + 1 + 2 + 2 + 1) * sizeof(double));
-  const size_t fit_b = rates ? hist + al(4 * nbn * sizeof(double)) : 0;
-  if (ctx->adj_scratch.reserve(4 * hist + half + mu_b + small + fit_b) != cudaSuccess) return PC_ERR_CUDA;
-  char *p = (char *)ctx->adj_scratch.ptr;
-  double *d = (double *)p, *dd = (double *)(p + hist), *ddd = (double *)(p + 2 * hist), *Ed = (double *)(p + 3 * hist);
-  double *Eh = (double *)(p + 4 * hist);
-  double *mu = (double *)(p + 4 * hist + half);
-  double *sm = (double *)(p + 4 * hist + half + mu_b);
-  double *ke = rates ? (double *)(p + 4 * hist + half + mu_b + small) : nullptr;
-  double *fpar = rates ? ke + hist / sizeof(double) : nullptr;  // gamma, omega, amp, phase [nbn] each
-  // forward run with the full history and the half-step fields
   pc_run_opts fo = *opts;
   fo.fit = 0;
-  pc_run_out fw;
-  memset(&fw, 0, sizeof(fw));
-  fw.d = d;
-  fw.d_dot = dd;
-  fw.d_ddot = ddd;
-  fw.Ed = Ed;
+  fo.checkpoint_every = 0;
+  const int64_t first = rates ? opts->first_index : 0;
+  const int64_t flen = S - first;  // the fit window's samples
+  // ---- geometry: causal block length K and state depth D (tables only) ----
   int K = 1;
+  int64_t D = 1;
+  {
+    pc_run_out none;
+    memset(&none, 0, sizeof(none));
+    RunPlan pl;
+    pl.k_out = &K;
+    pl.reach_out = &D;
+    pl.tables_only = true;
+    pc_status rs = run_impl(ctx, dp, dt, 0, &fo, &none, st, pl);
+    if (rs != PC_OK) return rs;
+  }
+  // segment length: a multiple of K, so that the recomputed segments' causal blocks are the ones of
+  // the uninterrupted run (bit-identical histories)
+  const int64_t C = Cask > 0 ? ((Cask + K - 1) / K) * K : S;
+  const int64_t nseg = Cask > 0 ? (n_steps + C - 1) / C : 1;
+  const int64_t st_len = state_doubles((int64_t)nbn, D);
+  // ---- scratch: history store, E_d at the whole and half steps of a segment, history adjoints,
+  // small per-dipole arrays, the fit's inputs and its cotangent, the checkpoint states ----
+  const int64_t Sg = Cask > 0 ? std::min(C, n_steps) + 1 : S;   // samples of a segment's outputs
+  const int64_t Wg = Cask > 0 ? pow2_at_least(D + C + kMaxBlock + 2) : S;  // store rows
+  const size_t hist = al(nbn * (size_t)Wg * sizeof(double));
+  const size_t edb = al(nbn * (size_t)Sg * sizeof(double));
+  const size_t half = al(nbn * (size_t)(Sg - 1) * sizeof(double));
+  const size_t mu_b = al(nbn * (size_t)Wg * 3 * sizeof(double));
+  const size_t small = al(nbn * (2 + 1 + (2 * kMaxBlock + 1) + 1 + 2 + 2 + 1) * sizeof(double));
+  const size_t fit_b = rates ? 3 * al(nbn * (size_t)flen * sizeof(double)) + al(4 * nbn * sizeof(double)) : 0;
+  const size_t ck_b = Cask > 0 ? al((size_t)std::max<int64_t>(nseg - 1, 0) * st_len * sizeof(double)) : 0;
+  if (ctx->adj_scratch.reserve(3 * hist + edb + half + mu_b + small + fit_b + ck_b) != cudaSuccess) return PC_ERR_CUDA;
+  char *p = (char *)ctx->adj_scratch.ptr;
+  double *d = (double *)p, *dd = (double *)(p + hist), *ddd = (double *)(p + 2 * hist);
+  double *Ed = (double *)(p + 3 * hist);
+  double *Eh = (double *)(p + 3 * hist + edb);
+  double *mu = (double *)(p + 3 * hist + edb + half);
+  double *sm = (double *)(p + 3 * hist + edb + half + mu_b);
+  char *fp_ = p + 3 * hist + edb + half + mu_b + small;
+  double *ke = rates ? (double *)fp_ : nullptr;                             // [nbn][flen]
+  double *kdd = rates ? (double *)(fp_ + al(nbn * (size_t)flen * 8)) : nullptr;  // d' over the window
+  double *dseed = rates ? (double *)(fp_ + 2 * al(nbn * (size_t)flen * 8)) : nullptr;
+  double *fpar = rates ? (double *)(fp_ + 3 * al(nbn * (size_t)flen * 8)) : nullptr;  // gamma, omega, amp, phase
+  double *ck = Cask > 0 ? (double *)(fp_ + fit_b) : nullptr;  // state at step c C: ck + (c - 1) st_len
   const int2 *delay = nullptr;
-  pc_status rs = run_impl(ctx, dp, dt, n_steps, &fo, &fw, Eh, st, &K, motion, &delay);
-  if (rs != PC_OK) return rs;
+  const double *tab = nullptr;
+  // ---- forward ----
+  if (Cask == 0) {
+    // the whole history and the half-step fields, in the adjoint's scratch
+    pc_run_out fw;
+    memset(&fw, 0, sizeof(fw));
+    fw.d = d;
+    fw.d_dot = dd;
+    fw.d_ddot = ddd;
+    fw.Ed = Ed;
+    RunPlan pl;
+    pl.Ehalf = Eh;
+    pl.motion = motion;
+    pl.delay_out = &delay;
+    pl.rk4tab_out = &tab;
+    if (rates) {
+      pl.ke = ke;
+      pl.kdd = kdd;
+      pl.ke_first = first;
+      pl.ke_len = flen;
+    }
+    pc_status rs = run_impl(ctx, dp, dt, n_steps, &fo, &fw, st, pl);
+    if (rs != PC_OK) return rs;
+  } else {
+    // segment by segment in a ring of the context, keeping the state at every segment boundary
+    // (and the fit window's kinetic energies and d')
+    for (int64_t c = 0; c < nseg; ++c) {
+      const int64_t n0 = c * C, len = std::min(C, n_steps - n0);
+      pc_run_opts so = fo;
+      so.state_in = c > 0 ? ck + (c - 1) * st_len : nullptr;
+      so.state_out = c + 1 < nseg ? ck + c * st_len : nullptr;
+      pc_run_out none;
+      memset(&none, 0, sizeof(none));
+      RunPlan pl;
+      if (rates) {
+        pl.ke = ke;
+        pl.kdd = kdd;
+        pl.ke_first = first;
+        pl.ke_len = flen;
+      }
+      pc_status rs = run_impl(ctx, dp, dt, len, &so, &none, st, pl);
+      if (rs != PC_OK) return rs;
+    }
+  }
   const size_t hs = (size_t)(2 * n_steps + 1) * 3 * sizeof(double);
   if (motion && gm)
     for (double *gp : {gm->pos, gm->vel, gm->acc})
@@ -2137,12 +2478,16 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   a.omega0 = dp->omega0;
   a.d0 = dp->d0;
   a.dt = dt;
+  a.n_begin = 0;
   a.n_steps = n_steps;
   a.d = d;
   a.dd = dd;
   a.ddd = ddd;
+  a.hs = Wg;
+  a.wm = Cask > 0 ? Wg - 1 : -1;
   a.Ed = Ed;
   a.Ehalf = Eh;
+  a.rk4tab = const_cast<double *>(tab);
   a.nsplit = 1;
   a.status = ctx->d_status;
   A.wE = wE;
@@ -2168,38 +2513,72 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
   A.g_origin = g->origin;
   A.g_omega0 = g->omega0;
   A.g_d0 = g->d0;
-  if (cudaMemsetAsync(mu, 0, nbn * S * 3 * sizeof(double), st) != cudaSuccess) return PC_ERR_CUDA;
+  if (cudaMemsetAsync(mu, 0, nbn * (size_t)Wg * 3 * sizeof(double), st) != cudaSuccess) return PC_ERR_CUDA;
   if (rates) {
-    // the fit of the forward run's kinetic energies, then its adjoint into the d' history adjoints
-    ke_series_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a, ke);
-    double *fg = fpar, *fw_ = fpar + nbn, *fa_ = fpar + 2 * nbn, *fp = fpar + 3 * nbn;
-    pc_status ls = launch_fit(ctx, ke, (int)nbn, S, dt, opts->first_index, fg, fw_, fa_, fp, st);
+    // the fit of the forward run's kinetic energies, then its adjoint: a cotangent on every d'
+    // sample of the window, added to that sample's adjoint when the reverse sweep consumes it
+    if (cudaMemsetAsync(dseed, 0, nbn * (size_t)flen * sizeof(double), st) != cudaSuccess) return PC_ERR_CUDA;
+    double *fg = fpar, *fw_ = fpar + nbn, *fa_ = fpar + 2 * nbn, *fph = fpar + 3 * nbn;
+    pc_status ls = launch_fit(ctx, ke, (int)nbn, flen, dt, 0, fg, fw_, fa_, fph, st);
     if (ls != PC_OK) return ls;
     FitAdjArgs fj;
     fj.ke = ke;
     fj.K = (int)nbn;
-    fj.S = S;
-    fj.first = opts->first_index;
+    fj.S = flen;
+    fj.first = 0;
     fj.dt = dt;
     fj.gamma = fg;
     fj.omega = fw_;
     fj.amp = fa_;
-    fj.phase = fp;
+    fj.phase = fph;
     fj.dL_dgamma = dL_dgamma;
     fj.dL_domega = dL_domega;
-    fj.dd = dd;
+    fj.dd = kdd;
     fj.m1 = dp->m1;
     fj.m2 = dp->m2;
     fj.q = dp->q;
-    fj.mu = mu;
+    fj.seed = dseed;
     fj.status = ctx->d_status;
     ke_fit_adjoint_kernel<<<(unsigned)nbn, kFitThreads, 0, st>>>(fj);
+    A.dseed = dseed;
+    A.seed_first = first;
+    A.seed_len = flen;
     if (gamma_out && cudaMemcpyAsync(gamma_out, fg, nbn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return PC_ERR_CUDA;
     if (omega_out && cudaMemcpyAsync(omega_out, fw_, nbn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return PC_ERR_CUDA;
   }
   const unsigned rgrid = (unsigned)((nbn + 127) / 128);
+  // recompute segment c into the segment store (its E_d at the whole and half steps with it), and
+  // point the reverse's arguments at it
+  auto recompute = [&](int64_t c) -> pc_status {
+    const int64_t n0 = c * C, len = std::min(C, n_steps - n0);
+    pc_run_opts so = fo;
+    so.state_in = c > 0 ? ck + (c - 1) * st_len : nullptr;
+    pc_run_out ro;
+    memset(&ro, 0, sizeof(ro));
+    ro.Ed = Ed;
+    RunPlan pl;
+    pl.Ehalf = Eh;
+    pl.sd = d;
+    pl.sdd = dd;
+    pl.sddd = ddd;
+    pl.shs = Wg;
+    pl.swm = Wg - 1;
+    pl.delay_out = &delay;
+    pl.rk4tab_out = &tab;
+    pc_status rs = run_impl(ctx, dp, dt, len, &so, &ro, st, pl);
+    if (rs != PC_OK) return rs;
+    a.n_begin = n0;
+    a.n_steps = n0 + len;
+    a.rk4tab = const_cast<double *>(tab);
+    A.delay = delay;
+    return PC_OK;
+  };
+  if (Cask > 0) {
+    pc_status rs = recompute(nseg - 1);
+    if (rs != PC_OK) return rs;
+  }
   adj_init_kernel<<<rgrid, 128, 0, st>>>(A);
   // margin for charge offsets: three times the largest initial |r_dip|, in samples, plus one
   std::vector<double> hq(nbn), hd0(nbn), htau(2 * nbn), hdisp(nbn);
@@ -2235,13 +2614,21 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
     fields_adj_kernel<<<dim3((unsigned)dp->N, (unsigned)fseed->T, (unsigned)dp->B), 128, fsm, st>>>(A, *fseed, fw);
   }
   const dim3 fgrid((unsigned)dp->N, (unsigned)dp->B);
-  const int64_t nblocks = (n_steps + K - 1) / K;
-  for (int64_t bk = nblocks - 1; bk >= 0; --bk) {
-    const int64_t n0 = bk * K;
-    const int kb = (int)std::min((int64_t)K, n_steps - n0);
-    adj_rk4_kernel<<<rgrid, 128, 0, st>>>(A, n0, kb);
-    if (mov) adj_field_kernel<true><<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
-    else adj_field_kernel<false><<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
+  // reverse sweep over the causal blocks, last first (segment by segment when checkpointing)
+  for (int64_t c = nseg - 1; c >= 0; --c) {
+    if (Cask > 0 && c < nseg - 1) {
+      pc_status rs = recompute(c);
+      if (rs != PC_OK) return rs;
+    }
+    const int64_t s0 = c * C, s1 = std::min(n_steps, s0 + C);
+    const int64_t nblocks = (s1 - s0 + K - 1) / K;
+    for (int64_t bk = nblocks - 1; bk >= 0; --bk) {
+      const int64_t n0 = s0 + bk * K;
+      const int kb = (int)std::min((int64_t)K, s1 - n0);
+      adj_rk4_kernel<<<rgrid, 128, 0, st>>>(A, n0, kb);
+      if (mov) adj_field_kernel<true><<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
+      else adj_field_kernel<false><<<fgrid, 128, smem, st>>>(A, n0, 2 * kb, wmax);
+    }
   }
   // the driving field at t = 0 (static configuration) and the final gradients
   if (mov) adj_field_kernel<true><<<fgrid, 128, smem, st>>>(A, 0, 0, wmax);

@@ -48,7 +48,8 @@ struct pc_ctx {
   int *h_status = nullptr;   // pinned host copy
   pc::Buf hist_f32;          // float32 mirrors of source histories (mixed path)
   pc::Buf charge_ref;        // per-charge float64 reference positions
-  pc::Buf run_scratch;       // LO-run scratch (stage fields, fit work)
+  pc::Buf run_scratch;       // LO-run scratch (tables, stage fields)
+  pc::Buf run_store;         // LO-run history ring, its float32 mirror, per-step fit inputs
   pc::Buf adj_scratch;       // adjoint: forward history, history adjoints
   cudaGraph_t loop_graph = nullptr;     // causal-block loop of the last grid-path run
   cudaGraphExec_t loop_exec = nullptr;

@@ -79,6 +79,25 @@ struct HistF32T {
 };
 using HistF32 = HistF32T<true>;
 using HistF32RW = HistF32T<false>;
+// The oscillator run's float32 mirror: sample j at slot (j & mask) of the dipole's row (mask = -1:
+// every sample at its index; W - 1: a ring of W slots holding the samples a block can reach).
+// Coherent loads: the run appends to the rows it reads.
+struct HistF32Ring {
+  const float4 *H;
+  int mask;
+  __device__ __forceinline__ void get(int j, float &x, float &v, float &a) const {
+    float4 h = H[(j >= 0 ? j : 0) & mask];
+    x = h.x;
+    v = j >= 0 ? h.y : 0.f;
+    a = j >= 0 ? h.z : 0.f;
+  }
+  __device__ __forceinline__ void get_in(int j, float &x, float &v, float &a) const {
+    float4 h = H[j & mask];
+    x = h.x;
+    v = h.y;
+    a = h.z;
+  }
+};
 struct HistF64 {
   const double *d, *dd, *ddd;
   double sx, sv, sa;  // 1/(qL), 1/(qc), dt/(qc)

@@ -14,9 +14,13 @@ __device__ __forceinline__ double dot3(const double *a, const double *b) {
 struct TrajF64 {
   const double *pos;  // generic: [S][3]
   const double *vel, *acc;
-  const double *d, *dd, *ddd;  // dipole: [S]
+  const double *d, *dd, *ddd;  // dipole: sample k at row slot (k & wm)
+  int64_t wm = -1;             // -1: the row holds every sample at its index; W - 1: a ring of W slots
   double R[3], ax[3], w;       // dipole: origin, axis, signed weight / q
   bool dipole;
+  __device__ __forceinline__ double dk(int64_t k) const { return d[k & wm]; }
+  __device__ __forceinline__ double ddk(int64_t k) const { return dd[k & wm]; }
+  __device__ __forceinline__ double dddk(int64_t k) const { return ddd[k & wm]; }
   // moving dipole origin (or null): position, velocity, acceleration at the half steps, [2 S - 1][3];
   // the history holds the whole steps (half-step index 2k)
   const double *Rp = nullptr, *Rv = nullptr, *Ra = nullptr;
@@ -26,7 +30,7 @@ struct TrajF64 {
       o[1] = pos[3 * k + 1];
       o[2] = pos[3 * k + 2];
     } else {
-      double s = w * d[k];
+      double s = w * dk(k);
       const double *c = Rp ? Rp + 6 * k : R;
       o[0] = c[0] + s * ax[0];
       o[1] = c[1] + s * ax[1];
@@ -40,7 +44,7 @@ struct TrajF64 {
         a[i] = acc[3 * k + i];
       }
     } else {
-      double sv = w * dd[k], sa = w * ddd[k];
+      double sv = w * ddk(k), sa = w * dddk(k);
       for (int i = 0; i < 3; ++i) {
         v[i] = (Rv ? Rv[6 * k + i] : 0.0) + sv * ax[i];
         a[i] = (Ra ? Ra[6 * k + i] : 0.0) + sa * ax[i];
