@@ -671,6 +671,19 @@ def main():
         ds["ring_adjoint_f64"] = {"value": cfg4.N * cfg4.n_steps / (ms4 * 1e-3), "unit": "dipole-steps/s", "ms": ms4,
                                   "workload": "gradients of sum E(T) w.r.t. 768 origin coordinates, 256 omega0, "
                                               "256 d0 of the 256-oscillator ring, 20000 steps (forward + reverse)"}
+        # the same gradients with the run's state kept every 1000 steps and each segment recomputed
+        # in the reverse sweep (memory: the states plus one segment, not the whole history)
+        pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, 64, w4, checkpoint_every=1000)
+        torch.cuda.synchronize()
+        e0.record(s)
+        pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, cfg4.n_steps, w4, checkpoint_every=1000)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms4c = e0.elapsed_time(e1)
+        ds["ring_adjoint_f64_checkpointed"] = {
+            "value": cfg4.N * cfg4.n_steps / (ms4c * 1e-3), "unit": "dipole-steps/s", "ms": ms4c,
+            "workload": "the same gradients, the run's state kept every 1000 steps (1008: whole causal blocks), "
+                        "each segment recomputed in the reverse sweep"}
         pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, 64, w4, precision=pc.PC_MIXED)
         torch.cuda.synchronize()
         e0.record(s)
