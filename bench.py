@@ -656,9 +656,13 @@ def main():
         # precisions, and the float64 adjoint of sum E(T) (forward repeated inside, then reverse)
         cfg4 = W.cfg4()
         for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
+            # the grid path's launch shape tuned on this workload first (source slices per receiver)
+            sl = pc.pc_autotune_run(ctx, pc.lo_config_to_device(cfg4, dev), cfg4.dt, probe_steps=256, precision=prec)
             r = lo_time(cfg4, cfg4.n_steps, prec, False)
             r["workload"] = "ring: 256 oscillators on a 200 nm ring x 20000 RK4 steps"
+            r["source_slices"] = sl
             ds["ring_" + name] = r
+        pc.pc_set_run_tiling(ctx, 0)
         lod4 = pc.lo_config_to_device(cfg4, dev)
         w4 = torch.ones((1, cfg4.N), dtype=torch.float64, device=dev)
         pc.pc_dipoles_adjoint(ctx, lod4, cfg4.dt, 64, w4)
@@ -695,8 +699,10 @@ def main():
                                             "ms": ms4m, "workload": "the same gradients with the forward run's "
                                                                     "driving field mixed, the reverse float64"}
         cfg5 = W.cfg5()
+        sl = pc.pc_autotune_run(ctx, pc.lo_config_to_device(cfg5, dev), cfg5.dt, probe_steps=64, precision=pc.PC_MIXED)
         r = lo_time(cfg5, cfg5.n_steps, pc.PC_MIXED, False)
         r["workload"] = "cloud: 4096 oscillators in a 600 nm cube x 20000 RK4 steps (1250 causal blocks of 16 steps)"
+        r["source_slices"] = sl
         ds["cloud_mixed"] = r
         # the all-float64 GPU path on the same cloud over its first 1000 steps (the whole run takes
         # ~7 minutes in float64), and the mixed path over the same steps for a like-for-like factor
@@ -706,6 +712,7 @@ def main():
             r["workload"] = "cloud: 4096 oscillators in a 600 nm cube x the first 1000 RK4 steps"
             ds["cloud_1000_" + name] = r
         ds["cloud_1000_mixed_over_f64"] = ds["cloud_1000_f64"]["ms"] / ds["cloud_1000_mixed"]["ms"]
+        pc.pc_set_run_tiling(ctx, 0)
 
         def timed(fn):
             fn()

@@ -280,6 +280,24 @@ pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n
                          const pc_run_out *out, void *stream);
 
 /*
+ * pc_autotune_run -- picks the launch shape of the oscillator run for this workload and keeps it in
+ * the context for later pc_dipoles_run / adjoint calls: configurations of more than 64 dipoles run as
+ * grid-wide launches in which each receiver's sources are split into slices summed in a fixed order;
+ * each candidate slice count (powers of two up to min(64, N / 8) and the occupancy heuristic's choice)
+ * runs the caller's configuration (dp, dt, opts; no fit, no state) for probe_steps steps once to warm
+ * up and once timed, and the fastest is kept.  Writes the chosen count to *chosen (or NULL); smaller
+ * configurations run as one CTA each and have nothing to tune (*chosen = 1).  Results of different
+ * slice counts agree to the rounding of the driving-field sum (its terms are added in another order).
+ * Errors: those of pc_dipoles_run; PC_ERR_ARG for probe_steps < 1 or opts with a fit or a state.
+ */
+pc_status pc_autotune_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t probe_steps, const pc_run_opts *opts,
+                          int32_t *chosen, void *stream);
+
+/* pc_set_run_tiling -- sets the source slices per receiver of the grid path directly (0: the
+ * occupancy heuristic, 1..64: that many, capped at N / 8).  Errors: PC_ERR_ARG outside 0..64. */
+pc_status pc_set_run_tiling(pc_ctx *ctx, int32_t source_slices);
+
+/*
  * pc_dipoles_state_size -- the length (float64 values) of a run state of these dipoles at this dt
  * (pc_run_opts.state_in / state_out): a header (step, depth D, B N), E_d of every dipole at the state's
  * step and d, d', d'' of its last D + 1 samples, D the deepest sample a causal block can reach behind

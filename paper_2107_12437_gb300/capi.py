@@ -95,6 +95,9 @@ SIGNATURES = {
     "pc_dipoles_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                       ctypes.POINTER(PcRunOut), _vp]),
     "pc_dipoles_state_size": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, ctypes.POINTER(_i64), _vp]),
+    "pc_autotune_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
+                                       ctypes.POINTER(_i32), _vp]),
+    "pc_set_run_tiling": (ctypes.c_int, [_vp, _i32]),
     "pc_fields_to_host": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
                                          ctypes.POINTER(_f64), _i32, _i32, _i32, _f64, ctypes.POINTER(PcFieldOut),
                                          _vp]),
@@ -394,6 +397,22 @@ def lo_config_to_device(cfg, device="cuda"):
 def _dipoles(dp):
     return PcDipoles(B=int(dp.origin.shape[0]), N=int(dp.origin.shape[1]), origin=_ptr(dp.origin), axis=_ptr(dp.axis),
                      q=_ptr(dp.q), m1=_ptr(dp.m1), m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
+
+
+def pc_autotune_run(ctx, dp, dt, probe_steps=64, precision=PC_F64, near_f64=0.0, v_max=0.0, stream=None):
+    """pc_autotune_run: times the grid path's source-slice counts on this configuration and keeps
+    the fastest in the context; returns it (1 for configurations that run as one CTA each)."""
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=int(precision),
+                     near_f64=float(near_f64))
+    c = _i32(0)
+    _check(ctx.lib.pc_autotune_run(ctx.handle, ctypes.byref(_dipoles(dp)), float(dt), int(probe_steps),
+                                   ctypes.byref(opts), ctypes.byref(c), _stream(stream)), "pc_autotune_run")
+    return int(c.value)
+
+
+def pc_set_run_tiling(ctx, source_slices):
+    """pc_set_run_tiling: source slices per receiver of the grid path (0: the heuristic)."""
+    _check(ctx.lib.pc_set_run_tiling(ctx.handle, int(source_slices)), "pc_set_run_tiling")
 
 
 def pc_dipoles_state_size(ctx, dp, dt, stream=None):

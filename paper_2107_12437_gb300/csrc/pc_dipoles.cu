@@ -1663,6 +1663,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     const int64_t target = (int64_t)ctx->num_sms * 64;
     int nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, (target + (int64_t)nbn - 1) / (int64_t)nbn),
                                         std::max(1, dp->N / 8));
+    if (ctx->run_slices > 0) nsplit = std::min(ctx->run_slices, std::max(1, dp->N / 8));  // set or tuned
     nsplit = std::min(nsplit, kMaxSplit);
     a.nsplit = nsplit;
     a.Epart = nsplit > 1 ? (double *)(scr + part_off) : nullptr;
@@ -1738,6 +1739,63 @@ extern "C" pc_status pc_dipoles_state_size(pc_ctx *ctx, const pc_dipoles *dp, do
   if (rs != PC_OK) return rs;
   *n_doubles = pc::state_doubles((int64_t)dp->B * dp->N, D);
   return pc::end_call(ctx, st);
+}
+
+extern "C" pc_status pc_set_run_tiling(pc_ctx *ctx, int32_t source_slices) {
+  if (!ctx || source_slices < 0 || source_slices > pc::kMaxSplit) return PC_ERR_ARG;
+  ctx->run_slices = source_slices;
+  return PC_OK;
+}
+
+// Autotuning of the grid path's launch shape: each candidate number of source slices per receiver
+// (powers of two up to 64 and N / 8, and the occupancy heuristic's own choice) runs the caller's
+// configuration for probe_steps steps once to warm up and once timed; the fastest is kept in the
+// context.  Configurations that run as one CTA each have nothing to tune.
+extern "C" pc_status pc_autotune_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t probe_steps,
+                                     const pc_run_opts *opts, int32_t *chosen, void *stream) {
+  if (!ctx || !dp || !opts || probe_steps < 1 || opts->fit || opts->state_in || opts->state_out) return PC_ERR_ARG;
+  pc::DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dp->N <= pc::kSmallN) {
+    ctx->run_slices = 0;
+    if (chosen) *chosen = 1;
+    return PC_OK;
+  }
+  const int hi = std::min(pc::kMaxSplit, std::max(1, dp->N / 8));
+  const int64_t nbn = (int64_t)dp->B * dp->N;
+  const int heur = (int)std::min<int64_t>(
+      std::min<int64_t>(std::max<int64_t>(1, ((int64_t)ctx->num_sms * 64 + nbn - 1) / nbn), hi), pc::kMaxSplit);
+  std::vector<int> cand;
+  for (int c = 1; c <= hi; c *= 2) cand.push_back(c);
+  if (std::find(cand.begin(), cand.end(), heur) == cand.end()) cand.push_back(heur);
+  if (std::find(cand.begin(), cand.end(), hi) == cand.end()) cand.push_back(hi);
+  pc_run_out none;
+  memset(&none, 0, sizeof(none));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PC_ERR_CUDA;
+  float best = 1e30f;
+  int best_c = heur;
+  pc_status rs = PC_OK;
+  for (int c : cand) {
+    ctx->run_slices = c;
+    rs = pc_dipoles_run(ctx, dp, dt, probe_steps, opts, &none, stream);
+    if (rs != PC_OK) break;
+    cudaEventRecord(e0, st);
+    rs = pc_dipoles_run(ctx, dp, dt, probe_steps, opts, &none, stream);
+    cudaEventRecord(e1, st);
+    if (rs != PC_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->run_slices = best_c;
+  if (chosen) *chosen = best_c;
+  return rs;
 }
 
 extern "C" pc_status pc_dipoles_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t n_steps,

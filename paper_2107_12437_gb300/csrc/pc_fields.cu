@@ -106,6 +106,11 @@ struct Launch {
   float eu_L[3], ev_L[3];            // plane steps in units of c dt (dipole history)
   const float4 *srcf;
   float unit[4];                     // SI units of the float32 sums of E, B, phi, A
+  // loop constants of the dipole sum, read from the parameter bank rather than held in registers:
+  // r_excl in units of c dt, that plus 1.5 (the fast path's distance bound), and the number of
+  // interior segments S - 3 (fast segments 1 <= j <= S - 3)
+  float rex, rex_fast;
+  unsigned jlim;
   // point charges: each frame's time in their samples, 1/(c dt) of their history, and the scales
   // of their float32 terms to the output unit (E, phi)
   double ufc[kMaxT];
@@ -117,6 +122,11 @@ struct Launch {
 // A in k_e e / (L c), L = c dt of the dipoles (of the point charges when there are no dipoles)
 __host__ inline void set_units(Launch &L) {
   const double Lref = (L.src.N > 0) ? kC * L.src.dtd : kC * L.src.dt;
+  if (L.src.N > 0) {
+    L.rex = (float)(L.r_excl * L.iLd);
+    L.rex_fast = L.rex + 1.5f;
+    L.jlim = L.src.Sd > 3 ? (unsigned)(L.src.Sd - 3) : 0u;
+  }
   const double kE2 = kKe * kE / (Lref * Lref), kP = kKe * kE / Lref;
   L.unit[0] = (float)kE2;
   L.unit[1] = (float)(kE2 / kC);
@@ -475,6 +485,16 @@ __device__ __forceinline__ float kahan_get(const KahanArr &k, int tid, int i) {
   return hi[i] ? sv.y - cv.y : sv.x - cv.x;
 }
 
+// The point of thread tid in tile blockIdx.x (list: 256 consecutive points; plane: a block of rows x
+// columns of the grid), or P for a thread past the edge of the grid.
+__device__ __forceinline__ int64_t tile_point(const Launch &L, int64_t tiles_v, int tid) {
+  if (L.pts.list) return (int64_t)blockIdx.x * kMixThreads + tid;
+  const int64_t tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
+  const int sh = L.tile_shift, cols = 1 << sh, rows = kMixThreads >> sh;
+  const int64_t iu = tu * rows + (tid >> sh), iv = tv * cols + (tid & (cols - 1));
+  return (iu < L.pts.nu && iv < L.pts.nv) ? iu * L.pts.nv + iv : L.pts.P;
+}
+
 template <int KIND, bool LIST, int CH>
 __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Launch L, int64_t tiles_v) {
   __shared__ double s_anchor[3];
@@ -490,17 +510,9 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   const int tid = threadIdx.x;
   const int f = blockIdx.y;
   const Sources &s = L.src;
-  // ---- tile -> points ----
-  int64_t p;
-  if (L.pts.list) {
-    p = (int64_t)blockIdx.x * kMixThreads + tid;
-  } else {
-    int64_t tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
-    const int sh = L.tile_shift, cols = 1 << sh, rows = kMixThreads >> sh;
-    int64_t iu = tu * rows + (tid >> sh), iv = tv * cols + (tid & (cols - 1));
-    p = (iu < L.pts.nu && iv < L.pts.nv) ? iu * L.pts.nv + iv : L.pts.P;
-  }
-  const bool active = p < L.pts.P;
+  // ---- tile -> points (the index itself is formed again where it is needed, so that it does not
+  // occupy registers across the source loop) ----
+  const bool active = tile_point(L, tiles_v, tid) < L.pts.P;
   if (tid == 0) {
     double a[3];
     if (L.pts.list) {
@@ -523,7 +535,6 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
     }
   }
   __syncthreads();
-  const int64_t pp = active ? p : 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     s_kahan[0][i][tid] = make_float2(0.f, 0.f);
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       drz = du * L.eu_L[2] + dv * L.ev_L[2];
     } else {
       double r[3];
-      point_at(L.pts, pp, r);
+      point_at(L.pts, active ? tile_point(L, tiles_v, tid) : 0, r);
       const double drxd = (r[0] - s_anchor[0]) * iLd, dryd = (r[1] - s_anchor[1]) * iLd,
                    drzd = (r[2] - s_anchor[2]) * iLd;
       drx = (float)drxd;
@@ -559,10 +570,6 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
       drlz = (float)(drzd - (double)drz);
     }
     const float dr2 = drx * drx + dry * dry + drz * drz;
-    const float rex = (float)(L.r_excl * iLd);
-    const float rex_fast = rex + 1.5f;
-    const int Sd32 = (int)s.Sd;
-    const unsigned jlim = Sd32 > 3 ? (unsigned)(Sd32 - 3) : 0u;  // fast segments 1 <= j <= S-3
     for (int base = 0; base < s.N; base += CH) {
       const int nch = min(CH, s.N - base);
       __syncthreads();
@@ -638,7 +645,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
           float fl;
           const int kc = Num<float>::floor_int(xc, fl);
           const int j = kb + kc;
-          if ((unsigned)(j - 1) < jlim && rn > rex_fast) {
+          if ((unsigned)(j - 1) < L.jlim && rn > L.rex_fast) {
             const HistF32 H{s_hist[jj]};
             float x0, v0, a0, x1, v1, a1;
             H.get_in(j, x0, v0, a0);
@@ -693,9 +700,10 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
           xc = (x.hi - flf) + x.lo;
         }
         double rp64[3];
-        point_at(L.pts, pp, rp64);
-        const int e = slow_dipole<KIND>(s, base + jj, s_hist[jj], Sd32, kb, xc, rx, ry, rz, rn, ax, mx.x, mx.y, rex,
-                                        rp64, (L.times[f] - s.t0d) / s.dtd, kC * s.dtd, L.r_excl, sp, &smask);
+        point_at(L.pts, tile_point(L, tiles_v, tid), rp64);
+        const int e = slow_dipole<KIND>(s, base + jj, s_hist[jj], (int)s.Sd, kb, xc, rx, ry, rz, rn, ax, mx.x, mx.y,
+                                        L.rex, rp64, (L.times[f] - s.t0d) / s.dtd, kC * s.dtd, L.r_excl, sp,
+                                        &smask);
         if (e) err = e;
         mask |= smask;
         float2 SP[5];
@@ -707,7 +715,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   // ---------------- point charges ----------------
   if (s.M > 0) {
     double r[3];
-    point_at(L.pts, pp, r);
+    point_at(L.pts, active ? tile_point(L, tiles_v, tid) : 0, r);
     const double iLc = L.iLc;  // no float64 division on the way (the float64 unit is narrow here)
     const float drx = (float)((r[0] - s_anchor[0]) * iLc), dry = (float)((r[1] - s_anchor[1]) * iLc),
                 drz = (float)((r[2] - s_anchor[2]) * iLc);
@@ -853,7 +861,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   }
   // units: E in k_e e / L^2, B in k_e e / (L^2 c), phi in k_e e / L, A in k_e e / (L c)
   const float fE = L.unit[0], fB = L.unit[1], fP = L.unit[2], fA = L.unit[3];
-  const int64_t o = (L.frame0 + f) * L.pts.P + p;
+  const int64_t o = (L.frame0 + f) * L.pts.P + tile_point(L, tiles_v, tid);
   if (L.out.E) {
     float *e = (float *)L.out.E + 3 * o;
     e[0] = fE * kahan_get(s_kahan, tid, 0);

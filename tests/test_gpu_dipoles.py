@@ -328,3 +328,33 @@ def test_cloud_mixed_against_f64():
     assert float(np.max(np.abs(wm - wf) / wf)) < 1e-9
     assert float(np.max(np.abs(gm - gf) / g0)) < 2e-3
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
+def test_run_tuner_and_slice_counts_keep_parity(ctx, prec):
+    # the grid path's launch shape (source slices per receiver) chosen by the tuner, and every shape
+    # set by hand, against the oracle on 96 oscillators; the shapes differ only in the order the
+    # driving-field sum adds its terms
+    cfg = W.cfg5(N=96, n_steps=240, side=150e-9, min_spacing=5e-9, seed=7)
+    ref = oracle.dipoles_run(cfg)
+    assert ref["status"] == oracle.OK
+    lod = pc.lo_config_to_device(cfg)
+    try:
+        chosen = pc.pc_autotune_run(ctx, lod, cfg.dt, probe_steps=32, precision=prec)
+        assert chosen in (1, 2, 4, 8, 12)
+        outs = {}
+        for sl in (0, 1, 2, 4, 12):
+            pc.pc_set_run_tiling(ctx, sl)
+            outs[sl] = pc.pc_dipoles_run(ctx, lod, cfg.dt, cfg.n_steps, precision=prec, want_Ed=True)
+            for k in ("d", "d_dot", "Ed"):
+                assert hist_err(outs[sl][k][0], ref[k]) < HIST_TOL[prec], (sl, k)
+        for sl in (1, 2, 4, 12):
+            err = float(((outs[sl]["d"] - outs[0]["d"]).abs().amax(-1) / outs[0]["d"].abs().amax(-1)).max())
+            assert err < {pc.PC_F64: 1e-12, pc.PC_MIXED: 1e-6}[prec], (sl, err)
+        # one CTA per configuration: nothing to tune
+        small = W.cfg5(N=40, n_steps=40, side=120e-9, min_spacing=5e-9, seed=3)
+        assert pc.pc_autotune_run(ctx, pc.lo_config_to_device(small), small.dt, precision=prec) == 1
+        with pytest.raises(pc.PcError):
+            pc.pc_set_run_tiling(ctx, 65)
+    finally:
+        pc.pc_set_run_tiling(ctx, 0)
