@@ -636,6 +636,18 @@ def main():
         r["workload"] = ("the same, mixed with the sources within 10 nm summed in float64 (decay rates of the "
                          "closest pairs resolved)")
         ds["pairs_mixed_near_f64"] = r
+        # latency floor of the batch: its slowest configuration (1 nm, causal blocks of 3 steps,
+        # 13 334 blocks) run alone; the batch's time per block against that chain's
+        one = W.lo_batch(cfg3.origin[:1], cfg3.axis[:1], cfg3.omega0[:1], 1e-11, cfg3.dt, cfg3.n_steps,
+                         cfg3.first_index)
+        nblk = -(-cfg3.n_steps // 3)
+        for name, prec in (("mixed", pc.PC_MIXED), ("f64", pc.PC_F64)):
+            r1 = lo_time(one, one.n_steps, prec, False)
+            ds["pairs_latency_" + name] = {
+                "closest_alone_ms": r1["ms"], "us_per_block_alone": 1e3 * r1["ms"] / nblk,
+                "us_per_block_batch": 1e3 * ds["pairs_" + name]["ms"] / nblk,
+                "batch_over_floor": ds["pairs_" + name]["ms"] / r1["ms"],
+                "workload": "the 1 nm configuration alone: 13334 causal blocks of 3 steps, one CTA"}
         if rank == 0:
             line["pair_theory"] = pair_theory(pc, ctx, dev)
         # the Eq. KE fit of all 512 kinetic-energy series of that run (30 001 samples each)

@@ -210,14 +210,16 @@ def test_cloud_full_size_first_block(ctx, prec):
         assert np.all(np.abs(ed) > 1e-3 * scale)  # a field that does not cancel away
 
 
-@pytest.mark.parametrize("prec", [pc.PC_F64, pc.PC_MIXED])
-def test_cloud_grid_path(ctx, prec):
+@pytest.mark.parametrize("prec,near", [(pc.PC_F64, 0.0), (pc.PC_MIXED, 0.0), (pc.PC_MIXED, 12e-9)])
+def test_cloud_grid_path(ctx, prec, near):
     # 96 oscillators in a 150 nm cube (5 nm minimum spacing, random axes): above the size that runs
-    # as one CTA per configuration, so the run takes the grid-wide drive / RK4 launches
+    # as one CTA per configuration, so the run takes the grid-wide drive / RK4 launches; with near
+    # sources (within 12 nm) in float64
     cfg = W.cfg5(N=96, n_steps=240, side=150e-9, min_spacing=5e-9, seed=7)
     ref = oracle.dipoles_run(cfg)
     assert ref["status"] == oracle.OK
-    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=prec, want_Ed=True)
+    out = pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg), cfg.dt, cfg.n_steps, precision=prec, want_Ed=True,
+                            near_f64=near)
     for k in ("d", "d_dot", "Ed"):
         assert hist_err(out[k][0], ref[k]) < HIST_TOL[prec], k
 
@@ -358,3 +360,26 @@ def test_run_tuner_and_slice_counts_keep_parity(ctx, prec):
             pc.pc_set_run_tiling(ctx, 65)
     finally:
         pc.pc_set_run_tiling(ctx, 0)
+
+
+def test_near_sources_match_float64():
+    # separations up to 10 nm with the near sources (within 10 nm) in float64: every source of a pair
+    # is near, so the mixed run's driving field is the float64 one and the run follows the float64
+    # run to its rounding (moment histories within 1e-11 of their peaks, fitted omega within 1e-12
+    # and gamma within 1e-5 gamma0 -- where float32 alone is off by up to 0.7 gamma0)
+    ctx = pc.Context(0)
+    cfg, sep = W.cfg3(B=256, n_steps=40000)
+    sel = np.nonzero(sep < 9.9e-9)[0]  # clear of the 10 nm bound, which float32 distances blur
+    sub = W.lo_batch(cfg.origin[sel], cfg.axis[sel], cfg.omega0[sel], 1e-11, cfg.dt, cfg.n_steps, cfg.first_index)
+    assert sub.B >= 80
+    lod = pc.lo_config_to_device(sub)
+    kw = dict(fit=True, first_index=sub.first_index, want_energy=False)
+    f = pc.pc_dipoles_run(ctx, lod, sub.dt, sub.n_steps, precision=pc.PC_F64, **kw)
+    m = pc.pc_dipoles_run(ctx, lod, sub.dt, sub.n_steps, precision=pc.PC_MIXED, near_f64=10e-9, **kw)
+    for k in ("d", "d_dot"):
+        err = float(((m[k] - f[k]).abs().amax(-1) / f[k].abs().amax(-1)).max())
+        assert err < 1e-11, (k, err)
+    g0 = th.gamma0(W.E_CHARGE, W.M_E / 2, float(cfg.omega0[0, 0]))
+    assert float(((m["omega"] - f["omega"]).abs() / f["omega"]).max()) < 1e-12
+    assert float((m["gamma"] - f["gamma"]).abs().max()) / g0 < 1e-5
+    ctx.close()
