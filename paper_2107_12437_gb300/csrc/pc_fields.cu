@@ -864,26 +864,29 @@ __global__ void __launch_bounds__(kMixThreads, 4) fields_mixed_kernel(const Laun
   // units: E in k_e e / L^2, B in k_e e / (L^2 c), phi in k_e e / L, A in k_e e / (L c)
   const float fE = L.unit[0], fB = L.unit[1], fP = L.unit[2], fA = L.unit[3];
   const int64_t o = (L.frame0 + f) * L.pts.P + tile_point(L, tiles_v, tid);
+  // streaming stores (evict first): the outputs are not read again by this kernel, and L2 keeps the
+  // lines that are (the histories, the stack of the slow pairs' calls); on the 2048^2 x 16-frame
+  // grid this cut the DRAM writes of a launch from 3.48 to 3.19 GB (outputs: 2.75 GB)
   if (L.out.E) {
     float *e = (float *)L.out.E + 3 * o;
-    e[0] = fE * kahan_get(s_kahan, tid, 0);
-    e[1] = fE * kahan_get(s_kahan, tid, 1);
-    e[2] = fE * kahan_get(s_kahan, tid, 2);
+    __stcs(e + 0, fE * kahan_get(s_kahan, tid, 0));
+    __stcs(e + 1, fE * kahan_get(s_kahan, tid, 1));
+    __stcs(e + 2, fE * kahan_get(s_kahan, tid, 2));
   }
   if (L.out.B) {
     float *b = (float *)L.out.B + 3 * o;
-    b[0] = fB * kahan_get(s_kahan, tid, 3);
-    b[1] = fB * kahan_get(s_kahan, tid, 4);
-    b[2] = fB * kahan_get(s_kahan, tid, 5);
+    __stcs(b + 0, fB * kahan_get(s_kahan, tid, 3));
+    __stcs(b + 1, fB * kahan_get(s_kahan, tid, 4));
+    __stcs(b + 2, fB * kahan_get(s_kahan, tid, 5));
   }
-  if (L.out.phi) ((float *)L.out.phi)[o] = fP * kahan_get(s_kahan, tid, 6);
+  if (L.out.phi) __stcs((float *)L.out.phi + o, fP * kahan_get(s_kahan, tid, 6));
   if (L.out.A) {
     float *a = (float *)L.out.A + 3 * o;
-    a[0] = fA * kahan_get(s_kahan, tid, 7);
-    a[1] = fA * kahan_get(s_kahan, tid, 8);
-    a[2] = fA * kahan_get(s_kahan, tid, 9);
+    __stcs(a + 0, fA * kahan_get(s_kahan, tid, 7));
+    __stcs(a + 1, fA * kahan_get(s_kahan, tid, 8));
+    __stcs(a + 2, fA * kahan_get(s_kahan, tid, 9));
   }
-  if (L.out.mask) L.out.mask[o] = mask;
+  if (L.out.mask) __stcs(reinterpret_cast<unsigned char *>(L.out.mask) + o, (unsigned char)mask);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1112,26 +1115,28 @@ __global__ void __launch_bounds__(kMixThreads, 2) fields_mixed2_kernel(const Lau
       const float2 sv = s_kahan[0][i][tid], cv = s_kahan[1][i][tid];
       val[i] = lane == 0 ? sv.x - cv.x : sv.y - cv.y;
     }
+    // streaming stores, as in the one-point kernel
     if (L.out.E) {
       float *e = (float *)L.out.E + 3 * o;
-      e[0] = uE * val[0];
-      e[1] = uE * val[1];
-      e[2] = uE * val[2];
+      __stcs(e + 0, uE * val[0]);
+      __stcs(e + 1, uE * val[1]);
+      __stcs(e + 2, uE * val[2]);
     }
     if (L.out.B) {
       float *b = (float *)L.out.B + 3 * o;
-      b[0] = uB * val[3];
-      b[1] = uB * val[4];
-      b[2] = uB * val[5];
+      __stcs(b + 0, uB * val[3]);
+      __stcs(b + 1, uB * val[4]);
+      __stcs(b + 2, uB * val[5]);
     }
-    if (L.out.phi) ((float *)L.out.phi)[o] = uP * val[6];
+    if (L.out.phi) __stcs((float *)L.out.phi + o, uP * val[6]);
     if (L.out.A) {
       float *a = (float *)L.out.A + 3 * o;
-      a[0] = uA * val[7];
-      a[1] = uA * val[8];
-      a[2] = uA * val[9];
+      __stcs(a + 0, uA * val[7]);
+      __stcs(a + 1, uA * val[8]);
+      __stcs(a + 2, uA * val[9]);
     }
-    if (L.out.mask) L.out.mask[o] = lane == 0 ? maskA : maskB;
+    if (L.out.mask)
+      __stcs(reinterpret_cast<unsigned char *>(L.out.mask) + o, (unsigned char)(lane == 0 ? maskA : maskB));
   }
 }
 
