@@ -12,7 +12,7 @@ field kernel, clocks sampled during the timed region and the FP64 CPU oracle on 
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --profile fields_mixed_small|fields_mixed2_small|fields_f64_small|lo_small|lo_f64_small|
-                            ring_small|cloud_small|adj_small
+                            ring_small|cloud_small|cloud_late|adj_small
                                                      (one small run for ncu)
 Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own copy of the workload
 (independent problems, no data-path collective), so scaling is weak.
@@ -400,7 +400,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", default=None,
                     choices=["fields_mixed_small", "fields_mixed2_small", "fields_f64_small", "lo_small",
-                             "lo_f64_small", "ring_small", "cloud_small", "adj_small"])
+                             "lo_f64_small", "ring_small", "cloud_small", "cloud_late", "adj_small"])
     ap.add_argument("--no-extra", action="store_true", help="skip the float64, oscillator and CPU legs")
     ap.add_argument("--compare-cloud", type=int, default=0, metavar="STEPS",
                     help="run the 4096-oscillator cloud for STEPS steps in both precisions and compare them")
@@ -442,6 +442,23 @@ def main():
             cfg, _ = W.cfg3(B=256, n_steps=2000)
             prec = pc.PC_MIXED if args.profile == "lo_small" else pc.PC_F64
             pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=prec)
+        elif args.profile == "cloud_late":
+            # the cloud past its static pre-history: 4000 steps (graph loop), the state kept, then 32
+            # steps resumed from it with the block loop launched from the host; only the resumed run
+            # lies inside the profiler's range (ncu --profile-from-start off)
+            cfg = W.cfg5(n_steps=4000)
+            lod = pc.lo_config_to_device(cfg, dev)
+            pc.pc_set_run_tiling(ctx, 16)  # the slice count the tuner picks for the cloud
+            st = torch.empty(pc.pc_dipoles_state_size(ctx, lod, cfg.dt), dtype=torch.float64, device=dev)
+            pc.pc_dipoles_run(ctx, lod, cfg.dt, 4000, precision=pc.PC_MIXED, want_history=False, want_energy=False,
+                              state_out=st)
+            torch.cuda.synchronize()
+            os.environ["PYCHARGE_GB300_HOST_LOOP"] = "1"
+            torch.cuda.profiler.start()
+            pc.pc_dipoles_run(ctx, lod, cfg.dt, 32, precision=pc.PC_MIXED, want_history=False, want_energy=False,
+                              state_in=st)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         elif args.profile in ("ring_small", "cloud_small"):
             # grid path, mixed, block loop launched from the host so that the profiler sees every
             # launch: the 256-oscillator ring over 200 steps (13 causal blocks), or the 4096-oscillator

@@ -332,11 +332,10 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   const float4 cj = *reinterpret_cast<const float4 *>(fj + 8);  // (p_z, mu+, mu-, q/e)
   const HistF32Ring H{a.H32 + bj * (size_t)a.hs, RING ? (int)a.wm : -1};
   // fast path: both charges on the segment of the centre's retarded time (packed solve), then only
-  // the driving-field projection p_i . E of the pair
+  // the driving-field projection p_i . E of the pair (xc is the fraction in [0, 1) of the retarded
+  // sample kb + xc: the segment is kb's)
   {
-    float fl;
-    const int kc = Num<float>::floor_int(xc, fl);
-    const int k = kb + kc;
+    const int k = kb;
     if (k < -1) {
       // the centre's retarded time lies a sample or more before t = 0; when both charges' offsets
       // (at most |s| samples) keep them there too, they rest at their first position with no
@@ -361,7 +360,7 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
       // the first segment may not be extended backwards, the last one only by kEndTol
       const float lo = (k == 0) ? 0.f : -kExtrap, hi = 1.f + ((k == nvalid - 2) ? kEndTol : kExtrap);
       float2 X, V, Ac, dl;
-      if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, cj.y, cj.z, X, V, Ac, dl, 0.5f * (lo + hi),
+      if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc, rn, rp, cj.y, cj.z, X, V, Ac, dl, 0.5f * (lo + hi),
                                0.5f * (hi - lo)))
         return dipole_drive_fast(rn, rp, cj.y, cj.z, cj.w, X, V, Ac, dl, rpi, ppi);
     }
@@ -386,9 +385,62 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   return acc[0] * fi[6] + acc[1] * fi[7] + acc[2] * fi[8];
 }
 
+// The grid path's float32 source loop (sources j = j_lo + m, step slots): the pair-table rows, the
+// sources' records and history rows are reached by 32-bit indices and a pointer that advances with
+// j (no 64-bit products per source), and pair_drive_f32's fast path is written out here; every
+// other case (static pre-history, the general solve) goes to pair_drive_f32 itself, which then
+// takes the same steps as for the plain loop.  Groups of 32 sources are summed in float32, the
+// group sums added with Kahan compensation into (accf, comp).
+template <bool RING>
+__device__ __forceinline__ void drive_sources_grid(const RunArgs &a, int b, int i, int64_t n0, float stage_f, int m,
+                                                   int slots, int j_lo, int j_hi, float &accf, float &comp,
+                                                   int *err) {
+  const size_t row = (size_t)bidx(a, b, i) * a.N;
+  const size_t b0 = bidx(a, b, 0);
+  const int2 *pd = a.delay + row;
+  const float4 *pg = a.pgeo + row;
+  const float4 *pc = reinterpret_cast<const float4 *>(a.dipf + b0 * kDipF) + 2;  // (p_z, mu+, mu-, q/e)
+  const size_t hstep = (size_t)slots * (size_t)a.hs;
+  const int mask = RING ? (int)a.wm : -1;
+  const int n0i = (int)n0, nvalid = n0i + 1;
+  for (int j0 = j_lo + m; j0 < j_hi; j0 += 32 * slots) {
+    const int jend = min(j_hi, j0 + 32 * slots);
+    float grp = 0.f;
+    const float4 *hj = a.H32 + (b0 + (size_t)j0) * (size_t)a.hs;
+    for (int j = j0; j < jend; j += slots, hj += hstep) {
+      if (j == i) continue;
+      const int2 dl = pd[j];
+      const float4 geo = pg[j];
+      const float xs = stage_f - __int_as_float(dl.y);
+      float flf;
+      const int fl = Num<float>::floor_int(xs, flf);
+      const int k = n0i - dl.x + fl;
+      const float xc = xs - flf;
+      if (k >= 0 && k <= nvalid - 2) {
+        const float4 cj = pc[j * (kDipF / 4)];
+        const float4 h0 = hj[k & mask], h1 = hj[(k + 1) & mask];
+        const float lo = (k == 0) ? 0.f : -kExtrap, hi = 1.f + ((k == nvalid - 2) ? kEndTol : kExtrap);
+        float2 X, V, Ac, dlt;
+        if (dip_pair_states_fast(h0.x, h0.y, h0.z, h1.x, h1.y, h1.z, xc, geo.x, geo.y, cj.y, cj.z, X, V, Ac, dlt,
+                                 0.5f * (lo + hi), 0.5f * (hi - lo))) {
+          grp += dipole_drive_fast(geo.x, geo.y, cj.y, cj.z, cj.w, X, V, Ac, dlt, geo.z, geo.w);
+          continue;
+        }
+      }
+      grp += pair_drive_f32<RING>(a, b, i, j, k, xc, geo, nvalid, err);
+    }
+    const float y = grp - comp;
+    const float t = accf + y;
+    comp = (t - accf) - y;
+    accf = t;
+  }
+}
+
 // Phase A for one receiver (one warp): stage fields E_d(n0 + (s+1)/2), s < ns, into Es[1 + s];
-// ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.
-template <bool MIXED, bool NEAR = false, bool RING = true>
+// ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.  GROUPS: the float32
+// sources through drive_sources_grid (the grid path, whose warps loop over many sources; in the
+// persistent kernel a lane has one or two, and the group loop only raises its registers).
+template <bool MIXED, bool NEAR = false, bool RING = true, bool GROUPS = false>
 __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err,
                             int j_lo, int j_hi, double *dst, int sgsel = -1) {
   const int lane = threadIdx.x & 31;
@@ -436,7 +488,9 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
     }
   };
   if (m < slots) {
-    if constexpr (MIXED && !NEAR) {
+    if constexpr (MIXED && !NEAR && GROUPS) {
+      drive_sources_grid<RING>(a, b, i, n0, stage_f, m, slots, j_lo, j_hi, accf, comp, err);
+    } else if constexpr (MIXED && !NEAR) {
       for (int j = j_lo + m; j < j_hi; j += slots) source(j, 0, 2);
     } else {
       // one loop, so that the float64 pair is inlined once
@@ -773,7 +827,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs 
   const int j_lo = min(a.N, z * chunk), j_hi = min(a.N, j_lo + chunk);
   double *dst = a.nsplit > 1 ? a.Epart + (size_t)z * a.B * a.N * (2 * kMaxBlock + 1) : a.Es;
   int err = 0;
-  drive_phase<MIXED, NEAR, RING>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
+  drive_phase<MIXED, NEAR, RING, true>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
   if (err) set_status(a.status, err);
 }
 
