@@ -75,6 +75,17 @@ FLOP_TALLY = {
     },
 }
 FLOPS_PER_PAIR = sum(sum(v.values()) for v in FLOP_TALLY.values())
+# The same for one charge's contribution to an oscillator's driving field at one stage time: the
+# retarded time and interpolation as above, Griffiths' E alone, and its projection on the receiver's
+# axis added to the sum.
+DRIVE_FLOP_TALLY = {
+    "retarded time (quadratic on one segment)": FLOP_TALLY["retarded time (quadratic on one segment)"],
+    "interpolation at the root": FLOP_TALLY["interpolation at the root"],
+    "Lienard-Wiechert E (Griffiths)": {k: v for k, v in FLOP_TALLY["Lienard-Wiechert fields (Griffiths)"].items()
+                                       if not k.startswith(("E +=", "B +=", "phi +=", "A +="))},
+    "projection": {"p_i . E": 5, "sum +=": 1},
+}
+DRIVE_FLOPS_PER_PAIR = sum(sum(v.values()) for v in DRIVE_FLOP_TALLY.values())
 FP32_LANES_PER_SM = 128  # compute capability 10.x: 128 float32 FMA lanes per SM
 
 
@@ -733,6 +744,31 @@ def main():
         r["workload"] = "cloud: 4096 oscillators in a 600 nm cube x 20000 RK4 steps (1250 causal blocks of 16 steps)"
         r["source_slices"] = sl
         ds["cloud_mixed"] = r
+        # the cloud's dominant kernel, the grid-path drive, against the float32 roofline: 4000 steps to
+        # a state (past the static pre-history of most pairs), then 100 causal blocks resumed from it
+        # with every launch timed by the library (pc_set_run_timing: CUDA events on the run's stream)
+        lod5 = pc.lo_config_to_device(cfg5, dev)
+        st5 = torch.empty(pc.pc_dipoles_state_size(ctx, lod5, cfg5.dt), dtype=torch.float64, device=dev)
+        pc.pc_dipoles_run(ctx, lod5, cfg5.dt, 4000, precision=pc.PC_MIXED, want_history=False, want_energy=False,
+                          state_out=st5)
+        pc.pc_set_run_timing(ctx, 1)
+        pc.pc_dipoles_run(ctx, lod5, cfg5.dt, 1600, precision=pc.PC_MIXED, want_history=False, want_energy=False,
+                          state_in=st5)
+        tm = pc.pc_get_run_timing(ctx)
+        pc.pc_set_run_timing(ctx, 0)
+        del st5
+        drive_ms = tm["drive_ms"] / max(tm["drive_launches"], 1)
+        drive_pairs = 2 * cfg5.B * cfg5.N * (cfg5.N - 1) * 32  # charge pairs x stage times per block
+        drive_tf = DRIVE_FLOPS_PER_PAIR * drive_pairs / (drive_ms * 1e-3) / 1e12
+        line["roofline_drive"] = {
+            "kernel": "lo_drive_kernel (mixed, grid path)", "bound": "alu", "achieved": drive_tf,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": drive_tf / peak_tflops,
+            "frac_of_measured_fp32_fma": drive_tf / (2.0 * fp32_fma / 1e12),
+            "flops_per_pair": DRIVE_FLOPS_PER_PAIR, "flops_per_pair_basis": "bench.DRIVE_FLOP_TALLY",
+            "launch_ms": drive_ms, "launches": tm["drive_launches"], "rk4_launch_ms": tm["rk4_ms"] / max(tm["rk4_launches"], 1),
+            "charge_pair_evals_per_launch": drive_pairs, "source_slices": sl,
+            "workload": "cloud (4096 oscillators), blocks 250-349 (steps 4000-5599) resumed from a state, 16 steps "
+                        "(32 stage times) per launch; launch times from CUDA events on the run's stream"}
         # the all-float64 GPU path on the same cloud over its first 1000 steps (the whole run takes
         # ~7 minutes in float64), and the mixed path over the same steps for a like-for-like factor
         cfg5s = W.cfg5(n_steps=1000)

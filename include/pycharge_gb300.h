@@ -298,6 +298,31 @@ pc_status pc_autotune_run(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
 pc_status pc_set_run_tiling(pc_ctx *ctx, int32_t source_slices);
 
 /*
+ * Launch timing of the oscillator run (device time of its kernels, measured with CUDA events on the
+ * run's stream).  pc_set_run_timing(ctx, 1) clears the counters and makes later pc_dipoles_run /
+ * pc_dipoles_run_moving calls of this context record them: the grid path (more than 64 dipoles per
+ * configuration) then launches its causal-block loop from the host instead of as one CUDA graph
+ * (same kernels, same order, bitwise the same results) with an event pair around every drive
+ * (phase A: the driving fields of a block) and RK4 (phase B) launch, and the persistent path (64 or
+ * fewer) one around its single launch.  The calls synchronise their stream every 64 blocks to read
+ * the events back, so timed runs are for measurement, not production.  pc_set_run_timing(ctx, 0)
+ * turns it off; pc_get_run_timing copies the counters accumulated since the last enable.  The drive
+ * launches counted are those of whole and partial causal blocks (not the E_d(0) evaluation of a
+ * fresh run).  Errors: PC_ERR_ARG (null context or output, enable not 0 or 1), PC_ERR_CUDA.
+ */
+typedef struct {
+  int64_t drive_launches; /* grid path: phase-A launches timed */
+  double drive_ms;        /* their summed device time (ms) */
+  int64_t rk4_launches;   /* grid path: phase-B launches timed */
+  double rk4_ms;
+  int64_t run_launches;   /* persistent path: time-loop launches timed (one per call) */
+  double run_ms;
+} pc_run_timing;
+
+pc_status pc_set_run_timing(pc_ctx *ctx, int32_t enable);
+pc_status pc_get_run_timing(pc_ctx *ctx, pc_run_timing *out);
+
+/*
  * pc_dipoles_state_size -- the length (float64 values) of a run state of these dipoles at this dt
  * (pc_run_opts.state_in / state_out): a header (step, depth D, B N), E_d of every dipole at the state's
  * step and d, d', d'' of its last D + 1 samples, D the deepest sample a causal block can reach behind

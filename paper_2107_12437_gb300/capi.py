@@ -78,6 +78,11 @@ class PcPlaneTiling(ctypes.Structure):
     _fields_ = [("tile_rows", _i32), ("tile_cols", _i32), ("sources_per_stage", _i32)]
 
 
+class PcRunTiming(ctypes.Structure):
+    _fields_ = [("drive_launches", _i64), ("drive_ms", _f64), ("rk4_launches", _i64), ("rk4_ms", _f64),
+                ("run_launches", _i64), ("run_ms", _f64)]
+
+
 class PcDipoleGrads(ctypes.Structure):
     _fields_ = [("origin", _vp), ("omega0", _vp), ("d0", _vp)]
 
@@ -98,6 +103,8 @@ SIGNATURES = {
     "pc_autotune_run": (ctypes.c_int, [_vp, ctypes.POINTER(PcDipoles), _f64, _i64, ctypes.POINTER(PcRunOpts),
                                        ctypes.POINTER(_i32), _vp]),
     "pc_set_run_tiling": (ctypes.c_int, [_vp, _i32]),
+    "pc_set_run_timing": (ctypes.c_int, [_vp, _i32]),
+    "pc_get_run_timing": (ctypes.c_int, [_vp, _vp]),
     "pc_fields_to_host": (ctypes.c_int, [_vp, ctypes.POINTER(PcCharges), ctypes.POINTER(PcDipoleSources), _vp, _i64,
                                          ctypes.POINTER(_f64), _i32, _i32, _i32, _f64, ctypes.POINTER(PcFieldOut),
                                          _vp]),
@@ -413,6 +420,19 @@ def pc_autotune_run(ctx, dp, dt, probe_steps=64, precision=PC_F64, near_f64=0.0,
 def pc_set_run_tiling(ctx, source_slices):
     """pc_set_run_tiling: source slices per receiver of the grid path (0: the heuristic)."""
     _check(ctx.lib.pc_set_run_tiling(ctx.handle, int(source_slices)), "pc_set_run_tiling")
+
+
+def pc_set_run_timing(ctx, enable):
+    """pc_set_run_timing: 1 clears the launch-time counters and times later oscillator runs (their
+    grid-path block loop then launched from the host); 0 turns it off."""
+    _check(ctx.lib.pc_set_run_timing(ctx.handle, int(bool(enable))), "pc_set_run_timing")
+
+
+def pc_get_run_timing(ctx):
+    """pc_get_run_timing: the counters since the last enable, as a dict."""
+    t = PcRunTiming()
+    _check(ctx.lib.pc_get_run_timing(ctx.handle, ctypes.byref(t)), "pc_get_run_timing")
+    return {k: getattr(t, k) for k, _ in PcRunTiming._fields_}
 
 
 def pc_dipoles_state_size(ctx, dp, dt, stream=None):

@@ -58,6 +58,8 @@ extern "C" pc_status pc_ctx_destroy(pc_ctx *ctx) {
   ctx->out_chunks.release();
   for (int k = 0; k < 4; ++k)
     if (ctx->pipe_ev[k]) cudaEventDestroy(ctx->pipe_ev[k]);
+  for (cudaEvent_t e : ctx->tev)
+    if (e) cudaEventDestroy(e);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   delete ctx;
   return PC_OK;

@@ -332,10 +332,11 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   const float4 cj = *reinterpret_cast<const float4 *>(fj + 8);  // (p_z, mu+, mu-, q/e)
   const HistF32Ring H{a.H32 + bj * (size_t)a.hs, RING ? (int)a.wm : -1};
   // fast path: both charges on the segment of the centre's retarded time (packed solve), then only
-  // the driving-field projection p_i . E of the pair (xc is the fraction in [0, 1) of the retarded
-  // sample kb + xc: the segment is kb's)
+  // the driving-field projection p_i . E of the pair
   {
-    const int k = kb;
+    float fl;
+    const int kc = Num<float>::floor_int(xc, fl);
+    const int k = kb + kc;
     if (k < -1) {
       // the centre's retarded time lies a sample or more before t = 0; when both charges' offsets
       // (at most |s| samples) keep them there too, they rest at their first position with no
@@ -360,7 +361,7 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
       // the first segment may not be extended backwards, the last one only by kEndTol
       const float lo = (k == 0) ? 0.f : -kExtrap, hi = 1.f + ((k == nvalid - 2) ? kEndTol : kExtrap);
       float2 X, V, Ac, dl;
-      if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc, rn, rp, cj.y, cj.z, X, V, Ac, dl, 0.5f * (lo + hi),
+      if (dip_pair_states_fast(x0, v0, a0, x1, v1, a1, xc - fl, rn, rp, cj.y, cj.z, X, V, Ac, dl, 0.5f * (lo + hi),
                                0.5f * (hi - lo)))
         return dipole_drive_fast(rn, rp, cj.y, cj.z, cj.w, X, V, Ac, dl, rpi, ppi);
     }
@@ -385,10 +386,28 @@ __device__ float pair_drive_f32(const RunArgs &a, int b, int i, int j, int kb, f
   return acc[0] * fi[6] + acc[1] * fi[7] + acc[2] * fi[8];
 }
 
+// A source whose charges both still rest at their first position at their retarded times (a
+// sample or more before t = 0, Sec. 3.2): their distances in closed form without a solve, then the
+// driving-field projection, as in pair_drive_f32.  x0: the first sample's X; false where the
+// closed form does not apply.
+__device__ __forceinline__ bool static_pair_drive(float x0, const float4 cj, int kb, float xc, const float4 geo,
+                                                  float &v) {
+  const float rn = geo.x, rp = geo.y;
+  const float sp = cj.y * x0, sm = -cj.z * x0;
+  if (!((float)kb + xc + fmaxf(fabsf(sp), fabsf(sm)) < -0.01f)) return false;
+  const float Rp = sqrtf(fmaxf(rn * rn + sp * (sp - 2.f * rp), 0.f));
+  const float Rm = sqrtf(fmaxf(rn * rn + sm * (sm - 2.f * rp), 0.f));
+  const float2 dl = make_float2(__fdividef(sp * (sp - 2.f * rp), Rp + rn), __fdividef(sm * (sm - 2.f * rp), Rm + rn));
+  const float2 zero = make_float2(0.f, 0.f);
+  if (!(Rp > 0.f && Rm > 0.f)) return false;
+  v = dipole_drive_fast(rn, rp, cj.y, cj.z, cj.w, make_float2(x0, x0), zero, zero, dl, geo.z, geo.w);
+  return true;
+}
+
 // The grid path's float32 source loop (sources j = j_lo + m, step slots): the pair-table rows, the
 // sources' records and history rows are reached by 32-bit indices and a pointer that advances with
-// j (no 64-bit products per source), and pair_drive_f32's fast path is written out here; every
-// other case (static pre-history, the general solve) goes to pair_drive_f32 itself, which then
+// j (no 64-bit products per source), and pair_drive_f32's fast path and static pre-history are
+// written out here; every other case (the general solve) goes to pair_drive_f32 itself, which then
 // takes the same steps as for the plain loop.  Groups of 32 sources are summed in float32, the
 // group sums added with Kahan compensation into (accf, comp).
 template <bool RING>
@@ -424,6 +443,12 @@ __device__ __forceinline__ void drive_sources_grid(const RunArgs &a, int b, int 
         if (dip_pair_states_fast(h0.x, h0.y, h0.z, h1.x, h1.y, h1.z, xc, geo.x, geo.y, cj.y, cj.z, X, V, Ac, dlt,
                                  0.5f * (lo + hi), 0.5f * (hi - lo))) {
           grp += dipole_drive_fast(geo.x, geo.y, cj.y, cj.z, cj.w, X, V, Ac, dlt, geo.z, geo.w);
+          continue;
+        }
+      } else if (k < -1) {
+        float v;
+        if (static_pair_drive(hj[0].x, pc[j * (kDipF / 4)], k, xc, geo, v)) {
+          grp += v;
           continue;
         }
       }
@@ -1500,6 +1525,24 @@ static pc_status launch_block_loop(pc_ctx *ctx, const RunArgs &a, bool mixed, di
   return cudaGraphLaunch(ex, st) == cudaSuccess ? PC_OK : PC_ERR_CUDA;
 }
 
+// Timed grid path: the events of nev / 3 blocks (drive start, RK4 start, RK4 end) into the context's
+// sums, after the last of them has completed.
+static pc_status read_block_times(pc_ctx *ctx, int nev) {
+  if (nev < 3) return PC_OK;
+  if (cudaEventSynchronize(ctx->tev[nev - 1]) != cudaSuccess) return PC_ERR_CUDA;
+  for (int e = 0; e + 2 < nev; e += 3) {
+    float d = 0.f, r = 0.f;
+    if (cudaEventElapsedTime(&d, ctx->tev[e], ctx->tev[e + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&r, ctx->tev[e + 1], ctx->tev[e + 2]) != cudaSuccess)
+      return PC_ERR_CUDA;
+    ctx->timing.drive_ms += d;
+    ctx->timing.drive_launches += 1;
+    ctx->timing.rk4_ms += r;
+    ctx->timing.rk4_launches += 1;
+  }
+  return PC_OK;
+}
+
 // Internal knobs of run_impl beyond pc_run_opts (the adjoint's and the state-size query's).
 struct RunPlan {
   double *Ehalf = nullptr;                  // [B][N][n_steps] E_d at the half steps, or null
@@ -1705,11 +1748,22 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const unsigned rgrid = (unsigned)((nbn + 127) / 128);
   if (mixed) pc::lo_first_kernel<true><<<rgrid, 128, 0, st>>>(a);
   else pc::lo_first_kernel<false><<<rgrid, 128, 0, st>>>(a);
+  const bool timed = ctx->run_timing != 0;
   if (dp->N <= pc::kSmallN) {
     // small configurations: one persistent CTA each, the time loop inside
+    if (timed) cudaEventRecord(ctx->tev[0], st);
     if (pc::launch_run_args(pc::run_kernel_for(a, mixed), dim3(dp->B), dim3(pc::kRunWarps * 32), a, st) !=
         cudaSuccess)
       return PC_ERR_CUDA;
+    if (timed) {
+      cudaEventRecord(ctx->tev[1], st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(ctx->tev[1]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[1]) != cudaSuccess)
+        return PC_ERR_CUDA;
+      ctx->timing.run_ms += ms;
+      ctx->timing.run_launches += 1;
+    }
   } else {
     // large configurations: grid-wide phases, one drive and one RK4 launch per causal block of the
     // shortest block length over the batch; sources split so that about two resident warps per SM
@@ -1732,16 +1786,28 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
       // drive and one RK4 launch per block, same kernels and order) serves where that node is not
       // available, and on request through PYCHARGE_GB300_HOST_LOOP=1 (profilers that do not
       // descend into conditional graph nodes see every launch)
+      // (and always when the launches are timed, pc_set_run_timing: an event pair around each)
       const char *hl = getenv("PYCHARGE_GB300_HOST_LOOP");
-      pc_status gs = (hl && hl[0] == '1') ? PC_ERR_CUDA : pc::launch_block_loop(ctx, a, mixed, dgrid, rgrid, st);
+      pc_status gs = (timed || (hl && hl[0] == '1')) ? PC_ERR_CUDA
+                                                     : pc::launch_block_loop(ctx, a, mixed, dgrid, rgrid, st);
       if (gs != PC_OK) {
         cudaGetLastError();
+        int nev = 0;
         for (int64_t n0 = n_begin; n0 < n_end; n0 += K) {
           const int kb = (int)std::min<int64_t>(K, n_end - n0);
+          if (timed) cudaEventRecord(ctx->tev[nev++], st);
           pc::launch_drive(drive, dgrid, a, n0, 2 * kb, st);
+          if (timed) cudaEventRecord(ctx->tev[nev++], st);
           const unsigned wgrid = (unsigned)((nbn * 32 + 127) / 128);
           if (mixed) pc::lo_rk4_kernel<true><<<wgrid, 128, 0, st>>>(a, n0, kb);
           else pc::lo_rk4_kernel<false><<<wgrid, 128, 0, st>>>(a, n0, kb);
+          if (timed) {
+            cudaEventRecord(ctx->tev[nev++], st);
+            if (nev + 3 > 3 * 64 || n0 + K >= n_end) {
+              if (pc::read_block_times(ctx, nev) != PC_OK) return PC_ERR_CUDA;
+              nev = 0;
+            }
+          }
         }
         if (cudaGetLastError() != cudaSuccess) return PC_ERR_CUDA;
       }
@@ -1798,6 +1864,33 @@ extern "C" pc_status pc_dipoles_state_size(pc_ctx *ctx, const pc_dipoles *dp, do
 extern "C" pc_status pc_set_run_tiling(pc_ctx *ctx, int32_t source_slices) {
   if (!ctx || source_slices < 0 || source_slices > pc::kMaxSplit) return PC_ERR_ARG;
   ctx->run_slices = source_slices;
+  return PC_OK;
+}
+
+extern "C" pc_status pc_set_run_timing(pc_ctx *ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return PC_ERR_ARG;
+  pc::DeviceGuard g(ctx->device);
+  if (enable && !ctx->tev[0]) {
+    // all the events or none
+    for (cudaEvent_t &e : ctx->tev) {
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+        for (cudaEvent_t &f : ctx->tev) {
+          if (f) cudaEventDestroy(f);
+          f = nullptr;
+        }
+        return PC_ERR_CUDA;
+      }
+    }
+  }
+  ctx->run_timing = enable;
+  if (enable) ctx->timing = pc_run_timing{};  // disabling keeps the counters readable
+  return PC_OK;
+}
+
+extern "C" pc_status pc_get_run_timing(pc_ctx *ctx, pc_run_timing *out) {
+  if (!ctx || !out) return PC_ERR_ARG;
+  *out = ctx->timing;
   return PC_OK;
 }
 

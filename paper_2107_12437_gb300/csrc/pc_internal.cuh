@@ -57,6 +57,9 @@ struct pc_ctx {
   int pts_per_thread = 1;               // mixed plane grids of dipoles: 1, or 2 (tiles twice as tall)
   int src_chunk = 64;                   // mixed plane tiles: sources per shared-memory stage (32 or 64)
   int run_slices = 0;                   // oscillator grid path: source slices per receiver (0: heuristic)
+  int run_timing = 0;                   // oscillator run: record launch times (pc_set_run_timing)
+  pc_run_timing timing = {};            // their sums since the last enable
+  cudaEvent_t tev[3 * 64 + 2] = {};     // events of up to 64 timed blocks (or one persistent launch)
   pc::Buf out_chunks;                   // field outputs bound for the host: two alternating chunks
   cudaStream_t copy_stream = nullptr;   // their device-to-host copies
   cudaEvent_t pipe_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // chunk computed (2), chunk copied (2)
