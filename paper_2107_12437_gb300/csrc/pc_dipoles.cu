@@ -174,16 +174,21 @@ __device__ void rk4_table(const RunArgs &a, size_t bi) {
 // inclusive scan over the lanes (log2 kb shuffle rounds) instead of kb dependent steps.  Called by
 // all 32 lanes of a warp; appends d, d', d'' (and the float32 mirror, energy, E_d, the half-step
 // fields) to the history exactly as the stepwise form.
+// Es: the receiver's stage-field row (global, or shared in the persistent kernel); ys: null (the
+// block's starting state read from the history store), or the state (d, d') carried in shared
+// memory from the previous block, which the block's last lane updates; Tsh / fsc: null, or the
+// receiver's table row and the float32 mirror's three scales held in shared memory (the persistent
+// kernel: the chain of a block then waits on no global load of constants).
 template <bool MIXED>
-__device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop) {
+__device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop, double *Es,
+                               double *ys = nullptr, const double *Tsh = nullptr, const float *fsc = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t So = a.n_steps - a.n_begin + 1;
   const size_t bi = bidx(a, b, i);
-  double *Es = a.Es + bi * (2 * kMaxBlock + 1);
-  const double *T = a.rk4tab + bi * kTab;
+  const double *T = Tsh ? Tsh : a.rk4tab + bi * kTab;
   const double g0 = T[kTabC + 0], w2 = T[kTabC + 1], qm = T[kTabC + 2];
   const size_t row = bi * (size_t)a.hs;
-  const double y0 = a.d[row + (n0 & a.wm)], y1 = a.dd[row + (n0 & a.wm)];
+  const double y0 = ys ? ys[0] : a.d[row + (n0 & a.wm)], y1 = ys ? ys[1] : a.dd[row + (n0 & a.wm)];
   double vx = 0.0, vy = 0.0, e2 = 0.0, e4 = 0.0;
   if (lane < kb) {
     const double e1 = Es[2 * lane];
@@ -197,15 +202,15 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
     const double ox = __shfl_up_sync(0xffffffffu, vx, off), oy = __shfl_up_sync(0xffffffffu, vy, off);
     if (lane >= off) {
       const double *P = T + 4 * (off - 1);  // M^off
-      vx += P[0] * ox + P[1] * oy;
-      vy += P[2] * ox + P[3] * oy;
+      vx = fma(P[1], oy, fma(P[0], ox, vx));  // two dependent float64 steps, not three
+      vy = fma(P[3], oy, fma(P[2], ox, vy));
     }
   }
   int bad = 0;
   if (lane < kb) {
     const double *P = T + 4 * lane;  // M^(lane+1)
-    const double yn0 = P[0] * y0 + P[1] * y1 + vx;
-    const double yn1 = P[2] * y0 + P[3] * y1 + vy;
+    const double yn0 = fma(P[0], y0, fma(P[1], y1, vx));
+    const double yn1 = fma(P[2], y0, fma(P[3], y1, vy));
     const int64_t n = n0 + lane;
     const double ydd = qm * e4 - g0 * yn1 - w2 * yn0;
     const size_t sl = row + ((n + 1) & a.wm);
@@ -215,8 +220,9 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
     if (MIXED)
       // the float32 mirror scaled in float32 (one rounding more than scaling in float64: below the
       // mirror's own rounding budget), the values converted on the integer units
-      a.H32[sl] = make_float4(dbl2flt(yn0) * dbl2flt(T[kTabC + 4]), dbl2flt(yn1) * dbl2flt(T[kTabC + 5]),
-                              dbl2flt(ydd) * dbl2flt(T[kTabC + 6]), 0.f);
+      a.H32[sl] = make_float4(dbl2flt(yn0) * (fsc ? fsc[0] : dbl2flt(T[kTabC + 4])),
+                              dbl2flt(yn1) * (fsc ? fsc[1] : dbl2flt(T[kTabC + 5])),
+                              dbl2flt(ydd) * (fsc ? fsc[2] : dbl2flt(T[kTabC + 6])), 0.f);
     const size_t o = bi * So + (size_t)(n + 1 - a.n_begin);
     if (a.od) a.od[o] = yn0;
     if (a.odd) a.odd[o] = yn1;
@@ -230,6 +236,10 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
       if (a.kdd) a.kdd[kk] = yn1;
     }
     bad = fabs(yn1) > T[kTabC + 10];
+    if (ys && lane == kb - 1) {
+      ys[0] = yn0;
+      ys[1] = yn1;
+    }
   }
   if (__any_sync(0xffffffffu, bad)) {
     if (lane == 0) set_status(a.status, PC_ERR_VELOCITY);
@@ -467,7 +477,7 @@ __device__ __forceinline__ void drive_sources_grid(const RunArgs &a, int b, int 
 // persistent kernel a lane has one or two, and the group loop only raises its registers).
 template <bool MIXED, bool NEAR = false, bool RING = true, bool GROUPS = false>
 __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err,
-                            int j_lo, int j_hi, double *dst, int sgsel = -1) {
+                            int j_lo, int j_hi, double *dst_row, int sgsel = -1) {
   const int lane = threadIdx.x & 31;
   const int nst = ns > 0 ? ns : 1;
   const int slots = 32 / nst;
@@ -535,7 +545,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
     if (lane < nst) {
       float t = 0.f;
       for (int mm = 0; mm < slots; ++mm) t += shf[mm * nst + lane];
-      dst[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = (double)t * a.e_unit;
+      dst_row[ns > 0 ? 1 + lane : 0] = (double)t * a.e_unit;
     }
   } else {
     double mine = MIXED ? (double)accf * a.e_unit + accd : accd;
@@ -544,40 +554,62 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
     if (lane < nst) {
       double t = 0.0;
       for (int mm = 0; mm < slots; ++mm) t += sh[mm * nst + lane];
-      dst[bidx(a, b, i) * (2 * kMaxBlock + 1) + (ns > 0 ? 1 + lane : 0)] = t;
+      dst_row[ns > 0 ? 1 + lane : 0] = t;
     }
   }
   __syncwarp();
 }
 
 // NEAR: the mixed drive sums its near sources in float64 (near_f64 > 0), a separate instantiation
-// so that the float32 source loop of the default one keeps its registers
+// so that the float32 source loop of the default one keeps its registers.  At most two CTAs share
+// an SM here (one per configuration), so the register bound is one CTA's: held to the 80 of the
+// compiler's default choice the time loop spilled and ran 7 % slower.
 template <bool MIXED, bool NEAR = false, bool RING = true>
-__global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a) {
+__global__ void __launch_bounds__(kRunWarps * 32, 1) lo_run_kernel(const RunArgs a) {
   const int b = blockIdx.x;
   const int N = a.N;
   const int64_t So = a.n_steps - a.n_begin + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double sh[kRunWarps][32];
+  // the stage fields of the block and each receiver's state (d, d') at the block's start stay in
+  // shared memory (the phases hand them over within the CTA, not through global memory); the
+  // float64 drive's second-charge partial fields (2 N <= kRunWarps) beside them
+  __shared__ double s_Es[kSmallN][2 * kMaxBlock + 1];
+  __shared__ double s_ys[kSmallN][2];
+  __shared__ double s_Ep[kRunWarps / 2][2 * kMaxBlock + 1];
+  __shared__ float s_fsc[kSmallN][3];
+  extern __shared__ double s_tab[];  // [N][kTab]: the configuration's RK4 tables (dynamic)
   __shared__ int s_stop, s_K;
   if (threadIdx.x == 0) {
     s_K = a.kblock[b];
     s_stop = 0;
   }
+  {
+    const double *gT = a.rk4tab + bidx(a, b, 0) * kTab;  // the configuration's rows are contiguous
+    for (int t = threadIdx.x; t < N * kTab; t += blockDim.x) s_tab[t] = gT[t];
+    for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) s_fsc[t / 3][t % 3] = dbl2flt(gT[(t / 3) * kTab + kTabC + 4 + t % 3]);
+  }
   // (the first sample and, when resuming, the earlier ones are in the store: lo_first_kernel)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const size_t sl = bidx(a, b, i) * (size_t)a.hs + (a.n_begin & a.wm);
+    s_ys[i][0] = a.d[sl];
+    s_ys[i][1] = a.dd[sl];
+    if (a.state_in) s_Es[i][0] = a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)];
+  }
   __syncthreads();
   const int K = s_K;
   // ---- E_d at the first step: the resumed state's, or that of the static configuration ----
   for (int i = warp; i < N; i += kRunWarps) {
     if (!a.state_in) {
       int err = 0;
-      drive_phase<MIXED, NEAR, RING>(a, b, i, a.n_begin, 0, sh[warp], &err, 0, N, a.Es);
+      drive_phase<MIXED, NEAR, RING>(a, b, i, a.n_begin, 0, sh[warp], &err, 0, N, s_Es[i]);
       if (err) {
         set_status(a.status, err);
         s_stop = 1;
       }
     }
-    if (lane == 0 && a.Ed) a.Ed[bidx(a, b, i) * So] = a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)];
+    __syncwarp();
+    if (lane == 0 && a.Ed) a.Ed[bidx(a, b, i) * So] = s_Es[i][0];
   }
   __syncthreads();
   for (int64_t n0 = a.n_begin; n0 < a.n_steps; n0 += K) {
@@ -592,7 +624,8 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     for (int w = warp; w < (xsplit ? 2 * N : N); w += kRunWarps) {
       int err = 0;
       drive_phase<MIXED, NEAR, RING>(a, b, xsplit ? w >> 1 : w, n0, nst, sh[warp], &err, 0, N,
-                               (xsplit && (w & 1)) ? a.Epart : a.Es, xsplit ? w & 1 : -1);
+                                     (xsplit && (w & 1)) ? s_Ep[w >> 1] : s_Es[xsplit ? w >> 1 : w],
+                                     xsplit ? w & 1 : -1);
       if (err) {
         set_status(a.status, err);
         s_stop = 1;
@@ -601,20 +634,19 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_run_kernel(const RunArgs a)
     __syncthreads();
     if (s_stop) break;
     if (xsplit) {
-      for (int t = threadIdx.x; t < N * nst; t += blockDim.x) {
-        const size_t o = bidx(a, b, t / nst) * (2 * kMaxBlock + 1) + 1 + t % nst;
-        a.Es[o] += a.Epart[o];
-      }
+      for (int t = threadIdx.x; t < N * nst; t += blockDim.x) s_Es[t / nst][1 + t % nst] += s_Ep[t / nst][1 + t % nst];
       __syncthreads();
     }
     // phase B: the kb RK4 steps of each receiver, one warp per receiver, one lane per step
     for (int i = warp; i < N; i += kRunWarps) {
       int stop = 0;
-      rk4_block_warp<MIXED>(a, b, i, n0, kb, &stop);
+      rk4_block_warp<MIXED>(a, b, i, n0, kb, &stop, s_Es[i], s_ys[i], s_tab + (size_t)i * kTab, s_fsc[i]);
       if (stop && lane == 0) s_stop = 1;
     }
     __syncthreads();
   }
+  // E_d at the last step for a state saved after the run (lo_save_kernel)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a.Es[bidx(a, b, i) * (2 * kMaxBlock + 1)] = s_Es[i][0];
 }
 
 // The first sample of the call (step n_begin) into the store and the outputs: at rest with moment d0
@@ -852,7 +884,8 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs 
   const int j_lo = min(a.N, z * chunk), j_hi = min(a.N, j_lo + chunk);
   double *dst = a.nsplit > 1 ? a.Epart + (size_t)z * a.B * a.N * (2 * kMaxBlock + 1) : a.Es;
   int err = 0;
-  drive_phase<MIXED, NEAR, RING, true>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi, dst);
+  drive_phase<MIXED, NEAR, RING, true>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi,
+                                       dst + bidx(a, b, i) * (2 * kMaxBlock + 1));
   if (err) set_status(a.status, err);
 }
 
@@ -892,7 +925,7 @@ __global__ void lo_rk4_kernel(const RunArgs a, int64_t n0, int kb) {
   if (a.nsplit > 1 && lane < 2 * kb) sum_slices(a, bi, 1 + lane, 1 + lane);
   __syncwarp();
   int stop = 0;
-  rk4_block_warp<MIXED>(a, (int)(bi / a.N), (int)(bi % a.N), n0, kb, &stop);
+  rk4_block_warp<MIXED>(a, (int)(bi / a.N), (int)(bi % a.N), n0, kb, &stop, a.Es + bi * (2 * kMaxBlock + 1));
 }
 
 // Advances the device cursor by one block and sets the loop condition of the graph.
@@ -1454,10 +1487,15 @@ static void *run_kernel_for(const RunArgs &a, bool mixed) {
     return ring ? (void *)lo_run_kernel<true, true, true> : (void *)lo_run_kernel<true, true, false>;
   return ring ? (void *)lo_run_kernel<true, false, true> : (void *)lo_run_kernel<true, false, false>;
 }
-static cudaError_t launch_run_args(void *fn, dim3 grid, dim3 block, const RunArgs &a, cudaStream_t st) {
+static cudaError_t launch_run_args(void *fn, dim3 grid, dim3 block, const RunArgs &a, cudaStream_t st,
+                                   size_t smem = 0) {
   RunArgs aa = a;
   void *args[] = {&aa};
-  return cudaLaunchKernel(fn, grid, block, args, 0, st);
+  if (smem > 0) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaLaunchKernel(fn, grid, block, args, smem, st);
 }
 static cudaError_t launch_drive(void *fn, dim3 grid, const RunArgs &a, int64_t n0, int ns, cudaStream_t st) {
   RunArgs aa = a;
@@ -1752,8 +1790,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   if (dp->N <= pc::kSmallN) {
     // small configurations: one persistent CTA each, the time loop inside
     if (timed) cudaEventRecord(ctx->tev[0], st);
-    if (pc::launch_run_args(pc::run_kernel_for(a, mixed), dim3(dp->B), dim3(pc::kRunWarps * 32), a, st) !=
-        cudaSuccess)
+    // (dynamic shared memory: the configuration's RK4 tables, N x kTab doubles, 41 KB at N = 64)
+    if (pc::launch_run_args(pc::run_kernel_for(a, mixed), dim3(dp->B), dim3(pc::kRunWarps * 32), a, st,
+                            (size_t)dp->N * pc::kTab * sizeof(double)) != cudaSuccess)
       return PC_ERR_CUDA;
     if (timed) {
       cudaEventRecord(ctx->tev[1], st);
