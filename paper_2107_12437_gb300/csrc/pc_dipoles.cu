@@ -250,11 +250,96 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
   __syncwarp();
 }
 
+// pair_drive_f64 for fixed origins in scalar form.  Every vector of the pair lies in the plane of
+// rho = R_i - R_j and the source's unit axis p_j: a charge sits at R_j + s p_j (s = w d), moves
+// with v = s' p_j and accelerates with s'' p_j, so the quadratic of the retarded time on a segment
+// and the Lienard-Wiechert field projected on p_i need only |rho|^2, rho.p_j, rho.p_i and p_j.p_i.
+// The same steps as solve_f64 (the root on the segment of the centre's retarded time, other
+// segments searched the same way) and lw_E_f64 (Griffiths' E with u = c n - v), on the same
+// samples, with a third fewer float64 instructions: the float64 unit, one per SM on this GPU, sets
+// the pace of this path.  Returns false, leaving *out, where the general form must decide (the
+// static pre-history, the end of the history, no root).
+__device__ bool pair_drive_f64_scalar(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int64_t kg,
+                                      int sg0, int sg1, double *out) {
+  const double cdt = kC * a.dt, cdt2 = cdt * cdt;
+  const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+  const double *Ri = a.origin + 3 * bi, *Rj = a.origin + 3 * bj;
+  const double *pi = a.axis + 3 * bi, *pj = a.axis + 3 * bj;
+  const double rho[3] = {Ri[0] - Rj[0], Ri[1] - Rj[1], Ri[2] - Rj[2]};
+  const double rr = dot3(rho, rho), ra = dot3(rho, pj), rp = dot3(rho, pi), ap = dot3(pj, pi);
+  const double *Tj = a.rk4tab + bj * kTab;
+  const double q = a.q[bj];
+  const double *dh = a.d + bj * a.hs, *ddh = a.dd + bj * a.hs, *dddh = a.ddd + bj * a.hs;
+  const int64_t wm = a.wm;
+  const double c = kC;
+  double acc = 0.0;
+  for (int sg = sg0; sg < sg1; ++sg) {
+    const double w = Tj[kTabC + 8 + sg];
+    int64_t k = kg < 0 ? 0 : kg;
+    if (k > nv - 1) k = nv - 1;
+    double th = 0.0, s0 = 0.0, ds = 0.0;
+    bool found = false;
+    for (int it = 0; it < 96 && !found; ++it) {
+      s0 = w * dh[k & wm];
+      ds = w * dh[(k + 1) & wm] - s0;
+      const double T = u - (double)k;
+      const double A = cdt2 - ds * ds;
+      const double B = ds * (ra - s0) - cdt2 * T;
+      const double C = cdt2 * T * T - (rr - s0 * (2.0 * ra - s0));
+      const double sq = sqrt(fmax(B * B - A * C, 0.0));
+      double t;
+      if (B <= 0.0) {
+        const double den = -B + sq;
+        t = (den > 0.0) ? C / den : T;
+      } else {
+        t = (-B - sq) / A;
+      }
+      if (!(t == t)) return false;
+      if (t >= -1e-12 && t <= 1.0 + 1e-12) {
+        th = fmin(fmax(t, 0.0), 1.0);
+        found = true;
+      } else if (t < 0.0) {
+        if (k == 0) return false;  // before the first sample: the general form decides
+        const double st = floor(t);
+        k += (st < -1e15) ? -k : (int64_t)st;
+        if (k < 0) k = 0;
+      } else {
+        if (k == nv - 1) return false;
+        const double st = floor(t);
+        k += (st > 1e15) ? nv : (int64_t)st;
+        if (k > nv - 1) k = nv - 1;
+      }
+    }
+    if (!found || (k == 0 && th == 0.0)) return false;
+    const double sv0 = w * ddh[k & wm], sa0 = w * dddh[k & wm];
+    const double s = s0 + th * ds;
+    const double sv = sv0 + th * (w * ddh[(k + 1) & wm] - sv0);
+    const double sa = sa0 + th * (w * dddh[(k + 1) & wm] - sa0);
+    // a = rho - s p_j: a.a, a.p_j, a.p_i
+    const double aj = ra - s, aiv = rp - s * ap;
+    const double R2 = rr - s * (2.0 * ra - s);
+    const double iR = rsqrt(R2);
+    const double R = R2 * iR;
+    const double Ru = c * R - sv * aj;  // R c - a . v
+    const double iRu = 1.0 / Ru;
+    const double f = kKe * (sg == 0 ? q : -q) * R * iRu * iRu * iRu;
+    const double g = f * (c * c - sv * sv);
+    const double pu = c * iR * aiv - sv * ap;  // p_i . u
+    acc += g * pu + f * (pu * (sa * aj) - sa * ap * Ru);
+  }
+  *out = acc;
+  return true;
+}
+
 // Contribution of dipole j to the driving field of receiver i at time u (steps), history 0..nv.
 // float64: charge by charge (Eqs. r_1, r_2, E), charges sg0 .. sg1 - 1 (0 = +q, 1 = -q); returns
 // p_i . E.
 __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int64_t kg_fixed,
                                  int *err, int sg0 = 0, int sg1 = 2) {
+  if (!a.org_pos && nv > 0) {
+    double v;
+    if (pair_drive_f64_scalar(a, b, i, j, u, nv, kg_fixed, sg0, sg1, &v)) return v;
+  }
   const double cdt = kC * a.dt;
   const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
   // receiver at its origin; a moving origin at the stage time (half-step index 2u; moving runs start
