@@ -259,6 +259,55 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
 // samples, with a third fewer float64 instructions: the float64 unit, one per SM on this GPU, sets
 // the pace of this path.  Returns false, leaving *out, where the general form must decide (the
 // static pre-history, the end of the history, no root).
+// The retarded sample of a charge at offset s = w d along its axis, fixed origins, in scalar form
+// (rr = |rho|^2, ra = rho.p_j): the root th on segment k of the quadratic of solve_f64, starting from
+// segment kg, with s0 = w d_k and ds = w d_(k+1) - s0.  False where the general form must decide
+// (before the first sample, past the last, no root).
+__device__ __forceinline__ bool scalar_root(const double *dh, int64_t wm, double w, double rr, double ra, double u,
+                                            double cdt2, int64_t nv, int64_t kg, int64_t *k_out, double *th_out,
+                                            double *s0_out, double *ds_out) {
+  int64_t k = kg < 0 ? 0 : kg;
+  if (k > nv - 1) k = nv - 1;
+  for (int it = 0; it < 96; ++it) {
+    const double s0 = w * dh[k & wm];
+    const double ds = w * dh[(k + 1) & wm] - s0;
+    const double T = u - (double)k;
+    const double A = cdt2 - ds * ds;
+    const double B = ds * (ra - s0) - cdt2 * T;
+    const double C = cdt2 * T * T - (rr - s0 * (2.0 * ra - s0));
+    const double sq = sqrt(fmax(B * B - A * C, 0.0));
+    double t;
+    if (B <= 0.0) {
+      const double den = -B + sq;
+      t = (den > 0.0) ? C / den : T;
+    } else {
+      t = (-B - sq) / A;
+    }
+    if (!(t == t)) return false;
+    if (t >= -1e-12 && t <= 1.0 + 1e-12) {
+      const double th = fmin(fmax(t, 0.0), 1.0);
+      if (k == 0 && th == 0.0) return false;  // exactly at the first sample: the general form
+      *k_out = k;
+      *th_out = th;
+      *s0_out = s0;
+      *ds_out = ds;
+      return true;
+    }
+    if (t < 0.0) {
+      if (k == 0) return false;  // before the first sample
+      const double st = floor(t);
+      k += (st < -1e15) ? -k : (int64_t)st;
+      if (k < 0) k = 0;
+    } else {
+      if (k == nv - 1) return false;
+      const double st = floor(t);
+      k += (st > 1e15) ? nv : (int64_t)st;
+      if (k > nv - 1) k = nv - 1;
+    }
+  }
+  return false;
+}
+
 __device__ bool pair_drive_f64_scalar(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int64_t kg,
                                       int sg0, int sg1, double *out) {
   const double cdt = kC * a.dt, cdt2 = cdt * cdt;
@@ -275,42 +324,9 @@ __device__ bool pair_drive_f64_scalar(const RunArgs &a, int b, int i, int j, dou
   double acc = 0.0;
   for (int sg = sg0; sg < sg1; ++sg) {
     const double w = Tj[kTabC + 8 + sg];
-    int64_t k = kg < 0 ? 0 : kg;
-    if (k > nv - 1) k = nv - 1;
-    double th = 0.0, s0 = 0.0, ds = 0.0;
-    bool found = false;
-    for (int it = 0; it < 96 && !found; ++it) {
-      s0 = w * dh[k & wm];
-      ds = w * dh[(k + 1) & wm] - s0;
-      const double T = u - (double)k;
-      const double A = cdt2 - ds * ds;
-      const double B = ds * (ra - s0) - cdt2 * T;
-      const double C = cdt2 * T * T - (rr - s0 * (2.0 * ra - s0));
-      const double sq = sqrt(fmax(B * B - A * C, 0.0));
-      double t;
-      if (B <= 0.0) {
-        const double den = -B + sq;
-        t = (den > 0.0) ? C / den : T;
-      } else {
-        t = (-B - sq) / A;
-      }
-      if (!(t == t)) return false;
-      if (t >= -1e-12 && t <= 1.0 + 1e-12) {
-        th = fmin(fmax(t, 0.0), 1.0);
-        found = true;
-      } else if (t < 0.0) {
-        if (k == 0) return false;  // before the first sample: the general form decides
-        const double st = floor(t);
-        k += (st < -1e15) ? -k : (int64_t)st;
-        if (k < 0) k = 0;
-      } else {
-        if (k == nv - 1) return false;
-        const double st = floor(t);
-        k += (st > 1e15) ? nv : (int64_t)st;
-        if (k > nv - 1) k = nv - 1;
-      }
-    }
-    if (!found || (k == 0 && th == 0.0)) return false;
+    int64_t k;
+    double th, s0, ds;
+    if (!scalar_root(dh, wm, w, rr, ra, u, cdt2, nv, kg, &k, &th, &s0, &ds)) return false;
     const double sv0 = w * ddh[k & wm], sa0 = w * dddh[k & wm];
     const double s = s0 + th * ds;
     const double sv = sv0 + th * (w * ddh[(k + 1) & wm] - sv0);
@@ -2309,10 +2325,82 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
     kg = nv - dl.x + Num<float>::floor_int((float)(u - (double)nv) - __int_as_float(dl.y));
   }
   const double Eb[3] = {eb * pi[0], eb * pi[1], eb * pi[2]};
+  // fixed origins: the pair's scalars (rho = R_i - R_j; |p_j| = 1) for the scalar form below
+  double rho[3] = {0.0, 0.0, 0.0}, rr = 0.0, ra = 0.0, rp = 0.0, apj = 0.0;
+  if (!mov) {
+    for (int c = 0; c < 3; ++c) rho[c] = Ri[c] - tr.R[c];
+    rr = dot3(rho, rho);
+    ra = dot3(rho, pj);
+    rp = dot3(rho, pi);
+    apj = dot3(pj, pi);
+  }
   for (int sg = 0; sg < 2; ++sg) {
     const double w = A.wts[2 * bj + sg];
     tr.w = w;
     const double qc = sg == 0 ? q : -q;
+    if (!mov && nv > 0) {
+      // scalar form (the reverse of pair_drive_f64_scalar): F = p_i . E depends on the charge only
+      // through R = |a|, a.p_j, a.p_i (a = rho - s p_j) and s', s''; the adjoint of a is assembled
+      // from theirs, the history adjoints take those of s, s', s'' and of the retarded time
+      int64_t k;
+      double th, s0, ds;
+      if (scalar_root(tr.d, a.wm, w, rr, ra, u, cdt * cdt, nv, kg, &k, &th, &s0, &ds)) {
+        const int64_t k0 = k & a.wm, k1 = (k + 1) & a.wm;
+        const double Dd = tr.d[k1] - tr.d[k0], Dv = tr.dd[k1] - tr.dd[k0], Da = tr.ddd[k1] - tr.ddd[k0];
+        const double sv0 = w * tr.dd[k0], sa0 = w * tr.ddd[k0];
+        const double sp = s0 + th * ds;
+        const double sv = sv0 + th * (w * tr.dd[k1] - sv0);
+        const double sa = sa0 + th * (w * tr.ddd[k1] - sa0);
+        const double c = kC;
+        const double aj = ra - sp, ai = rp - sp * apj;
+        const double R2 = rr - sp * (2.0 * ra - sp);
+        const double iR = rsqrt(R2), R = R2 * iR;
+        const double Ru = c * R - sv * aj;
+        const double iRu = 1.0 / Ru;
+        const double f = kKe * qc * R * iRu * iRu * iRu;
+        const double pu = c * ai * iR - sv * apj;
+        const double Wf = c * c - sv * sv + sa * aj;
+        // reverse of F = f (Wf pu - Ru sa p_i.p_j)
+        const double fb = eb * (Wf * pu - Ru * sa * apj);
+        const double Wb = eb * f * pu, pub = eb * f * Wf;
+        double Rub = -eb * f * sa * apj;
+        const double sab = -eb * f * Ru * apj + aj * Wb;
+        double svb = -2.0 * sv * Wb - pub * apj;
+        double ajb = sa * Wb;
+        const double aib = pub * c * iR;
+        double Rb = -pub * c * ai * iR * iR + fb * f * iR;
+        Rub += -3.0 * fb * f * iRu;
+        Rb += c * Rub;
+        svb += -Rub * aj;
+        ajb += -Rub * sv;
+        double av[3];
+        for (int cc = 0; cc < 3; ++cc) {
+          av[cc] = rho[cc] - sp * pj[cc];
+          const double abc = Rb * iR * av[cc] + ajb * pj[cc] + aib * pi[cc];
+          Rib[cc] += abc;
+          Rjb[cc] -= abc;
+        }
+        const double pb_p = -(Rb * iR * aj + ajb + aib * apj);  // -ab . p_j
+        if (k < wlo || k + 1 >= wlo + W) return PC_ERR_NOCONV;
+        const double Db = w * pb_p, Vb = w * svb, Ab = w * sab;
+        const double thb = Db * Dd + Vb * Dv + Ab * Da;
+        const double Gth = -2.0 * cdt * cdt * (u - (double)k - th) + 2.0 * w * Dd * aj;
+        const double sfac = -thb / Gth;
+        for (int cc = 0; cc < 3; ++cc) {
+          Rib[cc] += sfac * (-2.0 * av[cc]);
+          Rjb[cc] += sfac * (2.0 * av[cc]);
+        }
+        const double dbar = Db + sfac * 2.0 * aj * w;
+        double *w0p = win + 3 * (k - wlo), *w1p = w0p + 3;
+        atomicAdd(&w0p[0], (1.0 - th) * dbar);
+        atomicAdd(&w0p[1], (1.0 - th) * Vb);
+        atomicAdd(&w0p[2], (1.0 - th) * Ab);
+        atomicAdd(&w1p[0], th * dbar);
+        atomicAdd(&w1p[1], th * Vb);
+        atomicAdd(&w1p[2], th * Ab);
+        continue;
+      }
+    }
     int64_t k = -1;
     double th = 0.0;
     bool stat = true;
@@ -2423,7 +2511,7 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
 // samples the block's retarded times reach lie in [n0 + 1/2 - tau_max - margin,
 // n0 + ns/2 - tau_min + margin]; their adjoints are gathered in a shared-memory window.
 template <bool MOV>
-__global__ void __launch_bounds__(128) adj_field_kernel(const AdjArgs A, int64_t n0, int ns, int wmax) {
+__global__ void __launch_bounds__(128, 4) adj_field_kernel(const AdjArgs A, int64_t n0, int ns, int wmax) {
   extern __shared__ double win[];  // [wmax][3]
   __shared__ double s_rj[3][128];
   const RunArgs &a = A.f;
