@@ -352,7 +352,9 @@ __device__ bool pair_drive_f64_scalar(const RunArgs &a, int b, int i, int j, dou
 // p_i . E.
 __device__ double pair_drive_f64(const RunArgs &a, int b, int i, int j, double u, int64_t nv, int64_t kg_fixed,
                                  int *err, int sg0 = 0, int sg1 = 2) {
-  if (!a.org_pos && nv > 0) {
+  // (a centre whose retarded sample precedes the history: its charges are in the static
+  // pre-history, which the general form takes directly)
+  if (!a.org_pos && nv > 0 && kg_fixed >= 0) {
     double v;
     if (pair_drive_f64_scalar(a, b, i, j, u, nv, kg_fixed, sg0, sg1, &v)) return v;
   }
@@ -2338,7 +2340,7 @@ __device__ int pair_rev_f64(const AdjArgs &A, int b, int i, int j, double u, int
     const double w = A.wts[2 * bj + sg];
     tr.w = w;
     const double qc = sg == 0 ? q : -q;
-    if (!mov && nv > 0) {
+    if (!mov && nv > 0 && kg >= 0) {
       // scalar form (the reverse of pair_drive_f64_scalar): F = p_i . E depends on the charge only
       // through R = |a|, a.p_j, a.p_i (a = rho - s p_j) and s', s''; the adjoint of a is assembled
       // from theirs, the history adjoints take those of s, s', s'' and of the retarded time
