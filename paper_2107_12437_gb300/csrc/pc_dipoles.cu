@@ -179,7 +179,10 @@ __device__ void rk4_table(const RunArgs &a, size_t bi) {
 // memory from the previous block, which the block's last lane updates; Tsh / fsc: null, or the
 // receiver's table row and the float32 mirror's three scales held in shared memory (the persistent
 // kernel: the chain of a block then waits on no global load of constants).
-template <bool MIXED>
+// HWCVT: the float32 mirror converted by the hardware conversion (round to nearest even) instead
+// of dbl2flt: on the persistent path a block's chain waits on these conversions, while the grid
+// path keeps the float64 unit for its drive
+template <bool MIXED, bool HWCVT = false>
 __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int kb, int *stop, double *Es,
                                double *ys = nullptr, const double *Tsh = nullptr, const float *fsc = nullptr) {
   const int lane = threadIdx.x & 31;
@@ -220,9 +223,11 @@ __device__ void rk4_block_warp(const RunArgs &a, int b, int i, int64_t n0, int k
     if (MIXED)
       // the float32 mirror scaled in float32 (one rounding more than scaling in float64: below the
       // mirror's own rounding budget), the values converted on the integer units
-      a.H32[sl] = make_float4(dbl2flt(yn0) * (fsc ? fsc[0] : dbl2flt(T[kTabC + 4])),
-                              dbl2flt(yn1) * (fsc ? fsc[1] : dbl2flt(T[kTabC + 5])),
-                              dbl2flt(ydd) * (fsc ? fsc[2] : dbl2flt(T[kTabC + 6])), 0.f);
+      a.H32[sl] = HWCVT ? make_float4(__double2float_rn(yn0) * fsc[0], __double2float_rn(yn1) * fsc[1],
+                                      __double2float_rn(ydd) * fsc[2], 0.f)
+                        : make_float4(dbl2flt(yn0) * (fsc ? fsc[0] : dbl2flt(T[kTabC + 4])),
+                                      dbl2flt(yn1) * (fsc ? fsc[1] : dbl2flt(T[kTabC + 5])),
+                                      dbl2flt(ydd) * (fsc ? fsc[2] : dbl2flt(T[kTabC + 6])), 0.f);
     const size_t o = bi * So + (size_t)(n + 1 - a.n_begin);
     if (a.od) a.od[o] = yn0;
     if (a.odd) a.odd[o] = yn1;
@@ -743,7 +748,7 @@ __global__ void __launch_bounds__(kRunWarps * 32, 1) lo_run_kernel(const RunArgs
     // phase B: the kb RK4 steps of each receiver, one warp per receiver, one lane per step
     for (int i = warp; i < N; i += kRunWarps) {
       int stop = 0;
-      rk4_block_warp<MIXED>(a, b, i, n0, kb, &stop, s_Es[i], s_ys[i], s_tab + (size_t)i * kTab, s_fsc[i]);
+      rk4_block_warp<MIXED, true>(a, b, i, n0, kb, &stop, s_Es[i], s_ys[i], s_tab + (size_t)i * kTab, s_fsc[i]);
       if (stop && lane == 0) s_stop = 1;
     }
     __syncthreads();
