@@ -20,6 +20,13 @@ pc_status end_call(pc_ctx *ctx, cudaStream_t s) {
   return (pc_status)(*ctx->h_status);
 }
 
+__global__ void check_axes_kernel(const double *axis, int64_t n, int *status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = axis[3 * i], y = axis[3 * i + 1], z = axis[3 * i + 2];
+  if (!(fabs(x * x + y * y + z * z - 1.0) <= kAxisTol)) set_status(status, PC_ERR_ARG);
+}
+
 }  // namespace pc
 
 extern "C" pc_status pc_ctx_create(pc_ctx **out, int device) {

@@ -851,6 +851,10 @@ __global__ void lo_tables_kernel(const RunArgs a) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const size_t bi = bidx(a, b, i);
     float *f = a.dipf + bi * kDipF;
+    {
+      const double *ax = a.axis + 3 * bi;
+      if (!(fabs(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2] - 1.0) <= kAxisTol)) set_status(a.status, PC_ERR_ARG);
+    }
     for (int c = 0; c < 3; ++c) {
       const double x = a.origin[3 * bi + c] / L;
       const float hi = (float)x;
@@ -1816,11 +1820,15 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     pc::lo_pairs_kernel<<<dim3(gx, gy), 256, 0, st>>>(a);
   }
   pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
-  // block lengths and reaches back on the host
-  std::vector<int> kr(2 * (size_t)dp->B);
-  if (cudaMemcpyAsync(kr.data(), a.kblock, kr.size() * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  // block lengths and reaches back on the host, and the status of the tables (unit axes)
+  std::vector<int> kr(2 * (size_t)dp->B + 1);
+  if (cudaMemcpyAsync(kr.data(), a.kblock, 2 * (size_t)dp->B * sizeof(int), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(kr.data() + 2 * (size_t)dp->B, a.status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return PC_ERR_CUDA;
+  if (kr[2 * (size_t)dp->B] == PC_ERR_ARG) return PC_ERR_ARG;
   int K = pc::kMaxBlock;
   int64_t D = 1;
   for (int b = 0; b < dp->B; ++b) {

@@ -1272,6 +1272,7 @@ static pc_status fields_impl(pc_ctx *ctx, const pc_charges *ch, const pc_dipole_
   L.out.mask = out->mask;
   L.r_excl = r_excl;
   L.status = ctx->d_status;
+  if (has_dp) check_axes_kernel<<<(unsigned)((dp->N + 255) / 256), 256, 0, st>>>(dp->axis, dp->N, L.status);
   L.tile_shift = ctx->tile_shift;
 
   L.iLd = has_dp ? 1.0 / (kC * s.dtd) : 0.0;  // 1/(c dt): first guesses without a division
@@ -1552,6 +1553,7 @@ extern "C" pc_status pc_fields_noalloc(const pc_charges *ch, const pc_dipole_sou
   L.out.mask = out->mask;
   L.r_excl = r_excl;
   L.status = status;
+  if (has_dp) check_axes_kernel<<<(unsigned)((dp->N + 255) / 256), 256, 0, st>>>(dp->axis, dp->N, status);
   L.Hd = Hd;
   L.Hc = Hc;
   L.cref = cref;

@@ -87,4 +87,9 @@ pc_status begin_call(pc_ctx *ctx, cudaStream_t s);
 // Read the status word back (synchronises the stream) and merge a launch error.
 pc_status end_call(pc_ctx *ctx, cudaStream_t s);
 
+// Dipole axes are unit vectors (a dipole's charges move along its axis; the pair algebra of both
+// paths uses p . p = 1): an axis whose squared norm is more than kAxisTol from 1 sets PC_ERR_ARG.
+constexpr double kAxisTol = 1e-10;
+__global__ void check_axes_kernel(const double *axis, int64_t n, int *status);
+
 }  // namespace pc
