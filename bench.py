@@ -7,8 +7,9 @@ pair algebra), i.e. 16 * 2048^2 * 128 = 8.59e9 retarded Lienard-Wiechert pair ev
 
 Also reported on the same line: the plain float64 GPU path on a bounded sample of the same
 workload, the batched two-oscillator run (256 separations x 40 000 RK4 steps + fit) in
-dipole-steps/s, the end-to-end number through the C ABI with host buffers, the roofline of the
-field kernel, clocks sampled during the timed region and the FP64 CPU oracle on a bounded sample.
+dipole-steps/s, the end-to-end number through the C ABI with host buffers, the rooflines of the
+field kernel and of the cloud's drive kernel, clocks sampled during the timed region and the FP64
+CPU oracle on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --profile fields_mixed_small|fields_mixed2_small|fields_f64_small|lo_small|lo_f64_small|
@@ -478,8 +479,10 @@ def main():
             cfg = W.cfg4(n_steps=200) if args.profile == "ring_small" else W.cfg5(n_steps=64)
             pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=pc.PC_MIXED)
         else:
-            # adjoint of the ring's float64 run over 200 steps
-            cfg = W.cfg4(n_steps=200)
+            # adjoint of the ring's float64 run over 2000 steps (past the ring's largest delay, 1 334
+            # samples, so that the last blocks, reversed first, see no source in its static
+            # pre-history)
+            cfg = W.cfg4(n_steps=2000)
             w = torch.ones((1, cfg.N), dtype=torch.float64, device=dev)
             pc.pc_dipoles_adjoint(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, w)
         torch.cuda.synchronize()
