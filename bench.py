@@ -599,7 +599,9 @@ def main():
                    "tile": f"{tile_rows} x {tile_cols} points, {tile_rows * tile_cols // 256} per thread, "
                            f"{tile_stage} sources per shared-memory stage (autotuned)",
                    "l2": "flushed between steps (256 MB write); outputs 2.7 GB > L2"},
-        "gpu_launches": 2 * args.steps,
+        # per step: the dipole-axis check, the float32 mirror of the histories, the field kernel
+        # (all 16 frames in one launch)
+        "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": "LW pair evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "host_cpus": f"{len(cpus_gpu)} GPU-local" if cpus_gpu else "unbound"},
