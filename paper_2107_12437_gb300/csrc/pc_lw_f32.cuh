@@ -322,7 +322,9 @@ __device__ __forceinline__ void dipole_pair_fast(float2 rxy, float rz, float rn,
   const float2 s = __fmul2_rn(mu2, X);   // (s1, s0): charge offsets along the axis
   const float2 v = __fmul2_rn(mu2, V);   // (v1, v0)
   const float2 al = __fmul2_rn(mu2, Ac);  // (a1, a0)
-  const float ds = mup * X.x + mum * X.y, dv = mup * V.x + mum * V.y, da = mup * Ac.x + mum * Ac.y;
+  // the separations of the two charges' offsets, velocities and accelerations: differences of the
+  // products above (mup X.x - (-mum X.y)), one add each
+  const float ds = s.x - s.y, dv = v.x - v.y, da = al.x - al.y;
   const float2 R = __fadd2_rn(f2(rn), dl);  // (R1, R0)
   const float dR = dl.x - dl.y;
   const float2 ap = __fadd2_rn(f2(rp), make_float2(-s.x, -s.y));  // (ap1, ap0)
