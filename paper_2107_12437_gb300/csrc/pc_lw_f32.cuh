@@ -333,9 +333,10 @@ __device__ __forceinline__ void dipole_pair_fast(float2 rxy, float rz, float rn,
   const float2 i = make_float2(__fdividef(1.f, Ru.x), __fdividef(1.f, Ru.y));  // (i1, i0)
   const float2 i2 = __fmul2_rn(i, i);
   const float2 i3 = __fmul2_rn(i2, i);
-  const float di = -dRu * i.y * i.x;
+  const float ixy = i.x * i.y;  // formed once for di and di3
+  const float di = -dRu * ixy;
   const float di2 = di * (i.x + i.y);
-  const float di3 = di * (i2.x + i.x * i.y + i2.y);
+  const float di3 = di * (i2.x + ixy + i2.y);
   const float v0 = v.y, a0 = al.y, ap0 = ap.y, R0 = R.y;
   float G0 = 0.f, dG = 0.f;
   if (KIND != PC_RADIATION) {
@@ -349,11 +350,12 @@ __device__ __forceinline__ void dipole_pair_fast(float2 rxy, float rz, float rn,
   const float G1 = G0 + dG;
   const float2 Ca = __fmul2_rn(make_float2(G1, G0), i3);  // (Ca1, Ca0)
   const float dCa = dG * i3.x + G0 * di3;
-  const float P0 = R0 * v0 * G0;
+  const float vG0 = v0 * G0;  // formed once for P0 and dBc
+  const float P0 = R0 * vG0;
   const float dvG = dv * G1 + v0 * dG;
   const float dP = dR * v.x * G1 + R0 * dvG;
   float dCp = -(dP * i3.x + P0 * di3);
-  float dBc = -(dvG * i3.x + v0 * G0 * di3);
+  float dBc = -(dvG * i3.x + vG0 * di3);
   if (KIND != PC_COULOMB) {
     const float Q0 = a0 * R0, dQ = da * R.x + a0 * dR;
     dCp -= dQ * i2.x + Q0 * di2;
