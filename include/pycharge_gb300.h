@@ -377,7 +377,7 @@ pc_status pc_ke_fit(pc_ctx *ctx, const double *ke, int32_t K, int64_t S, double 
  *   16 * N * S_dipoles + 64 * N + 48 * M * S_charges + 24 * M  <=  16 MiB  (bytes),
  * otherwise the call returns PC_ERR_ARG without touching the device.
  * Set-up: the first call on a device resolves the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  A failed lookup
+ * with that device current.  A failed lookup
  * returns PC_ERR_CUDA and is retried by the next call.  The device used is the caller's current
  * device; `points` must be device memory of that device (PC_ERR_ARG otherwise).
  * Every call shares the one array and leaves its contents behind: each call clears the status word
