@@ -812,7 +812,14 @@ def main():
         ds["ring_moving_f64"] = {"value": cfg4m.N * cfg4m.n_steps / (ms * 1e-3), "unit": "dipole-steps/s", "ms": ms,
                                  "workload": "ring of 256 oscillators, origins oscillating along x "
                                              "(1e-10 m, 20 THz), 4000 RK4 steps, float64"}
-        del mot
+        ms = timed(lambda: pc.pc_dipoles_run_moving(ctx, lod4m, mot, cfg4m.dt, cfg4m.n_steps, precision=pc.PC_MIXED))
+        om = pc.pc_dipoles_run_moving(ctx, lod4m, mot, cfg4m.dt, cfg4m.n_steps, precision=pc.PC_MIXED)
+        of = pc.pc_dipoles_run_moving(ctx, lod4m, mot, cfg4m.dt, cfg4m.n_steps)
+        ds["ring_moving_mixed"] = {
+            "value": cfg4m.N * cfg4m.n_steps / (ms * 1e-3), "unit": "dipole-steps/s", "ms": ms,
+            "max_rel_d_vs_f64": float((om["d"] - of["d"]).abs().max() / of["d"].abs().max()),
+            "workload": "the same, mixed (sources whose retarded times precede sample 1 in float64)"}
+        del mot, om, of
         # population dynamics (App. A): one excited and one unexcited dipole, q = 20 e, 80 nm,
         # one beating period (2.1e6 steps of 10 as)
         cfgp = W.population_pair()

@@ -340,7 +340,7 @@ typedef struct {
 } pc_dipole_motion;
 
 /*
- * pc_dipoles_run_moving -- pc_dipoles_run with moving origins (Sec. 4.3), float64 only.
+ * pc_dipoles_run_moving -- pc_dipoles_run with moving origins (Sec. 4.3), PC_F64 or PC_MIXED.
  * The driving field of each RK4 stage is evaluated at the receiver's origin at that stage's time
  * (half-step samples 2n, 2n+1, 2n+2); each source charge sits at its origin plus its offset along
  * the axis, with the origin's whole-step samples (even h) joining the moment in the linearly
@@ -348,7 +348,15 @@ typedef struct {
  * t <= 0 the origins rest at their first sample.  dp->origin holds the origins at t = 0 (the
  * first samples of pos); the causal block length accounts for the closest approach of the origins
  * over the run and their largest speed.
- * Errors: those of pc_dipoles_run; PC_ERR_ARG for opts->precision other than PC_F64.
+ * opts->precision PC_MIXED: each source's two charges in float32 in difference form, as in
+ * pc_dipoles_run, with the origin's motion added: within the history segment of the origin's own
+ * retarded time the origin moves linearly, each charge's retarded time is solved relative to the
+ * origin's, and the two charges' fields are differenced term by term (the origin's velocity and
+ * acceleration join the charges').  Sources whose retarded times fall before sample 1 or leave that
+ * segment by more than 0.1 sample (and, with opts->near_f64 > 0, sources closer than near_f64) take
+ * the float64 pair.  The context keeps a float32 copy of the origin samples for the run (48 bytes
+ * per dipole and half step).  The moment, the RK4 state and the stored histories stay float64.
+ * Errors: those of pc_dipoles_run.
  */
 pc_status pc_dipoles_run_moving(pc_ctx *ctx, const pc_dipoles *dp, const pc_dipole_motion *motion, double dt,
                                 int64_t n_steps, const pc_run_opts *opts, const pc_run_out *out, void *stream);

@@ -611,8 +611,9 @@ def final_energy(ctx, dp, dt, n_steps, v_max=0.0):
 
 
 def pc_dipoles_run_moving(ctx, dp, motion, dt, n_steps, v_max=0.0, ed_mode=0, fit=False, first_index=0,
-                          want_energy=True, want_Ed=False, stream=None):
-    """pc_dipoles_run_moving: motion = (pos, vel, acc) CUDA float64 tensors [B][N][2 n_steps + 1][3]."""
+                          want_energy=True, want_Ed=False, precision=PC_F64, near_f64=0.0, stream=None):
+    """pc_dipoles_run_moving: motion = (pos, vel, acc) CUDA float64 tensors [B][N][2 n_steps + 1][3];
+    precision PC_F64 or PC_MIXED (near_f64: sources closer than this many metres in float64)."""
     B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
     S = int(n_steps) + 1
     dev = dp.origin.device
@@ -634,7 +635,7 @@ def pc_dipoles_run_moving(ctx, dp, motion, dt, n_steps, v_max=0.0, ed_mode=0, fi
                   m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
     mo = PcDipoleMotion(pos=_ptr(pos), vel=_ptr(vel), acc=_ptr(acc))
     opts = PcRunOpts(v_max=float(v_max), ed_mode=int(ed_mode), fit=int(bool(fit)), first_index=int(first_index),
-                     precision=PC_F64)
+                     precision=int(precision), near_f64=float(near_f64))
     ro = PcRunOut(d=_ptr(out["d"]), d_dot=_ptr(out["d_dot"]), d_ddot=_ptr(out["d_ddot"]),
                   energy=_ptr(out.get("energy")), Ed=_ptr(out.get("Ed")), gamma=_ptr(out.get("gamma")),
                   omega=_ptr(out.get("omega")))

@@ -80,6 +80,10 @@ struct RunArgs {
   // moving dipoles (float64 path): origin position, velocity, acceleration at the half steps,
   // [B][N][2 n_steps + 1][3], or null for fixed origins
   const double *org_pos, *org_vel, *org_acc;
+  // their float32 mirror for the mixed drive, [B][N][2 n_steps + 1][3] float4 per half-step
+  // sample: (P_hi, V_x), (P_lo, V_y), (V_z, A): the position in units of c dt as hi + lo parts,
+  // the velocity in units of c, the acceleration in units of c / dt; or null
+  float4 *omf;
   // per dipole: the RK4 step as an affine map y' = M y + c1 e1 + c2 e2 + c4 e4, as
   // [B][N][kTab]: M^1 .. M^kMaxBlock (row-major 2x2 each), then c1, c2, c4
   double *rk4tab;
@@ -522,6 +526,179 @@ __device__ __forceinline__ bool static_pair_drive(float x0, const float4 cj, int
   return true;
 }
 
+__device__ __forceinline__ float dot3f(float ax, float ay, float az, float bx, float by, float bz) {
+  return fmaf(az, bz, fmaf(ay, by, ax * bx));
+}
+
+// Moving origins, mixed precision (Sec. 4.3 with Eqs. r_1, r_2, E): p_i . E of source j's two charges
+// at the receiver's origin at half-step hh (time u = n0 + stage_f, history samples 0..n0 known), in
+// the units of dipole_drive_fast.  Each charge sits at the origin plus its offset along the axis;
+// within one history segment k both move linearly, the origin by W per sample.  Steps:
+//  1. the origin's own retarded time k + t_o: |rho_k - t_o W| = T - t_o with rho_k = R_i(u) - P_j(k),
+//     T = u - k (the root of that quadratic near T - |rho_k|; k moved by one while t_o leaves
+//     [0, 1]); rn = T - t_o, rho_o = rho_k - t_o W;
+//  2. each charge's retarded time k + t_o - delta_c relative to it: with b = rho_o - s_c p_j and the
+//     charge's velocity per sample m = W + w_c p_j, A delta^2 + 2 B delta + C = 0 where A = 1 - m.m,
+//     B = rn - b.m, C = s_c (2 rho_o.p_j - s_c) (the fixed-origin quadratic with the origin's motion
+//     added), solved as a series in A C / B^2 so that delta_c keeps its own precision;
+//  3. E per charge in Griffiths' form E = (G / Ru^3) a - (G R / Ru^3) v - (R / Ru^2) acc with
+//     a = rho_o + delta_c W - s_c p_j, v = V + s_c' p_j, acc = A + s_c'' p_j, Ru = R - a.v,
+//     G = 1 - v.v + a.acc, R = rn + delta_c; the difference of the two charges' fields from the
+//     differences of their inputs (da = dR W - ds p_j, dv = -dR dV + ds' p_j, ...), every product
+//     differenced as d(f g) = df g+ + f- dg, so that the +-q cancellation costs no digits.
+// A source still wholly in the static pre-history is the fixed dipole at its first position
+// (static_pair_drive).  Returns false where neither applies (a retarded time on segment 0 or past the
+// newest sample, a charge more than kExtrap samples off the origin's segment, a near source with
+// near_f64 set); the caller then takes the float64 pair.
+__device__ bool pair_drive_mov_f32(const RunArgs &a, int b, int i, int j, int n0, int hh, float stage_f, float &out) {
+  const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+  const int64_t H = 2 * a.n_steps + 1;
+  const float4 *Oi = a.omf + ((size_t)bi * H + hh) * 3;
+  const float4 *Oj = a.omf + (size_t)bj * H * 3;  // sample k at Oj + 6 k (half-step index 2 k)
+  const float4 ri0 = Oi[0], ri1 = Oi[1];
+  const float *fi = a.dipf + bi * kDipF, *fj = a.dipf + bj * kDipF;
+  // 1. the origin's retarded time: first guess from the origin at the block start
+  int k;
+  {
+    const float4 p0 = Oj[6 * (size_t)n0], p1 = Oj[6 * (size_t)n0 + 1];
+    const float rx = (ri0.x - p0.x) + (ri1.x - p1.x), ry = (ri0.y - p0.y) + (ri1.y - p1.y),
+                rz = (ri0.z - p0.z) + (ri1.z - p1.z);
+    float fl;
+    k = n0 + Num<float>::floor_int(stage_f - sqrtf(dot3f(rx, ry, rz, rx, ry, rz)), fl);
+  }
+  if (k < 1) {
+    // the static pre-history: before t = 0 the origin rests at its first sample and the charges at
+    // their first offsets (Sec. 3.2), so a source whose two charges both have retarded times there is
+    // a fixed dipole at rho_0 = R_i(u) - P_j(0): the fixed-origin form, no solve
+    const float4 p0 = Oj[0], p1 = Oj[1];
+    const float rx = (ri0.x - p0.x) + (ri1.x - p1.x), ry = (ri0.y - p0.y) + (ri1.y - p1.y),
+                rz = (ri0.z - p0.z) + (ri1.z - p1.z);
+    const float rn0 = sqrtf(dot3f(rx, ry, rz, rx, ry, rz));
+    const float xu = ((float)n0 - rn0) + stage_f;  // the origin's retarded time if it precedes t = 0
+    if (xu < 0.f) {
+      if (a.near_L > 0.f && rn0 < a.near_L) return false;
+      const float4 cj = *reinterpret_cast<const float4 *>(fj + 8);  // (p_z, mu+, mu-, q/e)
+      const float4 geo = make_float4(rn0, dot3f(rx, ry, rz, fj[6], fj[7], cj.x), dot3f(rx, ry, rz, fi[6], fi[7], fi[8]),
+                                     dot3f(fj[6], fj[7], cj.x, fi[6], fi[7], fi[8]));
+      if (static_pair_drive(a.H32[bj * (size_t)a.hs].x, cj, 0, xu, geo, out)) return true;
+    }
+    return false;
+  }
+  float to = -1.f, T = 0.f, rkx = 0.f, rky = 0.f, rkz = 0.f, Wx = 0.f, Wy = 0.f, Wz = 0.f;
+  for (int it = 0; it < 3; ++it) {
+    if (k < 1 || k > n0 - 1) return false;
+    const float4 *Pk = Oj + 6 * (size_t)k;
+    const float4 a0 = Pk[0], a1 = Pk[1], b0 = Pk[6], b1 = Pk[7];
+    rkx = (ri0.x - a0.x) + (ri1.x - a1.x);
+    rky = (ri0.y - a0.y) + (ri1.y - a1.y);
+    rkz = (ri0.z - a0.z) + (ri1.z - a1.z);
+    Wx = (b0.x - a0.x) + (b1.x - a1.x);
+    Wy = (b0.y - a0.y) + (b1.y - a1.y);
+    Wz = (b0.z - a0.z) + (b1.z - a1.z);
+    T = (float)(n0 - k) + stage_f;
+    const float rk = sqrtf(dot3f(rkx, rky, rkz, rkx, rky, rkz));
+    const float Ao = 1.f - dot3f(Wx, Wy, Wz, Wx, Wy, Wz);
+    const float Bo = T - dot3f(rkx, rky, rkz, Wx, Wy, Wz);
+    const float Co = (T - rk) * (T + rk);
+    to = Co / (Bo + sqrtf(fmaxf(Bo * Bo - Ao * Co, 0.f)));
+    if (to < 0.f) {
+      --k;
+    } else if (to > 1.f) {
+      ++k;
+    } else {
+      break;
+    }
+  }
+  if (!(to >= 0.f && to <= 1.f)) return false;
+  const float rn = T - to;
+  if (a.near_L > 0.f && rn < a.near_L) return false;
+  const float rox = rkx - to * Wx, roy = rky - to * Wy, roz = rkz - to * Wz;
+  const float pjx = fj[6], pjy = fj[7], pjz = fj[8], mup = fj[9], mum = fj[10], qs = fj[11];
+  const float pix = fi[6], piy = fi[7], piz = fi[8];
+  const float rp = dot3f(rox, roy, roz, pjx, pjy, pjz), rW = dot3f(rox, roy, roz, Wx, Wy, Wz);
+  const float Wp = dot3f(Wx, Wy, Wz, pjx, pjy, pjz), W2 = dot3f(Wx, Wy, Wz, Wx, Wy, Wz);
+  // 2. the two charges' retarded times relative to the origin's (+ charge in .x, - charge in .y)
+  const HistF32Ring Hj{a.H32 + bj * (size_t)a.hs, -1};
+  float x0, v0, a0, x1, v1, a1;
+  Hj.get_in(k, x0, v0, a0);
+  Hj.get_in(k + 1, x1, v1, a1);
+  const float dx = x1 - x0, dvm = v1 - v0, dam = a1 - a0;
+  const float Xc = x0 + to * dx;
+  const float2 mu = make_float2(mup, -mum);
+  float2 dl, th;
+  float epsum = 0.f;
+  {
+    const float sc[2] = {mu.x * Xc, mu.y * Xc}, w[2] = {mu.x * dx, mu.y * dx};
+    float dlc[2], thc[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float A = 1.f - (W2 + w[c] * (2.f * Wp + w[c]));
+      const float B = rn - (rW + w[c] * rp - sc[c] * (Wp + w[c]));
+      const float C = sc[c] * (2.f * rp - sc[c]);
+      const float r = __fdividef(1.f, B);
+      const float Cr = C * r;
+      const float h = 0.5f * Cr;
+      const float eps = A * Cr * r;
+      const float ndl = fmaf(h, eps * fmaf(eps, 0.125f, 0.25f), h);  // -delta_c
+      dlc[c] = -ndl;
+      thc[c] = to + ndl;
+      epsum += fabsf(eps);
+    }
+    dl = make_float2(dlc[0], dlc[1]);
+    th = make_float2(thc[0], thc[1]);
+  }
+  // the last segment may be extended only by kEndTol (no sample beyond n0)
+  const float lo = -kExtrap, hi = 1.f + ((k == n0 - 1) ? kEndTol : kExtrap);
+  if (!(th.x >= lo && th.x <= hi && th.y >= lo && th.y <= hi && epsum < 1e-2f)) return false;
+  // 3. the charges' states at their retarded times
+  const float Xp = x0 + th.x * dx, Xm = x0 + th.y * dx;
+  const float Sp = v0 + th.x * dvm, Sm = v0 + th.y * dvm;
+  const float Lp = a0 + th.x * dam, Lm = a0 + th.y * dam;
+  const float sm = mu.y * Xm, sdm = mu.y * Sm, sam = mu.y * Lm;
+  const float ds = mup * Xp + mum * Xm, dsd = mup * Sp + mum * Sm, dsa = mup * Lp + mum * Lm;
+  const float dR = dl.x - dl.y;
+  const float Rm = rn + dl.y, Rp = rn + dl.x;
+  // the origin's velocity and acceleration on segment k (the - charge's time) and their slopes
+  const float4 *Pk = Oj + 6 * (size_t)k;
+  const float4 c00 = Pk[0], c01 = Pk[1], c02 = Pk[2], c10 = Pk[6], c11 = Pk[7], c12 = Pk[8];
+  const float dVx = c10.w - c00.w, dVy = c11.w - c01.w, dVz = c12.x - c02.x;
+  const float dAx = c12.y - c02.y, dAy = c12.z - c02.z, dAz = c12.w - c02.w;
+  const float vmx = fmaf(th.y, dVx, c00.w) + sdm * pjx, vmy = fmaf(th.y, dVy, c01.w) + sdm * pjy,
+              vmz = fmaf(th.y, dVz, c02.x) + sdm * pjz;
+  const float gmx = fmaf(th.y, dAx, c02.y) + sam * pjx, gmy = fmaf(th.y, dAy, c02.z) + sam * pjy,
+              gmz = fmaf(th.y, dAz, c02.w) + sam * pjz;
+  const float amx = rox + dl.y * Wx - sm * pjx, amy = roy + dl.y * Wy - sm * pjy, amz = roz + dl.y * Wz - sm * pjz;
+  // differences (+ minus -) of position, velocity and acceleration
+  const float Dax = dR * Wx - ds * pjx, Day = dR * Wy - ds * pjy, Daz = dR * Wz - ds * pjz;
+  const float Dvx = dsd * pjx - dR * dVx, Dvy = dsd * pjy - dR * dVy, Dvz = dsd * pjz - dR * dVz;
+  const float Dgx = dsa * pjx - dR * dAx, Dgy = dsa * pjy - dR * dAy, Dgz = dsa * pjz - dR * dAz;
+  const float apx = amx + Dax, apy = amy + Day, apz = amz + Daz;
+  const float vpx = vmx + Dvx, vpy = vmy + Dvy, vpz = vmz + Dvz;
+  const float gpx = gmx + Dgx, gpy = gmy + Dgy, gpz = gmz + Dgz;
+  // R_u and G of the - charge and their differences
+  const float Rum = Rm - dot3f(amx, amy, amz, vmx, vmy, vmz);
+  const float dRu = dR - (dot3f(Dax, Day, Daz, vpx, vpy, vpz) + dot3f(amx, amy, amz, Dvx, Dvy, Dvz));
+  const float Rup = Rum + dRu;
+  const float Gm = 1.f - dot3f(vmx, vmy, vmz, vmx, vmy, vmz) + dot3f(amx, amy, amz, gmx, gmy, gmz);
+  const float dG = dot3f(Dax, Day, Daz, gpx, gpy, gpz) + dot3f(amx, amy, amz, Dgx, Dgy, Dgz) -
+                   dot3f(Dvx, Dvy, Dvz, vpx + vmx, vpy + vmy, vpz + vmz);
+  const float ip = __fdividef(1.f, Rup), im = __fdividef(1.f, Rum);
+  const float di = -dRu * ip * im;
+  const float di2 = di * (ip + im);
+  const float di3 = di * (ip * ip + ip * im + im * im);
+  const float ip2 = ip * ip, ip3 = ip2 * ip, im2 = im * im, im3 = im2 * im;
+  // coefficients of a, v, acc: C = G / Ru^3, K = G R / Ru^3, L = R / Ru^2 (- charge and differences)
+  const float Cm = Gm * im3, dC = dG * ip3 + Gm * di3;
+  const float GRm = Gm * Rm, dGR = dG * Rp + Gm * dR;
+  const float Km = GRm * im3, dK = dGR * ip3 + GRm * di3;
+  const float Lm_ = Rm * im2, dL = dR * ip2 + Rm * di2;
+  const float pE = dC * dot3f(apx, apy, apz, pix, piy, piz) + Cm * dot3f(Dax, Day, Daz, pix, piy, piz) -
+                   dK * dot3f(vpx, vpy, vpz, pix, piy, piz) - Km * dot3f(Dvx, Dvy, Dvz, pix, piy, piz) -
+                   dL * dot3f(gpx, gpy, gpz, pix, piy, piz) - Lm_ * dot3f(Dgx, Dgy, Dgz, pix, piy, piz);
+  out = qs * pE;
+  return true;
+}
+
 // The grid path's float32 source loop (sources j = j_lo + m, step slots): the pair-table rows, the
 // sources' records and history rows are reached by 32-bit indices and a pointer that advances with
 // j (no 64-bit products per source), and pair_drive_f32's fast path and static pre-history are
@@ -583,7 +760,8 @@ __device__ __forceinline__ void drive_sources_grid(const RunArgs &a, int b, int 
 // ns == 0 evaluates E_d(n0) into Es[0].  History samples 0..n0 are known.  GROUPS: the float32
 // sources through drive_sources_grid (the grid path, whose warps loop over many sources; in the
 // persistent kernel a lane has one or two, and the group loop only raises its registers).
-template <bool MIXED, bool NEAR = false, bool RING = true, bool GROUPS = false>
+// MOV: moving origins in the mixed drive (pair_drive_mov_f32, the float64 pair where it declines).
+template <bool MIXED, bool NEAR = false, bool RING = true, bool GROUPS = false, bool MOV = false>
 __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, double *sh /* [32] */, int *err,
                             int j_lo, int j_hi, double *dst_row, int sgsel = -1) {
   const int lane = threadIdx.x & 31;
@@ -603,6 +781,20 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
   // source j's charges sg0 .. sg1 - 1
   auto source = [&](int j, int sg0, int sg1) {
     if (j == i) return;
+    if constexpr (MIXED && MOV) {
+      // the receiver at its origin of the stage time: half-step index 2 n0 + s + 1 (2 n0 for ns = 0)
+      float v;
+      if (pair_drive_mov_f32(a, b, i, j, (int)n0, 2 * (int)n0 + (ns > 0 ? s + 1 : 0), stage_f, v)) {
+        const float y = v - comp;
+        const float t = accf + y;
+        comp = (t - accf) - y;
+        accf = t;
+      } else {
+        // (the float64 pair takes its first guess from the moving origins)
+        accd += pair_drive_f64(a, b, i, j, (double)n0 + stage, n0, 0, err, 0, 2);
+      }
+      return;
+    }
     if (MIXED) {
       // retarded time of j's centre: n0 + stage - |R_i - R_j| / (c dt), split in integer + fraction
       const size_t ij = (size_t)bidx(a, b, i) * a.N + j;
@@ -631,7 +823,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
     }
   };
   if (m < slots) {
-    if constexpr (MIXED && !NEAR && GROUPS) {
+    if constexpr (MIXED && !NEAR && !MOV && GROUPS) {
       drive_sources_grid<RING>(a, b, i, n0, stage_f, m, slots, j_lo, j_hi, accf, comp, err);
     } else if constexpr (MIXED && !NEAR) {
       for (int j = j_lo + m; j < j_hi; j += slots) source(j, 0, 2);
@@ -644,7 +836,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
       }
     }
   }
-  if (MIXED && !NEAR) {
+  if (MIXED && !NEAR && !MOV) {
     // the slots' float32 sums added in float32, one conversion per stage (conversions and float64
     // arithmetic issue to the narrow float64 unit)
     float *shf = reinterpret_cast<float *>(sh);
@@ -672,7 +864,7 @@ __device__ void drive_phase(const RunArgs &a, int b, int i, int64_t n0, int ns, 
 // so that the float32 source loop of the default one keeps its registers.  At most two CTAs share
 // an SM here (one per configuration), so the register bound is one CTA's: held to the 80 of the
 // compiler's default choice the time loop spilled and ran 7 % slower.
-template <bool MIXED, bool NEAR = false, bool RING = true>
+template <bool MIXED, bool NEAR = false, bool RING = true, bool MOV = false>
 __global__ void __launch_bounds__(kRunWarps * 32, 1) lo_run_kernel(const RunArgs a) {
   const int b = blockIdx.x;
   const int N = a.N;
@@ -710,7 +902,7 @@ __global__ void __launch_bounds__(kRunWarps * 32, 1) lo_run_kernel(const RunArgs
   for (int i = warp; i < N; i += kRunWarps) {
     if (!a.state_in) {
       int err = 0;
-      drive_phase<MIXED, NEAR, RING>(a, b, i, a.n_begin, 0, sh[warp], &err, 0, N, s_Es[i]);
+      drive_phase<MIXED, NEAR, RING, false, MOV>(a, b, i, a.n_begin, 0, sh[warp], &err, 0, N, s_Es[i]);
       if (err) {
         set_status(a.status, err);
         s_stop = 1;
@@ -731,7 +923,7 @@ __global__ void __launch_bounds__(kRunWarps * 32, 1) lo_run_kernel(const RunArgs
     const bool xsplit = !MIXED && 2 * N <= kRunWarps && 2 * N > 32 / nst;
     for (int w = warp; w < (xsplit ? 2 * N : N); w += kRunWarps) {
       int err = 0;
-      drive_phase<MIXED, NEAR, RING>(a, b, xsplit ? w >> 1 : w, n0, nst, sh[warp], &err, 0, N,
+      drive_phase<MIXED, NEAR, RING, false, MOV>(a, b, xsplit ? w >> 1 : w, n0, nst, sh[warp], &err, 0, N,
                                      (xsplit && (w & 1)) ? s_Ep[w >> 1] : s_Es[xsplit ? w >> 1 : w],
                                      xsplit ? w & 1 : -1);
       if (err) {
@@ -886,6 +1078,26 @@ __global__ void lo_tables_kernel(const RunArgs a) {
   }
 }
 
+// The float32 mirror of moving origins for the mixed drive (RunArgs::omf), once per run,
+// grid-stride over the [B][N][2 n_steps + 1] half-step samples.
+__global__ void lo_origin_mirror_kernel(const RunArgs a) {
+  const int64_t H = 2 * a.n_steps + 1, n = (int64_t)a.B * a.N * H;
+  const double iL = 1.0 / (kC * a.dt), ic = 1.0 / kC, adt = a.dt / kC;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double *p = a.org_pos + 3 * t, *v = a.org_vel + 3 * t, *ac = a.org_acc + 3 * t;
+    float hi[3], lo[3];
+    for (int c = 0; c < 3; ++c) {
+      const double x = p[c] * iL;
+      hi[c] = (float)x;
+      lo[c] = (float)(x - (double)hi[c]);
+    }
+    float4 *o = a.omf + 3 * t;
+    o[0] = make_float4(hi[0], hi[1], hi[2], (float)(v[0] * ic));
+    o[1] = make_float4(lo[0], lo[1], lo[2], (float)(v[1] * ic));
+    o[2] = make_float4((float)(v[2] * ic), (float)(ac[0] * adt), (float)(ac[1] * adt), (float)(ac[2] * adt));
+  }
+}
+
 // Presets a.rstat to (a large distance, 0, 0): 0x7f7f... is about 1.4e306 as a double.
 __global__ void lo_rstat_init_kernel(const RunArgs a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -978,7 +1190,7 @@ __global__ void lo_init_kernel(const RunArgs a, int K) {
 
 // Grid path, phase A: one warp per (receiver, source slice).  ns < 0 takes the block from the
 // device cursor a.blk (graph replay); ns == 0 evaluates E_d(0).
-template <bool MIXED, bool NEAR = false, bool RING = true>
+template <bool MIXED, bool NEAR = false, bool RING = true, bool MOV = false>
 __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs a, int64_t n0, int ns) {
   __shared__ double sh[kRunWarps][32];
   if (*((volatile int *)a.status)) return;  // an earlier block failed
@@ -996,7 +1208,7 @@ __global__ void __launch_bounds__(kRunWarps * 32) lo_drive_kernel(const RunArgs 
   const int j_lo = min(a.N, z * chunk), j_hi = min(a.N, j_lo + chunk);
   double *dst = a.nsplit > 1 ? a.Epart + (size_t)z * a.B * a.N * (2 * kMaxBlock + 1) : a.Es;
   int err = 0;
-  drive_phase<MIXED, NEAR, RING, true>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi,
+  drive_phase<MIXED, NEAR, RING, true, MOV>(a, b, i, n0, ns, sh[warp], &err, j_lo, j_hi,
                                        dst + bidx(a, b, i) * (2 * kMaxBlock + 1));
   if (err) set_status(a.status, err);
 }
@@ -1587,6 +1799,7 @@ namespace pc {
 // the mixed ones specialised for a full-history store (no slot mask)
 static void *drive_kernel_for(const RunArgs &a, bool mixed) {
   if (!mixed) return (void *)lo_drive_kernel<false>;
+  if (a.org_pos) return (void *)lo_drive_kernel<true, false, false, true>;  // moving runs keep every sample
   const bool ring = a.wm >= 0;
   if (a.near_L > 0.f)
     return ring ? (void *)lo_drive_kernel<true, true, true> : (void *)lo_drive_kernel<true, true, false>;
@@ -1594,6 +1807,7 @@ static void *drive_kernel_for(const RunArgs &a, bool mixed) {
 }
 static void *run_kernel_for(const RunArgs &a, bool mixed) {
   if (!mixed) return (void *)lo_run_kernel<false>;
+  if (a.org_pos) return (void *)lo_run_kernel<true, false, false, true>;
   const bool ring = a.wm >= 0;
   if (a.near_L > 0.f)
     return ring ? (void *)lo_run_kernel<true, true, true> : (void *)lo_run_kernel<true, true, false>;
@@ -1736,7 +1950,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const pc_dipole_motion *motion = pl.motion;
   const size_t nbn = (size_t)dp->B * dp->N;
   const bool mixed = opts->precision == PC_MIXED;
-  if (motion && (mixed || !motion->pos || !motion->vel || !motion->acc)) return PC_ERR_ARG;
+  if (motion && (!motion->pos || !motion->vel || !motion->acc)) return PC_ERR_ARG;
   if (dp->N > pc::kSmallN && dp->B > 65535) return PC_ERR_ARG;  // grid path: configurations on grid y
   // the resumed state's step (and a check of its header)
   int64_t n_begin = 0, D_in = 0;
@@ -1859,7 +2073,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   // the fit's kinetic energies: after the run from the full store, or per step into their own rows
   const int64_t first = opts->fit ? opts->first_index : 0;
   const size_t ke_b = opts->fit ? al(nbn * (size_t)(full_store ? So : So - first) * sizeof(double)) : 0;
-  if (ctx->run_store.reserve(3 * ring_b + h_bytes + ke_b) != cudaSuccess) return PC_ERR_CUDA;
+  // moving origins in the mixed drive: their float32 mirror (three float4 per half-step sample)
+  const size_t om_b = (motion && mixed) ? al(nbn * (size_t)(2 * n_end + 1) * 3 * sizeof(float4)) : 0;
+  if (ctx->run_store.reserve(3 * ring_b + h_bytes + ke_b + om_b) != cudaSuccess) return PC_ERR_CUDA;
   char *sto = (char *)ctx->run_store.ptr;
   a.hs = hs;
   a.wm = wm;
@@ -1886,6 +2102,8 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.energy_loop = (out->energy && !full_store) ? 1 : 0;
   a.Ed = out->Ed;
   double *ke_fit = opts->fit ? (double *)(sto + 3 * ring_b + h_bytes) : nullptr;
+  a.omf = om_b ? (float4 *)(sto + 3 * ring_b + h_bytes + ke_b) : nullptr;
+  if (a.omf) pc::lo_origin_mirror_kernel<<<ctx->num_sms * 4, 256, 0, st>>>(a);
   if (pl.ke) {
     a.ke = pl.ke;
     a.kdd = pl.kdd;

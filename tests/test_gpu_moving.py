@@ -1,5 +1,5 @@
-"""Moving dipoles (Sec. 4.3): pc_dipoles_run_moving (CUDA, float64, through the C ABI) against the
-FP64 oracle with the same half-step origin trajectories."""
+"""Moving dipoles (Sec. 4.3): pc_dipoles_run_moving (CUDA, float64 and mixed, through the C ABI)
+against the FP64 oracle with the same half-step origin trajectories."""
 import math
 
 import numpy as np
@@ -58,22 +58,54 @@ def test_moving_cloud_grid_path_matches_oracle(ctx):
         assert _err(out[k][0], ref[k]) < 1e-10, k
 
 
-def test_moving_rejects_mixed_precision(ctx):
-    cfg = W.adjoint_cluster(B=1, N=2, n_steps=20)
-    motion = _dev(W.oscillating_origins(cfg, 1e-10, 1e13))
-    dp = pc.lo_config_to_device(cfg)
-    d = pc.capi.PcDipoles(B=1, N=2, origin=pc.capi._ptr(dp.origin), axis=pc.capi._ptr(dp.axis), q=pc.capi._ptr(dp.q),
-                          m1=pc.capi._ptr(dp.m1), m2=pc.capi._ptr(dp.m2), omega0=pc.capi._ptr(dp.omega0),
-                          d0=pc.capi._ptr(dp.d0))
-    mo = pc.capi.PcDipoleMotion(pos=pc.capi._ptr(motion[0]), vel=pc.capi._ptr(motion[1]), acc=pc.capi._ptr(motion[2]))
-    opts = pc.capi.PcRunOpts(v_max=0.0, ed_mode=0, fit=0, first_index=0, precision=pc.PC_MIXED)
-    outs = [torch.empty((1, 2, 21), dtype=torch.float64, device="cuda") for _ in range(3)]
-    ro = pc.capi.PcRunOut(d=pc.capi._ptr(outs[0]), d_dot=pc.capi._ptr(outs[1]), d_ddot=pc.capi._ptr(outs[2]))
-    import ctypes
+def _pair_case():
+    origins = np.array([[[0.0, 0.0, 0.0], [20e-9, 0.0, 0.0]], [[0.0, 0.0, 0.0], [0.0, 35e-9, 0.0]]])
+    axes = np.array([[[0.0, 1.0, 0.0], [0.0, 1.0, 0.0]], [[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]])
+    cfg = W.lo_batch(origins, axes, 2 * math.pi * 200e12, 1e-11, 1e-18, 4000, 0, q=10 * W.E_CHARGE)
+    motion = W.oscillating_origins(cfg, np.array([[1e-10, 0.0], [2e-10, 5e-11]]), 2 * math.pi * 20e12)
+    return cfg, motion
 
-    st = ctx.lib.pc_dipoles_run_moving(ctx.handle, ctypes.byref(d), ctypes.byref(mo), cfg.dt, 20, ctypes.byref(opts),
-                                       ctypes.byref(ro), None)
-    assert st == 1  # PC_ERR_ARG
+
+def test_moving_mixed_pair_matches_oracle(ctx):
+    # the mixed drive with moving origins (the float32 pair in difference form with the origin's
+    # motion, one persistent CTA per configuration): histories and driving fields within 1e-5 of the
+    # oracle's; and not the float64 run's to rounding, so the float32 pairs did run
+    cfg, motion = _pair_case()
+    dp = pc.lo_config_to_device(cfg)
+    mx = pc.pc_dipoles_run_moving(ctx, dp, _dev(motion), cfg.dt, cfg.n_steps, want_Ed=True, precision=pc.PC_MIXED)
+    f64 = pc.pc_dipoles_run_moving(ctx, dp, _dev(motion), cfg.dt, cfg.n_steps, want_Ed=True)
+    for b in range(cfg.B):
+        ref = oracle.dipoles_run(cfg, b=b, motion=motion)
+        assert ref["status"] == oracle.OK
+        for k in ("d", "d_dot", "d_ddot", "energy", "Ed"):
+            assert _err(mx[k][b], ref[k]) < 1e-5, (b, k, _err(mx[k][b], ref[k]))
+        assert _err(mx["Ed"][b], f64["Ed"][b].cpu().numpy()) > 1e-12
+
+
+def test_moving_mixed_cloud_grid_path_matches_oracle(ctx):
+    # 80 dipoles: the grid-wide mixed drive with moving origins
+    cfg = W.cfg5(N=80, n_steps=400, side=200e-9, min_spacing=12e-9, seed=W.SEED_CFG5 + 3)
+    rng = np.random.default_rng(5)
+    motion = W.oscillating_origins(cfg, rng.uniform(0.0, 2e-10, size=(1, 80)), 2 * math.pi * 30e12,
+                                   direction=(1.0, 1.0, 0.0))
+    out = pc.pc_dipoles_run_moving(ctx, pc.lo_config_to_device(cfg), _dev(motion), cfg.dt, cfg.n_steps, want_Ed=True,
+                                   precision=pc.PC_MIXED)
+    ref = oracle.dipoles_run(cfg, motion=motion)
+    assert ref["status"] == oracle.OK
+    for k in ("d", "d_dot", "Ed"):
+        assert _err(out[k][0], ref[k]) < 1e-5, (k, _err(out[k][0], ref[k]))
+
+
+def test_moving_mixed_all_near_is_the_float64_run(ctx):
+    # near_f64 beyond every distance: each source takes the float64 pair, so the mixed run is the
+    # float64 run up to the order of the float64 sums
+    cfg, motion = _pair_case()
+    dp = pc.lo_config_to_device(cfg)
+    mx = pc.pc_dipoles_run_moving(ctx, dp, _dev(motion), cfg.dt, cfg.n_steps, want_Ed=True, precision=pc.PC_MIXED,
+                                  near_f64=1e-6)
+    f64 = pc.pc_dipoles_run_moving(ctx, dp, _dev(motion), cfg.dt, cfg.n_steps, want_Ed=True)
+    for k in ("d", "d_dot", "Ed"):
+        assert _err(mx[k], f64[k].cpu().numpy()) < 1e-12, k
 
 
 def _weights(cfg, seed=5):
