@@ -13,7 +13,7 @@ CPU oracle on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --profile fields_mixed_small|fields_mixed2_small|fields_f64_small|lo_small|lo_f64_small|
-                            ring_small|cloud_small|cloud_late|adj_small
+                            ring_small|cloud_small|cloud_late|ring_moving_small|adj_small
                                                      (one small run for ncu)
 Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own copy of the workload
 (independent problems, no data-path collective), so scaling is weak.
@@ -412,7 +412,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", default=None,
                     choices=["fields_mixed_small", "fields_mixed2_small", "fields_f64_small", "lo_small",
-                             "lo_f64_small", "ring_small", "cloud_small", "cloud_late", "adj_small"])
+                             "lo_f64_small", "ring_small", "cloud_small", "cloud_late", "ring_moving_small",
+                             "adj_small"])
     ap.add_argument("--no-extra", action="store_true", help="skip the float64, oscillator and CPU legs")
     ap.add_argument("--compare-cloud", type=int, default=0, metavar="STEPS",
                     help="run the 4096-oscillator cloud for STEPS steps in both precisions and compare them")
@@ -478,6 +479,15 @@ def main():
             os.environ["PYCHARGE_GB300_HOST_LOOP"] = "1"
             cfg = W.cfg4(n_steps=200) if args.profile == "ring_small" else W.cfg5(n_steps=64)
             pc.pc_dipoles_run(ctx, pc.lo_config_to_device(cfg, dev), cfg.dt, cfg.n_steps, precision=pc.PC_MIXED)
+        elif args.profile == "ring_moving_small":
+            # the ring with moving origins (1e-10 m along x at 20 THz), mixed, 1600 steps (100 causal
+            # blocks of 16), block loop launched from the host; from block 84 on (step 1344) every
+            # source is past its static pre-history, past the ring's largest delay of 1 334 samples
+            os.environ["PYCHARGE_GB300_HOST_LOOP"] = "1"
+            cfg = W.cfg4(n_steps=1600)
+            mot = tuple(torch.from_numpy(x).to(dev) for x in W.oscillating_origins(cfg, 1e-10, 2 * math.pi * 20e12))
+            pc.pc_dipoles_run_moving(ctx, pc.lo_config_to_device(cfg, dev), mot, cfg.dt, cfg.n_steps,
+                                     precision=pc.PC_MIXED)
         else:
             # adjoint of the ring's float64 run over 2000 steps (past the ring's largest delay, 1 334
             # samples, so that the last blocks, reversed first, see no source in its static

@@ -1131,18 +1131,22 @@ __global__ void __launch_bounds__(256) lo_pairs_kernel(const RunArgs a) {
         rmin = fmin(rmin, r);
         rmax = fmax(rmax, r);
         if (a.org_pos) {
-          // closest approach of the two origins over the run
+          // closest approach of the two origins over the run (squared distances, one square root)
+          double r2min = r * r;
           for (int64_t h = 0; h < H; ++h) {
             const double *pi_ = a.org_pos + (bi * H + h) * 3, *pj_ = a.org_pos + (bj * H + h) * 3;
             const double ex = pi_[0] - pj_[0], ey = pi_[1] - pj_[1], ez = pi_[2] - pj_[2];
-            rmin = fmin(rmin, sqrt(ex * ex + ey * ey + ez * ez));
+            r2min = fmin(r2min, ex * ex + ey * ey + ez * ez);
           }
+          rmin = fmin(rmin, sqrt(r2min));
         }
       } else if (a.org_pos) {
+        double v2max = 0.0;
         for (int64_t h = 0; h < H; ++h) {
           const double *vi = a.org_vel + (bi * H + h) * 3;
-          vmax = fmax(vmax, sqrt(vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+          v2max = fmax(v2max, vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
         }
+        vmax = fmax(vmax, sqrt(v2max));
       }
       const double x = r / L;
       const double fl = floor(x);
@@ -2144,7 +2148,20 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     const int64_t target = (int64_t)ctx->num_sms * 64;
     int nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, (target + (int64_t)nbn - 1) / (int64_t)nbn),
                                         std::max(1, dp->N / 8));
-    if (ctx->run_slices > 0) nsplit = std::min(ctx->run_slices, std::max(1, dp->N / 8));  // set or tuned
+    if (ctx->run_slices > 0) {
+      nsplit = std::min(ctx->run_slices, std::max(1, dp->N / 8));  // set or tuned
+    } else if (motion && mixed) {
+      // the moving mixed drive holds about twice the registers of the fixed one (two CTAs per SM
+      // instead of four): as many slices as fill two whole waves of its CTAs
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pc::drive_kernel_for(a, mixed), pc::kRunWarps * 32, 0) !=
+              cudaSuccess ||
+          occ < 1)
+        occ = 1;
+      const int64_t per_slice = (int64_t)((dp->N + pc::kRunWarps - 1) / pc::kRunWarps) * dp->B;  // CTAs
+      nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, 2 * (int64_t)ctx->num_sms * occ / per_slice),
+                                      std::max(1, dp->N / 8));
+    }
     nsplit = std::min(nsplit, kMaxSplit);
     a.nsplit = nsplit;
     a.Epart = nsplit > 1 ? (double *)(scr + part_off) : nullptr;
