@@ -444,7 +444,9 @@ typedef struct {
  * dependence on the origin samples is taken through its defining equation (Eq. ret_t, implicit-
  * function theorem) as in pc_dipoles_adjoint.  g->origin receives zeros: the static origins do not
  * enter a moving run.
- *   dp, motion, dt, n_steps, opts   as for pc_dipoles_run_moving (PC_F64, ed_mode 0)
+ *   dp, motion, dt, n_steps, opts   as for pc_dipoles_run_moving (ed_mode 0; opts->precision PC_F64
+ *                                    or PC_MIXED selects the forward's driving field, the reverse is
+ *                                    float64 as in pc_dipoles_adjoint)
  *   dL_dEnergyFinal                  device [B][N]
  *   g, gm                            gradients (device); the call clears gm's arrays first
  * Errors: those of pc_dipoles_adjoint and of pc_dipoles_run_moving.

@@ -645,10 +645,11 @@ def pc_dipoles_run_moving(ctx, dp, motion, dt, n_steps, v_max=0.0, ed_mode=0, fi
     return out
 
 
-def pc_dipoles_adjoint_moving(ctx, dp, motion, dt, n_steps, dL_dEnergyFinal, v_max=0.0, stream=None):
+def pc_dipoles_adjoint_moving(ctx, dp, motion, dt, n_steps, dL_dEnergyFinal, v_max=0.0, precision=PC_F64,
+                              stream=None):
     """pc_dipoles_adjoint_moving: gradients of sum w E(T) of a moving run (motion = (pos, vel, acc)
-    CUDA float64 [B][N][2 n_steps + 1][3]); returns (g_origin (zeros), g_omega0, g_d0, g_pos, g_vel,
-    g_acc)."""
+    CUDA float64 [B][N][2 n_steps + 1][3]; precision: the forward's driving field, the reverse is
+    float64); returns (g_origin (zeros), g_omega0, g_d0, g_pos, g_vel, g_acc)."""
     B, N = int(dp.origin.shape[0]), int(dp.origin.shape[1])
     dev = dp.origin.device
     H = 2 * int(n_steps) + 1
@@ -664,7 +665,7 @@ def pc_dipoles_adjoint_moving(ctx, dp, motion, dt, n_steps, dL_dEnergyFinal, v_m
     d = PcDipoles(B=B, N=N, origin=_ptr(dp.origin), axis=_ptr(dp.axis), q=_ptr(dp.q), m1=_ptr(dp.m1),
                   m2=_ptr(dp.m2), omega0=_ptr(dp.omega0), d0=_ptr(dp.d0))
     mo = PcDipoleMotion(pos=_ptr(pos), vel=_ptr(vel), acc=_ptr(acc))
-    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=PC_F64)
+    opts = PcRunOpts(v_max=float(v_max), ed_mode=0, fit=0, first_index=0, precision=int(precision))
     g = PcDipoleGrads(origin=_ptr(g_origin), omega0=_ptr(g_omega0), d0=_ptr(g_d0))
     gmo = PcDipoleMotion(pos=_ptr(gm[0]), vel=_ptr(gm[1]), acc=_ptr(gm[2]))
     st = ctx.lib.pc_dipoles_adjoint_moving(ctx.handle, ctypes.byref(d), ctypes.byref(mo), float(dt), int(n_steps),

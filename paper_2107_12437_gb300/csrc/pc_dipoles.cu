@@ -3019,9 +3019,8 @@ static pc_status adjoint_core(pc_ctx *ctx, const pc_dipoles *dp, double dt, int6
                               const FieldSeed *fseed = nullptr, const pc_dipole_motion *motion = nullptr,
                               const pc_dipole_motion_grads *gm = nullptr) {
   if (!dp || !opts || !g || !g->origin || !g->omega0 || !g->d0) return PC_ERR_ARG;
-  // moving origins: the energy loss with the float64 forward only
-  if (motion && (rates || fseed || opts->precision != PC_F64 || !motion->pos || !motion->vel || !motion->acc))
-    return PC_ERR_ARG;
+  // moving origins: the energy loss (the forward in either precision, as below)
+  if (motion && (rates || fseed || !motion->pos || !motion->vel || !motion->acc)) return PC_ERR_ARG;
   // the forward may run its driving field in either precision (the reverse is float64 throughout);
   // the fitted rates' adjoint keeps the float64 forward
   if (opts->ed_mode != 0 || n_steps < 1) return PC_ERR_ARG;
