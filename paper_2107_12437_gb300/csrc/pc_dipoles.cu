@@ -535,8 +535,8 @@ __device__ __forceinline__ float dot3f(float ax, float ay, float az, float bx, f
 // the units of dipole_drive_fast.  Each charge sits at the origin plus its offset along the axis;
 // within one history segment k both move linearly, the origin by W per sample.  Steps:
 //  1. the origin's own retarded time k + t_o: |rho_k - t_o W| = T - t_o with rho_k = R_i(u) - P_j(k),
-//     T = u - k (the root of that quadratic near T - |rho_k|; k moved by one while t_o leaves
-//     [0, 1]); rn = T - t_o, rho_o = rho_k - t_o W;
+//     T = u - k (the root of that quadratic near T - |rho_k|; while t_o leaves [0, 1], k moves to
+//     the segment it points at, at most three segments tried); rn = T - t_o, rho_o = rho_k - t_o W;
 //  2. each charge's retarded time k + t_o - delta_c relative to it: with b = rho_o - s_c p_j and the
 //     charge's velocity per sample m = W + w_c p_j, A delta^2 + 2 B delta + C = 0 where A = 1 - m.m,
 //     B = rn - b.m, C = s_c (2 rho_o.p_j - s_c) (the fixed-origin quadratic with the origin's motion
@@ -601,13 +601,10 @@ __device__ bool pair_drive_mov_f32(const RunArgs &a, int b, int i, int j, int n0
     const float Bo = T - dot3f(rkx, rky, rkz, Wx, Wy, Wz);
     const float Co = (T - rk) * (T + rk);
     to = Co / (Bo + sqrtf(fmaxf(Bo * Bo - Ao * Co, 0.f)));
-    if (to < 0.f) {
-      --k;
-    } else if (to > 1.f) {
-      ++k;
-    } else {
-      break;
-    }
+    if (!(to == to)) return false;
+    if (to >= 0.f && to <= 1.f) break;
+    // the segment the root on this one's linear extension falls in (one or more samples away)
+    k += (int)fmaxf(-64.f, fminf(64.f, floorf(to)));
   }
   if (!(to >= 0.f && to <= 1.f)) return false;
   const float rn = T - to;
