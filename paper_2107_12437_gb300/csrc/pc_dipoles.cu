@@ -84,6 +84,8 @@ struct RunArgs {
   // sample: (P_hi, V_x), (P_lo, V_y), (V_z, A): the position in units of c dt as hi + lo parts,
   // the velocity in units of c, the acceleration in units of c / dt; or null
   float4 *omf;
+  // moving origins: each origin's largest distance from its first sample over the run, [B][N]
+  double *odisp;
   // per dipole: the RK4 step as an affine map y' = M y + c1 e1 + c2 e2 + c4 e4, as
   // [B][N][kTab]: M^1 .. M^kMaxBlock (row-major 2x2 each), then c1, c2, c4
   double *rk4tab;
@@ -1095,6 +1097,53 @@ __global__ void lo_origin_mirror_kernel(const RunArgs a) {
   }
 }
 
+// Moving origins: each origin's largest distance from its first sample over the run (RunArgs::odisp),
+// one thread per dipole.
+__global__ void lo_origin_disp_kernel(const RunArgs a) {
+  const int64_t H = 2 * a.n_steps + 1, nbn = (int64_t)a.B * a.N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nbn; t += (int64_t)gridDim.x * blockDim.x) {
+    const double *p = a.org_pos + t * H * 3;
+    double d2 = 0.0;
+    for (int64_t h = 1; h < H; ++h) {
+      const double ex = p[3 * h] - p[0], ey = p[3 * h + 1] - p[1], ez = p[3 * h + 2] - p[2];
+      d2 = fmax(d2, ex * ex + ey * ey + ez * ez);
+    }
+    a.odisp[t] = sqrt(d2);
+  }
+}
+
+// Moving origins, after lo_pairs_kernel: the exact closest approach over the run of every pair
+// i < j whose distance can fall to the configuration's bound in a.rstat (|R_i(0) - R_j(0)| - D_i
+// - D_j <= bound: the triangle inequality bounds it from below); the pair that attains the minimum
+// is one of them, so the minimum over these scans is the closest approach of the configuration.
+// Grid: x over pairs, y over configurations.
+__global__ void __launch_bounds__(256) lo_closest_kernel(const RunArgs a) {
+  const int N = a.N;
+  const int64_t NN = (int64_t)N * N;
+  const int64_t H = 2 * a.n_steps + 1;
+  for (int b = blockIdx.y; b < a.B; b += gridDim.y) {
+    const double bound = __longlong_as_double((long long)a.rstat[3 * b]);
+    for (int64_t ij = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ij < NN;
+         ij += (int64_t)gridDim.x * blockDim.x) {
+      const int i = (int)(ij / N), j = (int)(ij % N);
+      if (i >= j) continue;
+      const size_t bi = bidx(a, b, i), bj = bidx(a, b, j);
+      const double *Ri = a.origin + 3 * bi, *Rj = a.origin + 3 * bj;
+      const double dx = Ri[0] - Rj[0], dy = Ri[1] - Rj[1], dz = Ri[2] - Rj[2];
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      if (r - a.odisp[bi] - a.odisp[bj] > bound * (1.0 + 1e-12)) continue;
+      // squared distances, one square root
+      double r2min = r * r;
+      for (int64_t h = 0; h < H; ++h) {
+        const double *pi_ = a.org_pos + (bi * H + h) * 3, *pj_ = a.org_pos + (bj * H + h) * 3;
+        const double ex = pi_[0] - pj_[0], ey = pi_[1] - pj_[1], ez = pi_[2] - pj_[2];
+        r2min = fmin(r2min, ex * ex + ey * ey + ez * ez);
+      }
+      atomicMin(a.rstat + 3 * b, (unsigned long long)__double_as_longlong(sqrt(r2min)));
+    }
+  }
+}
+
 // Presets a.rstat to (a large distance, 0, 0): 0x7f7f... is about 1.4e306 as a double.
 __global__ void lo_rstat_init_kernel(const RunArgs a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1127,16 +1176,10 @@ __global__ void __launch_bounds__(256) lo_pairs_kernel(const RunArgs a) {
       if (i != j) {
         rmin = fmin(rmin, r);
         rmax = fmax(rmax, r);
-        if (a.org_pos) {
-          // closest approach of the two origins over the run (squared distances, one square root)
-          double r2min = r * r;
-          for (int64_t h = 0; h < H; ++h) {
-            const double *pi_ = a.org_pos + (bi * H + h) * 3, *pj_ = a.org_pos + (bj * H + h) * 3;
-            const double ex = pi_[0] - pj_[0], ey = pi_[1] - pj_[1], ez = pi_[2] - pj_[2];
-            r2min = fmin(r2min, ex * ex + ey * ey + ez * ez);
-          }
-          rmin = fmin(rmin, sqrt(r2min));
-        }
+        // moving origins: r + D_i + D_j bounds the pair's distance from above at every time, so
+        // their minimum bounds the closest approach; lo_closest_kernel then scans the pairs that
+        // can reach below it
+        if (a.org_pos) rmin = fmin(rmin, r + a.odisp[bi] + a.odisp[bj]);
       } else if (a.org_pos) {
         double v2max = 0.0;
         for (int64_t h = 0; h < H; ++h) {
@@ -1988,7 +2031,8 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   const size_t f_off = es_bytes, dl_off = f_off + f_bytes, k_off = dl_off + dl_bytes;
   const size_t part_off = k_off + k_bytes, blk_off = part_off + part_bytes, tab_off = blk_off + blk_bytes;
   const size_t geo_off = tab_off + tab_bytes, rs_off = geo_off + geo_bytes;
-  if (ctx->run_scratch.reserve(rs_off + rs_bytes) != cudaSuccess) return PC_ERR_CUDA;
+  const size_t od_off = rs_off + rs_bytes, od_bytes = motion ? al(nbn * sizeof(double)) : 0;
+  if (ctx->run_scratch.reserve(od_off + od_bytes) != cudaSuccess) return PC_ERR_CUDA;
   char *scr = (char *)ctx->run_scratch.ptr;
   pc::RunArgs a;
   memset(&a, 0, sizeof(a));
@@ -2023,6 +2067,7 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
   a.org_pos = motion ? motion->pos : nullptr;
   a.org_vel = motion ? motion->vel : nullptr;
   a.org_acc = motion ? motion->acc : nullptr;
+  a.odisp = motion ? (double *)(scr + od_off) : nullptr;
   a.status = ctx->d_status;
   if (pl.delay_out) *pl.delay_out = a.delay;
   if (pl.rk4tab_out) *pl.rk4tab_out = a.rk4tab;
@@ -2032,7 +2077,9 @@ static pc_status run_impl(pc_ctx *ctx, const pc_dipoles *dp, double dt, int64_t 
     const unsigned gx = (unsigned)std::min<int64_t>((NN + 255) / 256, 2048);
     const unsigned gy = (unsigned)std::min(dp->B, 65535);
     pc::lo_rstat_init_kernel<<<(dp->B + 255) / 256, 256, 0, st>>>(a);
+    if (motion) pc::lo_origin_disp_kernel<<<(unsigned)std::min<size_t>((nbn + 127) / 128, 4096), 128, 0, st>>>(a);
     pc::lo_pairs_kernel<<<dim3(gx, gy), 256, 0, st>>>(a);
+    if (motion) pc::lo_closest_kernel<<<dim3(gx, gy), 256, 0, st>>>(a);
   }
   pc::lo_tables_kernel<<<dp->B, 256, 0, st>>>(a);
   // block lengths and reaches back on the host, and the status of the tables (unit axes)
